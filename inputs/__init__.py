@@ -1,0 +1,17 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This package only describes the scattering problem: surface
+parametrisations (and their exact parametric derivatives) sampled at
+caller-chosen parameter points, the incident field, material constants and
+random densities.  It contains none of the solver's arithmetic (no
+quadrature weights, kernels, interpolation or operator algebra), so both the
+CPU oracle and the GPU library can consume it without sharing code.
+"""
+from .geometry import (Body, cubed_sphere, ellipsoid, star_body, superellipsoid_bar,
+                       open_cheb_nodes, sample_body)
+from .problems import (Problem, sphere_problem, CONFIG_SPHERE_SMALL, CONFIG_SPHERE_MEDIUM,
+                       random_densities, plane_wave)
+
+__all__ = ["Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar",
+           "open_cheb_nodes", "sample_body", "Problem", "sphere_problem",
+           "CONFIG_SPHERE_SMALL", "CONFIG_SPHERE_MEDIUM", "random_densities", "plane_wave"]

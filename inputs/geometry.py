@@ -1,0 +1,245 @@
+"""Synthetic closed surfaces made of curvilinear quadrilateral patches.
+
+Every body is a list of patches eta_p : [-1,1]^2 -> R^3 with
+eta_u x eta_v pointing out of the enclosed volume (Sec. III-A, the patch
+decomposition Gamma = U_p Gamma_p).  ``Body.eval(p, u, v)`` returns the
+exact point and both exact parametric tangents at arbitrary parameter
+points; nothing here depends on how the solver discretises the patches.
+
+Node layout contract (Sec. III-A, the node index l = j + Nc*i + p*Nc^2):
+``sample_body(body, u)`` returns arrays shaped [P, n, n, 3] whose entry
+[p, i, j] is eta_p(u[i], u[j]); ``open_cheb_nodes(n)`` gives the open
+Chebyshev parameter points cos((k + 1/2) pi / n) that the surface grids use.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar",
+           "open_cheb_nodes", "sample_body"]
+
+
+def open_cheb_nodes(n: int) -> np.ndarray:
+    """Parameter points of the open Chebyshev grid, cos((k+1/2)pi/n), k = 0..n-1."""
+    k = np.arange(n, dtype=np.float64)
+    return np.cos((k + 0.5) * np.pi / n)
+
+
+# Proper rotations (det = +1) taking the +z cube face to the six faces, so
+# that the outward orientation of the +z face map is preserved.
+_FACE_ROT = [
+    np.eye(3),
+    np.array([[1.0, 0, 0], [0, -1, 0], [0, 0, -1]]),      # -z
+    np.array([[0.0, 0, 1], [0, 1, 0], [-1, 0, 0]]),       # +x
+    np.array([[0.0, 0, -1], [0, 1, 0], [1, 0, 0]]),       # -x
+    np.array([[1.0, 0, 0], [0, 0, 1], [0, -1, 0]]),       # +y
+    np.array([[1.0, 0, 0], [0, 0, -1], [0, 1, 0]]),       # -y
+]
+
+
+class Body:
+    """A closed surface given by patch maps.
+
+    Each patch is a tuple (face, I, J, split): the cube face index, the
+    sub-square (I along u, J along v) and the number of sub-squares per face
+    edge.  ``radial`` maps unit directions w (shape [..., 3]) to surface
+    points and returns (x, dx/dw as a [..., 3, 3] Jacobian); the cube-face
+    direction map is q/|q|_norm with q = (tan(pi U/4), tan(pi V/4), 1) for
+    spheres, or the generalised q/|q|_p for superellipsoids.
+    """
+
+    def __init__(self, patches, surf, name: str):
+        self.patches = list(patches)
+        self._surf = surf
+        self.name = name
+
+    @property
+    def num_patches(self) -> int:
+        return len(self.patches)
+
+    def eval(self, p: int, u, v):
+        """Exact eta_p(u, v), d eta_p/du and d eta_p/dv for arrays u, v of equal shape."""
+        face, I, J, split = self.patches[p]
+        u = np.asarray(u, dtype=np.float64)
+        v = np.asarray(v, dtype=np.float64)
+        U = -1.0 + (2.0 * I + (u + 1.0)) / split
+        V = -1.0 + (2.0 * J + (v + 1.0)) / split
+        tu = np.tan(np.pi * U / 4.0)
+        tv = np.tan(np.pi * V / 4.0)
+        q = np.stack([tu, tv, np.ones_like(tu)], axis=-1)
+        dq_du = np.zeros_like(q)
+        dq_dv = np.zeros_like(q)
+        dq_du[..., 0] = (np.pi / 4.0) * (1.0 + tu * tu) / split
+        dq_dv[..., 1] = (np.pi / 4.0) * (1.0 + tv * tv) / split
+        R = _FACE_ROT[face]
+        q = q @ R.T
+        dq_du = dq_du @ R.T
+        dq_dv = dq_dv @ R.T
+        x, jac = self._surf(q)                       # x [...,3], jac [...,3,3] = dx/dq
+        xu = np.einsum("...ij,...j->...i", jac, dq_du)
+        xv = np.einsum("...ij,...j->...i", jac, dq_dv)
+        return x, xu, xv
+
+
+def _face_patches(split: int):
+    return [(f, I, J, split) for f in range(6) for I in range(split) for J in range(split)]
+
+
+def _sphere_surf(radius, axes, center):
+    A = np.diag(np.asarray(axes, dtype=np.float64)) * radius
+    c = np.asarray(center, dtype=np.float64)
+
+    def surf(q):
+        nq = np.sqrt(np.sum(q * q, axis=-1))
+        w = q / nq[..., None]
+        # d(q/|q|)/dq = (I - w w^T)/|q|
+        eye = np.eye(3)
+        dw = (eye - w[..., :, None] * w[..., None, :]) / nq[..., None, None]
+        x = w @ A.T + c
+        jac = np.einsum("ij,...jk->...ik", A, dw)
+        return x, jac
+
+    return surf
+
+
+def cubed_sphere(radius: float, split: int, center=(0.0, 0.0, 0.0)) -> Body:
+    """Equiangular cubed sphere: 6 * split^2 patches."""
+    return Body(_face_patches(split), _sphere_surf(radius, (1.0, 1.0, 1.0), center),
+                f"sphere(r={radius},split={split})")
+
+
+def ellipsoid(semi_axes, split: int, center=(0.0, 0.0, 0.0)) -> Body:
+    """Cubed-sphere map stretched along the axes: x = diag(a,b,c) q/|q|."""
+    return Body(_face_patches(split), _sphere_surf(1.0, semi_axes, center),
+                f"ellipsoid({tuple(semi_axes)},split={split})")
+
+
+def superellipsoid_bar(half_lengths, exponent: int, split_per_face, center=(0.0, 0.0, 0.0)) -> Body:
+    """|x/A|^e + |y/B|^e + |z/C|^e = 1 (e even): x = diag(A,B,C) q/|q|_e.
+
+    ``split_per_face`` is an int (same split on every face) or a list of six
+    (nu, nv) pairs; faces are listed in the order +z, -z, +x, -x, +y, -y.
+    """
+    e = int(exponent)
+    if e % 2:
+        raise ValueError("exponent must be even")
+    A = np.diag(np.asarray(half_lengths, dtype=np.float64))
+    c = np.asarray(center, dtype=np.float64)
+
+    def surf(q):
+        s = np.sum(q ** e, axis=-1)
+        nrm = s ** (1.0 / e)
+        w = q / nrm[..., None]
+        # d(q/|q|_e)/dq = I/|q|_e - q (q^{e-1})^T / |q|_e^{e+1}
+        g = q ** (e - 1)
+        eye = np.eye(3)
+        dw = eye / nrm[..., None, None] - q[..., :, None] * g[..., None, :] / (nrm ** (e + 1))[..., None, None]
+        x = w @ A.T + c
+        jac = np.einsum("ij,...jk->...ik", A, dw)
+        return x, jac
+
+    if isinstance(split_per_face, int):
+        patches = _face_patches(split_per_face)
+        return Body(patches, surf, f"superellipsoid({tuple(half_lengths)},e={e})")
+    patches = []
+    for f, (nu, nv) in enumerate(split_per_face):
+        for I in range(nu):
+            for J in range(nv):
+                patches.append((f, I, J, (nu, nv)))
+    body = Body(patches, surf, f"superellipsoid({tuple(half_lengths)},e={e})")
+    body.eval = _anisotropic_eval(body, surf)
+    return body
+
+
+def _anisotropic_eval(body, surf):
+    def ev(p, u, v):
+        face, I, J, (nu, nv) = body.patches[p]
+        u = np.asarray(u, dtype=np.float64)
+        v = np.asarray(v, dtype=np.float64)
+        U = -1.0 + (2.0 * I + (u + 1.0)) / nu
+        V = -1.0 + (2.0 * J + (v + 1.0)) / nv
+        tu = np.tan(np.pi * U / 4.0)
+        tv = np.tan(np.pi * V / 4.0)
+        q = np.stack([tu, tv, np.ones_like(tu)], axis=-1)
+        dq_du = np.zeros_like(q)
+        dq_dv = np.zeros_like(q)
+        dq_du[..., 0] = (np.pi / 4.0) * (1.0 + tu * tu) / nu
+        dq_dv[..., 1] = (np.pi / 4.0) * (1.0 + tv * tv) / nv
+        R = _FACE_ROT[face]
+        x, jac = surf(q @ R.T)
+        xu = np.einsum("...ij,...j->...i", jac, dq_du @ R.T)
+        xv = np.einsum("...ij,...j->...i", jac, dq_dv @ R.T)
+        return x, xu, xv
+    return ev
+
+
+def _real_ylm_cartesian(l, m, w):
+    """Unnormalised real solid-harmonic-like smooth functions of the unit vector w.
+
+    Only used to perturb star-shaped bodies; any smooth function works, so a
+    simple polynomial family in (x, y, z) of degree l is used.
+    """
+    x, y, z = w[..., 0], w[..., 1], w[..., 2]
+    terms = {
+        (1, -1): y, (1, 0): z, (1, 1): x,
+        (2, -2): x * y, (2, -1): y * z, (2, 0): 3 * z * z - 1, (2, 1): x * z, (2, 2): x * x - y * y,
+        (3, -3): y * (3 * x * x - y * y), (3, -2): x * y * z, (3, -1): y * (5 * z * z - 1),
+        (3, 0): z * (5 * z * z - 3), (3, 1): x * (5 * z * z - 1), (3, 2): z * (x * x - y * y),
+        (3, 3): x * (x * x - 3 * y * y),
+        (4, -4): x * y * (x * x - y * y), (4, -3): y * z * (3 * x * x - y * y), (4, -2): x * y * (7 * z * z - 1),
+        (4, -1): y * z * (7 * z * z - 3), (4, 0): 35 * z ** 4 - 30 * z * z + 3, (4, 1): x * z * (7 * z * z - 3),
+        (4, 2): (x * x - y * y) * (7 * z * z - 1), (4, 3): x * z * (x * x - 3 * y * y),
+        (4, 4): x ** 4 - 6 * x * x * y * y + y ** 4,
+    }
+    return terms[(l, m)]
+
+
+def star_body(radius: float, coeffs: dict, split: int, center=(0.0, 0.0, 0.0)) -> Body:
+    """r(w) = radius (1 + sum c_lm Y_lm(w)) along the cubed-sphere direction w."""
+    c = np.asarray(center, dtype=np.float64)
+    items = sorted(coeffs.items())
+    h = 1e-6
+
+    def rad(w):
+        r = np.ones(w.shape[:-1])
+        for (l, m), cl in items:
+            r = r + cl * _real_ylm_cartesian(l, m, w)
+        return radius * r
+
+    def surf(q):
+        nq = np.sqrt(np.sum(q * q, axis=-1))
+        w = q / nq[..., None]
+        eye = np.eye(3)
+        dw = (eye - w[..., :, None] * w[..., None, :]) / nq[..., None, None]
+        r = rad(w)
+        # gradient of r(w) along w by central differences on the polynomial (exact to ~1e-10)
+        grad = np.zeros(w.shape)
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            grad[..., k] = (rad(w + e) - rad(w - e)) / (2 * h)
+        x = r[..., None] * w + c
+        # dx/dw = r I + w grad^T ; dx/dq = dx/dw dw/dq
+        dxdw = r[..., None, None] * eye + w[..., :, None] * grad[..., None, :]
+        jac = np.einsum("...ij,...jk->...ik", dxdw, dw)
+        return x, jac
+
+    return Body(_face_patches(split), surf, f"star(r={radius})")
+
+
+def sample_body(body: Body, u: np.ndarray):
+    """Sample every patch on the tensor grid u x u.
+
+    Returns (x, xu, xv), each shaped [P, n, n, 3] with entry [p, i, j] at
+    (u[i], u[j]).
+    """
+    u = np.asarray(u, dtype=np.float64)
+    U, V = np.meshgrid(u, u, indexing="ij")
+    P = body.num_patches
+    n = u.size
+    x = np.empty((P, n, n, 3))
+    xu = np.empty_like(x)
+    xv = np.empty_like(x)
+    for p in range(P):
+        x[p], xu[p], xv[p] = body.eval(p, U, V)
+    return x, xu, xv

@@ -1,0 +1,98 @@
+"""Scattering problems: body, discretisation sizes, materials and excitation.
+
+Conventions: time dependence e^{-i omega t}, c = 1, so kappa_s = omega
+sqrt(eps_s mu_s) (Sec. II, the Maxwell systems for the interior and exterior
+media).  Wavelengths are exterior wavelengths lambda_e = 2 pi / kappa_e.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .geometry import Body, cubed_sphere, open_cheb_nodes, sample_body
+
+__all__ = ["Problem", "sphere_problem", "CONFIG_SPHERE_SMALL", "CONFIG_SPHERE_MEDIUM",
+           "random_densities", "plane_wave"]
+
+
+@dataclass
+class Problem:
+    body: Body
+    nc: int                      # Chebyshev nodes per patch direction
+    ng: int                      # oversampled geometry grid per patch direction
+    eps_ext: float
+    eps_int: float
+    mu_ext: float = 1.0
+    mu_int: float = 1.0
+    omega: float = 2 * np.pi
+    name: str = ""
+    _cache: dict = field(default_factory=dict, repr=False)
+
+    @property
+    def k_ext(self) -> float:
+        return self.omega * np.sqrt(self.eps_ext * self.mu_ext)
+
+    @property
+    def k_int(self) -> float:
+        return self.omega * np.sqrt(self.eps_int * self.mu_int)
+
+    @property
+    def num_patches(self) -> int:
+        return self.body.num_patches
+
+    @property
+    def n(self) -> int:
+        return self.num_patches * self.nc * self.nc
+
+    def nodes(self):
+        """(x, x_u, x_v) flattened to [N, 3] in node order l = j + Nc i + p Nc^2."""
+        if "nodes" not in self._cache:
+            x, xu, xv = sample_body(self.body, open_cheb_nodes(self.nc))
+            self._cache["nodes"] = tuple(a.reshape(-1, 3).copy() for a in (x, xu, xv))
+        return self._cache["nodes"]
+
+    def fine(self):
+        """Oversampled geometry [P, Ng, Ng, 9] = (x, x_u, x_v) on the Ng open Chebyshev grid."""
+        if "fine" not in self._cache:
+            x, xu, xv = sample_body(self.body, open_cheb_nodes(self.ng))
+            self._cache["fine"] = np.ascontiguousarray(np.concatenate([x, xu, xv], axis=-1))
+        return self._cache["fine"]
+
+
+def sphere_problem(radius: float, split: int, nc: int, eps_int: float, ng: int | None = None,
+                   eps_ext: float = 1.0, wavelength: float = 1.0, name: str = "") -> Problem:
+    omega = 2 * np.pi / (wavelength * np.sqrt(eps_ext))
+    return Problem(body=cubed_sphere(radius, split), nc=nc, ng=ng or max(2 * nc, 24),
+                   eps_ext=eps_ext, eps_int=eps_int, omega=omega, name=name)
+
+
+def CONFIG_SPHERE_SMALL(nc: int = 8, ng: int | None = None) -> Problem:
+    """Sphere of radius lambda_e/2 (kappa_e a = pi), eps_r = 2.25, 6 patches x Nc^2 nodes."""
+    return sphere_problem(0.5, 1, nc, 2.25, ng=ng, name="sphere_r0.5_eps2.25_P6")
+
+
+def CONFIG_SPHERE_MEDIUM(nc: int = 10, ng: int | None = None) -> Problem:
+    """Sphere of radius 2 lambda_e, eps_r = 4, 96 patches (4x4 per cube face) x Nc^2 nodes."""
+    return sphere_problem(2.0, 4, nc, 4.0, ng=ng, name="sphere_r2_eps4_P96")
+
+
+def random_densities(n: int, seed: int, batch: int | None = None) -> np.ndarray:
+    """Complex Gaussian CN(0,1) densities y = [m1, m2, j1, j2], shape [4, N] (or [B, 4, N])."""
+    rng = np.random.default_rng(seed)
+    shape = (4, n) if batch is None else (batch, 4, n)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0)
+
+
+def plane_wave(x: np.ndarray, k_ext: float, omega: float, mu_ext: float = 1.0,
+               direction=(0.0, 0.0, 1.0), polarization=(1.0, 0.0, 0.0)):
+    """Incident plane wave E = p e^{i k d.x}, H = (k/(omega mu)) (d x p) e^{i k d.x}.
+
+    Returns an array [6, N] complex: (Ex, Ey, Ez, Hx, Hy, Hz) at the points x [N, 3].
+    """
+    d = np.asarray(direction, dtype=np.float64)
+    p = np.asarray(polarization, dtype=np.float64)
+    ph = np.exp(1j * k_ext * (x @ d))
+    E = p[:, None] * ph[None, :]
+    H = (k_ext / (omega * mu_ext)) * np.cross(d, p)[:, None] * ph[None, :]
+    return np.concatenate([E, H], axis=0)

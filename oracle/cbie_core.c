@@ -1,0 +1,347 @@
+/*
+ * CPU FP64 oracle core: the unaccelerated Chebyshev boundary-integral (CBIE)
+ * kernel rows of Paul & Sideris, "Accelerated 3D Maxwell Integral Equation
+ * Solver using the Interpolated Factored Green Function Method".
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the GPU product path may call,
+ * link or load this file; it exists so tests, smoke() and the benchmark's
+ * CPU-baseline leg can check the CUDA library against a plain, slow,
+ * independent implementation.  It shares no code with the CUDA library.
+ *
+ * For each requested target x_l this fills four dense rows K_s[l][m]
+ * (s = S_e, S_i, D_e, D_i) such that S_s[phi](x_l) = sum_m K_s[l][m] phi_m
+ * and D_s[phi](x_l) likewise, where
+ *   - for patches p in the regular set R_l (Eq. patch_reg): the Fejer rule
+ *     of Sec. III-C, K = G(x_l, x_m) * omega_m, omega_m = J w_i w_j;
+ *   - for patches p in the singular set S_l (Eq. patch_sing): the
+ *     precomputed-moment rule of Sec. III-D: beta_mn (Eq. int_moments) by
+ *     the clustering change of variables (Eqs. mk_cov_1, mk_cov_2, cov) and
+ *     an N_beta-point Fejer rule (Eq. int_moments_cov), then
+ *     S_p(x_l) = sum_mn a_mn beta_mn (Eq. rp_exp) with a_mn the Chebyshev
+ *     coefficients of phi on the patch (Eq. phi_cheby), i.e. the row entry
+ *     for node (i', j') of p is sum_mn beta_mn A[m][i'] A[n][j'].
+ * The normal-derivative kernel is dG/dn(x) = n(x).(x-y)(i k r - 1) e^{ikr}/(4 pi r^3).
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC cbie_core.c -o libcbie_oracle.so -lm
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef double _Complex cplx;
+
+/* Chebyshev polynomials T_0..T_{n-1} at t by the three-term recurrence. */
+static void cheb_T(double t, int n, double *T) {
+  if (n > 0) T[0] = 1.0;
+  if (n > 1) T[1] = t;
+  for (int k = 2; k < n; ++k) T[k] = 2.0 * t * T[k - 1] - T[k - 2];
+}
+
+/* Patch geometry as the Chebyshev interpolant of its oversampled samples:
+ * coef is [ng][ng][9] (x, x_u, x_v), value(u,v) = sum_mn coef[m][n] T_m(u) T_n(v). */
+typedef struct {
+  const double *coef;
+  int ng;
+} patch_geom;
+
+static void geom_eval(const patch_geom *g, double u, double v, int nch, double *out) {
+  double Tu[64], Tv[64];
+  cheb_T(u, g->ng, Tu);
+  cheb_T(v, g->ng, Tv);
+  for (int c = 0; c < nch; ++c) out[c] = 0.0;
+  for (int m = 0; m < g->ng; ++m) {
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int n = 0; n < g->ng; ++n) {
+      const double *cf = g->coef + ((size_t)m * g->ng + n) * 9;
+      for (int c = 0; c < nch; ++c) acc[c] += cf[c] * Tv[n];
+    }
+    for (int c = 0; c < nch; ++c) out[c] += acc[c] * Tu[m];
+  }
+}
+
+/* ---------------- closest point (Eq. dist_min): golden-section search ---------------- */
+static const double GOLD = 0.6180339887498948482;
+
+typedef struct {
+  const patch_geom *g;
+  const double *x;
+  double u;
+} inner_ctx;
+
+static double dist2_uv(const patch_geom *g, const double *x, double u, double v) {
+  double y[3];
+  geom_eval(g, u, v, 3, y);
+  double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  return dx * dx + dy * dy + dz * dz;
+}
+
+/* min over v in [a, b] of |x - eta(u, v)|^2 by golden section, fixed iteration count */
+static double golden_v(const patch_geom *g, const double *x, double u, double a, double b,
+                       int iters, double *vbest) {
+  double c = b - GOLD * (b - a), d = a + GOLD * (b - a);
+  double fc = dist2_uv(g, x, u, c), fd = dist2_uv(g, x, u, d);
+  for (int it = 0; it < iters; ++it) {
+    if (fc < fd) {
+      b = d; d = c; fd = fc; c = b - GOLD * (b - a); fc = dist2_uv(g, x, u, c);
+    } else {
+      a = c; c = d; fc = fd; d = a + GOLD * (b - a); fd = dist2_uv(g, x, u, d);
+    }
+  }
+  *vbest = 0.5 * (a + b);
+  return dist2_uv(g, x, u, *vbest);
+}
+
+static double golden_uv(const patch_geom *g, const double *x, double ua, double ub, double va,
+                        double vb, int iters, double *ubest, double *vbest) {
+  double a = ua, b = ub;
+  double vt;
+  double c = b - GOLD * (b - a), d = a + GOLD * (b - a);
+  double fc = golden_v(g, x, c, va, vb, iters, &vt), fd = golden_v(g, x, d, va, vb, iters, &vt);
+  for (int it = 0; it < iters; ++it) {
+    if (fc < fd) {
+      b = d; d = c; fd = fc; c = b - GOLD * (b - a); fc = golden_v(g, x, c, va, vb, iters, &vt);
+    } else {
+      a = c; c = d; fc = fd; d = a + GOLD * (b - a); fd = golden_v(g, x, d, va, vb, iters, &vt);
+    }
+  }
+  *ubest = 0.5 * (a + b);
+  double f = golden_v(g, x, *ubest, va, vb, iters, vbest);
+  return f;
+}
+
+static double snap_edge(double t) {
+  if (t > 1.0 - 1e-9) return 1.0;
+  if (t < -1.0 + 1e-9) return -1.0;
+  return t;
+}
+
+/* ---------------- clustering change of variables (Eqs. mk_cov_1, mk_cov_2, cov) ---------------- */
+static double nu_f(double t, double d) {
+  double a = (M_PI - t) / M_PI;
+  return (1.0 / d - 0.5) * a * a * a + (1.0 / d) * ((t - M_PI) / M_PI) + 0.5;
+}
+static double nu_df(double t, double d) {
+  double a = (M_PI - t) / M_PI;
+  return -(1.0 / d - 0.5) * 3.0 * a * a / M_PI + 1.0 / (d * M_PI);
+}
+/* w(t) = 2 pi nu(t)^d / (nu(t)^d + nu(2pi - t)^d) and its derivative */
+static void w_f(double t, double d, double *w, double *dw) {
+  double n1 = nu_f(t, d), n2 = nu_f(2.0 * M_PI - t, d);
+  double a = pow(n1, d), b = pow(n2, d);
+  double da = d * pow(n1, d - 1.0) * nu_df(t, d);
+  double db = -d * pow(n2, d - 1.0) * nu_df(2.0 * M_PI - t, d);
+  *w = 2.0 * M_PI * a / (a + b);
+  *dw = 2.0 * M_PI * (da * b - a * db) / ((a + b) * (a + b));
+}
+/* xi_alpha(tau) and d xi_alpha / d tau on tau in [-1, 1] */
+static void xi_f(double alpha, double tau, double d, double *xi, double *mu) {
+  double w, dw;
+  if (alpha == 1.0) {
+    w_f(M_PI * fabs((tau - 1.0) * 0.5), d, &w, &dw);
+    *xi = alpha - ((1.0 + alpha) / M_PI) * w;
+    *mu = dw;
+  } else if (alpha == -1.0) {
+    w_f(M_PI * fabs((tau + 1.0) * 0.5), d, &w, &dw);
+    *xi = alpha + ((1.0 - alpha) / M_PI) * w;
+    *mu = dw;
+  } else {
+    double s = (tau > 0) ? 1.0 : ((tau < 0) ? -1.0 : 0.0);
+    w_f(M_PI * fabs(tau), d, &w, &dw);
+    *xi = alpha + ((s - alpha) / M_PI) * w;
+    *mu = (s - alpha) * s * dw;
+    if (s == 0.0) *mu = 0.0;
+  }
+}
+
+/* The four kernels at (x, n_x; y): G_e, G_i, dG_e/dn_x, dG_i/dn_x. r == 0 -> zeros. */
+static void kernels4(const double *x, const double *nx, const double *y, double ke, double ki,
+                     cplx *K) {
+  double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+  double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+  if (r == 0.0) {
+    K[0] = K[1] = K[2] = K[3] = 0.0;
+    return;
+  }
+  double nd = nx[0] * d0 + nx[1] * d1 + nx[2] * d2;
+  double kk[2] = {ke, ki};
+  for (int s = 0; s < 2; ++s) {
+    cplx g = cexp(I * kk[s] * r) / (4.0 * M_PI * r);
+    K[s] = g;
+    K[2 + s] = nd * (I * kk[s] * r - 1.0) * g / (r * r);
+  }
+}
+
+/*
+ * Four kernel rows for the targets rows[0..nrows-1].
+ *   nodes, normals: [N][3]; qw: [N] Fejer-times-Jacobian weights omega_m;
+ *   fine_coef: [P][ng][ng][9] Chebyshev coefficients of (x, x_u, x_v) per patch;
+ *   gap: [P] margin added to delta before a patch is ruled regular from its
+ *        node distances alone (the node-grid covering radius);
+ *   u_nodes: [nc] open Chebyshev nodes; A: [nc][nc] values-to-coefficients map;
+ *   t_beta, w_beta: [nbeta] Fejer nodes and weights for the moment rule.
+ * Output K: [4][nrows][N] complex (interleaved re, im), sing: [nrows] |S_l|.
+ */
+int ora_kernel_rows(int P, int nc, int ng, const double *nodes, const double *normals,
+                    const double *qw, const double *fine_coef, const double *gap,
+                    const double *u_nodes, const double *A, double ke, double ki, double delta,
+                    int nbeta, const double *t_beta, const double *w_beta, double cov_d,
+                    int gs_iters, int nrows, const int *rows, double *K_out, int *sing) {
+  const int npp = nc * nc;
+  const size_t N = (size_t)P * npp;
+  if (ng > 64 || nc > 64 || nbeta > 256) return -1;
+  cplx *K = (cplx *)K_out;
+  memset(K_out, 0, sizeof(cplx) * 4 * (size_t)nrows * N);
+
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int r = 0; r < nrows; ++r) {
+    const int l = rows[r];
+    const double *x = nodes + 3 * (size_t)l;
+    const double *nx = normals + 3 * (size_t)l;
+    const int pl = l / npp;
+    int nsing = 0;
+    double *ub = malloc(sizeof(double) * nbeta * 2);
+    double *vb = malloc(sizeof(double) * nbeta * 2);
+    double *Tu = malloc(sizeof(double) * nbeta * nc);
+    double *Tv = malloc(sizeof(double) * nbeta * nc);
+    cplx *f = malloc(sizeof(cplx) * 4 * nbeta * nbeta);
+    cplx *tmp = malloc(sizeof(cplx) * 4 * nbeta * nc);
+    cplx *beta = malloc(sizeof(cplx) * 4 * nc * nc);
+    cplx *tmp2 = malloc(sizeof(cplx) * 4 * nc * nc);
+    for (int p = 0; p < P; ++p) {
+      patch_geom g = {fine_coef + (size_t)p * ng * ng * 9, ng};
+      double uc, vc;
+      int singular = 0;
+      if (p == pl) {
+        /* target is a node of this patch: its own parameters are the closest point */
+        int il = (l % npp) / nc, jl = l % nc;
+        uc = u_nodes[il];
+        vc = u_nodes[jl];
+        singular = 1;
+      } else {
+        double dmin = INFINITY;
+        int im = 0, jm = 0;
+        for (int i = 0; i < nc; ++i)
+          for (int j = 0; j < nc; ++j) {
+            const double *y = nodes + 3 * ((size_t)p * npp + i * nc + j);
+            double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+            double dd = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            if (dd < dmin) { dmin = dd; im = i; jm = j; }
+          }
+        if (dmin <= delta + gap[p]) {
+          /* bracket from the neighbouring nodes (the grid is descending in u) */
+          double ua = (im == nc - 1) ? -1.0 : u_nodes[im + 1];
+          double uz = (im == 0) ? 1.0 : u_nodes[im - 1];
+          double va = (jm == nc - 1) ? -1.0 : u_nodes[jm + 1];
+          double vz = (jm == 0) ? 1.0 : u_nodes[jm - 1];
+          double d2 = golden_uv(&g, x, ua, uz, va, vz, gs_iters, &uc, &vc);
+          uc = snap_edge(uc);
+          vc = snap_edge(vc);
+          (void)d2;
+          double dist = sqrt(dist2_uv(&g, x, uc, vc));
+          singular = dist <= delta;
+        }
+      }
+      const size_t m0 = (size_t)p * npp;
+      if (!singular) {
+        for (int mm = 0; mm < npp; ++mm) {
+          cplx k4[4];
+          kernels4(x, nx, nodes + 3 * (m0 + mm), ke, ki, k4);
+          for (int s = 0; s < 4; ++s) K[((size_t)s * nrows + r) * N + m0 + mm] = k4[s] * qw[m0 + mm];
+        }
+        continue;
+      }
+      ++nsing;
+      /* For the target's own patch the kernel is evaluated at the interpolated
+       * surface point eta_p(u_i, v_j) itself, so the target lies exactly on the
+       * surface being integrated (reading R12). */
+      double xs[3] = {x[0], x[1], x[2]};
+      if (p == pl) geom_eval(&g, uc, vc, 3, xs);
+      /* clustered nodes and their Jacobians mu (Eq. int_moments_1) */
+      for (int i = 0; i < nbeta; ++i) {
+        xi_f(uc, t_beta[i], cov_d, &ub[2 * i], &ub[2 * i + 1]);
+        xi_f(vc, t_beta[i], cov_d, &vb[2 * i], &vb[2 * i + 1]);
+        cheb_T(ub[2 * i], nc, Tu + (size_t)i * nc);
+        cheb_T(vb[2 * i], nc, Tv + (size_t)i * nc);
+      }
+      /* integrand samples f_ij = K(x, eta(u_i, v_j)) J mu_i mu_j w_i w_j (Eq. int_moments_cov) */
+      for (int i = 0; i < nbeta; ++i)
+        for (int j = 0; j < nbeta; ++j) {
+          double gv[9];
+          geom_eval(&g, ub[2 * i], vb[2 * j], 9, gv);
+          double cx = gv[4] * gv[8] - gv[5] * gv[7];
+          double cy = gv[5] * gv[6] - gv[3] * gv[8];
+          double cz = gv[3] * gv[7] - gv[4] * gv[6];
+          double J = sqrt(cx * cx + cy * cy + cz * cz);
+          double wt = J * ub[2 * i + 1] * vb[2 * j + 1] * w_beta[i] * w_beta[j];
+          cplx k4[4];
+          kernels4(xs, nx, gv, ke, ki, k4);
+          for (int s = 0; s < 4; ++s) f[((size_t)s * nbeta + i) * nbeta + j] = k4[s] * wt;
+        }
+      /* beta_mn = sum_ij f_ij T_m(u_i) T_n(v_j) */
+      for (int s = 0; s < 4; ++s) {
+        for (int i = 0; i < nbeta; ++i)
+          for (int n = 0; n < nc; ++n) {
+            cplx acc = 0;
+            for (int j = 0; j < nbeta; ++j) acc += f[((size_t)s * nbeta + i) * nbeta + j] * Tv[(size_t)j * nc + n];
+            tmp[((size_t)s * nbeta + i) * nc + n] = acc;
+          }
+        for (int m = 0; m < nc; ++m)
+          for (int n = 0; n < nc; ++n) {
+            cplx acc = 0;
+            for (int i = 0; i < nbeta; ++i) acc += Tu[(size_t)i * nc + m] * tmp[((size_t)s * nbeta + i) * nc + n];
+            beta[((size_t)s * nc + m) * nc + n] = acc;
+          }
+        /* node weights W[i'][j'] = sum_mn beta_mn A[m][i'] A[n][j'] */
+        for (int m = 0; m < nc; ++m)
+          for (int jp = 0; jp < nc; ++jp) {
+            cplx acc = 0;
+            for (int n = 0; n < nc; ++n) acc += beta[((size_t)s * nc + m) * nc + n] * A[n * nc + jp];
+            tmp2[((size_t)s * nc + m) * nc + jp] = acc;
+          }
+        for (int ip = 0; ip < nc; ++ip)
+          for (int jp = 0; jp < nc; ++jp) {
+            cplx acc = 0;
+            for (int m = 0; m < nc; ++m) acc += A[m * nc + ip] * tmp2[((size_t)s * nc + m) * nc + jp];
+            K[((size_t)s * nrows + r) * N + m0 + (size_t)ip * nc + jp] = acc;
+          }
+      }
+    }
+    sing[r] = nsing;
+    free(ub); free(vb); free(Tu); free(Tv); free(f); free(tmp); free(beta); free(tmp2);
+  }
+  return 0;
+}
+
+/* Closest point of x to patch p (exposed for tests): returns dist, writes (u, v). */
+double ora_closest_point(int nc, int ng, const double *patch_nodes, const double *coef,
+                         const double *u_nodes, const double *x, int gs_iters, double *uv) {
+  patch_geom g = {coef, ng};
+  double dmin = INFINITY;
+  int im = 0, jm = 0;
+  for (int i = 0; i < nc; ++i)
+    for (int j = 0; j < nc; ++j) {
+      const double *y = patch_nodes + 3 * (i * nc + j);
+      double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+      double dd = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      if (dd < dmin) { dmin = dd; im = i; jm = j; }
+    }
+  double ua = (im == nc - 1) ? -1.0 : u_nodes[im + 1];
+  double uz = (im == 0) ? 1.0 : u_nodes[im - 1];
+  double va = (jm == nc - 1) ? -1.0 : u_nodes[jm + 1];
+  double vz = (jm == 0) ? 1.0 : u_nodes[jm - 1];
+  double uc, vc;
+  golden_uv(&g, x, ua, uz, va, vz, gs_iters, &uc, &vc);
+  uv[0] = snap_edge(uc);
+  uv[1] = snap_edge(vc);
+  return sqrt(dist2_uv(&g, x, uv[0], uv[1]));
+}
+
+/* The change of variables itself (exposed for tests). */
+void ora_cov(double alpha, int n, const double *tau, double d, double *xi, double *mu) {
+  for (int i = 0; i < n; ++i) xi_f(alpha, tau[i], d, &xi[i], &mu[i]);
+}

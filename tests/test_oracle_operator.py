@@ -1,0 +1,107 @@
+"""Pins for the oracle's scalar operators S and D (Eqs. sl_scalar, dl_scalar)
+and its singular quadrature (Sec. III-D) against closed forms on the sphere."""
+import numpy as np
+import pytest
+from scipy.special import sph_harm_y, spherical_jn, spherical_yn
+
+from inputs import sphere_problem
+from oracle import cbie
+
+
+def ylm_real(l, m, x):
+    r = np.linalg.norm(x, axis=1)
+    th = np.arccos(np.clip(x[:, 2] / r, -1, 1))
+    ph = np.arctan2(x[:, 1], x[:, 0])
+    Y = sph_harm_y(l, abs(m), th, ph)
+    return np.real(Y) if m >= 0 else np.imag(Y)
+
+
+def eigenvalues(l, k, a):
+    """S[Y] = i k a^2 j_l h_l Y and p.v. dS/dn[Y] = (i k^2 a^2 / 2)(j_l' h_l + j_l h_l') Y."""
+    x = k * a
+    j, dj = spherical_jn(l, x), spherical_jn(l, x, derivative=True)
+    h = j + 1j * spherical_yn(l, x)
+    dh = dj + 1j * spherical_yn(l, x, derivative=True)
+    return 1j * k * a * a * j * h, 0.5j * k * k * a * a * (dj * h + j * dh)
+
+
+@pytest.fixture(scope="module")
+def rows_sphere():
+    a = 1.0
+    prob = sphere_problem(a, 2, 10, 4.0)
+    prob.omega = 2.0                       # k_e = 2, k_i = 4
+    g = cbie.geometry_of(prob)
+    qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=48, cov_d=4.0)
+    rows = np.arange(0, g.x.shape[0], 37)
+    K, sing = cbie.kernel_rows(prob, g, rows, qp)
+    return prob, g, rows, K, sing, a
+
+
+@pytest.mark.parametrize("l,m", [(0, 0), (1, 1), (2, -1), (3, 2), (4, 0)])
+def test_sphere_eigen_relations(rows_sphere, l, m):
+    prob, g, rows, K, sing, a = rows_sphere
+    Y = ylm_real(l, m, g.x)
+    for s, k in enumerate([prob.k_ext, prob.k_int]):
+        lamS, lamD = eigenvalues(l, k, a)
+        scale = np.abs(Y).max()
+        eS = np.abs(K[s] @ Y - lamS * Y[rows]).max() / (abs(lamS) * scale)
+        eD = np.abs(K[2 + s] @ Y - lamD * Y[rows]).max() / (abs(lamD) * scale)
+        assert eS < 1e-4, (l, s, eS)
+        assert eD < 1e-4, (l, s, eD)
+
+
+def test_jump_identity_from_closed_forms():
+    # interior-minus-exterior normal derivative of S[Y_l] equals Y_l (Wronskian):
+    # a check on the eigenvalue formulas used above, independent of the oracle
+    for l in range(5):
+        x = 2.7
+        j, dj = spherical_jn(l, x), spherical_jn(l, x, derivative=True)
+        h = j + 1j * spherical_yn(l, x)
+        dh = dj + 1j * spherical_yn(l, x, derivative=True)
+        k, a = 2.7, 1.0
+        inner = 1j * k * a * a * k * dj * h
+        outer = 1j * k * a * a * k * j * dh
+        assert abs((inner - outer) - 1.0) < 1e-12
+
+
+def test_singular_sets_contain_own_patch(rows_sphere):
+    _, _, _, _, sing, _ = rows_sphere
+    assert np.all(sing >= 1)
+
+
+def test_moment_rule_reduces_to_fejer_for_smooth_integrands():
+    # For a patch far from the target, the moment rule (Eq. int_moments_cov)
+    # and the plain Fejer rule (Eq. non_sing) integrate the same smooth
+    # integrand: forcing every patch into the singular set must not change
+    # the rows beyond quadrature error.
+    prob = sphere_problem(1.0, 2, 10, 4.0)
+    prob.omega = 2.0
+    g = cbie.geometry_of(prob)
+    rows = np.array([0, 555, 1234])
+    K1, s1 = cbie.kernel_rows(prob, g, rows, cbie.QuadParams(delta=0.3, n_beta=48))
+    K2, s2 = cbie.kernel_rows(prob, g, rows, cbie.QuadParams(delta=10.0, n_beta=48))
+    assert np.all(s2 == prob.num_patches) and np.all(s1 < prob.num_patches)
+    phi = cbie.densities(np.ones((4, g.x.shape[0])) * (1 + 0.5j), g)[0]
+    for s in range(4):
+        v1, v2 = K1[s] @ phi, K2[s] @ phi
+        assert np.abs(v1 - v2).max() < 1e-5 * np.abs(v1).max()
+
+
+def test_closest_point_against_dense_sampling():
+    prob = sphere_problem(1.0, 2, 8, 4.0)
+    body = prob.body
+    x, _, _ = prob.nodes()
+    rng = np.random.default_rng(7)
+    t = np.linspace(-1, 1, 801)
+    U, V = np.meshgrid(t, t, indexing="ij")
+    for _ in range(4):
+        p = int(rng.integers(prob.num_patches))
+        l = int(rng.integers(x.shape[0]))
+        if l // 64 == p:
+            continue
+        d, uv = cbie.closest_point(prob, p, x[l])
+        xs, _, _ = body.eval(p, U, V)
+        dense = np.linalg.norm(xs - x[l], axis=-1).min()
+        assert d <= dense + 1e-9
+        assert d >= dense - 5e-3
+        assert -1 <= uv[0] <= 1 and -1 <= uv[1] <= 1

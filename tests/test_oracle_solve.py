@@ -1,0 +1,87 @@
+"""Pins for the oracle's Mie series, GMRES and the full N-Mueller solve.
+
+The solve is pinned to the Mie series of a dielectric sphere (Sec. IV-B):
+that checks the operator algebra (R, K, T from S and D), the right-hand
+side and the field representation together.
+"""
+import numpy as np
+import pytest
+
+from inputs import CONFIG_SPHERE_SMALL, plane_wave
+from oracle import cbie, mie
+
+
+def test_mie_incident_expansion_is_the_plane_wave():
+    k, om = 2 * np.pi, 2 * np.pi
+    pts = mie.fibonacci_sphere(60, 0.41)
+    E, H = mie.fields(pts, "inc", k, 3 * np.pi, 0.5, om)
+    ph = np.exp(1j * k * pts[:, 2])
+    assert np.abs(E[:, 0] - ph).max() < 1e-12 and np.abs(E[:, 1:]).max() < 1e-12
+    assert np.abs(H[:, 1] - (k / om) * ph).max() < 1e-12
+
+
+def test_mie_tangential_continuity_and_optical_theorem():
+    k, ki, a, om = 2 * np.pi, 3 * np.pi, 0.5, 2 * np.pi
+    p = mie.fibonacci_sphere(50, a)
+    n = p / a
+    Ei, Hi = mie.fields(p, "inc", k, ki, a, om)
+    Es, Hs = mie.fields(p, "sca", k, ki, a, om)
+    E1, H1 = mie.fields(p, "int", k, ki, a, om)
+    assert np.abs(np.cross(n, Ei + Es - E1)).max() < 1e-12
+    assert np.abs(np.cross(n, Hi + Hs - H1)).max() < 1e-12
+    qext, qsca = mie.efficiencies(k, ki, a)
+    assert abs(qext - qsca) < 1e-12 * qext
+
+
+def test_mie_limits():
+    # index-matched sphere does not scatter; small spheres follow the Rayleigh limit
+    an, bn, cn, dn = mie.coefficients(2.0, 2.0, 1.0)
+    assert np.abs(an).max() < 1e-14 and np.abs(bn).max() < 1e-14
+    assert np.allclose(cn, 1) and np.allclose(dn, 1)
+    x, m = 1e-2, 1.7
+    an, _, _, _ = mie.coefficients(1.0, m, x)
+    ray = -2j / 3 * x ** 3 * (m * m - 1) / (m * m + 2)
+    assert abs(an[0] - ray) < 1e-3 * abs(ray)
+
+
+def test_gmres_matches_dense_solve():
+    rng = np.random.default_rng(3)
+    n = 200
+    A = 3 * np.eye(n) + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    y, it, res = cbie.gmres(lambda v: A @ v, b, tol=1e-12, maxiter=n)
+    assert res < 1e-12
+    assert np.linalg.norm(y - np.linalg.solve(A, b)) < 1e-10 * np.linalg.norm(y)
+
+
+@pytest.fixture(scope="module")
+def sphere_solution():
+    prob = CONFIG_SPHERE_SMALL(8)
+    qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=48)
+    op = cbie.build_operator(prob, qp)
+    inc = plane_wave(op.g.x, prob.k_ext, prob.omega)
+    b = cbie.rhs(prob, op.g, inc)
+    y, it, res = cbie.gmres(lambda v: cbie.apply(op, v.reshape(4, -1)).reshape(-1), b.reshape(-1),
+                            tol=1e-10, maxiter=300)
+    return prob, op, y.reshape(4, -1), it, res, b
+
+
+def test_sphere_solution_matches_mie(sphere_solution):
+    prob, op, y, it, res, _ = sphere_solution
+    a = 0.5
+    pin = mie.fibonacci_sphere(200, 0.7 * a)
+    pout = mie.fibonacci_sphere(200, 1.5 * a)
+    Ei, Hi = cbie.fields_off_surface(prob, y, pin, "int")
+    Es, Hs = cbie.fields_off_surface(prob, y, pout, "ext")
+    Mi, MHi = mie.fields(pin, "int", prob.k_ext, prob.k_int, a, prob.omega)
+    Ms, MHs = mie.fields(pout, "sca", prob.k_ext, prob.k_int, a, prob.omega)
+    for got, ref in [(Ei, Mi), (Hi, MHi), (Es, Ms), (Hs, MHs)]:
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 3e-3
+
+
+def test_dense_operator_solve_agrees_with_gmres(sphere_solution):
+    prob, op, y, it, res, b = sphere_solution
+    A = cbie.assemble(op)
+    yd = np.linalg.solve(A, b.reshape(-1))
+    assert np.linalg.norm(yd - y.reshape(-1)) < 1e-8 * np.linalg.norm(yd)
+    assert 10 <= it <= 60
