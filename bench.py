@@ -1,0 +1,335 @@
+"""Benchmark: CBIE-IFGF N-Mueller GMRES solves on one GB300 (or N replicas).
+
+A step is one GMRES solve of A y = b (Eq. lin_system) on the 9,600-node
+dielectric sphere (radius 2 wavelengths, eps_r = 4, 96 patches x 10 x 10
+Chebyshev nodes), x-polarised plane wave along +z: every solver iteration
+runs the whole forward map (density prep, near matrix, IFGF leaf step,
+upward interpolation, target evaluation, N-Mueller combination) and a CGS2
+Arnoldi step.  value = unknowns x matvecs / s over the timed solves (4N
+unknowns per matvec).  The GMRES time-to-solve is reported beside it.
+
+--impl reference times the CPU FP64 oracle (the unaccelerated CBIE forward
+map) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "sphere r=2 lambda, eps_r=4, 96 patches x 10x10 nodes (N=9600, 38400 unknowns)"
+METRIC = "IFGF N-Mueller unknown*matvecs/s at rel err <=1e-4; GMRES time-to-solve"
+UNIT = "unknown*matvecs/s"
+# cone segments at level D+1: (2, 3) keeps the forward-map error <= 1e-4 on this body
+NS0, NA0 = 2, 3
+
+
+def problem():
+    from inputs import CONFIG_SPHERE_MEDIUM
+    return CONFIG_SPHERE_MEDIUM(10)
+
+
+def delta_of(prob):
+    # 0.6 x the largest patch diameter (largest distance between two nodes of one patch)
+    x, _, _ = prob.nodes()
+    P, nc = prob.num_patches, prob.nc
+    xp = x.reshape(P, nc * nc, 3)
+    diam = max(np.linalg.norm(xp[p][:, None] - xp[p][None], axis=-1).max() for p in range(P))
+    return 0.6 * diam
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def kernel_work(stats):
+    """Algorithmic work per launch kind, summed over one forward map."""
+    inter = sum(stats["interactions"])
+    return {
+        # (c): per (target, cone) pair 75 x 32 real FMAs for F and 75 x 24 for dF/dn
+        "target": {"flops": inter * 2.0 * 75 * (32 + 24)},
+        # (b): per (parent point, child) 75 x 32 real FMAs plus the complex re-centring multiply
+        "up": {"flops": stats["up_pairs"] * (2.0 * 75 * 32 + 6 * 16)},
+        # (a): per (interpolation point, source) 2 kernels x 8 complex multiply-adds
+        "leaf": {"flops": stats["leaf_pairs"] * 2 * 8 * 8.0},
+        # (d): FP32 weights (4 complex) + int32 column per nonzero, row pointers, densities and outputs once
+        "near": {"bytes": stats["near_nnz"] * (32 + 4) + (stats["n"] + 1) * 8 + stats["n"] * (16 + 56) * 4},
+    }
+
+
+def alu_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_gpu(args):
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import plane_wave
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prob = problem()
+    delta = delta_of(prob)
+    plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=400)
+    st = plan.stats()
+    N = prob.n
+    x, _, _ = prob.nodes()
+    # replicas solve different incidences (direction tilted per rank); rank 0 keeps +z
+    ang = 0.1 * rank
+    dvec = (np.sin(ang), 0.0, np.cos(ang))
+    inc = plane_wave(x, prob.k_ext, prob.omega, direction=dvec)
+    inc_h = torch.from_numpy(np.ascontiguousarray(inc)).pin_memory()
+    inc_d = inc_h.cuda()
+    y_d = torch.empty((4, N), dtype=torch.complex128, device="cuda")
+    y_h = torch.empty((4, N), dtype=torch.complex128).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    tol = args.tol
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.solve(inc_d, y_d, tol=tol, max_iter=400)
+    # ---- timed device-resident solves (L2 flushed between steps, outside the events)
+    lib.ifgf_set_timing(plan.handle, True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    times, iters = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it, rr, status = plan.solve(inc_d, y_d, tol=tol, max_iter=400)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        iters.append(it)
+    barrier()
+    clk = clocks.stop()
+    ktime, launches = lib.ifgf_get_timing(plan.handle)
+    lib.ifgf_set_timing(plan.handle, False)
+    t_tot = float(np.sum(times))
+    mv_total = float(np.sum(iters))
+    # ---- end to end: host buffers through bie_solve (copies inside the timed call)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it_h, _, _ = plan.solve(inc_h.numpy(), y_h.numpy(), tol=tol, max_iter=400)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    # ---- accuracy of the timed path: one IFGF FP32 matvec vs the plain FP64 direct path
+    yv = torch.from_numpy(np.ascontiguousarray(
+        (np.random.default_rng(7).standard_normal((4, N)) + 1j * np.random.default_rng(8).standard_normal((4, N)))
+        / np.sqrt(2))).cuda()
+    o1 = torch.empty_like(yv)
+    plan.apply(yv, o1)
+    ref_plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP64,
+                                     far_mode=lib.IFGF_FAR_DIRECT, max_krylov=10)
+    o2 = torch.empty_like(yv)
+    ref_plan.apply(yv, o2)
+    torch.cuda.synchronize()
+    matvec_err = float(torch.linalg.norm(o1 - o2) / torch.linalg.norm(o2))
+    ref_plan.close()
+    # ---- aggregate over ranks (max time)
+    t_step = t_tot / args.steps
+    if dist is not None:
+        tt = torch.tensor([t_tot, max(e2e_times)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_tot, e2e_max = float(tt[0]), float(tt[1])
+    else:
+        e2e_max = max(e2e_times)
+    units_per_step = 4.0 * N * float(np.mean(iters))
+    value = world * units_per_step * args.steps / t_tot
+    e2e_value = world * 4.0 * N * it_h / e2e_max
+    # ---- roofline of the dominant kernel (largest summed time in the timed region)
+    work = kernel_work(st)
+    per_apply_launch = {"target": st["levels"] - 2, "up": st["levels"] - 3, "leaf": 1, "near": 1}
+    dom = max(("target", "up", "leaf", "near"), key=lambda k: ktime[k][0])
+    dom_ms, dom_calls = ktime[dom]
+    napply = ktime["prep"][1]
+    peaks, peaks_src = measured_peaks()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if dom == "near":
+        per_launch = work["near"]["bytes"]
+        achieved = per_launch / (dom_ms / dom_calls / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{peaks_src} hbm_gbs"}
+    else:
+        per_launch = work[dom]["flops"] / per_apply_launch[dom]
+        achieved = per_launch / (dom_ms / dom_calls / 1e3) / 1e12
+        peak = alu_peak_tflops(sm_mhz)
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled)"}
+    roof["kernel"] = {"target": "k_target (c)", "up": "k_up (b)", "leaf": "k_leaf (a)", "near": "k_near (d)"}[dom]
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Arnoldi, FP64 setup)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "far_field": f"IFGF, Ps=3 Pa=5, (ns,na)_(D+1)=({NS0},{NA0})",
+                   "levels": st["levels"], "gmres_tol": tol, "rhs": "plane wave +z, x-pol",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "256 MiB buffer written between timed steps (outside the events)"},
+        "gmres_time_to_solve_s": t_step, "gmres_iters": int(np.mean(iters)),
+        "matvec_rel_err_vs_fp64_direct": matvec_err,
+        "stage_ms_per_apply": {k: ktime[k][0] / max(napply, 1) for k in ktime},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * N * 16,
+                "d2h_bytes_per_step": 4 * N * 16},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "plan": {"near_nnz": st["near_nnz"], "cones": st["cones"], "interactions": st["interactions"],
+                 "setup_s": st["setup_seconds"], "device_bytes": st["device_bytes"]},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(prob, delta, budget_s=args.cpu_budget)
+    plan.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return result if rank == 0 else None
+
+
+def cpu_baseline(prob, delta, budget_s=15.0, reference_units=False):
+    """The CPU FP64 oracle as it stands: kernel rows of the unaccelerated CBIE
+    operator for whole patches plus the combination, on the host cores; the
+    full forward-map time is extrapolated from the sampled rows."""
+    import os as _os
+    from oracle import cbie
+    cores = _os.cpu_count() or 1
+    _os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    g = cbie.geometry_of(prob)
+    qp = cbie.QuadParams(delta=delta, n_beta=48, cov_d=4.0)
+    npp = prob.nc ** 2
+    from inputs import random_densities
+    y = random_densities(prob.n, 11)
+    phi = cbie.densities(y, g)
+    t0 = time.perf_counter()
+    rows_done = 0
+    p = 0
+    while True:
+        rows = np.arange(p * npp, (p + 1) * npp)
+        K, _ = cbie.kernel_rows(prob, g, rows, qp)
+        cbie.scalar_fields(K, phi)
+        rows_done += npp
+        p += 1
+        if time.perf_counter() - t0 > budget_s or p >= prob.num_patches:
+            break
+    dt = time.perf_counter() - t0
+    t_full = dt * prob.n / rows_done
+    return {"value": 4.0 * prob.n / t_full, "unit": UNIT, "cores": int(_os.environ.get("OMP_NUM_THREADS", cores)),
+            "kind": "oracle",
+            "sample": f"{p} of {prob.num_patches} patches ({rows_done} target rows) of the FP64 CBIE forward map "
+                      f"(kernel rows with singular moments + sums), {dt:.1f} s; full matvec extrapolated "
+                      f"to {t_full:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    prob = problem()
+    delta = delta_of(prob)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(prob, delta, budget_s=max(2.0, 30.0 / max(1, args.steps + args.warmup))))
+    timed = vals[args.warmup:]
+    v = float(np.mean([t["value"] for t in timed]))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": timed[0]["cores"], "kind": "oracle",
+                             "sample": timed[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tol", type=float, default=1e-4)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * ifgf.h -- C ABI of the GB300 (sm_103a) CBIE-IFGF N-Mueller library.
+ *
+ * The library evaluates the forward map of the discretised indirect
+ * N-Mueller boundary integral equation for a dielectric scatterer and solves
+ * it with GMRES on the device (Paul & Sideris, "Accelerated 3D Maxwell
+ * Integral Equation Solver using the Interpolated Factored Green Function
+ * Method": Eq. n_muller with Eqs. k_delta, r_delta, t_delta; the linear
+ * system Eq. lin_system).  The far interactions are accelerated with the
+ * IFGF method (Sec. III-E to III-I), the near interactions use precomputed
+ * singular weights (Sec. III-D) with the local corrections of Sec. III-H.
+ *
+ * Conventions used by every entry point:
+ *  - All sizes are int32 unless stated; N = num_patches * nc * nc nodes.
+ *  - Node order is l = j + nc*i + p*nc^2 (Eq. mesh_pts_l): node l of patch p
+ *    sits at the parameter point (u_i, u_j), u_k = cos((k + 1/2) pi / nc)
+ *    (Eq. cheby_nodes).  The caller samples the surface there.
+ *  - Complex numbers are interleaved (re, im) doubles (C99 double _Complex /
+ *    std::complex<double> / torch.complex128 layout).
+ *  - "device pointer" means memory of the current CUDA device; "host or
+ *    device" entry points accept either (detected per call).
+ *  - Every function returns an ifgf_status; 0 is success.  No C++ exception
+ *    crosses this boundary.  A CUDA error inside apply or solve poisons the
+ *    plan: later calls on it return IFGF_ECUDA.
+ *  - Time dependence e^{-i omega t}; kappa_s = omega sqrt(eps_s mu_s).
+ */
+#ifndef IFGF_H
+#define IFGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ifgf_status;
+enum {
+  IFGF_OK = 0,
+  IFGF_EINVAL = 1,        /* a descriptor field or argument is invalid */
+  IFGF_ENOMEM = 2,        /* a host or device allocation failed (plan_create only) */
+  IFGF_ECUDA = 3,         /* a CUDA call failed; the plan is poisoned */
+  IFGF_ENOCONV = 4,       /* GMRES reached max_iter above the tolerance (y still written) */
+  IFGF_ETIMEOUT = 5,      /* reserved: a bounded device wait expired */
+  IFGF_EUNSUPPORTED = 6,  /* the combination of options is not implemented */
+  IFGF_EINTERNAL = 7      /* an internal consistency check failed */
+};
+
+enum { IFGF_FP64 = 0, IFGF_FP32 = 1 };          /* arithmetic of the per-apply work */
+enum { IFGF_FAR_IFGF = 0, IFGF_FAR_DIRECT = 1 }; /* far-field algorithm */
+
+typedef struct ifgf_plan_t* ifgf_plan;
+typedef void* ifgf_stream;                       /* a cudaStream_t (NULL = legacy default stream) */
+
+/*
+ * Plan descriptor.  All pointers are HOST pointers; plan_create copies what
+ * it needs, the caller keeps ownership.
+ */
+typedef struct {
+  int32_t num_patches;     /* P >= 1 */
+  int32_t nc;              /* Chebyshev nodes per patch direction, 2..24 */
+  const double* nodes;     /* [N][3] surface points eta_p(u_i, u_j) */
+  const double* dxdu;      /* [N][3] d eta_p / du at the nodes */
+  const double* dxdv;      /* [N][3] d eta_p / dv at the nodes; dxdu x dxdv points outward */
+  int32_t ng;              /* oversampled geometry grid per direction, nc..48 */
+  const double* fine;      /* [P][ng][ng][9]: (eta, d eta/du, d eta/dv) on the ng open Chebyshev
+                              grid; the patch between nodes is the Chebyshev interpolant of these
+                              samples (used by the singular quadrature of Sec. III-D) */
+  double k_ext, k_int;     /* kappa_e, kappa_i > 0 */
+  double eps_ext, eps_int; /* permittivities > 0 */
+  double mu_ext, mu_int;   /* permeabilities > 0; omega = k_ext / sqrt(eps_ext mu_ext) */
+  int32_t ps, pa;          /* interpolation points per cone segment, radial and angular
+                              (Remark 2: the paper uses 3 and 5; only 3, 5 is built) */
+  int32_t ns0, na0;        /* n_{s;D+1}, n_{a;D+1} (paper: 1, 2), >= 1 */
+  double leaf_size;        /* upper bound on the leaf box side H_D; 0 -> 0.25 * 2 pi / k_ext */
+  int32_t min_levels;      /* lower bound on D (>= 3; 0 -> 3) */
+  double delta;            /* singular-set distance threshold of Eq. patch_sing; must be > 0 */
+  int32_t n_beta;          /* Fejer points per direction of the moment rule (Eq. int_moments_cov), 4..96 */
+  double cov_d;            /* change-of-variables order d >= 2 (Eq. mk_cov_1) */
+  int32_t gs_iters;        /* golden-section iterations per direction (Eq. dist_min); 0 -> 60 */
+  int32_t precision;       /* IFGF_FP64 or IFGF_FP32: arithmetic of steps (a)-(d) per apply */
+  int32_t far_mode;        /* IFGF_FAR_IFGF or IFGF_FAR_DIRECT (plain O(N^2) far sum) */
+  int32_t max_krylov;      /* GMRES basis capacity allocated by plan_create (0 -> 300, <= 1000) */
+} ifgf_plan_desc;
+
+/* Counts describing a plan (ifgf_plan_stats). */
+typedef struct {
+  int32_t n;                 /* nodes */
+  int32_t levels;            /* D */
+  int32_t boxes[24];         /* relevant boxes per level d = 1..D (index d) */
+  int32_t cones[24];         /* relevant cone segments per level */
+  int32_t ns[24], na[24];    /* cone counts per level */
+  int64_t interactions[24];  /* (target, cousin box) pairs evaluated per level */
+  int64_t leaf_pairs;        /* (interpolation point, source) pairs of the leaf step */
+  int64_t up_pairs;          /* (parent point, child box) pairs of the upward steps */
+  int64_t near_nnz;          /* nonzeros of the near-field matrix (per kernel) */
+  int64_t singular_pairs;    /* (target, patch) pairs treated with the moment rule */
+  int64_t device_bytes;      /* device memory held by the plan */
+  double setup_seconds;      /* wall time of plan_create */
+} ifgf_stats;
+
+/*
+ * Build a plan: octree, cone segments and interaction lists on the host
+ * (Sec. III-F, steps "determine relevant boxes and cones"), then on the
+ * device the node geometry, closest points and singular moments (Sec. III-D)
+ * and the near-field matrix with local corrections (Sec. III-H).  The plan
+ * owns all device memory it uses; apply and solve allocate nothing.  Runs on
+ * the current device, synchronously.  Errors: IFGF_EINVAL (descriptor),
+ * IFGF_ENOMEM, IFGF_ECUDA, IFGF_EUNSUPPORTED.  On error *out is NULL.
+ */
+ifgf_status ifgf_plan_create(const ifgf_plan_desc* desc, ifgf_plan* out);
+
+/* Release a plan (NULL is allowed). Synchronises the device. */
+ifgf_status ifgf_plan_destroy(ifgf_plan plan);
+
+/*
+ * Forward map out = A y, the left-hand side of Eq. n_muller (Sec. IV-A,
+ * "forward map").  y and out are DEVICE pointers to [4][N] complex128:
+ * the components (m.t1, m.t2, j.t1, j.t2) on the orthonormal frame
+ * t1 = eta_u/|eta_u|, t2 = n x t1 at every node; out uses the same layout
+ * (projections of the two rows of Eq. n_muller on t1, t2).  Asynchronous on
+ * `stream`; y and out must not alias.  Allocates nothing.
+ */
+ifgf_status ifgf_apply(ifgf_plan plan, const void* y, void* out, ifgf_stream stream);
+
+/*
+ * Raw scalar sums for tests: given the eight densities phi (DEVICE [N][8]
+ * complex128, order m_x m_y m_z j_x j_y j_z div m div j; Sec. III first
+ * paragraph), write f28 (DEVICE [N][28] complex128): S_e[phi_k] (k=0..7),
+ * S_i[phi_k], dS_e/dn[phi_k] (k=0..5), dS_i/dn[phi_k] at every node, where
+ * `which` selects the part:  IFGF_PART_NEAR (near matrix only),
+ * IFGF_PART_FAR (the plan's far algorithm only: the sum of Eq. ifgf_sum_em
+ * over sources outside the target's neighbour boxes, with a = phi * omega),
+ * IFGF_PART_ALL (both).  Arithmetic in the plan's precision.
+ */
+enum { IFGF_PART_NEAR = 1, IFGF_PART_FAR = 2, IFGF_PART_ALL = 3 };
+ifgf_status ifgf_apply_fields(ifgf_plan plan, const void* phi, void* f28, int32_t which,
+                              ifgf_stream stream);
+
+/*
+ * Solve A y = b with GMRES (Eq. lin_system; no restart, CGS2 Arnoldi in FP64,
+ * y0 = 0), where b = omega^{-1} (n x E^inc, n x H^inc) projected on (t1, t2)
+ * (right-hand side of Eq. n_muller).  inc: HOST or DEVICE [6][N] complex128
+ * (E_x, E_y, E_z, H_x, H_y, H_z of the incident field at the nodes).
+ * y: HOST or DEVICE [4][N] complex128 output.  Stops when the Arnoldi
+ * residual estimate |b - A y| / |b| <= tol or after max_iter iterations
+ * (<= 1000).  iters / relres (host pointers, may be NULL) receive the
+ * iteration count and the final relative residual estimate.  Returns
+ * IFGF_ENOCONV if tol was not reached (y holds the last iterate).
+ * Synchronises `stream` (one scalar is read back per iteration).
+ */
+ifgf_status bie_solve(ifgf_plan plan, const void* inc, double tol, int32_t max_iter, void* y,
+                      int32_t* iters, double* relres, ifgf_stream stream);
+
+/* Counts and sizes of a plan. */
+ifgf_status ifgf_plan_stats(ifgf_plan plan, ifgf_stats* st);
+
+/*
+ * Optional CUDA-event timing of the library's kernels, for profiling.
+ * ifgf_set_timing(plan, 1) resets the counters and records an event pair
+ * around every timed launch on the launch stream from then on (0 stops).
+ * ifgf_get_timing synchronises on the recorded events and returns, per kind
+ * k = 0 density prep (a0), 1 near matrix (d), 2 leaf step (a), 3 upward
+ * step (b), 4 target evaluation (c), 5 combination, 6 direct far sum,
+ * 7 GMRES orthogonalisation (per iteration), the summed time ms[k] and the
+ * number of timed records calls[k] (arrays of 8), and the number of kernels
+ * launched by apply/solve since the reset.  Any pointer may be NULL.
+ */
+ifgf_status ifgf_set_timing(ifgf_plan plan, int32_t enable);
+ifgf_status ifgf_get_timing(ifgf_plan plan, double* ms, int64_t* calls, int64_t* launches);
+
+/* Human-readable message for a status code (static storage). */
+const char* ifgf_status_string(ifgf_status s);
+
+/*
+ * Host-only octree and cone-segment tables (no GPU work): the setup of
+ * Sec. III-F (relevant boxes Eq. rele_boxes, neighbours and cousins Eqs.
+ * box_neighbor / box_cousin, cone counts of Remark 2, relevant cone segments
+ * Eq. rele_cone_d) for a point set, exposed for inspection and tests.
+ * nodes: host [n][3]; k_max: the largest wavenumber the cones must resolve.
+ * A tree from ifgf_tree_create is released with ifgf_tree_destroy; the tree
+ * of a plan (ifgf_plan_tree) is borrowed and lives as long as the plan.
+ * Output arrays are caller-owned host arrays; pass NULL to query sizes.
+ */
+typedef struct ifgf_tree_t* ifgf_tree;
+ifgf_status ifgf_tree_create(const double* nodes, int32_t n, double leaf_size, int32_t min_levels,
+                             double k_max, int32_t ns0, int32_t na0, ifgf_tree* out);
+ifgf_status ifgf_tree_destroy(ifgf_tree tree);
+ifgf_status ifgf_plan_tree(ifgf_plan plan, ifgf_tree* out);
+/* levels D, level-1 cube corner [3] and side H_1 */
+ifgf_status ifgf_tree_info(ifgf_tree tree, int32_t* levels, double* corner, double* h1);
+/* perm [n]: sorted position -> node; leaf_coords [n][3]: integer leaf box of each node */
+ifgf_status ifgf_tree_perm(ifgf_tree tree, int32_t* perm, int32_t* leaf_coords);
+/* level d (1..D): box count, relevant-cone count, (n_s, n_a), integer box coordinates [nb][3],
+ * relevant cones CSR per box (box_slot_ptr [nb+1], slot_cone [nslots] cone ids
+ * (g1*na + g2)*2na + g3) */
+ifgf_status ifgf_tree_level(ifgf_tree tree, int32_t d, int32_t* nboxes, int32_t* nslots, int32_t* ns,
+                            int32_t* na, int32_t* box_coords, int32_t* box_slot_ptr, int32_t* slot_cone);
+/* level d (3..D): per sorted target, the relevant cones (slots of level d) it is evaluated from:
+ * tgt_ptr [n+1] (int64), tgt_slot [ninter]; slot_box [nslots] box of each slot */
+ifgf_status ifgf_tree_targets(ifgf_tree tree, int32_t d, int64_t* ninter, int64_t* tgt_ptr,
+                              int32_t* tgt_slot, int32_t* slot_box);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IFGF_H */

@@ -138,30 +138,55 @@ static void w_f(double t, double d, double *w, double *dw) {
   *w = 2.0 * M_PI * a / (a + b);
   *dw = 2.0 * M_PI * (da * b - a * db) / ((a + b) * (a + b));
 }
-/* xi_alpha(tau) and d xi_alpha / d tau on tau in [-1, 1] */
-static void xi_f(double alpha, double tau, double d, double *xi, double *mu) {
+/* xi_alpha(tau), d xi_alpha / d tau and the displacement xi_alpha(tau) - alpha on tau in [-1, 1] */
+static void xi_f(double alpha, double tau, double d, double *xi, double *mu, double *dxi) {
   double w, dw;
   if (alpha == 1.0) {
     w_f(M_PI * fabs((tau - 1.0) * 0.5), d, &w, &dw);
-    *xi = alpha - ((1.0 + alpha) / M_PI) * w;
+    *dxi = -((1.0 + alpha) / M_PI) * w;
     *mu = dw;
   } else if (alpha == -1.0) {
     w_f(M_PI * fabs((tau + 1.0) * 0.5), d, &w, &dw);
-    *xi = alpha + ((1.0 - alpha) / M_PI) * w;
+    *dxi = ((1.0 - alpha) / M_PI) * w;
     *mu = dw;
   } else {
     double s = (tau > 0) ? 1.0 : ((tau < 0) ? -1.0 : 0.0);
     w_f(M_PI * fabs(tau), d, &w, &dw);
-    *xi = alpha + ((s - alpha) / M_PI) * w;
+    *dxi = ((s - alpha) / M_PI) * w;
     *mu = (s - alpha) * s * dw;
     if (s == 0.0) *mu = 0.0;
   }
+  *xi = alpha + *dxi;
 }
 
-/* The four kernels at (x, n_x; y): G_e, G_i, dG_e/dn_x, dG_i/dn_x. r == 0 -> zeros. */
-static void kernels4(const double *x, const double *nx, const double *y, double ke, double ki,
-                     cplx *K) {
-  double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+/* T_k(a) and the differences T_k(a + delta) - T_k(a), k < n, without cancellation:
+ * D_{k+1} = 2 delta T_k(a + delta) + 2 a D_k - D_{k-1}, D_0 = 0, D_1 = delta. */
+static void cheb_T_diff(double a, double delta, int n, double *Ta, double *Dk) {
+  cheb_T(a, n, Ta);
+  if (n > 0) Dk[0] = 0.0;
+  if (n > 1) Dk[1] = delta;
+  for (int k = 1; k + 1 < n; ++k) Dk[k + 1] = 2.0 * delta * (Ta[k] + Dk[k]) + 2.0 * a * Dk[k] - Dk[k - 1];
+}
+
+/* Displacement eta(a + du, b + dv) - eta(a, b) of the patch interpolant, cancellation-free:
+ * sum_mn c_mn [D_m(u) T_n(b + dv) + T_m(a) D_n(v)]. */
+static void geom_disp(const patch_geom *g, double a, double du, double b, double dv, double *e) {
+  double Ta[64], Da[64], Tb[64], Db[64];
+  cheb_T_diff(a, du, g->ng, Ta, Da);
+  cheb_T_diff(b, dv, g->ng, Tb, Db);
+  e[0] = e[1] = e[2] = 0.0;
+  for (int m = 0; m < g->ng; ++m)
+    for (int n = 0; n < g->ng; ++n) {
+      const double *cf = g->coef + ((size_t)m * g->ng + n) * 9;
+      double f = Da[m] * (Tb[n] + Db[n]) + Ta[m] * Db[n];
+      for (int c = 0; c < 3; ++c) e[c] += cf[c] * f;
+    }
+}
+
+/* The four kernels for the separation d = x - y and the target normal n_x:
+ * G_e, G_i, dG_e/dn_x, dG_i/dn_x.  r == 0 -> zeros. */
+static void kernels4(const double *dv, const double *nx, double ke, double ki, cplx *K) {
+  double d0 = dv[0], d1 = dv[1], d2 = dv[2];
   double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
   if (r == 0.0) {
     K[0] = K[1] = K[2] = K[3] = 0.0;
@@ -174,6 +199,11 @@ static void kernels4(const double *x, const double *nx, const double *y, double 
     K[s] = g;
     K[2 + s] = nd * (I * kk[s] * r - 1.0) * g / (r * r);
   }
+}
+
+static void kernels4_xy(const double *x, const double *nx, const double *y, double ke, double ki, cplx *K) {
+  double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
+  kernels4(d, nx, ke, ki, K);
 }
 
 /*
@@ -250,21 +280,17 @@ int ora_kernel_rows(int P, int nc, int ng, const double *nodes, const double *no
       if (!singular) {
         for (int mm = 0; mm < npp; ++mm) {
           cplx k4[4];
-          kernels4(x, nx, nodes + 3 * (m0 + mm), ke, ki, k4);
+          kernels4_xy(x, nx, nodes + 3 * (m0 + mm), ke, ki, k4);
           for (int s = 0; s < 4; ++s) K[((size_t)s * nrows + r) * N + m0 + mm] = k4[s] * qw[m0 + mm];
         }
         continue;
       }
       ++nsing;
-      /* For the target's own patch the kernel is evaluated at the interpolated
-       * surface point eta_p(u_i, v_j) itself, so the target lies exactly on the
-       * surface being integrated (reading R12). */
-      double xs[3] = {x[0], x[1], x[2]};
-      if (p == pl) geom_eval(&g, uc, vc, 3, xs);
-      /* clustered nodes and their Jacobians mu (Eq. int_moments_1) */
+      /* clustered nodes, their Jacobians mu (Eq. int_moments_1) and displacements */
+      double dub[256], dvb[256];
       for (int i = 0; i < nbeta; ++i) {
-        xi_f(uc, t_beta[i], cov_d, &ub[2 * i], &ub[2 * i + 1]);
-        xi_f(vc, t_beta[i], cov_d, &vb[2 * i], &vb[2 * i + 1]);
+        xi_f(uc, t_beta[i], cov_d, &ub[2 * i], &ub[2 * i + 1], &dub[i]);
+        xi_f(vc, t_beta[i], cov_d, &vb[2 * i], &vb[2 * i + 1], &dvb[i]);
         cheb_T(ub[2 * i], nc, Tu + (size_t)i * nc);
         cheb_T(vb[2 * i], nc, Tv + (size_t)i * nc);
       }
@@ -279,7 +305,17 @@ int ora_kernel_rows(int P, int nc, int ng, const double *nodes, const double *no
           double J = sqrt(cx * cx + cy * cy + cz * cz);
           double wt = J * ub[2 * i + 1] * vb[2 * j + 1] * w_beta[i] * w_beta[j];
           cplx k4[4];
-          kernels4(xs, nx, gv, ke, ki, k4);
+          if (p == pl) {
+            /* Target on this patch: it is the interpolated surface point eta_p(u_i', v_j')
+             * (reading R12) and x - y = -(eta(u, v) - eta(uc, vc)) is formed from
+             * Chebyshev differences so that no cancellation occurs near the target. */
+            double e[3];
+            geom_disp(&g, uc, dub[i], vc, dvb[j], e);
+            double dneg[3] = {-e[0], -e[1], -e[2]};
+            kernels4(dneg, nx, ke, ki, k4);
+          } else {
+            kernels4_xy(x, nx, gv, ke, ki, k4);
+          }
           for (int s = 0; s < 4; ++s) f[((size_t)s * nbeta + i) * nbeta + j] = k4[s] * wt;
         }
       /* beta_mn = sum_ij f_ij T_m(u_i) T_n(v_j) */
@@ -343,5 +379,6 @@ double ora_closest_point(int nc, int ng, const double *patch_nodes, const double
 
 /* The change of variables itself (exposed for tests). */
 void ora_cov(double alpha, int n, const double *tau, double d, double *xi, double *mu) {
-  for (int i = 0; i < n; ++i) xi_f(alpha, tau[i], d, &xi[i], &mu[i]);
+  double dx;
+  for (int i = 0; i < n; ++i) xi_f(alpha, tau[i], d, &xi[i], &mu[i], &dx);
 }

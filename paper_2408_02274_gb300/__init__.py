@@ -1,0 +1,319 @@
+"""GB300 (sm_103a) CBIE-IFGF N-Mueller library: Python binding of the C ABI.
+
+The functions here carry the names of the C entry points in include/ifgf.h
+and only marshal arguments: every step of the forward map and the solver
+runs in the CUDA library ``libifgf.so`` built in-tree by ``build.py``.
+There is no CPU fallback: importing the binding without the library raises.
+PyTorch provides device memory and the current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libifgf.so")
+
+IFGF_OK, IFGF_EINVAL, IFGF_ENOMEM, IFGF_ECUDA, IFGF_ENOCONV, IFGF_ETIMEOUT, IFGF_EUNSUPPORTED, IFGF_EINTERNAL = range(8)
+IFGF_FP64, IFGF_FP32 = 0, 1
+IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
+IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
+
+EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_fields", "bie_solve",
+           "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
+           "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
+           "ifgf_tree_level", "ifgf_tree_targets"]
+
+
+class ifgf_plan_desc(ctypes.Structure):
+    _fields_ = [
+        ("num_patches", ctypes.c_int32), ("nc", ctypes.c_int32),
+        ("nodes", ctypes.POINTER(ctypes.c_double)), ("dxdu", ctypes.POINTER(ctypes.c_double)),
+        ("dxdv", ctypes.POINTER(ctypes.c_double)),
+        ("ng", ctypes.c_int32), ("fine", ctypes.POINTER(ctypes.c_double)),
+        ("k_ext", ctypes.c_double), ("k_int", ctypes.c_double),
+        ("eps_ext", ctypes.c_double), ("eps_int", ctypes.c_double),
+        ("mu_ext", ctypes.c_double), ("mu_int", ctypes.c_double),
+        ("ps", ctypes.c_int32), ("pa", ctypes.c_int32), ("ns0", ctypes.c_int32), ("na0", ctypes.c_int32),
+        ("leaf_size", ctypes.c_double), ("min_levels", ctypes.c_int32),
+        ("delta", ctypes.c_double), ("n_beta", ctypes.c_int32), ("cov_d", ctypes.c_double),
+        ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
+        ("max_krylov", ctypes.c_int32),
+    ]
+
+
+class ifgf_stats(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("levels", ctypes.c_int32),
+        ("boxes", ctypes.c_int32 * 24), ("cones", ctypes.c_int32 * 24),
+        ("ns", ctypes.c_int32 * 24), ("na", ctypes.c_int32 * 24),
+        ("interactions", ctypes.c_int64 * 24),
+        ("leaf_pairs", ctypes.c_int64), ("up_pairs", ctypes.c_int64), ("near_nnz", ctypes.c_int64),
+        ("singular_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("setup_seconds", ctypes.c_double),
+    ]
+
+
+class IfgfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = load().ifgf_status_string(status).decode()
+        super().__init__(f"{where}: status {status} ({msg})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libifgf.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.ifgf_plan_create.argtypes = [ctypes.POINTER(ifgf_plan_desc), ctypes.POINTER(vp)]
+    lib.ifgf_plan_destroy.argtypes = [vp]
+    lib.ifgf_apply.argtypes = [vp, vp, vp, vp]
+    lib.ifgf_apply_fields.argtypes = [vp, vp, vp, i32, vp]
+    lib.bie_solve.argtypes = [vp, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
+                              ctypes.POINTER(ctypes.c_double), vp]
+    lib.ifgf_plan_stats.argtypes = [vp, ctypes.POINTER(ifgf_stats)]
+    lib.ifgf_set_timing.argtypes = [vp, i32]
+    lib.ifgf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    lib.ifgf_status_string.argtypes = [i32]
+    lib.ifgf_status_string.restype = ctypes.c_char_p
+    lib.ifgf_tree_create.argtypes = [vp, i32, ctypes.c_double, i32, ctypes.c_double, i32, i32,
+                                     ctypes.POINTER(vp)]
+    lib.ifgf_tree_destroy.argtypes = [vp]
+    lib.ifgf_plan_tree.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.ifgf_tree_info.argtypes = [vp, ctypes.POINTER(i32), vp, ctypes.POINTER(ctypes.c_double)]
+    lib.ifgf_tree_perm.argtypes = [vp, vp, vp]
+    lib.ifgf_tree_level.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4 + [vp, vp, vp]
+    lib.ifgf_tree_targets.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, vp]
+    for name in EXPORTS:
+        if name != "ifgf_status_string":
+            getattr(lib, name).restype = ctypes.c_int32
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(st: int, where: str):
+    if st != IFGF_OK:
+        raise IfgfError(st, where)
+
+
+def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: float, k_int: float,
+                     eps_ext: float, eps_int: float, mu_ext: float = 1.0, mu_int: float = 1.0, *,
+                     delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
+                     leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
+                     gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
+                     max_krylov: int = 0):
+    """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
+    lib = load()
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
+    ng = int(arrs[3].shape[1])
+    d = ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
+                       k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
+                       min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov)
+    h = ctypes.c_void_p()
+    _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
+    return h
+
+
+def ifgf_plan_destroy(plan):
+    _check(load().ifgf_plan_destroy(plan), "ifgf_plan_destroy")
+
+
+def ifgf_apply(plan, y, out, stream=None):
+    """out = A y for torch complex128 CUDA tensors y, out of shape [4, N]."""
+    _check(load().ifgf_apply(plan, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                             _stream(stream)), "ifgf_apply")
+
+
+def ifgf_apply_fields(plan, phi, f28, which: int = IFGF_PART_ALL, stream=None):
+    """Scalar S/D sums: phi [N, 8] complex128 CUDA -> f28 [N, 28] complex128 CUDA."""
+    _check(load().ifgf_apply_fields(plan, ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(f28.data_ptr()),
+                                    int(which), _stream(stream)), "ifgf_apply_fields")
+
+
+def _addr(a):
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def bie_solve(plan, inc, tol: float, max_iter: int, y, stream=None, raise_on_noconv: bool = False):
+    """GMRES solve; inc [6, N] and y [4, N] complex128, host (numpy) or CUDA (torch).
+
+    Returns (iterations, relative residual estimate, status)."""
+    it = ctypes.c_int32(0)
+    rr = ctypes.c_double(0.0)
+    st = load().bie_solve(plan, _addr(inc), float(tol), int(max_iter), _addr(y), ctypes.byref(it),
+                          ctypes.byref(rr), _stream(stream))
+    if st not in (IFGF_OK, IFGF_ENOCONV) or (raise_on_noconv and st == IFGF_ENOCONV):
+        raise IfgfError(st, "bie_solve")
+    return it.value, rr.value, st
+
+
+def ifgf_plan_stats(plan) -> dict:
+    s = ifgf_stats()
+    _check(load().ifgf_plan_stats(plan, ctypes.byref(s)), "ifgf_plan_stats")
+    D = s.levels
+    return {
+        "n": s.n, "levels": D,
+        "boxes": list(s.boxes[:D + 1]), "cones": list(s.cones[:D + 1]),
+        "ns": list(s.ns[:D + 1]), "na": list(s.na[:D + 1]),
+        "interactions": list(s.interactions[:D + 1]),
+        "leaf_pairs": s.leaf_pairs, "up_pairs": s.up_pairs, "near_nnz": s.near_nnz,
+        "singular_pairs": s.singular_pairs, "device_bytes": s.device_bytes,
+        "setup_seconds": s.setup_seconds,
+    }
+
+
+def ifgf_set_timing(plan, enable: bool = True):
+    _check(load().ifgf_set_timing(plan, int(enable)), "ifgf_set_timing")
+
+
+TIMED_KINDS = ["prep", "near", "leaf", "up", "target", "combine", "far_direct", "gmres"]
+
+
+def ifgf_get_timing(plan):
+    """{kind: (total ms, timed records)} and the kernel launch count since ifgf_set_timing."""
+    ms = (ctypes.c_double * 8)()
+    calls = (ctypes.c_int64 * 8)()
+    nl = ctypes.c_int64(0)
+    _check(load().ifgf_get_timing(plan, ms, calls, ctypes.byref(nl)), "ifgf_get_timing")
+    return {k: (ms[i], calls[i]) for i, k in enumerate(TIMED_KINDS)}, nl.value
+
+
+class Tree:
+    """Host-only octree and cone-segment tables (ifgf_tree_*); no GPU is used."""
+
+    def __init__(self, nodes=None, leaf_size=None, k_max=None, min_levels=0, ns0=1, na0=2, handle=None,
+                 owned=True):
+        lib = load()
+        if handle is None:
+            x = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64))
+            h = ctypes.c_void_p()
+            _check(lib.ifgf_tree_create(ctypes.c_void_p(x.ctypes.data), x.shape[0], float(leaf_size),
+                                        int(min_levels), float(k_max), int(ns0), int(na0), ctypes.byref(h)),
+                   "ifgf_tree_create")
+            handle = h
+            self.n = x.shape[0]
+        self.handle, self.owned = handle, owned
+        lv = ctypes.c_int32(0)
+        corner = np.zeros(3)
+        h1 = ctypes.c_double(0)
+        _check(lib.ifgf_tree_info(self.handle, ctypes.byref(lv), ctypes.c_void_p(corner.ctypes.data),
+                                  ctypes.byref(h1)), "ifgf_tree_info")
+        self.levels, self.corner, self.h1 = lv.value, corner, h1.value
+
+    @classmethod
+    def of_plan(cls, plan_handle, n):
+        h = ctypes.c_void_p()
+        _check(load().ifgf_plan_tree(plan_handle, ctypes.byref(h)), "ifgf_plan_tree")
+        t = cls(handle=h, owned=False)
+        t.n = n
+        return t
+
+    def perm(self):
+        perm = np.zeros(self.n, dtype=np.int32)
+        lc = np.zeros((self.n, 3), dtype=np.int32)
+        _check(load().ifgf_tree_perm(self.handle, ctypes.c_void_p(perm.ctypes.data),
+                                     ctypes.c_void_p(lc.ctypes.data)), "ifgf_tree_perm")
+        return perm, lc
+
+    def level(self, d: int):
+        """(box_coords [nb,3], box_slot_ptr [nb+1], slot_cone [nslots], ns, na)."""
+        lib = load()
+        nb, nsl, ns, na = (ctypes.c_int32(0) for _ in range(4))
+        _check(lib.ifgf_tree_level(self.handle, d, ctypes.byref(nb), ctypes.byref(nsl), ctypes.byref(ns),
+                                   ctypes.byref(na), None, None, None), "ifgf_tree_level")
+        coords = np.zeros((nb.value, 3), dtype=np.int32)
+        ptr = np.zeros(nb.value + 1, dtype=np.int32)
+        cones = np.zeros(max(nsl.value, 1), dtype=np.int32)
+        _check(lib.ifgf_tree_level(self.handle, d, ctypes.byref(nb), ctypes.byref(nsl), ctypes.byref(ns),
+                                   ctypes.byref(na), ctypes.c_void_p(coords.ctypes.data),
+                                   ctypes.c_void_p(ptr.ctypes.data), ctypes.c_void_p(cones.ctypes.data)),
+               "ifgf_tree_level")
+        return coords, ptr, cones[:nsl.value], ns.value, na.value
+
+    def targets(self, d: int):
+        """(tgt_ptr [n+1] int64, tgt_slot [ninter], slot_box [nslots]) of level d >= 3."""
+        lib = load()
+        ni = ctypes.c_int64(0)
+        _check(lib.ifgf_tree_targets(self.handle, d, ctypes.byref(ni), None, None, None), "ifgf_tree_targets")
+        _, ptr, cones, _, _ = self.level(d)
+        tp = np.zeros(self.n + 1, dtype=np.int64)
+        ts = np.zeros(max(ni.value, 1), dtype=np.int32)
+        sb = np.zeros(max(cones.size, 1), dtype=np.int32)
+        _check(lib.ifgf_tree_targets(self.handle, d, ctypes.byref(ni), ctypes.c_void_p(tp.ctypes.data),
+                                     ctypes.c_void_p(ts.ctypes.data), ctypes.c_void_p(sb.ctypes.data)),
+               "ifgf_tree_targets")
+        return tp, ts[:ni.value], sb[:cones.size]
+
+    def close(self):
+        if self.handle and self.owned:
+            load().ifgf_tree_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owning wrapper around an ifgf_plan for one Problem-like description."""
+
+    def __init__(self, nodes, dxdu, dxdv, fine, num_patches, nc, k_ext, k_int, eps_ext, eps_int,
+                 mu_ext=1.0, mu_int=1.0, **kw):
+        self.N = num_patches * nc * nc
+        self.handle = ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches, nc, k_ext, k_int, eps_ext,
+                                       eps_int, mu_ext, mu_int, **kw)
+
+    @classmethod
+    def from_problem(cls, problem, **kw):
+        x, xu, xv = problem.nodes()
+        return cls(x, xu, xv, problem.fine(), problem.num_patches, problem.nc, problem.k_ext, problem.k_int,
+                   problem.eps_ext, problem.eps_int, problem.mu_ext, problem.mu_int, **kw)
+
+    def apply(self, y, out, stream=None):
+        ifgf_apply(self.handle, y, out, stream)
+
+    def fields(self, phi, f28, which=IFGF_PART_ALL, stream=None):
+        ifgf_apply_fields(self.handle, phi, f28, which, stream)
+
+    def solve(self, inc, y, tol=1e-6, max_iter=300, stream=None):
+        return bie_solve(self.handle, inc, tol, max_iter, y, stream)
+
+    def stats(self):
+        return ifgf_plan_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            ifgf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,536 @@
+// C ABI of the CBIE-IFGF library: plan creation (host octree + device setup
+// kernels), forward map, raw scalar fields, GMRES solve, stats.
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <stdexcept>
+
+#include "gmres.h"
+#include "host_setup.h"
+#include "kernels.h"
+
+namespace ifgf {
+
+static thread_local char g_last_err[512] = "";
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+namespace {
+
+struct Alloc {
+  ifgf_plan_t* p;
+  template <typename T>
+  T* dev(size_t count) {
+    if (count == 0) count = 1;
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, count * sizeof(T)) != cudaSuccess) throw std::bad_alloc();
+    p->allocations.push_back(ptr);
+    p->stats.device_bytes += (int64_t)(count * sizeof(T));
+    return static_cast<T*>(ptr);
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    T* d = dev<T>(v.size());
+    if (!v.empty() && cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      throw std::runtime_error("cudaMemcpy H2D failed");
+    return d;
+  }
+  template <typename T>
+  T* upload(const T* v, size_t count) {
+    T* d = dev<T>(count);
+    if (count && cudaMemcpy(d, v, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      throw std::runtime_error("cudaMemcpy H2D failed");
+    return d;
+  }
+};
+
+void free_all(ifgf_plan_t* p) {
+  for (void* a : p->allocations) cudaFree(a);
+  p->allocations.clear();
+  if (p->gm.hres) cudaFreeHost(p->gm.hres);
+  p->gm.hres = nullptr;
+  for (auto& e : p->timer.pool)
+    if (e) cudaEventDestroy(e);
+  p->timer.pool.clear();
+}
+
+void check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, what, __FILE__, __LINE__);
+    throw std::runtime_error(g_last_err);
+  }
+}
+
+ifgf_status validate(const ifgf_plan_desc* d) {
+  if (!d) return IFGF_EINVAL;
+  if (d->num_patches < 1 || d->nc < 2 || d->nc > 24) return IFGF_EINVAL;
+  if (!d->nodes || !d->dxdu || !d->dxdv || !d->fine) return IFGF_EINVAL;
+  if (d->ng < 2 || d->ng > 48) return IFGF_EINVAL;
+  if (!(d->k_ext > 0) || !(d->k_int > 0)) return IFGF_EINVAL;
+  if (!(d->eps_ext > 0) || !(d->eps_int > 0) || !(d->mu_ext > 0) || !(d->mu_int > 0)) return IFGF_EINVAL;
+  if (!(d->delta > 0)) return IFGF_EINVAL;
+  if (d->n_beta < 4 || d->n_beta > 96) return IFGF_EINVAL;
+  if (!(d->cov_d >= 2)) return IFGF_EINVAL;
+  if (d->ns0 < 1 || d->na0 < 1 || d->ns0 > 64 || d->na0 > 64) return IFGF_EINVAL;
+  if (d->leaf_size < 0 || d->gs_iters < 0 || d->gs_iters > 200) return IFGF_EINVAL;
+  if (d->precision != IFGF_FP64 && d->precision != IFGF_FP32) return IFGF_EINVAL;
+  if (d->far_mode != IFGF_FAR_IFGF && d->far_mode != IFGF_FAR_DIRECT) return IFGF_EINVAL;
+  if (d->max_krylov < 0 || d->max_krylov > 1000) return IFGF_EINVAL;
+  if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
+  if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
+  return IFGF_OK;
+}
+
+void build(ifgf_plan_t* p) {
+  const ifgf_plan_desc& d = p->desc;
+  Alloc A{p};
+  const int N = p->N, P = p->P, nc = p->nc, ng = p->ng, npp = nc * nc;
+  check(cudaGetDevice(&p->device), "cudaGetDevice");
+  check(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device), "attr");
+  // ---------------- host octree and cone segments
+  double leaf = d.leaf_size > 0 ? d.leaf_size : 0.25 * 2.0 * kPi / d.k_ext;
+  double kmax = std::max(d.k_ext, d.k_int);
+  build_tree(p->tree, d.nodes, N, leaf, d.min_levels > 0 ? d.min_levels : 3, kmax, d.ns0, d.na0);
+  const HostTree& t = p->tree;
+  // ---------------- node geometry
+  p->geo.x = A.upload(d.nodes, 3 * (size_t)N);
+  p->geo.xu = A.upload(d.dxdu, 3 * (size_t)N);
+  p->geo.xv = A.upload(d.dxdv, 3 * (size_t)N);
+  p->geo.n = A.dev<double>(3 * (size_t)N);
+  p->geo.t1 = A.dev<double>(3 * (size_t)N);
+  p->geo.t2 = A.dev<double>(3 * (size_t)N);
+  p->geo.J = A.dev<double>(N);
+  p->geo.w = A.dev<double>(N);
+  p->geo.g = A.dev<double>(3 * (size_t)N);
+  double* fej = A.dev<double>(nc);
+  double* Anc = A.dev<double>(npp);
+  p->tab_D = A.dev<double>(npp);
+  k_cheb_tables<<<(npp + 127) / 128, 128>>>(nc, fej, Anc, p->tab_D);
+  k_node_geom<<<(N + 127) / 128, 128>>>(N, nc, fej, p->geo);
+  double* Ang = A.dev<double>((size_t)ng * ng);
+  k_cheb_tables<<<(ng * ng + 127) / 128, 128>>>(ng, nullptr, Ang, nullptr);
+  double* fine = A.upload(d.fine, (size_t)P * ng * ng * 9);
+  double* fcoef = A.dev<double>((size_t)P * ng * ng * 9);
+  k_fine_coefs<<<P, 256>>>(ng, Ang, fine, fcoef);
+  double* unodes_h = new double[nc];
+  for (int k = 0; k < nc; ++k) unodes_h[k] = cheb_node(k, nc);
+  double* unodes = A.upload(unodes_h, nc);
+  delete[] unodes_h;
+  check(cudaGetLastError(), "geometry kernels");
+  // sorted geometry, permutations, leaf coordinates
+  {
+    std::vector<double> xs(3 * (size_t)N), ns(3 * (size_t)N);
+    std::vector<double> nrm(3 * (size_t)N);
+    check(cudaDeviceSynchronize(), "geometry sync");
+    check(cudaMemcpy(nrm.data(), p->geo.n, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost), "normals D2H");
+    for (int s = 0; s < N; ++s)
+      for (int k = 0; k < 3; ++k) {
+        xs[3 * (size_t)s + k] = d.nodes[3 * (size_t)t.perm[s] + k];
+        ns[3 * (size_t)s + k] = nrm[3 * (size_t)t.perm[s] + k];
+      }
+    p->x_sorted = A.upload(xs);
+    p->n_sorted = A.upload(ns);
+    std::vector<int> pp(2 * (size_t)N);
+    for (int s = 0; s < N; ++s) {
+      pp[s] = t.perm[s];
+      pp[N + s] = t.iperm[s];
+    }
+    p->perm = A.upload(pp);
+    std::vector<int> lc(3 * (size_t)N);
+    for (int l = 0; l < N; ++l)
+      for (int k = 0; k < 3; ++k) lc[3 * (size_t)l + k] = t.leafc[l][k];
+    p->leafc = A.upload(lc);
+  }
+  // ---------------- near field: candidates, closest points, singular moments, matrix
+  {
+    std::vector<double> gap;
+    std::vector<int64_t> cptr;
+    std::vector<int> cpatch;
+    near_candidates(d.nodes, P, nc, d.delta, gap, cptr, cpatch);
+    const int npairs = (int)cpatch.size();
+    std::vector<int> ptgt(npairs);
+    for (int l = 0; l < N; ++l)
+      for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) ptgt[e] = l;
+    int* d_ptgt = A.upload(ptgt);
+    int* d_ppatch = A.upload(cpatch);
+    double* d_uv = A.dev<double>(2 * (size_t)npairs);
+    uint8_t* d_sing = A.dev<uint8_t>(npairs);
+    int iters = d.gs_iters > 0 ? d.gs_iters : 60;
+    k_closest<<<(npairs + 127) / 128, 128>>>(npairs, nc, ng, iters, d.delta, d_ptgt, d_ppatch, p->geo.x,
+                                             fcoef, unodes, d_uv, d_sing);
+    check(cudaGetLastError(), "k_closest launch");
+    std::vector<uint8_t> sing(npairs);
+    check(cudaMemcpy(sing.data(), d_sing, npairs, cudaMemcpyDeviceToHost), "singular flags D2H");
+    std::vector<int> sp_pair, sp_of_pair(npairs, -1);
+    for (int e = 0; e < npairs; ++e)
+      if (sing[e]) {
+        sp_of_pair[e] = (int)sp_pair.size();
+        sp_pair.push_back(e);
+      }
+    const int nsp = (int)sp_pair.size();
+    p->stats.singular_pairs = nsp;
+    int* d_sp_pair = A.upload(sp_pair);
+    int* d_sp_of = A.upload(sp_of_pair);
+    double* W = A.dev<double>((size_t)nsp * 8 * npp);
+    std::vector<double> tb(d.n_beta);
+    for (int k = 0; k < d.n_beta; ++k) tb[k] = cheb_node(k, d.n_beta);
+    double* d_tb = A.upload(tb);
+    double* d_wb = A.dev<double>(d.n_beta);
+    k_cheb_tables<<<1, 128>>>(d.n_beta, d_wb, nullptr, nullptr);
+    size_t smw = moments_smem_per_warp(nc, ng, d.n_beta);
+    int wpb = 1;
+    check(cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smw * wpb)),
+          "moments smem attr");
+    if (nsp > 0)
+      k_moments<<<(nsp + wpb - 1) / wpb, 32 * wpb, smw * wpb>>>(nsp, d_sp_pair, d_ptgt, d_ppatch, d_uv, nc, ng,
+          d.n_beta, d.cov_d, d_tb, d_wb, Anc, p->geo.x, p->geo.n, fcoef, d.k_ext, d.k_int, W);
+    check(cudaGetLastError(), "k_moments launch");
+    std::vector<int64_t> row_ptr;
+    std::vector<int> col, pair;
+    near_structure(t, P, nc, cptr, cpatch, sing, row_ptr, col, pair);
+    p->near.nnz = (int64_t)col.size();
+    p->stats.near_nnz = p->near.nnz;
+    p->near.row_ptr = A.upload(row_ptr);
+    p->near.col = A.upload(col);
+    int* d_pair = A.upload(pair);
+    p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);
+    p->near.val32 = A.dev<float>(8 * (size_t)p->near.nnz);
+    k_near_values<<<(unsigned)(((size_t)N * 32 + 255) / 256), 256>>>(N, nc, p->near.row_ptr, p->near.col, d_pair,
+        d_sp_of, W, p->geo.x, p->geo.n, p->geo.w, p->leafc, d.k_ext, d.k_int, p->near.val64, p->near.val32);
+    check(cudaGetLastError(), "k_near_values launch");
+    check(cudaDeviceSynchronize(), "near setup");
+  }
+  // ---------------- IFGF level tables
+  p->dl.assign(t.D + 1, DevLevel());
+  for (int dd = 3; dd <= t.D; ++dd) {
+    const HostLevel& L = t.lv[dd];
+    DevLevel& Dl = p->dl[dd];
+    Dl.d = dd;
+    Dl.nboxes = (int)L.key.size();
+    Dl.nslots = (int)L.slot_box.size();
+    Dl.cg = L.cg();
+    Dl.H = L.H;
+    std::vector<double> cen(3 * (size_t)Dl.nboxes);
+    for (int b = 0; b < Dl.nboxes; ++b)
+      for (int k = 0; k < 3; ++k) cen[3 * (size_t)b + k] = t.corner[k] + L.H * (L.ic[b][k] + 0.5);
+    Dl.box_center = A.upload(cen);
+    Dl.cone_map = A.upload(L.cone_map);
+    Dl.slot_box = A.upload(L.slot_box);
+    Dl.slot_cone = A.upload(L.slot_cone);
+    Dl.box_slot_ptr = A.upload(L.box_slot_ptr);
+    std::vector<int> bp(Dl.nboxes + 1);
+    for (int b = 0; b < Dl.nboxes; ++b) bp[b] = L.pt_begin[b];
+    bp[Dl.nboxes] = N;
+    Dl.box_pt_ptr = A.upload(bp);
+    std::vector<int> ch(8 * (size_t)Dl.nboxes);
+    for (int b = 0; b < Dl.nboxes; ++b)
+      for (int o = 0; o < 8; ++o) ch[8 * (size_t)b + o] = L.child[b][o];
+    Dl.child = A.upload(ch);
+    Dl.slot_upidx = A.upload(L.slot_upidx);
+    Dl.up_cc = A.upload(L.up_cc);
+    Dl.tgt_ptr = A.upload(L.tgt_ptr);
+    Dl.tgt_slot = A.upload(L.tgt_slot);
+    Dl.ninter = (int64_t)L.tgt_slot.size();
+    size_t creal = (size_t)Dl.nslots * kQ * 32;
+    if (d.far_mode == IFGF_FAR_IFGF) {
+      if (d.precision == IFGF_FP64)
+        Dl.coefs = A.dev<double>(creal);
+      else
+        Dl.coefs = A.dev<float>(creal);
+    }
+    p->stats.boxes[dd] = Dl.nboxes;
+    p->stats.cones[dd] = Dl.nslots;
+    p->stats.ns[dd] = L.ns;
+    p->stats.na[dd] = L.na;
+    p->stats.interactions[dd] = Dl.ninter;
+  }
+  for (int dd = 1; dd < 3 && dd <= t.D; ++dd) p->stats.boxes[dd] = (int)t.lv[dd].key.size();
+  {
+    const HostLevel& L = t.lv[t.D];
+    int64_t lp = 0;
+    for (size_t b = 0; b < L.key.size(); ++b)
+      lp += (int64_t)(L.pt_end[b] - L.pt_begin[b]) * (L.box_slot_ptr[b + 1] - L.box_slot_ptr[b]) * kQ;
+    p->stats.leaf_pairs = lp;
+    int64_t up = 0;
+    for (int dd = t.D; dd > 3; --dd) {
+      const HostLevel& Pp = t.lv[dd - 1];
+      for (size_t s = 0; s < Pp.slot_box.size(); ++s) {
+        int nchild = 0;
+        for (int o = 0; o < 8; ++o) nchild += Pp.child[Pp.slot_box[s]][o] >= 0;
+        up += (int64_t)nchild * kQ;
+      }
+    }
+    p->stats.up_pairs = up;
+  }
+  p->stats.n = N;
+  p->stats.levels = t.D;
+  // ---------------- per-apply buffers and GMRES workspace
+  const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
+  p->phi = A.dev<char>(16 * (size_t)N * el);
+  p->a_sorted = A.dev<char>(16 * (size_t)N * el);
+  p->a_orig = A.dev<char>(16 * (size_t)N * el);
+  p->f28 = A.dev<char>(56 * (size_t)N * el);
+  p->phi64 = A.dev<double>(16 * (size_t)N);
+  GmresWork& G = p->gm;
+  G.max_iter = d.max_krylov > 0 ? d.max_krylov : 300;
+  const size_t n4 = 4 * (size_t)N;
+  G.V = A.dev<double>(2 * n4 * (G.max_iter + 1));
+  G.H = A.dev<double>(2 * (size_t)(G.max_iter + 1) * (G.max_iter + 1));
+  G.cs = A.dev<double>(2 * (size_t)(G.max_iter + 1));
+  G.sn = A.dev<double>(2 * (size_t)(G.max_iter + 1));
+  G.g = A.dev<double>(2 * (size_t)(G.max_iter + 1));
+  G.h = A.dev<double>(4 * (size_t)(G.max_iter + 1));
+  G.part = A.dev<double>(2 * (size_t)dots_blocks((int64_t)n4) * (G.max_iter + 1));
+  G.scal = A.dev<double>(8);
+  G.w = A.dev<double>(2 * n4);
+  G.b = A.dev<double>(2 * n4);
+  G.y = A.dev<double>(2 * n4);
+  G.inc = A.dev<double>(12 * (size_t)N);
+  check(cudaMallocHost(&G.hres, 4 * sizeof(double)), "pinned scalar");
+  p->timer.pool.assign(256, nullptr);
+  p->timer.kind.assign(128, 0);
+  for (auto& e : p->timer.pool) check(cudaEventCreate(&e), "event");
+  check(cudaDeviceSynchronize(), "plan_create sync");
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+cudaError_t forward(ifgf_plan_t* p, const double* y, double* out, cudaStream_t s) {
+  cudaError_t e;
+  if (p->timer.on && p->timer.npending > 0 && (e = timer_flush(p)) != cudaSuccess) return e;
+  int r = timer_begin(p, TK_PREP, s);
+  if ((e = launch_density_prep(p, y, nullptr, s)) != cudaSuccess) return e;
+  timer_end(p, r, s);
+  r = timer_begin(p, TK_NEAR, s);
+  if ((e = launch_near(p, s)) != cudaSuccess) return e;
+  timer_end(p, r, s);
+  p->launches += 3;   // prep, near, combine
+  if (p->desc.far_mode == IFGF_FAR_IFGF) {
+    if ((e = launch_far_ifgf(p, s)) != cudaSuccess) return e;
+  } else {
+    r = timer_begin(p, TK_FAR_DIRECT, s);
+    if ((e = launch_far_direct(p, s)) != cudaSuccess) return e;
+    timer_end(p, r, s);
+    ++p->launches;
+  }
+  r = timer_begin(p, TK_COMBINE, s);
+  if ((e = launch_combine(p, y, out, s)) != cudaSuccess) return e;
+  timer_end(p, r, s);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+int timer_begin(ifgf_plan_t* p, int kind, cudaStream_t s) {
+  KernelTimer& T = p->timer;
+  if (!T.on) return -1;
+  if (2 * (T.npending + 1) > (int)T.pool.size()) {
+    if (timer_flush(p) != cudaSuccess) return -1;
+  }
+  int r = T.npending++;
+  T.kind[r] = kind;
+  cudaEventRecord(T.pool[2 * r], s);
+  return r;
+}
+
+void timer_end(ifgf_plan_t* p, int rec, cudaStream_t s) {
+  if (rec < 0) return;
+  cudaEventRecord(p->timer.pool[2 * rec + 1], s);
+}
+
+cudaError_t timer_flush(ifgf_plan_t* p) {
+  KernelTimer& T = p->timer;
+  if (T.npending == 0) return cudaSuccess;
+  cudaError_t e = cudaEventSynchronize(T.pool[2 * T.npending - 1]);
+  if (e != cudaSuccess) return e;
+  for (int r = 0; r < T.npending; ++r) {
+    float ms = 0;
+    if ((e = cudaEventElapsedTime(&ms, T.pool[2 * r], T.pool[2 * r + 1])) != cudaSuccess) return e;
+    T.total_ms[T.kind[r]] += ms;
+    T.calls[T.kind[r]] += 1;
+  }
+  T.npending = 0;
+  return cudaSuccess;
+}
+
+}  // namespace ifgf
+
+using namespace ifgf;
+
+extern "C" {
+
+const char* ifgf_status_string(ifgf_status s) {
+  switch (s) {
+    case IFGF_OK: return "ok";
+    case IFGF_EINVAL: return "invalid argument";
+    case IFGF_ENOMEM: return "out of memory";
+    case IFGF_ECUDA: return g_last_err[0] ? g_last_err : "CUDA error";
+    case IFGF_ENOCONV: return "GMRES did not reach the tolerance";
+    case IFGF_ETIMEOUT: return "device wait timed out";
+    case IFGF_EUNSUPPORTED: return "unsupported option";
+    case IFGF_EINTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+ifgf_status ifgf_plan_create(const ifgf_plan_desc* desc, ifgf_plan* out) {
+  if (!out) return IFGF_EINVAL;
+  *out = nullptr;
+  ifgf_status st = validate(desc);
+  if (st != IFGF_OK) return st;
+  auto t0 = std::chrono::steady_clock::now();
+  ifgf_plan_t* p = new (std::nothrow) ifgf_plan_t();
+  if (!p) return IFGF_ENOMEM;
+  p->desc = *desc;
+  p->P = desc->num_patches;
+  p->nc = desc->nc;
+  p->ng = desc->ng;
+  p->N = p->P * p->nc * p->nc;
+  p->omega = desc->k_ext / std::sqrt(desc->eps_ext * desc->mu_ext);
+  try {
+    build(p);
+  } catch (const std::bad_alloc&) {
+    free_all(p);
+    delete p;
+    return IFGF_ENOMEM;
+  } catch (const std::invalid_argument& e) {
+    snprintf(g_last_err, sizeof(g_last_err), "%s", e.what());
+    free_all(p);
+    delete p;
+    return IFGF_EINVAL;
+  } catch (const std::exception& e) {
+    if (!g_last_err[0]) snprintf(g_last_err, sizeof(g_last_err), "%s", e.what());
+    free_all(p);
+    delete p;
+    return IFGF_ECUDA;
+  }
+  // descriptor pointers belong to the caller: do not keep them
+  p->desc.nodes = p->desc.dxdu = p->desc.dxdv = p->desc.fine = nullptr;
+  p->stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = p;
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_destroy(ifgf_plan plan) {
+  if (!plan) return IFGF_OK;
+  cudaDeviceSynchronize();
+  free_all(plan);
+  delete plan;
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_apply(ifgf_plan p, const void* y, void* out, ifgf_stream stream) {
+  if (!p || !y || !out || y == out) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = forward(p, (const double*)y, (double*)out, s);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_apply", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t which, ifgf_stream stream) {
+  if (!p || !phi || !f28 || which < 1 || which > 3) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_density_prep(p, nullptr, (const double*)phi, s);
+  if (e == cudaSuccess) e = (which & IFGF_PART_NEAR) ? launch_near(p, s) : launch_zero_f28(p, s);
+  if (e == cudaSuccess && (which & IFGF_PART_FAR))
+    e = (p->desc.far_mode == IFGF_FAR_IFGF) ? launch_far_ifgf(p, s) : launch_far_direct(p, s);
+  if (e == cudaSuccess) e = launch_f28_export(p, (double*)f28, s);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_apply_fields", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter, void* y, int32_t* iters,
+                      double* relres, ifgf_stream stream) {
+  if (!p || !inc || !y || !(tol > 0) || max_iter < 1) return IFGF_EINVAL;
+  if (max_iter > p->gm.max_iter) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n4 = 4 * (size_t)p->N;
+  cudaError_t e = cudaSuccess;
+  const double* dinc = (const double*)inc;
+  if (!is_device_ptr(inc)) {
+    e = cudaMemcpyAsync(p->gm.inc, inc, sizeof(double) * 12 * (size_t)p->N, cudaMemcpyHostToDevice, s);
+    dinc = p->gm.inc;
+  }
+  if (e == cudaSuccess) e = launch_rhs(p, dinc, p->gm.b, s);
+  ++p->launches;
+  int it = 0;
+  double rr = 0;
+  if (e == cudaSuccess) {
+    MatvecFn mv = [p](const double* v, double* w, cudaStream_t st) { return forward(p, v, w, st); };
+    e = gmres_run(p, mv, tol, max_iter, &it, &rr, s);
+  }
+  if (e == cudaSuccess) {
+    if (is_device_ptr(y))
+      e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4, cudaMemcpyDeviceToDevice, s);
+    else
+      e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "bie_solve", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rr;
+  return rr <= tol ? IFGF_OK : IFGF_ENOCONV;
+}
+
+ifgf_status ifgf_plan_stats(ifgf_plan p, ifgf_stats* st) {
+  if (!p || !st) return IFGF_EINVAL;
+  *st = p->stats;
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_set_timing(ifgf_plan p, int32_t enable) {
+  if (!p) return IFGF_EINVAL;
+  if (timer_flush(p) != cudaSuccess) return IFGF_ECUDA;
+  p->timer.on = enable != 0;
+  for (int k = 0; k < TK_COUNT; ++k) {
+    p->timer.total_ms[k] = 0;
+    p->timer.calls[k] = 0;
+  }
+  p->launches = 0;
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_get_timing(ifgf_plan p, double* ms, int64_t* calls, int64_t* launches) {
+  if (!p) return IFGF_EINVAL;
+  if (timer_flush(p) != cudaSuccess) return IFGF_ECUDA;
+  for (int k = 0; k < TK_COUNT; ++k) {
+    if (ms) ms[k] = p->timer.total_ms[k];
+    if (calls) calls[k] = p->timer.calls[k];
+  }
+  if (launches) *launches = p->launches;
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_tree(ifgf_plan p, ifgf_tree* out) {
+  if (!p || !out) return IFGF_EINVAL;
+  *out = &p->tree;
+  return IFGF_OK;
+}
+
+}  // extern "C"

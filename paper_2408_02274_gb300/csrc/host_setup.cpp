@@ -1,0 +1,368 @@
+// One-time host setup of the IFGF octree and cone segments (Sec. III-F):
+// relevant boxes (Eq. rele_boxes), neighbours and cousins (Eqs. box_neighbor,
+// box_cousin), cone-segment counts per level (Remark 2), relevant cone
+// segments (Eq. rele_cone_d) and the per-target evaluation lists of step 3 of
+// the algorithm summary.  Integer and FP64 geometric work only.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "host_setup.h"
+
+namespace ifgf {
+
+static uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+static uint64_t morton(int x, int y, int z) {
+  return spread3((uint64_t)x) | (spread3((uint64_t)y) << 1) | (spread3((uint64_t)z) << 2);
+}
+
+// Cone segment of the point (x, y, z) relative to a box centre (Eq. box_cone_seg):
+// half-open cells in s, theta, phi, clamped at the top (reading of the cone intervals).
+int cone_of(const ConeGeom& cg, double x, double y, double z) {
+  double rho = std::sqrt(x * x + y * y);
+  double r = std::sqrt(rho * rho + z * z);
+  double s = cg.h / r;
+  double th = std::atan2(rho, z);
+  double ph = std::atan2(y, x);
+  if (ph < 0) ph += 2 * kPi;
+  int g1 = (int)std::floor(s / cg.ds());
+  int g2 = (int)std::floor(th / cg.dth());
+  int g3 = (int)std::floor(ph / cg.dth());
+  g1 = std::min(std::max(g1, 0), cg.ns - 1);
+  g2 = std::min(std::max(g2, 0), cg.na - 1);
+  g3 = std::min(std::max(g3, 0), 2 * cg.na - 1);
+  return cone_encode(g1, g2, g3, cg.na);
+}
+
+// Interpolation point q of a cone segment relative to the box centre:
+// tensor product of Ps x Pa x Pa open Chebyshev nodes mapped to the cone domain.
+void interp_point(const ConeGeom& cg, int cone, int q, double* X) {
+  int g1, g2, g3;
+  cone_decode(cone, cg.na, &g1, &g2, &g3);
+  int is = q / (kPa * kPa), it = (q / kPa) % kPa, ip = q % kPa;
+  double s = (g1 + 0.5 * (1.0 + cheb_node(is, kPs))) * cg.ds();
+  double th = (g2 + 0.5 * (1.0 + cheb_node(it, kPa))) * cg.dth();
+  double ph = (g3 + 0.5 * (1.0 + cheb_node(ip, kPa))) * cg.dth();
+  double r = cg.h / s;
+  X[0] = r * std::sin(th) * std::cos(ph);
+  X[1] = r * std::sin(th) * std::sin(ph);
+  X[2] = r * std::cos(th);
+}
+
+static void box_center(const HostTree& t, int d, const std::array<int, 3>& ic, double* c) {
+  double H = t.lv[d].H;
+  for (int a = 0; a < 3; ++a) c[a] = t.corner[a] + H * (ic[a] + 0.5);
+}
+
+void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_levels,
+                double k_max, int ns0, int na0) {
+  if (N <= 0) throw std::invalid_argument("no nodes");
+  double lo[3] = {x[0], x[1], x[2]}, hi[3] = {x[0], x[1], x[2]};
+  for (int i = 0; i < N; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], x[3 * i + a]);
+      hi[a] = std::max(hi[a], x[3 * i + a]);
+    }
+  double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  if (!(ext > 0)) throw std::invalid_argument("degenerate bounding box");
+  // level-1 cube: slightly larger than the bounding box, centred on it (reading R11)
+  t.H1 = ext * (1.0 + 1e-9);
+  for (int a = 0; a < 3; ++a) t.corner[a] = 0.5 * (lo[a] + hi[a]) - 0.5 * t.H1;
+  int D = std::max(3, min_levels);
+  while (t.H1 / std::ldexp(1.0, D - 1) > leaf_size && D < 21) ++D;
+  t.D = D;
+  t.lv.assign(D + 1, HostLevel());
+  for (int d = 1; d <= D; ++d) {
+    t.lv[d].d = d;
+    t.lv[d].H = t.H1 / std::ldexp(1.0, d - 1);
+    t.lv[d].h = 0.5 * std::sqrt(3.0) * t.lv[d].H;
+  }
+  // cone counts (Remark 2, reading R9): n_{.;d} = a_d n_{.;d+1}, a_d = 2 iff k_max H_d > 1/2
+  int ns = ns0, na = na0;
+  for (int d = D; d >= 1; --d) {
+    int a = (k_max * t.lv[d].H > 0.5) ? 2 : 1;
+    if (d >= 3) {
+      ns *= a;
+      na *= a;
+    }
+    t.lv[d].ns = (d >= 3) ? ns : 0;
+    t.lv[d].na = (d >= 3) ? na : 0;
+  }
+  // leaf keys and Morton order
+  const int nside = 1 << (D - 1);
+  const double HD = t.lv[D].H;
+  t.leafc.resize(N);
+  std::vector<uint64_t> key(N);
+  for (int i = 0; i < N; ++i) {
+    std::array<int, 3> k;
+    for (int a = 0; a < 3; ++a) {
+      int v = (int)std::floor((x[3 * i + a] - t.corner[a]) / HD);
+      k[a] = std::min(std::max(v, 0), nside - 1);
+    }
+    t.leafc[i] = k;
+    key[i] = morton(k[0], k[1], k[2]);
+  }
+  t.perm.resize(N);
+  for (int i = 0; i < N; ++i) t.perm[i] = i;
+  std::stable_sort(t.perm.begin(), t.perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+  t.iperm.resize(N);
+  for (int s = 0; s < N; ++s) t.iperm[t.perm[s]] = s;
+  // relevant boxes per level (Eq. rele_boxes): runs of equal key prefixes in Morton order
+  t.box_of.assign(D + 1, std::vector<int>(N, -1));
+  for (int d = D; d >= 1; --d) {
+    HostLevel& L = t.lv[d];
+    int shift = 3 * (D - d);
+    uint64_t prev = ~0ULL;
+    for (int s = 0; s < N; ++s) {
+      uint64_t k = key[t.perm[s]] >> shift;
+      if (k != prev) {
+        if (!L.key.empty()) L.pt_end.push_back(s);
+        L.key.push_back(k);
+        L.pt_begin.push_back(s);
+        const auto& lc = t.leafc[t.perm[s]];
+        L.ic.push_back({lc[0] >> (D - d), lc[1] >> (D - d), lc[2] >> (D - d)});
+        prev = k;
+      }
+      t.box_of[d][s] = (int)L.key.size() - 1;
+    }
+    L.pt_end.push_back(N);
+    for (int b = 0; b < (int)L.key.size(); ++b) L.index[L.key[b]] = b;
+  }
+  // parents, children
+  for (int d = 1; d <= D; ++d) {
+    HostLevel& L = t.lv[d];
+    int nb = (int)L.key.size();
+    L.parent.assign(nb, -1);
+    L.child.assign(nb, {-1, -1, -1, -1, -1, -1, -1, -1});
+    if (d > 1) {
+      HostLevel& Pp = t.lv[d - 1];
+      for (int b = 0; b < nb; ++b) {
+        int p = Pp.index.at(L.key[b] >> 3);
+        L.parent[b] = p;
+        int o = (L.ic[b][0] & 1) | ((L.ic[b][1] & 1) << 1) | ((L.ic[b][2] & 1) << 2);
+        Pp.child[p][o] = b;
+      }
+    }
+  }
+  // neighbours (infinity-norm, reading R10) and cousins
+  for (int d = 1; d <= D; ++d) {
+    HostLevel& L = t.lv[d];
+    int nb = (int)L.key.size();
+    int side = 1 << (d - 1);
+    L.nbr.assign(nb, {});
+    for (int b = 0; b < nb; ++b) {
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            int X = L.ic[b][0] + dx, Y = L.ic[b][1] + dy, Z = L.ic[b][2] + dz;
+            if (X < 0 || Y < 0 || Z < 0 || X >= side || Y >= side || Z >= side) continue;
+            auto it = L.index.find(morton(X, Y, Z));
+            if (it != L.index.end()) L.nbr[b].push_back(it->second);
+          }
+      std::sort(L.nbr[b].begin(), L.nbr[b].end());
+    }
+    L.cousin.assign(nb, {});
+    if (d >= 2) {
+      HostLevel& Pp = t.lv[d - 1];
+      for (int b = 0; b < nb; ++b) {
+        for (int pn : Pp.nbr[L.parent[b]])
+          for (int o = 0; o < 8; ++o) {
+            int c = Pp.child[pn][o];
+            if (c < 0) continue;
+            if (!std::binary_search(L.nbr[b].begin(), L.nbr[b].end(), c)) L.cousin[b].push_back(c);
+          }
+        std::sort(L.cousin[b].begin(), L.cousin[b].end());
+      }
+    }
+  }
+  // relevant cone segments, top-down from level 3 (Eq. rele_cone_d), and the
+  // per-target evaluation lists of step 3 (cousin points of every source box)
+  for (int d = 3; d <= D; ++d) {
+    HostLevel& L = t.lv[d];
+    ConeGeom cg = L.cg();
+    const int nb = (int)L.key.size();
+    const int nco = cg.ncones();
+    std::vector<uint8_t> mark((size_t)nb * nco, 0);
+    // (1) cones containing cousin points; record (target, box, cone)
+    std::vector<int64_t> ptr(N + 1, 0);
+    std::vector<int> rb, rc;
+    for (int s = 0; s < N; ++s) {
+      const double* xs = x + 3 * (size_t)t.perm[s];
+      int A = t.box_of[d][s];
+      for (int B : L.cousin[A]) {
+        double c[3];
+        box_center(t, d, L.ic[B], c);
+        int cone = cone_of(cg, xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]);
+        mark[(size_t)B * nco + cone] = 1;
+        rb.push_back(B);
+        rc.push_back(cone);
+      }
+      ptr[s + 1] = (int64_t)rb.size();
+    }
+    // (2) cones containing interpolation points of the parent's relevant cones
+    if (d >= 4) {
+      HostLevel& Pp = t.lv[d - 1];
+      ConeGeom pg = Pp.cg();
+      int ncomp = (int)Pp.upcone_list.size();
+      Pp.up_cc.assign((size_t)ncomp * 8 * kQ, -1);
+      for (int ci = 0; ci < ncomp; ++ci) {
+        int pc = Pp.upcone_list[ci];
+        for (int q = 0; q < kQ; ++q) {
+          double X[3];
+          interp_point(pg, pc, q, X);
+          for (int o = 0; o < 8; ++o) {
+            double off = 0.5 * L.H;
+            double cx = X[0] - off * ((o & 1) ? 1 : -1);
+            double cy = X[1] - off * ((o & 2) ? 1 : -1);
+            double cz = X[2] - off * ((o & 4) ? 1 : -1);
+            Pp.up_cc[((size_t)ci * 8 + o) * kQ + q] = cone_of(cg, cx, cy, cz);
+          }
+        }
+      }
+      for (int b = 0; b < nb; ++b) {
+        int p = L.parent[b];
+        int o = (L.ic[b][0] & 1) | ((L.ic[b][1] & 1) << 1) | ((L.ic[b][2] & 1) << 2);
+        for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps) {
+          int ci = Pp.slot_upidx[ps];
+          for (int q = 0; q < kQ; ++q) mark[(size_t)b * nco + Pp.up_cc[((size_t)ci * 8 + o) * kQ + q]] = 1;
+        }
+      }
+    }
+    // slots: relevant (box, cone) pairs sorted by box then cone
+    L.cone_map.assign((size_t)nb * nco, -1);
+    L.box_slot_ptr.assign(nb + 1, 0);
+    L.relcones.assign(nb, {});
+    for (int b = 0; b < nb; ++b) {
+      for (int c = 0; c < nco; ++c)
+        if (mark[(size_t)b * nco + c]) {
+          L.cone_map[(size_t)b * nco + c] = (int)L.slot_box.size();
+          L.slot_box.push_back(b);
+          L.slot_cone.push_back(c);
+          L.relcones[b].push_back(c);
+        }
+      L.box_slot_ptr[b + 1] = (int)L.slot_box.size();
+    }
+    // compact list of this level's relevant cone ids, for the upward step into it
+    {
+      std::vector<int> used(nco, -1);
+      for (int c : L.slot_cone) used[c] = 1;
+      L.upcone_list.clear();
+      for (int c = 0; c < nco; ++c)
+        if (used[c] > 0) {
+          used[c] = (int)L.upcone_list.size();
+          L.upcone_list.push_back(c);
+        }
+      L.slot_upidx.resize(L.slot_cone.size());
+      for (size_t s = 0; s < L.slot_cone.size(); ++s) L.slot_upidx[s] = used[L.slot_cone[s]];
+    }
+    L.tgt_ptr = ptr;
+    L.tgt_slot.resize(rb.size());
+    for (size_t e = 0; e < rb.size(); ++e) L.tgt_slot[e] = L.cone_map[(size_t)rb[e] * nco + rc[e]];
+  }
+}
+
+void near_candidates(const double* x, int P, int nc, double delta, std::vector<double>& gap,
+                     std::vector<int64_t>& cptr, std::vector<int>& cpatch) {
+  const int npp = nc * nc;
+  const int N = P * npp;
+  gap.assign(P, 0.0);
+  std::vector<double> cen(3 * P, 0.0), rad(P, 0.0);
+  auto X = [&](int p, int i, int j) { return x + 3 * ((size_t)p * npp + i * nc + j); };
+  for (int p = 0; p < P; ++p) {
+    double g = 0;
+    for (int i = 0; i + 1 < nc; ++i)
+      for (int j = 0; j + 1 < nc; ++j) {
+        const double *a = X(p, i, j), *b = X(p, i + 1, j + 1), *c = X(p, i + 1, j), *e = X(p, i, j + 1);
+        double d1 = 0, d2 = 0;
+        for (int k = 0; k < 3; ++k) {
+          d1 += (a[k] - b[k]) * (a[k] - b[k]);
+          d2 += (c[k] - e[k]) * (c[k] - e[k]);
+        }
+        g = std::max(g, std::max(std::sqrt(d1), std::sqrt(d2)));
+      }
+    gap[p] = 2.0 * g;   // twice the largest node-cell diagonal (reading R15)
+    for (int m = 0; m < npp; ++m)
+      for (int k = 0; k < 3; ++k) cen[3 * p + k] += x[3 * ((size_t)p * npp + m) + k] / npp;
+    for (int m = 0; m < npp; ++m) {
+      double dd = 0;
+      for (int k = 0; k < 3; ++k) {
+        double v = x[3 * ((size_t)p * npp + m) + k] - cen[3 * p + k];
+        dd += v * v;
+      }
+      rad[p] = std::max(rad[p], std::sqrt(dd));
+    }
+  }
+  cptr.assign(N + 1, 0);
+  cpatch.clear();
+  for (int l = 0; l < N; ++l) {
+    const double* xl = x + 3 * (size_t)l;
+    int pl = l / npp;
+    for (int p = 0; p < P; ++p) {
+      bool cand = (p == pl);
+      if (!cand) {
+        double dc = 0;
+        for (int k = 0; k < 3; ++k) dc += (xl[k] - cen[3 * p + k]) * (xl[k] - cen[3 * p + k]);
+        if (std::sqrt(dc) - rad[p] <= delta + gap[p]) {
+          double dmin = INFINITY;
+          for (int m = 0; m < npp; ++m) {
+            const double* y = x + 3 * ((size_t)p * npp + m);
+            double dd = 0;
+            for (int k = 0; k < 3; ++k) dd += (xl[k] - y[k]) * (xl[k] - y[k]);
+            dmin = std::min(dmin, std::sqrt(dd));
+          }
+          cand = dmin <= delta + gap[p];
+        }
+      }
+      if (cand) cpatch.push_back(p);
+    }
+    cptr[l + 1] = (int64_t)cpatch.size();
+  }
+}
+
+void near_structure(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
+                    const std::vector<int>& cpatch, const std::vector<uint8_t>& singular,
+                    std::vector<int64_t>& row_ptr, std::vector<int>& col, std::vector<int>& pair) {
+  const int npp = nc * nc;
+  const int N = P * npp;
+  const int D = t.D;
+  const HostLevel& L = t.lv[D];
+  row_ptr.assign(N + 1, 0);
+  col.clear();
+  pair.clear();
+  std::vector<int> mark(P, -1);   // patch -> singular pair index for the current row
+  for (int l = 0; l < N; ++l) {
+    for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e)
+      if (singular[e]) mark[cpatch[e]] = (int)e;
+    // all nodes of the singular patches of x_l (Eq. patch_sing)
+    for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e)
+      if (singular[e]) {
+        int p = cpatch[e];
+        for (int m = 0; m < npp; ++m) {
+          col.push_back(p * npp + m);
+          pair.push_back((int)e);
+        }
+      }
+    // neighbour points on regular patches (reading R12): IFGF leaves them out
+    int A = t.box_of[D][t.iperm[l]];
+    for (int B : L.nbr[A])
+      for (int s = L.pt_begin[B]; s < L.pt_end[B]; ++s) {
+        int m = t.perm[s];
+        if (mark[m / npp] >= 0) continue;
+        col.push_back(m);
+        pair.push_back(-1);
+      }
+    for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = -1;
+    row_ptr[l + 1] = (int64_t)col.size();
+  }
+}
+
+}  // namespace ifgf

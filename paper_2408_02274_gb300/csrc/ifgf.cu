@@ -1,0 +1,454 @@
+// IFGF far-field kernels (Sec. III-E to III-G, vectorised over 8 densities x
+// 2 wavenumbers as in Eq. ifgf_sum_em):
+//   (a) k_leaf:   F^D_k at the interpolation points of every relevant cone
+//                 segment of every leaf box by direct summation of Eq.
+//                 bkd_contr_ana_fac (algorithm step 2), then values ->
+//                 Chebyshev coefficients per cone (Sec. III-E interpolation).
+//   (b) k_up:     F^{d-1}_j at the parent's interpolation points: interpolate
+//                 each child's F^d_k, multiply by G(x,x_k)/G(x,x_j) and sum
+//                 over the children (algorithm step 3, second item).
+//   (c) k_target: I^d_k at the cousin points: interpolate F^d_k and multiply by
+//                 the centred factor G(x, x_k) (algorithm step 3, first item),
+//                 plus the normal derivative of the same product (Sec. III-I).
+// Coefficients are stored per cone segment as [75][32] reals: Chebyshev index
+// (i_s*5 + i_theta)*5 + i_phi, then 16 complex fields (kernel*8 + density).
+#include "kernels.h"
+
+namespace ifgf {
+
+namespace {
+
+// 1D values -> coefficients maps for 3 and 5 open Chebyshev nodes, and the nodes.
+template <typename T>
+struct SmallMaps {
+  T A3[9], A5[25];
+  T x3[3], x5[5];
+};
+
+template <typename T>
+__device__ void init_maps(SmallMaps<T>& M) {
+  int t = threadIdx.x;
+  if (t < 9) {
+    int i = t / 3, j = t % 3;
+    M.A3[t] = (T)((i == 0 ? 1.0 : 2.0) / 3.0 * cos(i * (j + 0.5) * kPi / 3.0));
+  }
+  if (t < 25) {
+    int i = t / 5, j = t % 5;
+    M.A5[t] = (T)((i == 0 ? 1.0 : 2.0) / 5.0 * cos(i * (j + 0.5) * kPi / 5.0));
+  }
+  if (t < 3) M.x3[t] = (T)cheb_node(t, 3);
+  if (t < 5) M.x5[t] = (T)cheb_node(t, 5);
+}
+
+// Interpolation point q of cone `cone` relative to the box centre.
+template <typename T>
+__device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeom& cg, int cone, int q, T* X) {
+  int g1, g2, g3;
+  cone_decode(cone, cg.na, &g1, &g2, &g3);
+  int is = q / 25, it = (q / 5) % 5, ip = q % 5;
+  T ds = (T)cg.ds(), dth = (T)cg.dth();
+  T s = ((T)g1 + T(0.5) * (T(1) + M.x3[is])) * ds;
+  T th = ((T)g2 + T(0.5) * (T(1) + M.x5[it])) * dth;
+  T ph = ((T)g3 + T(0.5) * (T(1) + M.x5[ip])) * dth;
+  T r = (T)cg.h / s;
+  T st, ct, sp, cp;
+  sincos_t(th, &st, &ct);
+  sincos_t(ph, &sp, &cp);
+  X[0] = r * st * cp;
+  X[1] = r * st * sp;
+  X[2] = r * ct;
+}
+
+// Local coordinates in [-1, 1]^3 of a point (relative to the box centre) inside cone `cone`.
+template <typename T>
+__device__ inline void local_coords(const ConeGeom& cg, int cone, T x, T y, T z, T* ts, T* tt, T* tp,
+                                    T* rr, T* sth, T* cth, T* sph, T* cph) {
+  int g1, g2, g3;
+  cone_decode(cone, cg.na, &g1, &g2, &g3);
+  T rho = sqrt_t(x * x + y * y);
+  T r = sqrt_t(rho * rho + z * z);
+  T s = (T)cg.h / r;
+  T th = atan2_t(rho, z);
+  T ph = atan2_t(y, x);
+  T dth = (T)cg.dth(), ds = (T)cg.ds();
+  T php = ph - (T)g3 * dth;
+  if (php < T(-kPi)) php += T(2 * kPi);   // phi wraps: measure from the cell start
+  if (php > T(kPi)) php -= T(2 * kPi);
+  *ts = T(2) * (s - (T)g1 * ds) / ds - T(1);
+  *tt = T(2) * (th - (T)g2 * dth) / dth - T(1);
+  *tp = T(2) * php / dth - T(1);
+  *rr = r;
+  *sth = rho / r;
+  *cth = z / r;
+  T irho = rho > T(0) ? T(1) / rho : T(0);
+  *cph = rho > T(0) ? x * irho : T(1);
+  *sph = rho > T(0) ? y * irho : T(0);
+}
+
+// In-place 3D values -> coefficients transform of one real column (stride `st`) of 75 values.
+template <typename T>
+__device__ void vals_to_coefs_col(const SmallMaps<T>& M, T* v, int st) {
+  T t5[5];
+  // phi (innermost)
+  for (int a = 0; a < 15; ++a) {
+    for (int k = 0; k < 5; ++k) t5[k] = v[(a * 5 + k) * st];
+    for (int k = 0; k < 5; ++k) {
+      T acc = 0;
+      for (int kk = 0; kk < 5; ++kk) acc += M.A5[k * 5 + kk] * t5[kk];
+      v[(a * 5 + k) * st] = acc;
+    }
+  }
+  // theta
+  for (int is = 0; is < 3; ++is)
+    for (int k = 0; k < 5; ++k) {
+      for (int j = 0; j < 5; ++j) t5[j] = v[((is * 5 + j) * 5 + k) * st];
+      for (int j = 0; j < 5; ++j) {
+        T acc = 0;
+        for (int jj = 0; jj < 5; ++jj) acc += M.A5[j * 5 + jj] * t5[jj];
+        v[((is * 5 + j) * 5 + k) * st] = acc;
+      }
+    }
+  // s
+  for (int jk = 0; jk < 25; ++jk) {
+    for (int i = 0; i < 3; ++i) t5[i] = v[(i * 25 + jk) * st];
+    for (int i = 0; i < 3; ++i) {
+      T acc = 0;
+      for (int ii = 0; ii < 3; ++ii) acc += M.A3[i * 3 + ii] * t5[ii];
+      v[(i * 25 + jk) * st] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ (a) leaf direct
+constexpr int kLeafThreads = 160;   // two cone segments (2 x 75 points) per pass
+constexpr int kLeafChunk = 256;     // sources staged per pass
+constexpr int kVS = 33;             // padded row stride of the value buffers
+
+template <typename T>
+struct LeafArgs {
+  const int* box_pt_ptr;
+  const int* box_slot_ptr;
+  const int* slot_cone;
+  const double* box_center;
+  ConeGeom cg;
+  const double* x_sorted;
+  const T* a_sorted;
+  T* coefs;
+  T ke, ki;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
+  __shared__ SmallMaps<T> M;
+  // source staging and the value buffer are never live at the same time: alias them
+  constexpr int kSrcWords = kLeafChunk * 20, kValWords = 2 * kQ * kVS;
+  __shared__ T pool[kSrcWords > kValWords ? kSrcWords : kValWords];
+  T (*src)[4] = reinterpret_cast<T (*)[4]>(pool);
+  T (*sa)[16] = reinterpret_cast<T (*)[16]>(pool + kLeafChunk * 4);
+  T* vbuf = pool;
+  const int box = blockIdx.x;
+  const int t = threadIdx.x;
+  init_maps(M);
+  const double c0 = A.box_center[3 * box], c1 = A.box_center[3 * box + 1], c2 = A.box_center[3 * box + 2];
+  const int pb = A.box_pt_ptr[box], pe = A.box_pt_ptr[box + 1];
+  const int sb = A.box_slot_ptr[box], se = A.box_slot_ptr[box + 1];
+  const int nsrc = pe - pb;
+  const T kk[2] = {A.ke, A.ki};
+  for (int s0 = sb; s0 < se; s0 += 2) {
+    const int sl = t / kQ, q = t % kQ;
+    const int slot = s0 + sl;
+    const bool act = (t < 2 * kQ) && (slot < se);
+    T X[3] = {0, 0, 0}, r = 1;
+    __syncthreads();
+    if (act) {
+      cone_point(M, A.cg, A.slot_cone[slot], q, X);
+      r = sqrt_t(X[0] * X[0] + X[1] * X[1] + X[2] * X[2]);
+    }
+    T acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] = 0;
+    for (int cb = 0; cb < nsrc; cb += kLeafChunk) {
+      const int nchunk = min(kLeafChunk, nsrc - cb);
+      __syncthreads();
+      for (int e = t; e < nchunk; e += blockDim.x) {
+        const int m = pb + cb + e;
+        T y0 = (T)(A.x_sorted[3 * (size_t)m] - c0);
+        T y1 = (T)(A.x_sorted[3 * (size_t)m + 1] - c1);
+        T y2 = (T)(A.x_sorted[3 * (size_t)m + 2] - c2);
+        src[e][0] = y0; src[e][1] = y1; src[e][2] = y2;
+        src[e][3] = y0 * y0 + y1 * y1 + y2 * y2;
+        for (int k = 0; k < 16; ++k) sa[e][k] = A.a_sorted[16 * (size_t)m + k];
+      }
+      __syncthreads();
+      if (act) {
+        for (int e = 0; e < nchunk; ++e) {
+          // g_S(X, y) = (r/|X-y|) exp(i k (|X-y| - r)), |X-y| - r = (|y|^2 - 2 X.y)/(|X-y| + r)
+          T dxy = src[e][3] - T(2) * (X[0] * src[e][0] + X[1] * src[e][1] + X[2] * src[e][2]);
+          T d = sqrt_t(r * r + dxy);
+          T rd = r / d;
+          T dd = dxy / (d + r);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            T sn, cs;
+            sincos_t(kk[ks] * dd, &sn, &cs);
+            T gr = rd * cs, gi = rd * sn;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              T ar = sa[e][2 * k], ai = sa[e][2 * k + 1];
+              acc[2 * (8 * ks + k)] += ar * gr - ai * gi;
+              acc[2 * (8 * ks + k) + 1] += ar * gi + ai * gr;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (act)
+      for (int k = 0; k < 32; ++k) vbuf[(sl * kQ + q) * kVS + k] = acc[k];
+    __syncthreads();
+    if (t < 64) {
+      const int s2 = t / 32, col = t % 32;
+      if (s0 + s2 < se) {
+        T* v = vbuf + s2 * kQ * kVS + col;
+        vals_to_coefs_col(M, v, kVS);
+        T* out = A.coefs + (size_t)(s0 + s2) * kQ * 32 + col;
+        for (int qq = 0; qq < kQ; ++qq) out[qq * 32] = v[qq * kVS];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ (b) upward pass
+constexpr int kUpThreads = 128;
+
+template <typename T>
+struct UpArgs {
+  // parent level d-1
+  const int* slot_box;
+  const int* slot_cone;
+  const int* slot_upidx;
+  const int* child;        // [nboxes_p][8]
+  ConeGeom cgp;
+  // child level d
+  const int* cone_map_c;
+  int ncones_c;
+  ConeGeom cgc;
+  double Hc;
+  const int* up_cc;        // [ncompact][8][75]
+  const T* coefs_c;
+  T* coefs_p;
+  T ke, ki;
+};
+
+template <typename T>
+struct PtInfo {
+  int cslot;
+  T ts, tt, tp;
+  T fr[2], fi[2];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
+  __shared__ SmallMaps<T> M;
+  __shared__ T Xp[kQ][3];
+  __shared__ PtInfo<T> info[kQ];
+  __shared__ T vals[kQ * kVS];
+  const int pslot = blockIdx.x;
+  const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  init_maps(M);
+  const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
+  __syncthreads();
+  if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
+  for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = 0;
+  const T off = (T)(0.5 * A.Hc);
+  const T kk[2] = {A.ke, A.ki};
+  for (int o = 0; o < 8; ++o) {
+    const int cb = A.child[8 * P + o];
+    if (cb < 0) continue;
+    __syncthreads();
+    if (t < kQ) {
+      const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
+      const T x = Xp[t][0] - ox, y = Xp[t][1] - oy, z = Xp[t][2] - oz;
+      const int cc = A.up_cc[((size_t)ci * 8 + o) * kQ + t];
+      info[t].cslot = A.cone_map_c[(size_t)cb * A.ncones_c + cc];
+      T rc, sth, cth, sph, cph;
+      local_coords(A.cgc, cc, x, y, z, &info[t].ts, &info[t].tt, &info[t].tp, &rc, &sth, &cth, &sph, &cph);
+      // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
+      const T rp = sqrt_t(Xp[t][0] * Xp[t][0] + Xp[t][1] * Xp[t][1] + Xp[t][2] * Xp[t][2]);
+      const T dr = (T(3) * off * off - T(2) * (Xp[t][0] * ox + Xp[t][1] * oy + Xp[t][2] * oz)) / (rc + rp);
+      for (int ks = 0; ks < 2; ++ks) {
+        T sn, cs;
+        sincos_t(kk[ks] * dr, &sn, &cs);
+        info[t].fr[ks] = rp / rc * cs;
+        info[t].fi[ks] = rp / rc * sn;
+      }
+    }
+    __syncthreads();
+    for (int q = warp; q < kQ; q += kUpThreads / 32) {
+      const PtInfo<T>& I = info[q];
+      if (I.cslot < 0) continue;   // cannot happen: the host marked every such cone relevant
+      T Ts[3], Tt[5], Tp[5];
+      cheb_vals<T, 3>(I.ts, Ts);
+      cheb_vals<T, 5>(I.tt, Tt);
+      cheb_vals<T, 5>(I.tp, Tp);
+      const T* C = A.coefs_c + (size_t)I.cslot * kQ * 32 + lane;
+      T v = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const T b = Ts[i] * Tt[j];
+#pragma unroll
+          for (int k = 0; k < 5; ++k) v += b * Tp[k] * __ldg(C + ((i * 5 + j) * 5 + k) * 32);
+        }
+      const T w = __shfl_xor_sync(0xffffffffu, v, 1);
+      const int ks = lane >> 4;
+      const T re = (lane & 1) ? w : v, im = (lane & 1) ? v : w;
+      const T fr = I.fr[ks], fi = I.fi[ks];
+      vals[q * kVS + lane] += (lane & 1) ? (re * fi + im * fr) : (re * fr - im * fi);
+    }
+  }
+  __syncthreads();
+  if (t < 32) {
+    vals_to_coefs_col(M, vals + t, kVS);
+    T* out = A.coefs_p + (size_t)pslot * kQ * 32 + t;
+    for (int q = 0; q < kQ; ++q) out[q * 32] = vals[q * kVS + t];
+  }
+}
+
+// ------------------------------------------------------------------ (c) target evaluation
+template <typename T>
+struct TgtArgs {
+  int N;
+  const int64_t* tgt_ptr;
+  const int* tgt_slot;
+  const int* slot_box;
+  const int* slot_cone;
+  const double* box_center;
+  ConeGeom cg;
+  const T* coefs;
+  const double* x_sorted;
+  const double* n_sorted;
+  const int* perm;
+  T* f28;
+  T ke, ki;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_target(TgtArgs<T> A) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= A.N) return;
+  const int64_t e0 = A.tgt_ptr[t], e1 = A.tgt_ptr[t + 1];
+  if (e0 == e1) return;
+  const double x0 = A.x_sorted[3 * (size_t)t], x1 = A.x_sorted[3 * (size_t)t + 1], x2 = A.x_sorted[3 * (size_t)t + 2];
+  const T n0 = (T)A.n_sorted[3 * (size_t)t], n1 = (T)A.n_sorted[3 * (size_t)t + 1], n2 = (T)A.n_sorted[3 * (size_t)t + 2];
+  const int ks = lane >> 4;
+  const T kap = ks ? A.ki : A.ke;
+  const T ds = (T)A.cg.ds(), dth = (T)A.cg.dth(), h = (T)A.cg.h;
+  T accS = 0, accD = 0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int slot = A.tgt_slot[e];
+    const int box = A.slot_box[slot], cone = A.slot_cone[slot];
+    const T xr = (T)(x0 - A.box_center[3 * box]);
+    const T yr = (T)(x1 - A.box_center[3 * box + 1]);
+    const T zr = (T)(x2 - A.box_center[3 * box + 2]);
+    T ts, tt, tp, r, sth, cth, sph, cph;
+    local_coords(A.cg, cone, xr, yr, zr, &ts, &tt, &tp, &r, &sth, &cth, &sph, &cph);
+    T Ts[3], Tt[5], Tp[5], dTs[3], dTt[5], dTp[5];
+    cheb_vals<T, 3>(ts, Ts);
+    cheb_vals<T, 5>(tt, Tt);
+    cheb_vals<T, 5>(tp, Tp);
+    cheb_dvals<T, 3>(ts, dTs);
+    cheb_dvals<T, 5>(tt, dTt);
+    cheb_dvals<T, 5>(tp, dTp);
+    // n . grad of (s, theta, phi): grad s = -(h/r^2) r_hat, grad theta = theta_hat / r,
+    // grad phi = phi_hat / (r sin theta)   (analytic derivative of the interpolant, reading R1)
+    const T ir = T(1) / r;
+    const T nr = (n0 * xr + n1 * yr + n2 * zr) * ir;
+    const T nth = n0 * cth * cph + n1 * cth * sph - n2 * sth;
+    const T nph = -n0 * sph + n1 * cph;
+    const T as = -(h * ir * ir) * nr * (T(2) / ds);
+    const T at = nth * ir * (T(2) / dth);
+    const T sthg = sth > T(1e-7) ? sth : T(1e-7);
+    const T ap = nph * ir / sthg * (T(2) / dth);
+    const T* C = A.coefs + (size_t)slot * kQ * 32 + lane;
+    T F = 0, dF = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        const T b = Ts[i] * Tt[j];
+        const T p1 = as * dTs[i] * Tt[j] + at * Ts[i] * dTt[j];
+        const T p2 = ap * b;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const T c = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
+          F += b * Tp[k] * c;
+          dF += (p1 * Tp[k] + p2 * dTp[k]) * c;
+        }
+      }
+    // centred factor G = e^{i k r}/(4 pi r) and its normal derivative (n.r_hat)(i k - 1/r) G
+    T sn, cs;
+    sincos_t(kap * r, &sn, &cs);
+    const T g = T(1.0 / (4.0 * kPi)) * ir;
+    const T Gr = g * cs, Gi = g * sn;
+    const T dGr = nr * (-ir * Gr - kap * Gi), dGi = nr * (-ir * Gi + kap * Gr);
+    const T Fw = __shfl_xor_sync(0xffffffffu, F, 1);
+    const T dFw = __shfl_xor_sync(0xffffffffu, dF, 1);
+    const bool odd = lane & 1;
+    const T Fr = odd ? Fw : F, Fi = odd ? F : Fw;
+    const T dFr = odd ? dFw : dF, dFi = odd ? dF : dFw;
+    accS += odd ? (Gr * Fi + Gi * Fr) : (Gr * Fr - Gi * Fi);
+    const T Dr = dGr * Fr - dGi * Fi + Gr * dFr - Gi * dFi;
+    const T Di = dGr * Fi + dGi * Fr + Gr * dFi + Gi * dFr;
+    accD += odd ? Di : Dr;
+  }
+  T* out = A.f28 + 56 * (size_t)A.perm[t];
+  out[lane] += accS;
+  const int dens = (lane >> 1) & 7;
+  if (dens < 6) out[2 * (16 + 6 * ks + dens) + (lane & 1)] += accD;
+}
+
+template <typename T>
+cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
+  const int D = p->tree.D;
+  const T ke = (T)p->desc.k_ext, ki = (T)p->desc.k_int;
+  {
+    const DevLevel& L = p->dl[D];
+    LeafArgs<T> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, L.cg,
+                  p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki};
+    int rec = timer_begin(p, TK_LEAF, s);
+    if (L.nboxes > 0) k_leaf<T><<<L.nboxes, kLeafThreads, 0, s>>>(A);
+    timer_end(p, rec, s);
+    ++p->launches;
+  }
+  for (int d = D; d >= 3; --d) {
+    const DevLevel& L = p->dl[d];
+    TgtArgs<T> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, L.cg,
+                 (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (T*)p->f28, ke, ki};
+    int rec = timer_begin(p, TK_TARGET, s);
+    k_target<T><<<(unsigned)(((size_t)p->N * 32 + 255) / 256), 256, 0, s>>>(B);
+    timer_end(p, rec, s);
+    ++p->launches;
+    if (d > 3) {
+      const DevLevel& Pp = p->dl[d - 1];
+      UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, Pp.cg,
+                  L.cone_map, L.cg.ncones(), L.cg, L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki};
+      rec = timer_begin(p, TK_UP, s);
+      if (Pp.nslots > 0) k_up<T><<<Pp.nslots, kUpThreads, 0, s>>>(U);
+      timer_end(p, rec, s);
+      ++p->launches;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s) {
+  if (p->desc.precision == IFGF_FP64) return run_ifgf<double>(p, s);
+  return run_ifgf<float>(p, s);
+}
+
+}  // namespace ifgf

@@ -1,0 +1,57 @@
+// Kernel declarations and launch-argument structs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "plan.h"
+
+namespace ifgf {
+
+// ---- setup (setup_kernels.cu)
+__global__ void k_cheb_tables(int n, double* fejer, double* A, double* Dm);
+__global__ void k_node_geom(int N, int nc, const double* fejer, NodeGeom g);
+__global__ void k_fine_coefs(int ng, const double* A, const double* fine, double* coef);
+__global__ void k_closest(int npairs, int nc, int ng, int iters, double delta, const int* pair_tgt,
+                          const int* pair_patch, const double* x, const double* coef,
+                          const double* unodes, double* uv, uint8_t* singular);
+__global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, const int* pair_patch,
+                          const double* uvc, int nc, int ng, int nbeta, double cov_d,
+                          const double* tb, const double* wb, const double* A, const double* x,
+                          const double* nrm, const double* coef, double ke, double ki, double* W);
+size_t moments_smem_per_warp(int nc, int ng, int nbeta);
+__global__ void k_near_values(int N, int nc, const int64_t* row_ptr, const int* col, const int* pair,
+                              const int* sp_of_pair, const double* W, const double* x,
+                              const double* nrm, const double* qw, const int* leafc, double ke,
+                              double ki, double* val64, float* val32);
+
+// ---- per-apply launchers (return cudaGetLastError of the launches)
+struct Materials {
+  double ke, ki, eps_e, eps_i, mu_e, mu_i, omega;
+};
+
+// a0: y [4][N] complex128 -> phi (orig, plan precision), a_sorted, a_orig (phi * omega)
+cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const double* phi_in,
+                                cudaStream_t s);
+// c-post: f28 + y -> out [4][N] complex128
+cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s);
+// (d): f28 = near * phi   (overwrites f28)
+cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s);
+// far field by the plain direct sum (accumulates into f28)
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s);
+// far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
+cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s);
+// zero f28
+cudaError_t launch_zero_f28(const ifgf_plan_t* p, cudaStream_t s);
+// f28 (plan precision) -> complex128 [N][28]
+cudaError_t launch_f28_export(const ifgf_plan_t* p, double* out, cudaStream_t s);
+
+// ---- optional event timing (api.cu)
+int timer_begin(ifgf_plan_t* p, int kind, cudaStream_t s);   // -1 when timing is off
+void timer_end(ifgf_plan_t* p, int rec, cudaStream_t s);
+cudaError_t timer_flush(ifgf_plan_t* p);
+
+// ---- GMRES helpers (gmres.cu)
+cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s);
+
+}  // namespace ifgf

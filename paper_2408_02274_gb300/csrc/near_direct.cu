@@ -1,0 +1,166 @@
+// (d) Near-field correction matvec and the plain direct far sum.
+//
+// Near: f28[l] = sum_m N_s[l][m] phi_m for the four precomputed complex
+// matrices N = (S_e, S_i, D_e, D_i) (singular weights of Sec. III-D with the
+// local corrections of Sec. III-H); S acts on all 8 densities, D on the 6
+// Cartesian ones.  One warp per target row; the weights stream once from HBM.
+//
+// Direct far: the sum of Eq. ifgf_sum_em written out, over all sources
+// outside the target's neighbour boxes (the pairs the IFGF approximates),
+// for G_e, G_i and their normal derivatives at the target.
+#include "kernels.h"
+
+namespace ifgf {
+
+namespace {
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, typename VT>
+__global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__ row_ptr,
+                                              const int* __restrict__ col, const VT* __restrict__ val,
+                                              const T* __restrict__ phi, T* __restrict__ f28) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  T acc[56];
+#pragma unroll
+  for (int k = 0; k < 56; ++k) acc[k] = T(0);
+  const int64_t e0 = row_ptr[row], e1 = row_ptr[row + 1];
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    const int m = __ldg(col + e);
+    T w[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = (T)__ldg(val + 8 * e + k);
+    T ph[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) ph[k] = __ldg(phi + 16 * (size_t)m + k);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const T wr = w[2 * s], wi = w[2 * s + 1];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        acc[2 * (8 * s + k)] += wr * ph[2 * k] - wi * ph[2 * k + 1];
+        acc[2 * (8 * s + k) + 1] += wr * ph[2 * k + 1] + wi * ph[2 * k];
+      }
+      const T dr = w[4 + 2 * s], di = w[4 + 2 * s + 1];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        acc[2 * (16 + 6 * s + k)] += dr * ph[2 * k] - di * ph[2 * k + 1];
+        acc[2 * (16 + 6 * s + k) + 1] += dr * ph[2 * k + 1] + di * ph[2 * k];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 56; ++k) acc[k] = warp_sum(acc[k]);
+  T* out = f28 + 56 * (size_t)row;
+#pragma unroll
+  for (int k = 0; k < 56; ++k)
+    if ((k & 31) == lane) out[k] = acc[k];
+}
+
+template <typename T>
+struct SrcTile {
+  T x[3];
+  int c[3];
+  T a[16];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restrict__ x,
+                                                    const double* __restrict__ nrm,
+                                                    const int* __restrict__ leafc,
+                                                    const T* __restrict__ a, T ke, T ki,
+                                                    T* __restrict__ f28) {
+  __shared__ SrcTile<T> tile[128];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = l < N;
+  T xl[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
+  int cl[3] = {0, 0, 0};
+  if (act)
+    for (int k = 0; k < 3; ++k) {
+      xl[k] = (T)x[3 * (size_t)l + k];
+      nl[k] = (T)nrm[3 * (size_t)l + k];
+      cl[k] = leafc[3 * l + k];
+    }
+  T acc[56];
+#pragma unroll
+  for (int k = 0; k < 56; ++k) acc[k] = T(0);
+  const T kk[2] = {ke, ki};
+  const T inv4pi = T(1.0 / (4.0 * kPi));
+  for (int base = 0; base < N; base += 128) {
+    __syncthreads();
+    int m = base + threadIdx.x;
+    if (m < N) {
+      for (int k = 0; k < 3; ++k) {
+        tile[threadIdx.x].x[k] = (T)x[3 * (size_t)m + k];
+        tile[threadIdx.x].c[k] = leafc[3 * m + k];
+      }
+      for (int k = 0; k < 16; ++k) tile[threadIdx.x].a[k] = a[16 * (size_t)m + k];
+    }
+    __syncthreads();
+    const int nt = min(128, N - base);
+    if (!act) continue;
+    for (int q = 0; q < nt; ++q) {
+      const SrcTile<T>& s = tile[q];
+      if (abs(s.c[0] - cl[0]) <= 1 && abs(s.c[1] - cl[1]) <= 1 && abs(s.c[2] - cl[2]) <= 1) continue;
+      T d0 = xl[0] - s.x[0], d1 = xl[1] - s.x[1], d2 = xl[2] - s.x[2];
+      T r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      T r = sqrt_t(r2);
+      T ir = T(1) / r;
+      T nd = (nl[0] * d0 + nl[1] * d1 + nl[2] * d2) * ir * ir;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        T sn, cs;
+        sincos_t(kk[ks] * r, &sn, &cs);
+        T g = inv4pi * ir;
+        T gr = g * cs, gi = g * sn;
+        T dr = nd * (-gr - kk[ks] * r * gi), di = nd * (-gi + kk[ks] * r * gr);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          acc[2 * (8 * ks + k)] += gr * s.a[2 * k] - gi * s.a[2 * k + 1];
+          acc[2 * (8 * ks + k) + 1] += gr * s.a[2 * k + 1] + gi * s.a[2 * k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          acc[2 * (16 + 6 * ks + k)] += dr * s.a[2 * k] - di * s.a[2 * k + 1];
+          acc[2 * (16 + 6 * ks + k) + 1] += dr * s.a[2 * k + 1] + di * s.a[2 * k];
+        }
+      }
+    }
+  }
+  if (act)
+    for (int k = 0; k < 56; ++k) f28[56 * (size_t)l + k] += acc[k];
+}
+
+}  // namespace
+
+cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s) {
+  const int threads = 256;
+  const unsigned blocks = (unsigned)(((size_t)p->N * 32 + threads - 1) / threads);
+  if (p->desc.precision == IFGF_FP64)
+    k_near<double, double><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
+        p->near.val64, (const double*)p->phi, (double*)p->f28);
+  else
+    k_near<float, float><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
+        p->near.val32, (const float*)p->phi, (float*)p->f28);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((p->N + 127) / 128);
+  if (p->desc.precision == IFGF_FP64)
+    k_far_direct<double><<<blocks, 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28);
+  else
+    k_far_direct<float><<<blocks, 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28);
+  return cudaGetLastError();
+}
+
+}  // namespace ifgf

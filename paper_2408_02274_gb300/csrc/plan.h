@@ -1,0 +1,152 @@
+// Internal plan layout of the CBIE-IFGF library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <array>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/ifgf.h"
+#include "common.cuh"
+
+namespace ifgf {
+
+// ------------------------------------------------------------------ host octree
+struct HostLevel {
+  int d = 0;
+  double H = 0, h = 0;
+  int ns = 0, na = 0;
+  std::vector<uint64_t> key;                  // Morton key per relevant box
+  std::vector<std::array<int, 3>> ic;         // integer box coordinates
+  std::vector<int> pt_begin, pt_end;          // sorted point range per box
+  std::vector<int> parent;                    // box index at level d-1
+  std::vector<std::array<int, 8>> child;      // box index at level d+1 (-1 absent)
+  std::unordered_map<uint64_t, int> index;    // key -> box
+  std::vector<std::vector<int>> nbr;          // neighbours (incl. self), Eq. box_neighbor
+  std::vector<std::vector<int>> cousin;       // cousins, Eq. box_cousin
+  std::vector<std::vector<int>> relcones;     // sorted relevant cone ids per box (Eq. rele_cone_d)
+  // slots (relevant cones, sorted by box then cone)
+  std::vector<int> slot_box, slot_cone, box_slot_ptr, cone_map;
+  // this level as a parent of level d+1: compact list of its relevant cone ids
+  std::vector<int> upcone_list;               // compact -> cone id
+  std::vector<int> slot_upidx;                // slot -> compact index
+  std::vector<int32_t> up_cc;                 // [ncompact][8][75] child cone at level d+1
+  // target evaluation lists at this level: per sorted target, its slots
+  std::vector<int64_t> tgt_ptr;
+  std::vector<int32_t> tgt_slot;
+  ConeGeom cg() const { return ConeGeom{h, ns, na}; }
+};
+
+struct HostTree {
+  int D = 0;
+  double corner[3] = {0, 0, 0};
+  double H1 = 0;
+  std::vector<int> perm;                      // sorted -> original
+  std::vector<int> iperm;                     // original -> sorted
+  std::vector<std::array<int, 3>> leafc;      // per original node: integer leaf coordinates
+  std::vector<std::vector<int>> box_of;       // [d][sorted point] -> box index at level d
+  std::vector<HostLevel> lv;                  // index d = 0..D (0 unused)
+};
+
+// ------------------------------------------------------------------ device level tables
+struct DevLevel {
+  int d = 0, nboxes = 0, nslots = 0;
+  ConeGeom cg{};
+  double H = 0;
+  double* box_center = nullptr;   // [nboxes][3]
+  int* cone_map = nullptr;        // [nboxes][ncones] -> slot or -1
+  int* slot_box = nullptr;        // [nslots]
+  int* slot_cone = nullptr;       // [nslots]
+  int* box_slot_ptr = nullptr;    // [nboxes+1]
+  int* box_pt_ptr = nullptr;      // [nboxes+1] sorted point ranges
+  int* child = nullptr;           // [nboxes][8] boxes at level d+1
+  int* slot_upidx = nullptr;      // [nslots] compact cone index (as parent)
+  int* up_cc = nullptr;           // [ncompact][8][75]
+  int64_t* tgt_ptr = nullptr;     // [N+1]
+  int* tgt_slot = nullptr;        // [ninter]
+  int64_t ninter = 0;
+  void* coefs = nullptr;          // [nslots][75][32] real (precision of the plan)
+};
+
+struct NodeGeom {           // per-node geometry, original order (FP64 SoA)
+  double* x = nullptr;      // [N][3]
+  double* xu = nullptr;     // [N][3]
+  double* xv = nullptr;     // [N][3]
+  double* n = nullptr;      // [N][3]
+  double* t1 = nullptr;     // [N][3]
+  double* t2 = nullptr;     // [N][3]
+  double* J = nullptr;      // [N]
+  double* w = nullptr;      // [N] quadrature weight J w_i w_j
+  double* g = nullptr;      // [N][3] inverse metric (g^uu, g^uv, g^vv)
+};
+
+struct NearMatrix {
+  int64_t nnz = 0;
+  int64_t* row_ptr = nullptr;   // [N+1]
+  int* col = nullptr;           // [nnz]
+  double* val64 = nullptr;      // [nnz][4][2] (S_e, S_i, D_e, D_i)
+  float* val32 = nullptr;       // [nnz][4][2]
+};
+
+struct GmresWork {
+  int max_iter = 0;
+  double* V = nullptr;          // [(max_iter+1)][4N][2]
+  double* H = nullptr;          // [(max_iter+1)][max_iter][2]
+  double* cs = nullptr;         // [max_iter][2]
+  double* sn = nullptr;         // [max_iter][2]
+  double* g = nullptr;          // [max_iter+1][2]
+  double* h = nullptr;          // [max_iter+1][2] projection scratch
+  double* part = nullptr;       // [nblk][max_iter+1][2] partial dot products
+  double* scal = nullptr;       // small scalars
+  double* w = nullptr;          // [4N][2]
+  double* b = nullptr;          // [4N][2]
+  double* y = nullptr;          // [4N][2]
+  double* inc = nullptr;        // [6N][2]
+  double* hres = nullptr;       // pinned host scalar
+};
+
+// Per-kernel-kind CUDA-event timing of the per-apply work (optional).
+enum TimedKind { TK_PREP = 0, TK_NEAR, TK_LEAF, TK_UP, TK_TARGET, TK_COMBINE, TK_FAR_DIRECT, TK_GMRES, TK_COUNT };
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;   // 2 events per record
+  std::vector<int> kind;           // kind of each pending record
+  int npending = 0;
+  double total_ms[TK_COUNT] = {};
+  int64_t calls[TK_COUNT] = {};
+};
+
+}  // namespace ifgf
+
+struct ifgf_tree_t : ifgf::HostTree {};
+
+struct ifgf_plan_t {
+  ifgf_plan_desc desc{};
+  int N = 0, P = 0, nc = 0, ng = 0;
+  double omega = 0;
+  bool poisoned = false;
+  ifgf::KernelTimer timer;
+  int64_t launches = 0;         // kernels launched by apply/solve since the last reset
+  int device = 0;
+  int num_sms = 0;
+  ifgf_tree_t tree;
+  // device data
+  ifgf::NodeGeom geo;
+  double* tab_D = nullptr;      // [nc][nc] Chebyshev differentiation matrix
+  double* x_sorted = nullptr;   // [N][3] nodes in sorted order
+  double* n_sorted = nullptr;   // [N][3]
+  int* perm = nullptr;          // [N] sorted -> original
+  int* leafc = nullptr;         // [N][3] integer leaf coordinates (original order)
+  std::vector<ifgf::DevLevel> dl;  // index d
+  ifgf::NearMatrix near;
+  void* phi = nullptr;          // [N][8][2] densities (plan precision), original order
+  void* a_sorted = nullptr;     // [N][8][2] phi * omega, sorted order
+  void* a_orig = nullptr;       // [N][8][2] phi * omega, original order (direct far)
+  void* f28 = nullptr;          // [N][28][2] scalar fields (plan precision)
+  double* phi64 = nullptr;      // [N][8][2] FP64 densities (prep output)
+  ifgf::GmresWork gm;
+  ifgf_stats stats{};
+  std::vector<void*> allocations;
+};

@@ -1,0 +1,138 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol,
+rejects bad descriptors without touching a GPU, and its host-only octree /
+cone-segment setup (Sec. III-F) satisfies the invariants the IFGF relies on."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2408_02274_gb300 as lib
+from inputs import CONFIG_SPHERE_SMALL, sphere_problem
+from paper_2408_02274_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    libbuild.build()
+    lib.load()
+
+
+def test_every_declared_symbol_is_exported():
+    header = open(os.path.join(ROOT, "include", "ifgf.h")).read()
+    declared = set(re.findall(r"^(?:ifgf_status|const char\*)\s+(\w+)\s*\(", header, flags=re.M))
+    assert {"ifgf_plan_create", "ifgf_apply", "bie_solve", "ifgf_plan_destroy"} <= declared
+    L = lib.load()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(lib.EXPORTS) == declared
+
+
+def test_status_strings():
+    L = lib.load()
+    for s in range(8):
+        assert len(L.ifgf_status_string(s)) > 0
+
+
+def test_invalid_descriptors_rejected_before_any_gpu_work():
+    prob = CONFIG_SPHERE_SMALL(4, ng=8)
+    x, xu, xv = prob.nodes()
+    base = dict(nodes=x, dxdu=xu, dxdv=xv, fine=prob.fine(), num_patches=prob.num_patches, nc=prob.nc,
+                k_ext=prob.k_ext, k_int=prob.k_int, eps_ext=1.0, eps_int=2.25, delta=0.3)
+    for bad, status in [({"delta": 0.0}, lib.IFGF_EINVAL), ({"k_ext": -1.0}, lib.IFGF_EINVAL),
+                        ({"n_beta": 2}, lib.IFGF_EINVAL), ({"cov_d": 1.0}, lib.IFGF_EINVAL),
+                        ({"precision": 7}, lib.IFGF_EINVAL), ({"ps": 4}, lib.IFGF_EUNSUPPORTED),
+                        ({"nc": 1}, lib.IFGF_EINVAL), ({"max_krylov": 5000}, lib.IFGF_EINVAL)]:
+        kw = dict(base)
+        kw.update(bad)
+        with pytest.raises(lib.IfgfError) as e:
+            lib.ifgf_plan_create(**kw)
+        assert e.value.status == status
+
+
+def _coverage(tree, x, k_max):
+    """Count, for every (target, source) pair, the levels at which the source's
+    box is evaluated at the target (step 3 of the algorithm summary)."""
+    n = x.shape[0]
+    perm, leafc = tree.perm()
+    D = tree.levels
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[perm] = np.arange(n)
+    cover = np.zeros((n, n), dtype=np.int32)
+    max_s = 0.0
+    for d in range(3, D + 1):
+        coords, ptr, cones, ns, na = tree.level(d)
+        tp, ts, sb = tree.targets(d)
+        key = {tuple(c): b for b, c in enumerate(coords)}
+        src_box = np.array([key[tuple(c >> (D - d))] for c in leafc])           # original order
+        E = np.zeros((n, coords.shape[0]), dtype=np.int32)                      # original target order
+        H = tree.h1 / 2 ** (d - 1)
+        for s in range(n):
+            l = perm[s]
+            boxes = sb[ts[tp[s]:tp[s + 1]]]
+            assert len(set(boxes.tolist())) == boxes.size                      # one cone per source box
+            E[l, boxes] += 1
+            cen = tree.corner + H * (coords[boxes] + 0.5)
+            r = np.linalg.norm(x[l] - cen, axis=1)
+            if r.size:
+                max_s = max(max_s, (np.sqrt(3) / 2 * H / r).max())
+        cover += E[:, src_box]
+    near = np.all(np.abs(leafc[:, None, :] - leafc[None, :, :]) <= 1, axis=-1)
+    return cover, near, max_s
+
+
+@pytest.mark.parametrize("split,leaf", [(1, 0.25), (2, 0.11), (2, 0.06)])
+def test_ifgf_exactly_once_coverage(split, leaf):
+    prob = sphere_problem(0.5, split, 6, 2.25)
+    x, _, _ = prob.nodes()
+    tree = lib.Tree(x, leaf_size=leaf, k_max=prob.k_int)
+    cover, near, max_s = _coverage(tree, x, prob.k_int)
+    assert tree.levels >= 3
+    assert np.all(cover[near] == 0)
+    assert np.all(cover[~near] == 1)
+    # every evaluated target is at least one box away: s = h/r <= sqrt(3)/3 (Sec. III-E)
+    assert max_s <= np.sqrt(3) / 3 + 1e-12
+
+
+def test_cone_counts_follow_the_doubling_rule():
+    prob = sphere_problem(2.0, 2, 6, 4.0)
+    x, _, _ = prob.nodes()
+    k = prob.k_int
+    tree = lib.Tree(x, leaf_size=0.25, k_max=k, ns0=1, na0=2)
+    D = tree.levels
+    ns_prev, na_prev = 1, 2
+    for d in range(D, 2, -1):
+        _, _, _, ns, na = tree.level(d)
+        H = tree.h1 / 2 ** (d - 1)
+        a = 2 if k * H > 0.5 else 1
+        assert (ns, na) == (a * ns_prev, a * na_prev)
+        ns_prev, na_prev = ns, na
+
+
+def test_relevant_cones_contain_their_targets():
+    # every (target, slot) pair of step 3 refers to the cone segment that holds the target
+    prob = sphere_problem(0.5, 2, 6, 2.25)
+    x, _, _ = prob.nodes()
+    tree = lib.Tree(x, leaf_size=0.11, k_max=prob.k_int)
+    perm, _ = tree.perm()
+    D = tree.levels
+    for d in range(3, D + 1):
+        coords, ptr, cones, ns, na = tree.level(d)
+        tp, ts, sb = tree.targets(d)
+        H = tree.h1 / 2 ** (d - 1)
+        h = np.sqrt(3) / 2 * H
+        for s in range(0, x.shape[0], 7):
+            for slot in ts[tp[s]:tp[s + 1]]:
+                b, cone = sb[slot], cones[slot]
+                rel = x[perm[s]] - (tree.corner + H * (coords[b] + 0.5))
+                r = np.linalg.norm(rel)
+                sv, th = h / r, np.arctan2(np.hypot(rel[0], rel[1]), rel[2])
+                ph = np.arctan2(rel[1], rel[0]) % (2 * np.pi)
+                g3 = cone % (2 * na)
+                g2 = (cone // (2 * na)) % na
+                g1 = cone // (2 * na * na)
+                assert min(int(sv / (np.sqrt(3) / 3 / ns)), ns - 1) == g1
+                assert min(int(th / (np.pi / na)), na - 1) == g2
+                assert min(int(ph / (np.pi / na)), 2 * na - 1) == g3
