@@ -296,6 +296,25 @@ def cpu_baseline(prob, delta, budget_s=15.0, reference_units=False):
                       f"to {t_full:.1f} s"}
 
 
+def run_apply(args):
+    """Forward maps only (no GMRES, no timing output): a short command for profilers."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import random_densities
+    libbuild.build()
+    prob = problem()
+    plan = lib.Plan.from_problem(prob, delta=delta_of(prob), n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=10)
+    y = torch.from_numpy(random_densities(prob.n, 1)).cuda()
+    out = torch.empty_like(y)
+    for _ in range(args.warmup + args.steps):
+        plan.apply(y, out)
+    torch.cuda.synchronize()
+    plan.close()
+    return {"mode": "apply", "applies": args.warmup + args.steps}
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -325,8 +344,14 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply"])
     args = ap.parse_args()
-    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.impl == "reference":
+        res = run_reference(args)
+    elif args.mode == "apply":
+        res = run_apply(args)
+    else:
+        res = run_gpu(args)
     if res is not None:
         print(json.dumps(res))
 

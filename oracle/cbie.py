@@ -19,8 +19,8 @@ What it computes is the unaccelerated discrete operator of Paul & Sideris
 * the right-hand side omega^{-1}(n x E^inc, n x H^inc) and GMRES on A y = b
   (Eq. lin_system).
 
-Readings of points the paper leaves open are listed in the design doc and noted
-at each function (R1..R16 there).
+Where the paper leaves a point open, the reading taken is noted at the
+function that uses it (readings R1..R16).
 """
 from __future__ import annotations
 

@@ -119,19 +119,60 @@ __device__ inline double dist2_at(const PatchCoef& pc, const double* x, double u
 // ---------------------------------------------------------------- closest point (Eq. dist_min)
 __device__ const double kGold = 0.6180339887498948482;
 
+// Geometry contracted along u at a fixed u: cu[n][c] = sum_m coef[m][n][c] T_m(u), c < 3.
+__device__ inline void contract_u(const PatchCoef& pc, double u, double* cu) {
+  for (int t = 0; t < pc.ng * 3; ++t) cu[t] = 0;
+  double T0 = 1, T1 = u;
+  for (int m = 0; m < pc.ng; ++m) {
+    double Tm = (m == 0) ? 1.0 : (m == 1 ? u : 0);
+    if (m >= 2) {
+      Tm = 2 * u * T1 - T0;
+      T0 = T1;
+      T1 = Tm;
+    }
+    for (int n = 0; n < pc.ng; ++n) {
+      const double* cf = pc.c + ((size_t)m * pc.ng + n) * 9;
+      cu[3 * n] += cf[0] * Tm;
+      cu[3 * n + 1] += cf[1] * Tm;
+      cu[3 * n + 2] += cf[2] * Tm;
+    }
+  }
+}
+
+__device__ inline double dist2_v(const double* cu, int ng, const double* x, double v) {
+  double y0 = 0, y1 = 0, y2 = 0, T0 = 1, T1 = v;
+  for (int n = 0; n < ng; ++n) {
+    double Tn = (n == 0) ? 1.0 : (n == 1 ? v : 0);
+    if (n >= 2) {
+      Tn = 2 * v * T1 - T0;
+      T0 = T1;
+      T1 = Tn;
+    }
+    y0 += cu[3 * n] * Tn;
+    y1 += cu[3 * n + 1] * Tn;
+    y2 += cu[3 * n + 2] * Tn;
+  }
+  double a = x[0] - y0, b = x[1] - y1, c = x[2] - y2;
+  return a * a + b * b + c * c;
+}
+
+// min over v in [a, b] of |x - eta(u, v)|^2 by golden section (fixed iteration count);
+// the interpolant is contracted along u once and then evaluated in v only.
 __device__ double golden_inner(const PatchCoef& pc, const double* x, double u, double a, double b,
                                int iters, double* vbest) {
+  double cu[3 * 48];
+  contract_u(pc, u, cu);
   double c = b - kGold * (b - a), d = a + kGold * (b - a);
-  double fc = dist2_at(pc, x, u, c), fd = dist2_at(pc, x, u, d);
+  double fc = dist2_v(cu, pc.ng, x, c), fd = dist2_v(cu, pc.ng, x, d);
   for (int it = 0; it < iters; ++it) {
     if (fc < fd) {
-      b = d; d = c; fd = fc; c = b - kGold * (b - a); fc = dist2_at(pc, x, u, c);
+      b = d; d = c; fd = fc; c = b - kGold * (b - a); fc = dist2_v(cu, pc.ng, x, c);
     } else {
-      a = c; c = d; fc = fd; d = a + kGold * (b - a); fd = dist2_at(pc, x, u, d);
+      a = c; c = d; fc = fd; d = a + kGold * (b - a); fd = dist2_v(cu, pc.ng, x, d);
     }
   }
   *vbest = 0.5 * (a + b);
-  return dist2_at(pc, x, u, *vbest);
+  return dist2_v(cu, pc.ng, x, *vbest);
 }
 
 __device__ inline double snap_edge(double t) {
