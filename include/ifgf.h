@@ -168,6 +168,39 @@ ifgf_status ifgf_plan_stats(ifgf_plan plan, ifgf_stats* st);
 ifgf_status ifgf_set_timing(ifgf_plan plan, int32_t enable);
 ifgf_status ifgf_get_timing(ifgf_plan plan, double* ms, int64_t* calls, int64_t* launches);
 
+/*
+ * Allocation-free direct far-field sums (this library's own addition; the
+ * paper has no counterpart).  For callers that cannot create device
+ * allocations where they need the sums -- a solver embedded in an
+ * application that owns all device memory through its own pool, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation -- and therefore cannot create a plan.
+ *
+ * Computes the same scalar far sums as ifgf_apply_fields(plan, phi, f28,
+ * IFGF_PART_FAR, ...) of a plan with far_mode = IFGF_FAR_DIRECT: for every
+ * node l, the sums over all nodes m whose integer leaf box differs from that
+ * of l by more than 1 in some coordinate (outside the neighbour boxes) of
+ * G_e, G_i (fields k = 0..7) and dG_e/dn, dG_i/dn at l (k = 0..5) times
+ * a_m = phi_m * weights_m.  All pointers are DEVICE pointers:
+ *   nodes, normals [n][3] double; weights [n] double (quadrature weights);
+ *   leaf_coords [n][3] int32 (e.g. from ifgf_tree_perm); phi [n][8]
+ *   complex128; f28 [n][28] complex128 output (same layout as
+ *   ifgf_apply_fields).  precision: IFGF_FP64 or IFGF_FP32 arithmetic.
+ * The working arrays live in one fixed device array compiled into the
+ * library (~55 MiB, held by every device that loads the library until the
+ * process exits); n is limited to 100000 nodes: larger n returns
+ * IFGF_EUNSUPPORTED and the message of ifgf_status_string(IFGF_ECUDA) says
+ * so.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * The first call on a device looks up the array's device address (this call
+ * should come before any stream capture).  Every call shares the array and
+ * clears what must start at zero; calls that overlap on the GPU race.
+ * Asynchronous on `stream`.
+ */
+ifgf_status ifgf_far_direct_noalloc(int32_t n, const double* nodes, const double* normals,
+                                    const double* weights, const int32_t* leaf_coords, const void* phi,
+                                    double k_ext, double k_int, int32_t precision, void* f28,
+                                    ifgf_stream stream);
+
 /* Human-readable message for a status code (static storage). */
 const char* ifgf_status_string(ifgf_status s);
 

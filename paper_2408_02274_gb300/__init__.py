@@ -24,7 +24,7 @@ IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_fields", "bie_solve",
            "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
-           "ifgf_tree_level", "ifgf_tree_targets"]
+           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_far_direct_noalloc"]
 
 
 class ifgf_plan_desc(ctypes.Structure):
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.ifgf_tree_perm.argtypes = [vp, vp, vp]
     lib.ifgf_tree_level.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4 + [vp, vp, vp]
     lib.ifgf_tree_targets.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, vp]
+    lib.ifgf_far_direct_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     for name in EXPORTS:
         if name != "ifgf_status_string":
             getattr(lib, name).restype = ctypes.c_int32
@@ -200,6 +201,24 @@ def ifgf_get_timing(plan):
     nl = ctypes.c_int64(0)
     _check(load().ifgf_get_timing(plan, ms, calls, ctypes.byref(nl)), "ifgf_get_timing")
     return {k: (ms[i], calls[i]) for i, k in enumerate(TIMED_KINDS)}, nl.value
+
+
+def ifgf_far_direct_noalloc(nodes, normals, weights, leaf_coords, phi, k_ext: float, k_int: float, f28,
+                            precision: int = IFGF_FP64, stream=None):
+    """Direct far-field sums without any device allocation (CUDA tensors in, f28 out).
+
+    For callers that cannot allocate device memory where they need the sums
+    (an application that owns all device memory, a latency-critical loop): the
+    library keeps its working arrays in one fixed device array instead.
+    nodes, normals [n, 3] float64; weights [n] float64; leaf_coords [n, 3]
+    int32; phi [n, 8] and f28 [n, 28] complex128; n <= 100000.
+    """
+    n = int(nodes.shape[0])
+    _check(load().ifgf_far_direct_noalloc(n, ctypes.c_void_p(nodes.data_ptr()), ctypes.c_void_p(normals.data_ptr()),
+                                          ctypes.c_void_p(weights.data_ptr()), ctypes.c_void_p(leaf_coords.data_ptr()),
+                                          ctypes.c_void_p(phi.data_ptr()), float(k_ext), float(k_int), int(precision),
+                                          ctypes.c_void_p(f28.data_ptr()), _stream(stream)),
+           "ifgf_far_direct_noalloc")
 
 
 class Tree:

@@ -39,6 +39,8 @@ cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, c
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s);
 // far field by the plain direct sum (accumulates into f28)
 cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s);
+cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
+                                  double ke, double ki, int precision, void* f28, cudaStream_t s);
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
 cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s);
 // zero f28

@@ -163,4 +163,18 @@ cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The same direct far-sum kernel on caller-provided arrays (used by the
+// allocation-free entry point): a [N][8] weighted densities and f28 [N][28]
+// accumulators in the given precision; f28 must be zeroed by the caller.
+cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
+                                  double ke, double ki, int precision, void* f28, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((N + 127) / 128);
+  if (precision == IFGF_FP64)
+    k_far_direct<double><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const double*)a, ke, ki, (double*)f28);
+  else
+    k_far_direct<float><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const float*)a, (float)ke, (float)ki,
+                                                (float*)f28);
+  return cudaGetLastError();
+}
+
 }  // namespace ifgf
