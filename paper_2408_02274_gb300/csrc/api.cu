@@ -232,6 +232,9 @@ void build(ifgf_plan_t* p) {
     Dl.child = A.upload(ch);
     Dl.slot_upidx = A.upload(L.slot_upidx);
     Dl.up_cc = A.upload(L.up_cc);
+    Dl.up_order = A.upload(L.up_order);
+    Dl.up_task = A.upload(L.up_task);
+    Dl.up_ntask = A.upload(L.up_ntask);
     Dl.tgt_ptr = A.upload(L.tgt_ptr);
     Dl.tgt_slot = A.upload(L.tgt_slot);
     Dl.ninter = (int64_t)L.tgt_slot.size();

@@ -228,6 +228,25 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           }
         }
       }
+      // per (parent cone, octant): the points ranked by the child cone they fall in, and
+      // runs of at most 4 consecutive ranked points that share one child cone
+      Pp.up_order.assign((size_t)ncomp * 8 * kQ, 0);
+      Pp.up_task.assign((size_t)ncomp * 8 * kQ, 0);
+      Pp.up_ntask.assign((size_t)ncomp * 8, 0);
+      for (size_t g = 0; g < (size_t)ncomp * 8; ++g) {
+        const int32_t* cc = &Pp.up_cc[g * kQ];
+        int32_t* ord = &Pp.up_order[g * kQ];
+        for (int q = 0; q < kQ; ++q) ord[q] = q;
+        std::stable_sort(ord, ord + kQ, [&](int a, int b) { return cc[a] < cc[b]; });
+        int n = 0, r = 0;
+        while (r < kQ) {
+          int len = 1;
+          while (len < 4 && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
+          Pp.up_task[g * kQ + n++] = r | (len << 8);
+          r += len;
+        }
+        Pp.up_ntask[g] = n;
+      }
       for (int b = 0; b < nb; ++b) {
         int p = L.parent[b];
         int o = (L.ic[b][0] & 1) | ((L.ic[b][1] & 1) << 1) | ((L.ic[b][2] & 1) << 2);

@@ -12,11 +12,25 @@
 //                 plus the normal derivative of the same product (Sec. III-I).
 // Coefficients are stored per cone segment as [75][32] reals: Chebyshev index
 // (i_s*5 + i_theta)*5 + i_phi, then 16 complex fields (kernel*8 + density).
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace ifgf {
 
 namespace {
+
+// Inner-loop helpers of the leaf step: in FP32 the hardware approximations
+// (__fdividef, __sincosf; the phase argument there is bounded by k h_leaf,
+// a few radians, where __sincosf is accurate to ~4e-7); in FP64 the exact ones.
+template <typename T>
+__device__ inline T leaf_div(T a, T b) { return a / b; }
+template <>
+__device__ inline float leaf_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ inline void leaf_sincos(T x, T* s, T* c) { sincos_t(x, s, c); }
+template <>
+__device__ inline void leaf_sincos<float>(float x, float* s, float* c) { __sincosf(x, s, c); }
 
 // 1D values -> coefficients maps for 3 and 5 open Chebyshev nodes, and the nodes.
 template <typename T>
@@ -185,12 +199,12 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
           // g_S(X, y) = (r/|X-y|) exp(i k (|X-y| - r)), |X-y| - r = (|y|^2 - 2 X.y)/(|X-y| + r)
           T dxy = src[e][3] - T(2) * (X[0] * src[e][0] + X[1] * src[e][1] + X[2] * src[e][2]);
           T d = sqrt_t(r * r + dxy);
-          T rd = r / d;
-          T dd = dxy / (d + r);
+          T rd = leaf_div(r, d);
+          T dd = leaf_div(dxy, d + r);
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             T sn, cs;
-            sincos_t(kk[ks] * dd, &sn, &cs);
+            leaf_sincos(kk[ks] * dd, &sn, &cs);
             T gr = rd * cs, gi = rd * sn;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
@@ -316,6 +330,132 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
   }
 }
 
+// (b), grouped variant.  The parent points are processed in runs of up to 4
+// points that fall in the same child cone (box-independent tables built with
+// the octree), one warp per run and one lane per real column: each
+// coefficient the warp loads serves every point of the run, and the 3D
+// Chebyshev sum is contracted separably (over phi, then theta, then s).  All
+// children are processed in one pass; runs of different children add into
+// the parent values with shared-memory atomics (one column per lane, so no
+// bank conflicts within a warp).
+struct RunTabs {
+  const int* order;   // [ncompact][8][75]
+  const int* task;    // [ncompact][8][75]
+  const int* ntask;   // [ncompact][8]
+};
+
+template <typename T>
+struct PtInfo2 {
+  int cslot;
+  T ts, tt, tp;
+  T fr[2], fi[2];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kUpThreads) k_up_grouped(UpArgs<T> A, RunTabs RT) {
+  static_assert(sizeof(T) == 4, "the grouped upward kernel is built for FP32");
+  __shared__ SmallMaps<T> M;
+  __shared__ T Xp[kQ][3];
+  __shared__ PtInfo2<T> info[8][kQ];
+  __shared__ T vals[kQ * kVS];
+  __shared__ int tstart[9];
+  const int pslot = blockIdx.x;
+  const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  init_maps(M);
+  const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
+  if (t == 0) {
+    int acc = 0;
+    for (int o = 0; o < 8; ++o) {
+      tstart[o] = acc;
+      if (A.child[8 * P + o] >= 0) acc += RT.ntask[(size_t)ci * 8 + o];
+    }
+    tstart[8] = acc;
+  }
+  __syncthreads();
+  if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
+  for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
+  __syncthreads();
+  const T off = (T)(0.5 * A.Hc);
+  const T kk[2] = {A.ke, A.ki};
+  for (int e = t; e < 8 * kQ; e += blockDim.x) {
+    const int o = e / kQ, q = e % kQ;
+    const int cb = A.child[8 * P + o];
+    if (cb < 0) continue;
+    const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
+    const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
+    const int cc = A.up_cc[((size_t)ci * 8 + o) * kQ + q];
+    PtInfo2<T>& I = info[o][q];
+    I.cslot = A.cone_map_c[(size_t)cb * A.ncones_c + cc];
+    T rc, sth, cth, sph, cph;
+    local_coords(A.cgc, cc, x, y, z, &I.ts, &I.tt, &I.tp, &rc, &sth, &cth, &sph, &cph);
+    // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
+    const T rp = sqrt_t(Xp[q][0] * Xp[q][0] + Xp[q][1] * Xp[q][1] + Xp[q][2] * Xp[q][2]);
+    const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
+    for (int ks = 0; ks < 2; ++ks) {
+      T sn, cs;
+      sincos_t(kk[ks] * dr, &sn, &cs);
+      I.fr[ks] = rp / rc * cs;
+      I.fi[ks] = rp / rc * sn;
+    }
+  }
+  __syncthreads();
+  const int ntot = tstart[8];
+  const int ks = lane >> 4;   // columns 0..15 belong to kernel e, 16..31 to kernel i
+  for (int w = warp; w < ntot; w += kUpThreads / 32) {
+    int o = 0;
+    while (w >= tstart[o + 1]) ++o;
+    const size_t g = (size_t)ci * 8 + o;
+    const int tk = __ldg(RT.task + g * kQ + (w - tstart[o]));
+    const int r0 = tk & 255, len = tk >> 8;
+    int q[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q[a] = __ldg(RT.order + g * kQ + r0 + (a < len ? a : 0));
+    const int cslot = info[o][q[0]].cslot;
+    if (cslot < 0) continue;   // cannot happen: the host marked every such cone relevant
+    T Ts[4][3], Tt[4][5], Tp[4][5];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      cheb_vals<T, 3>(info[o][q[a]].ts, Ts[a]);
+      cheb_vals<T, 5>(info[o][q[a]].tt, Tt[a]);
+      cheb_vals<T, 5>(info[o][q[a]].tp, Tp[a]);
+    }
+    const T* C = A.coefs_c + (size_t)cslot * kQ * 32 + lane;
+    T E[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) E[a][0] = E[a][1] = E[a][2] = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        T c[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) c[k] = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T d = Tp[a][0] * c[0];
+#pragma unroll
+          for (int k = 1; k < 5; ++k) d += Tp[a][k] * c[k];
+          E[a][i] += Tt[a][j] * d;
+        }
+      }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const T v = Ts[a][0] * E[a][0] + Ts[a][1] * E[a][1] + Ts[a][2] * E[a][2];
+      const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
+      if (a >= len) continue;
+      const T re = (lane & 1) ? wv : v, im = (lane & 1) ? v : wv;
+      const T fr = info[o][q[a]].fr[ks], fi = info[o][q[a]].fi[ks];
+      atomicAdd(vals + q[a] * kVS + lane, (lane & 1) ? (re * fi + im * fr) : (re * fr - im * fi));
+    }
+  }
+  __syncthreads();
+  if (t < 32) {
+    vals_to_coefs_col(M, vals + t, kVS);
+    T* out = A.coefs_p + (size_t)pslot * kQ * 32 + t;
+    for (int qq = 0; qq < kQ; ++qq) out[qq * 32] = vals[qq * kVS + t];
+  }
+}
+
 // ------------------------------------------------------------------ (c) target evaluation
 template <typename T>
 struct TgtArgs {
@@ -334,9 +474,25 @@ struct TgtArgs {
   T ke, ki;
 };
 
+// Per (target, cone) scalars, computed one cone per lane and read back by the
+// whole warp: Chebyshev values and derivatives in (s, theta, phi), the
+// directional-derivative weights and the centred factors of both kernels.
 template <typename T>
-__global__ void __launch_bounds__(256) k_target(TgtArgs<T> A) {
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+struct TgtScal {
+  T Ts[3], dTs[3], Tt[5], dTt[5], Tp[5], dTp[5];
+  T as, at, ap;
+  T G[2][4];   // per kernel: Re G, Im G, Re dG/dn, Im dG/dn
+  int slot;
+};
+
+template <typename T>
+__host__ __device__ constexpr int tgt_warps() { return sizeof(T) == 4 ? 8 : 4; }   // keeps the scalars under 48 KB
+
+template <typename T>
+__global__ void __launch_bounds__(32 * tgt_warps<T>()) k_target(TgtArgs<T> A) {
+  __shared__ TgtScal<T> sc[tgt_warps<T>()][32];
+  const int warp = threadIdx.x >> 5;
+  const int t = blockIdx.x * tgt_warps<T>() + warp;
   const int lane = threadIdx.x & 31;
   if (t >= A.N) return;
   const int64_t e0 = A.tgt_ptr[t], e1 = A.tgt_ptr[t + 1];
@@ -344,65 +500,82 @@ __global__ void __launch_bounds__(256) k_target(TgtArgs<T> A) {
   const double x0 = A.x_sorted[3 * (size_t)t], x1 = A.x_sorted[3 * (size_t)t + 1], x2 = A.x_sorted[3 * (size_t)t + 2];
   const T n0 = (T)A.n_sorted[3 * (size_t)t], n1 = (T)A.n_sorted[3 * (size_t)t + 1], n2 = (T)A.n_sorted[3 * (size_t)t + 2];
   const int ks = lane >> 4;
-  const T kap = ks ? A.ki : A.ke;
   const T ds = (T)A.cg.ds(), dth = (T)A.cg.dth(), h = (T)A.cg.h;
+  TgtScal<T>* S = sc[warp];
   T accS = 0, accD = 0;
-  for (int64_t e = e0; e < e1; ++e) {
-    const int slot = A.tgt_slot[e];
-    const int box = A.slot_box[slot], cone = A.slot_cone[slot];
-    const T xr = (T)(x0 - A.box_center[3 * box]);
-    const T yr = (T)(x1 - A.box_center[3 * box + 1]);
-    const T zr = (T)(x2 - A.box_center[3 * box + 2]);
-    T ts, tt, tp, r, sth, cth, sph, cph;
-    local_coords(A.cg, cone, xr, yr, zr, &ts, &tt, &tp, &r, &sth, &cth, &sph, &cph);
-    T Ts[3], Tt[5], Tp[5], dTs[3], dTt[5], dTp[5];
-    cheb_vals<T, 3>(ts, Ts);
-    cheb_vals<T, 5>(tt, Tt);
-    cheb_vals<T, 5>(tp, Tp);
-    cheb_dvals<T, 3>(ts, dTs);
-    cheb_dvals<T, 5>(tt, dTt);
-    cheb_dvals<T, 5>(tp, dTp);
-    // n . grad of (s, theta, phi): grad s = -(h/r^2) r_hat, grad theta = theta_hat / r,
-    // grad phi = phi_hat / (r sin theta)   (analytic derivative of the interpolant, reading R1)
-    const T ir = T(1) / r;
-    const T nr = (n0 * xr + n1 * yr + n2 * zr) * ir;
-    const T nth = n0 * cth * cph + n1 * cth * sph - n2 * sth;
-    const T nph = -n0 * sph + n1 * cph;
-    const T as = -(h * ir * ir) * nr * (T(2) / ds);
-    const T at = nth * ir * (T(2) / dth);
-    const T sthg = sth > T(1e-7) ? sth : T(1e-7);
-    const T ap = nph * ir / sthg * (T(2) / dth);
-    const T* C = A.coefs + (size_t)slot * kQ * 32 + lane;
-    T F = 0, dF = 0;
+  for (int64_t c0 = e0; c0 < e1; c0 += 32) {
+    const int nc = (int)min((int64_t)32, e1 - c0);
+    if (lane < nc) {
+      TgtScal<T>& Q = S[lane];
+      const int slot = A.tgt_slot[c0 + lane];
+      const int box = A.slot_box[slot], cone = A.slot_cone[slot];
+      const T xr = (T)(x0 - A.box_center[3 * box]);
+      const T yr = (T)(x1 - A.box_center[3 * box + 1]);
+      const T zr = (T)(x2 - A.box_center[3 * box + 2]);
+      T ts, tt, tp, r, sth, cth, sph, cph;
+      local_coords(A.cg, cone, xr, yr, zr, &ts, &tt, &tp, &r, &sth, &cth, &sph, &cph);
+      cheb_vals<T, 3>(ts, Q.Ts);
+      cheb_vals<T, 5>(tt, Q.Tt);
+      cheb_vals<T, 5>(tp, Q.Tp);
+      cheb_dvals<T, 3>(ts, Q.dTs);
+      cheb_dvals<T, 5>(tt, Q.dTt);
+      cheb_dvals<T, 5>(tp, Q.dTp);
+      // n . grad of (s, theta, phi): grad s = -(h/r^2) r_hat, grad theta = theta_hat / r,
+      // grad phi = phi_hat / (r sin theta)   (analytic derivative of the interpolant, reading R1)
+      const T ir = T(1) / r;
+      const T nr = (n0 * xr + n1 * yr + n2 * zr) * ir;
+      const T nth = n0 * cth * cph + n1 * cth * sph - n2 * sth;
+      const T nph = -n0 * sph + n1 * cph;
+      Q.as = -(h * ir * ir) * nr * (T(2) / ds);
+      Q.at = nth * ir * (T(2) / dth);
+      const T sthg = sth > T(1e-7) ? sth : T(1e-7);
+      Q.ap = nph * ir / sthg * (T(2) / dth);
+      // centred factor G = e^{i k r}/(4 pi r) and its normal derivative (n.r_hat)(i k - 1/r) G
+      const T g = T(1.0 / (4.0 * kPi)) * ir;
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        const T b = Ts[i] * Tt[j];
-        const T p1 = as * dTs[i] * Tt[j] + at * Ts[i] * dTt[j];
-        const T p2 = ap * b;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-          const T c = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
-          F += b * Tp[k] * c;
-          dF += (p1 * Tp[k] + p2 * dTp[k]) * c;
-        }
+      for (int kk = 0; kk < 2; ++kk) {
+        const T kap = kk ? A.ki : A.ke;
+        T sn, cs;
+        sincos_t(kap * r, &sn, &cs);
+        const T Gr = g * cs, Gi = g * sn;
+        Q.G[kk][0] = Gr;
+        Q.G[kk][1] = Gi;
+        Q.G[kk][2] = nr * (-ir * Gr - kap * Gi);
+        Q.G[kk][3] = nr * (-ir * Gi + kap * Gr);
       }
-    // centred factor G = e^{i k r}/(4 pi r) and its normal derivative (n.r_hat)(i k - 1/r) G
-    T sn, cs;
-    sincos_t(kap * r, &sn, &cs);
-    const T g = T(1.0 / (4.0 * kPi)) * ir;
-    const T Gr = g * cs, Gi = g * sn;
-    const T dGr = nr * (-ir * Gr - kap * Gi), dGi = nr * (-ir * Gi + kap * Gr);
-    const T Fw = __shfl_xor_sync(0xffffffffu, F, 1);
-    const T dFw = __shfl_xor_sync(0xffffffffu, dF, 1);
-    const bool odd = lane & 1;
-    const T Fr = odd ? Fw : F, Fi = odd ? F : Fw;
-    const T dFr = odd ? dFw : dF, dFi = odd ? dF : dFw;
-    accS += odd ? (Gr * Fi + Gi * Fr) : (Gr * Fr - Gi * Fi);
-    const T Dr = dGr * Fr - dGi * Fi + Gr * dFr - Gi * dFi;
-    const T Di = dGr * Fi + dGi * Fr + Gr * dFi + Gi * dFr;
-    accD += odd ? Di : Dr;
+      Q.slot = slot;
+    }
+    __syncwarp();
+    for (int cI = 0; cI < nc; ++cI) {
+      const TgtScal<T>& Q = S[cI];
+      const T* C = A.coefs + (size_t)Q.slot * kQ * 32 + lane;
+      T F = 0, dF = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const T b = Q.Ts[i] * Q.Tt[j];
+          const T p1 = Q.as * Q.dTs[i] * Q.Tt[j] + Q.at * Q.Ts[i] * Q.dTt[j];
+          const T p2 = Q.ap * b;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const T c = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
+            F += b * Q.Tp[k] * c;
+            dF += (p1 * Q.Tp[k] + p2 * Q.dTp[k]) * c;
+          }
+        }
+      const T Gr = Q.G[ks][0], Gi = Q.G[ks][1], dGr = Q.G[ks][2], dGi = Q.G[ks][3];
+      const T Fw = __shfl_xor_sync(0xffffffffu, F, 1);
+      const T dFw = __shfl_xor_sync(0xffffffffu, dF, 1);
+      const bool odd = lane & 1;
+      const T Fr = odd ? Fw : F, Fi = odd ? F : Fw;
+      const T dFr = odd ? dFw : dF, dFi = odd ? dF : dFw;
+      accS += odd ? (Gr * Fi + Gi * Fr) : (Gr * Fr - Gi * Fi);
+      const T Dr = dGr * Fr - dGi * Fi + Gr * dFr - Gi * dFi;
+      const T Di = dGr * Fi + dGi * Fr + Gr * dFi + Gi * dFr;
+      accD += odd ? Di : Dr;
+    }
+    __syncwarp();
   }
   T* out = A.f28 + 56 * (size_t)A.perm[t];
   out[lane] += accS;
@@ -428,7 +601,7 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
     TgtArgs<T> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, L.cg,
                  (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (T*)p->f28, ke, ki};
     int rec = timer_begin(p, TK_TARGET, s);
-    k_target<T><<<(unsigned)(((size_t)p->N * 32 + 255) / 256), 256, 0, s>>>(B);
+    k_target<T><<<(unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), 32 * tgt_warps<T>(), 0, s>>>(B);
     timer_end(p, rec, s);
     ++p->launches;
     if (d > 3) {
@@ -436,7 +609,12 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
       UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, Pp.cg,
                   L.cone_map, L.cg.ncones(), L.cg, L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki};
       rec = timer_begin(p, TK_UP, s);
-      if (Pp.nslots > 0) k_up<T><<<Pp.nslots, kUpThreads, 0, s>>>(U);
+      if (Pp.nslots > 0) {
+        if constexpr (std::is_same<T, float>::value)
+          k_up_grouped<float><<<Pp.nslots, kUpThreads, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_ntask});
+        else
+          k_up<T><<<Pp.nslots, kUpThreads, 0, s>>>(U);
+      }
       timer_end(p, rec, s);
       ++p->launches;
     }
