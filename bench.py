@@ -25,15 +25,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "sphere r=2 lambda, eps_r=4, 96 patches x 10x10 nodes (N=9600, 38400 unknowns)"
+WORKLOADS = {
+    "sphere9600": "sphere r=2 lambda, eps_r=4, 96 patches x 10x10 nodes (N=9600, 38400 unknowns)",
+    "sphere153600": "sphere r=4 lambda, eps_r=2.25, 600 patches x 16x16 nodes (N=153600, 614400 unknowns)",
+}
+WORKLOAD = WORKLOADS["sphere9600"]
 METRIC = "IFGF N-Mueller unknown*matvecs/s at rel err <=1e-4; GMRES time-to-solve"
 UNIT = "unknown*matvecs/s"
 # cone segments at level D+1: (2, 3) keeps the forward-map error <= 1e-4 on this body
 NS0, NA0 = 2, 3
 
 
-def problem():
-    from inputs import CONFIG_SPHERE_MEDIUM
+def problem(name: str = "sphere9600"):
+    from inputs import CONFIG_SPHERE_MEDIUM, sphere_problem
+    if name == "sphere153600":
+        return sphere_problem(4.0, 10, 16, 2.25, name="sphere_r4_eps2.25_P600")
     return CONFIG_SPHERE_MEDIUM(10)
 
 
@@ -133,7 +139,7 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    prob = problem()
+    prob = problem(args.workload)
     delta = delta_of(prob)
     plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
                                  far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=400)
@@ -195,7 +201,8 @@ def run_gpu(args):
         / np.sqrt(2))).cuda()
     o1 = torch.empty_like(yv)
     plan.apply(yv, o1)
-    ref_plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP64,
+    ref_plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0,
+                                     precision=lib.IFGF_FP64 if prob.n <= 20000 else lib.IFGF_FP32,
                                      far_mode=lib.IFGF_FAR_DIRECT, max_krylov=10)
     o2 = torch.empty_like(yv)
     ref_plan.apply(yv, o2)
@@ -239,12 +246,13 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Arnoldi, FP64 setup)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "far_field": f"IFGF, Ps=3 Pa=5, (ns,na)_(D+1)=({NS0},{NA0})",
+        "config": {"workload": WORKLOADS[args.workload], "far_field": f"IFGF, Ps=3 Pa=5, (ns,na)_(D+1)=({NS0},{NA0})",
                    "levels": st["levels"], "gmres_tol": tol, "rhs": "plane wave +z, x-pol",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the events)"},
         "gmres_time_to_solve_s": t_step, "gmres_iters": int(np.mean(iters)),
-        "matvec_rel_err_vs_fp64_direct": matvec_err,
+        "matvec_rel_err_vs_direct": matvec_err,
+        "matvec_err_reference": "plain direct far sum, FP64" if prob.n <= 20000 else "plain direct far sum, FP32",
         "stage_ms_per_apply": {k: ktime[k][0] / max(napply, 1) for k in ktime},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * N * 16,
@@ -297,22 +305,39 @@ def cpu_baseline(prob, delta, budget_s=15.0, reference_units=False):
 
 
 def run_apply(args):
-    """Forward maps only (no GMRES, no timing output): a short command for profilers."""
+    """Forward maps only (no GMRES): a short command for profilers, and a
+    forward-map throughput line (stage times from the library's events)."""
     import torch
     import paper_2408_02274_gb300 as lib
     from paper_2408_02274_gb300 import build as libbuild
     from inputs import random_densities
     libbuild.build()
-    prob = problem()
+    prob = problem(args.workload)
+    t0 = time.perf_counter()
     plan = lib.Plan.from_problem(prob, delta=delta_of(prob), n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
                                  far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=10)
+    setup = time.perf_counter() - t0
     y = torch.from_numpy(random_densities(prob.n, 1)).cuda()
     out = torch.empty_like(y)
-    for _ in range(args.warmup + args.steps):
+    for _ in range(args.warmup):
         plan.apply(y, out)
     torch.cuda.synchronize()
+    lib.ifgf_set_timing(plan.handle, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.apply(y, out)
+    e1.record()
+    torch.cuda.synchronize()
+    kt, launches = lib.ifgf_get_timing(plan.handle)
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    st = plan.stats()
     plan.close()
-    return {"mode": "apply", "applies": args.warmup + args.steps}
+    return {"mode": "apply", "workload": WORKLOADS[args.workload], "applies": args.steps,
+            "ms_per_forward_map": ms, "unknown_matvecs_per_s": 4.0 * prob.n / (ms / 1e3),
+            "stage_ms_per_apply": {k: v[0] / max(args.steps, 1) for k, v in kt.items()},
+            "setup_s": setup, "levels": st["levels"], "cones": st["cones"], "near_nnz": st["near_nnz"],
+            "device_bytes": st["device_bytes"]}
 
 
 def run_reference(args):
@@ -345,6 +370,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="solve", choices=["solve", "apply"])
+    ap.add_argument("--workload", default="sphere9600", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

@@ -120,6 +120,67 @@ static double snap_edge(double t) {
   return t;
 }
 
+/* Position, first and second parametric derivatives of the interpolant (channels 0..2):
+ * out = [x, x_u, x_v, x_uu, x_uv, x_vv] (3 each).  T'' by differentiating the recurrence twice. */
+static void geom_eval_d2(const patch_geom *g, double u, double v, double *out) {
+  double T[2][64], dT[2][64], ddT[2][64];
+  double xs[2] = {u, v};
+  for (int a = 0; a < 2; ++a) {
+    double t = xs[a];
+    for (int k = 0; k < g->ng; ++k) {
+      if (k == 0) { T[a][0] = 1; dT[a][0] = 0; ddT[a][0] = 0; }
+      else if (k == 1) { T[a][1] = t; dT[a][1] = 1; ddT[a][1] = 0; }
+      else {
+        T[a][k] = 2 * t * T[a][k - 1] - T[a][k - 2];
+        dT[a][k] = 2 * T[a][k - 1] + 2 * t * dT[a][k - 1] - dT[a][k - 2];
+        ddT[a][k] = 4 * dT[a][k - 1] + 2 * t * ddT[a][k - 1] - ddT[a][k - 2];
+      }
+    }
+  }
+  for (int c = 0; c < 18; ++c) out[c] = 0;
+  for (int m = 0; m < g->ng; ++m)
+    for (int n = 0; n < g->ng; ++n) {
+      const double *cf = g->coef + ((size_t)m * g->ng + n) * 9;
+      double w[6] = {T[0][m] * T[1][n], dT[0][m] * T[1][n], T[0][m] * dT[1][n],
+                     ddT[0][m] * T[1][n], dT[0][m] * dT[1][n], T[0][m] * ddT[1][n]};
+      for (int q = 0; q < 6; ++q)
+        for (int c = 0; c < 3; ++c) out[3 * q + c] += cf[c] * w[q];
+    }
+}
+
+/* Newton steps on the stationarity conditions (x - eta).eta_u = (x - eta).eta_v = 0 after the
+ * golden-section search: the search only resolves a flat minimum to ~sqrt(eps); these steps
+ * make the closest point reproducible to rounding (reading R15).  Coordinates on an edge
+ * (|t| = 1 after snapping) stay fixed; a step is taken only where the Hessian is positive. */
+static void newton_polish(const patch_geom *g, const double *x, double *u, double *v, int iters) {
+  const int fu = (*u == 1.0 || *u == -1.0), fv = (*v == 1.0 || *v == -1.0);
+  if (fu && fv) return;
+  for (int it = 0; it < iters; ++it) {
+    double o[18];
+    geom_eval_d2(g, *u, *v, o);
+    double r[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
+    double gu = -(r[0] * o[3] + r[1] * o[4] + r[2] * o[5]);
+    double gv = -(r[0] * o[6] + r[1] * o[7] + r[2] * o[8]);
+    double Huu = o[3] * o[3] + o[4] * o[4] + o[5] * o[5] - (r[0] * o[9] + r[1] * o[10] + r[2] * o[11]);
+    double Huv = o[3] * o[6] + o[4] * o[7] + o[5] * o[8] - (r[0] * o[12] + r[1] * o[13] + r[2] * o[14]);
+    double Hvv = o[6] * o[6] + o[7] * o[7] + o[8] * o[8] - (r[0] * o[15] + r[1] * o[16] + r[2] * o[17]);
+    double du = 0, dv = 0;
+    if (fu) {
+      if (Hvv > 0) dv = -gv / Hvv;
+    } else if (fv) {
+      if (Huu > 0) du = -gu / Huu;
+    } else {
+      double det = Huu * Hvv - Huv * Huv;
+      if (Huu > 0 && det > 0) {
+        du = -(Hvv * gu - Huv * gv) / det;
+        dv = -(Huu * gv - Huv * gu) / det;
+      }
+    }
+    *u = fmin(1.0, fmax(-1.0, *u + du));
+    *v = fmin(1.0, fmax(-1.0, *v + dv));
+  }
+}
+
 /* ---------------- clustering change of variables (Eqs. mk_cov_1, mk_cov_2, cov) ---------------- */
 static double nu_f(double t, double d) {
   double a = (M_PI - t) / M_PI;
@@ -168,31 +229,55 @@ static void cheb_T_diff(double a, double delta, int n, double *Ta, double *Dk) {
   for (int k = 1; k + 1 < n; ++k) Dk[k + 1] = 2.0 * delta * (Ta[k] + Dk[k]) + 2.0 * a * Dk[k] - Dk[k - 1];
 }
 
-/* Displacement eta(a + du, b + dv) - eta(a, b) of the patch interpolant, cancellation-free:
- * sum_mn c_mn [D_m(u) T_n(b + dv) + T_m(a) D_n(v)]. */
-static void geom_disp(const patch_geom *g, double a, double du, double b, double dv, double *e) {
-  double Ta[64], Da[64], Tb[64], Db[64];
+/* Second differences E_k = T_k(a + delta) - T_k(a) - delta T_k'(a), k < n:
+ * E_{k+1} = 2 delta D_k + 2 a E_k - E_{k-1}, E_0 = E_1 = 0 (D_k as above). */
+static void cheb_T_diff2(double a, double delta, int n, const double *Dk, double *Ek) {
+  if (n > 0) Ek[0] = 0.0;
+  if (n > 1) Ek[1] = 0.0;
+  for (int k = 1; k + 1 < n; ++k) Ek[k + 1] = 2.0 * delta * Dk[k] + 2.0 * a * Ek[k] - Ek[k - 1];
+}
+
+/* Displacement e = eta(a + du, b + dv) - eta(a, b) of the patch interpolant and its
+ * component along the target normal nrm, both without cancellation:
+ *   e = sum_mn c_mn [D_m(u) (T_n(b) + D_n(v)) + T_m(a) D_n(v)],
+ *   nrm.e = nrm.R,  R = sum_mn c_mn [D_m D_n + T_n(b) E_m + T_m(a) E_n]
+ * (E the second differences).  nrm.e is second order in the distance while e is first
+ * order, so it must not be formed from e.  The first-order part du nrm.eta_u + dv nrm.eta_v
+ * vanishes on the surface (the normal is orthogonal to the tangent plane); on the
+ * interpolant it is the derivative of the interpolation error, which differentiation
+ * near an edge inflates to ~ng^2 times the coefficient rounding, so it is left out
+ * (reading R21). */
+static void geom_disp(const patch_geom *g, double a, double du, double b, double dv, const double *nrm,
+                      double *e, double *ne) {
+  double Ta[64], Da[64], Ea[64], Tb[64], Db[64], Eb[64];
   cheb_T_diff(a, du, g->ng, Ta, Da);
   cheb_T_diff(b, dv, g->ng, Tb, Db);
+  cheb_T_diff2(a, du, g->ng, Da, Ea);
+  cheb_T_diff2(b, dv, g->ng, Db, Eb);
+  double R[3] = {0, 0, 0};
   e[0] = e[1] = e[2] = 0.0;
   for (int m = 0; m < g->ng; ++m)
     for (int n = 0; n < g->ng; ++n) {
       const double *cf = g->coef + ((size_t)m * g->ng + n) * 9;
       double f = Da[m] * (Tb[n] + Db[n]) + Ta[m] * Db[n];
-      for (int c = 0; c < 3; ++c) e[c] += cf[c] * f;
+      double r2 = Da[m] * Db[n] + Tb[n] * Ea[m] + Ta[m] * Eb[n];
+      for (int c = 0; c < 3; ++c) {
+        e[c] += cf[c] * f;
+        R[c] += cf[c] * r2;
+      }
     }
+  *ne = nrm[0] * R[0] + nrm[1] * R[1] + nrm[2] * R[2];
 }
 
-/* The four kernels for the separation d = x - y and the target normal n_x:
- * G_e, G_i, dG_e/dn_x, dG_i/dn_x.  r == 0 -> zeros. */
-static void kernels4(const double *dv, const double *nx, double ke, double ki, cplx *K) {
+/* The four kernels for the separation d = x - y, its component nd = n_x.d along the
+ * target normal, and the wavenumbers: G_e, G_i, dG_e/dn_x, dG_i/dn_x.  r == 0 -> zeros. */
+static void kernels4n(const double *dv, double nd, double ke, double ki, cplx *K) {
   double d0 = dv[0], d1 = dv[1], d2 = dv[2];
   double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
   if (r == 0.0) {
     K[0] = K[1] = K[2] = K[3] = 0.0;
     return;
   }
-  double nd = nx[0] * d0 + nx[1] * d1 + nx[2] * d2;
   double kk[2] = {ke, ki};
   for (int s = 0; s < 2; ++s) {
     cplx g = cexp(I * kk[s] * r) / (4.0 * M_PI * r);
@@ -203,7 +288,7 @@ static void kernels4(const double *dv, const double *nx, double ke, double ki, c
 
 static void kernels4_xy(const double *x, const double *nx, const double *y, double ke, double ki, cplx *K) {
   double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
-  kernels4(d, nx, ke, ki, K);
+  kernels4n(d, nx[0] * d[0] + nx[1] * d[1] + nx[2] * d[2], ke, ki, K);
 }
 
 /*
@@ -271,6 +356,7 @@ int ora_kernel_rows(int P, int nc, int ng, const double *nodes, const double *no
           double d2 = golden_uv(&g, x, ua, uz, va, vz, gs_iters, &uc, &vc);
           uc = snap_edge(uc);
           vc = snap_edge(vc);
+          newton_polish(&g, x, &uc, &vc, 4);
           (void)d2;
           double dist = sqrt(dist2_uv(&g, x, uc, vc));
           singular = dist <= delta;
@@ -307,12 +393,12 @@ int ora_kernel_rows(int P, int nc, int ng, const double *nodes, const double *no
           cplx k4[4];
           if (p == pl) {
             /* Target on this patch: it is the interpolated surface point eta_p(u_i', v_j')
-             * (reading R12) and x - y = -(eta(u, v) - eta(uc, vc)) is formed from
-             * Chebyshev differences so that no cancellation occurs near the target. */
-            double e[3];
-            geom_disp(&g, uc, dub[i], vc, dvb[j], e);
+             * (reading R12); x - y = -(eta(u, v) - eta(uc, vc)) and its normal component are
+             * formed from Chebyshev differences so that no cancellation occurs near the target. */
+            double e[3], ne;
+            geom_disp(&g, uc, dub[i], vc, dvb[j], nx, e, &ne);
             double dneg[3] = {-e[0], -e[1], -e[2]};
-            kernels4(dneg, nx, ke, ki, k4);
+            kernels4n(dneg, -ne, ke, ki, k4);
           } else {
             kernels4_xy(x, nx, gv, ke, ki, k4);
           }
@@ -374,6 +460,7 @@ double ora_closest_point(int nc, int ng, const double *patch_nodes, const double
   golden_uv(&g, x, ua, uz, va, vz, gs_iters, &uc, &vc);
   uv[0] = snap_edge(uc);
   uv[1] = snap_edge(vc);
+  newton_polish(&g, x, &uv[0], &uv[1], 4);
   return sqrt(dist2_uv(&g, x, uv[0], uv[1]));
 }
 

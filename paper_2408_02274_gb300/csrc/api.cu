@@ -271,6 +271,7 @@ void build(ifgf_plan_t* p) {
   }
   p->stats.n = N;
   p->stats.levels = t.D;
+  check(setup_combine_kernels(), "combine kernel attributes");
   // ---------------- per-apply buffers and GMRES workspace
   const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
   p->phi = A.dev<char>(16 * (size_t)N * el);

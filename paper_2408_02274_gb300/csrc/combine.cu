@@ -250,6 +250,16 @@ cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const dou
   return cudaGetLastError();
 }
 
+// Opt the patch-wise kernels into the dynamic shared memory their largest
+// patch (nc = 24) needs: k_combine keeps 16 complex FP64 fields per node.
+cudaError_t setup_combine_kernels() {
+  const int smax = (int)(sizeof(double) * 32 * 24 * 24);
+  cudaError_t e = cudaFuncSetAttribute(k_combine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_combine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  return e;
+}
+
 cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s) {
   const int npp = p->nc * p->nc;
   size_t smem = sizeof(double) * 32 * npp;

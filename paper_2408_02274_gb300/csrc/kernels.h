@@ -35,6 +35,7 @@ cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const dou
                                 cudaStream_t s);
 // c-post: f28 + y -> out [4][N] complex128
 cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s);
+cudaError_t setup_combine_kernels();
 // (d): f28 = near * phi   (overwrites f28)
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s);
 // far field by the plain direct sum (accumulates into f28)

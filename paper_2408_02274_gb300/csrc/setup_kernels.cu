@@ -181,6 +181,84 @@ __device__ inline double snap_edge(double t) {
   return t;
 }
 
+// Position, first and second parametric derivatives of the interpolant (channels 0..2):
+// out = [x, x_u, x_v, x_uu, x_uv, x_vv], T'' by differentiating the recurrence twice.
+__device__ void geom_d2(const PatchCoef& pc, double u, double v, double* out) {
+  for (int c = 0; c < 18; ++c) out[c] = 0;
+  double Tu0 = 1, Tu1 = u, dTu0 = 0, dTu1 = 1, ddTu0 = 0, ddTu1 = 0;
+  for (int m = 0; m < pc.ng; ++m) {
+    double Tm, dTm, ddTm;
+    if (m == 0) { Tm = 1; dTm = 0; ddTm = 0; }
+    else if (m == 1) { Tm = u; dTm = 1; ddTm = 0; }
+    else {
+      Tm = 2 * u * Tu1 - Tu0;
+      dTm = 2 * Tu1 + 2 * u * dTu1 - dTu0;
+      ddTm = 4 * dTu1 + 2 * u * ddTu1 - ddTu0;
+      Tu0 = Tu1; Tu1 = Tm; dTu0 = dTu1; dTu1 = dTm; ddTu0 = ddTu1; ddTu1 = ddTm;
+    }
+    double a[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};   // sum_n c_mn {T_n, T_n', T_n''}(v)
+    double Tv0 = 1, Tv1 = v, dTv0 = 0, dTv1 = 1, ddTv0 = 0, ddTv1 = 0;
+    for (int n = 0; n < pc.ng; ++n) {
+      double Tn, dTn, ddTn;
+      if (n == 0) { Tn = 1; dTn = 0; ddTn = 0; }
+      else if (n == 1) { Tn = v; dTn = 1; ddTn = 0; }
+      else {
+        Tn = 2 * v * Tv1 - Tv0;
+        dTn = 2 * Tv1 + 2 * v * dTv1 - dTv0;
+        ddTn = 4 * dTv1 + 2 * v * ddTv1 - ddTv0;
+        Tv0 = Tv1; Tv1 = Tn; dTv0 = dTv1; dTv1 = dTn; ddTv0 = ddTv1; ddTv1 = ddTn;
+      }
+      const double* cf = pc.c + ((size_t)m * pc.ng + n) * 9;
+      for (int c = 0; c < 3; ++c) {
+        a[0][c] += cf[c] * Tn;
+        a[1][c] += cf[c] * dTn;
+        a[2][c] += cf[c] * ddTn;
+      }
+    }
+    for (int c = 0; c < 3; ++c) {
+      out[c] += a[0][c] * Tm;
+      out[3 + c] += a[0][c] * dTm;
+      out[6 + c] += a[1][c] * Tm;
+      out[9 + c] += a[0][c] * ddTm;
+      out[12 + c] += a[1][c] * dTm;
+      out[15 + c] += a[2][c] * Tm;
+    }
+  }
+}
+
+// Newton steps on the stationarity conditions (x - eta).eta_u = (x - eta).eta_v = 0 after
+// the golden-section search, which resolves a flat minimum only to ~sqrt(eps): they make
+// the closest point reproducible to rounding (reading R15).  Edge coordinates (|t| = 1
+// after snapping) stay fixed; a step is taken only where the Hessian is positive.
+__device__ void newton_polish(const PatchCoef& pc, const double* x, double* u, double* v, int iters) {
+  const bool fu = (*u == 1.0 || *u == -1.0), fv = (*v == 1.0 || *v == -1.0);
+  if (fu && fv) return;
+  for (int it = 0; it < iters; ++it) {
+    double o[18];
+    geom_d2(pc, *u, *v, o);
+    const double r0 = x[0] - o[0], r1 = x[1] - o[1], r2 = x[2] - o[2];
+    const double gu = -(r0 * o[3] + r1 * o[4] + r2 * o[5]);
+    const double gv = -(r0 * o[6] + r1 * o[7] + r2 * o[8]);
+    const double Huu = o[3] * o[3] + o[4] * o[4] + o[5] * o[5] - (r0 * o[9] + r1 * o[10] + r2 * o[11]);
+    const double Huv = o[3] * o[6] + o[4] * o[7] + o[5] * o[8] - (r0 * o[12] + r1 * o[13] + r2 * o[14]);
+    const double Hvv = o[6] * o[6] + o[7] * o[7] + o[8] * o[8] - (r0 * o[15] + r1 * o[16] + r2 * o[17]);
+    double du = 0, dv = 0;
+    if (fu) {
+      if (Hvv > 0) dv = -gv / Hvv;
+    } else if (fv) {
+      if (Huu > 0) du = -gu / Huu;
+    } else {
+      const double det = Huu * Hvv - Huv * Huv;
+      if (Huu > 0 && det > 0) {
+        du = -(Hvv * gu - Huv * gv) / det;
+        dv = -(Huu * gv - Huv * gu) / det;
+      }
+    }
+    *u = fmin(1.0, fmax(-1.0, *u + du));
+    *v = fmin(1.0, fmax(-1.0, *v + dv));
+  }
+}
+
 // One thread per candidate (target, patch) pair: closest parameters and the
 // singular-set decision dist(x_l, Gamma_p) <= delta (Eq. patch_sing).
 __global__ void k_closest(int npairs, int nc, int ng, int iters, double delta, const int* pair_tgt,
@@ -228,6 +306,7 @@ __global__ void k_closest(int npairs, int nc, int ng, int iters, double delta, c
   golden_inner(pc, xl, uc, va, vb, iters, &vc);
   uc = snap_edge(uc);
   vc = snap_edge(vc);
+  newton_polish(pc, xl, &uc, &vc, 4);
   uv[2 * e] = uc;
   uv[2 * e + 1] = vc;
   singular[e] = sqrt(dist2_at(pc, xl, uc, vc)) <= delta ? 1 : 0;
@@ -271,26 +350,26 @@ __device__ inline void xi_f(double alpha, double tau, double d, double* xi, doub
   *xi = alpha + *dxi;
 }
 
-// T_k(a + delta) - T_k(a) for k = 0.. by the difference recurrence
-// D_{k+1} = 2 delta T_k(a + delta) + 2 a D_k - D_{k-1}  (no cancellation for small delta).
+// T_k(a + delta) - T_k(a) (first differences D_k) and T_k(a + delta) - T_k(a) - delta T_k'(a)
+// (second differences E_k) for k = 0.. by the recurrences
+//   D_{k+1} = 2 delta T_k(a + delta) + 2 a D_k - D_{k-1},  E_{k+1} = 2 delta D_k + 2 a E_k - E_{k-1},
+// which do not cancel for small delta.
 struct ChebDiff {
-  double a, delta, T0, T1, D0, D1;
+  double a, delta, T0, T1, D0, D1, E0, E1;
   int k;
-  __device__ ChebDiff(double a_, double d_) : a(a_), delta(d_), T0(1), T1(a_), D0(0), D1(d_), k(0) {}
-  // returns (T_k(a), D_k) and advances
-  __device__ inline void next(double* Tk, double* Dk) {
+  __device__ ChebDiff(double a_, double d_) : a(a_), delta(d_), T0(1), T1(a_), D0(0), D1(d_), E0(0), E1(0), k(0) {}
+  // returns (T_k(a), D_k, E_k) and advances
+  __device__ inline void next(double* Tk, double* Dk, double* Ek) {
     if (k == 0) {
-      *Tk = 1.0;
-      *Dk = 0.0;
+      *Tk = 1.0; *Dk = 0.0; *Ek = 0.0;
     } else if (k == 1) {
-      *Tk = a;
-      *Dk = delta;
+      *Tk = a; *Dk = delta; *Ek = 0.0;
     } else {
       double T2 = 2 * a * T1 - T0;
       double D2 = 2 * delta * (T1 + D1) + 2 * a * D1 - D0;
-      T0 = T1; T1 = T2; D0 = D1; D1 = D2;
-      *Tk = T2;
-      *Dk = D2;
+      double E2 = 2 * delta * D1 + 2 * a * E1 - E0;
+      T0 = T1; T1 = T2; D0 = D1; D1 = D2; E0 = E1; E1 = E2;
+      *Tk = T2; *Dk = D2; *Ek = E2;
     }
     ++k;
   }
@@ -314,7 +393,7 @@ __global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, cons
   // per-warp shared layout
   const int nb = nbeta, npp = nc * nc;
   size_t per = 6 * (size_t)nb + (size_t)ng * 9 + 8 * (size_t)nb + (size_t)nb * nc + 8 * (size_t)nc +
-               (size_t)nc + 8 * (size_t)npp + 6 * (size_t)ng;
+               (size_t)nc + 8 * (size_t)npp + 9 * (size_t)ng;
   double* base = sm + per * warp;
   double* ub = base;                 // [nb] u_i
   double* mub = ub + nb;             // [nb]
@@ -330,6 +409,7 @@ __global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, cons
   double* dvb = dub + nb;                // [nb] v_j - vc
   double* cua = dvb + nb;                // [ng][3] geometry contracted at uc
   double* cud = cua + 3 * (size_t)ng;    // [ng][3] contracted with T_m(u_i) - T_m(uc)
+  double* cuE = cud + 3 * (size_t)ng;    // [ng][3] contracted with the second differences at u_i
   if (sp >= nsp) return;
   const int e = sp_pair[sp];
   const int l = pair_tgt[e], p = pair_patch[e];
@@ -397,13 +477,15 @@ __global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, cons
       for (int t = lane; t < ng * 3; t += 32) {
         int n = t / 3, ch = t % 3;
         ChebDiff cd(uc, dub[i]);
-        double acc = 0;
+        double acc = 0, acce = 0;
         for (int m = 0; m < ng; ++m) {
-          double Tm, Dm;
-          cd.next(&Tm, &Dm);
+          double Tm, Dm, Em;
+          cd.next(&Tm, &Dm, &Em);
           acc += pc.c[((size_t)m * ng + n) * 9 + ch] * Dm;
+          acce += pc.c[((size_t)m * ng + n) * 9 + ch] * Em;
         }
         cud[t] = acc;
+        cuE[t] = acce;
       }
     if (lane < nc) {
       double T0 = 1, T1 = u, acc = A[lane];
@@ -436,18 +518,28 @@ __global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, cons
       double J = sqrt(c0 * c0 + c1 * c1 + c2 * c2);
       double wt = J * mub[i] * mvb[j] * wb[i] * wb[j];
       double d0 = xs[0] - gv[0], d1 = xs[1] - gv[1], d2 = xs[2] - gv[2];
+      double ndn = nx0 * d0 + nx1 * d1 + nx2 * d2;
       if (self) {
+        // e = eta(u, v) - eta(uc, vc) and, separately, its normal component from the
+        // second-order remainder (n.e is second order in the distance, e first order).
+        // The first-order part du n.eta_u + dv n.eta_v vanishes on the surface; on the
+        // interpolant it is the derivative of the interpolation error, which near an edge
+        // carries ~ng^2 times the coefficient rounding, so it is left out (reading R21).
         ChebDiff cd(vc, dvb[j]);
-        double e0 = 0, e1 = 0, e2 = 0;
+        double e0 = 0, e1 = 0, e2 = 0, R0 = 0, R1 = 0, R2 = 0;
         for (int n = 0; n < ng; ++n) {
-          double Tn, Dn;
-          cd.next(&Tn, &Dn);
+          double Tn, Dn, En;
+          cd.next(&Tn, &Dn, &En);
           const double tv = Tn + Dn;   // T_n(v_j)
           e0 += cud[3 * n] * tv + cua[3 * n] * Dn;
           e1 += cud[3 * n + 1] * tv + cua[3 * n + 1] * Dn;
           e2 += cud[3 * n + 2] * tv + cua[3 * n + 2] * Dn;
+          R0 += cud[3 * n] * Dn + cuE[3 * n] * Tn + cua[3 * n] * En;
+          R1 += cud[3 * n + 1] * Dn + cuE[3 * n + 1] * Tn + cua[3 * n + 1] * En;
+          R2 += cud[3 * n + 2] * Dn + cuE[3 * n + 2] * Tn + cua[3 * n + 2] * En;
         }
         d0 = -e0; d1 = -e1; d2 = -e2;
+        ndn = -(nx0 * R0 + nx1 * R1 + nx2 * R2);
       }
       double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
       for (int s = 0; s < 2; ++s) {
@@ -458,7 +550,7 @@ __global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, cons
           double g = wt / (4.0 * kPi * r);
           fr = g * cs;
           fi = g * sn;
-          double nd = (nx0 * d0 + nx1 * d1 + nx2 * d2) / (r * r);
+          double nd = ndn / (r * r);
           // (i k r - 1) * (fr + i fi) * nd
           dr = nd * (-fr - kk[s] * r * fi);
           di = nd * (-fi + kk[s] * r * fr);
@@ -498,7 +590,7 @@ __global__ void k_moments(int nsp, const int* sp_pair, const int* pair_tgt, cons
 size_t moments_smem_per_warp(int nc, int ng, int nbeta) {
   int npp = nc * nc;
   return sizeof(double) * (6 * (size_t)nbeta + (size_t)ng * 9 + 8 * (size_t)nbeta + (size_t)nbeta * nc +
-                           8 * (size_t)nc + (size_t)nc + 8 * (size_t)npp + 6 * (size_t)ng);
+                           8 * (size_t)nc + (size_t)nc + 8 * (size_t)npp + 9 * (size_t)ng);
 }
 
 // ---------------------------------------------------------------- near-field matrix values
