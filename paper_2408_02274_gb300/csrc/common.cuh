@@ -15,6 +15,7 @@ constexpr int kQ = kPs * kPa * kPa;               // 75 interpolation points per
 constexpr int kF = 16;                            // complex fields carried by the IFGF: 8 densities x 2 kernels
 constexpr int kFR = 2 * kF;                       // real components (re, im interleaved)
 constexpr int kNearFields = 28;                   // S_e[8], S_i[8], D_e[6], D_i[6]
+constexpr int kUpRunMax = 32;                     // parent points per upward-pass run (<= 32: one per lane)
 
 // Complex helpers on plain real pairs (the library keeps complex data interleaved).
 template <typename T>
@@ -40,6 +41,15 @@ template <>
 __device__ inline float sqrt_t<float>(float x) { return sqrtf(x); }
 template <>
 __device__ inline double sqrt_t<double>(double x) { return sqrt(x); }
+
+#if defined(__CUDACC__)
+template <typename T>
+__device__ inline T cospi_t(T x);
+template <>
+__device__ inline float cospi_t<float>(float x) { return cospif(x); }
+template <>
+__device__ inline double cospi_t<double>(double x) { return cospi(x); }
+#endif
 
 template <typename T>
 __device__ inline T atan2_t(T y, T x);
@@ -81,6 +91,19 @@ struct ConeGeom {
   __host__ __device__ double ds() const { return kEta / ns; }
   __host__ __device__ double dth() const { return kPi / na; }
 };
+
+// The same geometry in the arithmetic type of a kernel, with the spacings and their
+// reciprocals formed once on the host (no FP64 division inside the FP32 kernels).
+template <typename T>
+struct ConeGeomT {
+  T h, ds, dth, ids, idth;
+  int ns, na;
+  __host__ __device__ int ncones() const { return ns * na * 2 * na; }
+};
+template <typename T>
+inline ConeGeomT<T> cone_geom_t(const ConeGeom& g) {
+  return ConeGeomT<T>{(T)g.h, (T)g.ds(), (T)g.dth(), (T)(1.0 / g.ds()), (T)(1.0 / g.dth()), g.ns, g.na};
+}
 
 __host__ __device__ inline void cone_decode(int id, int na, int* g1, int* g2, int* g3) {
   int n3 = 2 * na;

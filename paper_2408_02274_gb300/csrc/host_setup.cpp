@@ -229,7 +229,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
         }
       }
       // per (parent cone, octant): the points ranked by the child cone they fall in, and
-      // runs of at most 4 consecutive ranked points that share one child cone
+      // runs of at most kUpRunMax consecutive ranked points that share one child cone
       Pp.up_order.assign((size_t)ncomp * 8 * kQ, 0);
       Pp.up_task.assign((size_t)ncomp * 8 * kQ, 0);
       Pp.up_ntask.assign((size_t)ncomp * 8, 0);
@@ -241,10 +241,13 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
         int n = 0, r = 0;
         while (r < kQ) {
           int len = 1;
-          while (len < 4 && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
+          while (len < kUpRunMax && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
           Pp.up_task[g * kQ + n++] = r | (len << 8);
           r += len;
         }
+        // longest runs first: the warps of a block take runs in this order
+        std::stable_sort(&Pp.up_task[g * kQ], &Pp.up_task[g * kQ] + n,
+                         [](int32_t a, int32_t b) { return (a >> 8) > (b >> 8); });
         Pp.up_ntask[g] = n;
       }
       for (int b = 0; b < nb; ++b) {

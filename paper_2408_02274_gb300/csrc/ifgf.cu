@@ -42,29 +42,30 @@ struct SmallMaps {
 template <typename T>
 __device__ void init_maps(SmallMaps<T>& M) {
   int t = threadIdx.x;
+  // in the kernel's own precision (cos(pi x) of exact arguments)
   if (t < 9) {
     int i = t / 3, j = t % 3;
-    M.A3[t] = (T)((i == 0 ? 1.0 : 2.0) / 3.0 * cos(i * (j + 0.5) * kPi / 3.0));
+    M.A3[t] = (i == 0 ? T(1) : T(2)) / T(3) * cospi_t<T>(T(i * (2 * j + 1)) / T(6));
   }
   if (t < 25) {
     int i = t / 5, j = t % 5;
-    M.A5[t] = (T)((i == 0 ? 1.0 : 2.0) / 5.0 * cos(i * (j + 0.5) * kPi / 5.0));
+    M.A5[t] = (i == 0 ? T(1) : T(2)) / T(5) * cospi_t<T>(T(i * (2 * j + 1)) / T(10));
   }
-  if (t < 3) M.x3[t] = (T)cheb_node(t, 3);
-  if (t < 5) M.x5[t] = (T)cheb_node(t, 5);
+  if (t < 3) M.x3[t] = cospi_t<T>(T(2 * t + 1) / T(6));
+  if (t < 5) M.x5[t] = cospi_t<T>(T(2 * t + 1) / T(10));
 }
 
 // Interpolation point q of cone `cone` relative to the box centre.
 template <typename T>
-__device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeom& cg, int cone, int q, T* X) {
+__device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeomT<T>& cg, int cone, int q, T* X) {
   int g1, g2, g3;
   cone_decode(cone, cg.na, &g1, &g2, &g3);
   int is = q / 25, it = (q / 5) % 5, ip = q % 5;
-  T ds = (T)cg.ds(), dth = (T)cg.dth();
+  const T ds = cg.ds, dth = cg.dth;
   T s = ((T)g1 + T(0.5) * (T(1) + M.x3[is])) * ds;
   T th = ((T)g2 + T(0.5) * (T(1) + M.x5[it])) * dth;
   T ph = ((T)g3 + T(0.5) * (T(1) + M.x5[ip])) * dth;
-  T r = (T)cg.h / s;
+  T r = cg.h / s;
   T st, ct, sp, cp;
   sincos_t(th, &st, &ct);
   sincos_t(ph, &sp, &cp);
@@ -75,22 +76,21 @@ __device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeom& cg, int
 
 // Local coordinates in [-1, 1]^3 of a point (relative to the box centre) inside cone `cone`.
 template <typename T>
-__device__ inline void local_coords(const ConeGeom& cg, int cone, T x, T y, T z, T* ts, T* tt, T* tp,
+__device__ inline void local_coords(const ConeGeomT<T>& cg, int cone, T x, T y, T z, T* ts, T* tt, T* tp,
                                     T* rr, T* sth, T* cth, T* sph, T* cph) {
   int g1, g2, g3;
   cone_decode(cone, cg.na, &g1, &g2, &g3);
   T rho = sqrt_t(x * x + y * y);
   T r = sqrt_t(rho * rho + z * z);
-  T s = (T)cg.h / r;
+  T s = cg.h / r;
   T th = atan2_t(rho, z);
   T ph = atan2_t(y, x);
-  T dth = (T)cg.dth(), ds = (T)cg.ds();
-  T php = ph - (T)g3 * dth;
+  T php = ph - (T)g3 * cg.dth;
   if (php < T(-kPi)) php += T(2 * kPi);   // phi wraps: measure from the cell start
   if (php > T(kPi)) php -= T(2 * kPi);
-  *ts = T(2) * (s - (T)g1 * ds) / ds - T(1);
-  *tt = T(2) * (th - (T)g2 * dth) / dth - T(1);
-  *tp = T(2) * php / dth - T(1);
+  *ts = T(2) * (s * cg.ids - (T)g1) - T(1);
+  *tt = T(2) * (th * cg.idth - (T)g2) - T(1);
+  *tp = T(2) * php * cg.idth - T(1);
   *rr = r;
   *sth = rho / r;
   *cth = z / r;
@@ -133,10 +133,63 @@ __device__ void vals_to_coefs_col(const SmallMaps<T>& M, T* v, int st) {
   }
 }
 
+constexpr int kVS = 33;   // padded row stride of the value buffers
+
+// The same transform for all 32 columns of a [75][kVS] value buffer by the whole
+// block (one (line, column) task per thread and pass, consecutive threads on
+// consecutive columns), followed by a coalesced store of the 75 x 32 coefficients.
+// Every thread of the block must call it.
+template <typename T, int kStride>
+__device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* v, T* out) {
+  const int nt = blockDim.x;
+  for (int e = threadIdx.x; e < 15 * 32; e += nt) {   // phi lines
+    const int a = e >> 5, col = e & 31;
+    T t5[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) t5[k] = v[(a * 5 + k) * kStride + col];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      T acc = 0;
+#pragma unroll
+      for (int kk = 0; kk < 5; ++kk) acc += M.A5[k * 5 + kk] * t5[kk];
+      v[(a * 5 + k) * kStride + col] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 15 * 32; e += nt) {   // theta lines
+    const int ik = e >> 5, col = e & 31, is = ik / 5, k = ik % 5;
+    T t5[5];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) t5[j] = v[((is * 5 + j) * 5 + k) * kStride + col];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      T acc = 0;
+#pragma unroll
+      for (int jj = 0; jj < 5; ++jj) acc += M.A5[j * 5 + jj] * t5[jj];
+      v[((is * 5 + j) * 5 + k) * kStride + col] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 25 * 32; e += nt) {   // s lines
+    const int jk = e >> 5, col = e & 31;
+    T t3[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) t3[i] = v[(i * 25 + jk) * kStride + col];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      T acc = 0;
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) acc += M.A3[i * 3 + ii] * t3[ii];
+      v[(i * 25 + jk) * kStride + col] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kQ * 32; e += nt) out[e] = v[(e >> 5) * kStride + (e & 31)];
+}
+
 // ------------------------------------------------------------------ (a) leaf direct
 constexpr int kLeafThreads = 160;   // two cone segments (2 x 75 points) per pass
 constexpr int kLeafChunk = 256;     // sources staged per pass
-constexpr int kVS = 33;             // padded row stride of the value buffers
 
 template <typename T>
 struct LeafArgs {
@@ -144,7 +197,7 @@ struct LeafArgs {
   const int* box_slot_ptr;
   const int* slot_cone;
   const double* box_center;
-  ConeGeom cg;
+  ConeGeomT<T> cg;
   const double* x_sorted;
   const T* a_sorted;
   T* coefs;
@@ -242,11 +295,11 @@ struct UpArgs {
   const int* slot_cone;
   const int* slot_upidx;
   const int* child;        // [nboxes_p][8]
-  ConeGeom cgp;
+  ConeGeomT<T> cgp;
   // child level d
   const int* cone_map_c;
   int ncones_c;
-  ConeGeom cgc;
+  ConeGeomT<T> cgc;
   double Hc;
   const int* up_cc;        // [ncompact][8][75]
   const T* coefs_c;
@@ -330,17 +383,18 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
   }
 }
 
-// (b), grouped variant.  The parent points are processed in runs of up to 4
-// points that fall in the same child cone (box-independent tables built with
-// the octree), one warp per run and one lane per real column: each
-// coefficient the warp loads serves every point of the run, and the 3D
-// Chebyshev sum is contracted separably (over phi, then theta, then s).  All
-// children are processed in one pass; runs of different children add into
-// the parent values with shared-memory atomics (one column per lane, so no
-// bank conflicts within a warp).
+// (b), FP32 variant.  The parent points are processed in runs of up to
+// kUpRunMax points that fall in the same child cone (box-independent tables
+// built with the octree), one warp per run and one lane per real column.  The
+// warp loads the child cone's 75 x 32 coefficients once into registers (75
+// per lane) and then sweeps the run: per point only the cone scalars are read
+// from shared memory, and the 3D Chebyshev sum is contracted separably (over
+// phi, then theta, then s).  Runs of different children add into the parent
+// values with shared-memory atomics (one column per lane, so no bank
+// conflicts within a warp).
 struct RunTabs {
-  const int* order;   // [ncompact][8][75]
-  const int* task;    // [ncompact][8][75]
+  const int* order;   // [ncompact][8][75] points ranked by child cone
+  const int* task;    // [ncompact][8][75] run start | (length << 8)
   const int* ntask;   // [ncompact][8]
 };
 
@@ -351,14 +405,16 @@ struct PtInfo2 {
   T fr[2], fi[2];
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kUpThreads) k_up_grouped(UpArgs<T> A, RunTabs RT) {
-  static_assert(sizeof(T) == 4, "the grouped upward kernel is built for FP32");
+constexpr int kUpRunWarps = 4;
+
+__global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A, RunTabs RT) {
+  using T = float;
   __shared__ SmallMaps<T> M;
   __shared__ T Xp[kQ][3];
   __shared__ PtInfo2<T> info[8][kQ];
   __shared__ T vals[kQ * kVS];
   __shared__ int tstart[9];
+  __shared__ int next_task;
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
   init_maps(M);
@@ -370,6 +426,7 @@ __global__ void __launch_bounds__(kUpThreads) k_up_grouped(UpArgs<T> A, RunTabs 
       if (A.child[8 * P + o] >= 0) acc += RT.ntask[(size_t)ci * 8 + o];
     }
     tstart[8] = acc;
+    next_task = kUpRunWarps;
   }
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
@@ -401,59 +458,72 @@ __global__ void __launch_bounds__(kUpThreads) k_up_grouped(UpArgs<T> A, RunTabs 
   __syncthreads();
   const int ntot = tstart[8];
   const int ks = lane >> 4;   // columns 0..15 belong to kernel e, 16..31 to kernel i
-  for (int w = warp; w < ntot; w += kUpThreads / 32) {
+  // runs are taken dynamically (each octant's list is sorted longest first)
+  for (int w = warp; w < ntot;) {
     int o = 0;
     while (w >= tstart[o + 1]) ++o;
     const size_t g = (size_t)ci * 8 + o;
     const int tk = __ldg(RT.task + g * kQ + (w - tstart[o]));
     const int r0 = tk & 255, len = tk >> 8;
-    int q[4];
+    const int myq = (lane < len) ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
+    const int cslot = info[o][__shfl_sync(0xffffffffu, myq, 0)].cslot;
+    if (cslot >= 0) {   // always: the host marked every such cone relevant
+      const T* C = A.coefs_c + (size_t)cslot * kQ * 32 + lane;
+      T c[kQ];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) q[a] = __ldg(RT.order + g * kQ + r0 + (a < len ? a : 0));
-    const int cslot = info[o][q[0]].cslot;
-    if (cslot < 0) continue;   // cannot happen: the host marked every such cone relevant
-    T Ts[4][3], Tt[4][5], Tp[4][5];
+      for (int k = 0; k < kQ; ++k) c[k] = __ldg(C + k * 32);
+      // two points per step (the second one repeats the last point of an odd run and
+      // is not added): their contractions interleave
+      for (int a = 0; a < len; a += 2) {
+        const bool two = a + 1 < len;
+        const int q0 = __shfl_sync(0xffffffffu, myq, a);
+        const int q1 = __shfl_sync(0xffffffffu, myq, two ? a + 1 : a);
+        const PtInfo2<T>& I0 = info[o][q0];
+        const PtInfo2<T>& I1 = info[o][q1];
+        T Ts0[3], Tt0[5], Tp0[5], Ts1[3], Tt1[5], Tp1[5];
+        cheb_vals<T, 3>(I0.ts, Ts0);
+        cheb_vals<T, 5>(I0.tt, Tt0);
+        cheb_vals<T, 5>(I0.tp, Tp0);
+        cheb_vals<T, 3>(I1.ts, Ts1);
+        cheb_vals<T, 5>(I1.tt, Tt1);
+        cheb_vals<T, 5>(I1.tp, Tp1);
+        T E0[3] = {T(0), T(0), T(0)}, E1[3] = {T(0), T(0), T(0)};
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      cheb_vals<T, 3>(info[o][q[a]].ts, Ts[a]);
-      cheb_vals<T, 5>(info[o][q[a]].tt, Tt[a]);
-      cheb_vals<T, 5>(info[o][q[a]].tp, Tp[a]);
-    }
-    const T* C = A.coefs_c + (size_t)cslot * kQ * 32 + lane;
-    T E[4][3];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) E[a][0] = E[a][1] = E[a][2] = T(0);
+          for (int j = 0; j < 5; ++j) {
+            const T* cij = c + (i * 5 + j) * 5;
+            T d0 = Tp0[0] * cij[0], d1 = Tp1[0] * cij[0];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        T c[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) c[k] = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          T d = Tp[a][0] * c[0];
-#pragma unroll
-          for (int k = 1; k < 5; ++k) d += Tp[a][k] * c[k];
-          E[a][i] += Tt[a][j] * d;
+            for (int k = 1; k < 5; ++k) {
+              d0 += Tp0[k] * cij[k];
+              d1 += Tp1[k] * cij[k];
+            }
+            E0[i] += Tt0[j] * d0;
+            E1[i] += Tt1[j] * d1;
+          }
+        const T v0 = Ts0[0] * E0[0] + Ts0[1] * E0[1] + Ts0[2] * E0[2];
+        const T v1 = Ts1[0] * E1[0] + Ts1[1] * E1[1] + Ts1[2] * E1[2];
+        const T w0 = __shfl_xor_sync(0xffffffffu, v0, 1);
+        const T w1 = __shfl_xor_sync(0xffffffffu, v1, 1);
+        const bool odd = lane & 1;
+        {
+          const T re = odd ? w0 : v0, im = odd ? v0 : w0;
+          const T fr = I0.fr[ks], fi = I0.fi[ks];
+          atomicAdd(vals + q0 * kVS + lane, odd ? (re * fi + im * fr) : (re * fr - im * fi));
+        }
+        if (two) {
+          const T re = odd ? w1 : v1, im = odd ? v1 : w1;
+          const T fr = I1.fr[ks], fi = I1.fi[ks];
+          atomicAdd(vals + q1 * kVS + lane, odd ? (re * fi + im * fr) : (re * fr - im * fi));
         }
       }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const T v = Ts[a][0] * E[a][0] + Ts[a][1] * E[a][1] + Ts[a][2] * E[a][2];
-      const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
-      if (a >= len) continue;
-      const T re = (lane & 1) ? wv : v, im = (lane & 1) ? v : wv;
-      const T fr = info[o][q[a]].fr[ks], fi = info[o][q[a]].fi[ks];
-      atomicAdd(vals + q[a] * kVS + lane, (lane & 1) ? (re * fi + im * fr) : (re * fr - im * fi));
     }
+    if (lane == 0) w = atomicAdd(&next_task, 1);
+    w = __shfl_sync(0xffffffffu, w, 0);
   }
   __syncthreads();
-  if (t < 32) {
-    vals_to_coefs_col(M, vals + t, kVS);
-    T* out = A.coefs_p + (size_t)pslot * kQ * 32 + t;
-    for (int qq = 0; qq < kQ; ++qq) out[qq * 32] = vals[qq * kVS + t];
-  }
+  vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32);
 }
 
 // ------------------------------------------------------------------ (c) target evaluation
@@ -465,7 +535,7 @@ struct TgtArgs {
   const int* slot_box;
   const int* slot_cone;
   const double* box_center;
-  ConeGeom cg;
+  ConeGeomT<T> cg;
   const T* coefs;
   const double* x_sorted;
   const double* n_sorted;
@@ -500,7 +570,7 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>()) k_target(TgtArgs<T> A) {
   const double x0 = A.x_sorted[3 * (size_t)t], x1 = A.x_sorted[3 * (size_t)t + 1], x2 = A.x_sorted[3 * (size_t)t + 2];
   const T n0 = (T)A.n_sorted[3 * (size_t)t], n1 = (T)A.n_sorted[3 * (size_t)t + 1], n2 = (T)A.n_sorted[3 * (size_t)t + 2];
   const int ks = lane >> 4;
-  const T ds = (T)A.cg.ds(), dth = (T)A.cg.dth(), h = (T)A.cg.h;
+  const T two_ids = T(2) * A.cg.ids, two_idth = T(2) * A.cg.idth, h = A.cg.h;
   TgtScal<T>* S = sc[warp];
   T accS = 0, accD = 0;
   for (int64_t c0 = e0; c0 < e1; c0 += 32) {
@@ -526,10 +596,10 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>()) k_target(TgtArgs<T> A) {
       const T nr = (n0 * xr + n1 * yr + n2 * zr) * ir;
       const T nth = n0 * cth * cph + n1 * cth * sph - n2 * sth;
       const T nph = -n0 * sph + n1 * cph;
-      Q.as = -(h * ir * ir) * nr * (T(2) / ds);
-      Q.at = nth * ir * (T(2) / dth);
+      Q.as = -(h * ir * ir) * nr * two_ids;
+      Q.at = nth * ir * two_idth;
       const T sthg = sth > T(1e-7) ? sth : T(1e-7);
-      Q.ap = nph * ir / sthg * (T(2) / dth);
+      Q.ap = nph * ir / sthg * two_idth;
       // centred factor G = e^{i k r}/(4 pi r) and its normal derivative (n.r_hat)(i k - 1/r) G
       const T g = T(1.0 / (4.0 * kPi)) * ir;
 #pragma unroll
@@ -589,7 +659,7 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
   const T ke = (T)p->desc.k_ext, ki = (T)p->desc.k_int;
   {
     const DevLevel& L = p->dl[D];
-    LeafArgs<T> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, L.cg,
+    LeafArgs<T> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
                   p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki};
     int rec = timer_begin(p, TK_LEAF, s);
     if (L.nboxes > 0) k_leaf<T><<<L.nboxes, kLeafThreads, 0, s>>>(A);
@@ -598,7 +668,7 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
   }
   for (int d = D; d >= 3; --d) {
     const DevLevel& L = p->dl[d];
-    TgtArgs<T> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, L.cg,
+    TgtArgs<T> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
                  (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (T*)p->f28, ke, ki};
     int rec = timer_begin(p, TK_TARGET, s);
     k_target<T><<<(unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), 32 * tgt_warps<T>(), 0, s>>>(B);
@@ -606,12 +676,12 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
     ++p->launches;
     if (d > 3) {
       const DevLevel& Pp = p->dl[d - 1];
-      UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, Pp.cg,
-                  L.cone_map, L.cg.ncones(), L.cg, L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki};
+      UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, cone_geom_t<T>(Pp.cg),
+                  L.cone_map, L.cg.ncones(), cone_geom_t<T>(L.cg), L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki};
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {
         if constexpr (std::is_same<T, float>::value)
-          k_up_grouped<float><<<Pp.nslots, kUpThreads, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_ntask});
+          k_up_runs<<<Pp.nslots, 32 * kUpRunWarps, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_ntask});
         else
           k_up<T><<<Pp.nslots, kUpThreads, 0, s>>>(U);
       }
