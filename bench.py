@@ -119,6 +119,22 @@ def kernel_work(stats):
     }
 
 
+def aggregate_over_ranks(t_local, e2e_local, dist=None, device="cpu"):
+    """Timed-region and end-to-end seconds, max over ranks.  Every rank solves its
+    own problem (replicas, weak scaling); the slowest rank sets the job time."""
+    if dist is None:
+        return float(t_local), float(e2e_local)
+    import torch
+    tt = torch.tensor([t_local, e2e_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt[0]), float(tt[1])
+
+
+def whole_job_value(world, units_per_step, steps, t_max):
+    """Units all ranks processed divided by the job time."""
+    return world * units_per_step * steps / t_max
+
+
 def alu_peak_tflops(sm_mhz):
     # 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -211,15 +227,10 @@ def run_gpu(args):
     ref_plan.close()
     # ---- aggregate over ranks (max time)
     t_step = t_tot / args.steps
-    if dist is not None:
-        tt = torch.tensor([t_tot, max(e2e_times)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_tot, e2e_max = float(tt[0]), float(tt[1])
-    else:
-        e2e_max = max(e2e_times)
+    t_tot, e2e_max = aggregate_over_ranks(t_tot, max(e2e_times), dist, device="cuda")
     units_per_step = 4.0 * N * float(np.mean(iters))
-    value = world * units_per_step * args.steps / t_tot
-    e2e_value = world * 4.0 * N * it_h / e2e_max
+    value = whole_job_value(world, units_per_step, args.steps, t_tot)
+    e2e_value = whole_job_value(world, 4.0 * N * it_h, 1, e2e_max)
     # ---- roofline of the dominant kernel (largest summed time in the timed region)
     work = kernel_work(st)
     per_apply_launch = {"target": st["levels"] - 2, "up": st["levels"] - 3, "leaf": 1, "near": 1}

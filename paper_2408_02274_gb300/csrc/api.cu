@@ -222,6 +222,8 @@ void build(ifgf_plan_t* p) {
     Dl.slot_box = A.upload(L.slot_box);
     Dl.slot_cone = A.upload(L.slot_cone);
     Dl.box_slot_ptr = A.upload(L.box_slot_ptr);
+    for (int b = 0; b < Dl.nboxes; ++b)
+      Dl.max_box_slots = std::max(Dl.max_box_slots, L.box_slot_ptr[b + 1] - L.box_slot_ptr[b]);
     std::vector<int> bp(Dl.nboxes + 1);
     for (int b = 0; b < Dl.nboxes; ++b) bp[b] = L.pt_begin[b];
     bp[Dl.nboxes] = N;

@@ -135,15 +135,18 @@ __device__ void vals_to_coefs_col(const SmallMaps<T>& M, T* v, int st) {
 
 constexpr int kVS = 33;   // padded row stride of the value buffers
 
-// The same transform for all 32 columns of a [75][kVS] value buffer by the whole
-// block (one (line, column) task per thread and pass, consecutive threads on
-// consecutive columns), followed by a coalesced store of the 75 x 32 coefficients.
-// Every thread of the block must call it.
+// The same transform for all 32 columns of `ns` consecutive [75][kStride] value
+// buffers by the whole block (one (buffer, line, column) task per thread and pass,
+// consecutive threads on consecutive columns), followed by a coalesced store of the
+// 75 x 32 coefficients of buffer i to out + i * 75 * 32.  Every thread of the block
+// must call it.
 template <typename T, int kStride>
-__device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* v, T* out) {
+__device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* vb, T* out, int ns = 1) {
   const int nt = blockDim.x;
-  for (int e = threadIdx.x; e < 15 * 32; e += nt) {   // phi lines
-    const int a = e >> 5, col = e & 31;
+  constexpr int kBuf = kQ * kStride;
+  for (int e = threadIdx.x; e < ns * 15 * 32; e += nt) {   // phi lines
+    const int b = e / (15 * 32), r = e - b * 15 * 32, a = r >> 5, col = r & 31;
+    T* v = vb + b * kBuf;
     T t5[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) t5[k] = v[(a * 5 + k) * kStride + col];
@@ -156,8 +159,9 @@ __device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* v, T* out) {
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 15 * 32; e += nt) {   // theta lines
-    const int ik = e >> 5, col = e & 31, is = ik / 5, k = ik % 5;
+  for (int e = threadIdx.x; e < ns * 15 * 32; e += nt) {   // theta lines
+    const int b = e / (15 * 32), r = e - b * 15 * 32, ik = r >> 5, col = r & 31, is = ik / 5, k = ik % 5;
+    T* v = vb + b * kBuf;
     T t5[5];
 #pragma unroll
     for (int j = 0; j < 5; ++j) t5[j] = v[((is * 5 + j) * 5 + k) * kStride + col];
@@ -170,8 +174,9 @@ __device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* v, T* out) {
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 25 * 32; e += nt) {   // s lines
-    const int jk = e >> 5, col = e & 31;
+  for (int e = threadIdx.x; e < ns * 25 * 32; e += nt) {   // s lines
+    const int b = e / (25 * 32), r = e - b * 25 * 32, jk = r >> 5, col = r & 31;
+    T* v = vb + b * kBuf;
     T t3[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) t3[i] = v[(i * 25 + jk) * kStride + col];
@@ -184,12 +189,16 @@ __device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* v, T* out) {
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kQ * 32; e += nt) out[e] = v[(e >> 5) * kStride + (e & 31)];
+  for (int e = threadIdx.x; e < ns * kQ * 32; e += nt) {
+    const int b = e / (kQ * 32), r = e - b * kQ * 32;
+    out[e] = vb[b * kBuf + (r >> 5) * kStride + (r & 31)];
+  }
 }
 
 // ------------------------------------------------------------------ (a) leaf direct
 constexpr int kLeafThreads = 160;   // two cone segments (2 x 75 points) per pass
 constexpr int kLeafChunk = 256;     // sources staged per pass
+constexpr int kLeafSlots = 8;       // cone segments of one box per block (grid.y splits a box)
 
 template <typename T>
 struct LeafArgs {
@@ -207,20 +216,38 @@ struct LeafArgs {
 template <typename T>
 __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
   __shared__ SmallMaps<T> M;
-  // source staging and the value buffer are never live at the same time: alias them
+  // FP32: the staged sources and the value buffer have separate space, so a box's
+  // sources are staged once; FP64 (which would need more than 48 KB) aliases them and
+  // restages per pass.
+  constexpr bool kSep = sizeof(T) == 4;
   constexpr int kSrcWords = kLeafChunk * 20, kValWords = 2 * kQ * kVS;
-  __shared__ T pool[kSrcWords > kValWords ? kSrcWords : kValWords];
+  __shared__ T pool[kSep ? kSrcWords + kValWords : (kSrcWords > kValWords ? kSrcWords : kValWords)];
   T (*src)[4] = reinterpret_cast<T (*)[4]>(pool);
   T (*sa)[16] = reinterpret_cast<T (*)[16]>(pool + kLeafChunk * 4);
-  T* vbuf = pool;
+  T* vbuf = pool + (kSep ? kSrcWords : 0);
   const int box = blockIdx.x;
   const int t = threadIdx.x;
+  const int sb = A.box_slot_ptr[box] + blockIdx.y * kLeafSlots;
+  const int se = min(A.box_slot_ptr[box + 1], sb + kLeafSlots);
+  if (sb >= se) return;   // the box has fewer segments than this block's range (uniform per block)
   init_maps(M);
   const double c0 = A.box_center[3 * box], c1 = A.box_center[3 * box + 1], c2 = A.box_center[3 * box + 2];
   const int pb = A.box_pt_ptr[box], pe = A.box_pt_ptr[box + 1];
-  const int sb = A.box_slot_ptr[box], se = A.box_slot_ptr[box + 1];
   const int nsrc = pe - pb;
+  const bool staged_once = kSep && nsrc <= kLeafChunk;   // the usual case for FP32
   const T kk[2] = {A.ke, A.ki};
+  auto stage = [&](int cb, int nchunk) {
+    for (int e = t; e < nchunk; e += blockDim.x) {
+      const int m = pb + cb + e;
+      T y0 = (T)(A.x_sorted[3 * (size_t)m] - c0);
+      T y1 = (T)(A.x_sorted[3 * (size_t)m + 1] - c1);
+      T y2 = (T)(A.x_sorted[3 * (size_t)m + 2] - c2);
+      src[e][0] = y0; src[e][1] = y1; src[e][2] = y2;
+      src[e][3] = y0 * y0 + y1 * y1 + y2 * y2;
+      for (int k = 0; k < 16; ++k) sa[e][k] = A.a_sorted[16 * (size_t)m + k];
+    }
+  };
+  if (staged_once) stage(0, nsrc);
   for (int s0 = sb; s0 < se; s0 += 2) {
     const int sl = t / kQ, q = t % kQ;
     const int slot = s0 + sl;
@@ -236,17 +263,11 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
     for (int k = 0; k < 32; ++k) acc[k] = 0;
     for (int cb = 0; cb < nsrc; cb += kLeafChunk) {
       const int nchunk = min(kLeafChunk, nsrc - cb);
-      __syncthreads();
-      for (int e = t; e < nchunk; e += blockDim.x) {
-        const int m = pb + cb + e;
-        T y0 = (T)(A.x_sorted[3 * (size_t)m] - c0);
-        T y1 = (T)(A.x_sorted[3 * (size_t)m + 1] - c1);
-        T y2 = (T)(A.x_sorted[3 * (size_t)m + 2] - c2);
-        src[e][0] = y0; src[e][1] = y1; src[e][2] = y2;
-        src[e][3] = y0 * y0 + y1 * y1 + y2 * y2;
-        for (int k = 0; k < 16; ++k) sa[e][k] = A.a_sorted[16 * (size_t)m + k];
+      if (!staged_once) {
+        __syncthreads();
+        stage(cb, nchunk);
+        __syncthreads();
       }
-      __syncthreads();
       if (act) {
         for (int e = 0; e < nchunk; ++e) {
           // g_S(X, y) = (r/|X-y|) exp(i k (|X-y| - r)), |X-y| - r = (|y|^2 - 2 X.y)/(|X-y| + r)
@@ -269,19 +290,11 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
         }
       }
     }
-    __syncthreads();
+    if (!kSep) __syncthreads();   // the value buffer overlays the staged sources
     if (act)
       for (int k = 0; k < 32; ++k) vbuf[(sl * kQ + q) * kVS + k] = acc[k];
     __syncthreads();
-    if (t < 64) {
-      const int s2 = t / 32, col = t % 32;
-      if (s0 + s2 < se) {
-        T* v = vbuf + s2 * kQ * kVS + col;
-        vals_to_coefs_col(M, v, kVS);
-        T* out = A.coefs + (size_t)(s0 + s2) * kQ * 32 + col;
-        for (int qq = 0; qq < kQ; ++qq) out[qq * 32] = v[qq * kVS];
-      }
-    }
+    vals_to_coefs_block<T, kVS>(M, vbuf, A.coefs + (size_t)s0 * kQ * 32, min(2, se - s0));
   }
 }
 
@@ -619,21 +632,37 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>()) k_target(TgtArgs<T> A) {
     for (int cI = 0; cI < nc; ++cI) {
       const TgtScal<T>& Q = S[cI];
       const T* C = A.coefs + (size_t)Q.slot * kQ * 32 + lane;
-      T F = 0, dF = 0;
+      // separable contraction: the phi sums with T and T' are shared by F and its three
+      // partial derivatives, dF = a_s F_s + a_theta F_theta + a_phi F_phi
+      T Tp[5], dTp[5], Tt[5], dTt[5];
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 5; ++k) {
+        Tp[k] = Q.Tp[k]; dTp[k] = Q.dTp[k]; Tt[k] = Q.Tt[k]; dTt[k] = Q.dTt[k];
+      }
+      T Fs[3], Ft[3], Fp[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        Fs[i] = Ft[i] = Fp[i] = T(0);
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-          const T b = Q.Ts[i] * Q.Tt[j];
-          const T p1 = Q.as * Q.dTs[i] * Q.Tt[j] + Q.at * Q.Ts[i] * Q.dTt[j];
-          const T p2 = Q.ap * b;
+          T c[5];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            const T c = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
-            F += b * Q.Tp[k] * c;
-            dF += (p1 * Q.Tp[k] + p2 * Q.dTp[k]) * c;
+          for (int k = 0; k < 5; ++k) c[k] = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
+          T d = Tp[0] * c[0], e = dTp[0] * c[0];
+#pragma unroll
+          for (int k = 1; k < 5; ++k) {
+            d += Tp[k] * c[k];
+            e += dTp[k] * c[k];
           }
+          Fs[i] += Tt[j] * d;    // -> F and dF/d(ts)
+          Ft[i] += dTt[j] * d;   // -> dF/d(tt)
+          Fp[i] += Tt[j] * e;    // -> dF/d(tp)
         }
+      }
+      const T F = Q.Ts[0] * Fs[0] + Q.Ts[1] * Fs[1] + Q.Ts[2] * Fs[2];
+      const T dF = Q.as * (Q.dTs[0] * Fs[0] + Q.dTs[1] * Fs[1] + Q.dTs[2] * Fs[2]) +
+                   Q.at * (Q.Ts[0] * Ft[0] + Q.Ts[1] * Ft[1] + Q.Ts[2] * Ft[2]) +
+                   Q.ap * (Q.Ts[0] * Fp[0] + Q.Ts[1] * Fp[1] + Q.Ts[2] * Fp[2]);
       const T Gr = Q.G[ks][0], Gi = Q.G[ks][1], dGr = Q.G[ks][2], dGi = Q.G[ks][3];
       const T Fw = __shfl_xor_sync(0xffffffffu, F, 1);
       const T dFw = __shfl_xor_sync(0xffffffffu, dF, 1);
@@ -662,7 +691,10 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
     LeafArgs<T> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
                   p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki};
     int rec = timer_begin(p, TK_LEAF, s);
-    if (L.nboxes > 0) k_leaf<T><<<L.nboxes, kLeafThreads, 0, s>>>(A);
+    if (L.nboxes > 0 && L.max_box_slots > 0) {
+      const dim3 grid((unsigned)L.nboxes, (unsigned)((L.max_box_slots + kLeafSlots - 1) / kLeafSlots));
+      k_leaf<T><<<grid, kLeafThreads, 0, s>>>(A);
+    }
     timer_end(p, rec, s);
     ++p->launches;
   }

@@ -56,6 +56,7 @@ struct HostTree {
 // ------------------------------------------------------------------ device level tables
 struct DevLevel {
   int d = 0, nboxes = 0, nslots = 0;
+  int max_box_slots = 0;          // largest number of relevant cones of one box
   ConeGeom cg{};
   double H = 0;
   double* box_center = nullptr;   // [nboxes][3]
