@@ -572,7 +572,7 @@ template <typename T>
 __host__ __device__ constexpr int tgt_warps() { return sizeof(T) == 4 ? 8 : 4; }   // keeps the scalars under 48 KB
 
 template <typename T>
-__global__ void __launch_bounds__(32 * tgt_warps<T>()) k_target(TgtArgs<T> A) {
+__global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T> A) {
   __shared__ TgtScal<T> sc[tgt_warps<T>()][32];
   const int warp = threadIdx.x >> 5;
   const int t = blockIdx.x * tgt_warps<T>() + warp;
@@ -639,15 +639,17 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>()) k_target(TgtArgs<T> A) {
       for (int k = 0; k < 5; ++k) {
         Tp[k] = Q.Tp[k]; dTp[k] = Q.dTp[k]; Tt[k] = Q.Tt[k]; dTt[k] = Q.dTt[k];
       }
+      // all 75 coefficient loads are issued before the arithmetic: one round trip per pair
+      T cc[kQ];
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) cc[k] = __ldg(C + k * 32);
       T Fs[3], Ft[3], Fp[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         Fs[i] = Ft[i] = Fp[i] = T(0);
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-          T c[5];
-#pragma unroll
-          for (int k = 0; k < 5; ++k) c[k] = __ldg(C + ((i * 5 + j) * 5 + k) * 32);
+          const T* c = cc + (i * 5 + j) * 5;
           T d = Tp[0] * c[0], e = dTp[0] * c[0];
 #pragma unroll
           for (int k = 1; k < 5; ++k) {
