@@ -36,11 +36,15 @@ __global__ void k_rhs(int N, const double* __restrict__ inc, NodeGeom g, double 
   }
 }
 
-// part[blk][j] = sum over this block's chunk of conj(V_j) w, j = 0..k (complex)
+// part[chunk][j] = sum over the chunk of conj(V_j) w for j = 0..k1-1 (complex).  Grid:
+// (chunks of kDotThreads * kDotItems elements) x (groups of kDotJ vectors); w is read once
+// per block and the kDotJ sums are reduced together.
+constexpr int kDotJ = 8;
 __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const double* __restrict__ V,
                                                       const double* __restrict__ w, double* __restrict__ part) {
-  __shared__ double red[kDotThreads / 32][2];
+  __shared__ double red[kDotThreads / 32][2 * kDotJ];
   const int64_t base = (int64_t)blockIdx.x * kDotThreads * kDotItems;
+  const int j0 = blockIdx.y * kDotJ;
   double wr[kDotItems], wi[kDotItems];
   int64_t idx[kDotItems];
 #pragma unroll
@@ -49,35 +53,38 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const d
     wr[it] = idx[it] < n ? w[2 * idx[it]] : 0.0;
     wi[it] = idx[it] < n ? w[2 * idx[it] + 1] : 0.0;
   }
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int j = 0; j < k1; ++j) {
-    const double* v = V + 2 * (size_t)j * n;
-    double ar = 0, ai = 0;
+  double acc[2 * kDotJ];
 #pragma unroll
-    for (int it = 0; it < kDotItems; ++it)
-      if (idx[it] < n) {
-        double vr = v[2 * idx[it]], vi = v[2 * idx[it] + 1];
-        ar += vr * wr[it] + vi * wi[it];
-        ai += vr * wi[it] - vi * wr[it];
-      }
-    for (int o = 16; o > 0; o >>= 1) {
-      ar += __shfl_xor_sync(0xffffffffu, ar, o);
-      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+  for (int jj = 0; jj < kDotJ; ++jj) {
+    double ar = 0, ai = 0;
+    const int j = j0 + jj;
+    if (j < k1) {
+      const double* v = V + 2 * (size_t)j * n;
+#pragma unroll
+      for (int it = 0; it < kDotItems; ++it)
+        if (idx[it] < n) {
+          const double vr = v[2 * idx[it]], vi = v[2 * idx[it] + 1];
+          ar += vr * wr[it] + vi * wi[it];
+          ai += vr * wi[it] - vi * wr[it];
+        }
     }
-    __syncthreads();
-    if (lane == 0) {
-      red[warp][0] = ar;
-      red[warp][1] = ai;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double sr = 0, si = 0;
-      for (int q = 0; q < kDotThreads / 32; ++q) {
-        sr += red[q][0];
-        si += red[q][1];
-      }
-      part[2 * ((size_t)blockIdx.x * k1 + j)] = sr;
-      part[2 * ((size_t)blockIdx.x * k1 + j) + 1] = si;
+    acc[2 * jj] = ar;
+    acc[2 * jj + 1] = ai;
+  }
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+  for (int q = 0; q < 2 * kDotJ; ++q)
+    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 2 * kDotJ; ++q) red[warp][q] = acc[q];
+  __syncthreads();
+  if (threadIdx.x < 2 * kDotJ) {
+    const int q = threadIdx.x, j = j0 + q / 2;
+    if (j < k1) {
+      double sum = 0;
+      for (int ww = 0; ww < kDotThreads / 32; ++ww) sum += red[ww][q];
+      part[2 * ((size_t)blockIdx.x * k1 + j) + (q & 1)] = sum;
     }
   }
 }
@@ -221,7 +228,7 @@ int dots_blocks(int64_t n) { return (int)((n + kDotThreads * kDotItems - 1) / (k
 static cudaError_t project(GmresWork& G, int64_t n, int k1, double* hpass, double* htot, int first,
                            cudaStream_t s) {
   int nb = dots_blocks(n);
-  k_dots<<<nb, kDotThreads, 0, s>>>(n, k1, G.V, G.w, G.part);
+  k_dots<<<dim3(nb, (k1 + kDotJ - 1) / kDotJ), kDotThreads, 0, s>>>(n, k1, G.V, G.w, G.part);
   k_reduce_parts<<<(k1 + 127) / 128, 128, 0, s>>>(nb, k1, G.part, hpass, 0);
   k_combo<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, k1, G.V, hpass, G.w, 0);
   k_reduce_parts<<<(k1 + 127) / 128, 128, 0, s>>>(nb, k1, G.part, htot, first ? 0 : 1);

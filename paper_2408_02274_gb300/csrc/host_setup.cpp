@@ -229,26 +229,33 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
         }
       }
       // per (parent cone, octant): the points ranked by the child cone they fall in, and
-      // runs of at most kUpRunMax consecutive ranked points that share one child cone
+      // runs of at most kUpRunMax consecutive ranked points that share one child cone;
+      // per parent cone, the runs of all eight octants sorted longest first (the warps
+      // of a block take them in this order), each as start | len << 8 | octant << 16
       Pp.up_order.assign((size_t)ncomp * 8 * kQ, 0);
       Pp.up_task.assign((size_t)ncomp * 8 * kQ, 0);
-      Pp.up_ntask.assign((size_t)ncomp * 8, 0);
-      for (size_t g = 0; g < (size_t)ncomp * 8; ++g) {
-        const int32_t* cc = &Pp.up_cc[g * kQ];
-        int32_t* ord = &Pp.up_order[g * kQ];
-        for (int q = 0; q < kQ; ++q) ord[q] = q;
-        std::stable_sort(ord, ord + kQ, [&](int a, int b) { return cc[a] < cc[b]; });
-        int n = 0, r = 0;
-        while (r < kQ) {
-          int len = 1;
-          while (len < kUpRunMax && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
-          Pp.up_task[g * kQ + n++] = r | (len << 8);
-          r += len;
+      Pp.up_ntask.assign((size_t)ncomp, 0);
+      std::vector<int32_t> runs;
+      for (size_t ci = 0; ci < (size_t)ncomp; ++ci) {
+        runs.clear();
+        for (int o = 0; o < 8; ++o) {
+          const size_t g = ci * 8 + o;
+          const int32_t* cc = &Pp.up_cc[g * kQ];
+          int32_t* ord = &Pp.up_order[g * kQ];
+          for (int q = 0; q < kQ; ++q) ord[q] = q;
+          std::stable_sort(ord, ord + kQ, [&](int a, int b) { return cc[a] < cc[b]; });
+          int r = 0;
+          while (r < kQ) {
+            int len = 1;
+            while (len < kUpRunMax && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
+            runs.push_back(r | (len << 8) | (o << 16));
+            r += len;
+          }
         }
-        // longest runs first: the warps of a block take runs in this order
-        std::stable_sort(&Pp.up_task[g * kQ], &Pp.up_task[g * kQ] + n,
-                         [](int32_t a, int32_t b) { return (a >> 8) > (b >> 8); });
-        Pp.up_ntask[g] = n;
+        std::stable_sort(runs.begin(), runs.end(),
+                         [](int32_t a, int32_t b) { return ((a >> 8) & 255) > ((b >> 8) & 255); });
+        std::copy(runs.begin(), runs.end(), Pp.up_task.begin() + ci * 8 * kQ);
+        Pp.up_ntask[ci] = (int32_t)runs.size();
       }
       for (int b = 0; b < nb; ++b) {
         int p = L.parent[b];

@@ -407,8 +407,8 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
 // conflicts within a warp).
 struct RunTabs {
   const int* order;   // [ncompact][8][75] points ranked by child cone
-  const int* task;    // [ncompact][8][75] run start | (length << 8)
-  const int* ntask;   // [ncompact][8]
+  const int* task;    // [ncompact][8 * 75] runs, longest first: start | len << 8 | octant << 16
+  const int* ntask;   // [ncompact] runs over all octants
 };
 
 template <typename T>
@@ -426,21 +426,12 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
   __shared__ T Xp[kQ][3];
   __shared__ PtInfo2<T> info[8][kQ];
   __shared__ T vals[kQ * kVS];
-  __shared__ int tstart[9];
   __shared__ int next_task;
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
   init_maps(M);
   const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
-  if (t == 0) {
-    int acc = 0;
-    for (int o = 0; o < 8; ++o) {
-      tstart[o] = acc;
-      if (A.child[8 * P + o] >= 0) acc += RT.ntask[(size_t)ci * 8 + o];
-    }
-    tstart[8] = acc;
-    next_task = kUpRunWarps;
-  }
+  if (t == 0) next_task = kUpRunWarps;
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
   for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
@@ -469,18 +460,18 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
     }
   }
   __syncthreads();
-  const int ntot = tstart[8];
+  const int ntot = RT.ntask[ci];
   const int ks = lane >> 4;   // columns 0..15 belong to kernel e, 16..31 to kernel i
-  // runs are taken dynamically (each octant's list is sorted longest first)
+  // runs are taken dynamically, longest first over all octants; runs of absent children
+  // are skipped
   for (int w = warp; w < ntot;) {
-    int o = 0;
-    while (w >= tstart[o + 1]) ++o;
+    const int tk = __ldg(RT.task + (size_t)ci * 8 * kQ + w);
+    const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
     const size_t g = (size_t)ci * 8 + o;
-    const int tk = __ldg(RT.task + g * kQ + (w - tstart[o]));
-    const int r0 = tk & 255, len = tk >> 8;
-    const int myq = (lane < len) ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
-    const int cslot = info[o][__shfl_sync(0xffffffffu, myq, 0)].cslot;
-    if (cslot >= 0) {   // always: the host marked every such cone relevant
+    const bool have = A.child[8 * P + o] >= 0;
+    const int myq = (have && lane < len) ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
+    const int cslot = have ? info[o][__shfl_sync(0xffffffffu, myq, 0)].cslot : -1;
+    if (cslot >= 0) {   // always, for a present child: the host marked every such cone relevant
       const T* C = A.coefs_c + (size_t)cslot * kQ * 32 + lane;
       T c[kQ];
 #pragma unroll

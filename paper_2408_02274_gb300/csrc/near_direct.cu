@@ -21,9 +21,40 @@ __device__ inline T warp_sum(T v) {
   return v;
 }
 
-template <typename T, typename VT>
+// n values of type T from a 16-byte aligned address as 16-byte vector loads
+template <typename T, int n>
+__device__ __forceinline__ void ldg_vec(const T* __restrict__ src, T* dst) {
+  static_assert((n * sizeof(T)) % 16 == 0, "whole 16-byte vectors");
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < (int)(n * sizeof(T) / 16); ++i) d4[i] = __ldg(s4 + i);
+}
+
+template <typename T>
+__device__ __forceinline__ void near_madd(const T* w, const T* ph, T* acc) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T wr = w[2 * s], wi = w[2 * s + 1];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      acc[2 * (8 * s + k)] += wr * ph[2 * k] - wi * ph[2 * k + 1];
+      acc[2 * (8 * s + k) + 1] += wr * ph[2 * k + 1] + wi * ph[2 * k];
+    }
+    const T dr = w[4 + 2 * s], di = w[4 + 2 * s + 1];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      acc[2 * (16 + 6 * s + k)] += dr * ph[2 * k] - di * ph[2 * k + 1];
+      acc[2 * (16 + 6 * s + k) + 1] += dr * ph[2 * k + 1] + di * ph[2 * k];
+    }
+  }
+}
+
+// One warp per target row; each lane takes two nonzeros per step with independent
+// loads (column, weights, gathered densities) so that more of them are in flight.
+template <typename T>
 __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__ row_ptr,
-                                              const int* __restrict__ col, const VT* __restrict__ val,
+                                              const int* __restrict__ col, const T* __restrict__ val,
                                               const T* __restrict__ phi, T* __restrict__ f28) {
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -32,29 +63,23 @@ __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__
 #pragma unroll
   for (int k = 0; k < 56; ++k) acc[k] = T(0);
   const int64_t e0 = row_ptr[row], e1 = row_ptr[row + 1];
-  for (int64_t e = e0 + lane; e < e1; e += 32) {
-    const int m = __ldg(col + e);
-    T w[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = (T)__ldg(val + 8 * e + k);
-    T ph[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) ph[k] = __ldg(phi + 16 * (size_t)m + k);
-#pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      const T wr = w[2 * s], wi = w[2 * s + 1];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        acc[2 * (8 * s + k)] += wr * ph[2 * k] - wi * ph[2 * k + 1];
-        acc[2 * (8 * s + k) + 1] += wr * ph[2 * k + 1] + wi * ph[2 * k];
-      }
-      const T dr = w[4 + 2 * s], di = w[4 + 2 * s + 1];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        acc[2 * (16 + 6 * s + k)] += dr * ph[2 * k] - di * ph[2 * k + 1];
-        acc[2 * (16 + 6 * s + k) + 1] += dr * ph[2 * k + 1] + di * ph[2 * k];
-      }
-    }
+  int64_t e = e0 + lane;
+  for (; e + 32 < e1; e += 64) {
+    const int m0 = __ldg(col + e), m1 = __ldg(col + e + 32);
+    alignas(16) T w0[8], w1[8], p0[16], p1[16];
+    ldg_vec<T, 8>(val + 8 * e, w0);
+    ldg_vec<T, 8>(val + 8 * (e + 32), w1);
+    ldg_vec<T, 16>(phi + 16 * (size_t)m0, p0);
+    ldg_vec<T, 16>(phi + 16 * (size_t)m1, p1);
+    near_madd(w0, p0, acc);
+    near_madd(w1, p1, acc);
+  }
+  if (e < e1) {
+    const int m0 = __ldg(col + e);
+    alignas(16) T w0[8], p0[16];
+    ldg_vec<T, 8>(val + 8 * e, w0);
+    ldg_vec<T, 16>(phi + 16 * (size_t)m0, p0);
+    near_madd(w0, p0, acc);
   }
 #pragma unroll
   for (int k = 0; k < 56; ++k) acc[k] = warp_sum(acc[k]);
@@ -144,10 +169,10 @@ cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s) {
   const int threads = 256;
   const unsigned blocks = (unsigned)(((size_t)p->N * 32 + threads - 1) / threads);
   if (p->desc.precision == IFGF_FP64)
-    k_near<double, double><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
+    k_near<double><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
         p->near.val64, (const double*)p->phi, (double*)p->f28);
   else
-    k_near<float, float><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
+    k_near<float><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
         p->near.val32, (const float*)p->phi, (float*)p->f28);
   return cudaGetLastError();
 }
