@@ -95,6 +95,90 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# sources whose change invalidates a recorded DRAM traffic figure of the IFGF kernels
+KERNEL_SOURCES = ("paper_2408_02274_gb300/csrc/ifgf.cu", "paper_2408_02274_gb300/csrc/common.cuh",
+                  "paper_2408_02274_gb300/csrc/host_setup.cpp")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary
+    profiles/dram_traffic.json, or None when the kernel sources changed since the
+    counters were taken or no record exists for this workload."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kernel)
+    if not rec or rec.get("workload") != workload or rec.get("source_sha256") != kernel_source_hash():
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+def cpu_info():
+    """CPU model, affinity and thread count of the host the CPU baseline runs on."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        model = platform.processor() or platform.machine()
+    aff = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
+    return {"cpu_model": model, "machine": platform.machine(), "nproc": os.cpu_count(),
+            "affinity": f"{len(aff)} cpus" + (f" ({aff[0]}..{aff[-1]})" if aff else ""),
+            "omp_threads": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))}
+
+
+def graph_apply_throughput(plan, N, flush, reps=20, warm=3):
+    """Forward-map throughput as 4N / t_apply, t_apply the median of `reps` CUDA-graph
+    replays of one ifgf_apply (timed with events on the replay stream, L2 flushed
+    between replays outside the events)."""
+    import torch
+    rng = np.random.default_rng(5)
+    y = torch.from_numpy(np.ascontiguousarray(
+        (rng.standard_normal((4, N)) + 1j * rng.standard_normal((4, N))) / np.sqrt(2))).cuda()
+    out = torch.empty_like(y)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warm):
+            plan.apply(y, out)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.apply(y, out)
+    for _ in range(warm):
+        graph.replay()
+    torch.cuda.synchronize()
+    ts = []
+    stream = torch.cuda.current_stream()
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    t = float(np.median(ts)) / 1e3
+    return {"value": 4.0 * N / t, "unit": UNIT, "t_apply_ms_median": 1e3 * t, "replays": reps, "graph": True}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -211,6 +295,8 @@ def run_gpu(args):
         it_h, _, _ = plan.solve(inc_h.numpy(), y_h.numpy(), tol=tol, max_iter=400)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
+    # ---- forward map alone, graph-replayed (median of 20)
+    apply_tp = graph_apply_throughput(plan, N, flush)
     # ---- accuracy of the timed path: one IFGF FP32 matvec vs the plain FP64 direct path
     yv = torch.from_numpy(np.ascontiguousarray(
         (np.random.default_rng(7).standard_normal((4, N)) + 1j * np.random.default_rng(8).standard_normal((4, N)))
@@ -250,9 +336,11 @@ def run_gpu(args):
         achieved = per_launch / (dom_ms / dom_calls / 1e3) / 1e12
         peak = alu_peak_tflops(sm_mhz)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": recorded_traffic("k_up_runs", args.workload) if dom == "up" else None,
                 "peak_source": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled)"}
-    roof["kernel"] = {"target": "k_target (c)", "up": "k_up (b)", "leaf": "k_leaf (a)", "near": "k_near (d)"}[dom]
+    roof["kernel"] = {"target": "k_target (c)", "up": "k_up_runs (b)", "leaf": "k_leaf (a)", "near": "k_near (d)"}[dom]
+    if roof["traffic"] is not None:
+        roof["traffic_source"] = "profiles/dram_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
@@ -265,12 +353,14 @@ def run_gpu(args):
         "matvec_rel_err_vs_direct": matvec_err,
         "matvec_err_reference": "plain direct far sum, FP64" if prob.n <= 20000 else "plain direct far sum, FP32",
         "stage_ms_per_apply": {k: ktime[k][0] / max(napply, 1) for k in ktime},
+        "apply_throughput": apply_tp,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * N * 16,
                 "d2h_bytes_per_step": 4 * N * 16},
         "gpu_launches": int(launches),
         "clocks": clk,
         "plan": {"near_nnz": st["near_nnz"], "cones": st["cones"], "interactions": st["interactions"],
+                 "up_pairs": st["up_pairs"], "leaf_pairs": st["leaf_pairs"],
                  "setup_s": st["setup_seconds"], "device_bytes": st["device_bytes"]},
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -309,7 +399,7 @@ def cpu_baseline(prob, delta, budget_s=15.0, reference_units=False):
     dt = time.perf_counter() - t0
     t_full = dt * prob.n / rows_done
     return {"value": 4.0 * prob.n / t_full, "unit": UNIT, "cores": int(_os.environ.get("OMP_NUM_THREADS", cores)),
-            "kind": "oracle",
+            "kind": "oracle", "host": cpu_info(),
             "sample": f"{p} of {prob.num_patches} patches ({rows_done} target rows) of the FP64 CBIE forward map "
                       f"(kernel rows with singular moments + sums), {dt:.1f} s; full matvec extrapolated "
                       f"to {t_full:.1f} s"}
@@ -367,7 +457,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": timed[0]["cores"], "kind": "oracle",
-                             "sample": timed[0]["sample"]},
+                             "sample": timed[0]["sample"], "host": timed[0]["host"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

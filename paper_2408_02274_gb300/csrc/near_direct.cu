@@ -50,7 +50,7 @@ __device__ __forceinline__ void near_madd(const T* w, const T* ph, T* acc) {
   }
 }
 
-// One warp per target row; each lane takes two nonzeros per step with independent
+// One warp per target row; each lane takes two nonzeros per step (FP32) with independent
 // loads (column, weights, gathered densities) so that more of them are in flight.
 template <typename T>
 __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__ row_ptr,
@@ -64,7 +64,9 @@ __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__
   for (int k = 0; k < 56; ++k) acc[k] = T(0);
   const int64_t e0 = row_ptr[row], e1 = row_ptr[row + 1];
   int64_t e = e0 + lane;
-  for (; e + 32 < e1; e += 64) {
+  // FP32: two nonzeros per step; FP64 (twice the registers per nonzero) takes one
+  constexpr bool kTwo = sizeof(T) == 4;
+  for (; kTwo && e + 32 < e1; e += 64) {
     const int m0 = __ldg(col + e), m1 = __ldg(col + e + 32);
     alignas(16) T w0[8], w1[8], p0[16], p1[16];
     ldg_vec<T, 8>(val + 8 * e, w0);
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__
     near_madd(w0, p0, acc);
     near_madd(w1, p1, acc);
   }
-  if (e < e1) {
+  for (; e < e1; e += 32) {
     const int m0 = __ldg(col + e);
     alignas(16) T w0[8], p0[16];
     ldg_vec<T, 8>(val + 8 * e, w0);
