@@ -236,7 +236,7 @@ void build(ifgf_plan_t* p) {
     Dl.up_cc = A.upload(L.up_cc);
     Dl.up_order = A.upload(L.up_order);
     Dl.up_task = A.upload(L.up_task);
-    Dl.up_ntask = A.upload(L.up_ntask);
+    Dl.up_task_ptr = A.upload(L.up_task_ptr);
     Dl.tgt_ptr = A.upload(L.tgt_ptr);
     Dl.tgt_slot = A.upload(L.tgt_slot);
     Dl.ninter = (int64_t)L.tgt_slot.size();

@@ -16,6 +16,7 @@ constexpr int kF = 16;                            // complex fields carried by t
 constexpr int kFR = 2 * kF;                       // real components (re, im interleaved)
 constexpr int kNearFields = 28;                   // S_e[8], S_i[8], D_e[6], D_i[6]
 constexpr int kUpRunMax = 32;                     // parent points per upward-pass run (<= 32: one per lane)
+constexpr int kUpGroups = 4;                      // disjoint parent-point groups, one per warp of the upward block
 
 // Complex helpers on plain real pairs (the library keeps complex data interleaved).
 template <typename T>

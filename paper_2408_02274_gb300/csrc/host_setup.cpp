@@ -58,6 +58,14 @@ void interp_point(const ConeGeom& cg, int cone, int q, double* X) {
   X[2] = r * std::cos(th);
 }
 
+// Group (0 .. kUpGroups-1) of interpolation point q = (is * 5 + it) * 5 + ip: the 25 angular
+// positions (it, ip) in snake order (ip reversed on odd it), cut into chunks of 6, 6, 6, 7.
+static int up_group(int q) {
+  const int a = q % (kPa * kPa), it = a / kPa, ip = a % kPa;
+  const int sidx = it * kPa + ((it & 1) ? kPa - 1 - ip : ip);
+  return sidx < 6 ? 0 : (sidx < 12 ? 1 : (sidx < 18 ? 2 : 3));
+}
+
 static void box_center(const HostTree& t, int d, const std::array<int, 3>& ic, double* c) {
   double H = t.lv[d].H;
   for (int a = 0; a < 3; ++a) c[a] = t.corner[a] + H * (ic[a] + 0.5);
@@ -228,34 +236,45 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           }
         }
       }
-      // per (parent cone, octant): the points ranked by the child cone they fall in, and
-      // runs of at most kUpRunMax consecutive ranked points that share one child cone;
-      // per parent cone, the runs of all eight octants sorted longest first (the warps
-      // of a block take them in this order), each as start | len << 8 | octant << 16
+      // The 75 points of a parent cone are split into kUpGroups fixed groups, one per warp
+      // of the upward block: contiguous chunks of the 5 x 5 angular grid in snake order
+      // (all three radial points of an angular position together), so a group's points
+      // fall in few child cones.  A warp only ever adds into its own group's points, for
+      // every octant, so no two warps write the same parent value.  Per (parent cone,
+      // octant) the points are ranked by (group, child cone); per (parent cone, group) the
+      // runs of at most kUpRunMax consecutive ranked points that share one child cone, over
+      // all octants, are listed longest first as start | len << 8 | octant << 16.
       Pp.up_order.assign((size_t)ncomp * 8 * kQ, 0);
-      Pp.up_task.assign((size_t)ncomp * 8 * kQ, 0);
-      Pp.up_ntask.assign((size_t)ncomp, 0);
-      std::vector<int32_t> runs;
+      Pp.up_task.clear();
+      Pp.up_task_ptr.assign((size_t)ncomp * kUpGroups + 1, 0);
+      std::vector<int32_t> runs[kUpGroups];
       for (size_t ci = 0; ci < (size_t)ncomp; ++ci) {
-        runs.clear();
+        for (auto& r : runs) r.clear();
         for (int o = 0; o < 8; ++o) {
           const size_t g = ci * 8 + o;
           const int32_t* cc = &Pp.up_cc[g * kQ];
           int32_t* ord = &Pp.up_order[g * kQ];
           for (int q = 0; q < kQ; ++q) ord[q] = q;
-          std::stable_sort(ord, ord + kQ, [&](int a, int b) { return cc[a] < cc[b]; });
+          std::stable_sort(ord, ord + kQ, [&](int a, int b) {
+            const int ga = up_group(a), gb = up_group(b);
+            return ga != gb ? ga < gb : cc[a] < cc[b];
+          });
           int r = 0;
           while (r < kQ) {
+            const int w = up_group(ord[r]);
             int len = 1;
-            while (len < kUpRunMax && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
-            runs.push_back(r | (len << 8) | (o << 16));
+            while (len < kUpRunMax && r + len < kQ && up_group(ord[r + len]) == w && cc[ord[r + len]] == cc[ord[r]])
+              ++len;
+            runs[w].push_back(r | (len << 8) | (o << 16));
             r += len;
           }
         }
-        std::stable_sort(runs.begin(), runs.end(),
-                         [](int32_t a, int32_t b) { return ((a >> 8) & 255) > ((b >> 8) & 255); });
-        std::copy(runs.begin(), runs.end(), Pp.up_task.begin() + ci * 8 * kQ);
-        Pp.up_ntask[ci] = (int32_t)runs.size();
+        for (int w = 0; w < kUpGroups; ++w) {
+          std::stable_sort(runs[w].begin(), runs[w].end(),
+                           [](int32_t a, int32_t b) { return ((a >> 8) & 255) > ((b >> 8) & 255); });
+          Pp.up_task.insert(Pp.up_task.end(), runs[w].begin(), runs[w].end());
+          Pp.up_task_ptr[ci * kUpGroups + w + 1] = (int32_t)Pp.up_task.size();
+        }
       }
       for (int b = 0; b < nb; ++b) {
         int p = L.parent[b];

@@ -406,9 +406,9 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
 // values with shared-memory atomics (one column per lane, so no bank
 // conflicts within a warp).
 struct RunTabs {
-  const int* order;   // [ncompact][8][75] points ranked by child cone
-  const int* task;    // [ncompact][8 * 75] runs, longest first: start | len << 8 | octant << 16
-  const int* ntask;   // [ncompact] runs over all octants
+  const int* order;      // [ncompact][8][75] points ranked by (group, child cone)
+  const int* task;       // runs per (compact cone, group), longest first: start | len << 8 | octant << 16
+  const int* task_ptr;   // [ncompact * kUpGroups + 1]
 };
 
 template <typename T>
@@ -418,7 +418,7 @@ struct PtInfo2 {
   T fr[2], fi[2];
 };
 
-constexpr int kUpRunWarps = 4;
+constexpr int kUpRunWarps = kUpGroups;   // warp w adds only into the parent points of group w
 
 __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A, RunTabs RT) {
   using T = float;
@@ -426,12 +426,10 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
   __shared__ T Xp[kQ][3];
   __shared__ PtInfo2<T> info[8][kQ];
   __shared__ T vals[kQ * kVS];
-  __shared__ int next_task;
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
   init_maps(M);
   const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
-  if (t == 0) next_task = kUpRunWarps;
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
   for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
@@ -460,12 +458,12 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
     }
   }
   __syncthreads();
-  const int ntot = RT.ntask[ci];
   const int ks = lane >> 4;   // columns 0..15 belong to kernel e, 16..31 to kernel i
-  // runs are taken dynamically, longest first over all octants; runs of absent children
-  // are skipped
-  for (int w = warp; w < ntot;) {
-    const int tk = __ldg(RT.task + (size_t)ci * 8 * kQ + w);
+  // the warp's own runs (its group of parent points, all octants); runs of absent children
+  // are skipped.  Only this warp adds into these points' values: plain shared-memory adds.
+  const int w1 = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp + 1);
+  for (int w = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp); w < w1; ++w) {
+    const int tk = __ldg(RT.task + w);
     const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
     const size_t g = (size_t)ci * 8 + o;
     const bool have = A.child[8 * P + o] >= 0;
@@ -514,17 +512,15 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
         {
           const T re = odd ? w0 : v0, im = odd ? v0 : w0;
           const T fr = I0.fr[ks], fi = I0.fi[ks];
-          atomicAdd(vals + q0 * kVS + lane, odd ? (re * fi + im * fr) : (re * fr - im * fi));
+          vals[q0 * kVS + lane] += odd ? (re * fi + im * fr) : (re * fr - im * fi);
         }
         if (two) {
           const T re = odd ? w1 : v1, im = odd ? v1 : w1;
           const T fr = I1.fr[ks], fi = I1.fi[ks];
-          atomicAdd(vals + q1 * kVS + lane, odd ? (re * fi + im * fr) : (re * fr - im * fi));
+          vals[q1 * kVS + lane] += odd ? (re * fi + im * fr) : (re * fr - im * fi);
         }
       }
     }
-    if (lane == 0) w = atomicAdd(&next_task, 1);
-    w = __shfl_sync(0xffffffffu, w, 0);
   }
   __syncthreads();
   vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32);
@@ -706,7 +702,7 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {
         if constexpr (std::is_same<T, float>::value)
-          k_up_runs<<<Pp.nslots, 32 * kUpRunWarps, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_ntask});
+          k_up_runs<<<Pp.nslots, 32 * kUpRunWarps, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
         else
           k_up<T><<<Pp.nslots, kUpThreads, 0, s>>>(U);
       }

@@ -33,9 +33,9 @@ struct HostLevel {
   std::vector<int> upcone_list;               // compact -> cone id
   std::vector<int> slot_upidx;                // slot -> compact index
   std::vector<int32_t> up_cc;                 // [ncompact][8][75] child cone at level d+1
-  std::vector<int32_t> up_order;              // [ncompact][8][75] points ranked by child cone
-  std::vector<int32_t> up_task;               // [ncompact][8 * 75] runs: start | len << 8 | octant << 16
-  std::vector<int32_t> up_ntask;              // [ncompact] runs over all octants
+  std::vector<int32_t> up_order;              // [ncompact][8][75] points ranked by (group, child cone)
+  std::vector<int32_t> up_task;               // runs start | len << 8 | octant << 16, per (cone, group)
+  std::vector<int32_t> up_task_ptr;           // [ncompact * kUpGroups + 1] CSR offsets into up_task
   // target evaluation lists at this level: per sorted target, its slots
   std::vector<int64_t> tgt_ptr;
   std::vector<int32_t> tgt_slot;
@@ -69,8 +69,8 @@ struct DevLevel {
   int* slot_upidx = nullptr;      // [nslots] compact cone index (as parent)
   int* up_cc = nullptr;           // [ncompact][8][75]
   int* up_order = nullptr;        // [ncompact][8][75]
-  int* up_task = nullptr;         // [ncompact][8 * 75]
-  int* up_ntask = nullptr;        // [ncompact]
+  int* up_task = nullptr;         // runs per (compact cone, group)
+  int* up_task_ptr = nullptr;     // [ncompact * kUpGroups + 1]
   int64_t* tgt_ptr = nullptr;     // [N+1]
   int* tgt_slot = nullptr;        // [ninter]
   int64_t ninter = 0;
