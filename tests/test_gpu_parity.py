@@ -213,3 +213,30 @@ def test_invalid_solve_arguments(small):
     it, rr, st = plan.solve(inc, y, tol=1e-6, max_iter=10)  # zero right-hand side
     assert it == 0 and st == lib.IFGF_OK and np.all(y == 0)
     plan.close()
+
+
+@pytest.mark.parametrize("prec", [lib.IFGF_FP32, lib.IFGF_FP64])
+def test_apply_is_graph_capturable(small, prec):
+    # ifgf_apply only launches kernels on the caller's stream: a CUDA graph of one call,
+    # replayed, gives bit-identical output to the eager call (the bench times replays)
+    prob, qp, op = small
+    plan = plan_of(prob, qp, far_mode=lib.IFGF_FAR_IFGF, precision=prec, ns0=2, na0=3)
+    y = torch.from_numpy(np.ascontiguousarray(random_densities(prob.n, 21))).cuda()
+    eager = torch.empty_like(y)
+    plan.apply(y, eager)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.apply(y, torch.empty_like(y))
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    out = torch.zeros_like(y)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.apply(y, out)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, eager)
+    plan.close()
