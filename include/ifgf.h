@@ -80,6 +80,9 @@ typedef struct {
   int32_t precision;       /* IFGF_FP64 or IFGF_FP32: arithmetic of steps (a)-(d) per apply */
   int32_t far_mode;        /* IFGF_FAR_IFGF or IFGF_FAR_DIRECT (plain O(N^2) far sum) */
   int32_t max_krylov;      /* GMRES basis capacity allocated by plan_create (0 -> 300, <= 1000) */
+  int32_t batch;           /* right-hand sides one batched call may carry (ifgf_apply_batch,
+                              bie_solve_batch): the per-apply buffers, cone coefficients and GMRES
+                              workspace are allocated this many times (0 -> 1, <= 1024) */
 } ifgf_plan_desc;
 
 /* Counts describing a plan (ifgf_plan_stats). */
@@ -123,6 +126,16 @@ ifgf_status ifgf_plan_destroy(ifgf_plan plan);
 ifgf_status ifgf_apply(ifgf_plan plan, const void* y, void* out, ifgf_stream stream);
 
 /*
+ * Batched forward map: out_r = A y_r for r = 0 .. nrhs-1 with one launch per kernel (the
+ * right-hand side is a grid dimension of every per-apply kernel; the near-field matrix,
+ * octree and cone tables are shared).  y, out: DEVICE [nrhs][4][N] complex128,
+ * 1 <= nrhs <= the plan's batch, not aliased.  Each out_r equals ifgf_apply on y_r bit for
+ * bit.  Asynchronous on `stream`; allocates nothing.  Errors as ifgf_apply, and
+ * IFGF_EINVAL for nrhs outside [1, batch].
+ */
+ifgf_status ifgf_apply_batch(ifgf_plan plan, int32_t nrhs, const void* y, void* out, ifgf_stream stream);
+
+/*
  * Raw scalar sums for tests: given the eight densities phi (DEVICE [N][8]
  * complex128, order m_x m_y m_z j_x j_y j_z div m div j; Sec. III first
  * paragraph), write f28 (DEVICE [N][28] complex128): S_e[phi_k] (k=0..7),
@@ -150,6 +163,19 @@ ifgf_status ifgf_apply_fields(ifgf_plan plan, const void* phi, void* f28, int32_
  */
 ifgf_status bie_solve(ifgf_plan plan, const void* inc, double tol, int32_t max_iter, void* y,
                       int32_t* iters, double* relres, ifgf_stream stream);
+
+/*
+ * nrhs independent solves of Eq. lin_system (as bie_solve) that share every forward map:
+ * each GMRES iteration applies A to the current Krylov vectors of all right-hand sides with
+ * one batched forward map.  inc: HOST or DEVICE [nrhs][6][N] complex128; y: HOST or DEVICE
+ * [nrhs][4][N] complex128; iters, relres: HOST arrays [nrhs] (may be NULL).  A right-hand
+ * side whose residual estimate reaches tol keeps its iterate (its Arnoldi state is frozen)
+ * while the others continue, up to max_iter.  1 <= nrhs <= the plan's batch.  Returns
+ * IFGF_ENOCONV if any right-hand side did not reach tol.  Synchronises `stream` (nrhs x 8
+ * scalars are read back per iteration).
+ */
+ifgf_status bie_solve_batch(ifgf_plan plan, int32_t nrhs, const void* inc, double tol, int32_t max_iter,
+                            void* y, int32_t* iters, double* relres, ifgf_stream stream);
 
 /* Counts and sizes of a plan. */
 ifgf_status ifgf_plan_stats(ifgf_plan plan, ifgf_stats* st);

@@ -21,7 +21,8 @@ IFGF_FP64, IFGF_FP32 = 0, 1
 IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
 IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 
-EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_fields", "bie_solve",
+EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_batch", "ifgf_apply_fields",
+           "bie_solve", "bie_solve_batch",
            "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
            "ifgf_tree_level", "ifgf_tree_targets", "ifgf_far_direct_noalloc"]
@@ -40,7 +41,7 @@ class ifgf_plan_desc(ctypes.Structure):
         ("leaf_size", ctypes.c_double), ("min_levels", ctypes.c_int32),
         ("delta", ctypes.c_double), ("n_beta", ctypes.c_int32), ("cov_d", ctypes.c_double),
         ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
-        ("max_krylov", ctypes.c_int32),
+        ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32),
     ]
 
 
@@ -78,9 +79,12 @@ def load(path: str = LIB_PATH):
     lib.ifgf_plan_create.argtypes = [ctypes.POINTER(ifgf_plan_desc), ctypes.POINTER(vp)]
     lib.ifgf_plan_destroy.argtypes = [vp]
     lib.ifgf_apply.argtypes = [vp, vp, vp, vp]
+    lib.ifgf_apply_batch.argtypes = [vp, i32, vp, vp, vp]
     lib.ifgf_apply_fields.argtypes = [vp, vp, vp, i32, vp]
     lib.bie_solve.argtypes = [vp, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
                               ctypes.POINTER(ctypes.c_double), vp]
+    lib.bie_solve_batch.argtypes = [vp, i32, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_double), vp]
     lib.ifgf_plan_stats.argtypes = [vp, ctypes.POINTER(ifgf_stats)]
     lib.ifgf_set_timing.argtypes = [vp, i32]
     lib.ifgf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
@@ -124,14 +128,14 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                      gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
-                     max_krylov: int = 0):
+                     max_krylov: int = 0, batch: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     ng = int(arrs[3].shape[1])
     d = ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
                        k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
-                       min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov)
+                       min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h
@@ -145,6 +149,12 @@ def ifgf_apply(plan, y, out, stream=None):
     """out = A y for torch complex128 CUDA tensors y, out of shape [4, N]."""
     _check(load().ifgf_apply(plan, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                              _stream(stream)), "ifgf_apply")
+
+
+def ifgf_apply_batch(plan, y, out, stream=None):
+    """out[r] = A y[r] for torch complex128 CUDA tensors y, out of shape [nrhs, 4, N]."""
+    _check(load().ifgf_apply_batch(plan, int(y.shape[0]), ctypes.c_void_p(y.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), _stream(stream)), "ifgf_apply_batch")
 
 
 def ifgf_apply_fields(plan, phi, f28, which: int = IFGF_PART_ALL, stream=None):
@@ -170,6 +180,19 @@ def bie_solve(plan, inc, tol: float, max_iter: int, y, stream=None, raise_on_noc
     if st not in (IFGF_OK, IFGF_ENOCONV) or (raise_on_noconv and st == IFGF_ENOCONV):
         raise IfgfError(st, "bie_solve")
     return it.value, rr.value, st
+
+
+def bie_solve_batch(plan, inc, tol: float, max_iter: int, y, stream=None):
+    """Batched GMRES solves; inc [nrhs, 6, N] and y [nrhs, 4, N] complex128, host (numpy) or
+    CUDA (torch).  Returns (iterations [nrhs], relative residual estimates [nrhs], status)."""
+    nrhs = int(inc.shape[0])
+    it = (ctypes.c_int32 * nrhs)()
+    rr = (ctypes.c_double * nrhs)()
+    st = load().bie_solve_batch(plan, nrhs, _addr(inc), float(tol), int(max_iter), _addr(y), it, rr,
+                                _stream(stream))
+    if st not in (IFGF_OK, IFGF_ENOCONV):
+        raise IfgfError(st, "bie_solve_batch")
+    return list(it), list(rr), st
 
 
 def ifgf_plan_stats(plan) -> dict:
@@ -316,6 +339,12 @@ class Plan:
 
     def apply(self, y, out, stream=None):
         ifgf_apply(self.handle, y, out, stream)
+
+    def apply_batch(self, y, out, stream=None):
+        ifgf_apply_batch(self.handle, y, out, stream)
+
+    def solve_batch(self, inc, y, tol=1e-6, max_iter=300, stream=None):
+        return bie_solve_batch(self.handle, inc, tol, max_iter, y, stream)
 
     def fields(self, phi, f28, which=IFGF_PART_ALL, stream=None):
         ifgf_apply_fields(self.handle, phi, f28, which, stream)

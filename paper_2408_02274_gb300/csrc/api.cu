@@ -52,7 +52,10 @@ void free_all(ifgf_plan_t* p) {
   for (void* a : p->allocations) cudaFree(a);
   p->allocations.clear();
   if (p->gm.hres) cudaFreeHost(p->gm.hres);
+  if (p->gm.hactive) cudaFreeHost(p->gm.hactive);
+  if (p->gm.hk) cudaFreeHost(p->gm.hk);
   p->gm.hres = nullptr;
+  p->gm.hactive = p->gm.hk = nullptr;
   for (auto& e : p->timer.pool)
     if (e) cudaEventDestroy(e);
   p->timer.pool.clear();
@@ -80,6 +83,7 @@ ifgf_status validate(const ifgf_plan_desc* d) {
   if (d->precision != IFGF_FP64 && d->precision != IFGF_FP32) return IFGF_EINVAL;
   if (d->far_mode != IFGF_FAR_IFGF && d->far_mode != IFGF_FAR_DIRECT) return IFGF_EINVAL;
   if (d->max_krylov < 0 || d->max_krylov > 1000) return IFGF_EINVAL;
+  if (d->batch < 0 || d->batch > 1024) return IFGF_EINVAL;
   if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
   if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
   return IFGF_OK;
@@ -240,7 +244,8 @@ void build(ifgf_plan_t* p) {
     Dl.tgt_ptr = A.upload(L.tgt_ptr);
     Dl.tgt_slot = A.upload(L.tgt_slot);
     Dl.ninter = (int64_t)L.tgt_slot.size();
-    size_t creal = (size_t)Dl.nslots * kQ * 32;
+    Dl.cstride = (size_t)Dl.nslots * kQ * 32;
+    const size_t creal = Dl.cstride * (size_t)p->batch;
     if (d.far_mode == IFGF_FAR_IFGF) {
       if (d.precision == IFGF_FP64)
         Dl.coefs = A.dev<double>(creal);
@@ -276,27 +281,32 @@ void build(ifgf_plan_t* p) {
   check(setup_combine_kernels(), "combine kernel attributes");
   // ---------------- per-apply buffers and GMRES workspace
   const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
-  p->phi = A.dev<char>(16 * (size_t)N * el);
-  p->a_sorted = A.dev<char>(16 * (size_t)N * el);
-  p->a_orig = A.dev<char>(16 * (size_t)N * el);
-  p->f28 = A.dev<char>(56 * (size_t)N * el);
-  p->phi64 = A.dev<double>(16 * (size_t)N);
+  const size_t B = (size_t)p->batch;
+  p->phi = A.dev<char>(16 * (size_t)N * el * B);
+  p->a_sorted = A.dev<char>(16 * (size_t)N * el * B);
+  p->a_orig = A.dev<char>(16 * (size_t)N * el * B);
+  p->f28 = A.dev<char>(56 * (size_t)N * el * B);
+  p->phi64 = A.dev<double>(16 * (size_t)N * B);
   GmresWork& G = p->gm;
   G.max_iter = d.max_krylov > 0 ? d.max_krylov : 300;
-  const size_t n4 = 4 * (size_t)N;
-  G.V = A.dev<double>(2 * n4 * (G.max_iter + 1));
-  G.H = A.dev<double>(2 * (size_t)(G.max_iter + 1) * (G.max_iter + 1));
-  G.cs = A.dev<double>(2 * (size_t)(G.max_iter + 1));
-  G.sn = A.dev<double>(2 * (size_t)(G.max_iter + 1));
-  G.g = A.dev<double>(2 * (size_t)(G.max_iter + 1));
-  G.h = A.dev<double>(4 * (size_t)(G.max_iter + 1));
-  G.part = A.dev<double>(2 * (size_t)dots_blocks((int64_t)n4) * (G.max_iter + 1));
-  G.scal = A.dev<double>(8);
-  G.w = A.dev<double>(2 * n4);
-  G.b = A.dev<double>(2 * n4);
-  G.y = A.dev<double>(2 * n4);
-  G.inc = A.dev<double>(12 * (size_t)N);
-  check(cudaMallocHost(&G.hres, 4 * sizeof(double)), "pinned scalar");
+  const size_t n4 = 4 * (size_t)N, m1 = (size_t)(G.max_iter + 1);
+  G.V = A.dev<double>(2 * n4 * m1 * B);
+  G.H = A.dev<double>(2 * m1 * m1 * B);
+  G.cs = A.dev<double>(2 * m1 * B);
+  G.sn = A.dev<double>(2 * m1 * B);
+  G.g = A.dev<double>(2 * m1 * B);
+  G.h = A.dev<double>(4 * m1 * B);
+  G.part = A.dev<double>(2 * (size_t)dots_blocks((int64_t)n4) * m1 * B);
+  G.scal = A.dev<double>(8 * B);
+  G.w = A.dev<double>(2 * n4 * B);
+  G.b = A.dev<double>(2 * n4 * B);
+  G.y = A.dev<double>(2 * n4 * B);
+  G.inc = A.dev<double>(12 * (size_t)N * B);
+  G.active = A.dev<int>(B);
+  G.kfin = A.dev<int>(B);
+  check(cudaMallocHost(&G.hres, 8 * B * sizeof(double)), "pinned scalars");
+  check(cudaMallocHost(&G.hactive, B * sizeof(int)), "pinned flags");
+  check(cudaMallocHost(&G.hk, B * sizeof(int)), "pinned counts");
   p->timer.pool.assign(256, nullptr);
   p->timer.kind.assign(128, 0);
   for (auto& e : p->timer.pool) check(cudaEventCreate(&e), "event");
@@ -312,26 +322,27 @@ bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-cudaError_t forward(ifgf_plan_t* p, const double* y, double* out, cudaStream_t s) {
+// out_r = A y_r for r < nrhs (y, out: device [nrhs][4N] complex128); one launch per kernel
+cudaError_t forward(ifgf_plan_t* p, const double* y, double* out, int nrhs, cudaStream_t s) {
   cudaError_t e;
   if (p->timer.on && p->timer.npending > 0 && (e = timer_flush(p)) != cudaSuccess) return e;
   int r = timer_begin(p, TK_PREP, s);
-  if ((e = launch_density_prep(p, y, nullptr, s)) != cudaSuccess) return e;
+  if ((e = launch_density_prep(p, y, nullptr, s, nrhs)) != cudaSuccess) return e;
   timer_end(p, r, s);
   r = timer_begin(p, TK_NEAR, s);
-  if ((e = launch_near(p, s)) != cudaSuccess) return e;
+  if ((e = launch_near(p, s, nrhs)) != cudaSuccess) return e;
   timer_end(p, r, s);
   p->launches += 3;   // prep, near, combine
   if (p->desc.far_mode == IFGF_FAR_IFGF) {
-    if ((e = launch_far_ifgf(p, s)) != cudaSuccess) return e;
+    if ((e = launch_far_ifgf(p, s, nrhs)) != cudaSuccess) return e;
   } else {
     r = timer_begin(p, TK_FAR_DIRECT, s);
-    if ((e = launch_far_direct(p, s)) != cudaSuccess) return e;
+    if ((e = launch_far_direct(p, s, nrhs)) != cudaSuccess) return e;
     timer_end(p, r, s);
     ++p->launches;
   }
   r = timer_begin(p, TK_COMBINE, s);
-  if ((e = launch_combine(p, y, out, s)) != cudaSuccess) return e;
+  if ((e = launch_combine(p, y, out, s, nrhs)) != cudaSuccess) return e;
   timer_end(p, r, s);
   return cudaSuccess;
 }
@@ -403,6 +414,7 @@ ifgf_status ifgf_plan_create(const ifgf_plan_desc* desc, ifgf_plan* out) {
   p->nc = desc->nc;
   p->ng = desc->ng;
   p->N = p->P * p->nc * p->nc;
+  p->batch = desc->batch > 0 ? desc->batch : 1;
   p->omega = desc->k_ext / std::sqrt(desc->eps_ext * desc->mu_ext);
   try {
     build(p);
@@ -436,17 +448,22 @@ ifgf_status ifgf_plan_destroy(ifgf_plan plan) {
   return IFGF_OK;
 }
 
-ifgf_status ifgf_apply(ifgf_plan p, const void* y, void* out, ifgf_stream stream) {
+ifgf_status ifgf_apply_batch(ifgf_plan p, int32_t nrhs, const void* y, void* out, ifgf_stream stream) {
   if (!p || !y || !out || y == out) return IFGF_EINVAL;
+  if (nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = forward(p, (const double*)y, (double*)out, s);
+  cudaError_t e = forward(p, (const double*)y, (double*)out, nrhs, s);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "ifgf_apply", __FILE__, __LINE__);
     p->poisoned = true;
     return IFGF_ECUDA;
   }
   return IFGF_OK;
+}
+
+ifgf_status ifgf_apply(ifgf_plan p, const void* y, void* out, ifgf_stream stream) {
+  return ifgf_apply_batch(p, 1, y, out, stream);
 }
 
 ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t which, ifgf_stream stream) {
@@ -466,9 +483,10 @@ ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t w
   return IFGF_OK;
 }
 
-ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter, void* y, int32_t* iters,
-                      double* relres, ifgf_stream stream) {
+ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
+                            int32_t* iters, double* relres, ifgf_stream stream) {
   if (!p || !inc || !y || !(tol > 0) || max_iter < 1) return IFGF_EINVAL;
+  if (nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
   if (max_iter > p->gm.max_iter) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
   cudaStream_t s = (cudaStream_t)stream;
@@ -476,22 +494,22 @@ ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter
   cudaError_t e = cudaSuccess;
   const double* dinc = (const double*)inc;
   if (!is_device_ptr(inc)) {
-    e = cudaMemcpyAsync(p->gm.inc, inc, sizeof(double) * 12 * (size_t)p->N, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(p->gm.inc, inc, sizeof(double) * 12 * (size_t)p->N * nrhs, cudaMemcpyHostToDevice, s);
     dinc = p->gm.inc;
   }
-  if (e == cudaSuccess) e = launch_rhs(p, dinc, p->gm.b, s);
+  if (e == cudaSuccess) e = launch_rhs(p, dinc, p->gm.b, s, nrhs);
   ++p->launches;
-  int it = 0;
-  double rr = 0;
+  std::vector<int> it(nrhs, 0);
+  std::vector<double> rr(nrhs, 0.0);
   if (e == cudaSuccess) {
-    MatvecFn mv = [p](const double* v, double* w, cudaStream_t st) { return forward(p, v, w, st); };
-    e = gmres_run(p, mv, tol, max_iter, &it, &rr, s);
+    MatvecFn mv = [p, nrhs](const double* v, double* w, cudaStream_t st) { return forward(p, v, w, nrhs, st); };
+    e = gmres_run(p, mv, nrhs, tol, max_iter, it.data(), rr.data(), s);
   }
   if (e == cudaSuccess) {
     if (is_device_ptr(y))
-      e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4, cudaMemcpyDeviceToDevice, s);
+      e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4 * nrhs, cudaMemcpyDeviceToDevice, s);
     else
-      e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4, cudaMemcpyDeviceToHost, s);
+      e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4 * nrhs, cudaMemcpyDeviceToHost, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -499,9 +517,18 @@ ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter
     p->poisoned = true;
     return IFGF_ECUDA;
   }
-  if (iters) *iters = it;
-  if (relres) *relres = rr;
-  return rr <= tol ? IFGF_OK : IFGF_ENOCONV;
+  bool all = true;
+  for (int r = 0; r < nrhs; ++r) {
+    if (iters) iters[r] = it[r];
+    if (relres) relres[r] = rr[r];
+    all = all && rr[r] <= tol;
+  }
+  return all ? IFGF_OK : IFGF_ENOCONV;
+}
+
+ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter, void* y, int32_t* iters,
+                      double* relres, ifgf_stream stream) {
+  return bie_solve_batch(p, 1, inc, tol, max_iter, y, iters, relres, stream);
 }
 
 ifgf_status ifgf_plan_stats(ifgf_plan p, ifgf_stats* st) {

@@ -44,6 +44,12 @@ __global__ void k_density_prep(int nc, const double* __restrict__ y, NodeGeom g,
   extern __shared__ double sm[];
   const int npp = nc * nc;
   double* JV = sm;   // [4][npp][2]: J m^u, J m^v, J j^u, J j^v
+  const size_t rb = blockIdx.y;   // right-hand side of a batched call
+  y += rb * 8 * (size_t)N;
+  phi += rb * 16 * (size_t)N;
+  a_sorted += rb * 16 * (size_t)N;
+  a_orig += rb * 16 * (size_t)N;
+  phi64 += rb * 16 * (size_t)N;
   const int p = blockIdx.x, t = threadIdx.x;
   const int l = p * npp + t;
   double vals[16];
@@ -119,6 +125,10 @@ __global__ void k_combine(int nc, int N, const T* __restrict__ f28, const double
   extern __shared__ double sm[];
   const int npp = nc * nc;
   double* S = sm;   // [16][npp][2] the S fields of this patch
+  const size_t rb = blockIdx.y;   // right-hand side of a batched call
+  f28 += rb * 56 * (size_t)N;
+  y += rb * 8 * (size_t)N;
+  out += rb * 8 * (size_t)N;
   const int p = blockIdx.x, t = threadIdx.x;
   const int l = p * npp + t;
   for (int e = t; e < 16 * npp; e += blockDim.x) {
@@ -226,7 +236,7 @@ __global__ void k_export(size_t n, const T* a, double* b) {
 }  // namespace
 
 cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const double* phi_in,
-                                cudaStream_t s) {
+                                cudaStream_t s, int nrhs) {
   const int npp = p->nc * p->nc;
   const int* iperm = p->perm + p->N;   // second half of the perm buffer holds original -> sorted
   if (phi_in) {
@@ -242,10 +252,10 @@ cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const dou
   size_t smem = sizeof(double) * 8 * npp;
   int threads = ((npp + 31) / 32) * 32;
   if (p->desc.precision == IFGF_FP64)
-    k_density_prep<double><<<p->P, threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm, p->N,
+    k_density_prep<double><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm, p->N,
         (double*)p->phi, (double*)p->a_sorted, (double*)p->a_orig, p->phi64);
   else
-    k_density_prep<float><<<p->P, threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm, p->N,
+    k_density_prep<float><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm, p->N,
         (float*)p->phi, (float*)p->a_sorted, (float*)p->a_orig, p->phi64);
   return cudaGetLastError();
 }
@@ -260,17 +270,17 @@ cudaError_t setup_combine_kernels() {
   return e;
 }
 
-cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s) {
+cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s, int nrhs) {
   const int npp = p->nc * p->nc;
   size_t smem = sizeof(double) * 32 * npp;
   int threads = ((npp + 31) / 32) * 32;
   Materials M{p->desc.k_ext, p->desc.k_int, p->desc.eps_ext, p->desc.eps_int,
               p->desc.mu_ext, p->desc.mu_int, p->omega};
   if (p->desc.precision == IFGF_FP64)
-    k_combine<double><<<p->P, threads, smem, s>>>(p->nc, p->N, (const double*)p->f28, y, p->geo,
+    k_combine<double><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, p->N, (const double*)p->f28, y, p->geo,
                                                     p->tab_D, M, out);
   else
-    k_combine<float><<<p->P, threads, smem, s>>>(p->nc, p->N, (const float*)p->f28, y, p->geo,
+    k_combine<float><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, p->N, (const float*)p->f28, y, p->geo,
                                                    p->tab_D, M, out);
   return cudaGetLastError();
 }

@@ -2,6 +2,14 @@
 // Gram-Schmidt applied twice, Givens rotations on the device, y0 = 0, no
 // restart.  The right-hand side is omega^{-1}(n x E^inc, n x H^inc) projected
 // on (t1, t2) (right side of Eq. n_muller).
+//
+// nrhs independent solves run side by side and share every forward map: the
+// Krylov basis is stored [k][rhs][4N], so the k-th vectors of all right-hand
+// sides form one contiguous [nrhs][4N] block, the input of one batched
+// forward map.  Every small kernel takes the right-hand side from its grid.
+// A right-hand side whose residual estimate reached the tolerance is frozen
+// (its Givens rotations, Hessenberg column and residual stop changing) while
+// the others continue.
 #include "gmres.h"
 
 namespace ifgf {
@@ -10,10 +18,15 @@ namespace {
 
 constexpr int kDotThreads = 256;
 constexpr int kDotItems = 4;
+constexpr int kDotJ = 8;
+constexpr int kScal = 8;   // scalars per right-hand side: |b|, beta, residual estimate
 
 __global__ void k_rhs(int N, const double* __restrict__ inc, NodeGeom g, double iw, double* __restrict__ b) {
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= N) return;
+  const size_t rb = blockIdx.y;   // right-hand side
+  inc += rb * 12 * (size_t)N;
+  b += rb * 8 * (size_t)N;
   const double* n = g.n + 3 * (size_t)l;
   const double* t1 = g.t1 + 3 * (size_t)l;
   const double* t2 = g.t2 + 3 * (size_t)l;
@@ -36,13 +49,18 @@ __global__ void k_rhs(int N, const double* __restrict__ inc, NodeGeom g, double 
   }
 }
 
-// part[chunk][j] = sum over the chunk of conj(V_j) w for j = 0..k1-1 (complex).  Grid:
-// (chunks of kDotThreads * kDotItems elements) x (groups of kDotJ vectors); w is read once
-// per block and the kDotJ sums are reduced together.
-constexpr int kDotJ = 8;
+// part[rb][chunk][j] = sum over the chunk of conj(V_{j,rb}) w_rb for j = 0..k1-1 (complex),
+// V_{j,rb} = V + 2 (j ldv + rb n), w_rb = w + 2 rb n.  Grid: (chunks of kDotThreads *
+// kDotItems elements) x (groups of kDotJ vectors) x (right-hand sides); w is read once per
+// block and the kDotJ sums are reduced together.
 __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const double* __restrict__ V,
-                                                      const double* __restrict__ w, double* __restrict__ part) {
+                                                      size_t ldv, const double* __restrict__ w,
+                                                      double* __restrict__ part, size_t pstride) {
   __shared__ double red[kDotThreads / 32][2 * kDotJ];
+  const size_t rb = blockIdx.z;
+  V += 2 * rb * (size_t)n;
+  w += 2 * rb * (size_t)n;
+  part += rb * pstride;
   const int64_t base = (int64_t)blockIdx.x * kDotThreads * kDotItems;
   const int j0 = blockIdx.y * kDotJ;
   double wr[kDotItems], wi[kDotItems];
@@ -59,7 +77,7 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const d
     double ar = 0, ai = 0;
     const int j = j0 + jj;
     if (j < k1) {
-      const double* v = V + 2 * (size_t)j * n;
+      const double* v = V + 2 * (size_t)j * ldv;
 #pragma unroll
       for (int it = 0; it < kDotItems; ++it)
         if (idx[it] < n) {
@@ -89,11 +107,13 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const d
   }
 }
 
-// h[j] (+)= sum_blk part[blk][j]
-__global__ void k_reduce_parts(int nblk, int k1, const double* __restrict__ part, double* __restrict__ h,
-                               int accumulate) {
+// h_rb[j] (+)= sum_blk part_rb[blk][j]
+__global__ void k_reduce_parts(int nblk, int k1, const double* __restrict__ part, size_t pstride,
+                               double* __restrict__ h, size_t hstride, int accumulate) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k1) return;
+  part += blockIdx.y * pstride;
+  h += blockIdx.y * hstride;
   double sr = 0, si = 0;
   for (int b = 0; b < nblk; ++b) {
     sr += part[2 * ((size_t)b * k1 + j)];
@@ -108,14 +128,21 @@ __global__ void k_reduce_parts(int nblk, int k1, const double* __restrict__ part
   }
 }
 
-// w -= sum_j V_j c_j (sign = -1) or y = sum_j V_j c_j (sign = +1, overwrite)
-__global__ void k_combo(int64_t n, int k1, const double* __restrict__ V, const double* __restrict__ c,
-                        double* __restrict__ w, int overwrite) {
+// w_rb -= sum_j V_{j,rb} c_rb[j] (overwrite = 0) or w_rb = sum_j V_{j,rb} c_rb[j] (overwrite = 1),
+// j < k1, or j < kvec[rb] when kvec is given
+__global__ void k_combo(int64_t n, int k1, const int* __restrict__ kvec, const double* __restrict__ V,
+                        size_t ldv, const double* __restrict__ c, size_t cstride, double* __restrict__ w,
+                        int overwrite) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const size_t rb = blockIdx.y;
+  if (kvec) k1 = kvec[rb];
+  V += 2 * rb * (size_t)n;
+  c += rb * cstride;
+  w += 2 * rb * (size_t)n;
   double ar = 0, ai = 0;
   for (int j = 0; j < k1; ++j) {
-    double vr = V[2 * ((size_t)j * n + i)], vi = V[2 * ((size_t)j * n + i) + 1];
+    double vr = V[2 * ((size_t)j * ldv + i)], vi = V[2 * ((size_t)j * ldv + i) + 1];
     double cr = c[2 * j], ci = c[2 * j + 1];
     ar += vr * cr - vi * ci;
     ai += vr * ci + vi * cr;
@@ -129,34 +156,54 @@ __global__ void k_combo(int64_t n, int k1, const double* __restrict__ V, const d
   }
 }
 
+// dst_rb = src_rb * f, f = 1 / sc_rb[0] (inv; 0 when sc_rb[0] = 0) or sc_rb[0]
 __global__ void k_scale_copy(int64_t n, const double* __restrict__ src, const double* __restrict__ sc,
                              int inv, double* __restrict__ dst) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double f = inv ? (sc[0] != 0.0 ? 1.0 / sc[0] : 0.0) : sc[0];
+  const size_t rb = blockIdx.y;
+  src += 2 * rb * (size_t)n;
+  dst += 2 * rb * (size_t)n;
+  const double s0 = sc[rb * kScal];
+  double f = inv ? (s0 != 0.0 ? 1.0 / s0 : 0.0) : s0;
   dst[2 * i] = src[2 * i] * f;
   dst[2 * i + 1] = src[2 * i + 1] * f;
 }
 
-// |w|^2 partials (reuses the dot kernel with V = w) -> scal[0] = |w|
-__global__ void k_norm_final(int nblk, const double* __restrict__ part, double* __restrict__ out) {
+// |w_rb|^2 partials -> out_rb = |w_rb|; one block per right-hand side
+__global__ void k_norm_final(int nblk, const double* __restrict__ part, size_t pstride, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  const size_t rb = blockIdx.x;
+  part += rb * pstride;
   double s = 0;
   for (int b = 0; b < nblk; ++b) s += part[2 * (size_t)b];
-  out[0] = sqrt(s);
+  out[rb * kScal] = sqrt(s);
 }
 
-// Arnoldi column k: Hcol[0..k] = h, Hcol[k+1] = beta; apply the previous
-// rotations, form the new one, update g; res[0] = |g_{k+1}| / |b|.
-__global__ void k_givens(int k, int ldh, double* __restrict__ H, const double* __restrict__ h,
-                         const double* __restrict__ beta, double* __restrict__ cs, double* __restrict__ sn,
-                         double* __restrict__ g, const double* __restrict__ bnorm, double* __restrict__ res) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+struct Arnoldi {                  // per-right-hand-side arrays and their strides (doubles)
+  double *H, *h, *cs, *sn, *g, *scal;
+  size_t sH, sh, sv;              // H: (max_iter + 1) ldh x 2; h, cs, sn, g: (max_iter + 1) x 2
+};
+
+// Arnoldi column k of right-hand side rb (one block each; frozen ones return): Hcol[0..k] = h,
+// Hcol[k+1] = beta; apply the previous rotations, form the new one, update g;
+// scal[2] = |g_{k+1}| / |b|.
+__global__ void k_givens(int k, int ldh, Arnoldi R, const int* __restrict__ active) {
+  if (threadIdx.x != 0) return;
+  const size_t rb = blockIdx.x;
+  if (!active[rb]) return;
+  double* H = R.H + rb * R.sH;
+  const double* h = R.h + rb * R.sh;
+  double* cs = R.cs + rb * R.sv;
+  double* sn = R.sn + rb * R.sv;
+  double* g = R.g + rb * R.sv;
+  double* scal = R.scal + rb * kScal;
   double* col = H + 2 * (size_t)k * ldh;   // column k, rows 0..k+1
   for (int i = 0; i <= k; ++i) {
     col[2 * i] = h[2 * i];
     col[2 * i + 1] = h[2 * i + 1];
   }
-  col[2 * (k + 1)] = beta[0];
+  col[2 * (k + 1)] = scal[1];
   col[2 * (k + 1) + 1] = 0.0;
   for (int i = 0; i < k; ++i) {
     // [a; b] <- [conj(c) conj(s); -s c] [a; b]
@@ -188,19 +235,25 @@ __global__ void k_givens(int k, int ldh, double* __restrict__ H, const double* _
   g[2 * (k + 1) + 1] = -(sr * gi + si * gr);
   g[2 * k] = cr * gr + ci * gi;
   g[2 * k + 1] = cr * gi - ci * gr;
-  res[0] = sqrt(g[2 * (k + 1)] * g[2 * (k + 1)] + g[2 * (k + 1) + 1] * g[2 * (k + 1) + 1]) / bnorm[0];
+  scal[2] = sqrt(g[2 * (k + 1)] * g[2 * (k + 1)] + g[2 * (k + 1) + 1] * g[2 * (k + 1) + 1]) / scal[0];
 }
 
-__global__ void k_init_g(const double* __restrict__ bnorm, double* __restrict__ g, int n) {
+__global__ void k_init_g(Arnoldi R, int n) {
+  const size_t rb = blockIdx.y;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double* g = R.g + rb * R.sv;
   if (i < 2 * n) g[i] = 0;
-  if (i == 0) g[0] = bnorm[0];
+  if (i == 0) g[0] = R.scal[rb * kScal];
 }
 
-// back substitution R z = g[0..k-1] (R upper triangular in H), z into c
-__global__ void k_backsub(int k, int ldh, const double* __restrict__ H, const double* __restrict__ g,
-                          double* __restrict__ z) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// back substitution R z = g[0..k_rb-1] (R upper triangular in H), z into h; one block per rhs
+__global__ void k_backsub(const int* __restrict__ kvec, int ldh, Arnoldi R) {
+  if (threadIdx.x != 0) return;
+  const size_t rb = blockIdx.x;
+  const int k = kvec[rb];
+  const double* H = R.H + rb * R.sH;
+  const double* g = R.g + rb * R.sv;
+  double* z = R.h + rb * R.sh;
   for (int i = k - 1; i >= 0; --i) {
     double sr = g[2 * i], si = g[2 * i + 1];
     for (int j = i + 1; j < k; ++j) {
@@ -217,79 +270,109 @@ __global__ void k_backsub(int k, int ldh, const double* __restrict__ H, const do
 
 }  // namespace
 
-cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s) {
-  k_rhs<<<(p->N + 127) / 128, 128, 0, s>>>(p->N, inc, p->geo, 1.0 / p->omega, b);
+cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s, int nrhs) {
+  k_rhs<<<dim3((p->N + 127) / 128, nrhs), 128, 0, s>>>(p->N, inc, p->geo, 1.0 / p->omega, b);
   return cudaGetLastError();
 }
 
 int dots_blocks(int64_t n) { return (int)((n + kDotThreads * kDotItems - 1) / (kDotThreads * kDotItems)); }
 
-// Gram-Schmidt projection h (+)= V[0..k1)^H w and w -= V h_pass.
-static cudaError_t project(GmresWork& G, int64_t n, int k1, double* hpass, double* htot, int first,
-                           cudaStream_t s) {
-  int nb = dots_blocks(n);
-  k_dots<<<dim3(nb, (k1 + kDotJ - 1) / kDotJ), kDotThreads, 0, s>>>(n, k1, G.V, G.w, G.part);
-  k_reduce_parts<<<(k1 + 127) / 128, 128, 0, s>>>(nb, k1, G.part, hpass, 0);
-  k_combo<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, k1, G.V, hpass, G.w, 0);
-  k_reduce_parts<<<(k1 + 127) / 128, 128, 0, s>>>(nb, k1, G.part, htot, first ? 0 : 1);
+namespace {
+
+struct Batch {
+  int nrhs;
+  int64_t n;        // 4N
+  int nb;           // dot-product chunks
+  size_t ldv;       // doubles / 2 between consecutive Krylov vectors of one right-hand side
+  size_t pstride;   // doubles of partial sums per right-hand side
+};
+
+// Gram-Schmidt projection of w against V[0..k1): h_pass = V^H w (per rhs), w -= V h_pass,
+// h_tot (+)= h_pass.
+cudaError_t project(GmresWork& G, const Batch& B, const Arnoldi& R, int k1, int first, cudaStream_t s) {
+  double* hpass = R.h + 2 * (size_t)(G.max_iter + 1);   // second half of each rhs's h block
+  k_dots<<<dim3(B.nb, (k1 + kDotJ - 1) / kDotJ, B.nrhs), kDotThreads, 0, s>>>(B.n, k1, G.V, B.ldv, G.w, G.part,
+                                                                              B.pstride);
+  k_reduce_parts<<<dim3((k1 + 127) / 128, B.nrhs), 128, 0, s>>>(B.nb, k1, G.part, B.pstride, hpass, R.sh, 0);
+  k_combo<<<dim3((unsigned)((B.n + 255) / 256), B.nrhs), 256, 0, s>>>(B.n, k1, nullptr, G.V, B.ldv, hpass, R.sh,
+                                                                        G.w, 0);
+  k_reduce_parts<<<dim3((k1 + 127) / 128, B.nrhs), 128, 0, s>>>(B.nb, k1, G.part, B.pstride, R.h, R.sh,
+                                                                  first ? 0 : 1);
   return cudaGetLastError();
 }
 
-cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, double tol, int max_iter, int* iters,
+}  // namespace
+
+cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, int nrhs, double tol, int max_iter, int* iters,
                       double* relres, cudaStream_t s) {
   GmresWork& G = p->gm;
   const int64_t n = 4 * (int64_t)p->N;
   const int ldh = G.max_iter + 1;
-  const int nb = dots_blocks(n);
+  Batch B{nrhs, n, dots_blocks(n), (size_t)nrhs * (size_t)n, 2 * (size_t)dots_blocks(n) * (G.max_iter + 1)};
+  const size_t sv = 2 * (size_t)(G.max_iter + 1);
+  Arnoldi R{G.H, G.h, G.cs, G.sn, G.g, G.scal, 2 * (size_t)(G.max_iter + 1) * ldh, 2 * sv, sv};
+  const unsigned vblocks = (unsigned)((n + 255) / 256);
   cudaError_t err;
-  // |b|
-  k_dots<<<nb, kDotThreads, 0, s>>>(n, 1, G.b, G.b, G.part);
-  k_norm_final<<<1, 1, 0, s>>>(nb, G.part, G.scal + 0);          // scal[0] = |b|
-  k_init_g<<<(2 * (G.max_iter + 1) + 127) / 128, 128, 0, s>>>(G.scal + 0, G.g, G.max_iter + 1);
-  k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, G.b, G.scal + 0, 1, G.V);   // v0 = b/|b|
+  // |b_rb|, g_rb = |b_rb| e_1, v_{0,rb} = b_rb / |b_rb|
+  k_dots<<<dim3(B.nb, 1, nrhs), kDotThreads, 0, s>>>(n, 1, G.b, 0, G.b, G.part, B.pstride);
+  k_norm_final<<<nrhs, 32, 0, s>>>(B.nb, G.part, B.pstride, G.scal + 0);
+  k_init_g<<<dim3((2 * (G.max_iter + 1) + 127) / 128, nrhs), 128, 0, s>>>(R, G.max_iter + 1);
+  k_scale_copy<<<dim3(vblocks, nrhs), 256, 0, s>>>(n, G.b, G.scal + 0, 1, G.V);
   p->launches += 4;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  if ((err = cudaMemcpyAsync(G.hres, G.scal, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return err;
+  if ((err = cudaMemcpyAsync(G.hres, G.scal, sizeof(double) * kScal * nrhs, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return err;
   if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
-  const double bnorm = G.hres[0];
-  int k = 0;
-  double res = 1.0;
-  if (bnorm == 0.0) {
-    cudaMemsetAsync(G.y, 0, sizeof(double) * 2 * n, s);
-    *iters = 0;
-    *relres = 0.0;
-    return cudaGetLastError();
+  int nactive = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    const bool a = G.hres[r * kScal] != 0.0;   // b = 0: y = 0 after zero iterations
+    G.hactive[r] = a ? 1 : 0;
+    G.hk[r] = 0;
+    relres[r] = a ? 1.0 : 0.0;
+    nactive += a;
   }
-  for (k = 0; k < max_iter; ++k) {
-    double* vk = G.V + 2 * (size_t)k * n;
-    if ((err = matvec(vk, G.w, s)) != cudaSuccess) return err;
+  if ((err = cudaMemcpyAsync(G.active, G.hactive, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return err;
+  int k = 0;
+  for (k = 0; k < max_iter && nactive > 0; ++k) {
+    // w_rb = A v_{k,rb} for all right-hand sides in one batched forward map
+    if ((err = matvec(G.V + 2 * (size_t)k * B.ldv, G.w, s)) != cudaSuccess) return err;
     const int rec = timer_begin(p, TK_GMRES, s);
     // CGS2: two projection passes, h = h1 + h2
-    if ((err = project(G, n, k + 1, G.h + 2 * (size_t)(G.max_iter + 1), G.h, 1, s)) != cudaSuccess) return err;
-    if ((err = project(G, n, k + 1, G.h + 2 * (size_t)(G.max_iter + 1), G.h, 0, s)) != cudaSuccess) return err;
-    k_dots<<<nb, kDotThreads, 0, s>>>(n, 1, G.w, G.w, G.part);
-    k_norm_final<<<1, 1, 0, s>>>(nb, G.part, G.scal + 1);         // scal[1] = beta
-    k_givens<<<1, 1, 0, s>>>(k, ldh, G.H, G.h, G.scal + 1, G.cs, G.sn, G.g, G.scal + 0, G.scal + 2);
-    k_scale_copy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, G.w, G.scal + 1, 1, G.V + 2 * (size_t)(k + 1) * n);
+    if ((err = project(G, B, R, k + 1, 1, s)) != cudaSuccess) return err;
+    if ((err = project(G, B, R, k + 1, 0, s)) != cudaSuccess) return err;
+    k_dots<<<dim3(B.nb, 1, nrhs), kDotThreads, 0, s>>>(n, 1, G.w, 0, G.w, G.part, B.pstride);
+    k_norm_final<<<nrhs, 32, 0, s>>>(B.nb, G.part, B.pstride, G.scal + 1);   // scal[1] = beta
+    k_givens<<<nrhs, 32, 0, s>>>(k, ldh, R, G.active);
+    k_scale_copy<<<dim3(vblocks, nrhs), 256, 0, s>>>(n, G.w, G.scal + 1, 1, G.V + 2 * (size_t)(k + 1) * B.ldv);
     timer_end(p, rec, s);
     p->launches += 12;   // 2 x (dots, reduce, combo, reduce), dots, norm, givens, scale
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    if ((err = cudaMemcpyAsync(G.hres, G.scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    if ((err = cudaMemcpyAsync(G.hres, G.scal, sizeof(double) * kScal * nrhs, cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
       return err;
     if ((err = cudaStreamSynchronize(s)) != cudaSuccess) return err;
-    res = G.hres[1];
-    if (res <= tol || G.hres[0] == 0.0) {
-      ++k;
-      break;
+    bool changed = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!G.hactive[r]) continue;
+      relres[r] = G.hres[r * kScal + 2];
+      G.hk[r] = k + 1;
+      if (relres[r] <= tol || G.hres[r * kScal + 1] == 0.0) {
+        G.hactive[r] = 0;
+        --nactive;
+        changed = true;
+      }
     }
+    if (changed && nactive > 0 &&
+        (err = cudaMemcpyAsync(G.active, G.hactive, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return err;
   }
-  if (k > max_iter) k = max_iter;
-  k_backsub<<<1, 1, 0, s>>>(k, ldh, G.H, G.g, G.h);
-  k_combo<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, k, G.V, G.h, G.y, 1);
+  if ((err = cudaMemcpyAsync(G.kfin, G.hk, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s)) != cudaSuccess) return err;
+  k_backsub<<<nrhs, 32, 0, s>>>(G.kfin, ldh, R);
+  k_combo<<<dim3(vblocks, nrhs), 256, 0, s>>>(n, 0, G.kfin, G.V, B.ldv, R.h, R.sh, G.y, 1);
   p->launches += 2;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  *iters = k;
-  *relres = res;
+  for (int r = 0; r < nrhs; ++r) iters[r] = G.hk[r];
   return cudaSuccess;
 }
 

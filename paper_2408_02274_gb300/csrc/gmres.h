@@ -6,11 +6,13 @@
 
 namespace ifgf {
 
-// matvec(v, w, stream): w = A v for device [4][N] complex128 vectors.
+// matvec(v, w, stream): w_r = A v_r for the right-hand sides of the solve, device
+// [nrhs][4N] complex128 blocks.
 using MatvecFn = std::function<cudaError_t(const double*, double*, cudaStream_t)>;
 
-// Solves A y = b with b in p->gm.b; the solution is written to p->gm.y.
-cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, double tol, int max_iter, int* iters,
+// Solves A y_r = b_r, r < nrhs, with b in p->gm.b [nrhs][4N]; solutions to p->gm.y [nrhs][4N];
+// iters[r], relres[r] (host arrays) receive the Krylov dimension and the residual estimate.
+cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, int nrhs, double tol, int max_iter, int* iters,
                       double* relres, cudaStream_t s);
 int dots_blocks(int64_t n);
 

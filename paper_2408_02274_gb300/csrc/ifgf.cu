@@ -211,6 +211,7 @@ struct LeafArgs {
   const T* a_sorted;
   T* coefs;
   T ke, ki;
+  size_t astride, cstride;   // per right-hand side: densities, cone coefficients
 };
 
 template <typename T>
@@ -227,6 +228,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
   T* vbuf = pool + (kSep ? kSrcWords : 0);
   const int box = blockIdx.x;
   const int t = threadIdx.x;
+  A.a_sorted += blockIdx.z * A.astride;   // right-hand side of a batched call
+  A.coefs += blockIdx.z * A.cstride;
   const int sb = A.box_slot_ptr[box] + blockIdx.y * kLeafSlots;
   const int se = min(A.box_slot_ptr[box + 1], sb + kLeafSlots);
   if (sb >= se) return;   // the box has fewer segments than this block's range (uniform per block)
@@ -318,6 +321,7 @@ struct UpArgs {
   const T* coefs_c;
   T* coefs_p;
   T ke, ki;
+  size_t cstride_c, cstride_p;   // per right-hand side
 };
 
 template <typename T>
@@ -335,6 +339,8 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
   __shared__ T vals[kQ * kVS];
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
+  A.coefs_p += blockIdx.y * A.cstride_p;
   init_maps(M);
   const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
   __syncthreads();
@@ -428,6 +434,8 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
   __shared__ T vals[kQ * kVS];
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
+  A.coefs_p += blockIdx.y * A.cstride_p;
   init_maps(M);
   const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
   __syncthreads();
@@ -542,6 +550,7 @@ struct TgtArgs {
   const int* perm;
   T* f28;
   T ke, ki;
+  size_t cstride;   // cone coefficients per right-hand side (fields: 56 N)
 };
 
 // Per (target, cone) scalars, computed one cone per lane and read back by the
@@ -565,6 +574,8 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T> A)
   const int t = blockIdx.x * tgt_warps<T>() + warp;
   const int lane = threadIdx.x & 31;
   if (t >= A.N) return;
+  A.coefs += blockIdx.y * A.cstride;   // right-hand side of a batched call
+  A.f28 += blockIdx.y * 56 * (size_t)A.N;
   const int64_t e0 = A.tgt_ptr[t], e1 = A.tgt_ptr[t + 1];
   if (e0 == e1) return;
   const double x0 = A.x_sorted[3 * (size_t)t], x1 = A.x_sorted[3 * (size_t)t + 1], x2 = A.x_sorted[3 * (size_t)t + 2];
@@ -672,16 +683,17 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T> A)
 }
 
 template <typename T>
-cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
+cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int D = p->tree.D;
   const T ke = (T)p->desc.k_ext, ki = (T)p->desc.k_int;
   {
     const DevLevel& L = p->dl[D];
     LeafArgs<T> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
-                  p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki};
+                  p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki, 16 * (size_t)p->N, L.cstride};
     int rec = timer_begin(p, TK_LEAF, s);
     if (L.nboxes > 0 && L.max_box_slots > 0) {
-      const dim3 grid((unsigned)L.nboxes, (unsigned)((L.max_box_slots + kLeafSlots - 1) / kLeafSlots));
+      const dim3 grid((unsigned)L.nboxes, (unsigned)((L.max_box_slots + kLeafSlots - 1) / kLeafSlots),
+                      (unsigned)nrhs);
       k_leaf<T><<<grid, kLeafThreads, 0, s>>>(A);
     }
     timer_end(p, rec, s);
@@ -690,21 +702,23 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
   for (int d = D; d >= 3; --d) {
     const DevLevel& L = p->dl[d];
     TgtArgs<T> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
-                 (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (T*)p->f28, ke, ki};
+                 (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (T*)p->f28, ke, ki, L.cstride};
     int rec = timer_begin(p, TK_TARGET, s);
-    k_target<T><<<(unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), 32 * tgt_warps<T>(), 0, s>>>(B);
+    k_target<T><<<dim3((unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), nrhs), 32 * tgt_warps<T>(), 0,
+                  s>>>(B);
     timer_end(p, rec, s);
     ++p->launches;
     if (d > 3) {
       const DevLevel& Pp = p->dl[d - 1];
       UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, cone_geom_t<T>(Pp.cg),
-                  L.cone_map, L.cg.ncones(), cone_geom_t<T>(L.cg), L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki};
+                  L.cone_map, L.cg.ncones(), cone_geom_t<T>(L.cg), L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki,
+                  L.cstride, Pp.cstride};
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {
         if constexpr (std::is_same<T, float>::value)
-          k_up_runs<<<Pp.nslots, 32 * kUpRunWarps, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
+          k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
         else
-          k_up<T><<<Pp.nslots, kUpThreads, 0, s>>>(U);
+          k_up<T><<<dim3(Pp.nslots, nrhs), kUpThreads, 0, s>>>(U);
       }
       timer_end(p, rec, s);
       ++p->launches;
@@ -715,9 +729,9 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s) {
-  if (p->desc.precision == IFGF_FP64) return run_ifgf<double>(p, s);
-  return run_ifgf<float>(p, s);
+cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
+  if (p->desc.precision == IFGF_FP64) return run_ifgf<double>(p, s, nrhs);
+  return run_ifgf<float>(p, s, nrhs);
 }
 
 }  // namespace ifgf

@@ -31,19 +31,21 @@ struct Materials {
 };
 
 // a0: y [4][N] complex128 -> phi (orig, plan precision), a_sorted, a_orig (phi * omega)
+// (every per-apply launcher takes nrhs right-hand sides as a grid dimension; buffers are
+//  [nrhs][...] with the per-right-hand-side strides of the plan)
 cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const double* phi_in,
-                                cudaStream_t s);
+                                cudaStream_t s, int nrhs = 1);
 // c-post: f28 + y -> out [4][N] complex128
-cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s);
+cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, cudaStream_t s, int nrhs = 1);
 cudaError_t setup_combine_kernels();
 // (d): f28 = near * phi   (overwrites f28)
-cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s);
+cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 // far field by the plain direct sum (accumulates into f28)
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s);
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
                                   double ke, double ki, int precision, void* f28, cudaStream_t s);
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
-cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s);
+cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 // zero f28
 cudaError_t launch_zero_f28(const ifgf_plan_t* p, cudaStream_t s);
 // f28 (plan precision) -> complex128 [N][28]
@@ -55,6 +57,6 @@ void timer_end(ifgf_plan_t* p, int rec, cudaStream_t s);
 cudaError_t timer_flush(ifgf_plan_t* p);
 
 // ---- GMRES helpers (gmres.cu)
-cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s);
+cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s, int nrhs = 1);
 
 }  // namespace ifgf

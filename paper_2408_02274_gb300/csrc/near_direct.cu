@@ -59,6 +59,9 @@ __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= N) return;
+  const size_t rb = blockIdx.y;   // right-hand side of a batched call
+  phi += rb * 16 * (size_t)N;
+  f28 += rb * 56 * (size_t)N;
   T acc[56];
 #pragma unroll
   for (int k = 0; k < 56; ++k) acc[k] = T(0);
@@ -105,6 +108,9 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
                                                     const T* __restrict__ a, T ke, T ki,
                                                     T* __restrict__ f28) {
   __shared__ SrcTile<T> tile[128];
+  const size_t rb = blockIdx.y;   // right-hand side of a batched call
+  a += rb * 16 * (size_t)N;
+  f28 += rb * 56 * (size_t)N;
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = l < N;
   T xl[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
@@ -167,25 +173,25 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
 
 }  // namespace
 
-cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s) {
+cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int threads = 256;
   const unsigned blocks = (unsigned)(((size_t)p->N * 32 + threads - 1) / threads);
   if (p->desc.precision == IFGF_FP64)
-    k_near<double><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
+    k_near<double><<<dim3(blocks, nrhs), threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
         p->near.val64, (const double*)p->phi, (double*)p->f28);
   else
-    k_near<float><<<blocks, threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
+    k_near<float><<<dim3(blocks, nrhs), threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
         p->near.val32, (const float*)p->phi, (float*)p->f28);
   return cudaGetLastError();
 }
 
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s) {
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const unsigned blocks = (unsigned)((p->N + 127) / 128);
   if (p->desc.precision == IFGF_FP64)
-    k_far_direct<double><<<blocks, 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+    k_far_direct<double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
         (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28);
   else
-    k_far_direct<float><<<blocks, 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+    k_far_direct<float><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
         (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28);
   return cudaGetLastError();
 }

@@ -74,7 +74,8 @@ struct DevLevel {
   int64_t* tgt_ptr = nullptr;     // [N+1]
   int* tgt_slot = nullptr;        // [ninter]
   int64_t ninter = 0;
-  void* coefs = nullptr;          // [nslots][75][32] real (precision of the plan)
+  void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan)
+  size_t cstride = 0;             // nslots * 75 * 32: coefficients per right-hand side
 };
 
 struct NodeGeom {           // per-node geometry, original order (FP64 SoA)
@@ -97,21 +98,25 @@ struct NearMatrix {
   float* val32 = nullptr;       // [nnz][4][2]
 };
 
-struct GmresWork {
+struct GmresWork {               // per right-hand side r < batch (layouts below)
   int max_iter = 0;
-  double* V = nullptr;          // [(max_iter+1)][4N][2]
-  double* H = nullptr;          // [(max_iter+1)][max_iter][2]
-  double* cs = nullptr;         // [max_iter][2]
-  double* sn = nullptr;         // [max_iter][2]
-  double* g = nullptr;          // [max_iter+1][2]
-  double* h = nullptr;          // [max_iter+1][2] projection scratch
-  double* part = nullptr;       // [nblk][max_iter+1][2] partial dot products
-  double* scal = nullptr;       // small scalars
-  double* w = nullptr;          // [4N][2]
-  double* b = nullptr;          // [4N][2]
-  double* y = nullptr;          // [4N][2]
-  double* inc = nullptr;        // [6N][2]
-  double* hres = nullptr;       // pinned host scalar
+  double* V = nullptr;          // [max_iter+1][nrhs][4N][2] Krylov basis (k-major)
+  double* H = nullptr;          // [batch][max_iter+1][max_iter+1][2]
+  double* cs = nullptr;         // [batch][max_iter+1][2]
+  double* sn = nullptr;         // [batch][max_iter+1][2]
+  double* g = nullptr;          // [batch][max_iter+1][2]
+  double* h = nullptr;          // [batch][2][max_iter+1][2] projections (total, pass)
+  double* part = nullptr;       // [batch][nblk][max_iter+1][2] partial dot products
+  double* scal = nullptr;       // [batch][8]: |b|, beta, residual estimate
+  double* w = nullptr;          // [batch][4N][2]
+  double* b = nullptr;          // [batch][4N][2]
+  double* y = nullptr;          // [batch][4N][2]
+  double* inc = nullptr;        // [batch][6N][2]
+  int* active = nullptr;        // [batch] 1 while a right-hand side iterates
+  int* kfin = nullptr;          // [batch] Krylov dimension at the end
+  double* hres = nullptr;       // pinned host copy of scal
+  int* hactive = nullptr;       // pinned host [batch]
+  int* hk = nullptr;            // pinned host [batch]
 };
 
 // Per-kernel-kind CUDA-event timing of the per-apply work (optional).
@@ -132,6 +137,7 @@ struct ifgf_tree_t : ifgf::HostTree {};
 struct ifgf_plan_t {
   ifgf_plan_desc desc{};
   int N = 0, P = 0, nc = 0, ng = 0;
+  int batch = 1;                // right-hand sides the per-apply buffers hold
   double omega = 0;
   bool poisoned = false;
   ifgf::KernelTimer timer;
@@ -148,11 +154,11 @@ struct ifgf_plan_t {
   int* leafc = nullptr;         // [N][3] integer leaf coordinates (original order)
   std::vector<ifgf::DevLevel> dl;  // index d
   ifgf::NearMatrix near;
-  void* phi = nullptr;          // [N][8][2] densities (plan precision), original order
-  void* a_sorted = nullptr;     // [N][8][2] phi * omega, sorted order
-  void* a_orig = nullptr;       // [N][8][2] phi * omega, original order (direct far)
-  void* f28 = nullptr;          // [N][28][2] scalar fields (plan precision)
-  double* phi64 = nullptr;      // [N][8][2] FP64 densities (prep output)
+  void* phi = nullptr;          // [batch][N][8][2] densities (plan precision), original order
+  void* a_sorted = nullptr;     // [batch][N][8][2] phi * omega, sorted order
+  void* a_orig = nullptr;       // [batch][N][8][2] phi * omega, original order (direct far)
+  void* f28 = nullptr;          // [batch][N][28][2] scalar fields (plan precision)
+  double* phi64 = nullptr;      // [batch][N][8][2] FP64 densities (prep output)
   ifgf::GmresWork gm;
   ifgf_stats stats{};
   std::vector<void*> allocations;
