@@ -26,6 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
+    "sphere384": "sphere r=0.5 lambda, eps_r=2.25, 6 patches x 8x8 nodes (N=384, 1536 unknowns)",
     "sphere9600": "sphere r=2 lambda, eps_r=4, 96 patches x 10x10 nodes (N=9600, 38400 unknowns)",
     "sphere153600": "sphere r=4 lambda, eps_r=2.25, 600 patches x 16x16 nodes (N=153600, 614400 unknowns)",
 }
@@ -37,7 +38,9 @@ NS0, NA0 = 2, 3
 
 
 def problem(name: str = "sphere9600"):
-    from inputs import CONFIG_SPHERE_MEDIUM, sphere_problem
+    from inputs import CONFIG_SPHERE_MEDIUM, CONFIG_SPHERE_SMALL, sphere_problem
+    if name == "sphere384":
+        return CONFIG_SPHERE_SMALL(8)
     if name == "sphere153600":
         return sphere_problem(4.0, 10, 16, 2.25, name="sphere_r4_eps2.25_P600")
     return CONFIG_SPHERE_MEDIUM(10)
@@ -461,6 +464,75 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_batch(args):
+    """Batched right-hand sides: the forward map for nrhs right-hand sides in one batched
+    call (CUDA-graph replays, median of 20) against nrhs single applies, and optionally a
+    batched GMRES solve of the first nrhs Fibonacci-sphere incidences."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import fibonacci_incidences
+    libbuild.build()
+    torch.cuda.set_device(0)
+    prob = problem(args.workload)
+    N, B = prob.n, args.nrhs
+    plan = lib.Plan.from_problem(prob, delta=delta_of(prob), n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, batch=B,
+                                 max_krylov=args.max_krylov if args.solve else 10)
+    rng = np.random.default_rng(9)
+    y = torch.from_numpy(np.ascontiguousarray(
+        (rng.standard_normal((B, 4, N)) + 1j * rng.standard_normal((B, 4, N))) / np.sqrt(2))).cuda()
+    out = torch.empty_like(y)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def replay_median(fn, reps=20, warm=3):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(warm):
+                fn()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        for _ in range(warm):
+            g.replay()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)) / 1e3
+
+    t_batch = replay_median(lambda: plan.apply_batch(y, out))
+    y0, o0 = y[0].contiguous(), torch.empty_like(y[0])
+    t_single = replay_median(lambda: plan.apply(y0, o0))
+    res = {"mode": "batch", "workload": WORKLOADS[args.workload], "nrhs": B,
+           "batched_apply_ms": 1e3 * t_batch, "single_apply_ms": 1e3 * t_single,
+           "batched_unknown_matvecs_per_s": 4.0 * N * B / t_batch,
+           "single_unknown_matvecs_per_s": 4.0 * N / t_single,
+           "speedup_per_rhs": t_single * B / t_batch, "device_bytes": plan.stats()["device_bytes"]}
+    if args.solve:
+        x, _, _ = prob.nodes()
+        inc = torch.from_numpy(np.ascontiguousarray(fibonacci_incidences(x, prob.k_ext, prob.omega)[:B])).cuda()
+        ys = torch.empty((B, 4, N), dtype=torch.complex128, device="cuda")
+        plan.solve_batch(inc, ys, tol=args.tol, max_iter=args.max_krylov)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rrs, st = plan.solve_batch(inc, ys, tol=args.tol, max_iter=args.max_krylov)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res.update({"batched_solve_s": dt, "iterations": its, "max_relres": max(rrs),
+                    "status": int(st), "solve_unknown_matvecs_per_s": 4.0 * N * float(np.sum(its)) / dt})
+    plan.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,13 +542,18 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch"])
+    ap.add_argument("--nrhs", type=int, default=8)
+    ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--max-krylov", type=int, default=200)
     ap.add_argument("--workload", default="sphere9600", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)
     elif args.mode == "apply":
         res = run_apply(args)
+    elif args.mode == "batch":
+        res = run_batch(args)
     else:
         res = run_gpu(args)
     if res is not None:
