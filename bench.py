@@ -533,6 +533,51 @@ def run_batch(args):
     return res
 
 
+def run_uneven(args):
+    """Uneven batch of 16 dielectric ellipsoids (one plane wave each): the solves one after
+    the other, then all at once with bie_solve_many (one host thread and stream per body)."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import ellipsoid_batch, plane_wave
+    libbuild.build()
+    torch.cuda.set_device(0)
+    bodies = ellipsoid_batch(args.nbodies)
+    t0 = time.perf_counter()
+    plans = [lib.Plan.from_problem(b, delta=delta_of(b), n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                   far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_krylov)
+             for b in bodies]
+    setup = time.perf_counter() - t0
+    incs, ys = [], []
+    for b in bodies:
+        x, _, _ = b.nodes()
+        incs.append(torch.from_numpy(np.ascontiguousarray(plane_wave(x, b.k_ext, b.omega)[None])).cuda())
+        ys.append(torch.empty((1, 4, b.n), dtype=torch.complex128, device="cuda"))
+    lib.bie_solve_many(plans, incs, ys, tol=args.tol, max_iter=args.max_krylov)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_its = []
+    for p, inc, y in zip(plans, incs, ys):
+        it, _, _ = p.solve(inc[0], y[0], tol=args.tol, max_iter=args.max_krylov)
+        seq_its.append(it)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    its, rrs, sts, _ = lib.bie_solve_many(plans, incs, ys, tol=args.tol, max_iter=args.max_krylov)
+    torch.cuda.synchronize()
+    t_conc = time.perf_counter() - t0
+    units = sum(4.0 * b.n * it[0] for b, it in zip(bodies, its))
+    res = {"mode": "uneven", "bodies": [{"n": b.n, "eps_r": round(b.eps_int, 3), "iters": it[0],
+                                         "relres": rr[0], "status": int(s)}
+                                        for b, it, rr, s in zip(bodies, its, rrs, sts)],
+           "setup_s": setup, "device_bytes": sum(p.stats()["device_bytes"] for p in plans),
+           "sequential_s": t_seq, "concurrent_s": t_conc, "speedup": t_seq / t_conc,
+           "concurrent_unknown_matvecs_per_s": units / t_conc, "sequential_iters": seq_its}
+    for p in plans:
+        p.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,7 +587,8 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven"])
+    ap.add_argument("--nbodies", type=int, default=16)
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--max-krylov", type=int, default=200)
@@ -554,6 +600,8 @@ def main():
         res = run_apply(args)
     elif args.mode == "batch":
         res = run_batch(args)
+    elif args.mode == "uneven":
+        res = run_uneven(args)
     else:
         res = run_gpu(args)
     if res is not None:

@@ -177,6 +177,23 @@ ifgf_status bie_solve(ifgf_plan plan, const void* inc, double tol, int32_t max_i
 ifgf_status bie_solve_batch(ifgf_plan plan, int32_t nrhs, const void* inc, double tol, int32_t max_iter,
                             void* y, int32_t* iters, double* relres, ifgf_stream stream);
 
+/*
+ * Uneven batch: independent solves on several plans (different bodies) at once.  Solve i is
+ * bie_solve_batch(plans[i], nrhs[i], incs[i], tol, max_iter, ys[i], iters[i], relres[i],
+ * streams[i]), each run from its own host thread so that the kernels of all solves share the
+ * device concurrently.  All arrays have nplans entries; iters[i] / relres[i] may be NULL (the
+ * outer arrays too).  The plans must be distinct and belong to the current device; streams[i]
+ * must be distinct, and a NULL entry (or a NULL streams array) makes the call create a
+ * non-blocking stream for that solve and destroy it before returning.  status[i] (HOST array,
+ * may be NULL) receives each solve's status.  Returns IFGF_OK if every solve reached tol,
+ * otherwise the first status other than IFGF_OK and IFGF_ENOCONV, otherwise IFGF_ENOCONV.
+ * Returns when all solves have finished.
+ */
+ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t* nrhs,
+                           const void* const* incs, double tol, int32_t max_iter, void* const* ys,
+                           int32_t* const* iters, double* const* relres, ifgf_status* status,
+                           const ifgf_stream* streams);
+
 /* Counts and sizes of a plan. */
 ifgf_status ifgf_plan_stats(ifgf_plan plan, ifgf_stats* st);
 

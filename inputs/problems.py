@@ -114,3 +114,21 @@ def fibonacci_incidences(x: np.ndarray, k_ext: float, omega: float, n_dirs: int 
         for p in (e1, e2):
             out.append(plane_wave(x, k_ext, omega, mu_ext, direction=d, polarization=p))
     return np.stack(out)
+
+
+def ellipsoid_batch(count: int = 16, seed: int = 3, nc: int = 10, wavelength: float = 1.0):
+    """The uneven batch of dielectric ellipsoids: semi-axes uniform in [0.5, 3] wavelengths,
+    eps_r uniform in [2, 12], ambient eps = 1; each cube face split s x s with s the smallest
+    number giving 8 nodes per interior wavelength along the longest quarter-ellipse, clipped
+    to [2, 6].  Returns a list of Problems."""
+    from .geometry import ellipsoid
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        axes = rng.uniform(0.5, 3.0, size=3) * wavelength
+        eps = float(rng.uniform(2.0, 12.0))
+        lam_i = wavelength / np.sqrt(eps)
+        s = int(np.clip(np.ceil(8.0 * (0.5 * np.pi * axes.max()) / (nc * lam_i)), 2, 6))
+        out.append(Problem(body=ellipsoid(tuple(axes), s), nc=nc, ng=max(2 * nc, 24), eps_ext=1.0,
+                           eps_int=eps, omega=2 * np.pi / wavelength, name=f"ellipsoid{i}"))
+    return out

@@ -22,7 +22,7 @@ IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
 IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 
 EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_batch", "ifgf_apply_fields",
-           "bie_solve", "bie_solve_batch",
+           "bie_solve", "bie_solve_batch", "bie_solve_many",
            "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
            "ifgf_tree_level", "ifgf_tree_targets", "ifgf_far_direct_noalloc"]
@@ -85,6 +85,10 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(ctypes.c_double), vp]
     lib.bie_solve_batch.argtypes = [vp, i32, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_double), vp]
+    lib.bie_solve_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.c_double,
+                                   i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.POINTER(i32)),
+                                   ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(i32),
+                                   ctypes.POINTER(vp)]
     lib.ifgf_plan_stats.argtypes = [vp, ctypes.POINTER(ifgf_stats)]
     lib.ifgf_set_timing.argtypes = [vp, i32]
     lib.ifgf_get_timing.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
@@ -193,6 +197,29 @@ def bie_solve_batch(plan, inc, tol: float, max_iter: int, y, stream=None):
     if st not in (IFGF_OK, IFGF_ENOCONV):
         raise IfgfError(st, "bie_solve_batch")
     return list(it), list(rr), st
+
+
+def bie_solve_many(plans, incs, ys, tol: float, max_iter: int, streams=None):
+    """Uneven batch: concurrent solves on several plans.  incs[i] [nrhs_i, 6, N_i] and
+    ys[i] [nrhs_i, 4, N_i] complex128 (host numpy or CUDA torch); streams: optional list of
+    distinct CUDA streams.  Returns (iterations per plan, residuals per plan, statuses, status)."""
+    n = len(plans)
+    vp = ctypes.c_void_p
+    nr = [int(a.shape[0]) for a in incs]
+    its = [(ctypes.c_int32 * k)() for k in nr]
+    rrs = [(ctypes.c_double * k)() for k in nr]
+    st = (ctypes.c_int32 * n)()
+    it_ptrs = (ctypes.POINTER(ctypes.c_int32) * n)(*[ctypes.cast(a, ctypes.POINTER(ctypes.c_int32)) for a in its])
+    rr_ptrs = (ctypes.POINTER(ctypes.c_double) * n)(*[ctypes.cast(a, ctypes.POINTER(ctypes.c_double)) for a in rrs])
+    strm = None
+    if streams is not None:
+        strm = (vp * n)(*[vp(int(getattr(s, "cuda_stream", s))) for s in streams])
+    status = load().bie_solve_many(n, (vp * n)(*[p.handle if hasattr(p, "handle") else p for p in plans]),
+                                   (ctypes.c_int32 * n)(*nr), (vp * n)(*[_addr(a) for a in incs]), float(tol),
+                                   int(max_iter), (vp * n)(*[_addr(a) for a in ys]), it_ptrs, rr_ptrs, st, strm)
+    if status not in (IFGF_OK, IFGF_ENOCONV):
+        raise IfgfError(status, "bie_solve_many")
+    return [list(a) for a in its], [list(a) for a in rrs], list(st), status
 
 
 def ifgf_plan_stats(plan) -> dict:

@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [nv, "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart"]
+    cmd = [nv, "-shared"] + ARCH + ["-o", tmp] + objs + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -6,6 +6,8 @@
 #include <mutex>
 #include <new>
 #include <stdexcept>
+#include <thread>
+#include <vector>
 
 #include "gmres.h"
 #include "host_setup.h"
@@ -529,6 +531,49 @@ ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double t
 ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter, void* y, int32_t* iters,
                       double* relres, ifgf_stream stream) {
   return bie_solve_batch(p, 1, inc, tol, max_iter, y, iters, relres, stream);
+}
+
+ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t* nrhs, const void* const* incs,
+                           double tol, int32_t max_iter, void* const* ys, int32_t* const* iters,
+                           double* const* relres, ifgf_status* status, const ifgf_stream* streams) {
+  if (nplans < 1 || !plans || !nrhs || !incs || !ys) return IFGF_EINVAL;
+  for (int i = 0; i < nplans; ++i) {
+    if (!plans[i] || !incs[i] || !ys[i]) return IFGF_EINVAL;
+    for (int j = 0; j < i; ++j) {
+      if (plans[j] == plans[i]) return IFGF_EINVAL;
+      if (streams && streams[i] && streams[j] == streams[i]) return IFGF_EINVAL;
+    }
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IFGF_ECUDA;
+  std::vector<ifgf_status> st(nplans, IFGF_OK);
+  std::vector<std::thread> workers;
+  workers.reserve(nplans);
+  for (int i = 0; i < nplans; ++i) {
+    workers.emplace_back([&, i]() {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        st[i] = IFGF_ECUDA;
+        return;
+      }
+      cudaStream_t s = streams ? (cudaStream_t)streams[i] : nullptr;
+      const bool own = (s == nullptr);
+      if (own && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        st[i] = IFGF_ECUDA;
+        return;
+      }
+      st[i] = bie_solve_batch(plans[i], nrhs[i], incs[i], tol, max_iter, ys[i], iters ? iters[i] : nullptr,
+                              relres ? relres[i] : nullptr, (ifgf_stream)s);
+      if (own) cudaStreamDestroy(s);
+    });
+  }
+  for (auto& w : workers) w.join();
+  ifgf_status out = IFGF_OK;
+  for (int i = 0; i < nplans; ++i) {
+    if (status) status[i] = st[i];
+    if (st[i] != IFGF_OK && st[i] != IFGF_ENOCONV && (out == IFGF_OK || out == IFGF_ENOCONV)) out = st[i];
+    else if (st[i] == IFGF_ENOCONV && out == IFGF_OK) out = IFGF_ENOCONV;
+  }
+  return out;
 }
 
 ifgf_status ifgf_plan_stats(ifgf_plan p, ifgf_stats* st) {

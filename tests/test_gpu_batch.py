@@ -66,3 +66,30 @@ def test_batch_limits():
     plan.apply_batch(y[:2].contiguous(), out[:2])           # within the limit
     torch.cuda.synchronize()
     plan.close()
+
+
+def test_uneven_batch_of_bodies_equals_separate_solves():
+    from inputs import ellipsoid
+    from inputs.problems import Problem
+    bodies = [Problem(body=ellipsoid((0.6, 0.45, 0.35), 1), nc=8, ng=24, eps_ext=1.0, eps_int=3.0, omega=2 * np.pi),
+              Problem(body=ellipsoid((0.8, 0.5, 0.5), 1), nc=8, ng=24, eps_ext=1.0, eps_int=6.0, omega=2 * np.pi),
+              CONFIG_SPHERE_SMALL(8)]
+    plans = [plan_of(b, precision=lib.IFGF_FP32, far_mode=lib.IFGF_FAR_IFGF, ns0=2, na0=3, max_krylov=150)
+             for b in bodies]
+    incs, ys = [], []
+    for b in bodies:
+        x, _, _ = b.nodes()
+        incs.append(torch.from_numpy(np.ascontiguousarray(plane_wave(x, b.k_ext, b.omega)[None])).cuda())
+        ys.append(torch.empty((1, 4, b.n), dtype=torch.complex128, device="cuda"))
+    its, rrs, sts, st = lib.bie_solve_many(plans, incs, ys, tol=1e-5, max_iter=150)
+    assert all(s in (lib.IFGF_OK, lib.IFGF_ENOCONV) for s in sts)
+    assert sts[2] == lib.IFGF_OK                             # the sphere converges well inside the cap
+    for i, (p, b) in enumerate(zip(plans, bodies)):
+        y1 = torch.empty((4, b.n), dtype=torch.complex128, device="cuda")
+        it, rr, s1 = p.solve(incs[i][0].contiguous(), y1, tol=1e-5, max_iter=150)
+        assert s1 == sts[i] and it == its[i][0] and rr == rrs[i][0]   # same solve, run concurrently
+        assert torch.equal(y1, ys[i][0])
+    with pytest.raises(lib.IfgfError):
+        lib.bie_solve_many([plans[0], plans[0]], incs[:1] * 2, ys[:1] * 2, tol=1e-6, max_iter=10)
+    for p in plans:
+        p.close()
