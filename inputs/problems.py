@@ -132,3 +132,21 @@ def ellipsoid_batch(count: int = 16, seed: int = 3, nc: int = 10, wavelength: fl
         out.append(Problem(body=ellipsoid(tuple(axes), s), nc=nc, ng=max(2 * nc, 24), eps_ext=1.0,
                            eps_int=eps, omega=2 * np.pi / wavelength, name=f"ellipsoid{i}"))
     return out
+
+
+def dipole_field(x: np.ndarray, k_ext: float, omega: float, r0, j, mu_ext: float = 1.0):
+    """Incident field of a point current j delta(x - r0) in the exterior medium (e^{-i omega t}):
+    E = i omega mu [g j + k^-2 (grad grad g) j], H = grad g x j, g = e^{i k R} / (4 pi R),
+    R = |x - r0|.  Returns [6, N] complex (Ex, Ey, Ez, Hx, Hy, Hz) at the points x [N, 3]."""
+    j = np.asarray(j, dtype=np.complex128)
+    d = np.asarray(x, dtype=np.float64) - np.asarray(r0, dtype=np.float64)[None, :]
+    R = np.linalg.norm(d, axis=1)
+    n = d / R[:, None]
+    k = k_ext
+    g = np.exp(1j * k * R) / (4 * np.pi * R)
+    nj = n @ j
+    ggj = g[:, None] * ((3 / R**2 - 3j * k / R - k * k)[:, None] * nj[:, None] * n +
+                        (1j * k / R - 1 / R**2)[:, None] * j[None, :])
+    E = 1j * omega * mu_ext * (g[:, None] * j[None, :] + ggj / (k * k))
+    H = (g * (1j * k - 1 / R))[:, None] * np.cross(n, j[None, :])
+    return np.concatenate([E.T, H.T], axis=0)

@@ -93,3 +93,24 @@ def test_uneven_batch_of_bodies_equals_separate_solves():
         lib.bie_solve_many([plans[0], plans[0]], incs[:1] * 2, ys[:1] * 2, tol=1e-6, max_iter=10)
     for p in plans:
         p.close()
+
+
+def test_dipole_reciprocity_on_the_gpu():
+    # point-current excitation, two right-hand sides in one batched solve on the plain FP64
+    # path: the reciprocity products equal the oracle's and meet the same bound
+    from test_oracle_solve import _reciprocity, oracle_solve, reciprocity_body
+    prob = reciprocity_body(10)
+    plan = plan_of(prob, precision=lib.IFGF_FP64, far_mode=lib.IFGF_FAR_DIRECT, batch=2, max_krylov=400)
+
+    def gpu_solve(incs):
+        inc = torch.from_numpy(np.ascontiguousarray(np.stack(incs))).cuda()
+        y = torch.empty((2, 4, prob.n), dtype=torch.complex128, device="cuda")
+        its, rrs, st = plan.solve_batch(inc, y, tol=1e-10, max_iter=400)
+        assert st == lib.IFGF_OK
+        return list(y.cpu().numpy())
+
+    a, b = _reciprocity(prob, gpu_solve)
+    ao, bo = _reciprocity(prob, oracle_solve(prob))
+    assert abs(a - ao) / abs(ao) < 1e-8 and abs(b - bo) / abs(bo) < 1e-8
+    assert abs(a - b) / abs(a) < 1e-2
+    plan.close()

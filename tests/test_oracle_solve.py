@@ -85,3 +85,48 @@ def test_dense_operator_solve_agrees_with_gmres(sphere_solution):
     yd = np.linalg.solve(A, b.reshape(-1))
     assert np.linalg.norm(yd - y.reshape(-1)) < 1e-8 * np.linalg.norm(yd)
     assert 10 <= it <= 60
+
+
+def _reciprocity(prob, solve):
+    """j2 . E^sc_1(r2) and j1 . E^sc_2(r1) for two point currents outside the body."""
+    from inputs import dipole_field
+    g = cbie.geometry_of(prob)
+    r1, j1 = np.array([0.9, 0.3, 0.2]), np.array([0.3, 1.0, -0.4j])
+    r2, j2 = np.array([-0.5, 0.7, -0.6]), np.array([1.0j, 0.2, 0.5])
+    incs = [dipole_field(g.x, prob.k_ext, prob.omega, r, j) for r, j in ((r1, j1), (r2, j2))]
+    y1, y2 = solve(incs)
+    E1, _ = cbie.fields_off_surface(prob, y1, r2[None], "ext")
+    E2, _ = cbie.fields_off_surface(prob, y2, r1[None], "ext")
+    return j2 @ E1[0], j1 @ E2[0]
+
+
+def reciprocity_body(nc):
+    from inputs import ellipsoid
+    from inputs.problems import Problem
+    return Problem(body=ellipsoid((0.6, 0.45, 0.35), 1), nc=nc, ng=24, eps_ext=1.0, eps_int=3.0, omega=2 * np.pi)
+
+
+def oracle_solve(prob):
+    qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=48)
+    op = cbie.build_operator(prob, qp)
+
+    def solve(incs):
+        out = []
+        for inc in incs:
+            b = cbie.rhs(prob, op.g, inc)
+            y, _, _ = cbie.gmres(lambda v: cbie.apply(op, v.reshape(4, -1)).reshape(-1), b.reshape(-1),
+                                 tol=1e-10, maxiter=400)
+            out.append(y.reshape(4, -1))
+        return out
+    return solve
+
+
+def test_dipole_reciprocity_converges():
+    # Lorentz reciprocity j2 . E1(r2) = j1 . E2(r1) holds for the exact fields; the discrete
+    # solution meets it to its discretisation error, which falls as the patches are refined
+    defects = []
+    for nc in (8, 10):
+        prob = reciprocity_body(nc)
+        a, b = _reciprocity(prob, oracle_solve(prob))
+        defects.append(abs(a - b) / abs(a))
+    assert defects[1] < 0.5 * defects[0] and defects[1] < 1e-2
