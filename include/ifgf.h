@@ -194,6 +194,44 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
                            int32_t* const* iters, double* const* relres, ifgf_status* status,
                            const ifgf_stream* streams);
 
+/*
+ * Learned right preconditioner for flexible GMRES (this library's addition; the paper
+ * solves with plain GMRES).  A two-layer network shared by all patches acts on each
+ * patch's unknowns: with v_p the 4 Nc^2 complex values of patch p (components
+ * m.t1, m.t2, j.t1, j.t2 of its nodes), read as in = 8 Nc^2 reals x (feature
+ * f = (c Nc^2 + q) 2 + ri: component c, node q of the patch, real/imaginary part) and
+ * s_p = |x|,   z_p = v_p + s_p (W2^T relu(W1^T x / s_p + b1) + b2).
+ * W1 [in][hidden], b1 [hidden], W2 [hidden][in], b2 [in] (row-major FP32 on the host);
+ * the device keeps FP32 master weights and BF16 copies, and the apply kernel accumulates
+ * in FP32.  All-zero W2 and b2 give z = v.
+ *
+ * ifgf_precond_attach: set (or replace) the weights, hidden in [1, 512]; the first call
+ *   allocates the weights and the flexible-GMRES basis (the plan's batch x its Krylov
+ *   capacity), a later call must keep `hidden`.  Synchronous.  It also restarts Adam.
+ * ifgf_precond_get: copy the FP32 master weights back (HOST arrays; any may be NULL).
+ * ifgf_precond_apply: z = M v for DEVICE [nrhs][4][N] complex128 v, z (not aliased).
+ * ifgf_precond_features: training pairs from DEVICE [nrhs][4][N] complex128 v and e
+ *   (v = A e): rows r P + p of the DEVICE FP32 arrays X, T [nrhs P][in] receive
+ *   x / s_p and (e_p - v_p) / s_p (zero rows for s_p = 0).
+ * ifgf_precond_train: `steps` Adam steps (beta 0.9, 0.999) on the mean squared error of
+ *   the network output against T over minibatches of `batch` rows of (X, T) (DEVICE FP32
+ *   [nsamples][in]) drawn with a counter-based generator from `seed`; the minibatch loss
+ *   before each step goes to `loss` (HOST [steps], may be NULL).  Allocates its scratch on
+ *   the first call (and when `batch` grows).  Synchronises `stream`.
+ * bie_solve_precond: as bie_solve_batch with flexible GMRES: z_k = M v_k, w = A z_k,
+ *   y = Z (H^-1 g); needs an attached network.
+ */
+ifgf_status ifgf_precond_attach(ifgf_plan plan, int32_t hidden, const float* W1, const float* b1, const float* W2,
+                                const float* b2);
+ifgf_status ifgf_precond_get(ifgf_plan plan, float* W1, float* b1, float* W2, float* b2);
+ifgf_status ifgf_precond_apply(ifgf_plan plan, int32_t nrhs, const void* v, void* z, ifgf_stream stream);
+ifgf_status ifgf_precond_features(ifgf_plan plan, int32_t nrhs, const void* v, const void* e, float* X, float* T,
+                                  ifgf_stream stream);
+ifgf_status ifgf_precond_train(ifgf_plan plan, int64_t nsamples, const float* X, const float* T, int32_t steps,
+                               int32_t batch, float lr, uint64_t seed, float* loss, ifgf_stream stream);
+ifgf_status bie_solve_precond(ifgf_plan plan, int32_t nrhs, const void* inc, double tol, int32_t max_iter,
+                              void* y, int32_t* iters, double* relres, ifgf_stream stream);
+
 /* Counts and sizes of a plan. */
 ifgf_status ifgf_plan_stats(ifgf_plan plan, ifgf_stats* st);
 

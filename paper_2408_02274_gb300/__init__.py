@@ -22,7 +22,8 @@ IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
 IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 
 EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_batch", "ifgf_apply_fields",
-           "bie_solve", "bie_solve_batch", "bie_solve_many",
+           "bie_solve", "bie_solve_batch", "bie_solve_many", "bie_solve_precond", "ifgf_precond_attach",
+           "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
            "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
            "ifgf_tree_level", "ifgf_tree_targets", "ifgf_far_direct_noalloc"]
@@ -85,6 +86,14 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(ctypes.c_double), vp]
     lib.bie_solve_batch.argtypes = [vp, i32, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_double), vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.bie_solve_precond.argtypes = [vp, i32, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
+                                      ctypes.POINTER(ctypes.c_double), vp]
+    lib.ifgf_precond_attach.argtypes = [vp, i32, fp, fp, fp, fp]
+    lib.ifgf_precond_get.argtypes = [vp, fp, fp, fp, fp]
+    lib.ifgf_precond_apply.argtypes = [vp, i32, vp, vp, vp]
+    lib.ifgf_precond_features.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.ifgf_precond_train.argtypes = [vp, ctypes.c_int64, vp, vp, i32, i32, ctypes.c_float, ctypes.c_uint64, fp, vp]
     lib.bie_solve_many.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(vp), ctypes.c_double,
                                    i32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.POINTER(i32)),
                                    ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(i32),
@@ -222,6 +231,73 @@ def bie_solve_many(plans, incs, ys, tol: float, max_iter: int, streams=None):
     return [list(a) for a in its], [list(a) for a in rrs], list(st), status
 
 
+def _f32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Preconditioner:
+    """The learned right preconditioner of a plan (ifgf_precond_*): per-patch two-layer
+    network, in = 8 Nc^2 features, `hidden` units."""
+
+    def __init__(self, plan, hidden=128, weights=None, seed=0):
+        self.plan = plan
+        self.hidden = hidden
+        self.n_in = 8 * plan.nc * plan.nc
+        if weights is None:   # small random first layer, zero output layer: z = v to start
+            rng = np.random.default_rng(seed)
+            weights = (rng.standard_normal((self.n_in, hidden)) * np.sqrt(2.0 / self.n_in),
+                       np.zeros(hidden), np.zeros((hidden, self.n_in)), np.zeros(self.n_in))
+        self.set(*weights)
+
+    def set(self, W1, b1, W2, b2):
+        arrs = [_f32(a) for a in (W1, b1, W2, b2)]
+        _check(load().ifgf_precond_attach(self.plan.handle, int(self.hidden), *[p for _, p in arrs]),
+               "ifgf_precond_attach")
+
+    def get(self):
+        W1 = np.zeros((self.n_in, self.hidden), np.float32)
+        b1 = np.zeros(self.hidden, np.float32)
+        W2 = np.zeros((self.hidden, self.n_in), np.float32)
+        b2 = np.zeros(self.n_in, np.float32)
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) for a in (W1, b1, W2, b2)]
+        _check(load().ifgf_precond_get(self.plan.handle, *ptrs), "ifgf_precond_get")
+        return W1, b1, W2, b2
+
+    def apply(self, v, z, stream=None):
+        """z = M v for torch complex128 CUDA tensors [nrhs, 4, N]."""
+        _check(load().ifgf_precond_apply(self.plan.handle, int(v.shape[0]), ctypes.c_void_p(v.data_ptr()),
+                                         ctypes.c_void_p(z.data_ptr()), _stream(stream)), "ifgf_precond_apply")
+
+    def features(self, v, e, X, T, stream=None):
+        """Per-patch training pairs from v = A e ([nrhs, 4, N] complex128 CUDA) into float32 CUDA
+        tensors X, T [nrhs * P, in]."""
+        _check(load().ifgf_precond_features(self.plan.handle, int(v.shape[0]), ctypes.c_void_p(v.data_ptr()),
+                                            ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                            ctypes.c_void_p(T.data_ptr()), _stream(stream)), "ifgf_precond_features")
+
+    def train(self, X, T, steps, batch=256, lr=1e-3, seed=1, stream=None):
+        """Adam on float32 CUDA tensors X, T [n, in]; returns the minibatch losses."""
+        loss = np.zeros(steps, np.float32)
+        _check(load().ifgf_precond_train(self.plan.handle, int(X.shape[0]), ctypes.c_void_p(X.data_ptr()),
+                                         ctypes.c_void_p(T.data_ptr()), int(steps), int(batch), float(lr),
+                                         int(seed), loss.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         _stream(stream)), "ifgf_precond_train")
+        return loss
+
+
+def bie_solve_precond(plan, inc, tol: float, max_iter: int, y, stream=None):
+    """Flexible GMRES with the attached preconditioner; as bie_solve_batch."""
+    nrhs = int(inc.shape[0])
+    it = (ctypes.c_int32 * nrhs)()
+    rr = (ctypes.c_double * nrhs)()
+    st = load().bie_solve_precond(plan, nrhs, _addr(inc), float(tol), int(max_iter), _addr(y), it, rr,
+                                  _stream(stream))
+    if st not in (IFGF_OK, IFGF_ENOCONV):
+        raise IfgfError(st, "bie_solve_precond")
+    return list(it), list(rr), st
+
+
 def ifgf_plan_stats(plan) -> dict:
     s = ifgf_stats()
     _check(load().ifgf_plan_stats(plan, ctypes.byref(s)), "ifgf_plan_stats")
@@ -355,6 +431,7 @@ class Plan:
     def __init__(self, nodes, dxdu, dxdv, fine, num_patches, nc, k_ext, k_int, eps_ext, eps_int,
                  mu_ext=1.0, mu_int=1.0, **kw):
         self.N = num_patches * nc * nc
+        self.nc, self.P = nc, num_patches
         self.handle = ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches, nc, k_ext, k_int, eps_ext,
                                        eps_int, mu_ext, mu_int, **kw)
 
@@ -372,6 +449,9 @@ class Plan:
 
     def solve_batch(self, inc, y, tol=1e-6, max_iter=300, stream=None):
         return bie_solve_batch(self.handle, inc, tol, max_iter, y, stream)
+
+    def solve_precond(self, inc, y, tol=1e-6, max_iter=300, stream=None):
+        return bie_solve_precond(self.handle, inc, tol, max_iter, y, stream)
 
     def fields(self, phi, f28, which=IFGF_PART_ALL, stream=None):
         ifgf_apply_fields(self.handle, phi, f28, which, stream)

@@ -485,9 +485,10 @@ ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t w
   return IFGF_OK;
 }
 
-ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
-                            int32_t* iters, double* relres, ifgf_stream stream) {
+static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
+                              int32_t* iters, double* relres, ifgf_stream stream, bool flexible) {
   if (!p || !inc || !y || !(tol > 0) || max_iter < 1) return IFGF_EINVAL;
+  if (flexible && p->pc.hidden == 0) return IFGF_EINVAL;
   if (nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
   if (max_iter > p->gm.max_iter) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
@@ -505,7 +506,10 @@ ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double t
   std::vector<double> rr(nrhs, 0.0);
   if (e == cudaSuccess) {
     MatvecFn mv = [p, nrhs](const double* v, double* w, cudaStream_t st) { return forward(p, v, w, nrhs, st); };
-    e = gmres_run(p, mv, nrhs, tol, max_iter, it.data(), rr.data(), s);
+    MatvecFn pc = [p, nrhs](const double* v, double* z, cudaStream_t st) {
+      return launch_mlp_apply(p, nrhs, v, z, st);
+    };
+    e = gmres_run(p, mv, nrhs, tol, max_iter, it.data(), rr.data(), s, flexible ? &pc : nullptr);
   }
   if (e == cudaSuccess) {
     if (is_device_ptr(y))
@@ -526,6 +530,146 @@ ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double t
     all = all && rr[r] <= tol;
   }
   return all ? IFGF_OK : IFGF_ENOCONV;
+}
+
+ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
+                            int32_t* iters, double* relres, ifgf_stream stream) {
+  return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, false);
+}
+
+ifgf_status bie_solve_precond(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
+                              int32_t* iters, double* relres, ifgf_stream stream) {
+  return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, true);
+}
+
+ifgf_status ifgf_precond_attach(ifgf_plan p, int32_t hidden, const float* W1, const float* b1, const float* W2,
+                                const float* b2) {
+  if (!p || hidden < 1 || hidden > 512 || !W1 || !b1 || !W2 || !b2) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  Precond& M = p->pc;
+  const int in = 8 * p->nc * p->nc;
+  if (M.hidden != 0 && M.hidden != hidden) return IFGF_EINVAL;
+  try {
+    Alloc A{p};
+    if (M.hidden == 0) {
+      M.in = in;
+      M.W1 = A.dev<float>((size_t)in * hidden);
+      M.b1 = A.dev<float>(hidden);
+      M.W2 = A.dev<float>((size_t)in * hidden);
+      M.b2 = A.dev<float>(in);
+      M.W1h = A.dev<uint16_t>((size_t)in * hidden);
+      M.W2h = A.dev<uint16_t>((size_t)in * hidden);
+      M.Z = A.dev<double>(2 * 4 * (size_t)p->N * (p->gm.max_iter + 1) * p->batch);
+    }
+    check(cudaMemcpy(M.W1, W1, sizeof(float) * in * hidden, cudaMemcpyHostToDevice), "weights");
+    check(cudaMemcpy(M.b1, b1, sizeof(float) * hidden, cudaMemcpyHostToDevice), "weights");
+    check(cudaMemcpy(M.W2, W2, sizeof(float) * in * hidden, cudaMemcpyHostToDevice), "weights");
+    check(cudaMemcpy(M.b2, b2, sizeof(float) * in, cudaMemcpyHostToDevice), "weights");
+    M.hidden = hidden;
+    M.adam_t = 0;
+    if (M.tw.batch > 0) {   // restart the optimiser
+      check(cudaMemset(M.tw.mW1, 0, sizeof(float) * in * hidden), "adam");
+      check(cudaMemset(M.tw.vW1, 0, sizeof(float) * in * hidden), "adam");
+      check(cudaMemset(M.tw.mW2, 0, sizeof(float) * in * hidden), "adam");
+      check(cudaMemset(M.tw.vW2, 0, sizeof(float) * in * hidden), "adam");
+      check(cudaMemset(M.tw.mb1, 0, sizeof(float) * hidden), "adam");
+      check(cudaMemset(M.tw.vb1, 0, sizeof(float) * hidden), "adam");
+      check(cudaMemset(M.tw.mb2, 0, sizeof(float) * in), "adam");
+      check(cudaMemset(M.tw.vb2, 0, sizeof(float) * in), "adam");
+    }
+    check(mlp_refresh_bf16(p, nullptr), "bf16 weights");
+    check(cudaDeviceSynchronize(), "precond attach");
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  } catch (const std::exception&) {
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_precond_get(ifgf_plan p, float* W1, float* b1, float* W2, float* b2) {
+  if (!p || p->pc.hidden == 0) return IFGF_EINVAL;
+  const Precond& M = p->pc;
+  const size_t n1 = (size_t)M.in * M.hidden;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && W1) e = cudaMemcpy(W1, M.W1, sizeof(float) * n1, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && b1) e = cudaMemcpy(b1, M.b1, sizeof(float) * M.hidden, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && W2) e = cudaMemcpy(W2, M.W2, sizeof(float) * n1, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && b2) e = cudaMemcpy(b2, M.b2, sizeof(float) * M.in, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_precond_get", __FILE__, __LINE__);
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_precond_apply(ifgf_plan p, int32_t nrhs, const void* v, void* z, ifgf_stream stream) {
+  if (!p || !v || !z || v == z || p->pc.hidden == 0 || nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaError_t e = launch_mlp_apply(p, nrhs, (const double*)v, (double*)z, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_precond_apply", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_precond_features(ifgf_plan p, int32_t nrhs, const void* v, const void* e, float* X, float* T,
+                                  ifgf_stream stream) {
+  if (!p || !v || !e || !X || !T || p->pc.hidden == 0 || nrhs < 1) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaError_t err = launch_mlp_features(p, nrhs, (const double*)v, (const double*)e, X, T, (cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    set_last_cuda_error(err, "ifgf_precond_features", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_precond_train(ifgf_plan p, int64_t nsamples, const float* X, const float* T, int32_t steps,
+                               int32_t batch, float lr, uint64_t seed, float* loss, ifgf_stream stream) {
+  if (!p || !X || !T || nsamples < 1 || steps < 1 || batch < 1 || batch > 65535 || !(lr > 0)) return IFGF_EINVAL;
+  if (p->pc.hidden == 0) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  Precond& M = p->pc;
+  TrainWork& W = M.tw;
+  const int in = M.in, H = M.hidden;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    Alloc A{p};
+    if (W.batch == 0) {   // optimiser state and gradients: sized by the network
+      const size_t n1 = (size_t)in * H;
+      W.gW1 = A.dev<float>(n1); W.gW2 = A.dev<float>(n1); W.gb1 = A.dev<float>(H); W.gb2 = A.dev<float>(in);
+      W.mW1 = A.dev<float>(n1); W.vW1 = A.dev<float>(n1); W.mW2 = A.dev<float>(n1); W.vW2 = A.dev<float>(n1);
+      W.mb1 = A.dev<float>(H); W.vb1 = A.dev<float>(H); W.mb2 = A.dev<float>(in); W.vb2 = A.dev<float>(in);
+      for (float* a : {W.mW1, W.vW1, W.mW2, W.vW2}) check(cudaMemset(a, 0, sizeof(float) * n1), "adam");
+      for (float* a : {W.mb1, W.vb1}) check(cudaMemset(a, 0, sizeof(float) * H), "adam");
+      for (float* a : {W.mb2, W.vb2}) check(cudaMemset(a, 0, sizeof(float) * in), "adam");
+    }
+    if (batch > W.batch) {   // minibatch scratch (grows, never shrinks)
+      W.Xb = A.dev<float>((size_t)batch * in); W.Tb = A.dev<float>((size_t)batch * in);
+      W.Y = A.dev<float>((size_t)batch * in); W.dY = A.dev<float>((size_t)batch * in);
+      W.Hpre = A.dev<float>((size_t)batch * H); W.H1 = A.dev<float>((size_t)batch * H);
+      W.dH = A.dev<float>((size_t)batch * H);
+      W.batch = batch;
+    }
+    if (steps > M.loss_cap) {
+      M.loss = A.dev<float>(steps);
+      M.loss_cap = steps;
+    }
+    check(cudaMemsetAsync(M.loss, 0, sizeof(float) * steps, s), "loss");
+    check(mlp_train(p, nsamples, X, T, steps, batch, lr, seed, M.loss, s), "training");
+    if (loss) check(cudaMemcpyAsync(loss, M.loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, s), "loss");
+    check(cudaStreamSynchronize(s), "training");
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  } catch (const std::exception&) {
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
 }
 
 ifgf_status bie_solve(ifgf_plan p, const void* inc, double tol, int32_t max_iter, void* y, int32_t* iters,

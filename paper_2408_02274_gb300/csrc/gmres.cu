@@ -304,7 +304,7 @@ cudaError_t project(GmresWork& G, const Batch& B, const Arnoldi& R, int k1, int 
 }  // namespace
 
 cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, int nrhs, double tol, int max_iter, int* iters,
-                      double* relres, cudaStream_t s) {
+                      double* relres, cudaStream_t s, const MatvecFn* precond) {
   GmresWork& G = p->gm;
   const int64_t n = 4 * (int64_t)p->N;
   const int ldh = G.max_iter + 1;
@@ -335,8 +335,16 @@ cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, int nrhs, double t
     return err;
   int k = 0;
   for (k = 0; k < max_iter && nactive > 0; ++k) {
-    // w_rb = A v_{k,rb} for all right-hand sides in one batched forward map
-    if ((err = matvec(G.V + 2 * (size_t)k * B.ldv, G.w, s)) != cudaSuccess) return err;
+    // w_rb = A v_{k,rb} (flexible: w_rb = A z_{k,rb}, z = M v) for all right-hand sides in one
+    // batched forward map
+    const double* vk = G.V + 2 * (size_t)k * B.ldv;
+    if (precond) {
+      double* zk = p->pc.Z + 2 * (size_t)k * B.ldv;
+      if ((err = (*precond)(vk, zk, s)) != cudaSuccess) return err;
+      vk = zk;
+      ++p->launches;
+    }
+    if ((err = matvec(vk, G.w, s)) != cudaSuccess) return err;
     const int rec = timer_begin(p, TK_GMRES, s);
     // CGS2: two projection passes, h = h1 + h2
     if ((err = project(G, B, R, k + 1, 1, s)) != cudaSuccess) return err;
@@ -369,7 +377,7 @@ cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, int nrhs, double t
   }
   if ((err = cudaMemcpyAsync(G.kfin, G.hk, sizeof(int) * nrhs, cudaMemcpyHostToDevice, s)) != cudaSuccess) return err;
   k_backsub<<<nrhs, 32, 0, s>>>(G.kfin, ldh, R);
-  k_combo<<<dim3(vblocks, nrhs), 256, 0, s>>>(n, 0, G.kfin, G.V, B.ldv, R.h, R.sh, G.y, 1);
+  k_combo<<<dim3(vblocks, nrhs), 256, 0, s>>>(n, 0, G.kfin, precond ? p->pc.Z : G.V, B.ldv, R.h, R.sh, G.y, 1);
   p->launches += 2;
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   for (int r = 0; r < nrhs; ++r) iters[r] = G.hk[r];

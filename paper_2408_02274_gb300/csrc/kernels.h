@@ -56,6 +56,14 @@ int timer_begin(ifgf_plan_t* p, int kind, cudaStream_t s);   // -1 when timing i
 void timer_end(ifgf_plan_t* p, int rec, cudaStream_t s);
 cudaError_t timer_flush(ifgf_plan_t* p);
 
+// ---- learned preconditioner (precond.cu)
+cudaError_t launch_mlp_apply(const ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s);
+cudaError_t launch_mlp_features(const ifgf_plan_t* p, int nrhs, const double* v, const double* e, float* X, float* T,
+                                cudaStream_t s);
+cudaError_t mlp_refresh_bf16(ifgf_plan_t* p, cudaStream_t s);
+cudaError_t mlp_train(ifgf_plan_t* p, int64_t nsamples, const float* X, const float* T, int steps, int batch, float lr,
+                      uint64_t seed, float* loss, cudaStream_t s);
+
 // ---- GMRES helpers (gmres.cu)
 cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s, int nrhs = 1);
 

@@ -119,6 +119,25 @@ struct GmresWork {               // per right-hand side r < batch (layouts below
   int* hk = nullptr;            // pinned host [batch]
 };
 
+// Learned right preconditioner: per-patch two-layer network (precond.cu).
+struct TrainWork {              // minibatch scratch, allocated by the first training call
+  int batch = 0;
+  float *Xb = nullptr, *Tb = nullptr, *Hpre = nullptr, *H1 = nullptr, *Y = nullptr, *dY = nullptr, *dH = nullptr;
+  float *gW1 = nullptr, *gb1 = nullptr, *gW2 = nullptr, *gb2 = nullptr;
+  float *mW1 = nullptr, *vW1 = nullptr, *mb1 = nullptr, *vb1 = nullptr;   // Adam moments
+  float *mW2 = nullptr, *vW2 = nullptr, *mb2 = nullptr, *vb2 = nullptr;
+};
+struct Precond {
+  int hidden = 0, in = 0;       // in = 8 Nc^2 real features per patch
+  int adam_t = 0;
+  float *W1 = nullptr, *b1 = nullptr, *W2 = nullptr, *b2 = nullptr;   // FP32 master weights [in][H], [H], [H][in], [in]
+  void *W1h = nullptr, *W2h = nullptr;   // BF16 copies used when applying the preconditioner
+  double* Z = nullptr;          // flexible GMRES basis [max_iter+1][batch][4N][2]
+  float* loss = nullptr;        // training losses of the last call (device)
+  int loss_cap = 0;
+  TrainWork tw;
+};
+
 // Per-kernel-kind CUDA-event timing of the per-apply work (optional).
 enum TimedKind { TK_PREP = 0, TK_NEAR, TK_LEAF, TK_UP, TK_TARGET, TK_COMBINE, TK_FAR_DIRECT, TK_GMRES, TK_COUNT };
 struct KernelTimer {
@@ -160,6 +179,7 @@ struct ifgf_plan_t {
   void* f28 = nullptr;          // [batch][N][28][2] scalar fields (plan precision)
   double* phi64 = nullptr;      // [batch][N][8][2] FP64 densities (prep output)
   ifgf::GmresWork gm;
+  ifgf::Precond pc;             // hidden == 0: no preconditioner attached
   ifgf_stats stats{};
   std::vector<void*> allocations;
 };
