@@ -578,6 +578,103 @@ def run_uneven(args):
     return res
 
 
+def run_precond(args):
+    """Learned right preconditioner: train the per-patch network on (v = A e, e) pairs from
+    plain GMRES on random star-shaped bodies (e = converged minus truncated iterates, plus
+    random fields), then compare plain GMRES and flexible GMRES on held-out bodies."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import plane_wave, random_densities, star_batch
+    libbuild.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(17)
+    H = 128
+
+    def plan_for(b, batch=2):
+        return lib.Plan.from_problem(b, delta=delta_of(b), n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                     far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, batch=batch,
+                                     max_krylov=args.max_krylov)
+
+    def incidences(b, n):
+        x, _, _ = b.nodes()
+        out = []
+        for _ in range(n):
+            d = rng.standard_normal(3)
+            d /= np.linalg.norm(d)
+            p = np.cross(d, rng.standard_normal(3))
+            p /= np.linalg.norm(p)
+            out.append(plane_wave(x, b.k_ext, b.omega, direction=d, polarization=p))
+        return torch.from_numpy(np.ascontiguousarray(np.stack(out))).cuda()
+
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    train = star_batch(args.ntrain, seed=1000)
+    for b in train:
+        plan = plan_for(b)
+        pc = lib.Preconditioner(plan, hidden=H)                 # used for its feature kernel only
+        inc = incidences(b, 2)
+        ystar = torch.empty((2, 4, b.n), dtype=torch.complex128, device="cuda")
+        plan.solve_batch(inc, ystar, tol=1e-6, max_iter=args.max_krylov)
+        errs = []
+        for k in (3, 6, 12, 24, 48):
+            yk = torch.empty_like(ystar)
+            plan.solve_batch(inc, yk, tol=1e-12, max_iter=k)
+            errs.append(ystar - yk)
+        errs.append(torch.from_numpy(np.stack([random_densities(b.n, 7 * len(Xs) + r) for r in range(2)])).cuda())
+        for e in errs:
+            e = e.contiguous()
+            v = torch.empty_like(e)
+            plan.apply_batch(e, v)
+            X = torch.empty((2 * b.num_patches, pc.n_in), dtype=torch.float32, device="cuda")
+            T = torch.empty_like(X)
+            pc.features(v, e, X, T)
+            Xs.append(X)
+            Ts.append(T)
+        plan.close()
+    X = torch.cat(Xs)
+    T = torch.cat(Ts)
+    t_data = time.perf_counter() - t0
+    # train on the first test plan's preconditioner (the weights are plan-independent)
+    test = star_batch(args.ntest, seed=5000)
+    plans = [plan_for(b, batch=1) for b in test]
+    pc0 = lib.Preconditioner(plans[0], hidden=H, seed=2)
+    t0 = time.perf_counter()
+    loss = pc0.train(X, T, steps=args.train_steps, batch=512, lr=1e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    weights = pc0.get()
+    rows = []
+    for b, plan in zip(test, plans):
+        if plan is not plans[0]:
+            lib.Preconditioner(plan, hidden=H, weights=weights)
+        inc = incidences(b, 1)
+        x, _, _ = b.nodes()
+        res = {"n": b.n, "eps_r": round(b.eps_int, 3)}
+        for name, fn in (("gmres", plan.solve_batch), ("fgmres", plan.solve_precond)):
+            y = torch.empty((1, 4, b.n), dtype=torch.complex128, device="cuda")
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            its, rrs, st = fn(inc, y, tol=args.tol, max_iter=args.max_krylov)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t1
+            # true residual |b - A y| / |b| with the plan's forward map and right-hand side
+            Ay = torch.empty_like(y)
+            plan.apply_batch(y, Ay)
+            bb = torch.empty_like(y)
+            plan.rhs(inc, bb)
+            torch.cuda.synchronize()
+            true_res = float(torch.linalg.norm(bb - Ay) / torch.linalg.norm(bb))
+            res[name] = {"iters": its[0], "relres_estimate": rrs[0], "true_relres": true_res, "status": int(st),
+                         "seconds": dt}
+        rows.append(res)
+    for p in plans:
+        p.close()
+    return {"mode": "precond", "train_bodies": args.ntrain, "samples": int(X.shape[0]), "hidden": H,
+            "data_s": t_data, "train_s": t_train, "train_steps": args.train_steps,
+            "loss_first": float(loss[:50].mean()), "loss_last": float(loss[-50:].mean()), "tol": args.tol,
+            "test": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -587,7 +684,10 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven", "precond"])
+    ap.add_argument("--ntrain", type=int, default=8)
+    ap.add_argument("--ntest", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--nbodies", type=int, default=16)
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--solve", action="store_true")
@@ -602,6 +702,8 @@ def main():
         res = run_batch(args)
     elif args.mode == "uneven":
         res = run_uneven(args)
+    elif args.mode == "precond":
+        res = run_precond(args)
     else:
         res = run_gpu(args)
     if res is not None:

@@ -195,6 +195,13 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
                            const ifgf_stream* streams);
 
 /*
+ * Right-hand side of Eq. lin_system: b_r = omega^{-1} (n x E^inc_r, n x H^inc_r) projected on
+ * (t1, t2) for r < nrhs.  inc: DEVICE [nrhs][6][N] complex128, b: DEVICE [nrhs][4][N]
+ * complex128 (the vector bie_solve solves for).  Asynchronous on `stream`.
+ */
+ifgf_status bie_rhs(ifgf_plan plan, int32_t nrhs, const void* inc, void* b, ifgf_stream stream);
+
+/*
  * Learned right preconditioner for flexible GMRES (this library's addition; the paper
  * solves with plain GMRES).  A two-layer network shared by all patches acts on each
  * patch's unknowns: with v_p the 4 Nc^2 complex values of patch p (components

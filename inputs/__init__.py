@@ -11,8 +11,8 @@ from .geometry import (Body, cubed_sphere, ellipsoid, star_body, superellipsoid_
                        open_cheb_nodes, sample_body)
 from .problems import (Problem, sphere_problem, CONFIG_SPHERE_SMALL, CONFIG_SPHERE_MEDIUM,
                        random_densities, plane_wave, fibonacci_incidences, ellipsoid_batch,
-                       dipole_field)
+                       dipole_field, star_batch)
 
-__all__ = ["dipole_field", "ellipsoid_batch", "fibonacci_incidences", "Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar",
+__all__ = ["star_batch", "dipole_field", "ellipsoid_batch", "fibonacci_incidences", "Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar",
            "open_cheb_nodes", "sample_body", "Problem", "sphere_problem",
            "CONFIG_SPHERE_SMALL", "CONFIG_SPHERE_MEDIUM", "random_densities", "plane_wave"]

@@ -150,3 +150,19 @@ def dipole_field(x: np.ndarray, k_ext: float, omega: float, r0, j, mu_ext: float
     E = 1j * omega * mu_ext * (g[:, None] * j[None, :] + ggj / (k * k))
     H = (g * (1j * k - 1 / R))[:, None] * np.cross(n, j[None, :])
     return np.concatenate([E.T, H.T], axis=0)
+
+
+def star_batch(count: int, seed: int, radius: float = 0.75, split: int = 4, nc: int = 8,
+               eps_range=(2.0, 12.0), wavelength: float = 1.0):
+    """Random star-shaped dielectric bodies r(w) = a (1 + sum_{1<=l<=4} c_lm Y_lm(w)) with
+    c_lm ~ N(0, 0.03^2) and eps_r uniform in eps_range, ambient eps = 1, cube faces split
+    split x split.  Returns a list of Problems."""
+    from .geometry import star_body
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        coeffs = {(l, m): 0.03 * rng.standard_normal() for l in range(1, 5) for m in range(-l, l + 1)}
+        eps = float(rng.uniform(*eps_range))
+        out.append(Problem(body=star_body(radius * wavelength, coeffs, split), nc=nc, ng=max(2 * nc, 24),
+                           eps_ext=1.0, eps_int=eps, omega=2 * np.pi / wavelength, name=f"star{seed}_{i}"))
+    return out

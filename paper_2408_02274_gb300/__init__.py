@@ -22,7 +22,7 @@ IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
 IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 
 EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_batch", "ifgf_apply_fields",
-           "bie_solve", "bie_solve_batch", "bie_solve_many", "bie_solve_precond", "ifgf_precond_attach",
+           "bie_solve", "bie_solve_batch", "bie_solve_many", "bie_solve_precond", "bie_rhs", "ifgf_precond_attach",
            "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
            "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
     lib.bie_solve_precond.argtypes = [vp, i32, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
                                       ctypes.POINTER(ctypes.c_double), vp]
     lib.ifgf_precond_attach.argtypes = [vp, i32, fp, fp, fp, fp]
+    lib.bie_rhs.argtypes = [vp, i32, vp, vp, vp]
     lib.ifgf_precond_get.argtypes = [vp, fp, fp, fp, fp]
     lib.ifgf_precond_apply.argtypes = [vp, i32, vp, vp, vp]
     lib.ifgf_precond_features.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -452,6 +453,11 @@ class Plan:
 
     def solve_precond(self, inc, y, tol=1e-6, max_iter=300, stream=None):
         return bie_solve_precond(self.handle, inc, tol, max_iter, y, stream)
+
+    def rhs(self, inc, b, stream=None):
+        """b = right-hand side of the solve for CUDA tensors inc [nrhs, 6, N], b [nrhs, 4, N]."""
+        _check(load().bie_rhs(self.handle, int(inc.shape[0]), ctypes.c_void_p(inc.data_ptr()),
+                              ctypes.c_void_p(b.data_ptr()), _stream(stream)), "bie_rhs")
 
     def fields(self, phi, f28, which=IFGF_PART_ALL, stream=None):
         ifgf_apply_fields(self.handle, phi, f28, which, stream)

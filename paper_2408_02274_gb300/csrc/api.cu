@@ -532,6 +532,18 @@ static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double
   return all ? IFGF_OK : IFGF_ENOCONV;
 }
 
+ifgf_status bie_rhs(ifgf_plan p, int32_t nrhs, const void* inc, void* b, ifgf_stream stream) {
+  if (!p || !inc || !b || nrhs < 1) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaError_t e = launch_rhs(p, (const double*)inc, (double*)b, (cudaStream_t)stream, nrhs);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "bie_rhs", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
 ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
                             int32_t* iters, double* relres, ifgf_stream stream) {
   return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, false);
