@@ -675,6 +675,52 @@ def run_precond(args):
             "test": rows}
 
 
+def run_compare(args):
+    """Mixed precision against the plain FP64 GPU method at equal tolerance: the same
+    right-hand side solved with the FP32 IFGF forward map, the FP64 IFGF forward map and the
+    FP64 direct far sum (the unaccelerated operator on the GPU); the true residual of every
+    solution is measured with the FP64 direct operator."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import plane_wave
+    libbuild.build()
+    torch.cuda.set_device(0)
+    prob = problem(args.workload)
+    N = prob.n
+    delta = delta_of(prob)
+    x, _, _ = prob.nodes()
+    inc = torch.from_numpy(np.ascontiguousarray(plane_wave(x, prob.k_ext, prob.omega)[None])).cuda()
+    ref = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP64,
+                                far_mode=lib.IFGF_FAR_DIRECT, max_krylov=args.max_krylov)
+    b = torch.empty((1, 4, N), dtype=torch.complex128, device="cuda")
+    ref.rhs(inc, b)
+    rows = {}
+    for name, prec, far in (("ifgf_fp32", lib.IFGF_FP32, lib.IFGF_FAR_IFGF), ("ifgf_fp64", lib.IFGF_FP64, lib.IFGF_FAR_IFGF),
+                            ("direct_fp64", lib.IFGF_FP64, lib.IFGF_FAR_DIRECT)):
+        plan = ref if name == "direct_fp64" else lib.Plan.from_problem(
+            prob, delta=delta, n_beta=48, cov_d=4.0, precision=prec, far_mode=far, ns0=NS0, na0=NA0,
+            max_krylov=args.max_krylov)
+        y = torch.empty((1, 4, N), dtype=torch.complex128, device="cuda")
+        plan.solve_batch(inc, y, tol=args.tol, max_iter=args.max_krylov)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rrs, st = plan.solve_batch(inc, y, tol=args.tol, max_iter=args.max_krylov)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        Ay = torch.empty_like(y)
+        ref.apply_batch(y, Ay)
+        torch.cuda.synchronize()
+        rows[name] = {"iters": its[0], "seconds": dt, "relres_estimate": rrs[0], "status": int(st),
+                      "true_relres_fp64_direct": float(torch.linalg.norm(b - Ay) / torch.linalg.norm(b)),
+                      "unknown_matvecs_per_s": 4.0 * N * its[0] / dt}
+        if plan is not ref:
+            plan.close()
+    ref.close()
+    rows["speedup_ifgf_fp32_vs_direct_fp64"] = rows["direct_fp64"]["seconds"] / rows["ifgf_fp32"]["seconds"]
+    return {"mode": "compare", "workload": WORKLOADS[args.workload], "tol": args.tol, **rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -684,7 +730,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven", "precond"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven", "precond", "compare"])
     ap.add_argument("--ntrain", type=int, default=8)
     ap.add_argument("--ntest", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=3000)
@@ -704,6 +750,8 @@ def main():
         res = run_uneven(args)
     elif args.mode == "precond":
         res = run_precond(args)
+    elif args.mode == "compare":
+        res = run_compare(args)
     else:
         res = run_gpu(args)
     if res is not None:
