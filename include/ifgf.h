@@ -83,6 +83,8 @@ typedef struct {
   int32_t batch;           /* right-hand sides one batched call may carry (ifgf_apply_batch,
                               bie_solve_batch): the per-apply buffers, cone coefficients and GMRES
                               workspace are allocated this many times (0 -> 1, <= 1024) */
+  int32_t max_leaf_pts;    /* point-count leaf rule: deepen the octree until no leaf box holds
+                              more nodes (0 -> off; thin bodies need it); <= 1e6 */
 } ifgf_plan_desc;
 
 /* Counts describing a plan (ifgf_plan_stats). */

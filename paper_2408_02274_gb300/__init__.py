@@ -42,7 +42,7 @@ class ifgf_plan_desc(ctypes.Structure):
         ("leaf_size", ctypes.c_double), ("min_levels", ctypes.c_int32),
         ("delta", ctypes.c_double), ("n_beta", ctypes.c_int32), ("cov_d", ctypes.c_double),
         ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
-        ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32),
+        ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_leaf_pts", ctypes.c_int32),
     ]
 
 
@@ -142,14 +142,15 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                      gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
-                     max_krylov: int = 0, batch: int = 0):
+                     max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     ng = int(arrs[3].shape[1])
     d = ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
                        k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
-                       min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch)
+                       min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
+                       max_leaf_pts)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h

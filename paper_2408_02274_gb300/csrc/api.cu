@@ -50,6 +50,35 @@ struct Alloc {
   }
 };
 
+// Device arrays needed only while a plan is being built (candidate pairs, closest points,
+// singular moments, fine-geometry coefficients ...): freed when the builder returns, so they
+// neither stay on the device nor count in the plan's device_bytes.
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* q : ptrs) cudaFree(q);
+  }
+  template <typename T>
+  T* dev(size_t count) {
+    if (count == 0) count = 1;
+    void* ptr = nullptr;
+    if (cudaMalloc(&ptr, count * sizeof(T)) != cudaSuccess) throw std::bad_alloc();
+    ptrs.push_back(ptr);
+    return static_cast<T*>(ptr);
+  }
+  template <typename T>
+  T* upload(const T* v, size_t count) {
+    T* d = dev<T>(count);
+    if (count && cudaMemcpy(d, v, count * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+      throw std::runtime_error("cudaMemcpy H2D failed");
+    return d;
+  }
+  template <typename T>
+  T* upload(const std::vector<T>& v) {
+    return upload(v.data(), v.size());
+  }
+};
+
 void free_all(ifgf_plan_t* p) {
   for (void* a : p->allocations) cudaFree(a);
   p->allocations.clear();
@@ -86,6 +115,7 @@ ifgf_status validate(const ifgf_plan_desc* d) {
   if (d->far_mode != IFGF_FAR_IFGF && d->far_mode != IFGF_FAR_DIRECT) return IFGF_EINVAL;
   if (d->max_krylov < 0 || d->max_krylov > 1000) return IFGF_EINVAL;
   if (d->batch < 0 || d->batch > 1024) return IFGF_EINVAL;
+  if (d->max_leaf_pts < 0 || d->max_leaf_pts > 1000000) return IFGF_EINVAL;
   if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
   if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
   return IFGF_OK;
@@ -94,13 +124,14 @@ ifgf_status validate(const ifgf_plan_desc* d) {
 void build(ifgf_plan_t* p) {
   const ifgf_plan_desc& d = p->desc;
   Alloc A{p};
+  Scratch S;   // setup-only arrays
   const int N = p->N, P = p->P, nc = p->nc, ng = p->ng, npp = nc * nc;
   check(cudaGetDevice(&p->device), "cudaGetDevice");
   check(cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device), "attr");
   // ---------------- host octree and cone segments
   double leaf = d.leaf_size > 0 ? d.leaf_size : 0.25 * 2.0 * kPi / d.k_ext;
   double kmax = std::max(d.k_ext, d.k_int);
-  build_tree(p->tree, d.nodes, N, leaf, d.min_levels > 0 ? d.min_levels : 3, kmax, d.ns0, d.na0);
+  build_tree(p->tree, d.nodes, N, leaf, d.min_levels > 0 ? d.min_levels : 3, kmax, d.ns0, d.na0, d.max_leaf_pts);
   const HostTree& t = p->tree;
   // ---------------- node geometry
   p->geo.x = A.upload(d.nodes, 3 * (size_t)N);
@@ -112,19 +143,19 @@ void build(ifgf_plan_t* p) {
   p->geo.J = A.dev<double>(N);
   p->geo.w = A.dev<double>(N);
   p->geo.g = A.dev<double>(3 * (size_t)N);
-  double* fej = A.dev<double>(nc);
-  double* Anc = A.dev<double>(npp);
+  double* fej = S.dev<double>(nc);
+  double* Anc = S.dev<double>(npp);
   p->tab_D = A.dev<double>(npp);
   k_cheb_tables<<<(npp + 127) / 128, 128>>>(nc, fej, Anc, p->tab_D);
   k_node_geom<<<(N + 127) / 128, 128>>>(N, nc, fej, p->geo);
-  double* Ang = A.dev<double>((size_t)ng * ng);
+  double* Ang = S.dev<double>((size_t)ng * ng);
   k_cheb_tables<<<(ng * ng + 127) / 128, 128>>>(ng, nullptr, Ang, nullptr);
-  double* fine = A.upload(d.fine, (size_t)P * ng * ng * 9);
-  double* fcoef = A.dev<double>((size_t)P * ng * ng * 9);
+  double* fine = S.upload(d.fine, (size_t)P * ng * ng * 9);
+  double* fcoef = S.dev<double>((size_t)P * ng * ng * 9);
   k_fine_coefs<<<P, 256>>>(ng, Ang, fine, fcoef);
   double* unodes_h = new double[nc];
   for (int k = 0; k < nc; ++k) unodes_h[k] = cheb_node(k, nc);
-  double* unodes = A.upload(unodes_h, nc);
+  double* unodes = S.upload(unodes_h, nc);
   delete[] unodes_h;
   check(cudaGetLastError(), "geometry kernels");
   // sorted geometry, permutations, leaf coordinates
@@ -161,10 +192,10 @@ void build(ifgf_plan_t* p) {
     std::vector<int> ptgt(npairs);
     for (int l = 0; l < N; ++l)
       for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) ptgt[e] = l;
-    int* d_ptgt = A.upload(ptgt);
-    int* d_ppatch = A.upload(cpatch);
-    double* d_uv = A.dev<double>(2 * (size_t)npairs);
-    uint8_t* d_sing = A.dev<uint8_t>(npairs);
+    int* d_ptgt = S.upload(ptgt);
+    int* d_ppatch = S.upload(cpatch);
+    double* d_uv = S.dev<double>(2 * (size_t)npairs);
+    uint8_t* d_sing = S.dev<uint8_t>(npairs);
     int iters = d.gs_iters > 0 ? d.gs_iters : 60;
     k_closest<<<(npairs + 127) / 128, 128>>>(npairs, nc, ng, iters, d.delta, d_ptgt, d_ppatch, p->geo.x,
                                              fcoef, unodes, d_uv, d_sing);
@@ -179,13 +210,13 @@ void build(ifgf_plan_t* p) {
       }
     const int nsp = (int)sp_pair.size();
     p->stats.singular_pairs = nsp;
-    int* d_sp_pair = A.upload(sp_pair);
-    int* d_sp_of = A.upload(sp_of_pair);
-    double* W = A.dev<double>((size_t)nsp * 8 * npp);
+    int* d_sp_pair = S.upload(sp_pair);
+    int* d_sp_of = S.upload(sp_of_pair);
+    double* W = S.dev<double>((size_t)nsp * 8 * npp);
     std::vector<double> tb(d.n_beta);
     for (int k = 0; k < d.n_beta; ++k) tb[k] = cheb_node(k, d.n_beta);
-    double* d_tb = A.upload(tb);
-    double* d_wb = A.dev<double>(d.n_beta);
+    double* d_tb = S.upload(tb);
+    double* d_wb = S.dev<double>(d.n_beta);
     k_cheb_tables<<<1, 128>>>(d.n_beta, d_wb, nullptr, nullptr);
     size_t smw = moments_smem_per_warp(nc, ng, d.n_beta);
     int wpb = 1;
@@ -202,9 +233,12 @@ void build(ifgf_plan_t* p) {
     p->stats.near_nnz = p->near.nnz;
     p->near.row_ptr = A.upload(row_ptr);
     p->near.col = A.upload(col);
-    int* d_pair = A.upload(pair);
-    p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);
-    p->near.val32 = A.dev<float>(8 * (size_t)p->near.nnz);
+    int* d_pair = S.upload(pair);
+    // the near values in the plan's precision only
+    if (d.precision == IFGF_FP64)
+      p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);
+    else
+      p->near.val32 = A.dev<float>(8 * (size_t)p->near.nnz);
     k_near_values<<<(unsigned)(((size_t)N * 32 + 255) / 256), 256>>>(N, nc, p->near.row_ptr, p->near.col, d_pair,
         d_sp_of, W, p->geo.x, p->geo.n, p->geo.w, p->leafc, d.k_ext, d.k_int, p->near.val64, p->near.val32);
     check(cudaGetLastError(), "k_near_values launch");

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
+#include <thread>
+#include <unordered_map>
 
 #include "host_setup.h"
 
@@ -72,7 +74,7 @@ static void box_center(const HostTree& t, int d, const std::array<int, 3>& ic, d
 }
 
 void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_levels,
-                double k_max, int ns0, int na0) {
+                double k_max, int ns0, int na0, int max_leaf_pts) {
   if (N <= 0) throw std::invalid_argument("no nodes");
   double lo[3] = {x[0], x[1], x[2]}, hi[3] = {x[0], x[1], x[2]};
   for (int i = 0; i < N; ++i)
@@ -87,6 +89,24 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
   for (int a = 0; a < 3; ++a) t.corner[a] = 0.5 * (lo[a] + hi[a]) - 0.5 * t.H1;
   int D = std::max(3, min_levels);
   while (t.H1 / std::ldexp(1.0, D - 1) > leaf_size && D < 21) ++D;
+  // point-count leaf rule: refine until no leaf box holds more than max_leaf_pts points
+  if (max_leaf_pts > 0) {
+    std::unordered_map<uint64_t, int> count;
+    while (D < 21) {
+      count.clear();
+      const double HD = t.H1 / std::ldexp(1.0, D - 1);
+      const int nside = 1 << (D - 1);
+      int mx = 0;
+      for (int i = 0; i < N; ++i) {
+        int c[3];
+        for (int a = 0; a < 3; ++a)
+          c[a] = std::min(nside - 1, std::max(0, (int)std::floor((x[3 * i + a] - t.corner[a]) / HD)));
+        mx = std::max(mx, ++count[morton(c[0], c[1], c[2])]);
+      }
+      if (mx <= max_leaf_pts) break;
+      ++D;
+    }
+  }
   t.D = D;
   t.lv.assign(D + 1, HostLevel());
   for (int d = 1; d <= D; ++d) {
@@ -323,7 +343,7 @@ void near_candidates(const double* x, int P, int nc, double delta, std::vector<d
   const int npp = nc * nc;
   const int N = P * npp;
   gap.assign(P, 0.0);
-  std::vector<double> cen(3 * P, 0.0), rad(P, 0.0);
+  std::vector<double> cen(3 * (size_t)P, 0.0), rad(P, 0.0);
   auto X = [&](int p, int i, int j) { return x + 3 * ((size_t)p * npp + i * nc + j); };
   for (int p = 0; p < P; ++p) {
     double g = 0;
@@ -349,30 +369,101 @@ void near_candidates(const double* x, int P, int nc, double delta, std::vector<d
       rad[p] = std::max(rad[p], std::sqrt(dd));
     }
   }
+  // patch centres binned in a uniform grid whose cell is the largest reach rad + delta + gap:
+  // every patch that can be a candidate of a target has its centre in one of the 27 cells
+  // around the target's cell
+  double reach = 0, lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int p = 0; p < P; ++p) {
+    reach = std::max(reach, rad[p] + delta + gap[p]);
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], cen[3 * p + k]);
+      hi[k] = std::max(hi[k], cen[3 * p + k]);
+    }
+  }
+  for (int l = 0; l < N; ++l)
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], x[3 * (size_t)l + k]);
+      hi[k] = std::max(hi[k], x[3 * (size_t)l + k]);
+    }
+  const double cell = std::max(reach, 1e-300);
+  int dim[3];
+  for (int k = 0; k < 3; ++k) dim[k] = std::max(1, std::min(4096, (int)std::floor((hi[k] - lo[k]) / cell) + 1));
+  auto cell_of = [&](const double* q, int* c) {
+    for (int k = 0; k < 3; ++k) c[k] = std::min(dim[k] - 1, std::max(0, (int)std::floor((q[k] - lo[k]) / cell)));
+  };
+  const size_t ncell = (size_t)dim[0] * dim[1] * dim[2];
+  std::vector<int> cell_ptr(ncell + 1, 0), cell_patch(P);
+  std::vector<size_t> pc(P);
+  for (int p = 0; p < P; ++p) {
+    int c[3];
+    cell_of(&cen[3 * p], c);
+    pc[p] = ((size_t)c[2] * dim[1] + c[1]) * dim[0] + c[0];
+    ++cell_ptr[pc[p] + 1];
+  }
+  for (size_t c = 0; c < ncell; ++c) cell_ptr[c + 1] += cell_ptr[c];
+  {
+    std::vector<int> fill(cell_ptr.begin(), cell_ptr.end() - 1);
+    for (int p = 0; p < P; ++p) cell_patch[fill[pc[p]]++] = p;   // patches ascending within a cell
+  }
+  // targets split over host threads; each target's candidates in increasing patch order
+  const int nth = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
+  std::vector<std::vector<int>> part(nth);
+  std::vector<std::vector<int64_t>> cnt(nth);
+  auto work = [&](int tid) {
+    const int l0 = (int)((int64_t)N * tid / nth), l1 = (int)((int64_t)N * (tid + 1) / nth);
+    std::vector<int>& out = part[tid];
+    std::vector<int64_t>& counts = cnt[tid];
+    counts.assign(l1 - l0, 0);
+    std::vector<int> found;
+    for (int l = l0; l < l1; ++l) {
+      const double* xl = x + 3 * (size_t)l;
+      const int pl = l / npp;
+      found.clear();
+      found.push_back(pl);
+      int c[3];
+      cell_of(xl, c);
+      for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dx = -1; dx <= 1; ++dx) {
+            const int cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+            if (cx < 0 || cy < 0 || cz < 0 || cx >= dim[0] || cy >= dim[1] || cz >= dim[2]) continue;
+            const size_t ci = ((size_t)cz * dim[1] + cy) * dim[0] + cx;
+            for (int e = cell_ptr[ci]; e < cell_ptr[ci + 1]; ++e) {
+              const int p = cell_patch[e];
+              if (p == pl) continue;
+              double dc = 0;
+              for (int k = 0; k < 3; ++k) dc += (xl[k] - cen[3 * p + k]) * (xl[k] - cen[3 * p + k]);
+              if (std::sqrt(dc) - rad[p] > delta + gap[p]) continue;
+              double dmin = INFINITY;
+              for (int m = 0; m < npp; ++m) {
+                const double* y = x + 3 * ((size_t)p * npp + m);
+                double dd = 0;
+                for (int k = 0; k < 3; ++k) dd += (xl[k] - y[k]) * (xl[k] - y[k]);
+                dmin = std::min(dmin, std::sqrt(dd));
+              }
+              if (dmin <= delta + gap[p]) found.push_back(p);
+            }
+          }
+      std::sort(found.begin(), found.end());
+      out.insert(out.end(), found.begin(), found.end());
+      counts[l - l0] = (int64_t)found.size();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int i = 0; i < nth; ++i) th.emplace_back(work, i);
+  for (auto& w : th) w.join();
   cptr.assign(N + 1, 0);
   cpatch.clear();
-  for (int l = 0; l < N; ++l) {
-    const double* xl = x + 3 * (size_t)l;
-    int pl = l / npp;
-    for (int p = 0; p < P; ++p) {
-      bool cand = (p == pl);
-      if (!cand) {
-        double dc = 0;
-        for (int k = 0; k < 3; ++k) dc += (xl[k] - cen[3 * p + k]) * (xl[k] - cen[3 * p + k]);
-        if (std::sqrt(dc) - rad[p] <= delta + gap[p]) {
-          double dmin = INFINITY;
-          for (int m = 0; m < npp; ++m) {
-            const double* y = x + 3 * ((size_t)p * npp + m);
-            double dd = 0;
-            for (int k = 0; k < 3; ++k) dd += (xl[k] - y[k]) * (xl[k] - y[k]);
-            dmin = std::min(dmin, std::sqrt(dd));
-          }
-          cand = dmin <= delta + gap[p];
-        }
-      }
-      if (cand) cpatch.push_back(p);
+  size_t total = 0;
+  for (auto& v : part) total += v.size();
+  cpatch.reserve(total);
+  int l = 0;
+  for (int i = 0; i < nth; ++i) {
+    cpatch.insert(cpatch.end(), part[i].begin(), part[i].end());
+    for (int64_t c : cnt[i]) {
+      cptr[l + 1] = cptr[l] + c;
+      ++l;
     }
-    cptr[l + 1] = (int64_t)cpatch.size();
   }
 }
 

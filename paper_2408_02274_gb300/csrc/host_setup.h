@@ -10,8 +10,9 @@ int cone_of(const ConeGeom& cg, double x, double y, double z);
 void interp_point(const ConeGeom& cg, int cone, int q, double* X);
 
 // Octree, cone counts, relevant cones and target lists.  Throws std::invalid_argument.
+// max_leaf_pts > 0: deepen the (uniform) octree until no leaf box holds more points.
 void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_levels, double k_max,
-                int ns0, int na0);
+                int ns0, int na0, int max_leaf_pts = 0);
 
 // Candidate singular patches per target (node-distance filter of the singular set).
 void near_candidates(const double* x, int P, int nc, double delta, std::vector<double>& gap,

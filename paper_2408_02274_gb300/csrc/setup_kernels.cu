@@ -594,6 +594,7 @@ size_t moments_smem_per_warp(int nc, int ng, int nbeta) {
 }
 
 // ---------------------------------------------------------------- near-field matrix values
+// Either output may be null (the plan keeps the values in its own precision only).
 // Row l (Sec. III-H, reading R12): for columns on singular patches the
 // singular weight minus the plain Fejer term wherever the far algorithm also
 // counts the pair (column outside the neighbour boxes of x_l); for neighbour
@@ -640,8 +641,8 @@ __global__ void k_near_values(int N, int nc, const int64_t* row_ptr, const int* 
       }
     }
     for (int t = 0; t < 8; ++t) {
-      val64[8 * e + t] = v[t];
-      val32[8 * e + t] = (float)v[t];
+      if (val64) val64[8 * e + t] = v[t];
+      if (val32) val32[8 * e + t] = (float)v[t];
     }
   }
 }

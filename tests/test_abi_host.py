@@ -45,7 +45,8 @@ def test_invalid_descriptors_rejected_before_any_gpu_work():
                         ({"n_beta": 2}, lib.IFGF_EINVAL), ({"cov_d": 1.0}, lib.IFGF_EINVAL),
                         ({"precision": 7}, lib.IFGF_EINVAL), ({"ps": 4}, lib.IFGF_EUNSUPPORTED),
                         ({"nc": 1}, lib.IFGF_EINVAL), ({"max_krylov": 5000}, lib.IFGF_EINVAL),
-                        ({"batch": -1}, lib.IFGF_EINVAL), ({"batch": 5000}, lib.IFGF_EINVAL)]:
+                        ({"batch": -1}, lib.IFGF_EINVAL), ({"batch": 5000}, lib.IFGF_EINVAL),
+                        ({"max_leaf_pts": -3}, lib.IFGF_EINVAL)]:
         kw = dict(base)
         kw.update(bad)
         with pytest.raises(lib.IfgfError) as e:
