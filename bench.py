@@ -721,6 +721,96 @@ def run_compare(args):
     return {"mode": "compare", "workload": WORKLOADS[args.workload], "tol": args.tol, **rows}
 
 
+def patch_diameters(prob):
+    """Largest distance between two nodes of each patch."""
+    x, _, _ = prob.nodes()
+    P, nc = prob.num_patches, prob.nc
+    xp = x.reshape(P, nc * nc, 3)
+    diam = np.empty(P)
+    for i in range(0, P, 512):
+        b = xp[i:i + 512]
+        diam[i:i + 512] = np.linalg.norm(b[:, :, None] - b[:, None], axis=-1).max(axis=(1, 2))
+    return diam
+
+
+def run_waveguide(args):
+    """The elongated waveguide bar (20 x 0.3 x 0.14 vacuum wavelengths, eps 12.1 in 2.1) at
+    patch side --bar-h: plan setup time and memory, forward-map time (CUDA events over
+    --steps applies), the FP32 IFGF forward map against the direct far sum on the nodes of
+    random patches (about --sample-rows target rows), and optionally (--solve) a GMRES solve for a Gaussian beam (waist
+    0.2, along +x, focus 0.5 outside the -x end, polarised y) to --tol."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import gaussian_beam, random_densities, waveguide_bar
+    libbuild.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    prob = waveguide_bar(args.bar_h)
+    x, _, _ = prob.nodes()
+    prob.fine()
+    N = prob.n
+    diam = patch_diameters(prob)
+    delta = 0.6 * float(np.median(diam))
+    t_host = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_krylov,
+                                 max_leaf_pts=args.leaf_pts, gmres_scaling=args.gmres_scaling)
+    torch.cuda.synchronize()
+    setup = time.perf_counter() - t0
+    st = plan.stats()
+    res = {"mode": "waveguide", "workload": f"bar 20 x 0.3 x 0.14 lambda0, eps 12.1 / 2.1, patch side {args.bar_h}",
+           "n": N, "unknowns": 4 * N, "patches": prob.num_patches, "delta": delta,
+           "patch_diameter_quantiles": [float(v) for v in np.quantile(diam, [0.0, 0.5, 1.0])],
+           "max_leaf_pts": args.leaf_pts, "gmres_scaling": args.gmres_scaling, "host_geometry_s": t_host,
+           "setup_s": setup,
+           "device_bytes": st["device_bytes"], "levels": st["levels"], "near_nnz": st["near_nnz"],
+           "singular_pairs": st["singular_pairs"], "boxes": st["boxes"], "cones": st["cones"],
+           "interactions": st["interactions"]}
+    y = torch.from_numpy(random_densities(N, 11)).cuda()
+    out = torch.empty_like(y)
+    for _ in range(max(args.warmup, 1)):
+        plan.apply(y, out)
+    torch.cuda.synchronize()
+    lib.ifgf_set_timing(plan.handle, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.apply(y, out)
+    e1.record()
+    torch.cuda.synchronize()
+    kt, _ = lib.ifgf_get_timing(plan.handle)
+    lib.ifgf_set_timing(plan.handle, False)
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    res.update({"ms_per_forward_map": ms, "unknown_matvecs_per_s": 4.0 * N / (ms / 1e3),
+                "stage_ms_per_apply": {k: v[0] / max(args.steps, 1) for k, v in kt.items()}})
+    npp = prob.nc ** 2
+    npat = min(prob.num_patches, max(1, -(-args.sample_rows // npp)))
+    pats = np.sort(np.random.default_rng(12).choice(prob.num_patches, size=npat, replace=False))
+    ref = torch.empty_like(y)
+    t0 = time.perf_counter()
+    plan.apply_direct_patches(y, ref, pats)
+    t_rows = time.perf_counter() - t0
+    r = torch.from_numpy((pats[:, None] * npp + np.arange(npp)[None]).ravel().astype(np.int64)).cuda()
+    err = float(torch.linalg.norm(out[:, r] - ref[:, r]) / torch.linalg.norm(ref[:, r]))
+    res.update({"sample_patches": int(npat), "sample_rows": int(npat * npp), "rel_err_vs_direct_on_rows": err,
+                "direct_rows_s": t_rows})
+    if args.solve:
+        inc = gaussian_beam(x, prob.k_ext, prob.omega, focus=(-10.5, 0.0, 0.0), waist=0.2)
+        incd = torch.from_numpy(np.ascontiguousarray(inc[None])).cuda()
+        ys = torch.empty((1, 4, N), dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rrs, stt = plan.solve_batch(incd, ys, tol=args.tol, max_iter=args.max_krylov)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res["solve"] = {"tol": args.tol, "max_iter": args.max_krylov, "iters": its[0], "relres_estimate": rrs[0],
+                        "status": int(stt), "seconds": dt, "unknown_matvecs_per_s": 4.0 * N * its[0] / dt}
+    plan.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -730,7 +820,7 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven", "precond", "compare"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "batch", "uneven", "precond", "compare", "waveguide"])
     ap.add_argument("--ntrain", type=int, default=8)
     ap.add_argument("--ntest", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=3000)
@@ -739,6 +829,10 @@ def main():
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--max-krylov", type=int, default=200)
     ap.add_argument("--workload", default="sphere9600", choices=sorted(WORKLOADS))
+    ap.add_argument("--bar-h", type=float, default=0.07)
+    ap.add_argument("--leaf-pts", type=int, default=64)
+    ap.add_argument("--sample-rows", type=int, default=10000)
+    ap.add_argument("--gmres-scaling", type=int, default=1, choices=[0, 1])
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)
@@ -752,6 +846,8 @@ def main():
         res = run_precond(args)
     elif args.mode == "compare":
         res = run_compare(args)
+    elif args.mode == "waveguide":
+        res = run_waveguide(args)
     else:
         res = run_gpu(args)
     if res is not None:

@@ -85,6 +85,10 @@ typedef struct {
                               workspace are allocated this many times (0 -> 1, <= 1024) */
   int32_t max_leaf_pts;    /* point-count leaf rule: deepen the octree until no leaf box holds
                               more nodes (0 -> off; thin bodies need it); <= 1e6 */
+  int32_t gmres_scaling;   /* 0: GMRES on Eq. n_muller as written; 1: GMRES on A D with D =
+                              diag(2/(mu_e+mu_i) on m, 2/(eps_e+eps_i) on j) and y = D z, so the
+                              identity parts of both block rows become 1 (a constant right
+                              scaling: same solution, residuals of the unscaled system) */
 } ifgf_plan_desc;
 
 /* Counts describing a plan (ifgf_plan_stats). */
@@ -136,6 +140,24 @@ ifgf_status ifgf_apply(ifgf_plan plan, const void* y, void* out, ifgf_stream str
  * IFGF_EINVAL for nrhs outside [1, batch].
  */
 ifgf_status ifgf_apply_batch(ifgf_plan plan, int32_t nrhs, const void* y, void* out, ifgf_stream stream);
+
+/*
+ * Sampled direct reference: the forward map with the far field taken by the plain
+ * O(N) sum per target (the sum of Eq. ifgf_sum_em written out, as IFGF_FAR_DIRECT) at the
+ * nodes of the listed patches only, and the plan's own near matrix.  For accuracy spot
+ * checks of the IFGF forward map at sizes where the full O(N^2) direct sum is too slow.
+ * Whole patches are the unit because the N-Mueller combination differentiates the
+ * potentials tangentially across each patch (Sec. III, surface divergence and curl).
+ * y and out: DEVICE [4][N] complex128 as ifgf_apply; only the entries of out at the nodes
+ * p Nc^2 .. (p+1) Nc^2 - 1 of each listed patch p (in all 4 components) are defined.
+ * patches: HOST int32 [npatches], distinct patch indices in [0, P), 1 <= npatches <= P.
+ * Arithmetic in the plan's precision.  Allocates a device list of the patches' nodes per
+ * call and returns after `stream` has finished.  IFGF_EINVAL on a null pointer, y == out,
+ * npatches out of range, a patch out of range or repeated; IFGF_ENOMEM if the node list
+ * cannot be allocated; IFGF_ECUDA poisons the plan.
+ */
+ifgf_status ifgf_apply_direct_patches(ifgf_plan plan, const void* y, void* out, const int32_t* patches,
+                                      int32_t npatches, ifgf_stream stream);
 
 /*
  * Raw scalar sums for tests: given the eight densities phi (DEVICE [N][8]
@@ -314,10 +336,10 @@ ifgf_status ifgf_tree_info(ifgf_tree tree, int32_t* levels, double* corner, doub
 /* perm [n]: sorted position -> node; leaf_coords [n][3]: integer leaf box of each node */
 ifgf_status ifgf_tree_perm(ifgf_tree tree, int32_t* perm, int32_t* leaf_coords);
 /* level d (1..D): box count, relevant-cone count, (n_s, n_a), integer box coordinates [nb][3],
- * relevant cones CSR per box (box_slot_ptr [nb+1], slot_cone [nslots] cone ids
- * (g1*na + g2)*2na + g3) */
+ * relevant cones CSR per box (box_slot_ptr [nb+1], slot_cone [nslots] cone keys
+ * g1 << 42 | g2 << 21 | g3 for the s-, theta- and phi-cell indices, sorted within a box) */
 ifgf_status ifgf_tree_level(ifgf_tree tree, int32_t d, int32_t* nboxes, int32_t* nslots, int32_t* ns,
-                            int32_t* na, int32_t* box_coords, int32_t* box_slot_ptr, int32_t* slot_cone);
+                            int32_t* na, int32_t* box_coords, int32_t* box_slot_ptr, int64_t* slot_cone);
 /* level d (3..D): per sorted target, the relevant cones (slots of level d) it is evaluated from:
  * tgt_ptr [n+1] (int64), tgt_slot [ninter]; slot_box [nslots] box of each slot */
 ifgf_status ifgf_tree_targets(ifgf_tree tree, int32_t d, int64_t* ninter, int64_t* tgt_ptr,

@@ -15,7 +15,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar",
+__all__ = ["Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar", "rounded_bar",
            "open_cheb_nodes", "sample_body"]
 
 
@@ -148,6 +148,90 @@ def superellipsoid_bar(half_lengths, exponent: int, split_per_face, center=(0.0,
                 patches.append((f, I, J, (nu, nv)))
     body = Body(patches, surf, f"superellipsoid({tuple(half_lengths)},e={e})")
     body.eval = _anisotropic_eval(body, surf)
+    return body
+
+
+def rounded_bar(half_lengths, end_length: float, patch_size: float, center=(0.0, 0.0, 0.0)) -> Body:
+    """A straight bar of length 2A along x with rounded-rectangle cross-section
+    |y/B|^8 + |z/C|^8 = 1, closed at each end by half of the superellipsoid
+    |x'/L|^8 + |y/B|^8 + |z/C|^8 = 1 (x' the distance past the end of the straight part,
+    L = `end_length`), so the total length stays 2A.  The surface is C^7 where the straight
+    part meets the ends and analytic on every patch.
+
+    Parts (each split into patches of side about `patch_size`):
+      - four straight sides (normals +z, -z, +y, -y): x = (A - L) U linear in U, and across the
+        side the 2-D cube map (t, 1)/(1 + t^8)^(1/8), t = tan(pi V/4), scaled by (B, C);
+      - at each end, the end face of the small superellipsoid (L, B, C) under the cube-face map
+        w = q/|q|_8, q = (tan(pi U/4), tan(pi V/4), 1) rotated, and the halves of its four side
+        faces that lie beyond the straight part; at the junction these take the same
+        cross-section parametrisation as the straight sides.
+    Patch tuples are (kind, face, I, J, (nu, nv), (U0, U1)) with kind 0 = straight side,
+    1 = end face, 2 = end half face, face the cube face of the rotation table, and U in
+    [U0, U1] split nu ways.  Derivatives come from complex-step differentiation of the
+    analytic maps (exact to rounding)."""
+    A, B, C = (float(v) for v in half_lengths)
+    L = float(end_length)
+    if not (0.0 < L < A):
+        raise ValueError("need 0 < end_length < A")
+    scale = np.array([1.0, B, C])
+    cen = np.asarray(center, dtype=np.float64)
+    a0 = A - L
+
+    def point(kind, face, side, uu, vv):
+        R = _FACE_ROT[face]
+        tv = np.tan(np.pi * vv / 4.0)
+        if kind == 0:
+            s = 1.0 / (1.0 + tv ** 8) ** 0.125
+            w = np.stack([np.zeros_like(tv), s * tv, s * np.ones_like(tv)], axis=-1) @ R.T
+            return w * scale + np.stack([a0 * uu + 0.0 * tv, 0.0 * tv, 0.0 * tv], axis=-1) + cen
+        tu = np.tan(np.pi * uu / 4.0)
+        q = np.stack([tu, tv, np.ones_like(tu)], axis=-1) @ R.T
+        w = q / np.sum(q ** 8, axis=-1)[..., None] ** 0.125
+        return w * np.array([L, B, C]) + np.array([side * a0, 0.0, 0.0]) + cen
+
+    # parts: (kind, face, U0, U1)
+    parts = [(0, f, -1.0, 1.0) for f in (0, 1, 4, 5)]
+    parts += [(1, 2, -1.0, 1.0), (1, 3, -1.0, 1.0)]
+    parts += [(2, f, 0.0, 1.0) for f in (0, 1, 4, 5)] + [(2, f, -1.0, 0.0) for f in (0, 1, 4, 5)]
+    g = np.linspace(0.0, 1.0, 801)
+    t, wq = np.polynomial.legendre.leggauss(60)
+    tq = 0.5 * (t + 1.0)
+    patches = []
+    for kind, face, U0, U1 in parts:
+        side = 1.0 if (face == 2 or (kind == 2 and U0 >= 0.0)) else -1.0
+        uu = U0 + (U1 - U0) * g
+        xa = point(kind, face, side, uu, np.zeros_like(g))
+        xb = point(kind, face, side, np.full_like(g, 0.5 * (U0 + U1)), -1.0 + 2.0 * g)
+        au = float(np.sum(np.linalg.norm(np.diff(xa, axis=0), axis=1)))
+        av = float(np.sum(np.linalg.norm(np.diff(xb, axis=0), axis=1)))
+        Uq, Vq = np.meshgrid(U0 + (U1 - U0) * tq, -1.0 + 2.0 * tq, indexing="ij")
+        h = 1e-30
+        xu = np.imag(point(kind, face, side, Uq + 1j * h, Vq.astype(np.complex128))) / h
+        xv = np.imag(point(kind, face, side, Uq.astype(np.complex128), Vq + 1j * h)) / h
+        area = float(np.sum(np.outer(wq, wq) * np.linalg.norm(np.cross(xu, xv), axis=-1))) * 0.5 * (U1 - U0)
+        sc = np.sqrt(area / (au * av))
+        nu = max(1, int(np.ceil(au * sc / patch_size)))
+        nv = max(1, int(np.ceil(av * sc / patch_size)))
+        for I in range(nu):
+            for J in range(nv):
+                patches.append((kind, face, I, J, (nu, nv), (U0, U1)))
+    body = Body(patches, None, f"rounded_bar({A},{B},{C},L={L},h={patch_size})")
+
+    def ev(p, u, v):
+        kind, face, I, J, (nu, nv), (U0, U1) = body.patches[p]
+        side = 1.0 if (face == 2 or (kind == 2 and U0 >= 0.0)) else -1.0
+        u = np.asarray(u, dtype=np.float64)
+        v = np.asarray(v, dtype=np.float64)
+        du = (U1 - U0) / nu
+        U = U0 + du * (I + 0.5 * (u + 1.0))
+        V = -1.0 + (2.0 * J + (v + 1.0)) / nv
+        h = 1e-30
+        x = point(kind, face, side, U, V)
+        xu = np.imag(point(kind, face, side, U + 1j * (0.5 * du * h), V.astype(np.complex128))) / h
+        xv = np.imag(point(kind, face, side, U.astype(np.complex128), V + 1j * (h / nv))) / h
+        return x, xu, xv
+
+    body.eval = ev
     return body
 
 

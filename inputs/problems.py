@@ -166,3 +166,43 @@ def star_batch(count: int, seed: int, radius: float = 0.75, split: int = 4, nc: 
         out.append(Problem(body=star_body(radius * wavelength, coeffs, split), nc=nc, ng=max(2 * nc, 24),
                            eps_ext=1.0, eps_int=eps, omega=2 * np.pi / wavelength, name=f"star{seed}_{i}"))
     return out
+
+
+def gaussian_beam(x: np.ndarray, k_ext: float, omega: float, focus, waist: float, mu_ext: float = 1.0,
+                  direction=(1.0, 0.0, 0.0), polarization=(0.0, 1.0, 0.0)):
+    """Paraxial Gaussian beam (e^{-i omega t}) with waist w0 at `focus`, travelling along d:
+    xi = d.(x - f), rho^2 = |x - f|^2 - xi^2, z_R = k w0^2 / 2, q = xi - i z_R,
+    E = p (-i z_R / q) exp(i k xi + i k rho^2 / (2 q)),  H = (k / (omega mu)) d x E.
+    |E| = (w0 / w(xi)) exp(-rho^2 / w(xi)^2) with w(xi) = w0 sqrt(1 + (xi/z_R)^2), and the phase
+    carries the Gouy term -atan(xi / z_R).  Only paraxially a Maxwell field: it serves as a
+    right-hand side.  Returns [6, N] complex (Ex, Ey, Ez, Hx, Hy, Hz) at the points x [N, 3]."""
+    d = np.asarray(direction, dtype=np.float64)
+    d = d / np.linalg.norm(d)
+    p = np.asarray(polarization, dtype=np.float64)
+    p = p - (p @ d) * d
+    p = p / np.linalg.norm(p)
+    r = np.asarray(x, dtype=np.float64) - np.asarray(focus, dtype=np.float64)[None, :]
+    xi = r @ d
+    rho2 = np.maximum(np.sum(r * r, axis=1) - xi * xi, 0.0)
+    k = k_ext
+    zr = 0.5 * k * waist * waist
+    q = xi - 1j * zr
+    u = (-1j * zr / q) * np.exp(1j * k * xi + 1j * k * rho2 / (2.0 * q))
+    E = p[:, None] * u[None, :]
+    H = (k / (omega * mu_ext)) * np.cross(d, p)[:, None] * u[None, :]
+    return np.concatenate([E, H], axis=0)
+
+
+def waveguide_bar(patch_size: float = 0.035, nc: int = 10, wavelength: float = 1.0,
+                  half_lengths=(10.0, 0.15, 0.07), end_length: float = 0.15, eps_ext: float = 2.1,
+                  eps_int: float = 12.1, center=(0.0, 0.0, 0.0)):
+    """The elongated waveguide bar: a straight bar 2A = 20 vacuum wavelengths long with the
+    rounded-rectangle cross-section |y/B|^8 + |z/C|^8 = 1 (B = 0.15, C = 0.07: 0.3 x 0.14),
+    closed by superellipsoidal ends 0.15 long (``rounded_bar``); silicon-like eps_int = 12.1
+    in an oxide-like eps_ext = 2.1, omega = 2 pi / lambda_0.  Patches of side about
+    `patch_size` wavelengths: 0.035 gives about 1.5M nodes at nc = 10."""
+    from .geometry import rounded_bar
+    hl = tuple(float(h) * wavelength for h in half_lengths)
+    body = rounded_bar(hl, end_length * wavelength, patch_size * wavelength, center=center)
+    return Problem(body=body, nc=nc, ng=max(2 * nc, 24), eps_ext=eps_ext, eps_int=eps_int,
+                   omega=2 * np.pi / wavelength, name=f"bar_h{patch_size:g}_P{body.num_patches}")

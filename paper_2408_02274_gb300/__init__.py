@@ -22,6 +22,7 @@ IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
 IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 
 EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_batch", "ifgf_apply_fields",
+           "ifgf_apply_direct_patches",
            "bie_solve", "bie_solve_batch", "bie_solve_many", "bie_solve_precond", "bie_rhs", "ifgf_precond_attach",
            "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
            "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
@@ -43,6 +44,7 @@ class ifgf_plan_desc(ctypes.Structure):
         ("delta", ctypes.c_double), ("n_beta", ctypes.c_int32), ("cov_d", ctypes.c_double),
         ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
         ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_leaf_pts", ctypes.c_int32),
+        ("gmres_scaling", ctypes.c_int32),
     ]
 
 
@@ -82,6 +84,7 @@ def load(path: str = LIB_PATH):
     lib.ifgf_apply.argtypes = [vp, vp, vp, vp]
     lib.ifgf_apply_batch.argtypes = [vp, i32, vp, vp, vp]
     lib.ifgf_apply_fields.argtypes = [vp, vp, vp, i32, vp]
+    lib.ifgf_apply_direct_patches.argtypes = [vp, vp, vp, ctypes.POINTER(i32), i32, vp]
     lib.bie_solve.argtypes = [vp, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
                               ctypes.POINTER(ctypes.c_double), vp]
     lib.bie_solve_batch.argtypes = [vp, i32, vp, ctypes.c_double, i32, vp, ctypes.POINTER(i32),
@@ -142,7 +145,8 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                      gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
-                     max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0):
+                     max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0,
+                     gmres_scaling: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
@@ -150,7 +154,7 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
     d = ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
                        k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
                        min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-                       max_leaf_pts)
+                       max_leaf_pts, gmres_scaling)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h
@@ -170,6 +174,16 @@ def ifgf_apply_batch(plan, y, out, stream=None):
     """out[r] = A y[r] for torch complex128 CUDA tensors y, out of shape [nrhs, 4, N]."""
     _check(load().ifgf_apply_batch(plan, int(y.shape[0]), ctypes.c_void_p(y.data_ptr()),
                                    ctypes.c_void_p(out.data_ptr()), _stream(stream)), "ifgf_apply_batch")
+
+
+def ifgf_apply_direct_patches(plan, y, out, patches, stream=None):
+    """out = A y with a direct far sum at the nodes of the listed patches only (torch
+    complex128 CUDA tensors [4, N]; patches: distinct patch indices).  Only the columns of
+    out at those patches' nodes are defined."""
+    q = np.ascontiguousarray(np.asarray(patches, dtype=np.int32))
+    _check(load().ifgf_apply_direct_patches(plan, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(q.size),
+                                            _stream(stream)), "ifgf_apply_direct_patches")
 
 
 def ifgf_apply_fields(plan, phi, f28, which: int = IFGF_PART_ALL, stream=None):
@@ -394,7 +408,7 @@ class Tree:
                                    ctypes.byref(na), None, None, None), "ifgf_tree_level")
         coords = np.zeros((nb.value, 3), dtype=np.int32)
         ptr = np.zeros(nb.value + 1, dtype=np.int32)
-        cones = np.zeros(max(nsl.value, 1), dtype=np.int32)
+        cones = np.zeros(max(nsl.value, 1), dtype=np.int64)
         _check(lib.ifgf_tree_level(self.handle, d, ctypes.byref(nb), ctypes.byref(nsl), ctypes.byref(ns),
                                    ctypes.byref(na), ctypes.c_void_p(coords.ctypes.data),
                                    ctypes.c_void_p(ptr.ctypes.data), ctypes.c_void_p(cones.ctypes.data)),
@@ -448,6 +462,9 @@ class Plan:
 
     def apply_batch(self, y, out, stream=None):
         ifgf_apply_batch(self.handle, y, out, stream)
+
+    def apply_direct_patches(self, y, out, patches, stream=None):
+        ifgf_apply_direct_patches(self.handle, y, out, patches, stream)
 
     def solve_batch(self, inc, y, tol=1e-6, max_iter=300, stream=None):
         return bie_solve_batch(self.handle, inc, tol, max_iter, y, stream)

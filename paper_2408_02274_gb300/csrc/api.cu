@@ -116,6 +116,7 @@ ifgf_status validate(const ifgf_plan_desc* d) {
   if (d->max_krylov < 0 || d->max_krylov > 1000) return IFGF_EINVAL;
   if (d->batch < 0 || d->batch > 1024) return IFGF_EINVAL;
   if (d->max_leaf_pts < 0 || d->max_leaf_pts > 1000000) return IFGF_EINVAL;
+  if (d->gmres_scaling < 0 || d->gmres_scaling > 1) return IFGF_EINVAL;
   if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
   if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
   return IFGF_OK;
@@ -184,6 +185,7 @@ void build(ifgf_plan_t* p) {
   }
   // ---------------- near field: candidates, closest points, singular moments, matrix
   {
+    Scratch SN;   // freed at the end of this block, before the IFGF tables are allocated
     std::vector<double> gap;
     std::vector<int64_t> cptr;
     std::vector<int> cpatch;
@@ -192,10 +194,10 @@ void build(ifgf_plan_t* p) {
     std::vector<int> ptgt(npairs);
     for (int l = 0; l < N; ++l)
       for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) ptgt[e] = l;
-    int* d_ptgt = S.upload(ptgt);
-    int* d_ppatch = S.upload(cpatch);
-    double* d_uv = S.dev<double>(2 * (size_t)npairs);
-    uint8_t* d_sing = S.dev<uint8_t>(npairs);
+    int* d_ptgt = SN.upload(ptgt);
+    int* d_ppatch = SN.upload(cpatch);
+    double* d_uv = SN.dev<double>(2 * (size_t)npairs);
+    uint8_t* d_sing = SN.dev<uint8_t>(npairs);
     int iters = d.gs_iters > 0 ? d.gs_iters : 60;
     k_closest<<<(npairs + 127) / 128, 128>>>(npairs, nc, ng, iters, d.delta, d_ptgt, d_ppatch, p->geo.x,
                                              fcoef, unodes, d_uv, d_sing);
@@ -210,13 +212,13 @@ void build(ifgf_plan_t* p) {
       }
     const int nsp = (int)sp_pair.size();
     p->stats.singular_pairs = nsp;
-    int* d_sp_pair = S.upload(sp_pair);
-    int* d_sp_of = S.upload(sp_of_pair);
-    double* W = S.dev<double>((size_t)nsp * 8 * npp);
+    int* d_sp_pair = SN.upload(sp_pair);
+    int* d_sp_of = SN.upload(sp_of_pair);
+    double* W = SN.dev<double>((size_t)nsp * 8 * npp);
     std::vector<double> tb(d.n_beta);
     for (int k = 0; k < d.n_beta; ++k) tb[k] = cheb_node(k, d.n_beta);
-    double* d_tb = S.upload(tb);
-    double* d_wb = S.dev<double>(d.n_beta);
+    double* d_tb = SN.upload(tb);
+    double* d_wb = SN.dev<double>(d.n_beta);
     k_cheb_tables<<<1, 128>>>(d.n_beta, d_wb, nullptr, nullptr);
     size_t smw = moments_smem_per_warp(nc, ng, d.n_beta);
     int wpb = 1;
@@ -233,7 +235,7 @@ void build(ifgf_plan_t* p) {
     p->stats.near_nnz = p->near.nnz;
     p->near.row_ptr = A.upload(row_ptr);
     p->near.col = A.upload(col);
-    int* d_pair = S.upload(pair);
+    int* d_pair = SN.upload(pair);
     // the near values in the plan's precision only
     if (d.precision == IFGF_FP64)
       p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);
@@ -258,7 +260,9 @@ void build(ifgf_plan_t* p) {
     for (int b = 0; b < Dl.nboxes; ++b)
       for (int k = 0; k < 3; ++k) cen[3 * (size_t)b + k] = t.corner[k] + L.H * (L.ic[b][k] + 0.5);
     Dl.box_center = A.upload(cen);
-    Dl.cone_map = A.upload(L.cone_map);
+    Dl.ncomp = (int)L.upcone_list.size();
+    Dl.ckeys = A.upload(L.upcone_list);
+    if (!L.cmap.empty()) Dl.cmap = A.upload(L.cmap);
     Dl.slot_box = A.upload(L.slot_box);
     Dl.slot_cone = A.upload(L.slot_cone);
     Dl.box_slot_ptr = A.upload(L.box_slot_ptr);
@@ -281,18 +285,22 @@ void build(ifgf_plan_t* p) {
     Dl.tgt_slot = A.upload(L.tgt_slot);
     Dl.ninter = (int64_t)L.tgt_slot.size();
     Dl.cstride = (size_t)Dl.nslots * kQ * 32;
-    const size_t creal = Dl.cstride * (size_t)p->batch;
-    if (d.far_mode == IFGF_FAR_IFGF) {
-      if (d.precision == IFGF_FP64)
-        Dl.coefs = A.dev<double>(creal);
-      else
-        Dl.coefs = A.dev<float>(creal);
-    }
     p->stats.boxes[dd] = Dl.nboxes;
     p->stats.cones[dd] = Dl.nslots;
     p->stats.ns[dd] = L.ns;
     p->stats.na[dd] = L.na;
     p->stats.interactions[dd] = Dl.ninter;
+  }
+  // Cone coefficients: a level's values are written by the leaf step (d = D) or the upward
+  // step from d+1, and read by the target step at d and the upward step into d-1, so only
+  // two consecutive levels are live at once: levels of equal parity share one buffer.
+  if (d.far_mode == IFGF_FAR_IFGF) {
+    size_t need[2] = {0, 0};
+    for (int dd = 3; dd <= t.D; ++dd) need[dd & 1] = std::max(need[dd & 1], p->dl[dd].cstride * (size_t)p->batch);
+    void* buf[2] = {nullptr, nullptr};
+    for (int a = 0; a < 2; ++a)
+      if (need[a]) buf[a] = (d.precision == IFGF_FP64) ? (void*)A.dev<double>(need[a]) : (void*)A.dev<float>(need[a]);
+    for (int dd = 3; dd <= t.D; ++dd) p->dl[dd].coefs = buf[dd & 1];
   }
   for (int dd = 1; dd < 3 && dd <= t.D; ++dd) p->stats.boxes[dd] = (int)t.lv[dd].key.size();
   {
@@ -502,6 +510,42 @@ ifgf_status ifgf_apply(ifgf_plan p, const void* y, void* out, ifgf_stream stream
   return ifgf_apply_batch(p, 1, y, out, stream);
 }
 
+ifgf_status ifgf_apply_direct_patches(ifgf_plan p, const void* y, void* out, const int32_t* patches,
+                                      int32_t npatches, ifgf_stream stream) {
+  if (!p || !y || !out || !patches || y == out) return IFGF_EINVAL;
+  if (npatches < 1 || npatches > p->P) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  const int npp = p->desc.nc * p->desc.nc;
+  std::vector<uint8_t> seen((size_t)p->P, 0);
+  std::vector<int> rows((size_t)npatches * npp);
+  for (int32_t i = 0; i < npatches; ++i) {
+    const int32_t q = patches[i];
+    if (q < 0 || q >= p->P || seen[q]) return IFGF_EINVAL;
+    seen[q] = 1;
+    for (int m = 0; m < npp; ++m) rows[(size_t)i * npp + m] = q * npp + m;
+  }
+  const int nrows = (int)rows.size();
+  cudaStream_t s = (cudaStream_t)stream;
+  int* d_rows = nullptr;
+  if (cudaMalloc(&d_rows, sizeof(int) * (size_t)nrows) != cudaSuccess) {
+    cudaGetLastError();
+    return IFGF_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * (size_t)nrows, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_density_prep(p, (const double*)y, nullptr, s, 1);
+  if (e == cudaSuccess) e = launch_near(p, s, 1);
+  if (e == cudaSuccess) e = launch_far_direct(p, s, 1, d_rows, nrows);
+  if (e == cudaSuccess) e = launch_combine(p, (const double*)y, (double*)out, s, 1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_rows);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_apply_direct_patches", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
 ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t which, ifgf_stream stream) {
   if (!p || !phi || !f28 || which < 1 || which > 3) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
@@ -539,11 +583,21 @@ static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double
   std::vector<int> it(nrhs, 0);
   std::vector<double> rr(nrhs, 0.0);
   if (e == cudaSuccess) {
-    MatvecFn mv = [p, nrhs](const double* v, double* w, cudaStream_t st) { return forward(p, v, w, nrhs, st); };
+    // right scaling: GMRES iterates on A D (D constant on the m and j blocks), y = D z after
+    const bool scaled = p->desc.gmres_scaling == 1 && !flexible;
+    const double cm = 2.0 / (p->desc.mu_ext + p->desc.mu_int), cj = 2.0 / (p->desc.eps_ext + p->desc.eps_int);
+    MatvecFn mv = [p, nrhs, scaled, cm, cj](const double* v, double* w, cudaStream_t st) {
+      if (!scaled) return forward(p, v, w, nrhs, st);
+      double* tmp = p->gm.inc;   // [nrhs][6N] complex: free once the right-hand side is formed
+      cudaError_t er = launch_block_scale(p->N, nrhs, cm, cj, v, tmp, st);
+      ++p->launches;
+      return er != cudaSuccess ? er : forward(p, tmp, w, nrhs, st);
+    };
     MatvecFn pc = [p, nrhs](const double* v, double* z, cudaStream_t st) {
       return launch_mlp_apply(p, nrhs, v, z, st);
     };
     e = gmres_run(p, mv, nrhs, tol, max_iter, it.data(), rr.data(), s, flexible ? &pc : nullptr);
+    if (e == cudaSuccess && scaled) e = launch_block_scale(p->N, nrhs, cm, cj, p->gm.y, p->gm.y, s);
   }
   if (e == cudaSuccess) {
     if (is_device_ptr(y))

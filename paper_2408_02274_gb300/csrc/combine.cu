@@ -285,6 +285,22 @@ cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, c
   return cudaGetLastError();
 }
 
+__global__ void k_block_scale(size_t n, size_t N, double cm, double cj, const double* in,
+                              double* out) {   // in == out allowed: each entry is read then written by one thread
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;   // complex entry
+  if (i >= n) return;
+  const double c = ((i / N) & 3) < 2 ? cm : cj;
+  out[2 * i] = c * in[2 * i];
+  out[2 * i + 1] = c * in[2 * i + 1];
+}
+
+cudaError_t launch_block_scale(int N, int nrhs, double cm, double cj, const double* in, double* out,
+                               cudaStream_t s) {
+  const size_t n = 4 * (size_t)N * nrhs;
+  k_block_scale<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (size_t)N, cm, cj, in, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero_f28(const ifgf_plan_t* p, cudaStream_t s) {
   size_t n = (size_t)p->N * 56;
   if (p->desc.precision == IFGF_FP64)

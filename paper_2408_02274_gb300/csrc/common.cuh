@@ -88,7 +88,7 @@ __device__ __forceinline__ void cheb_dvals(T t, T* d) {
 struct ConeGeom {
   double h;      // box radius sqrt(3)/2 H
   int ns, na;
-  __host__ __device__ int ncones() const { return ns * na * 2 * na; }
+  __host__ __device__ int64_t ncones() const { return (int64_t)ns * na * 2 * na; }
   __host__ __device__ double ds() const { return kEta / ns; }
   __host__ __device__ double dth() const { return kPi / na; }
 };
@@ -99,22 +99,26 @@ template <typename T>
 struct ConeGeomT {
   T h, ds, dth, ids, idth;
   int ns, na;
-  __host__ __device__ int ncones() const { return ns * na * 2 * na; }
+  __host__ __device__ int64_t ncones() const { return (int64_t)ns * na * 2 * na; }
 };
 template <typename T>
 inline ConeGeomT<T> cone_geom_t(const ConeGeom& g) {
   return ConeGeomT<T>{(T)g.h, (T)g.ds(), (T)g.dth(), (T)(1.0 / g.ds()), (T)(1.0 / g.dth()), g.ns, g.na};
 }
 
-__host__ __device__ inline void cone_decode(int id, int na, int* g1, int* g2, int* g3) {
-  int n3 = 2 * na;
-  *g3 = id % n3;
-  int r = id / n3;
-  *g2 = r % na;
-  *g1 = r / na;
+// A cone segment (g1, g2, g3) of a level (s-, theta-, phi-cell indices) as a key: three
+// 21-bit fields with g1 most significant, so keys order like (g1, g2, g3) and stay unique
+// for any level (ns, na < 2^20; the product ns * na * 2na may exceed 32 bits on deep trees).
+typedef int64_t cone_key;
+constexpr int kConeBits = 21;
+constexpr int64_t kConeMask = (int64_t(1) << kConeBits) - 1;
+__host__ __device__ inline void cone_decode(cone_key id, int* g1, int* g2, int* g3) {
+  *g3 = (int)(id & kConeMask);
+  *g2 = (int)((id >> kConeBits) & kConeMask);
+  *g1 = (int)(id >> (2 * kConeBits));
 }
-__host__ __device__ inline int cone_encode(int g1, int g2, int g3, int na) {
-  return (g1 * na + g2) * (2 * na) + g3;
+__host__ __device__ inline cone_key cone_encode(int g1, int g2, int g3) {
+  return ((cone_key)g1 << (2 * kConeBits)) | ((cone_key)g2 << kConeBits) | (cone_key)g3;
 }
 
 // Open Chebyshev node k of n on [-1, 1] (Eq. cheby_nodes).

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <stdexcept>
 #include <thread>
 #include <unordered_map>
@@ -29,7 +30,7 @@ static uint64_t morton(int x, int y, int z) {
 
 // Cone segment of the point (x, y, z) relative to a box centre (Eq. box_cone_seg):
 // half-open cells in s, theta, phi, clamped at the top (reading of the cone intervals).
-int cone_of(const ConeGeom& cg, double x, double y, double z) {
+cone_key cone_of(const ConeGeom& cg, double x, double y, double z) {
   double rho = std::sqrt(x * x + y * y);
   double r = std::sqrt(rho * rho + z * z);
   double s = cg.h / r;
@@ -42,14 +43,14 @@ int cone_of(const ConeGeom& cg, double x, double y, double z) {
   g1 = std::min(std::max(g1, 0), cg.ns - 1);
   g2 = std::min(std::max(g2, 0), cg.na - 1);
   g3 = std::min(std::max(g3, 0), 2 * cg.na - 1);
-  return cone_encode(g1, g2, g3, cg.na);
+  return cone_encode(g1, g2, g3);
 }
 
 // Interpolation point q of a cone segment relative to the box centre:
 // tensor product of Ps x Pa x Pa open Chebyshev nodes mapped to the cone domain.
-void interp_point(const ConeGeom& cg, int cone, int q, double* X) {
+void interp_point(const ConeGeom& cg, cone_key cone, int q, double* X) {
   int g1, g2, g3;
-  cone_decode(cone, cg.na, &g1, &g2, &g3);
+  cone_decode(cone, &g1, &g2, &g3);
   int is = q / (kPa * kPa), it = (q / kPa) % kPa, ip = q % kPa;
   double s = (g1 + 0.5 * (1.0 + cheb_node(is, kPs))) * cg.ds();
   double th = (g2 + 0.5 * (1.0 + cheb_node(it, kPa))) * cg.dth();
@@ -213,37 +214,42 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     }
   }
   // relevant cone segments, top-down from level 3 (Eq. rele_cone_d), and the
-  // per-target evaluation lists of step 3 (cousin points of every source box)
+  // per-target evaluation lists of step 3 (cousin points of every source box).  Relevant
+  // cones are kept per box as sorted key lists (the cone count of a level, ns * na * 2na,
+  // is far too large for dense per-box maps on deep trees).
   for (int d = 3; d <= D; ++d) {
     HostLevel& L = t.lv[d];
     ConeGeom cg = L.cg();
     const int nb = (int)L.key.size();
-    const int nco = cg.ncones();
-    std::vector<uint8_t> mark((size_t)nb * nco, 0);
+    std::vector<std::vector<cone_key>> rel(nb);
     // (1) cones containing cousin points; record (target, box, cone)
     std::vector<int64_t> ptr(N + 1, 0);
-    std::vector<int> rb, rc;
+    std::vector<int> rb;
+    std::vector<cone_key> rc;
     for (int s = 0; s < N; ++s) {
       const double* xs = x + 3 * (size_t)t.perm[s];
       int A = t.box_of[d][s];
       for (int B : L.cousin[A]) {
         double c[3];
         box_center(t, d, L.ic[B], c);
-        int cone = cone_of(cg, xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]);
-        mark[(size_t)B * nco + cone] = 1;
+        cone_key cone = cone_of(cg, xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]);
+        rel[B].push_back(cone);
         rb.push_back(B);
         rc.push_back(cone);
       }
       ptr[s + 1] = (int64_t)rb.size();
     }
-    // (2) cones containing interpolation points of the parent's relevant cones
+    // (2) cones containing interpolation points of the parent's relevant cones: the child
+    // cone of parent point q of compact parent cone ci in octant o (box independent)
+    std::vector<cone_key> cc_key;
+    int ncomp_p = 0;
     if (d >= 4) {
       HostLevel& Pp = t.lv[d - 1];
       ConeGeom pg = Pp.cg();
-      int ncomp = (int)Pp.upcone_list.size();
-      Pp.up_cc.assign((size_t)ncomp * 8 * kQ, -1);
-      for (int ci = 0; ci < ncomp; ++ci) {
-        int pc = Pp.upcone_list[ci];
+      ncomp_p = (int)Pp.upcone_list.size();
+      cc_key.assign((size_t)ncomp_p * 8 * kQ, 0);
+      for (int ci = 0; ci < ncomp_p; ++ci) {
+        cone_key pc = Pp.upcone_list[ci];
         for (int q = 0; q < kQ; ++q) {
           double X[3];
           interp_point(pg, pc, q, X);
@@ -252,9 +258,62 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
             double cx = X[0] - off * ((o & 1) ? 1 : -1);
             double cy = X[1] - off * ((o & 2) ? 1 : -1);
             double cz = X[2] - off * ((o & 4) ? 1 : -1);
-            Pp.up_cc[((size_t)ci * 8 + o) * kQ + q] = cone_of(cg, cx, cy, cz);
+            cc_key[((size_t)ci * 8 + o) * kQ + q] = cone_of(cg, cx, cy, cz);
           }
         }
+      }
+      for (int b = 0; b < nb; ++b) {
+        int p = L.parent[b];
+        int o = (L.ic[b][0] & 1) | ((L.ic[b][1] & 1) << 1) | ((L.ic[b][2] & 1) << 2);
+        for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps) {
+          int ci = Pp.slot_upidx[ps];
+          const cone_key* k = &cc_key[((size_t)ci * 8 + o) * kQ];
+          rel[b].insert(rel[b].end(), k, k + kQ);
+        }
+      }
+    }
+    // slots: relevant (box, cone) pairs sorted by box then cone
+    L.box_slot_ptr.assign(nb + 1, 0);
+    L.relcones.assign(nb, {});
+    L.slot_box.clear();
+    L.slot_cone.clear();
+    for (int b = 0; b < nb; ++b) {
+      std::vector<cone_key>& r = rel[b];
+      std::sort(r.begin(), r.end());
+      r.erase(std::unique(r.begin(), r.end()), r.end());
+      for (cone_key c : r) {
+        L.slot_box.push_back(b);
+        L.slot_cone.push_back(c);
+      }
+      L.box_slot_ptr[b + 1] = (int)L.slot_box.size();
+      L.relcones[b].swap(r);
+    }
+    // compact list of this level's relevant cone keys (sorted), and the slot -> compact map
+    L.upcone_list = L.slot_cone;
+    std::sort(L.upcone_list.begin(), L.upcone_list.end());
+    L.upcone_list.erase(std::unique(L.upcone_list.begin(), L.upcone_list.end()), L.upcone_list.end());
+    const int ncomp = (int)L.upcone_list.size();
+    auto compact_of = [&](cone_key c) {
+      return (int)(std::lower_bound(L.upcone_list.begin(), L.upcone_list.end(), c) - L.upcone_list.begin());
+    };
+    L.slot_upidx.resize(L.slot_cone.size());
+    for (size_t s = 0; s < L.slot_cone.size(); ++s) L.slot_upidx[s] = compact_of(L.slot_cone[s]);
+    // (box, compact cone) -> slot, read by the upward step from this level
+    if (d >= 4) {
+      if ((double)nb * ncomp > 2.0e9) throw std::bad_alloc();
+      L.cmap.assign((size_t)nb * ncomp, -1);
+      for (int b = 0; b < nb; ++b)
+        for (int s = L.box_slot_ptr[b]; s < L.box_slot_ptr[b + 1]; ++s)
+          L.cmap[(size_t)b * ncomp + L.slot_upidx[s]] = s;
+    }
+    // the parent's upward tables, with child cones as compact indices of this level
+    if (d >= 4) {
+      HostLevel& Pp = t.lv[d - 1];
+      // (a key that no child box holds belongs to octants without a child; never read: -1)
+      Pp.up_cc.resize(cc_key.size());
+      for (size_t e = 0; e < cc_key.size(); ++e) {
+        const int c = compact_of(cc_key[e]);
+        Pp.up_cc[e] = (c < ncomp && L.upcone_list[c] == cc_key[e]) ? c : -1;
       }
       // The 75 points of a parent cone are split into kUpGroups fixed groups, one per warp
       // of the upward block: contiguous chunks of the 5 x 5 angular grid in snake order
@@ -264,11 +323,11 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
       // octant) the points are ranked by (group, child cone); per (parent cone, group) the
       // runs of at most kUpRunMax consecutive ranked points that share one child cone, over
       // all octants, are listed longest first as start | len << 8 | octant << 16.
-      Pp.up_order.assign((size_t)ncomp * 8 * kQ, 0);
+      Pp.up_order.assign((size_t)ncomp_p * 8 * kQ, 0);
       Pp.up_task.clear();
-      Pp.up_task_ptr.assign((size_t)ncomp * kUpGroups + 1, 0);
+      Pp.up_task_ptr.assign((size_t)ncomp_p * kUpGroups + 1, 0);
       std::vector<int32_t> runs[kUpGroups];
-      for (size_t ci = 0; ci < (size_t)ncomp; ++ci) {
+      for (size_t ci = 0; ci < (size_t)ncomp_p; ++ci) {
         for (auto& r : runs) r.clear();
         for (int o = 0; o < 8; ++o) {
           const size_t g = ci * 8 + o;
@@ -296,45 +355,15 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           Pp.up_task_ptr[ci * kUpGroups + w + 1] = (int32_t)Pp.up_task.size();
         }
       }
-      for (int b = 0; b < nb; ++b) {
-        int p = L.parent[b];
-        int o = (L.ic[b][0] & 1) | ((L.ic[b][1] & 1) << 1) | ((L.ic[b][2] & 1) << 2);
-        for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps) {
-          int ci = Pp.slot_upidx[ps];
-          for (int q = 0; q < kQ; ++q) mark[(size_t)b * nco + Pp.up_cc[((size_t)ci * 8 + o) * kQ + q]] = 1;
-        }
-      }
     }
-    // slots: relevant (box, cone) pairs sorted by box then cone
-    L.cone_map.assign((size_t)nb * nco, -1);
-    L.box_slot_ptr.assign(nb + 1, 0);
-    L.relcones.assign(nb, {});
-    for (int b = 0; b < nb; ++b) {
-      for (int c = 0; c < nco; ++c)
-        if (mark[(size_t)b * nco + c]) {
-          L.cone_map[(size_t)b * nco + c] = (int)L.slot_box.size();
-          L.slot_box.push_back(b);
-          L.slot_cone.push_back(c);
-          L.relcones[b].push_back(c);
-        }
-      L.box_slot_ptr[b + 1] = (int)L.slot_box.size();
-    }
-    // compact list of this level's relevant cone ids, for the upward step into it
-    {
-      std::vector<int> used(nco, -1);
-      for (int c : L.slot_cone) used[c] = 1;
-      L.upcone_list.clear();
-      for (int c = 0; c < nco; ++c)
-        if (used[c] > 0) {
-          used[c] = (int)L.upcone_list.size();
-          L.upcone_list.push_back(c);
-        }
-      L.slot_upidx.resize(L.slot_cone.size());
-      for (size_t s = 0; s < L.slot_cone.size(); ++s) L.slot_upidx[s] = used[L.slot_cone[s]];
-    }
+    // per-target slots: the (box, cone) pairs recorded in (1), found in the box's sorted cones
     L.tgt_ptr = ptr;
     L.tgt_slot.resize(rb.size());
-    for (size_t e = 0; e < rb.size(); ++e) L.tgt_slot[e] = L.cone_map[(size_t)rb[e] * nco + rc[e]];
+    for (size_t e = 0; e < rb.size(); ++e) {
+      const int lo = L.box_slot_ptr[rb[e]], hi = L.box_slot_ptr[rb[e] + 1];
+      const auto first = L.slot_cone.begin() + lo, last = L.slot_cone.begin() + hi;
+      L.tgt_slot[e] = lo + (int)(std::lower_bound(first, last, rc[e]) - first);
+    }
   }
 }
 

@@ -6,8 +6,8 @@
 
 namespace ifgf {
 
-int cone_of(const ConeGeom& cg, double x, double y, double z);
-void interp_point(const ConeGeom& cg, int cone, int q, double* X);
+cone_key cone_of(const ConeGeom& cg, double x, double y, double z);
+void interp_point(const ConeGeom& cg, cone_key cone, int q, double* X);
 
 // Octree, cone counts, relevant cones and target lists.  Throws std::invalid_argument.
 // max_leaf_pts > 0: deepen the (uniform) octree until no leaf box holds more points.

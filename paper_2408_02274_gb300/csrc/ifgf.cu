@@ -57,9 +57,9 @@ __device__ void init_maps(SmallMaps<T>& M) {
 
 // Interpolation point q of cone `cone` relative to the box centre.
 template <typename T>
-__device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeomT<T>& cg, int cone, int q, T* X) {
+__device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeomT<T>& cg, cone_key cone, int q, T* X) {
   int g1, g2, g3;
-  cone_decode(cone, cg.na, &g1, &g2, &g3);
+  cone_decode(cone, &g1, &g2, &g3);
   int is = q / 25, it = (q / 5) % 5, ip = q % 5;
   const T ds = cg.ds, dth = cg.dth;
   T s = ((T)g1 + T(0.5) * (T(1) + M.x3[is])) * ds;
@@ -76,10 +76,10 @@ __device__ inline void cone_point(const SmallMaps<T>& M, const ConeGeomT<T>& cg,
 
 // Local coordinates in [-1, 1]^3 of a point (relative to the box centre) inside cone `cone`.
 template <typename T>
-__device__ inline void local_coords(const ConeGeomT<T>& cg, int cone, T x, T y, T z, T* ts, T* tt, T* tp,
+__device__ inline void local_coords(const ConeGeomT<T>& cg, cone_key cone, T x, T y, T z, T* ts, T* tt, T* tp,
                                     T* rr, T* sth, T* cth, T* sph, T* cph) {
   int g1, g2, g3;
-  cone_decode(cone, cg.na, &g1, &g2, &g3);
+  cone_decode(cone, &g1, &g2, &g3);
   T rho = sqrt_t(x * x + y * y);
   T r = sqrt_t(rho * rho + z * z);
   T s = cg.h / r;
@@ -204,7 +204,7 @@ template <typename T>
 struct LeafArgs {
   const int* box_pt_ptr;
   const int* box_slot_ptr;
-  const int* slot_cone;
+  const cone_key* slot_cone;
   const double* box_center;
   ConeGeomT<T> cg;
   const double* x_sorted;
@@ -308,16 +308,17 @@ template <typename T>
 struct UpArgs {
   // parent level d-1
   const int* slot_box;
-  const int* slot_cone;
+  const cone_key* slot_cone;
   const int* slot_upidx;
   const int* child;        // [nboxes_p][8]
   ConeGeomT<T> cgp;
   // child level d
-  const int* cone_map_c;
-  int ncones_c;
+  const int* cmap_c;       // [nboxes_c][ncomp_c] -> slot
+  int ncomp_c;
+  const cone_key* ckeys_c; // [ncomp_c]
   ConeGeomT<T> cgc;
   double Hc;
-  const int* up_cc;        // [ncompact][8][75]
+  const int* up_cc;        // [ncompact_p][8][75] child cone, compact index of level d
   const T* coefs_c;
   T* coefs_p;
   T ke, ki;
@@ -342,7 +343,8 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
   A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
   A.coefs_p += blockIdx.y * A.cstride_p;
   init_maps(M);
-  const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
+  const int P = A.slot_box[pslot], ci = A.slot_upidx[pslot];
+  const cone_key pcone = A.slot_cone[pslot];
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
   for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = 0;
@@ -355,8 +357,9 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
     if (t < kQ) {
       const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
       const T x = Xp[t][0] - ox, y = Xp[t][1] - oy, z = Xp[t][2] - oz;
-      const int cc = A.up_cc[((size_t)ci * 8 + o) * kQ + t];
-      info[t].cslot = A.cone_map_c[(size_t)cb * A.ncones_c + cc];
+      const int ccx = A.up_cc[((size_t)ci * 8 + o) * kQ + t];
+      const cone_key cc = A.ckeys_c[ccx];
+      info[t].cslot = A.cmap_c[(size_t)cb * A.ncomp_c + ccx];
       T rc, sth, cth, sph, cph;
       local_coords(A.cgc, cc, x, y, z, &info[t].ts, &info[t].tt, &info[t].tp, &rc, &sth, &cth, &sph, &cph);
       // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
@@ -437,7 +440,8 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
   A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
   A.coefs_p += blockIdx.y * A.cstride_p;
   init_maps(M);
-  const int P = A.slot_box[pslot], pcone = A.slot_cone[pslot], ci = A.slot_upidx[pslot];
+  const int P = A.slot_box[pslot], ci = A.slot_upidx[pslot];
+  const cone_key pcone = A.slot_cone[pslot];
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
   for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
@@ -450,9 +454,10 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
     if (cb < 0) continue;
     const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
     const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
-    const int cc = A.up_cc[((size_t)ci * 8 + o) * kQ + q];
+    const int ccx = A.up_cc[((size_t)ci * 8 + o) * kQ + q];
+    const cone_key cc = A.ckeys_c[ccx];
     PtInfo2<T>& I = info[o][q];
-    I.cslot = A.cone_map_c[(size_t)cb * A.ncones_c + cc];
+    I.cslot = A.cmap_c[(size_t)cb * A.ncomp_c + ccx];
     T rc, sth, cth, sph, cph;
     local_coords(A.cgc, cc, x, y, z, &I.ts, &I.tt, &I.tp, &rc, &sth, &cth, &sph, &cph);
     // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
@@ -541,7 +546,7 @@ struct TgtArgs {
   const int64_t* tgt_ptr;
   const int* tgt_slot;
   const int* slot_box;
-  const int* slot_cone;
+  const cone_key* slot_cone;
   const double* box_center;
   ConeGeomT<T> cg;
   const T* coefs;
@@ -589,7 +594,8 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T> A)
     if (lane < nc) {
       TgtScal<T>& Q = S[lane];
       const int slot = A.tgt_slot[c0 + lane];
-      const int box = A.slot_box[slot], cone = A.slot_cone[slot];
+      const int box = A.slot_box[slot];
+      const cone_key cone = A.slot_cone[slot];
       const T xr = (T)(x0 - A.box_center[3 * box]);
       const T yr = (T)(x1 - A.box_center[3 * box + 1]);
       const T zr = (T)(x2 - A.box_center[3 * box + 2]);
@@ -711,7 +717,7 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
     if (d > 3) {
       const DevLevel& Pp = p->dl[d - 1];
       UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, cone_geom_t<T>(Pp.cg),
-                  L.cone_map, L.cg.ncones(), cone_geom_t<T>(L.cg), L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki,
+                  L.cmap, L.ncomp, L.ckeys, cone_geom_t<T>(L.cg), L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki,
                   L.cstride, Pp.cstride};
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {

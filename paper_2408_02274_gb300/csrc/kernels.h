@@ -41,7 +41,9 @@ cudaError_t setup_combine_kernels();
 // (d): f28 = near * phi   (overwrites f28)
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 // far field by the plain direct sum (accumulates into f28)
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
+// rows (device, nrows distinct node indices) restricts the targets to those rows
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1, const int* rows = nullptr,
+                              int nrows = 0);
 cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
                                   double ke, double ki, int precision, void* f28, cudaStream_t s);
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
@@ -66,5 +68,9 @@ cudaError_t mlp_train(ifgf_plan_t* p, int64_t nsamples, const float* X, const fl
 
 // ---- GMRES helpers (gmres.cu)
 cudaError_t launch_rhs(const ifgf_plan_t* p, const double* inc, double* b, cudaStream_t s, int nrhs = 1);
+// out = D in for nrhs blocks [4][N] complex128: the first two components (m) times cm, the
+// last two (j) times cj; in == out allowed.
+cudaError_t launch_block_scale(int N, int nrhs, double cm, double cj, const double* in, double* out,
+                               cudaStream_t s);
 
 }  // namespace ifgf

@@ -106,13 +106,16 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
                                                     const double* __restrict__ nrm,
                                                     const int* __restrict__ leafc,
                                                     const T* __restrict__ a, T ke, T ki,
-                                                    T* __restrict__ f28) {
+                                                    T* __restrict__ f28, const int* __restrict__ rows,
+                                                    int nrows) {
   __shared__ SrcTile<T> tile[128];
   const size_t rb = blockIdx.y;   // right-hand side of a batched call
   a += rb * 16 * (size_t)N;
   f28 += rb * 56 * (size_t)N;
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = l < N;
+  // targets: every node, or the listed rows only (sampled direct evaluation)
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = i < (rows ? nrows : N);
+  const int l = act ? (rows ? rows[i] : i) : 0;
   T xl[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
   int cl[3] = {0, 0, 0};
   if (act)
@@ -185,14 +188,14 @@ cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
-  const unsigned blocks = (unsigned)((p->N + 127) / 128);
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs, const int* rows, int nrows) {
+  const unsigned blocks = (unsigned)(((rows ? nrows : p->N) + 127) / 128);
   if (p->desc.precision == IFGF_FP64)
     k_far_direct<double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28);
+        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, rows, nrows);
   else
     k_far_direct<float><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28);
+        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28, rows, nrows);
   return cudaGetLastError();
 }
 
@@ -203,10 +206,11 @@ cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, con
                                   double ke, double ki, int precision, void* f28, cudaStream_t s) {
   const unsigned blocks = (unsigned)((N + 127) / 128);
   if (precision == IFGF_FP64)
-    k_far_direct<double><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const double*)a, ke, ki, (double*)f28);
+    k_far_direct<double><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const double*)a, ke, ki, (double*)f28,
+                                                 nullptr, 0);
   else
     k_far_direct<float><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const float*)a, (float)ke, (float)ki,
-                                                (float*)f28);
+                                                (float*)f28, nullptr, 0);
   return cudaGetLastError();
 }
 

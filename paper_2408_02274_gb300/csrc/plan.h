@@ -26,13 +26,16 @@ struct HostLevel {
   std::unordered_map<uint64_t, int> index;    // key -> box
   std::vector<std::vector<int>> nbr;          // neighbours (incl. self), Eq. box_neighbor
   std::vector<std::vector<int>> cousin;       // cousins, Eq. box_cousin
-  std::vector<std::vector<int>> relcones;     // sorted relevant cone ids per box (Eq. rele_cone_d)
+  std::vector<std::vector<cone_key>> relcones;  // sorted relevant cone keys per box (Eq. rele_cone_d)
   // slots (relevant cones, sorted by box then cone)
-  std::vector<int> slot_box, slot_cone, box_slot_ptr, cone_map;
-  // this level as a parent of level d+1: compact list of its relevant cone ids
-  std::vector<int> upcone_list;               // compact -> cone id
+  std::vector<int> slot_box, box_slot_ptr;
+  std::vector<cone_key> slot_cone;
+  // compact list of this level's relevant cone keys (sorted, distinct)
+  std::vector<cone_key> upcone_list;          // compact -> cone key
   std::vector<int> slot_upidx;                // slot -> compact index
-  std::vector<int32_t> up_cc;                 // [ncompact][8][75] child cone at level d+1
+  std::vector<int> cmap;                      // [nboxes][ncompact] -> slot or -1 (levels >= 4)
+  // this level as a parent of level d+1
+  std::vector<int32_t> up_cc;                 // [ncompact][8][75] child cone, compact index at d+1
   std::vector<int32_t> up_order;              // [ncompact][8][75] points ranked by (group, child cone)
   std::vector<int32_t> up_task;               // runs start | len << 8 | octant << 16, per (cone, group)
   std::vector<int32_t> up_task_ptr;           // [ncompact * kUpGroups + 1] CSR offsets into up_task
@@ -60,9 +63,11 @@ struct DevLevel {
   ConeGeom cg{};
   double H = 0;
   double* box_center = nullptr;   // [nboxes][3]
-  int* cone_map = nullptr;        // [nboxes][ncones] -> slot or -1
+  int* cmap = nullptr;            // [nboxes][ncomp] -> slot or -1 (levels >= 4)
+  int ncomp = 0;                  // distinct relevant cones of the level
+  cone_key* ckeys = nullptr;      // [ncomp] compact index -> cone key
   int* slot_box = nullptr;        // [nslots]
-  int* slot_cone = nullptr;       // [nslots]
+  cone_key* slot_cone = nullptr;  // [nslots]
   int* box_slot_ptr = nullptr;    // [nboxes+1]
   int* box_pt_ptr = nullptr;      // [nboxes+1] sorted point ranges
   int* child = nullptr;           // [nboxes][8] boxes at level d+1
@@ -74,7 +79,8 @@ struct DevLevel {
   int64_t* tgt_ptr = nullptr;     // [N+1]
   int* tgt_slot = nullptr;        // [ninter]
   int64_t ninter = 0;
-  void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan)
+  void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan); one buffer
+                                  // serves all levels of equal parity (two live levels at a time)
   size_t cstride = 0;             // nslots * 75 * 32: coefficients per right-hand side
 };
 

@@ -55,7 +55,7 @@ ifgf_status ifgf_tree_perm(ifgf_tree t, int32_t* perm, int32_t* leaf_coords) {
 }
 
 ifgf_status ifgf_tree_level(ifgf_tree t, int32_t d, int32_t* nboxes, int32_t* nslots, int32_t* ns, int32_t* na,
-                            int32_t* box_coords, int32_t* box_slot_ptr, int32_t* slot_cone) {
+                            int32_t* box_coords, int32_t* box_slot_ptr, int64_t* slot_cone) {
   if (!t || d < 1 || d > t->D) return IFGF_EINVAL;
   const HostLevel& L = t->lv[d];
   if (nboxes) *nboxes = (int)L.key.size();

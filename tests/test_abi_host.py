@@ -1,6 +1,7 @@
 """CPU tests of the C-ABI library: it loads, exports every declared symbol,
 rejects bad descriptors without touching a GPU, and its host-only octree /
 cone-segment setup (Sec. III-F) satisfies the invariants the IFGF relies on."""
+import ctypes
 import os
 import re
 
@@ -52,6 +53,13 @@ def test_invalid_descriptors_rejected_before_any_gpu_work():
         with pytest.raises(lib.IfgfError) as e:
             lib.ifgf_plan_create(**kw)
         assert e.value.status == status
+
+
+def test_null_plan_arguments_rejected():
+    L = lib.load()
+    patches = (ctypes.c_int32 * 2)(0, 1)
+    assert L.ifgf_apply_direct_patches(None, None, None, patches, 2, None) == lib.IFGF_EINVAL
+    assert L.ifgf_apply(None, None, None, None) == lib.IFGF_EINVAL
 
 
 def _coverage(tree, x, k_max):
@@ -132,9 +140,9 @@ def test_relevant_cones_contain_their_targets():
                 r = np.linalg.norm(rel)
                 sv, th = h / r, np.arctan2(np.hypot(rel[0], rel[1]), rel[2])
                 ph = np.arctan2(rel[1], rel[0]) % (2 * np.pi)
-                g3 = cone % (2 * na)
-                g2 = (cone // (2 * na)) % na
-                g1 = cone // (2 * na * na)
+                g3 = int(cone) & ((1 << 21) - 1)
+                g2 = (int(cone) >> 21) & ((1 << 21) - 1)
+                g1 = int(cone) >> 42
                 assert min(int(sv / (np.sqrt(3) / 3 / ns)), ns - 1) == g1
                 assert min(int(th / (np.pi / na)), na - 1) == g2
                 assert min(int(ph / (np.pi / na)), 2 * na - 1) == g3

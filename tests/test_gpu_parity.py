@@ -193,6 +193,25 @@ def test_gmres_solve_matches_oracle_and_mie(small):
     plan.close()
 
 
+def test_right_scaled_gmres_solves_the_same_system(small):
+    """gmres_scaling = 1 iterates on A D (D = 2/(mu_e+mu_i) on m, 2/(eps_e+eps_i) on j) and
+    returns y = D z: the oracle's dense solution to the same accuracy, with residuals of the
+    unscaled system."""
+    prob, qp, op = small
+    g = op.g
+    inc = plane_wave(g.x, prob.k_ext, prob.omega)
+    b = cbie.rhs(prob, g, inc)
+    yref = np.linalg.solve(cbie.assemble(op), b.reshape(-1)).reshape(4, -1)
+    plan = plan_of(prob, qp, far_mode=lib.IFGF_FAR_DIRECT, precision=lib.IFGF_FP64, gmres_scaling=1)
+    yd = torch.empty((4, prob.n), dtype=torch.complex128, device="cuda")
+    it, rr, st = plan.solve(torch.from_numpy(inc).cuda(), yd, tol=1e-10, max_iter=200)
+    assert st == lib.IFGF_OK and rr <= 1e-10
+    y = yd.cpu().numpy()
+    assert rel(y, yref) < 1e-8
+    assert np.linalg.norm(cbie.apply(op, y) - b) <= 2e-10 * np.linalg.norm(b)
+    plan.close()
+
+
 def test_gmres_reports_non_convergence(small):
     prob, qp, _ = small
     plan = plan_of(prob, qp, far_mode=lib.IFGF_FAR_DIRECT, precision=lib.IFGF_FP64)

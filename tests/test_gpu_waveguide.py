@@ -1,0 +1,149 @@
+"""The waveguide bar: a 20 x 0.3 x 0.14 (vacuum wavelengths) silicon-like bar,
+eps 12.1 in eps 2.1, at patch side 0.2 (610 patches x 10 x 10 nodes, N = 61,000),
+planned with the point-count leaf rule (at most 64 points per leaf box).
+
+The plain FP64 path is compared with the oracle on whole sampled patches (a
+straight-side patch and an end patch); the FP32 IFGF forward map with the
+direct far sum on sampled patches (ifgf_apply_direct_patches), which is itself
+checked bit for bit against the full direct forward map; and a GMRES solve for
+the Gaussian-beam excitation is checked by its true residual."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2408_02274_gb300 as lib  # noqa: E402
+from inputs import gaussian_beam, random_densities, waveguide_bar  # noqa: E402
+from oracle import cbie  # noqa: E402
+
+LEAF_PTS = 64
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def bar():
+    prob = waveguide_bar(0.2)
+    x, _, _ = prob.nodes()
+    xp = x.reshape(prob.num_patches, prob.nc ** 2, 3)
+    diam = [np.linalg.norm(xp[p][:, None] - xp[p][None], axis=-1).max() for p in range(prob.num_patches)]
+    return prob, 0.6 * float(np.median(diam))
+
+
+def make(prob, delta, precision, far, **kw):
+    return lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=precision, far_mode=far,
+                                 ns0=2, na0=3, max_leaf_pts=LEAF_PTS, **kw)
+
+
+def oracle_rows(prob, delta, y, rows):
+    qp = cbie.QuadParams(delta=delta, n_beta=48, cov_d=4.0)
+    g = cbie.geometry_of(prob)
+    K, _ = cbie.kernel_rows(prob, g, rows, qp)
+    S = np.zeros((2, 8, prob.n), dtype=complex)
+    D = np.zeros((2, 6, prob.n), dtype=complex)
+    S[:, :, rows], D[:, :, rows] = cbie.scalar_fields(K, cbie.densities(y, g))
+    return cbie.combine(prob, g, y, S, D)[:, rows]
+
+
+def test_bar_fp64_direct_matches_oracle_on_sampled_patches(bar):
+    """A straight-side patch to 1e-12.  On the end patches the normal-derivative weights
+    lose digits to the body's coordinates (|x| ~ 10 against near distances ~1e-3, where
+    n.(x - y) is second order in |x - y|): the oracle itself moves by ~2e-11 when the same
+    bar is translated by 9.85 along x (an exact symmetry of the operator), so there the bar
+    is four times that measured translation change."""
+    prob, delta = bar
+    y = random_densities(prob.n, 81)
+    plan = make(prob, delta, lib.IFGF_FP64, lib.IFGF_FAR_DIRECT, max_krylov=10)
+    yd = torch.from_numpy(y).cuda()
+    out = torch.empty_like(yd)
+    plan.apply(yd, out)
+    out = out.cpu().numpy()
+    plan.close()
+    npp = prob.nc ** 2
+    end_patch = [k for k, p in enumerate(prob.body.patches) if p[0] == 1][0]
+    rows = np.arange(3 * npp, 4 * npp)
+    assert rel(out[:, rows], oracle_rows(prob, delta, y, rows)) < 1e-12
+    rows = np.arange(end_patch * npp, (end_patch + 1) * npp)
+    ref = oracle_rows(prob, delta, y, rows)
+    moved = waveguide_bar(0.2, center=(-9.85, 0.0, 0.0))
+    floor = rel(oracle_rows(moved, delta, y, rows), ref)
+    assert 1e-13 < floor < 1e-10
+    assert rel(out[:, rows], ref) < max(1e-12, 4 * floor), (rel(out[:, rows], ref), floor)
+
+
+def nodes_of(prob, pats):
+    npp = prob.nc ** 2
+    return torch.from_numpy((np.asarray(pats)[:, None] * npp + np.arange(npp)[None]).ravel().astype(np.int64)).cuda()
+
+
+def test_direct_patches_equal_the_full_direct_map_bitwise(bar):
+    prob, delta = bar
+    plan = make(prob, delta, lib.IFGF_FP32, lib.IFGF_FAR_DIRECT, max_krylov=10)
+    y = torch.from_numpy(random_densities(prob.n, 82)).cuda()
+    full = torch.empty_like(y)
+    part = torch.empty_like(y)
+    plan.apply(y, full)
+    pats = np.sort(np.random.default_rng(83).choice(prob.num_patches, size=37, replace=False))
+    plan.apply_direct_patches(y, part, pats)
+    r = nodes_of(prob, pats)
+    assert torch.equal(full[:, r], part[:, r])
+    plan.close()
+
+
+def test_direct_patches_rejects_invalid_lists(bar):
+    prob, delta = bar
+    plan = make(prob, delta, lib.IFGF_FP32, lib.IFGF_FAR_IFGF, max_krylov=10)
+    y = torch.from_numpy(random_densities(prob.n, 84)).cuda()
+    out = torch.empty_like(y)
+    for pats in ([1, 2, 2], [0, prob.num_patches], [-1], []):
+        with pytest.raises(lib.IfgfError) as e:
+            plan.apply_direct_patches(y, out, pats)
+        assert e.value.status == lib.IFGF_EINVAL
+    plan.apply(y, out)           # the plan stays usable
+    torch.cuda.synchronize()
+    plan.close()
+
+
+def test_bar_ifgf_fp32_matches_direct_on_sampled_patches(bar):
+    prob, delta = bar
+    plan = make(prob, delta, lib.IFGF_FP32, lib.IFGF_FAR_IFGF, max_krylov=10)
+    st = plan.stats()
+    assert st["levels"] >= 9      # the point-count rule deepens the tree past the wavelength rule (8)
+    y = torch.from_numpy(random_densities(prob.n, 85)).cuda()
+    out = torch.empty_like(y)
+    ref = torch.empty_like(y)
+    plan.apply(y, out)
+    pats = np.sort(np.random.default_rng(86).choice(prob.num_patches, size=40, replace=False))
+    plan.apply_direct_patches(y, ref, pats)
+    r = nodes_of(prob, pats)
+    err = float(torch.linalg.norm(out[:, r] - ref[:, r]) / torch.linalg.norm(ref[:, r]))
+    plan.close()
+    assert err < 1e-4, err
+
+
+def test_short_bar_gaussian_beam_solve_true_residual():
+    """GMRES on a 2.5-long bar (eps 12.1 in 2.1, patch side 0.2, 8,800 nodes) with the
+    right scaling converges to 1e-5 and its residual estimate is the true residual.  (The
+    iteration count grows about linearly with the bar's length: 83 at length 2.5, 148 at 5,
+    about 300 at 10.)"""
+    prob = waveguide_bar(0.2, half_lengths=(1.25, 0.15, 0.07))
+    x, _, _ = prob.nodes()
+    xp = x.reshape(prob.num_patches, prob.nc ** 2, 3)
+    delta = 0.6 * float(np.median([np.linalg.norm(xp[p][:, None] - xp[p][None], axis=-1).max()
+                                   for p in range(prob.num_patches)]))
+    plan = make(prob, delta, lib.IFGF_FP32, lib.IFGF_FAR_IFGF, max_krylov=200, gmres_scaling=1)
+    inc = torch.from_numpy(np.ascontiguousarray(
+        gaussian_beam(x, prob.k_ext, prob.omega, focus=(-1.75, 0.0, 0.0), waist=0.2)[None])).cuda()
+    y = torch.empty((1, 4, prob.n), dtype=torch.complex128, device="cuda")
+    its, rrs, st = plan.solve_batch(inc, y, tol=1e-5, max_iter=200)
+    b = torch.empty_like(y)
+    plan.rhs(inc, b)
+    Ay = torch.empty_like(y)
+    plan.apply_batch(y, Ay)
+    true = float(torch.linalg.norm(b - Ay) / torch.linalg.norm(b))
+    plan.close()
+    assert st == lib.IFGF_OK and rrs[0] <= 1e-5 and its[0] <= 150, (its, rrs, st)
+    assert true < 1.5e-5, true
