@@ -151,9 +151,13 @@ ifgf_status ifgf_apply_batch(ifgf_plan plan, int32_t nrhs, const void* y, void* 
  * y and out: DEVICE [4][N] complex128 as ifgf_apply; only the entries of out at the nodes
  * p Nc^2 .. (p+1) Nc^2 - 1 of each listed patch p (in all 4 components) are defined.
  * patches: HOST int32 [npatches], distinct patch indices in [0, P), 1 <= npatches <= P.
- * Arithmetic in the plan's precision.  Allocates a device list of the patches' nodes per
- * call and returns after `stream` has finished.  IFGF_EINVAL on a null pointer, y == out,
- * npatches out of range, a patch out of range or repeated; IFGF_ENOMEM if the node list
+ * The far sum is computed in FP64 whatever the plan's precision (an FP32 sum over all N
+ * sources carries ~sqrt(N) FP32 roundings, 1e-4 at N ~ 3e5: too coarse a reference); the
+ * densities, near matrix and fields are the plan's own, so against ifgf_apply on the same
+ * plan only the far algorithm differs.  For an FP64 plan the entries equal, bit for bit,
+ * those of ifgf_apply with far_mode IFGF_FAR_DIRECT.  Allocates a device copy of the patch
+ * list per call and returns after `stream` has finished.  IFGF_EINVAL on a null pointer, y == out,
+ * npatches out of range, a patch out of range or repeated; IFGF_ENOMEM if the patch list
  * cannot be allocated; IFGF_ECUDA poisons the plan.
  */
 ifgf_status ifgf_apply_direct_patches(ifgf_plan plan, const void* y, void* out, const int32_t* patches,

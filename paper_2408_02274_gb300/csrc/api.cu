@@ -515,26 +515,22 @@ ifgf_status ifgf_apply_direct_patches(ifgf_plan p, const void* y, void* out, con
   if (!p || !y || !out || !patches || y == out) return IFGF_EINVAL;
   if (npatches < 1 || npatches > p->P) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
-  const int npp = p->desc.nc * p->desc.nc;
   std::vector<uint8_t> seen((size_t)p->P, 0);
-  std::vector<int> rows((size_t)npatches * npp);
   for (int32_t i = 0; i < npatches; ++i) {
     const int32_t q = patches[i];
     if (q < 0 || q >= p->P || seen[q]) return IFGF_EINVAL;
     seen[q] = 1;
-    for (int m = 0; m < npp; ++m) rows[(size_t)i * npp + m] = q * npp + m;
   }
-  const int nrows = (int)rows.size();
   cudaStream_t s = (cudaStream_t)stream;
-  int* d_rows = nullptr;
-  if (cudaMalloc(&d_rows, sizeof(int) * (size_t)nrows) != cudaSuccess) {
+  int* d_rows = nullptr;   // the patch list on the device
+  if (cudaMalloc(&d_rows, sizeof(int) * (size_t)npatches) != cudaSuccess) {
     cudaGetLastError();
     return IFGF_ENOMEM;
   }
-  cudaError_t e = cudaMemcpyAsync(d_rows, rows.data(), sizeof(int) * (size_t)nrows, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(d_rows, patches, sizeof(int) * (size_t)npatches, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_density_prep(p, (const double*)y, nullptr, s, 1);
   if (e == cudaSuccess) e = launch_near(p, s, 1);
-  if (e == cudaSuccess) e = launch_far_direct(p, s, 1, d_rows, nrows);
+  if (e == cudaSuccess) e = launch_far_direct(p, s, 1, d_rows, npatches, true);
   if (e == cudaSuccess) e = launch_combine(p, (const double*)y, (double*)out, s, 1);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_rows);

@@ -115,7 +115,9 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     t.lv[d].H = t.H1 / std::ldexp(1.0, d - 1);
     t.lv[d].h = 0.5 * std::sqrt(3.0) * t.lv[d].H;
   }
-  // cone counts (Remark 2, reading R9): n_{.;d} = a_d n_{.;d+1}, a_d = 2 iff k_max H_d > 1/2
+  // cone counts (Remark 2, reading R9): n_{.;d} = a_d n_{.;d+1}, a_d = 2 iff k_max H_d > 1/2;
+  // the radial count is kept at least 2 n_{s;D+1} (reading R25: on low-frequency leaf levels,
+  // k_max H_D <= 1/2, the radial profile of the factored field needs the finer s cells)
   int ns = ns0, na = na0;
   for (int d = D; d >= 1; --d) {
     int a = (k_max * t.lv[d].H > 0.5) ? 2 : 1;
@@ -123,7 +125,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
       ns *= a;
       na *= a;
     }
-    t.lv[d].ns = (d >= 3) ? ns : 0;
+    t.lv[d].ns = (d >= 3) ? std::max(ns, 2 * ns0) : 0;
     t.lv[d].na = (d >= 3) ? na : 0;
   }
   // leaf keys and Morton order

@@ -101,62 +101,74 @@ struct SrcTile {
   T a[16];
 };
 
-template <typename T>
+// T: storage type of the densities and fields (the plan's precision); A: arithmetic type
+// (T, or FP64 for the sampled reference of an FP32 plan).
+template <typename T, typename A = T>
 __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restrict__ x,
                                                     const double* __restrict__ nrm,
                                                     const int* __restrict__ leafc,
-                                                    const T* __restrict__ a, T ke, T ki,
-                                                    T* __restrict__ f28, const int* __restrict__ rows,
-                                                    int nrows) {
-  __shared__ SrcTile<T> tile[128];
+                                                    const T* __restrict__ a, A ke, A ki,
+                                                    T* __restrict__ f28, const int* __restrict__ patches,
+                                                    int npp) {
+  __shared__ SrcTile<A> tile[128];
   const size_t rb = blockIdx.y;   // right-hand side of a batched call
   a += rb * 16 * (size_t)N;
   f28 += rb * 56 * (size_t)N;
-  // targets: every node, or the listed rows only (sampled direct evaluation)
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = i < (rows ? nrows : N);
-  const int l = act ? (rows ? rows[i] : i) : 0;
-  T xl[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
+  // targets: a chunk of up to 128 nodes of one patch (every patch, or the listed ones):
+  // a compact group whose first node is the block's origin, the same in both modes
+  const int cpp = (npp + 127) / 128, chunk = blockIdx.x % cpp;
+  const int patch = patches ? patches[blockIdx.x / cpp] : (int)(blockIdx.x / cpp);
+  const int l0 = patch * npp + chunk * 128;
+  const int nt_blk = min(min(128, npp - chunk * 128), N - l0);
+  const bool act = (int)threadIdx.x < nt_blk;
+  const int l = l0 + (act ? (int)threadIdx.x : 0);
+  // coordinates relative to the block origin, formed in FP64: the differences of
+  // nearby points keep their digits whatever the body's size
+  const double o0 = x[3 * (size_t)l0], o1 = x[3 * (size_t)l0 + 1], o2 = x[3 * (size_t)l0 + 2];
+  A xl[3] = {0, 0, 0}, nl[3] = {0, 0, 0};
   int cl[3] = {0, 0, 0};
-  if (act)
+  if (act) {
+    xl[0] = (A)(x[3 * (size_t)l] - o0);
+    xl[1] = (A)(x[3 * (size_t)l + 1] - o1);
+    xl[2] = (A)(x[3 * (size_t)l + 2] - o2);
     for (int k = 0; k < 3; ++k) {
-      xl[k] = (T)x[3 * (size_t)l + k];
-      nl[k] = (T)nrm[3 * (size_t)l + k];
+      nl[k] = (A)nrm[3 * (size_t)l + k];
       cl[k] = leafc[3 * l + k];
     }
-  T acc[56];
+  }
+  A acc[56];
 #pragma unroll
-  for (int k = 0; k < 56; ++k) acc[k] = T(0);
-  const T kk[2] = {ke, ki};
-  const T inv4pi = T(1.0 / (4.0 * kPi));
+  for (int k = 0; k < 56; ++k) acc[k] = A(0);
+  const A kk[2] = {ke, ki};
+  const A inv4pi = A(1.0 / (4.0 * kPi));
   for (int base = 0; base < N; base += 128) {
     __syncthreads();
     int m = base + threadIdx.x;
     if (m < N) {
-      for (int k = 0; k < 3; ++k) {
-        tile[threadIdx.x].x[k] = (T)x[3 * (size_t)m + k];
-        tile[threadIdx.x].c[k] = leafc[3 * m + k];
-      }
-      for (int k = 0; k < 16; ++k) tile[threadIdx.x].a[k] = a[16 * (size_t)m + k];
+      tile[threadIdx.x].x[0] = (A)(x[3 * (size_t)m] - o0);
+      tile[threadIdx.x].x[1] = (A)(x[3 * (size_t)m + 1] - o1);
+      tile[threadIdx.x].x[2] = (A)(x[3 * (size_t)m + 2] - o2);
+      for (int k = 0; k < 3; ++k) tile[threadIdx.x].c[k] = leafc[3 * m + k];
+      for (int k = 0; k < 16; ++k) tile[threadIdx.x].a[k] = (A)a[16 * (size_t)m + k];
     }
     __syncthreads();
     const int nt = min(128, N - base);
     if (!act) continue;
     for (int q = 0; q < nt; ++q) {
-      const SrcTile<T>& s = tile[q];
+      const SrcTile<A>& s = tile[q];
       if (abs(s.c[0] - cl[0]) <= 1 && abs(s.c[1] - cl[1]) <= 1 && abs(s.c[2] - cl[2]) <= 1) continue;
-      T d0 = xl[0] - s.x[0], d1 = xl[1] - s.x[1], d2 = xl[2] - s.x[2];
-      T r2 = d0 * d0 + d1 * d1 + d2 * d2;
-      T r = sqrt_t(r2);
-      T ir = T(1) / r;
-      T nd = (nl[0] * d0 + nl[1] * d1 + nl[2] * d2) * ir * ir;
+      A d0 = xl[0] - s.x[0], d1 = xl[1] - s.x[1], d2 = xl[2] - s.x[2];
+      A r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      A r = sqrt_t(r2);
+      A ir = A(1) / r;
+      A nd = (nl[0] * d0 + nl[1] * d1 + nl[2] * d2) * ir * ir;
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks) {
-        T sn, cs;
+        A sn, cs;
         sincos_t(kk[ks] * r, &sn, &cs);
-        T g = inv4pi * ir;
-        T gr = g * cs, gi = g * sn;
-        T dr = nd * (-gr - kk[ks] * r * gi), di = nd * (-gi + kk[ks] * r * gr);
+        A g = inv4pi * ir;
+        A gr = g * cs, gi = g * sn;
+        A dr = nd * (-gr - kk[ks] * r * gi), di = nd * (-gi + kk[ks] * r * gr);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           acc[2 * (8 * ks + k)] += gr * s.a[2 * k] - gi * s.a[2 * k + 1];
@@ -171,7 +183,7 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
     }
   }
   if (act)
-    for (int k = 0; k < 56; ++k) f28[56 * (size_t)l + k] += acc[k];
+    for (int k = 0; k < 56; ++k) f28[56 * (size_t)l + k] += (T)acc[k];
 }
 
 }  // namespace
@@ -188,29 +200,35 @@ cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs, const int* rows, int nrows) {
-  const unsigned blocks = (unsigned)(((rows ? nrows : p->N) + 127) / 128);
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs, const int* patches, int npatches,
+                              bool fp64) {
+  const int npp = p->desc.nc * p->desc.nc;
+  const unsigned blocks = (unsigned)((patches ? npatches : p->P) * ((npp + 127) / 128));
   if (p->desc.precision == IFGF_FP64)
     k_far_direct<double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, rows, nrows);
+        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, patches, npp);
+  else if (fp64)
+    k_far_direct<float, double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+        (const float*)p->a_orig, p->desc.k_ext, p->desc.k_int, (float*)p->f28, patches, npp);
   else
     k_far_direct<float><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28, rows, nrows);
+        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28, patches, npp);
   return cudaGetLastError();
 }
 
 // The same direct far-sum kernel on caller-provided arrays (used by the
 // allocation-free entry point): a [N][8] weighted densities and f28 [N][28]
-// accumulators in the given precision; f28 must be zeroed by the caller.
+// accumulators in the given precision; f28 must be zeroed by the caller.  Without a
+// patch structure the target groups are runs of 128 consecutive nodes.
 cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
                                   double ke, double ki, int precision, void* f28, cudaStream_t s) {
   const unsigned blocks = (unsigned)((N + 127) / 128);
   if (precision == IFGF_FP64)
     k_far_direct<double><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const double*)a, ke, ki, (double*)f28,
-                                                 nullptr, 0);
+                                                 nullptr, 128);
   else
     k_far_direct<float><<<blocks, 128, 0, s>>>(N, x, nrm, leafc, (const float*)a, (float)ke, (float)ki,
-                                                (float*)f28, nullptr, 0);
+                                                (float*)f28, nullptr, 128);
   return cudaGetLastError();
 }
 

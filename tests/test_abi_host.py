@@ -117,8 +117,8 @@ def test_cone_counts_follow_the_doubling_rule():
         _, _, _, ns, na = tree.level(d)
         H = tree.h1 / 2 ** (d - 1)
         a = 2 if k * H > 0.5 else 1
-        assert (ns, na) == (a * ns_prev, a * na_prev)
-        ns_prev, na_prev = ns, na
+        assert (ns, na) == (max(a * ns_prev, 2), a * na_prev)   # radial floor 2 n_{s;D+1}
+        ns_prev, na_prev = a * ns_prev, na
 
 
 def test_relevant_cones_contain_their_targets():
