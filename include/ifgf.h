@@ -325,14 +325,15 @@ const char* ifgf_status_string(ifgf_status s);
  * Sec. III-F (relevant boxes Eq. rele_boxes, neighbours and cousins Eqs.
  * box_neighbor / box_cousin, cone counts of Remark 2, relevant cone segments
  * Eq. rele_cone_d) for a point set, exposed for inspection and tests.
- * nodes: host [n][3]; k_max: the largest wavenumber the cones must resolve.
+ * nodes: host [n][3]; k_max: the largest wavenumber the cones must resolve;
+ * max_leaf_pts: the point-count leaf rule of the plan descriptor (0 -> off).
  * A tree from ifgf_tree_create is released with ifgf_tree_destroy; the tree
  * of a plan (ifgf_plan_tree) is borrowed and lives as long as the plan.
  * Output arrays are caller-owned host arrays; pass NULL to query sizes.
  */
 typedef struct ifgf_tree_t* ifgf_tree;
 ifgf_status ifgf_tree_create(const double* nodes, int32_t n, double leaf_size, int32_t min_levels,
-                             double k_max, int32_t ns0, int32_t na0, ifgf_tree* out);
+                             double k_max, int32_t ns0, int32_t na0, int32_t max_leaf_pts, ifgf_tree* out);
 ifgf_status ifgf_tree_destroy(ifgf_tree tree);
 ifgf_status ifgf_plan_tree(ifgf_plan plan, ifgf_tree* out);
 /* levels D, level-1 cube corner [3] and side H_1 */

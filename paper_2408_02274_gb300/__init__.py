@@ -108,7 +108,7 @@ def load(path: str = LIB_PATH):
                                     ctypes.POINTER(ctypes.c_int64)]
     lib.ifgf_status_string.argtypes = [i32]
     lib.ifgf_status_string.restype = ctypes.c_char_p
-    lib.ifgf_tree_create.argtypes = [vp, i32, ctypes.c_double, i32, ctypes.c_double, i32, i32,
+    lib.ifgf_tree_create.argtypes = [vp, i32, ctypes.c_double, i32, ctypes.c_double, i32, i32, i32,
                                      ctypes.POINTER(vp)]
     lib.ifgf_tree_destroy.argtypes = [vp]
     lib.ifgf_plan_tree.argtypes = [vp, ctypes.POINTER(vp)]
@@ -367,13 +367,14 @@ class Tree:
     """Host-only octree and cone-segment tables (ifgf_tree_*); no GPU is used."""
 
     def __init__(self, nodes=None, leaf_size=None, k_max=None, min_levels=0, ns0=1, na0=2, handle=None,
-                 owned=True):
+                 owned=True, max_leaf_pts=0):
         lib = load()
         if handle is None:
             x = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64))
             h = ctypes.c_void_p()
             _check(lib.ifgf_tree_create(ctypes.c_void_p(x.ctypes.data), x.shape[0], float(leaf_size),
-                                        int(min_levels), float(k_max), int(ns0), int(na0), ctypes.byref(h)),
+                                        int(min_levels), float(k_max), int(ns0), int(na0), int(max_leaf_pts),
+                                        ctypes.byref(h)),
                    "ifgf_tree_create")
             handle = h
             self.n = x.shape[0]

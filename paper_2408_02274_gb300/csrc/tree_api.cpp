@@ -10,15 +10,16 @@ using namespace ifgf;
 extern "C" {
 
 ifgf_status ifgf_tree_create(const double* nodes, int32_t n, double leaf_size, int32_t min_levels,
-                             double k_max, int32_t ns0, int32_t na0, ifgf_tree* out) {
+                             double k_max, int32_t ns0, int32_t na0, int32_t max_leaf_pts, ifgf_tree* out) {
   if (!out) return IFGF_EINVAL;
   *out = nullptr;
-  if (!nodes || n < 1 || !(leaf_size > 0) || !(k_max > 0) || ns0 < 1 || na0 < 1 || ns0 > 64 || na0 > 64)
+  if (!nodes || n < 1 || !(leaf_size > 0) || !(k_max > 0) || ns0 < 1 || na0 < 1 || ns0 > 64 || na0 > 64 ||
+      max_leaf_pts < 0 || max_leaf_pts > 1000000)
     return IFGF_EINVAL;
   ifgf_tree_t* t = new (std::nothrow) ifgf_tree_t();
   if (!t) return IFGF_ENOMEM;
   try {
-    build_tree(*t, nodes, n, leaf_size, min_levels > 0 ? min_levels : 3, k_max, ns0, na0);
+    build_tree(*t, nodes, n, leaf_size, min_levels > 0 ? min_levels : 3, k_max, ns0, na0, max_leaf_pts);
   } catch (const std::bad_alloc&) {
     delete t;
     return IFGF_ENOMEM;

@@ -146,3 +146,58 @@ def test_relevant_cones_contain_their_targets():
                 assert min(int(sv / (np.sqrt(3) / 3 / ns)), ns - 1) == g1
                 assert min(int(th / (np.pi / na)), na - 1) == g2
                 assert min(int(ph / (np.pi / na)), 2 * na - 1) == g3
+
+
+def test_point_count_leaf_rule_on_a_thin_bar():
+    """The point-count rule deepens the octree until no leaf box holds more than
+    max_leaf_pts nodes, and no further (one level less would exceed it)."""
+    from inputs import waveguide_bar
+    prob = waveguide_bar(0.2, nc=6)
+    x, _, _ = prob.nodes()
+    base = lib.Tree(x, leaf_size=0.25 * 2 * np.pi / prob.k_ext, k_max=prob.k_int, ns0=2, na0=3)
+    for cap in (64, 16):
+        tree = lib.Tree(x, leaf_size=0.25 * 2 * np.pi / prob.k_ext, k_max=prob.k_int, ns0=2, na0=3,
+                        max_leaf_pts=cap)
+        _, leafc = tree.perm()
+        counts = np.unique(leafc, axis=0, return_counts=True)[1]
+        assert counts.max() <= cap < 0 + np.unique(leafc >> 1, axis=0, return_counts=True)[1].max()
+        assert tree.levels > base.levels
+        tree.close()
+    base.close()
+
+
+def test_bar_tree_exact_once_coverage_sorted_keys_and_radial_floor():
+    """On a deep point-count tree of the bar: every far pair is evaluated exactly once,
+    each box's relevant cone keys are sorted and distinct, every (target, slot) pair refers
+    to the cell holding the target, and the leaf keeps at least 2 n_s;D+1 radial cells."""
+    from inputs import waveguide_bar
+    prob = waveguide_bar(0.5, nc=4, half_lengths=(2.5, 0.15, 0.07))
+    x, _, _ = prob.nodes()
+    tree = lib.Tree(x, leaf_size=0.25 * 2 * np.pi / prob.k_ext, k_max=prob.k_int, ns0=2, na0=3, max_leaf_pts=8)
+    cover, near, max_s = _coverage(tree, x, prob.k_int)
+    assert np.all(cover[near] == 0) and np.all(cover[~near] == 1)
+    assert max_s <= np.sqrt(3) / 3 + 1e-12
+    D = tree.levels
+    perm, _ = tree.perm()
+    for d in range(3, D + 1):
+        coords, ptr, cones, ns, na = tree.level(d)
+        for b in range(coords.shape[0]):
+            kb = cones[ptr[b]:ptr[b + 1]]
+            assert np.all(np.diff(kb) > 0)
+        tp, ts, sb = tree.targets(d)
+        H = tree.h1 / 2 ** (d - 1)
+        h = np.sqrt(3) / 2 * H
+        for s in range(0, x.shape[0], 5):
+            for slot in ts[tp[s]:tp[s + 1]]:
+                b, cone = sb[slot], int(cones[slot])
+                rel = x[perm[s]] - (tree.corner + H * (coords[b] + 0.5))
+                r = np.linalg.norm(rel)
+                g1, g2, g3 = cone >> 42, (cone >> 21) & ((1 << 21) - 1), cone & ((1 << 21) - 1)
+                assert min(int(h / r / (np.sqrt(3) / 3 / ns)), ns - 1) == g1
+                th = np.arctan2(np.hypot(rel[0], rel[1]), rel[2])
+                assert min(int(th / (np.pi / na)), na - 1) == g2
+                ph = np.arctan2(rel[1], rel[0]) % (2 * np.pi)
+                assert min(int(ph / (np.pi / na)), 2 * na - 1) == g3
+    _, _, _, ns_leaf, _ = tree.level(D)
+    assert ns_leaf >= 4
+    tree.close()
