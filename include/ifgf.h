@@ -91,6 +91,34 @@ typedef struct {
                               scaling: same solution, residuals of the unscaled system) */
 } ifgf_plan_desc;
 
+/*
+ * Device memory of a plan before it is created (Remark "On selection of IFGF approach": the
+ * memory of the interpolation data follows from the relevant cone segments, so it can be known
+ * before the run).  Host work only: the octree, cone tables and near-field candidates are
+ * built as ifgf_plan_create builds them; no GPU call is made.  The near matrix is bounded by
+ * counting every candidate patch of every target as singular (ifgf_plan_create keeps the
+ * candidates whose closest point lies within delta), so near_nnz_max, bytes_near_max and the
+ * totals are upper bounds; everything else is exact: bytes_plan_max - ifgf_plan_stats'
+ * device_bytes = (near_nnz_max - near_nnz) * (8 * sizeof(plan precision) + 4).
+ */
+typedef struct {
+  int32_t levels;                /* D */
+  int64_t cones[24];             /* relevant cone segments per level d (index d) */
+  int64_t candidate_pairs;       /* (target, candidate patch) pairs: bounds the singular pairs */
+  int64_t near_nnz_max;          /* near-matrix nonzeros if every candidate were singular */
+  int64_t bytes_geometry;        /* node geometry, sorted copies, permutations, leaf coordinates */
+  int64_t bytes_near_max;        /* near values in the plan's precision, columns, row pointers */
+  int64_t bytes_tables;          /* per-level octree and cone-segment tables */
+  int64_t bytes_coefs;           /* the two cone-coefficient buffers, times batch */
+  int64_t bytes_apply;           /* per-apply densities and fields, times batch */
+  int64_t bytes_gmres;           /* Krylov basis and GMRES work, times batch */
+  int64_t bytes_plan_max;        /* the created plan's device_bytes, upper bound */
+  int64_t bytes_setup_peak_max;  /* largest device use during ifgf_plan_create (temporaries
+                                    included), upper bound */
+} ifgf_plan_estimate_t;
+
+ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t* out);
+
 /* Counts describing a plan (ifgf_plan_stats). */
 typedef struct {
   int32_t n;                 /* nodes */

@@ -25,7 +25,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_ba
            "ifgf_apply_direct_patches",
            "bie_solve", "bie_solve_batch", "bie_solve_many", "bie_solve_precond", "bie_rhs", "ifgf_precond_attach",
            "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
-           "ifgf_plan_stats", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
+           "ifgf_plan_stats", "ifgf_plan_estimate", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
            "ifgf_tree_level", "ifgf_tree_targets", "ifgf_far_direct_noalloc"]
 
@@ -60,6 +60,17 @@ class ifgf_stats(ctypes.Structure):
     ]
 
 
+class ifgf_plan_estimate_t(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32), ("cones", ctypes.c_int64 * 24),
+        ("candidate_pairs", ctypes.c_int64), ("near_nnz_max", ctypes.c_int64),
+        ("bytes_geometry", ctypes.c_int64), ("bytes_near_max", ctypes.c_int64),
+        ("bytes_tables", ctypes.c_int64), ("bytes_coefs", ctypes.c_int64),
+        ("bytes_apply", ctypes.c_int64), ("bytes_gmres", ctypes.c_int64),
+        ("bytes_plan_max", ctypes.c_int64), ("bytes_setup_peak_max", ctypes.c_int64),
+    ]
+
+
 class IfgfError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -80,6 +91,7 @@ def load(path: str = LIB_PATH):
     lib = ctypes.CDLL(path)
     vp, i32 = ctypes.c_void_p, ctypes.c_int32
     lib.ifgf_plan_create.argtypes = [ctypes.POINTER(ifgf_plan_desc), ctypes.POINTER(vp)]
+    lib.ifgf_plan_estimate.argtypes = [ctypes.POINTER(ifgf_plan_desc), ctypes.POINTER(ifgf_plan_estimate_t)]
     lib.ifgf_plan_destroy.argtypes = [vp]
     lib.ifgf_apply.argtypes = [vp, vp, vp, vp]
     lib.ifgf_apply_batch.argtypes = [vp, i32, vp, vp, vp]
@@ -150,14 +162,41 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
-    ng = int(arrs[3].shape[1])
-    d = ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
-                       k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
-                       min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-                       max_leaf_pts, gmres_scaling)
+    d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
+              leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
+              max_leaf_pts, gmres_scaling)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h
+
+
+def _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
+          leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch, max_leaf_pts,
+          gmres_scaling):
+    ng = int(arrs[3].shape[1])
+    return ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
+                          k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
+                          min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
+                          max_leaf_pts, gmres_scaling)
+
+
+def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: float, k_int: float,
+                       eps_ext: float, eps_int: float, mu_ext: float = 1.0, mu_int: float = 1.0, *,
+                       delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
+                       leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
+                       gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
+                       max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0, gmres_scaling: int = 0) -> dict:
+    """ifgf_plan_estimate: the device memory ifgf_plan_create would allocate for the same
+    arguments (host work only; near-matrix figures are upper bounds)."""
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
+    d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
+              leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
+              max_leaf_pts, gmres_scaling)
+    e = ifgf_plan_estimate_t()
+    _check(load().ifgf_plan_estimate(ctypes.byref(d), ctypes.byref(e)), "ifgf_plan_estimate")
+    out = {name: getattr(e, name) for name, _ in ifgf_plan_estimate_t._fields_ if name != "cones"}
+    out["cones"] = list(e.cones[:e.levels + 1])
+    return out
 
 
 def ifgf_plan_destroy(plan):
@@ -451,6 +490,14 @@ class Plan:
         self.nc, self.P = nc, num_patches
         self.handle = ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches, nc, k_ext, k_int, eps_ext,
                                        eps_int, mu_ext, mu_int, **kw)
+
+    @staticmethod
+    def estimate(problem, **kw) -> dict:
+        """The device memory a plan for `problem` with these options would take (no GPU work)."""
+        x, xu, xv = problem.nodes()
+        return ifgf_plan_estimate(x, xu, xv, problem.fine(), problem.num_patches, problem.nc, problem.k_ext,
+                                  problem.k_int, problem.eps_ext, problem.eps_int, problem.mu_ext, problem.mu_int,
+                                  **kw)
 
     @classmethod
     def from_problem(cls, problem, **kw):

@@ -429,6 +429,18 @@ cudaError_t timer_flush(ifgf_plan_t* p) {
 
 using namespace ifgf;
 
+// Byte counts of the device arrays ifgf_plan_create allocates, in the order build() allocates
+// them (a zero-length array takes one element there too).  Keep in step with build().
+namespace {
+struct ByteCount {
+  int64_t total = 0;
+  template <typename T>
+  void dev(size_t count) {
+    total += (int64_t)((count ? count : 1) * sizeof(T));
+  }
+};
+}  // namespace
+
 extern "C" {
 
 const char* ifgf_status_string(ifgf_status s) {
@@ -481,6 +493,128 @@ ifgf_status ifgf_plan_create(const ifgf_plan_desc* desc, ifgf_plan* out) {
   p->desc.nodes = p->desc.dxdu = p->desc.dxdv = p->desc.fine = nullptr;
   p->stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = p;
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t* out) {
+  if (!out) return IFGF_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  ifgf_status st = validate(desc);
+  if (st != IFGF_OK) return st;
+  const ifgf_plan_desc& d = *desc;
+  const int P = d.num_patches, nc = d.nc, ng = d.ng, npp = nc * nc, N = P * npp;
+  const size_t B = (size_t)(d.batch > 0 ? d.batch : 1);
+  const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
+  try {
+    HostTree t;
+    const double leaf = d.leaf_size > 0 ? d.leaf_size : 0.25 * 2.0 * kPi / d.k_ext;
+    build_tree(t, d.nodes, N, leaf, d.min_levels > 0 ? d.min_levels : 3, std::max(d.k_ext, d.k_int), d.ns0, d.na0,
+               d.max_leaf_pts);
+    std::vector<double> gap;
+    std::vector<int64_t> cptr;
+    std::vector<int> cpatch;
+    near_candidates(d.nodes, P, nc, d.delta, gap, cptr, cpatch);
+    const size_t npairs = cpatch.size();
+    const int64_t nnz = near_nnz_bound(t, P, nc, cptr, cpatch);
+    out->levels = t.D;
+    out->candidate_pairs = (int64_t)npairs;
+    out->near_nnz_max = nnz;
+    // node geometry (x, x_u, x_v, n, t1, t2, J, w, g, D table), sorted copies, permutations
+    ByteCount g;
+    for (int k = 0; k < 6; ++k) g.dev<double>(3 * (size_t)N);
+    g.dev<double>(N);
+    g.dev<double>(N);
+    g.dev<double>(3 * (size_t)N);
+    g.dev<double>(npp);
+    g.dev<double>(3 * (size_t)N);
+    g.dev<double>(3 * (size_t)N);
+    g.dev<int>(2 * (size_t)N);
+    g.dev<int>(3 * (size_t)N);
+    // near matrix
+    ByteCount nm;
+    nm.dev<int64_t>((size_t)N + 1);
+    nm.dev<int>((size_t)nnz);
+    if (el == sizeof(double))
+      nm.dev<double>(8 * (size_t)nnz);
+    else
+      nm.dev<float>(8 * (size_t)nnz);
+    // setup temporaries: outer (geometry interpolation) and near-field (closest points, moments)
+    ByteCount so, sn;
+    so.dev<double>(nc);
+    so.dev<double>(npp);
+    so.dev<double>((size_t)ng * ng);
+    so.dev<double>((size_t)P * ng * ng * 9);
+    so.dev<double>((size_t)P * ng * ng * 9);
+    so.dev<double>(nc);
+    sn.dev<int>(npairs);
+    sn.dev<int>(npairs);
+    sn.dev<double>(2 * npairs);
+    sn.dev<uint8_t>(npairs);
+    sn.dev<int>(npairs);                    // singular pairs (at most every candidate)
+    sn.dev<int>(npairs);
+    sn.dev<double>(npairs * 8 * (size_t)npp);
+    sn.dev<double>((size_t)d.n_beta);
+    sn.dev<double>((size_t)d.n_beta);
+    sn.dev<int>((size_t)nnz);
+    // level tables and cone coefficients
+    ByteCount tb;
+    size_t need[2] = {0, 0};
+    for (int dd = 3; dd <= t.D; ++dd) {
+      const HostLevel& L = t.lv[dd];
+      const size_t nb = L.key.size(), nslots = L.slot_box.size();
+      tb.dev<double>(3 * nb);
+      tb.dev<cone_key>(L.upcone_list.size());
+      if (!L.cmap.empty()) tb.dev<int>(L.cmap.size());
+      tb.dev<int>(nslots);
+      tb.dev<cone_key>(nslots);
+      tb.dev<int>(L.box_slot_ptr.size());
+      tb.dev<int>(nb + 1);
+      tb.dev<int>(8 * nb);
+      tb.dev<int>(L.slot_upidx.size());
+      tb.dev<int32_t>(L.up_cc.size());
+      tb.dev<int32_t>(L.up_order.size());
+      tb.dev<int32_t>(L.up_task.size());
+      tb.dev<int32_t>(L.up_task_ptr.size());
+      tb.dev<int64_t>(L.tgt_ptr.size());
+      tb.dev<int32_t>(L.tgt_slot.size());
+      out->cones[dd] = (int64_t)nslots;
+      need[dd & 1] = std::max(need[dd & 1], nslots * kQ * 32 * B);
+    }
+    ByteCount cf;
+    if (d.far_mode == IFGF_FAR_IFGF)
+      for (int a = 0; a < 2; ++a)
+        if (need[a]) (el == sizeof(double)) ? cf.dev<double>(need[a]) : cf.dev<float>(need[a]);
+    // per-apply buffers and GMRES workspace
+    ByteCount ap, gm;
+    for (int k = 0; k < 3; ++k) ap.dev<char>(16 * (size_t)N * el * B);
+    ap.dev<char>(56 * (size_t)N * el * B);
+    ap.dev<double>(16 * (size_t)N * B);
+    const size_t n4 = 4 * (size_t)N, m1 = (size_t)((d.max_krylov > 0 ? d.max_krylov : 300) + 1);
+    gm.dev<double>(2 * n4 * m1 * B);
+    gm.dev<double>(2 * m1 * m1 * B);
+    for (int k = 0; k < 3; ++k) gm.dev<double>(2 * m1 * B);
+    gm.dev<double>(4 * m1 * B);
+    gm.dev<double>(2 * (size_t)dots_blocks((int64_t)n4) * m1 * B);
+    gm.dev<double>(8 * B);
+    for (int k = 0; k < 3; ++k) gm.dev<double>(2 * n4 * B);
+    gm.dev<double>(12 * (size_t)N * B);
+    gm.dev<int>(B);
+    gm.dev<int>(B);
+    out->bytes_geometry = g.total;
+    out->bytes_near_max = nm.total;
+    out->bytes_tables = tb.total;
+    out->bytes_coefs = cf.total;
+    out->bytes_apply = ap.total;
+    out->bytes_gmres = gm.total;
+    out->bytes_plan_max = g.total + nm.total + tb.total + cf.total + ap.total + gm.total;
+    // peak: while the near values are computed (geometry, near matrix and both temporaries
+    // live), or at the end (the whole plan and the outer temporaries)
+    out->bytes_setup_peak_max = std::max(g.total + nm.total + so.total + sn.total, out->bytes_plan_max + so.total);
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  } catch (const std::exception&) {
+    return IFGF_EINVAL;
+  }
   return IFGF_OK;
 }
 

@@ -498,6 +498,37 @@ void near_candidates(const double* x, int P, int nc, double delta, std::vector<d
   }
 }
 
+int64_t near_nnz_bound(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
+                       const std::vector<int>& cpatch) {
+  const int npp = nc * nc;
+  const int N = P * npp;
+  const int D = t.D;
+  const HostLevel& L = t.lv[D];
+  const int nth = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
+  std::vector<int64_t> part(nth, 0);
+  auto work = [&](int tid) {
+    const int l0 = (int)((int64_t)N * tid / nth), l1 = (int)((int64_t)N * (tid + 1) / nth);
+    std::vector<uint8_t> mark(P, 0);
+    int64_t n = 0;
+    for (int l = l0; l < l1; ++l) {
+      for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = 1;
+      n += (cptr[l + 1] - cptr[l]) * (int64_t)npp;
+      const int A = t.box_of[D][t.iperm[l]];
+      for (int B : L.nbr[A])
+        for (int s = L.pt_begin[B]; s < L.pt_end[B]; ++s) n += mark[t.perm[s] / npp] ? 0 : 1;
+      for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = 0;
+    }
+    part[tid] = n;
+  };
+  std::vector<std::thread> th;
+  for (int i = 1; i < nth; ++i) th.emplace_back(work, i);
+  work(0);
+  for (auto& x : th) x.join();
+  int64_t total = 0;
+  for (int64_t v : part) total += v;
+  return total;
+}
+
 void near_structure(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
                     const std::vector<int>& cpatch, const std::vector<uint8_t>& singular,
                     std::vector<int64_t>& row_ptr, std::vector<int>& col, std::vector<int>& pair) {

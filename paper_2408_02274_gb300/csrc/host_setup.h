@@ -18,6 +18,11 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
 void near_candidates(const double* x, int P, int nc, double delta, std::vector<double>& gap,
                      std::vector<int64_t>& cptr, std::vector<int>& cpatch);
 
+// Nonzeros of the near matrix if every candidate were singular (an upper bound on the
+// structure near_structure builds from the closest-point test).
+int64_t near_nnz_bound(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
+                       const std::vector<int>& cpatch);
+
 // CSR structure of the near matrix given which candidates are singular.
 void near_structure(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
                     const std::vector<int>& cpatch, const std::vector<uint8_t>& singular,

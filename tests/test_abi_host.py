@@ -201,3 +201,34 @@ def test_bar_tree_exact_once_coverage_sorted_keys_and_radial_floor():
     _, _, _, ns_leaf, _ = tree.level(D)
     assert ns_leaf >= 4
     tree.close()
+
+
+def test_plan_estimate_host_only():
+    """ifgf_plan_estimate runs on the host (no GPU here) and its parts add up; the GMRES
+    workspace grows by 16 * 4N bytes per Krylov vector (plus the Hessenberg matrix), the
+    per-apply and coefficient buffers scale with the batch, and FP64 near values take twice
+    the FP32 bytes per nonzero."""
+    prob = CONFIG_SPHERE_SMALL(6, ng=12)
+    base = dict(delta=0.3, ns0=2, na0=3, precision=lib.IFGF_FP32)
+    e = lib.Plan.estimate(prob, max_krylov=50, **base)
+    parts = ("bytes_geometry", "bytes_near_max", "bytes_tables", "bytes_coefs", "bytes_apply", "bytes_gmres")
+    assert e["bytes_plan_max"] == sum(e[k] for k in parts)
+    assert all(e[k] > 0 for k in parts)
+    assert e["bytes_setup_peak_max"] >= e["bytes_plan_max"]
+    assert e["levels"] >= 3 and e["near_nnz_max"] > 0 and e["candidate_pairs"] > 0
+    n4 = 4 * prob.n
+    e2 = lib.Plan.estimate(prob, max_krylov=60, **base)
+    dv = e2["bytes_gmres"] - e["bytes_gmres"]
+    basis_and_h = 10 * 16 * n4 + 16 * (61 ** 2 - 51 ** 2)   # 10 more basis vectors, Hessenberg 61^2 vs 51^2
+    assert basis_and_h <= dv < basis_and_h + 2000           # + rotations, projections, partial sums
+    e3 = lib.Plan.estimate(prob, max_krylov=50, batch=3, **base)
+    assert e3["bytes_apply"] == 3 * e["bytes_apply"] and e3["bytes_coefs"] == 3 * e["bytes_coefs"]
+    e4 = lib.Plan.estimate(prob, max_krylov=50, **dict(base, precision=lib.IFGF_FP64))
+    nnz = e["near_nnz_max"]
+    assert e4["bytes_near_max"] - e["bytes_near_max"] == 32 * nnz
+    assert e4["near_nnz_max"] == nnz and e4["cones"] == e["cones"]
+    e5 = lib.Plan.estimate(prob, max_krylov=50, far_mode=lib.IFGF_FAR_DIRECT, **base)
+    assert e5["bytes_coefs"] == 0
+    with pytest.raises(lib.IfgfError) as err:
+        lib.Plan.estimate(prob, **dict(base, delta=0.0))
+    assert err.value.status == lib.IFGF_EINVAL

@@ -259,3 +259,21 @@ def test_apply_is_graph_capturable(small, prec):
     torch.cuda.synchronize()
     assert torch.equal(out, eager)
     plan.close()
+
+
+@pytest.mark.parametrize("prec", [lib.IFGF_FP32, lib.IFGF_FP64])
+def test_plan_estimate_matches_the_created_plan(medium, prec):
+    """ifgf_plan_estimate is exact except for the near matrix, which it bounds by counting every
+    candidate patch as singular: the byte difference is exactly the nonzero difference times
+    the bytes per nonzero (8 values in the plan's precision + a 4-byte column)."""
+    prob, qp = medium[0], medium[1]
+    kw = dict(delta=qp.delta, n_beta=qp.n_beta, cov_d=qp.cov_d, gs_iters=qp.gs_iters, precision=prec,
+              ns0=2, na0=3, max_krylov=40, batch=2)
+    est = lib.Plan.estimate(prob, **kw)
+    plan = plan_of(prob, qp, precision=prec, ns0=2, na0=3, max_krylov=40, batch=2)
+    st = plan.stats()
+    plan.close()
+    el = 8 if prec == lib.IFGF_FP64 else 4
+    assert est["cones"] == st["cones"] and est["levels"] == st["levels"]
+    assert est["near_nnz_max"] >= st["near_nnz"] and est["candidate_pairs"] >= st["singular_pairs"]
+    assert est["bytes_plan_max"] - st["device_bytes"] == (est["near_nnz_max"] - st["near_nnz"]) * (8 * el + 4)
