@@ -88,7 +88,6 @@ __device__ __forceinline__ void cheb_dvals(T t, T* d) {
 struct ConeGeom {
   double h;      // box radius sqrt(3)/2 H
   int ns, na;
-  __host__ __device__ int64_t ncones() const { return (int64_t)ns * na * 2 * na; }
   __host__ __device__ double ds() const { return kEta / ns; }
   __host__ __device__ double dth() const { return kPi / na; }
 };
@@ -99,7 +98,6 @@ template <typename T>
 struct ConeGeomT {
   T h, ds, dth, ids, idth;
   int ns, na;
-  __host__ __device__ int64_t ncones() const { return (int64_t)ns * na * 2 * na; }
 };
 template <typename T>
 inline ConeGeomT<T> cone_geom_t(const ConeGeom& g) {

@@ -276,7 +276,6 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     }
     // slots: relevant (box, cone) pairs sorted by box then cone
     L.box_slot_ptr.assign(nb + 1, 0);
-    L.relcones.assign(nb, {});
     L.slot_box.clear();
     L.slot_cone.clear();
     for (int b = 0; b < nb; ++b) {
@@ -288,7 +287,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
         L.slot_cone.push_back(c);
       }
       L.box_slot_ptr[b + 1] = (int)L.slot_box.size();
-      L.relcones[b].swap(r);
+      std::vector<cone_key>().swap(r);
     }
     // compact list of this level's relevant cone keys (sorted), and the slot -> compact map
     L.upcone_list = L.slot_cone;

@@ -26,7 +26,6 @@ struct HostLevel {
   std::unordered_map<uint64_t, int> index;    // key -> box
   std::vector<std::vector<int>> nbr;          // neighbours (incl. self), Eq. box_neighbor
   std::vector<std::vector<int>> cousin;       // cousins, Eq. box_cousin
-  std::vector<std::vector<cone_key>> relcones;  // sorted relevant cone keys per box (Eq. rele_cone_d)
   // slots (relevant cones, sorted by box then cone)
   std::vector<int> slot_box, box_slot_ptr;
   std::vector<cone_key> slot_cone;
