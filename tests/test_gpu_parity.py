@@ -277,3 +277,27 @@ def test_plan_estimate_matches_the_created_plan(medium, prec):
     assert est["cones"] == st["cones"] and est["levels"] == st["levels"]
     assert est["near_nnz_max"] >= st["near_nnz"] and est["candidate_pairs"] >= st["singular_pairs"]
     assert est["bytes_plan_max"] - st["device_bytes"] == (est["near_nnz_max"] - st["near_nnz"]) * (8 * el + 4)
+
+
+def test_direct_fp64_forward_map_is_invariant_under_rigid_motion(small):
+    """The plain FP64 path on the 6-patch sphere moved by a rotation and a translation gives
+    the same forward map (densities and outputs live in the nodes' own frames); the oracle
+    itself is invariant to 2.4e-14 (tests/test_oracle_operator.py)."""
+    import copy
+    prob, qp, _ = small
+    y = random_densities(prob.n, 17)
+    a = 0.9
+    R = np.array([[np.cos(a), 0.0, np.sin(a)], [0.0, 1.0, 0.0], [-np.sin(a), 0.0, np.cos(a)]])
+    shift = np.array([-2.5, 0.3, 4.0])
+    x, xu, xv = prob.nodes()
+    fine = prob.fine()
+    moved = copy.copy(prob)
+    moved._cache = {"nodes": (x @ R.T + shift, xu @ R.T, xv @ R.T),
+                    "fine": np.concatenate([fine[..., 0:3] @ R.T + shift, fine[..., 3:6] @ R.T,
+                                            fine[..., 6:9] @ R.T], axis=-1)}
+    outs = []
+    for pb in (prob, moved):
+        plan = plan_of(pb, qp, far_mode=lib.IFGF_FAR_DIRECT, precision=lib.IFGF_FP64)
+        outs.append(gpu_apply(plan, y))
+        plan.close()
+    assert rel(outs[1], outs[0]) < 1e-12

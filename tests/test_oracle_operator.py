@@ -105,3 +105,41 @@ def test_closest_point_against_dense_sampling():
         assert d <= dense + 1e-9
         assert d >= dense - 5e-3
         assert -1 <= uv[0] <= 1 and -1 <= uv[1] <= 1
+
+
+def _moved(prob, R, shift):
+    """The same body rigidly moved: x -> R x + shift, tangents -> R (nodes and fine grid)."""
+    import copy
+    x, xu, xv = prob.nodes()
+    fine = prob.fine()
+    m = copy.copy(prob)
+    m._cache = {"nodes": (x @ R.T + shift, xu @ R.T, xv @ R.T),
+                "fine": np.concatenate([fine[..., 0:3] @ R.T + shift, fine[..., 3:6] @ R.T, fine[..., 6:9] @ R.T],
+                                       axis=-1)}
+    return m
+
+
+def test_forward_map_is_invariant_under_rigid_motion():
+    """The forward map acts on densities in each node's (t1, t2) frame and returns the
+    projections on the same frames, so moving the body rigidly (a rotation and a translation)
+    leaves it unchanged: a check on every place where absolute positions, frames or normals
+    enter (kernels, singular moments, closest points, surface derivatives)."""
+    prob = sphere_problem(0.5, 1, 6, 2.25, ng=12)
+    qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=24, cov_d=4.0)
+    y = (np.random.default_rng(2).standard_normal((4, prob.n)) +
+         1j * np.random.default_rng(3).standard_normal((4, prob.n)))
+    ref = cbie.apply(cbie.build_operator(prob, qp), y)
+    a, b, c = 0.3, -1.1, 2.0
+    Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1.0]])
+    Ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1.0, 0], [-np.sin(b), 0, np.cos(b)]])
+    Rx = np.array([[1.0, 0, 0], [0, np.cos(c), -np.sin(c)], [0, np.sin(c), np.cos(c)]])
+    R = Rz @ Ry @ Rx
+    moved = _moved(prob, R, np.array([0.7, -0.4, 1.3]))
+    got = cbie.apply(cbie.build_operator(moved, qp), y)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    # a mirror image is not a rigid motion of the parametrised surface (it reverses the
+    # normal): the same check must then fail, which guards the test against a vacuous pass
+    M = np.diag([1.0, 1.0, -1.0])
+    mirrored = _moved(prob, M, np.zeros(3))
+    bad = cbie.apply(cbie.build_operator(mirrored, qp), y)
+    assert np.linalg.norm(bad - ref) / np.linalg.norm(ref) > 1e-3
