@@ -373,6 +373,13 @@ ifgf_status ifgf_tree_perm(ifgf_tree tree, int32_t* perm, int32_t* leaf_coords);
  * g1 << 42 | g2 << 21 | g3 for the s-, theta- and phi-cell indices, sorted within a box) */
 ifgf_status ifgf_tree_level(ifgf_tree tree, int32_t d, int32_t* nboxes, int32_t* nslots, int32_t* ns,
                             int32_t* na, int32_t* box_coords, int32_t* box_slot_ptr, int64_t* slot_cone);
+/* level d (3..D-1) as the parent of level d+1: the upward tables.  ncompact distinct relevant
+ * cone keys of level d; up_cc [ncompact][8][75] the child cone (compact index at level d+1, -1
+ * where no child box holds it) of each interpolation point and octant; up_order
+ * [ncompact][8][75] the points ranked by (warp group, child cone); up_task [ntask] the runs
+ * start | len << 8 | octant << 16 per (compact cone, group), up_task_ptr [ncompact*4+1]. */
+ifgf_status ifgf_tree_upward(ifgf_tree tree, int32_t d, int64_t* ncompact, int32_t* up_cc, int32_t* up_order,
+                             int64_t* ntask, int32_t* up_task, int32_t* up_task_ptr);
 /* level d (3..D): per sorted target, the relevant cones (slots of level d) it is evaluated from:
  * tgt_ptr [n+1] (int64), tgt_slot [ninter]; slot_box [nslots] box of each slot */
 ifgf_status ifgf_tree_targets(ifgf_tree tree, int32_t d, int64_t* ninter, int64_t* tgt_ptr,

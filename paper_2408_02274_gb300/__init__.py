@@ -27,7 +27,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_ba
            "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
            "ifgf_plan_stats", "ifgf_plan_estimate", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
-           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_far_direct_noalloc"]
+           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_far_direct_noalloc"]
 
 
 class ifgf_plan_desc(ctypes.Structure):
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
     lib.ifgf_tree_perm.argtypes = [vp, vp, vp]
     lib.ifgf_tree_level.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4 + [vp, vp, vp]
     lib.ifgf_tree_targets.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, vp]
+    lib.ifgf_tree_upward.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(ctypes.c_int64), vp, vp]
     lib.ifgf_far_direct_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     for name in EXPORTS:
         if name != "ifgf_status_string":
@@ -468,6 +469,23 @@ class Tree:
                                      ctypes.c_void_p(ts.ctypes.data), ctypes.c_void_p(sb.ctypes.data)),
                "ifgf_tree_targets")
         return tp, ts[:ni.value], sb[:cones.size]
+
+    def upward(self, d: int):
+        """(up_cc [ncompact,8,75], up_order [ncompact,8,75], up_task [ntask], up_task_ptr) of
+        parent level d (3..D-1)."""
+        lib = load()
+        nc, nt = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib.ifgf_tree_upward(self.handle, d, ctypes.byref(nc), None, None, ctypes.byref(nt), None, None),
+               "ifgf_tree_upward")
+        cc = np.zeros((max(nc.value, 1), 8, 75), dtype=np.int32)
+        order = np.zeros_like(cc)
+        task = np.zeros(max(nt.value, 1), dtype=np.int32)
+        ptr = np.zeros(nc.value * 4 + 1, dtype=np.int32)
+        _check(lib.ifgf_tree_upward(self.handle, d, ctypes.byref(nc), ctypes.c_void_p(cc.ctypes.data),
+                                    ctypes.c_void_p(order.ctypes.data), ctypes.byref(nt),
+                                    ctypes.c_void_p(task.ctypes.data), ctypes.c_void_p(ptr.ctypes.data)),
+               "ifgf_tree_upward")
+        return cc[:nc.value], order[:nc.value], task[:nt.value], ptr
 
     def close(self):
         if self.handle and self.owned:

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <stdexcept>
 #include <thread>
@@ -72,6 +73,32 @@ static int up_group(int q) {
 static void box_center(const HostTree& t, int d, const std::array<int, 3>& ic, double* c) {
   double H = t.lv[d].H;
   for (int a = 0; a < 3; ++a) c[a] = t.corner[a] + H * (ic[a] + 0.5);
+}
+
+// f(begin, end) over [0, n) split into contiguous static chunks, one per host thread; an
+// exception thrown by a chunk is rethrown here after all threads have joined.
+template <typename F>
+static void parallel_for(int64_t n, F&& f) {
+  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n / 64 + 1));
+  if (nth == 1) {
+    f((int64_t)0, n);
+    return;
+  }
+  std::vector<std::exception_ptr> err(nth);
+  auto run = [&](int i) {
+    try {
+      f(n * i / nth, n * (i + 1) / nth);
+    } catch (...) {
+      err[i] = std::current_exception();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int i = 1; i < nth; ++i) th.emplace_back(run, i);
+  run(0);
+  for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
 }
 
 void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_levels,
@@ -218,78 +245,116 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
   // relevant cone segments, top-down from level 3 (Eq. rele_cone_d), and the
   // per-target evaluation lists of step 3 (cousin points of every source box).  Relevant
   // cones are kept per box as sorted key lists (the cone count of a level, ns * na * 2na,
-  // is far too large for dense per-box maps on deep trees).
+  // is far too large for dense per-box maps on deep trees).  Every step runs over host
+  // threads on disjoint outputs, in an order that makes the tables independent of the
+  // thread count.
   for (int d = 3; d <= D; ++d) {
     HostLevel& L = t.lv[d];
     ConeGeom cg = L.cg();
     const int nb = (int)L.key.size();
-    std::vector<std::vector<cone_key>> rel(nb);
-    // (1) cones containing cousin points; record (target, box, cone)
+    // (1) cones containing cousin points; record (target, box, cone) in target order
     std::vector<int64_t> ptr(N + 1, 0);
-    std::vector<int> rb;
-    std::vector<cone_key> rc;
-    for (int s = 0; s < N; ++s) {
-      const double* xs = x + 3 * (size_t)t.perm[s];
-      int A = t.box_of[d][s];
-      for (int B : L.cousin[A]) {
-        double c[3];
-        box_center(t, d, L.ic[B], c);
-        cone_key cone = cone_of(cg, xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]);
-        rel[B].push_back(cone);
-        rb.push_back(B);
-        rc.push_back(cone);
+    for (int s = 0; s < N; ++s) ptr[s + 1] = ptr[s] + (int64_t)L.cousin[t.box_of[d][s]].size();
+    std::vector<int> rb(ptr[N]);
+    std::vector<cone_key> rc(ptr[N]);
+    parallel_for(N, [&](int64_t s0, int64_t s1) {
+      for (int64_t s = s0; s < s1; ++s) {
+        const double* xs = x + 3 * (size_t)t.perm[s];
+        const std::vector<int>& cs = L.cousin[t.box_of[d][s]];
+        for (size_t j = 0; j < cs.size(); ++j) {
+          double c[3];
+          box_center(t, d, L.ic[cs[j]], c);
+          rb[ptr[s] + j] = cs[j];
+          rc[ptr[s] + j] = cone_of(cg, xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]);
+        }
       }
-      ptr[s + 1] = (int64_t)rb.size();
-    }
+    });
+    // candidate keys per box: the cousin-point cones of (1), then (2) below.  The cousin
+    // relation is symmetric, so box B's cousin points are the points of the boxes in
+    // cousin[B]; their cones relative to B are in (1) at B's position in their own lists.
+    std::vector<int64_t> koff(nb + 1, 0);
+    parallel_for(nb, [&](int64_t b0, int64_t b1) {
+      for (int64_t B = b0; B < b1; ++B)
+        for (int A : L.cousin[B]) koff[B + 1] += L.pt_end[A] - L.pt_begin[A];
+    });
     // (2) cones containing interpolation points of the parent's relevant cones: the child
     // cone of parent point q of compact parent cone ci in octant o (box independent)
     std::vector<cone_key> cc_key;
+    std::vector<int64_t> poff(nb + 1, 0);
     int ncomp_p = 0;
     if (d >= 4) {
       HostLevel& Pp = t.lv[d - 1];
       ConeGeom pg = Pp.cg();
       ncomp_p = (int)Pp.upcone_list.size();
       cc_key.assign((size_t)ncomp_p * 8 * kQ, 0);
-      for (int ci = 0; ci < ncomp_p; ++ci) {
-        cone_key pc = Pp.upcone_list[ci];
-        for (int q = 0; q < kQ; ++q) {
-          double X[3];
-          interp_point(pg, pc, q, X);
-          for (int o = 0; o < 8; ++o) {
-            double off = 0.5 * L.H;
-            double cx = X[0] - off * ((o & 1) ? 1 : -1);
-            double cy = X[1] - off * ((o & 2) ? 1 : -1);
-            double cz = X[2] - off * ((o & 4) ? 1 : -1);
-            cc_key[((size_t)ci * 8 + o) * kQ + q] = cone_of(cg, cx, cy, cz);
+      parallel_for(ncomp_p, [&](int64_t c0, int64_t c1) {
+        for (int64_t ci = c0; ci < c1; ++ci) {
+          cone_key pc = Pp.upcone_list[ci];
+          for (int q = 0; q < kQ; ++q) {
+            double X[3];
+            interp_point(pg, pc, q, X);
+            for (int o = 0; o < 8; ++o) {
+              double off = 0.5 * L.H;
+              double cx = X[0] - off * ((o & 1) ? 1 : -1);
+              double cy = X[1] - off * ((o & 2) ? 1 : -1);
+              double cz = X[2] - off * ((o & 4) ? 1 : -1);
+              cc_key[((size_t)ci * 8 + o) * kQ + q] = cone_of(cg, cx, cy, cz);
+            }
+          }
+        }
+      });
+      for (int b = 0; b < nb; ++b) {
+        const int p = L.parent[b];
+        poff[b + 1] = (int64_t)(Pp.box_slot_ptr[p + 1] - Pp.box_slot_ptr[p]) * kQ;
+      }
+    }
+    // per box: cousin keys, then parent-point keys; sorted and made distinct per box
+    for (int b = 0; b < nb; ++b) koff[b + 1] += koff[b] + poff[b + 1];
+    std::vector<cone_key> keys(koff[nb]);
+    parallel_for(nb, [&](int64_t b0, int64_t b1) {
+      for (int64_t B = b0; B < b1; ++B) {
+        int64_t w = koff[B];
+        for (int A : L.cousin[B]) {
+          const std::vector<int>& ca = L.cousin[A];
+          const auto it = std::lower_bound(ca.begin(), ca.end(), (int)B);
+          if (it == ca.end() || *it != (int)B) throw std::logic_error("cousin relation not symmetric");
+          const int64_t j = it - ca.begin();
+          for (int s = L.pt_begin[A]; s < L.pt_end[A]; ++s) keys[w++] = rc[ptr[s] + j];
+        }
+        if (d >= 4) {
+          const HostLevel& Pp = t.lv[d - 1];
+          const int p = L.parent[B];
+          const int o = (L.ic[B][0] & 1) | ((L.ic[B][1] & 1) << 1) | ((L.ic[B][2] & 1) << 2);
+          for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps) {
+            const cone_key* k = &cc_key[((size_t)Pp.slot_upidx[ps] * 8 + o) * kQ];
+            for (int q = 0; q < kQ; ++q) keys[w++] = k[q];
           }
         }
       }
-      for (int b = 0; b < nb; ++b) {
-        int p = L.parent[b];
-        int o = (L.ic[b][0] & 1) | ((L.ic[b][1] & 1) << 1) | ((L.ic[b][2] & 1) << 2);
-        for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps) {
-          int ci = Pp.slot_upidx[ps];
-          const cone_key* k = &cc_key[((size_t)ci * 8 + o) * kQ];
-          rel[b].insert(rel[b].end(), k, k + kQ);
-        }
+    });
+    std::vector<int64_t> nkeep(nb + 1, 0);
+    parallel_for(nb, [&](int64_t b0, int64_t b1) {
+      for (int64_t b = b0; b < b1; ++b) {
+        auto first = keys.begin() + koff[b], last = keys.begin() + koff[b + 1];
+        std::sort(first, last);
+        nkeep[b + 1] = std::unique(first, last) - first;
       }
-    }
+    });
     // slots: relevant (box, cone) pairs sorted by box then cone
     L.box_slot_ptr.assign(nb + 1, 0);
-    L.slot_box.clear();
-    L.slot_cone.clear();
-    for (int b = 0; b < nb; ++b) {
-      std::vector<cone_key>& r = rel[b];
-      std::sort(r.begin(), r.end());
-      r.erase(std::unique(r.begin(), r.end()), r.end());
-      for (cone_key c : r) {
-        L.slot_box.push_back(b);
-        L.slot_cone.push_back(c);
-      }
-      L.box_slot_ptr[b + 1] = (int)L.slot_box.size();
-      std::vector<cone_key>().swap(r);
-    }
-    // compact list of this level's relevant cone keys (sorted), and the slot -> compact map
+    for (int b = 0; b < nb; ++b) L.box_slot_ptr[b + 1] = L.box_slot_ptr[b] + (int)nkeep[b + 1];
+    const int nslots = L.box_slot_ptr[nb];
+    L.slot_box.resize(nslots);
+    L.slot_cone.resize(nslots);
+    parallel_for(nb, [&](int64_t b0, int64_t b1) {
+      for (int64_t b = b0; b < b1; ++b)
+        for (int i = 0; i < (int)nkeep[b + 1]; ++i) {
+          L.slot_box[L.box_slot_ptr[b] + i] = (int)b;
+          L.slot_cone[L.box_slot_ptr[b] + i] = keys[koff[b] + i];
+        }
+    });
+    std::vector<cone_key>().swap(keys);
+    // compact list of this level's relevant cone keys (sorted, distinct), and the slot -> compact map
     L.upcone_list = L.slot_cone;
     std::sort(L.upcone_list.begin(), L.upcone_list.end());
     L.upcone_list.erase(std::unique(L.upcone_list.begin(), L.upcone_list.end()), L.upcone_list.end());
@@ -297,25 +362,31 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     auto compact_of = [&](cone_key c) {
       return (int)(std::lower_bound(L.upcone_list.begin(), L.upcone_list.end(), c) - L.upcone_list.begin());
     };
-    L.slot_upidx.resize(L.slot_cone.size());
-    for (size_t s = 0; s < L.slot_cone.size(); ++s) L.slot_upidx[s] = compact_of(L.slot_cone[s]);
+    L.slot_upidx.resize(nslots);
+    parallel_for(nslots, [&](int64_t s0, int64_t s1) {
+      for (int64_t s = s0; s < s1; ++s) L.slot_upidx[s] = compact_of(L.slot_cone[s]);
+    });
     // (box, compact cone) -> slot, read by the upward step from this level
     if (d >= 4) {
       if ((double)nb * ncomp > 2.0e9) throw std::bad_alloc();
       L.cmap.assign((size_t)nb * ncomp, -1);
-      for (int b = 0; b < nb; ++b)
-        for (int s = L.box_slot_ptr[b]; s < L.box_slot_ptr[b + 1]; ++s)
-          L.cmap[(size_t)b * ncomp + L.slot_upidx[s]] = s;
+      parallel_for(nb, [&](int64_t b0, int64_t b1) {
+        for (int64_t b = b0; b < b1; ++b)
+          for (int s = L.box_slot_ptr[b]; s < L.box_slot_ptr[b + 1]; ++s)
+            L.cmap[(size_t)b * ncomp + L.slot_upidx[s]] = s;
+      });
     }
     // the parent's upward tables, with child cones as compact indices of this level
     if (d >= 4) {
       HostLevel& Pp = t.lv[d - 1];
       // (a key that no child box holds belongs to octants without a child; never read: -1)
       Pp.up_cc.resize(cc_key.size());
-      for (size_t e = 0; e < cc_key.size(); ++e) {
-        const int c = compact_of(cc_key[e]);
-        Pp.up_cc[e] = (c < ncomp && L.upcone_list[c] == cc_key[e]) ? c : -1;
-      }
+      parallel_for((int64_t)cc_key.size(), [&](int64_t e0, int64_t e1) {
+        for (int64_t e = e0; e < e1; ++e) {
+          const int c = compact_of(cc_key[e]);
+          Pp.up_cc[e] = (c < ncomp && L.upcone_list[c] == cc_key[e]) ? c : -1;
+        }
+      });
       // The 75 points of a parent cone are split into kUpGroups fixed groups, one per warp
       // of the upward block: contiguous chunks of the 5 x 5 angular grid in snake order
       // (all three radial points of an angular position together), so a group's points
@@ -325,46 +396,58 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
       // runs of at most kUpRunMax consecutive ranked points that share one child cone, over
       // all octants, are listed longest first as start | len << 8 | octant << 16.
       Pp.up_order.assign((size_t)ncomp_p * 8 * kQ, 0);
-      Pp.up_task.clear();
-      Pp.up_task_ptr.assign((size_t)ncomp_p * kUpGroups + 1, 0);
-      std::vector<int32_t> runs[kUpGroups];
-      for (size_t ci = 0; ci < (size_t)ncomp_p; ++ci) {
-        for (auto& r : runs) r.clear();
-        for (int o = 0; o < 8; ++o) {
-          const size_t g = ci * 8 + o;
-          const int32_t* cc = &Pp.up_cc[g * kQ];
-          int32_t* ord = &Pp.up_order[g * kQ];
-          for (int q = 0; q < kQ; ++q) ord[q] = q;
-          std::stable_sort(ord, ord + kQ, [&](int a, int b) {
-            const int ga = up_group(a), gb = up_group(b);
-            return ga != gb ? ga < gb : cc[a] < cc[b];
-          });
-          int r = 0;
-          while (r < kQ) {
-            const int w = up_group(ord[r]);
-            int len = 1;
-            while (len < kUpRunMax && r + len < kQ && up_group(ord[r + len]) == w && cc[ord[r + len]] == cc[ord[r]])
-              ++len;
-            runs[w].push_back(r | (len << 8) | (o << 16));
-            r += len;
+      std::vector<std::vector<int32_t>> ci_tasks(ncomp_p);
+      std::vector<int32_t> ci_count((size_t)ncomp_p * kUpGroups, 0);
+      parallel_for(ncomp_p, [&](int64_t c0, int64_t c1) {
+        std::vector<int32_t> runs[kUpGroups];
+        for (int64_t ci = c0; ci < c1; ++ci) {
+          for (auto& r : runs) r.clear();
+          for (int o = 0; o < 8; ++o) {
+            const size_t g = (size_t)ci * 8 + o;
+            const int32_t* cc = &Pp.up_cc[g * kQ];
+            int32_t* ord = &Pp.up_order[g * kQ];
+            for (int q = 0; q < kQ; ++q) ord[q] = q;
+            std::stable_sort(ord, ord + kQ, [&](int a, int b) {
+              const int ga = up_group(a), gb = up_group(b);
+              return ga != gb ? ga < gb : cc[a] < cc[b];
+            });
+            int r = 0;
+            while (r < kQ) {
+              const int w = up_group(ord[r]);
+              int len = 1;
+              while (len < kUpRunMax && r + len < kQ && up_group(ord[r + len]) == w && cc[ord[r + len]] == cc[ord[r]])
+                ++len;
+              runs[w].push_back(r | (len << 8) | (o << 16));
+              r += len;
+            }
+          }
+          std::vector<int32_t>& out = ci_tasks[ci];
+          for (int w = 0; w < kUpGroups; ++w) {
+            std::stable_sort(runs[w].begin(), runs[w].end(),
+                             [](int32_t a, int32_t b) { return ((a >> 8) & 255) > ((b >> 8) & 255); });
+            out.insert(out.end(), runs[w].begin(), runs[w].end());
+            ci_count[(size_t)ci * kUpGroups + w] = (int32_t)runs[w].size();
           }
         }
-        for (int w = 0; w < kUpGroups; ++w) {
-          std::stable_sort(runs[w].begin(), runs[w].end(),
-                           [](int32_t a, int32_t b) { return ((a >> 8) & 255) > ((b >> 8) & 255); });
-          Pp.up_task.insert(Pp.up_task.end(), runs[w].begin(), runs[w].end());
-          Pp.up_task_ptr[ci * kUpGroups + w + 1] = (int32_t)Pp.up_task.size();
-        }
-      }
+      });
+      Pp.up_task_ptr.assign((size_t)ncomp_p * kUpGroups + 1, 0);
+      for (size_t i = 0; i < ci_count.size(); ++i) Pp.up_task_ptr[i + 1] = Pp.up_task_ptr[i] + ci_count[i];
+      Pp.up_task.resize(Pp.up_task_ptr.back());
+      parallel_for(ncomp_p, [&](int64_t c0, int64_t c1) {
+        for (int64_t ci = c0; ci < c1; ++ci)
+          std::copy(ci_tasks[ci].begin(), ci_tasks[ci].end(), Pp.up_task.begin() + Pp.up_task_ptr[ci * kUpGroups]);
+      });
     }
     // per-target slots: the (box, cone) pairs recorded in (1), found in the box's sorted cones
     L.tgt_ptr = ptr;
     L.tgt_slot.resize(rb.size());
-    for (size_t e = 0; e < rb.size(); ++e) {
-      const int lo = L.box_slot_ptr[rb[e]], hi = L.box_slot_ptr[rb[e] + 1];
-      const auto first = L.slot_cone.begin() + lo, last = L.slot_cone.begin() + hi;
-      L.tgt_slot[e] = lo + (int)(std::lower_bound(first, last, rc[e]) - first);
-    }
+    parallel_for((int64_t)rb.size(), [&](int64_t e0, int64_t e1) {
+      for (int64_t e = e0; e < e1; ++e) {
+        const int lo = L.box_slot_ptr[rb[e]], hi = L.box_slot_ptr[rb[e] + 1];
+        const auto first = L.slot_cone.begin() + lo, last = L.slot_cone.begin() + hi;
+        L.tgt_slot[e] = lo + (int)(std::lower_bound(first, last, rc[e]) - first);
+      }
+    });
   }
 }
 
@@ -535,34 +618,50 @@ void near_structure(const HostTree& t, int P, int nc, const std::vector<int64_t>
   const int N = P * npp;
   const int D = t.D;
   const HostLevel& L = t.lv[D];
-  row_ptr.assign(N + 1, 0);
-  col.clear();
-  pair.clear();
-  std::vector<int> mark(P, -1);   // patch -> singular pair index for the current row
-  for (int l = 0; l < N; ++l) {
+  // Row l: all nodes of the singular patches of x_l (Eq. patch_sing), in candidate order, then
+  // the neighbour points on regular patches (reading R12: IFGF leaves them out), in sorted
+  // order.  Two passes over host threads (count, then fill), each thread with its own patch
+  // marks; the result does not depend on the thread count.
+  auto row = [&](int l, std::vector<int>& mark, int* c, int* q) -> int64_t {
+    int64_t n = 0;
     for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e)
       if (singular[e]) mark[cpatch[e]] = (int)e;
-    // all nodes of the singular patches of x_l (Eq. patch_sing)
     for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e)
       if (singular[e]) {
-        int p = cpatch[e];
-        for (int m = 0; m < npp; ++m) {
-          col.push_back(p * npp + m);
-          pair.push_back((int)e);
-        }
+        const int p = cpatch[e];
+        if (c)
+          for (int m = 0; m < npp; ++m) {
+            c[n + m] = p * npp + m;
+            q[n + m] = (int)e;
+          }
+        n += npp;
       }
-    // neighbour points on regular patches (reading R12): IFGF leaves them out
-    int A = t.box_of[D][t.iperm[l]];
+    const int A = t.box_of[D][t.iperm[l]];
     for (int B : L.nbr[A])
       for (int s = L.pt_begin[B]; s < L.pt_end[B]; ++s) {
-        int m = t.perm[s];
+        const int m = t.perm[s];
         if (mark[m / npp] >= 0) continue;
-        col.push_back(m);
-        pair.push_back(-1);
+        if (c) {
+          c[n] = m;
+          q[n] = -1;
+        }
+        ++n;
       }
     for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = -1;
-    row_ptr[l + 1] = (int64_t)col.size();
-  }
+    return n;
+  };
+  row_ptr.assign(N + 1, 0);
+  parallel_for(N, [&](int64_t l0, int64_t l1) {
+    std::vector<int> mark(P, -1);
+    for (int64_t l = l0; l < l1; ++l) row_ptr[l + 1] = row((int)l, mark, nullptr, nullptr);
+  });
+  for (int l = 0; l < N; ++l) row_ptr[l + 1] += row_ptr[l];
+  col.resize(row_ptr[N]);
+  pair.resize(row_ptr[N]);
+  parallel_for(N, [&](int64_t l0, int64_t l1) {
+    std::vector<int> mark(P, -1);
+    for (int64_t l = l0; l < l1; ++l) row((int)l, mark, col.data() + row_ptr[l], pair.data() + row_ptr[l]);
+  });
 }
 
 }  // namespace ifgf

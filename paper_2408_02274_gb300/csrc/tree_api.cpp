@@ -77,6 +77,19 @@ ifgf_status ifgf_tree_level(ifgf_tree t, int32_t d, int32_t* nboxes, int32_t* ns
   return IFGF_OK;
 }
 
+ifgf_status ifgf_tree_upward(ifgf_tree t, int32_t d, int64_t* ncompact, int32_t* up_cc, int32_t* up_order,
+                             int64_t* ntask, int32_t* up_task, int32_t* up_task_ptr) {
+  if (!t || d < 3 || d >= t->D) return IFGF_EINVAL;
+  const HostLevel& L = t->lv[d];
+  if (ncompact) *ncompact = (int64_t)L.upcone_list.size();
+  if (ntask) *ntask = (int64_t)L.up_task.size();
+  if (up_cc) std::memcpy(up_cc, L.up_cc.data(), sizeof(int32_t) * L.up_cc.size());
+  if (up_order) std::memcpy(up_order, L.up_order.data(), sizeof(int32_t) * L.up_order.size());
+  if (up_task) std::memcpy(up_task, L.up_task.data(), sizeof(int32_t) * L.up_task.size());
+  if (up_task_ptr) std::memcpy(up_task_ptr, L.up_task_ptr.data(), sizeof(int32_t) * L.up_task_ptr.size());
+  return IFGF_OK;
+}
+
 ifgf_status ifgf_tree_targets(ifgf_tree t, int32_t d, int64_t* ninter, int64_t* tgt_ptr, int32_t* tgt_slot,
                               int32_t* slot_box) {
   if (!t || d < 3 || d > t->D) return IFGF_EINVAL;
