@@ -232,3 +232,41 @@ def test_plan_estimate_host_only():
     with pytest.raises(lib.IfgfError) as err:
         lib.Plan.estimate(prob, **dict(base, delta=0.0))
     assert err.value.status == lib.IFGF_EINVAL
+
+
+def test_upward_run_tables_partition_every_parent_point():
+    """The upward tables of each parent level: per (compact cone, octant) the ranking is a
+    permutation of the 75 points; the runs of a (compact cone, warp group) cover each
+    (octant, point) of that group exactly once, are at most 32 long, longest first, and the
+    points of a run share their warp group and child cone."""
+    prob = sphere_problem(2.0, 2, 6, 4.0)
+    x, _, _ = prob.nodes()
+    tree = lib.Tree(x, leaf_size=0.25, k_max=prob.k_int, ns0=2, na0=3)
+
+    def group(q):
+        a = q % 25
+        it, ip = a // 5, a % 5
+        sidx = it * 5 + (4 - ip if it & 1 else ip)
+        return 0 if sidx < 6 else (1 if sidx < 12 else (2 if sidx < 18 else 3))
+
+    for d in range(3, tree.levels):
+        cc, order, task, ptr = tree.upward(d)
+        assert np.all(np.diff(ptr) >= 0) and ptr[-1] == task.size
+        for ci in range(cc.shape[0]):
+            for o in range(8):
+                assert sorted(order[ci, o].tolist()) == list(range(75))
+            for w in range(4):
+                seen = np.zeros((8, 75), dtype=np.int32)
+                lens = []
+                for tk in task[ptr[ci * 4 + w]:ptr[ci * 4 + w + 1]]:
+                    r0, ln, o = tk & 255, (tk >> 8) & 255, (tk >> 16) & 7
+                    assert 1 <= ln <= 32
+                    lens.append(ln)
+                    qs = order[ci, o, r0:r0 + ln]
+                    assert all(group(q) == w for q in qs)
+                    assert len(set(cc[ci, o, qs].tolist())) == 1
+                    seen[o, qs] += 1
+                assert lens == sorted(lens, reverse=True)
+                mine = np.array([group(q) == w for q in range(75)])
+                assert np.all(seen[:, mine] == 1) and np.all(seen[:, ~mine] == 0)
+    tree.close()
