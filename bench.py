@@ -764,7 +764,7 @@ def run_waveguide(args):
            "n": N, "unknowns": 4 * N, "patches": prob.num_patches, "delta": delta,
            "patch_diameter_quantiles": [float(v) for v in np.quantile(diam, [0.0, 0.5, 1.0])],
            "max_leaf_pts": args.leaf_pts, "gmres_scaling": args.gmres_scaling, "host_geometry_s": t_host,
-           "setup_s": setup,
+           "setup_s": setup, "setup_parts_s": st["setup_parts_s"],
            "device_bytes": st["device_bytes"], "levels": st["levels"], "near_nnz": st["near_nnz"],
            "singular_pairs": st["singular_pairs"], "boxes": st["boxes"], "cones": st["cones"],
            "interactions": st["interactions"]}

@@ -132,7 +132,13 @@ typedef struct {
   int64_t near_nnz;          /* nonzeros of the near-field matrix (per kernel) */
   int64_t singular_pairs;    /* (target, patch) pairs treated with the moment rule */
   int64_t device_bytes;      /* device memory held by the plan */
-  double setup_seconds;      /* wall time of plan_create */
+  double setup_seconds;      /* wall time of plan_create, and its parts: */
+  double setup_tree_s;       /*   host octree, cone segments and their tables */
+  double setup_geometry_s;   /*   node geometry and interpolant coefficients (device) */
+  double setup_near_host_s;  /*   near-field candidates and matrix structure (host) */
+  double setup_closest_s;    /*   closest points (device) */
+  double setup_moments_s;    /*   singular moments (device) */
+  double setup_near_values_s;/*   near-matrix values (device) */
 } ifgf_stats;
 
 /*

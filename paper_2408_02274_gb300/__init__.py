@@ -56,7 +56,10 @@ class ifgf_stats(ctypes.Structure):
         ("interactions", ctypes.c_int64 * 24),
         ("leaf_pairs", ctypes.c_int64), ("up_pairs", ctypes.c_int64), ("near_nnz", ctypes.c_int64),
         ("singular_pairs", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-        ("setup_seconds", ctypes.c_double),
+        ("setup_seconds", ctypes.c_double), ("setup_tree_s", ctypes.c_double),
+        ("setup_geometry_s", ctypes.c_double), ("setup_near_host_s", ctypes.c_double),
+        ("setup_closest_s", ctypes.c_double), ("setup_moments_s", ctypes.c_double),
+        ("setup_near_values_s", ctypes.c_double),
     ]
 
 
@@ -366,6 +369,9 @@ def ifgf_plan_stats(plan) -> dict:
         "leaf_pairs": s.leaf_pairs, "up_pairs": s.up_pairs, "near_nnz": s.near_nnz,
         "singular_pairs": s.singular_pairs, "device_bytes": s.device_bytes,
         "setup_seconds": s.setup_seconds,
+        "setup_parts_s": {"tree": s.setup_tree_s, "geometry": s.setup_geometry_s, "near_host": s.setup_near_host_s,
+                          "closest": s.setup_closest_s, "moments": s.setup_moments_s,
+                          "near_values": s.setup_near_values_s},
     }
 
 

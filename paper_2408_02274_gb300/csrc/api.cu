@@ -132,7 +132,12 @@ void build(ifgf_plan_t* p) {
   // ---------------- host octree and cone segments
   double leaf = d.leaf_size > 0 ? d.leaf_size : 0.25 * 2.0 * kPi / d.k_ext;
   double kmax = std::max(d.k_ext, d.k_int);
+  using clk = std::chrono::steady_clock;
+  auto since = [](clk::time_point a) { return std::chrono::duration<double>(clk::now() - a).count(); };
+  clk::time_point t0 = clk::now();
   build_tree(p->tree, d.nodes, N, leaf, d.min_levels > 0 ? d.min_levels : 3, kmax, d.ns0, d.na0, d.max_leaf_pts);
+  p->stats.setup_tree_s = since(t0);
+  t0 = clk::now();
   const HostTree& t = p->tree;
   // ---------------- node geometry
   p->geo.x = A.upload(d.nodes, 3 * (size_t)N);
@@ -183,9 +188,11 @@ void build(ifgf_plan_t* p) {
       for (int k = 0; k < 3; ++k) lc[3 * (size_t)l + k] = t.leafc[l][k];
     p->leafc = A.upload(lc);
   }
+  p->stats.setup_geometry_s = since(t0);
   // ---------------- near field: candidates, closest points, singular moments, matrix
   {
     Scratch SN;   // freed at the end of this block, before the IFGF tables are allocated
+    t0 = clk::now();
     std::vector<double> gap;
     std::vector<int64_t> cptr;
     std::vector<int> cpatch;
@@ -194,6 +201,8 @@ void build(ifgf_plan_t* p) {
     std::vector<int> ptgt(npairs);
     for (int l = 0; l < N; ++l)
       for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) ptgt[e] = l;
+    p->stats.setup_near_host_s = since(t0);
+    t0 = clk::now();
     int* d_ptgt = SN.upload(ptgt);
     int* d_ppatch = SN.upload(cpatch);
     double* d_uv = SN.dev<double>(2 * (size_t)npairs);
@@ -204,6 +213,9 @@ void build(ifgf_plan_t* p) {
     check(cudaGetLastError(), "k_closest launch");
     std::vector<uint8_t> sing(npairs);
     check(cudaMemcpy(sing.data(), d_sing, npairs, cudaMemcpyDeviceToHost), "singular flags D2H");
+    p->stats.setup_closest_s = since(t0);
+    cudaEvent_t ev[4];
+    for (auto& e : ev) check(cudaEventCreate(&e), "setup event");
     std::vector<int> sp_pair, sp_of_pair(npairs, -1);
     for (int e = 0; e < npairs; ++e)
       if (sing[e]) {
@@ -224,13 +236,17 @@ void build(ifgf_plan_t* p) {
     int wpb = 1;
     check(cudaFuncSetAttribute(k_moments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(smw * wpb)),
           "moments smem attr");
+    check(cudaEventRecord(ev[0]), "setup event");
     if (nsp > 0)
       k_moments<<<(nsp + wpb - 1) / wpb, 32 * wpb, smw * wpb>>>(nsp, d_sp_pair, d_ptgt, d_ppatch, d_uv, nc, ng,
           d.n_beta, d.cov_d, d_tb, d_wb, Anc, p->geo.x, p->geo.n, fcoef, d.k_ext, d.k_int, W);
     check(cudaGetLastError(), "k_moments launch");
+    check(cudaEventRecord(ev[1]), "setup event");
+    t0 = clk::now();
     std::vector<int64_t> row_ptr;
     std::vector<int> col, pair;
-    near_structure(t, P, nc, cptr, cpatch, sing, row_ptr, col, pair);
+    near_structure(t, P, nc, cptr, cpatch, sing, row_ptr, col, pair);   // overlaps the moments
+    p->stats.setup_near_host_s += since(t0);
     p->near.nnz = (int64_t)col.size();
     p->stats.near_nnz = p->near.nnz;
     p->near.row_ptr = A.upload(row_ptr);
@@ -241,10 +257,18 @@ void build(ifgf_plan_t* p) {
       p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);
     else
       p->near.val32 = A.dev<float>(8 * (size_t)p->near.nnz);
+    check(cudaEventRecord(ev[2]), "setup event");
     k_near_values<<<(unsigned)(((size_t)N * 32 + 255) / 256), 256>>>(N, nc, p->near.row_ptr, p->near.col, d_pair,
         d_sp_of, W, p->geo.x, p->geo.n, p->geo.w, p->leafc, d.k_ext, d.k_int, p->near.val64, p->near.val32);
     check(cudaGetLastError(), "k_near_values launch");
+    check(cudaEventRecord(ev[3]), "setup event");
     check(cudaDeviceSynchronize(), "near setup");
+    float ms_m = 0, ms_v = 0;
+    check(cudaEventElapsedTime(&ms_m, ev[0], ev[1]), "setup event");
+    check(cudaEventElapsedTime(&ms_v, ev[2], ev[3]), "setup event");
+    p->stats.setup_moments_s = 1e-3 * ms_m;
+    p->stats.setup_near_values_s = 1e-3 * ms_v;
+    for (auto& e : ev) cudaEventDestroy(e);
   }
   // ---------------- IFGF level tables
   p->dl.assign(t.D + 1, DevLevel());
