@@ -734,11 +734,12 @@ def patch_diameters(prob):
 
 
 def run_waveguide(args):
-    """The elongated waveguide bar (20 x 0.3 x 0.14 vacuum wavelengths, eps 12.1 in 2.1) at
-    patch side --bar-h: plan setup time and memory, forward-map time (CUDA events over
-    --steps applies), the FP32 IFGF forward map against the direct far sum on the nodes of
-    random patches (about --sample-rows target rows), and optionally (--solve) a GMRES solve for a Gaussian beam (waist
-    0.2, along +x, focus 0.5 outside the -x end, polarised y) to --tol."""
+    """The elongated waveguide bar (--bar-length x 0.3 x 0.14 vacuum wavelengths, default 20;
+    eps 12.1 in 2.1) at patch side --bar-h: plan setup time and memory, forward-map time (CUDA
+    events over --steps applies), the IFGF forward map (--precision) against the FP64 direct far
+    sum on the nodes of random patches (about --sample-rows target rows), and optionally
+    (--solve) a GMRES solve for a Gaussian beam (waist 0.2, along +x, focus 0.5 outside the -x
+    end, polarised y) to --tol."""
     import torch
     import paper_2408_02274_gb300 as lib
     from paper_2408_02274_gb300 import build as libbuild
@@ -746,7 +747,8 @@ def run_waveguide(args):
     libbuild.build()
     torch.cuda.set_device(0)
     t0 = time.perf_counter()
-    prob = waveguide_bar(args.bar_h)
+    A = 0.5 * args.bar_length
+    prob = waveguide_bar(args.bar_h, half_lengths=(A, 0.15, 0.07))
     x, _, _ = prob.nodes()
     prob.fine()
     N = prob.n
@@ -754,13 +756,15 @@ def run_waveguide(args):
     delta = 0.6 * float(np.median(diam))
     t_host = time.perf_counter() - t0
     t0 = time.perf_counter()
-    plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+    prec = lib.IFGF_FP64 if args.precision == "fp64" else lib.IFGF_FP32
+    plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=prec,
                                  far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_krylov,
                                  max_leaf_pts=args.leaf_pts, gmres_scaling=args.gmres_scaling)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     st = plan.stats()
-    res = {"mode": "waveguide", "workload": f"bar 20 x 0.3 x 0.14 lambda0, eps 12.1 / 2.1, patch side {args.bar_h}",
+    res = {"mode": "waveguide", "precision": args.precision,
+           "workload": f"bar {args.bar_length:g} x 0.3 x 0.14 lambda0, eps 12.1 / 2.1, patch side {args.bar_h}",
            "n": N, "unknowns": 4 * N, "patches": prob.num_patches, "delta": delta,
            "patch_diameter_quantiles": [float(v) for v in np.quantile(diam, [0.0, 0.5, 1.0])],
            "max_leaf_pts": args.leaf_pts, "gmres_scaling": args.gmres_scaling, "host_geometry_s": t_host,
@@ -797,7 +801,7 @@ def run_waveguide(args):
     res.update({"sample_patches": int(npat), "sample_rows": int(npat * npp), "rel_err_vs_direct_on_rows": err,
                 "direct_rows_s": t_rows})
     if args.solve:
-        inc = gaussian_beam(x, prob.k_ext, prob.omega, focus=(-10.5, 0.0, 0.0), waist=0.2)
+        inc = gaussian_beam(x, prob.k_ext, prob.omega, focus=(-A - 0.5, 0.0, 0.0), waist=0.2)
         incd = torch.from_numpy(np.ascontiguousarray(inc[None])).cuda()
         ys = torch.empty((1, 4, N), dtype=torch.complex128, device="cuda")
         torch.cuda.synchronize()
@@ -833,6 +837,8 @@ def main():
     ap.add_argument("--leaf-pts", type=int, default=64)
     ap.add_argument("--sample-rows", type=int, default=10000)
     ap.add_argument("--gmres-scaling", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--bar-length", type=float, default=20.0)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)
