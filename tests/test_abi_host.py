@@ -270,3 +270,19 @@ def test_upward_run_tables_partition_every_parent_point():
                 mine = np.array([group(q) == w for q in range(75)])
                 assert np.all(seen[:, mine] == 1) and np.all(seen[:, ~mine] == 0)
     tree.close()
+
+
+def test_plan_estimate_uses_the_plan_tree():
+    """The estimate's levels and relevant-cone counts are those of the host tree the plan
+    builds (same leaf rules, wavenumber and cone base)."""
+    from inputs import waveguide_bar
+    prob = waveguide_bar(0.5, nc=4, half_lengths=(2.5, 0.15, 0.07))
+    leaf = 0.25 * 2 * np.pi / prob.k_ext
+    e = lib.Plan.estimate(prob, delta=0.3, ns0=2, na0=3, max_leaf_pts=8, precision=lib.IFGF_FP32, max_krylov=10)
+    x, _, _ = prob.nodes()
+    tree = lib.Tree(x, leaf_size=leaf, k_max=max(prob.k_ext, prob.k_int), ns0=2, na0=3, max_leaf_pts=8)
+    assert e["levels"] == tree.levels
+    for d in range(3, tree.levels + 1):
+        _, _, cones, _, _ = tree.level(d)
+        assert e["cones"][d] == cones.size
+    tree.close()
