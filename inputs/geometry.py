@@ -152,18 +152,19 @@ def superellipsoid_bar(half_lengths, exponent: int, split_per_face, center=(0.0,
     return body
 
 
-def rounded_bar(half_lengths, end_length: float, patch_size: float, center=(0.0, 0.0, 0.0)) -> Body:
+def rounded_bar(half_lengths, end_length: float, patch_size: float, center=(0.0, 0.0, 0.0),
+                exponent: int = 8) -> Body:
     """A straight bar of length 2A along x with rounded-rectangle cross-section
-    |y/B|^8 + |z/C|^8 = 1, closed at each end by half of the superellipsoid
-    |x'/L|^8 + |y/B|^8 + |z/C|^8 = 1 (x' the distance past the end of the straight part,
-    L = `end_length`), so the total length stays 2A.  The surface is C^7 where the straight
-    part meets the ends and analytic on every patch.
+    |y/B|^e + |z/C|^e = 1 (e = `exponent`, even; 8 by default), closed at each end by half of the
+    superellipsoid |x'/L|^e + |y/B|^e + |z/C|^e = 1 (x' the distance past the end of the straight
+    part, L = `end_length`), so the total length stays 2A.  The surface is C^(e-1) where the
+    straight part meets the ends and analytic on every patch.
 
     Parts (each split into patches of side about `patch_size`):
       - four straight sides (normals +z, -z, +y, -y): x = (A - L) U linear in U, and across the
-        side the 2-D cube map (t, 1)/(1 + t^8)^(1/8), t = tan(pi V/4), scaled by (B, C);
+        side the 2-D cube map (t, 1)/(1 + t^e)^(1/e), t = tan(pi V/4), scaled by (B, C);
       - at each end, the end face of the small superellipsoid (L, B, C) under the cube-face map
-        w = q/|q|_8, q = (tan(pi U/4), tan(pi V/4), 1) rotated, and the halves of its four side
+        w = q/|q|_e, q = (tan(pi U/4), tan(pi V/4), 1) rotated, and the halves of its four side
         faces that lie beyond the straight part; at the junction these take the same
         cross-section parametrisation as the straight sides.
     Patch tuples are (kind, face, I, J, (nu, nv), (U0, U1)) with kind 0 = straight side,
@@ -172,6 +173,9 @@ def rounded_bar(half_lengths, end_length: float, patch_size: float, center=(0.0,
     analytic maps (exact to rounding)."""
     A, B, C = (float(v) for v in half_lengths)
     L = float(end_length)
+    e = int(exponent)
+    if e < 2 or e % 2:
+        raise ValueError("exponent must be even and >= 2")
     if not (0.0 < L < A):
         raise ValueError("need 0 < end_length < A")
     scale = np.array([1.0, B, C])
@@ -182,12 +186,12 @@ def rounded_bar(half_lengths, end_length: float, patch_size: float, center=(0.0,
         R = _FACE_ROT[face]
         tv = np.tan(np.pi * vv / 4.0)
         if kind == 0:
-            s = 1.0 / (1.0 + tv ** 8) ** 0.125
+            s = 1.0 / (1.0 + tv ** e) ** (1.0 / e)
             w = np.stack([np.zeros_like(tv), s * tv, s * np.ones_like(tv)], axis=-1) @ R.T
             return w * scale + np.stack([a0 * uu + 0.0 * tv, 0.0 * tv, 0.0 * tv], axis=-1) + cen
         tu = np.tan(np.pi * uu / 4.0)
         q = np.stack([tu, tv, np.ones_like(tu)], axis=-1) @ R.T
-        w = q / np.sum(q ** 8, axis=-1)[..., None] ** 0.125
+        w = q / np.sum(q ** e, axis=-1)[..., None] ** (1.0 / e)
         return w * np.array([L, B, C]) + np.array([side * a0, 0.0, 0.0]) + cen
 
     # parts: (kind, face, U0, U1)

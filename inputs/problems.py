@@ -195,7 +195,7 @@ def gaussian_beam(x: np.ndarray, k_ext: float, omega: float, focus, waist: float
 
 def waveguide_bar(patch_size: float = 0.035, nc: int = 10, wavelength: float = 1.0,
                   half_lengths=(10.0, 0.15, 0.07), end_length: float = 0.15, eps_ext: float = 2.1,
-                  eps_int: float = 12.1, center=(0.0, 0.0, 0.0)):
+                  eps_int: float = 12.1, center=(0.0, 0.0, 0.0), exponent: int = 8):
     """The elongated waveguide bar: a straight bar 2A = 20 vacuum wavelengths long with the
     rounded-rectangle cross-section |y/B|^8 + |z/C|^8 = 1 (B = 0.15, C = 0.07: 0.3 x 0.14),
     closed by superellipsoidal ends 0.15 long (``rounded_bar``); silicon-like eps_int = 12.1
@@ -203,6 +203,6 @@ def waveguide_bar(patch_size: float = 0.035, nc: int = 10, wavelength: float = 1
     `patch_size` wavelengths: 0.035 gives about 1.5M nodes at nc = 10."""
     from .geometry import rounded_bar
     hl = tuple(float(h) * wavelength for h in half_lengths)
-    body = rounded_bar(hl, end_length * wavelength, patch_size * wavelength, center=center)
+    body = rounded_bar(hl, end_length * wavelength, patch_size * wavelength, center=center, exponent=exponent)
     return Problem(body=body, nc=nc, ng=max(2 * nc, 24), eps_ext=eps_ext, eps_int=eps_int,
                    omega=2 * np.pi / wavelength, name=f"bar_h{patch_size:g}_P{body.num_patches}")
