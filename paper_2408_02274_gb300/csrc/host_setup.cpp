@@ -94,7 +94,12 @@ static void parallel_for(int64_t n, F&& f) {
     }
   };
   std::vector<std::thread> th;
-  for (int i = 1; i < nth; ++i) th.emplace_back(run, i);
+  int started = 1;
+  try {
+    for (; started < nth; ++started) th.emplace_back(run, started);
+  } catch (...) {   // no more threads: the remaining chunks run here
+  }
+  for (int i = started; i < nth; ++i) run(i);
   run(0);
   for (auto& x : th) x.join();
   for (auto& e : err)
