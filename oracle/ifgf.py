@@ -206,8 +206,9 @@ def local_coords(lv: Level, cones: np.ndarray, rel: np.ndarray):
 
 
 def build_tree(x: np.ndarray, leaf_size: float, k_max: float, ns0: int, na0: int, max_leaf_pts: int = 0,
-               min_levels: int = 3) -> Tree:
-    """Step 1 of the algorithm: boxes, neighbours, cousins, cone counts, relevant cones."""
+               min_levels: int = 3, radial_floor: bool = True) -> Tree:
+    """Step 1 of the algorithm: boxes, neighbours, cousins, cone counts, relevant cones.
+    `radial_floor` False drops reading R25 (the paper's recursion alone)."""
     x = np.asarray(x, dtype=np.float64)
     lo, hi = x.min(axis=0), x.max(axis=0)
     H1 = float(np.max(hi - lo)) * (1.0 + 1e-9)        # level-1 box: the bounding box's largest side (R11)
@@ -235,7 +236,8 @@ def build_tree(x: np.ndarray, leaf_size: float, k_max: float, ns0: int, na0: int
         a = 2 if k_max * H > 0.5 else 1
         if d >= 3:
             ns, na = ns * a, na * a
-        levels[d] = Level(d=d, H=H, ns=max(ns, 2 * ns0) if d >= 3 else 0, na=na if d >= 3 else 0)
+        levels[d] = Level(d=d, H=H, ns=(max(ns, 2 * ns0) if radial_floor else ns) if d >= 3 else 0,
+                          na=na if d >= 3 else 0)
     # relevant boxes per level, with their points (Eq. rele_boxes)
     box_of = {}
     for d in range(1, D + 1):

@@ -125,3 +125,22 @@ def test_oracle_tree_matches_the_library_host_tables(case):
         mine = {(int(n), tuple(lv.boxes[b].tolist()), int(k)) for n, b, k in zip(lv.tgt_node, lv.tgt_box, lv.tgt_key)}
         assert host == mine
     ht.close()
+
+
+def test_radial_floor_on_a_low_frequency_leaf():
+    """Reading R25 on the oracle: a deep point-count tree whose leaf level has k_max H_D <= 1/2
+    keeps the base radial count 2 without the floor; the floor's 4 cells cut the error about
+    four-fold (measured S 8.5e-5 -> 2.2e-5, dS/dn 6.4e-4 -> 1.6e-4)."""
+    prob = waveguide_bar(0.5, nc=4, half_lengths=(1.5, 0.15, 0.07), eps_ext=1.0, eps_int=2.25)
+    g, a = _densities(prob, 1)
+    leaf = 0.25 * 2 * np.pi / prob.k_ext
+    kmax = max(prob.k_ext, prob.k_int)
+    errs = {}
+    for floor in (False, True):
+        tree = ifgf.build_tree(g.x, leaf, kmax, 2, 3, max_leaf_pts=8, radial_floor=floor)
+        assert kmax * tree.levels[tree.D].H <= 0.5
+        assert tree.levels[tree.D].ns == (4 if floor else 2)
+        ref = ifgf.direct_far(g.x, g.n, a, prob.k_ext, prob.k_int, tree.leafc)
+        ap = ifgf.ifgf_far(tree, g.x, g.n, a, prob.k_ext, prob.k_int)
+        errs[floor] = (rel(ap[:, :16], ref[:, :16]), rel(ap[:, 16:], ref[:, 16:]))
+    assert errs[True][0] < 0.4 * errs[False][0] and errs[True][1] < 0.4 * errs[False][1], errs
