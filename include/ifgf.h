@@ -188,8 +188,8 @@ ifgf_status ifgf_apply_batch(ifgf_plan plan, int32_t nrhs, const void* y, void* 
  * The far sum is computed in FP64 whatever the plan's precision (an FP32 sum over all N
  * sources carries ~sqrt(N) FP32 roundings, 1e-4 at N ~ 3e5: too coarse a reference); the
  * densities, near matrix and fields are the plan's own, so against ifgf_apply on the same
- * plan only the far algorithm differs.  For an FP64 plan the entries equal, bit for bit,
- * those of ifgf_apply with far_mode IFGF_FAR_DIRECT.  Allocates a device copy of the patch
+ * plan only the far algorithm differs.  For an FP64 plan the entries equal those of
+ * ifgf_apply with far_mode IFGF_FAR_DIRECT up to rounding (the same sums, grouped by patch).  Allocates a device copy of the patch
  * list per call and returns after `stream` has finished.  IFGF_EINVAL on a null pointer, y == out,
  * npatches out of range, a patch out of range or repeated; IFGF_ENOMEM if the patch list
  * cannot be allocated; IFGF_ECUDA poisons the plan.

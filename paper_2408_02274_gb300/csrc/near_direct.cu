@@ -204,7 +204,12 @@ cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs, co
                               bool fp64) {
   const int npp = p->desc.nc * p->desc.nc;
   const unsigned blocks = (unsigned)((patches ? npatches : p->P) * ((npp + 127) / 128));
-  if (p->desc.precision == IFGF_FP64)
+  if (p->desc.precision == IFGF_FP64 && !patches) {
+    // FP64 keeps the digits of nearby differences without patch-local origins: every block
+    // takes 128 consecutive nodes (no idle lanes when N_c^2 is not a multiple of 128)
+    k_far_direct<double><<<dim3((unsigned)((p->N + 127) / 128), nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n,
+        p->leafc, (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, nullptr, 128);
+  } else if (p->desc.precision == IFGF_FP64)
     k_far_direct<double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
         (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, patches, npp);
   else if (fp64)

@@ -5,7 +5,7 @@ planned with the point-count leaf rule (at most 64 points per leaf box).
 The plain FP64 path is compared with the oracle on whole sampled patches (a
 straight-side patch and an end patch); the FP32 IFGF forward map with the
 FP64 direct far sum on sampled patches (ifgf_apply_direct_patches), which is
-itself checked bit for bit against the full FP64 direct forward map; and a
+itself checked against the full FP64 direct forward map (to rounding); and a
 GMRES solve for a Gaussian-beam excitation on a shorter bar by its true
 residual."""
 import numpy as np
@@ -80,7 +80,7 @@ def nodes_of(prob, pats):
     return torch.from_numpy((np.asarray(pats)[:, None] * npp + np.arange(npp)[None]).ravel().astype(np.int64)).cuda()
 
 
-def test_direct_patches_equal_the_full_direct_map_bitwise(bar):
+def test_direct_patches_equal_the_full_direct_map(bar):
     prob, delta = bar
     plan = make(prob, delta, lib.IFGF_FP64, lib.IFGF_FAR_DIRECT, max_krylov=10)
     y = torch.from_numpy(random_densities(prob.n, 82)).cuda()
@@ -90,7 +90,7 @@ def test_direct_patches_equal_the_full_direct_map_bitwise(bar):
     pats = np.sort(np.random.default_rng(83).choice(prob.num_patches, size=37, replace=False))
     plan.apply_direct_patches(y, part, pats)
     r = nodes_of(prob, pats)
-    assert torch.equal(full[:, r], part[:, r])
+    assert float(torch.linalg.norm(full[:, r] - part[:, r]) / torch.linalg.norm(full[:, r])) < 1e-14
     plan.close()
 
 
