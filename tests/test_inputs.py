@@ -146,3 +146,21 @@ def test_waveguide_bar_sizes():
     assert np.abs(w[straight, 1] ** 8 + w[straight, 2] ** 8 - 1.0).max() < 1e-12
     xe = (np.abs(x[~straight, 0]) - 9.85) / 0.15
     assert np.abs(xe ** 8 + w[~straight, 1] ** 8 + w[~straight, 2] ** 8 - 1.0).max() < 1e-12
+
+
+def test_rounded_bar_arguments_and_exponent():
+    """The bar's cross-section follows the chosen even exponent, and invalid shapes are
+    refused."""
+    import pytest
+    from inputs import waveguide_bar
+    from inputs.geometry import rounded_bar
+    with pytest.raises(ValueError):
+        rounded_bar((1.0, 0.15, 0.07), 0.15, 0.2, exponent=3)
+    with pytest.raises(ValueError):
+        rounded_bar((0.1, 0.15, 0.07), 0.15, 0.2)
+    for e in (2, 4):
+        prob = waveguide_bar(0.2, half_lengths=(1.0, 0.15, 0.07), exponent=e)
+        x, _, _ = prob.nodes()
+        straight = np.abs(x[:, 0]) <= 0.85
+        w = x[straight] / np.array([1.0, 0.15, 0.07])
+        assert np.abs(np.abs(w[:, 1]) ** e + np.abs(w[:, 2]) ** e - 1.0).max() < 1e-12
