@@ -301,24 +301,3 @@ def test_direct_fp64_forward_map_is_invariant_under_rigid_motion(small):
         outs.append(gpu_apply(plan, y))
         plan.close()
     assert rel(outs[1], outs[0]) < 1e-12
-
-
-@pytest.mark.parametrize("prec,tol", [(lib.IFGF_FP64, 1e-10), (lib.IFGF_FP32, 5e-5)])
-def test_ifgf_far_fields_match_the_oracle_ifgf(prec, tol):
-    """The IFGF far fields (S and dS/dn, both wavenumbers, 8 densities) against the oracle's
-    own IFGF (oracle/ifgf.py: the same algorithm and readings, written independently): equal
-    up to rounding in FP64 -- the approximation itself is compared, not only its distance to
-    the exact sum -- and to FP32 rounding in FP32."""
-    from oracle import ifgf as oifgf
-    prob = sphere_problem(0.5, 1, 6, 2.25)
-    qp = quad(prob)
-    g = cbie.geometry_of(prob)
-    rng = np.random.default_rng(23)
-    phi = rng.standard_normal((8, prob.n)) + 1j * rng.standard_normal((8, prob.n))
-    plan = plan_of(prob, qp, far_mode=lib.IFGF_FAR_IFGF, precision=prec, ns0=2, na0=3, leaf_size=0.11)
-    got = gpu_fields(plan, phi, lib.IFGF_PART_FAR)          # [28, N]
-    plan.close()
-    tree = oifgf.build_tree(g.x, 0.11, max(prob.k_ext, prob.k_int), 2, 3)
-    ref = oifgf.ifgf_far(tree, g.x, g.n, phi.T * g.omega[:, None], prob.k_ext, prob.k_int).T
-    assert rel(got[:16], ref[:16]) < tol
-    assert rel(got[16:], ref[16:]) < tol
