@@ -4,6 +4,7 @@
 // segments (Eq. rele_cone_d) and the per-target evaluation lists of step 3 of
 // the algorithm summary.  Integer and FP64 geometric work only.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <exception>
@@ -100,6 +101,41 @@ static void parallel_for(int64_t n, F&& f) {
   } catch (...) {   // no more threads: the remaining chunks run here
   }
   for (int i = started; i < nth; ++i) run(i);
+  run(0);
+  for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
+}
+
+// Number of workers parallel_dynamic uses for n items.
+static int dynamic_workers(int64_t n) {
+  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n));
+}
+
+// f(worker, begin, end) over [0, n) in chunks of `chunk` items handed out on demand, for loops
+// whose items differ widely in cost (boxes: a few large ones on the top levels, many small
+// ones below).  Workers are numbered 0 .. dynamic_workers(n) - 1 for per-worker scratch; the
+// result must not depend on which worker takes which chunk.
+template <typename F>
+static void parallel_dynamic(int64_t n, int64_t chunk, F&& f) {
+  const int nth = dynamic_workers(n);
+  std::atomic<int64_t> next{0};
+  std::vector<std::exception_ptr> err(nth);
+  auto run = [&](int w) {
+    try {
+      for (int64_t i0; (i0 = next.fetch_add(chunk)) < n;) f(w, i0, std::min(n, i0 + chunk));
+    } catch (...) {
+      err[w] = std::current_exception();
+      next.store(n);
+    }
+  };
+  std::vector<std::thread> th;
+  int started = 1;
+  try {
+    for (; started < nth; ++started) th.emplace_back(run, started);
+  } catch (...) {   // no more threads: worker 0 takes the remaining chunks
+  }
   run(0);
   for (auto& x : th) x.join();
   for (auto& e : err)
@@ -251,41 +287,41 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
   // per-target evaluation lists of step 3 (cousin points of every source box).  Relevant
   // cones are kept per box as sorted key lists (the cone count of a level, ns * na * 2na,
   // is far too large for dense per-box maps on deep trees).  Every step runs over host
-  // threads on disjoint outputs, in an order that makes the tables independent of the
-  // thread count.
+  // threads on disjoint outputs, so the tables do not depend on the thread count.
+  std::vector<double> xs(3 * (size_t)N);   // node coordinates in sorted order
+  parallel_for(N, [&](int64_t s0, int64_t s1) {
+    for (int64_t s = s0; s < s1; ++s)
+      for (int a = 0; a < 3; ++a) xs[3 * s + a] = x[3 * (size_t)t.perm[s] + a];
+  });
   for (int d = 3; d <= D; ++d) {
     HostLevel& L = t.lv[d];
     ConeGeom cg = L.cg();
     const int nb = (int)L.key.size();
-    // (1) cones containing cousin points; record (target, box, cone) in target order
+    // (1) the cone of every cousin point: target s in box A and the j-th cousin B of A give
+    // the cone of s relative to B's centre.  Records are numbered in target order, ptr[s] + j
+    // (the evaluation lists), but the cones are stored box by box, column j of box A holding
+    // the cones of all of A's points relative to B contiguously:
+    // rc[ptr[pt_begin[A]] + j * |A| + (s - pt_begin[A])].
     std::vector<int64_t> ptr(N + 1, 0);
     for (int s = 0; s < N; ++s) ptr[s + 1] = ptr[s] + (int64_t)L.cousin[t.box_of[d][s]].size();
-    std::vector<int> rb(ptr[N]);
     std::vector<cone_key> rc(ptr[N]);
     parallel_for(N, [&](int64_t s0, int64_t s1) {
       for (int64_t s = s0; s < s1; ++s) {
-        const double* xs = x + 3 * (size_t)t.perm[s];
-        const std::vector<int>& cs = L.cousin[t.box_of[d][s]];
+        const int A = t.box_of[d][s];
+        const int64_t b = L.pt_begin[A], n = L.pt_end[A] - b;
+        const double* p = &xs[3 * (size_t)s];
+        const std::vector<int>& cs = L.cousin[A];
+        cone_key* out = &rc[ptr[b] + (s - b)];
         for (size_t j = 0; j < cs.size(); ++j) {
           double c[3];
           box_center(t, d, L.ic[cs[j]], c);
-          rb[ptr[s] + j] = cs[j];
-          rc[ptr[s] + j] = cone_of(cg, xs[0] - c[0], xs[1] - c[1], xs[2] - c[2]);
+          out[(int64_t)j * n] = cone_of(cg, p[0] - c[0], p[1] - c[1], p[2] - c[2]);
         }
       }
-    });
-    // candidate keys per box: the cousin-point cones of (1), then (2) below.  The cousin
-    // relation is symmetric, so box B's cousin points are the points of the boxes in
-    // cousin[B]; their cones relative to B are in (1) at B's position in their own lists.
-    std::vector<int64_t> koff(nb + 1, 0);
-    parallel_for(nb, [&](int64_t b0, int64_t b1) {
-      for (int64_t B = b0; B < b1; ++B)
-        for (int A : L.cousin[B]) koff[B + 1] += L.pt_end[A] - L.pt_begin[A];
     });
     // (2) cones containing interpolation points of the parent's relevant cones: the child
     // cone of parent point q of compact parent cone ci in octant o (box independent)
     std::vector<cone_key> cc_key;
-    std::vector<int64_t> poff(nb + 1, 0);
     int ncomp_p = 0;
     if (d >= 4) {
       HostLevel& Pp = t.lv[d - 1];
@@ -308,57 +344,83 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           }
         }
       });
-      for (int b = 0; b < nb; ++b) {
-        const int p = L.parent[b];
-        poff[b + 1] = (int64_t)(Pp.box_slot_ptr[p + 1] - Pp.box_slot_ptr[p]) * kQ;
-      }
     }
-    // per box: cousin keys, then parent-point keys; sorted and made distinct per box
-    for (int b = 0; b < nb; ++b) koff[b + 1] += koff[b] + poff[b + 1];
-    std::vector<cone_key> keys(koff[nb]);
-    parallel_for(nb, [&](int64_t b0, int64_t b1) {
-      for (int64_t B = b0; B < b1; ++B) {
-        int64_t w = koff[B];
-        for (int A : L.cousin[B]) {
-          const std::vector<int>& ca = L.cousin[A];
-          const auto it = std::lower_bound(ca.begin(), ca.end(), (int)B);
-          if (it == ca.end() || *it != (int)B) throw std::logic_error("cousin relation not symmetric");
-          const int64_t j = it - ca.begin();
-          for (int s = L.pt_begin[A]; s < L.pt_end[A]; ++s) keys[w++] = rc[ptr[s] + j];
-        }
-        if (d >= 4) {
-          const HostLevel& Pp = t.lv[d - 1];
-          const int p = L.parent[B];
-          const int o = (L.ic[B][0] & 1) | ((L.ic[B][1] & 1) << 1) | ((L.ic[B][2] & 1) << 2);
-          for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps) {
-            const cone_key* k = &cc_key[((size_t)Pp.slot_upidx[ps] * 8 + o) * kQ];
-            for (int q = 0; q < kQ; ++q) keys[w++] = k[q];
+    // The relevant cones of box B: the distinct cones of (1) relative to B (the cousin
+    // relation is symmetric, so B's cousin points are the points of the boxes A in cousin[B],
+    // column B of each A) and of (2) for B's octant of each relevant parent cone, sorted.
+    // Where the level's cone count is small enough, duplicates are dropped through a
+    // per-worker bit per cone (cell-major index, the order of the keys); otherwise all keys
+    // are gathered, sorted and made distinct.
+    std::vector<std::vector<cone_key>> ukeys(nb);
+    {
+      const int64_t ndense = (int64_t)cg.ns * cg.na * 2 * cg.na;
+      const bool use_bits = ndense <= ((int64_t)1 << 24);
+      std::vector<std::vector<uint64_t>> bits(dynamic_workers(nb));
+      std::vector<std::vector<cone_key>> bufs(bits.size());
+      parallel_dynamic(nb, 1, [&](int w, int64_t b0, int64_t b1) {
+        std::vector<uint64_t>& seen = bits[w];
+        std::vector<cone_key>& buf = bufs[w];
+        if (use_bits && seen.empty()) seen.assign((size_t)((ndense + 63) / 64), 0);
+        for (int64_t B = b0; B < b1; ++B) {
+          buf.clear();
+          auto add = [&](const cone_key* k, int64_t n) {
+            if (!use_bits) {
+              buf.insert(buf.end(), k, k + n);
+              return;
+            }
+            for (int64_t i = 0; i < n; ++i) {
+              int g1, g2, g3;
+              cone_decode(k[i], &g1, &g2, &g3);
+              const int64_t c = ((int64_t)g1 * cg.na + g2) * (2 * cg.na) + g3;
+              const uint64_t m = 1ULL << (c & 63);
+              if (!(seen[c >> 6] & m)) {
+                seen[c >> 6] |= m;
+                buf.push_back(k[i]);
+              }
+            }
+          };
+          for (int A : L.cousin[B]) {
+            const std::vector<int>& ca = L.cousin[A];
+            const auto it = std::lower_bound(ca.begin(), ca.end(), (int)B);
+            if (it == ca.end() || *it != (int)B) throw std::logic_error("cousin relation not symmetric");
+            const int64_t j = it - ca.begin(), b = L.pt_begin[A], n = L.pt_end[A] - b;
+            add(&rc[ptr[b] + j * n], n);
           }
+          if (d >= 4) {
+            const HostLevel& Pp = t.lv[d - 1];
+            const int p = L.parent[B];
+            const int o = (L.ic[B][0] & 1) | ((L.ic[B][1] & 1) << 1) | ((L.ic[B][2] & 1) << 2);
+            for (int ps = Pp.box_slot_ptr[p]; ps < Pp.box_slot_ptr[p + 1]; ++ps)
+              add(&cc_key[((size_t)Pp.slot_upidx[ps] * 8 + o) * kQ], kQ);
+          }
+          std::sort(buf.begin(), buf.end());
+          if (use_bits) {
+            for (cone_key k : buf) {
+              int g1, g2, g3;
+              cone_decode(k, &g1, &g2, &g3);
+              const int64_t c = ((int64_t)g1 * cg.na + g2) * (2 * cg.na) + g3;
+              seen[c >> 6] &= ~(1ULL << (c & 63));
+            }
+          } else {
+            buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+          }
+          ukeys[B].assign(buf.begin(), buf.end());
         }
-      }
-    });
-    std::vector<int64_t> nkeep(nb + 1, 0);
-    parallel_for(nb, [&](int64_t b0, int64_t b1) {
-      for (int64_t b = b0; b < b1; ++b) {
-        auto first = keys.begin() + koff[b], last = keys.begin() + koff[b + 1];
-        std::sort(first, last);
-        nkeep[b + 1] = std::unique(first, last) - first;
-      }
-    });
+      });
+    }
     // slots: relevant (box, cone) pairs sorted by box then cone
     L.box_slot_ptr.assign(nb + 1, 0);
-    for (int b = 0; b < nb; ++b) L.box_slot_ptr[b + 1] = L.box_slot_ptr[b] + (int)nkeep[b + 1];
+    for (int b = 0; b < nb; ++b) L.box_slot_ptr[b + 1] = L.box_slot_ptr[b] + (int)ukeys[b].size();
     const int nslots = L.box_slot_ptr[nb];
     L.slot_box.resize(nslots);
     L.slot_cone.resize(nslots);
     parallel_for(nb, [&](int64_t b0, int64_t b1) {
-      for (int64_t b = b0; b < b1; ++b)
-        for (int i = 0; i < (int)nkeep[b + 1]; ++i) {
-          L.slot_box[L.box_slot_ptr[b] + i] = (int)b;
-          L.slot_cone[L.box_slot_ptr[b] + i] = keys[koff[b] + i];
-        }
+      for (int64_t b = b0; b < b1; ++b) {
+        std::copy(ukeys[b].begin(), ukeys[b].end(), L.slot_cone.begin() + L.box_slot_ptr[b]);
+        std::fill(L.slot_box.begin() + L.box_slot_ptr[b], L.slot_box.begin() + L.box_slot_ptr[b + 1], (int)b);
+      }
     });
-    std::vector<cone_key>().swap(keys);
+    std::vector<std::vector<cone_key>>().swap(ukeys);
     // compact list of this level's relevant cone keys (sorted, distinct), and the slot -> compact map
     L.upcone_list = L.slot_cone;
     std::sort(L.upcone_list.begin(), L.upcone_list.end());
@@ -443,14 +505,20 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           std::copy(ci_tasks[ci].begin(), ci_tasks[ci].end(), Pp.up_task.begin() + Pp.up_task_ptr[ci * kUpGroups]);
       });
     }
-    // per-target slots: the (box, cone) pairs recorded in (1), found in the box's sorted cones
+    // per-target slots: each record (s, j) of (1), found in the sorted cones of box cousin[A][j]
     L.tgt_ptr = ptr;
-    L.tgt_slot.resize(rb.size());
-    parallel_for((int64_t)rb.size(), [&](int64_t e0, int64_t e1) {
-      for (int64_t e = e0; e < e1; ++e) {
-        const int lo = L.box_slot_ptr[rb[e]], hi = L.box_slot_ptr[rb[e] + 1];
-        const auto first = L.slot_cone.begin() + lo, last = L.slot_cone.begin() + hi;
-        L.tgt_slot[e] = lo + (int)(std::lower_bound(first, last, rc[e]) - first);
+    L.tgt_slot.resize(ptr[N]);
+    parallel_for(N, [&](int64_t s0, int64_t s1) {
+      for (int64_t s = s0; s < s1; ++s) {
+        const int A = t.box_of[d][s];
+        const int64_t b = L.pt_begin[A], n = L.pt_end[A] - b;
+        const std::vector<int>& cs = L.cousin[A];
+        const cone_key* k = &rc[ptr[b] + (s - b)];
+        for (size_t j = 0; j < cs.size(); ++j) {
+          const int lo = L.box_slot_ptr[cs[j]], hi = L.box_slot_ptr[cs[j] + 1];
+          const auto first = L.slot_cone.begin() + lo, last = L.slot_cone.begin() + hi;
+          L.tgt_slot[ptr[s] + j] = lo + (int)(std::lower_bound(first, last, k[(int64_t)j * n]) - first);
+        }
       }
     });
   }
