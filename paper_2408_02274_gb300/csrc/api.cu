@@ -244,14 +244,14 @@ void build(ifgf_plan_t* p) {
     check(cudaEventRecord(ev[1]), "setup event");
     t0 = clk::now();
     std::vector<int64_t> row_ptr;
-    std::vector<int> col, pair;
+    host_array<int> col, pair;
     near_structure(t, P, nc, cptr, cpatch, sing, row_ptr, col, pair);   // overlaps the moments
     p->stats.setup_near_host_s += since(t0);
     p->near.nnz = (int64_t)col.size();
     p->stats.near_nnz = p->near.nnz;
     p->near.row_ptr = A.upload(row_ptr);
-    p->near.col = A.upload(col);
-    int* d_pair = SN.upload(pair);
+    p->near.col = A.upload(col.data(), col.size());
+    int* d_pair = SN.upload(pair.data(), pair.size());
     // the near values in the plan's precision only
     if (d.precision == IFGF_FP64)
       p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);

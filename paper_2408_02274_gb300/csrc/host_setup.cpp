@@ -686,7 +686,7 @@ int64_t near_nnz_bound(const HostTree& t, int P, int nc, const std::vector<int64
 
 void near_structure(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
                     const std::vector<int>& cpatch, const std::vector<uint8_t>& singular,
-                    std::vector<int64_t>& row_ptr, std::vector<int>& col, std::vector<int>& pair) {
+                    std::vector<int64_t>& row_ptr, host_array<int>& col, host_array<int>& pair) {
   const int npp = nc * nc;
   const int N = P * npp;
   const int D = t.D;
