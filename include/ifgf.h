@@ -147,8 +147,11 @@ typedef struct {
  * device the node geometry, closest points and singular moments (Sec. III-D)
  * and the near-field matrix with local corrections (Sec. III-H).  The plan
  * owns all device memory it uses; apply and solve allocate nothing.  Runs on
- * the current device, synchronously.  Errors: IFGF_EINVAL (descriptor),
- * IFGF_ENOMEM, IFGF_ECUDA, IFGF_EUNSUPPORTED.  On error *out is NULL.
+ * the current device, synchronously.  The host part runs on all cores, or on
+ * at most IFGF_HOST_THREADS threads when that environment variable holds a
+ * positive number; the tables built do not depend on the thread count.
+ * Errors: IFGF_EINVAL (descriptor), IFGF_ENOMEM, IFGF_ECUDA,
+ * IFGF_EUNSUPPORTED.  On error *out is NULL.
  */
 ifgf_status ifgf_plan_create(const ifgf_plan_desc* desc, ifgf_plan* out);
 

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -76,12 +77,22 @@ static void box_center(const HostTree& t, int d, const std::array<int, 3>& ic, d
   for (int a = 0; a < 3; ++a) c[a] = t.corner[a] + H * (ic[a] + 0.5);
 }
 
+// Host threads for the setup: IFGF_HOST_THREADS when set to a positive number (a cap for
+// shared hosts), else the hardware concurrency; at most 64.  The tables built do not depend on it.
+static int host_threads() {
+  int64_t n = std::max(1u, std::thread::hardware_concurrency());
+  if (const char* e = std::getenv("IFGF_HOST_THREADS")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v > 0) n = v;
+  }
+  return (int)std::min<int64_t>(n, 64);
+}
+
 // f(begin, end) over [0, n) split into contiguous static chunks, one per host thread; an
 // exception thrown by a chunk is rethrown here after all threads have joined.
 template <typename F>
 static void parallel_for(int64_t n, F&& f) {
-  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
-  const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n / 64 + 1));
+  const int nth = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n / 64 + 1));
   if (nth == 1) {
     f((int64_t)0, n);
     return;
@@ -109,8 +120,7 @@ static void parallel_for(int64_t n, F&& f) {
 
 // Number of workers parallel_dynamic uses for n items.
 static int dynamic_workers(int64_t n) {
-  const int64_t hw = std::max(1u, std::thread::hardware_concurrency());
-  return (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(hw, 64), n));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n));
 }
 
 // f(worker, begin, end) over [0, n) in chunks of `chunk` items handed out on demand, for loops
@@ -592,7 +602,7 @@ void near_candidates(const double* x, int P, int nc, double delta, std::vector<d
     for (int p = 0; p < P; ++p) cell_patch[fill[pc[p]]++] = p;   // patches ascending within a cell
   }
   // targets split over host threads; each target's candidates in increasing patch order
-  const int nth = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
+  const int nth = host_threads();
   std::vector<std::vector<int>> part(nth);
   std::vector<std::vector<int64_t>> cnt(nth);
   auto work = [&](int tid) {
@@ -659,7 +669,7 @@ int64_t near_nnz_bound(const HostTree& t, int P, int nc, const std::vector<int64
   const int N = P * npp;
   const int D = t.D;
   const HostLevel& L = t.lv[D];
-  const int nth = std::max(1, std::min(64, (int)std::thread::hardware_concurrency()));
+  const int nth = host_threads();
   std::vector<int64_t> part(nth, 0);
   auto work = [&](int tid) {
     const int l0 = (int)((int64_t)N * tid / nth), l1 = (int)((int64_t)N * (tid + 1) / nth);

@@ -286,3 +286,47 @@ def test_plan_estimate_uses_the_plan_tree():
         _, _, cones, _, _ = tree.level(d)
         assert e["cones"][d] == cones.size
     tree.close()
+
+
+def _all_tables(tree):
+    perm, leafc = tree.perm()
+    out = [perm, leafc]
+    for d in range(3, tree.levels + 1):
+        coords, ptr, cones, ns, na = tree.level(d)
+        out += [coords, ptr, cones, np.array([ns, na])]
+        out += list(tree.targets(d))
+        if d < tree.levels:
+            out += list(tree.upward(d))
+    return out
+
+
+@pytest.mark.parametrize("case", ["bar", "fine_cones"])
+def test_host_tables_do_not_depend_on_the_thread_count(case, monkeypatch):
+    """The host setup splits its work over IFGF_HOST_THREADS threads (default: all cores); the
+    octree, relevant-cone, target and upward tables are the same for 1, 3 and all threads.
+    'bar': a deep point-count tree (many boxes, small cone counts, bit-per-cone de-duplication);
+    'fine_cones': ns0 = na0 = 64, so that the top levels have more than 2^24 cones and the
+    relevant cones are de-duplicated by sorting."""
+    from inputs import waveguide_bar
+    if case == "bar":
+        prob = waveguide_bar(0.5, nc=4, half_lengths=(2.5, 0.15, 0.07))
+        kw = dict(leaf_size=0.25 * 2 * np.pi / prob.k_ext, k_max=prob.k_int, ns0=2, na0=3, max_leaf_pts=8)
+    else:
+        prob = sphere_problem(0.5, 1, 6, 2.25)
+        kw = dict(leaf_size=0.11, k_max=max(prob.k_ext, prob.k_int), ns0=64, na0=64)
+    x, _, _ = prob.nodes()
+    ref = None
+    for nth in ("", "1", "3"):
+        monkeypatch.setenv("IFGF_HOST_THREADS", nth)
+        tree = lib.Tree(x, **kw)
+        tabs = _all_tables(tree)
+        if case == "fine_cones":
+            _, _, _, ns, na = tree.level(3)
+            assert ns * na * 2 * na > 1 << 24
+        tree.close()
+        if ref is None:
+            ref = tabs
+        else:
+            assert len(tabs) == len(ref)
+            for a, b in zip(tabs, ref):
+                assert np.array_equal(a, b)

@@ -60,6 +60,9 @@ def test_exact_box_sums_reproduce_the_plain_far_sum(case):
     if case == "sphere":
         prob = sphere_problem(0.5, 1, 6, 2.25)
         tree_kw = dict(leaf_size=0.11, ns0=2, na0=3)
+    elif case == "fine_cones":
+        prob = sphere_problem(0.5, 1, 6, 2.25)
+        kw = dict(leaf_size=0.11, ns0=64, na0=64)
     else:
         prob = waveguide_bar(0.5, nc=4, half_lengths=(1.5, 0.15, 0.07))
         tree_kw = dict(leaf_size=0.25 * 2 * np.pi / prob.k_ext, ns0=2, na0=3, max_leaf_pts=8)
@@ -86,10 +89,12 @@ def test_interpolation_error_falls_with_cone_refinement():
     assert errs[2][0] < 2e-6 and errs[2][1] < 5e-5, errs
 
 
-@pytest.mark.parametrize("case", ["sphere", "sphere6", "bar"])
+@pytest.mark.parametrize("case", ["sphere", "sphere6", "bar", "fine_cones"])
 def test_oracle_tree_matches_the_library_host_tables(case):
     """Levels, cone counts, relevant cone segments per box and every (target, box, cone)
-    record of the oracle's tree equal the library's host tables (ifgf_tree_*)."""
+    record of the oracle's tree equal the library's host tables (ifgf_tree_*).  'fine_cones'
+    (ns0 = na0 = 64) gives levels with more than 2^24 cones, where the library de-duplicates a
+    box's cones by sorting instead of one bit per cone."""
     lib = pytest.importorskip("paper_2408_02274_gb300")
     if case == "sphere":
         prob = sphere_problem(0.5, 2, 6, 2.25)
@@ -97,6 +102,9 @@ def test_oracle_tree_matches_the_library_host_tables(case):
     elif case == "sphere6":     # the body of the GPU comparison of the IFGF fields
         prob = sphere_problem(0.5, 1, 6, 2.25)
         kw = dict(leaf_size=0.11, ns0=2, na0=3)
+    elif case == "fine_cones":
+        prob = sphere_problem(0.5, 1, 6, 2.25)
+        kw = dict(leaf_size=0.11, ns0=64, na0=64)
     else:
         prob = waveguide_bar(0.5, nc=4, half_lengths=(1.5, 0.15, 0.07))
         kw = dict(leaf_size=0.25 * 2 * np.pi / prob.k_ext, ns0=2, na0=3, max_leaf_pts=8)
