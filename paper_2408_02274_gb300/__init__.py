@@ -156,6 +156,45 @@ def _check(st: int, where: str):
         raise IfgfError(st, where)
 
 
+def _plan_n(plan) -> int:
+    """Node count N of a plan handle (host-side read of the plan's statistics)."""
+    st = ifgf_stats()
+    _check(load().ifgf_plan_stats(plan, ctypes.byref(st)), "ifgf_plan_stats")
+    return int(st.n)
+
+
+def _arg(a, dtype: str, numel: int, name: str, cuda: bool = True):
+    """Address of `a` once the checks the C ABI cannot make hold: a contiguous array of `dtype`
+    ("complex128", "float64", "float32", "int32") with `numel` elements; a tensor on the current
+    CUDA device when `cuda`, else a numpy array or a tensor in host or device memory.  Reads
+    metadata only (no device work), so it is safe inside CUDA graph capture."""
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch." + dtype:
+            raise TypeError(f"{name}: dtype {a.dtype}, expected torch.{dtype}")
+        if cuda:
+            import torch
+            if a.device.type != "cuda" or a.device.index != torch.cuda.current_device():
+                raise ValueError(f"{name}: a tensor on the current CUDA device is required, got {a.device}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: the tensor must be contiguous")
+        if a.numel() != numel:
+            raise ValueError(f"{name}: {a.numel()} elements, expected {numel}")
+        return ctypes.c_void_p(a.data_ptr())
+    if cuda:
+        raise TypeError(f"{name}: a torch CUDA tensor is required, got {type(a).__name__}")
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+        raise TypeError(f"{name}: a C-contiguous numpy {dtype} array or a torch tensor is required")
+    if a.size != numel:
+        raise ValueError(f"{name}: {a.size} elements, expected {numel}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _nrhs(a, name: str) -> int:
+    if len(a.shape) < 1:
+        raise ValueError(f"{name}: a leading batch dimension is required")
+    return int(a.shape[0])
+
+
 def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: float, k_int: float,
                      eps_ext: float, eps_int: float, mu_ext: float = 1.0, mu_int: float = 1.0, *,
                      delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
@@ -209,14 +248,16 @@ def ifgf_plan_destroy(plan):
 
 def ifgf_apply(plan, y, out, stream=None):
     """out = A y for torch complex128 CUDA tensors y, out of shape [4, N]."""
-    _check(load().ifgf_apply(plan, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+    n4 = 4 * _plan_n(plan)
+    _check(load().ifgf_apply(plan, _arg(y, "complex128", n4, "y"), _arg(out, "complex128", n4, "out"),
                              _stream(stream)), "ifgf_apply")
 
 
 def ifgf_apply_batch(plan, y, out, stream=None):
     """out[r] = A y[r] for torch complex128 CUDA tensors y, out of shape [nrhs, 4, N]."""
-    _check(load().ifgf_apply_batch(plan, int(y.shape[0]), ctypes.c_void_p(y.data_ptr()),
-                                   ctypes.c_void_p(out.data_ptr()), _stream(stream)), "ifgf_apply_batch")
+    nrhs, n4 = _nrhs(y, "y"), 4 * _plan_n(plan)
+    _check(load().ifgf_apply_batch(plan, nrhs, _arg(y, "complex128", nrhs * n4, "y"),
+                                   _arg(out, "complex128", nrhs * n4, "out"), _stream(stream)), "ifgf_apply_batch")
 
 
 def ifgf_apply_direct_patches(plan, y, out, patches, stream=None):
@@ -224,31 +265,29 @@ def ifgf_apply_direct_patches(plan, y, out, patches, stream=None):
     complex128 CUDA tensors [4, N]; patches: distinct patch indices).  Only the columns of
     out at those patches' nodes are defined."""
     q = np.ascontiguousarray(np.asarray(patches, dtype=np.int32))
-    _check(load().ifgf_apply_direct_patches(plan, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+    n4 = 4 * _plan_n(plan)
+    _check(load().ifgf_apply_direct_patches(plan, _arg(y, "complex128", n4, "y"), _arg(out, "complex128", n4, "out"),
                                             q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(q.size),
                                             _stream(stream)), "ifgf_apply_direct_patches")
 
 
 def ifgf_apply_fields(plan, phi, f28, which: int = IFGF_PART_ALL, stream=None):
     """Scalar S/D sums: phi [N, 8] complex128 CUDA -> f28 [N, 28] complex128 CUDA."""
-    _check(load().ifgf_apply_fields(plan, ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(f28.data_ptr()),
+    n = _plan_n(plan)
+    _check(load().ifgf_apply_fields(plan, _arg(phi, "complex128", 8 * n, "phi"), _arg(f28, "complex128", 28 * n, "f28"),
                                     int(which), _stream(stream)), "ifgf_apply_fields")
-
-
-def _addr(a):
-    if hasattr(a, "data_ptr"):
-        return ctypes.c_void_p(a.data_ptr())
-    return ctypes.c_void_p(a.ctypes.data)
 
 
 def bie_solve(plan, inc, tol: float, max_iter: int, y, stream=None, raise_on_noconv: bool = False):
     """GMRES solve; inc [6, N] and y [4, N] complex128, host (numpy) or CUDA (torch).
 
     Returns (iterations, relative residual estimate, status)."""
+    n = _plan_n(plan)
     it = ctypes.c_int32(0)
     rr = ctypes.c_double(0.0)
-    st = load().bie_solve(plan, _addr(inc), float(tol), int(max_iter), _addr(y), ctypes.byref(it),
-                          ctypes.byref(rr), _stream(stream))
+    st = load().bie_solve(plan, _arg(inc, "complex128", 6 * n, "inc", cuda=False), float(tol), int(max_iter),
+                          _arg(y, "complex128", 4 * n, "y", cuda=False), ctypes.byref(it), ctypes.byref(rr),
+                          _stream(stream))
     if st not in (IFGF_OK, IFGF_ENOCONV) or (raise_on_noconv and st == IFGF_ENOCONV):
         raise IfgfError(st, "bie_solve")
     return it.value, rr.value, st
@@ -257,10 +296,11 @@ def bie_solve(plan, inc, tol: float, max_iter: int, y, stream=None, raise_on_noc
 def bie_solve_batch(plan, inc, tol: float, max_iter: int, y, stream=None):
     """Batched GMRES solves; inc [nrhs, 6, N] and y [nrhs, 4, N] complex128, host (numpy) or
     CUDA (torch).  Returns (iterations [nrhs], relative residual estimates [nrhs], status)."""
-    nrhs = int(inc.shape[0])
+    nrhs, n = _nrhs(inc, "inc"), _plan_n(plan)
     it = (ctypes.c_int32 * nrhs)()
     rr = (ctypes.c_double * nrhs)()
-    st = load().bie_solve_batch(plan, nrhs, _addr(inc), float(tol), int(max_iter), _addr(y), it, rr,
+    st = load().bie_solve_batch(plan, nrhs, _arg(inc, "complex128", nrhs * 6 * n, "inc", cuda=False), float(tol),
+                                int(max_iter), _arg(y, "complex128", nrhs * 4 * n, "y", cuda=False), it, rr,
                                 _stream(stream))
     if st not in (IFGF_OK, IFGF_ENOCONV):
         raise IfgfError(st, "bie_solve_batch")
@@ -273,7 +313,13 @@ def bie_solve_many(plans, incs, ys, tol: float, max_iter: int, streams=None):
     distinct CUDA streams.  Returns (iterations per plan, residuals per plan, statuses, status)."""
     n = len(plans)
     vp = ctypes.c_void_p
-    nr = [int(a.shape[0]) for a in incs]
+    if len(incs) != n or len(ys) != n:
+        raise ValueError("bie_solve_many: one inc and one y per plan")
+    handles = [p.handle if hasattr(p, "handle") else p for p in plans]
+    nr = [_nrhs(a, f"incs[{i}]") for i, a in enumerate(incs)]
+    ns = [_plan_n(h) for h in handles]
+    inc_p = [_arg(a, "complex128", nr[i] * 6 * ns[i], f"incs[{i}]", cuda=False) for i, a in enumerate(incs)]
+    y_p = [_arg(a, "complex128", nr[i] * 4 * ns[i], f"ys[{i}]", cuda=False) for i, a in enumerate(ys)]
     its = [(ctypes.c_int32 * k)() for k in nr]
     rrs = [(ctypes.c_double * k)() for k in nr]
     st = (ctypes.c_int32 * n)()
@@ -282,9 +328,8 @@ def bie_solve_many(plans, incs, ys, tol: float, max_iter: int, streams=None):
     strm = None
     if streams is not None:
         strm = (vp * n)(*[vp(int(getattr(s, "cuda_stream", s))) for s in streams])
-    status = load().bie_solve_many(n, (vp * n)(*[p.handle if hasattr(p, "handle") else p for p in plans]),
-                                   (ctypes.c_int32 * n)(*nr), (vp * n)(*[_addr(a) for a in incs]), float(tol),
-                                   int(max_iter), (vp * n)(*[_addr(a) for a in ys]), it_ptrs, rr_ptrs, st, strm)
+    status = load().bie_solve_many(n, (vp * n)(*handles), (ctypes.c_int32 * n)(*nr), (vp * n)(*inc_p), float(tol),
+                                   int(max_iter), (vp * n)(*y_p), it_ptrs, rr_ptrs, st, strm)
     if status not in (IFGF_OK, IFGF_ENOCONV):
         raise IfgfError(status, "bie_solve_many")
     return [list(a) for a in its], [list(a) for a in rrs], list(st), status
@@ -325,21 +370,25 @@ class Preconditioner:
 
     def apply(self, v, z, stream=None):
         """z = M v for torch complex128 CUDA tensors [nrhs, 4, N]."""
-        _check(load().ifgf_precond_apply(self.plan.handle, int(v.shape[0]), ctypes.c_void_p(v.data_ptr()),
-                                         ctypes.c_void_p(z.data_ptr()), _stream(stream)), "ifgf_precond_apply")
+        nrhs, n4 = _nrhs(v, "v"), 4 * self.plan.N
+        _check(load().ifgf_precond_apply(self.plan.handle, nrhs, _arg(v, "complex128", nrhs * n4, "v"),
+                                         _arg(z, "complex128", nrhs * n4, "z"), _stream(stream)), "ifgf_precond_apply")
 
     def features(self, v, e, X, T, stream=None):
         """Per-patch training pairs from v = A e ([nrhs, 4, N] complex128 CUDA) into float32 CUDA
         tensors X, T [nrhs * P, in]."""
-        _check(load().ifgf_precond_features(self.plan.handle, int(v.shape[0]), ctypes.c_void_p(v.data_ptr()),
-                                            ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(X.data_ptr()),
-                                            ctypes.c_void_p(T.data_ptr()), _stream(stream)), "ifgf_precond_features")
+        nrhs, n4 = _nrhs(v, "v"), 4 * self.plan.N
+        nx = nrhs * self.plan.P * self.n_in
+        _check(load().ifgf_precond_features(self.plan.handle, nrhs, _arg(v, "complex128", nrhs * n4, "v"),
+                                            _arg(e, "complex128", nrhs * n4, "e"), _arg(X, "float32", nx, "X"),
+                                            _arg(T, "float32", nx, "T"), _stream(stream)), "ifgf_precond_features")
 
     def train(self, X, T, steps, batch=256, lr=1e-3, seed=1, stream=None):
         """Adam on float32 CUDA tensors X, T [n, in]; returns the minibatch losses."""
         loss = np.zeros(steps, np.float32)
-        _check(load().ifgf_precond_train(self.plan.handle, int(X.shape[0]), ctypes.c_void_p(X.data_ptr()),
-                                         ctypes.c_void_p(T.data_ptr()), int(steps), int(batch), float(lr),
+        nx = _nrhs(X, "X")
+        _check(load().ifgf_precond_train(self.plan.handle, nx, _arg(X, "float32", nx * self.n_in, "X"),
+                                         _arg(T, "float32", nx * self.n_in, "T"), int(steps), int(batch), float(lr),
                                          int(seed), loss.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                          _stream(stream)), "ifgf_precond_train")
         return loss
@@ -347,10 +396,11 @@ class Preconditioner:
 
 def bie_solve_precond(plan, inc, tol: float, max_iter: int, y, stream=None):
     """Flexible GMRES with the attached preconditioner; as bie_solve_batch."""
-    nrhs = int(inc.shape[0])
+    nrhs, n = _nrhs(inc, "inc"), _plan_n(plan)
     it = (ctypes.c_int32 * nrhs)()
     rr = (ctypes.c_double * nrhs)()
-    st = load().bie_solve_precond(plan, nrhs, _addr(inc), float(tol), int(max_iter), _addr(y), it, rr,
+    st = load().bie_solve_precond(plan, nrhs, _arg(inc, "complex128", nrhs * 6 * n, "inc", cuda=False), float(tol),
+                                  int(max_iter), _arg(y, "complex128", nrhs * 4 * n, "y", cuda=False), it, rr,
                                   _stream(stream))
     if st not in (IFGF_OK, IFGF_ENOCONV):
         raise IfgfError(st, "bie_solve_precond")
@@ -401,11 +451,13 @@ def ifgf_far_direct_noalloc(nodes, normals, weights, leaf_coords, phi, k_ext: fl
     nodes, normals [n, 3] float64; weights [n] float64; leaf_coords [n, 3]
     int32; phi [n, 8] and f28 [n, 28] complex128; n <= 100000.
     """
-    n = int(nodes.shape[0])
-    _check(load().ifgf_far_direct_noalloc(n, ctypes.c_void_p(nodes.data_ptr()), ctypes.c_void_p(normals.data_ptr()),
-                                          ctypes.c_void_p(weights.data_ptr()), ctypes.c_void_p(leaf_coords.data_ptr()),
-                                          ctypes.c_void_p(phi.data_ptr()), float(k_ext), float(k_int), int(precision),
-                                          ctypes.c_void_p(f28.data_ptr()), _stream(stream)),
+    n = _nrhs(nodes, "nodes")
+    _check(load().ifgf_far_direct_noalloc(n, _arg(nodes, "float64", 3 * n, "nodes"),
+                                          _arg(normals, "float64", 3 * n, "normals"),
+                                          _arg(weights, "float64", n, "weights"),
+                                          _arg(leaf_coords, "int32", 3 * n, "leaf_coords"),
+                                          _arg(phi, "complex128", 8 * n, "phi"), float(k_ext), float(k_int),
+                                          int(precision), _arg(f28, "complex128", 28 * n, "f28"), _stream(stream)),
            "ifgf_far_direct_noalloc")
 
 
@@ -546,8 +598,9 @@ class Plan:
 
     def rhs(self, inc, b, stream=None):
         """b = right-hand side of the solve for CUDA tensors inc [nrhs, 6, N], b [nrhs, 4, N]."""
-        _check(load().bie_rhs(self.handle, int(inc.shape[0]), ctypes.c_void_p(inc.data_ptr()),
-                              ctypes.c_void_p(b.data_ptr()), _stream(stream)), "bie_rhs")
+        nrhs = _nrhs(inc, "inc")
+        _check(load().bie_rhs(self.handle, nrhs, _arg(inc, "complex128", nrhs * 6 * self.N, "inc"),
+                              _arg(b, "complex128", nrhs * 4 * self.N, "b"), _stream(stream)), "bie_rhs")
 
     def fields(self, phi, f28, which=IFGF_PART_ALL, stream=None):
         ifgf_apply_fields(self.handle, phi, f28, which, stream)
