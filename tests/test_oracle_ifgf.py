@@ -60,9 +60,6 @@ def test_exact_box_sums_reproduce_the_plain_far_sum(case):
     if case == "sphere":
         prob = sphere_problem(0.5, 1, 6, 2.25)
         tree_kw = dict(leaf_size=0.11, ns0=2, na0=3)
-    elif case == "fine_cones":
-        prob = sphere_problem(0.5, 1, 6, 2.25)
-        kw = dict(leaf_size=0.11, ns0=64, na0=64)
     else:
         prob = waveguide_bar(0.5, nc=4, half_lengths=(1.5, 0.15, 0.07))
         tree_kw = dict(leaf_size=0.25 * 2 * np.pi / prob.k_ext, ns0=2, na0=3, max_leaf_pts=8)
