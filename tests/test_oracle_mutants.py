@@ -3,7 +3,8 @@
 Each mutant rewrites one expression of an oracle function's source (a flipped sign, a dropped
 term, a wrong wavenumber or index, a transposed operand), compiles it beside the original, and
 runs the pin that must catch it against the mutated oracle: the Mie comparison for the N-Mueller
-combination and the right-hand side, the distance to the plain far sum for the IFGF steps.  The
+combination and the right-hand side, the distance to the plain far sum for the IFGF steps, and the
+sphere eigenvalues of S and dS/dn for the C core (kernel rows, singular quadrature).  The
 unmutated oracle passes the same check in the same test, so a pin that cannot tell them apart
 fails here."""
 import inspect
@@ -107,3 +108,61 @@ def test_far_sum_pin_catches_planted_ifgf_mistakes(monkeypatch):
             m.setattr(ifgf, name, mutant(ifgf, name, old, new))
             e = errs()
         assert max(e) > 1e-2, (name, old, new, e)
+
+
+# ------------------------------------------------------------------ C core (kernel rows) vs sphere eigenvalues
+C_MUTANTS = [
+    ("K[2 + s] = nd * (I * kk[s] * r - 1.0) * g / (r * r);",
+     "K[2 + s] = nd * (I * kk[s] * r + 1.0) * g / (r * r);"),                       # dG/dn sign
+    ("if (n > 1) Dk[1] = delta;", "if (n > 1) Dk[1] = -delta;"),                  # first difference
+    ("double wt = J * ub[2 * i + 1] * vb[2 * j + 1] * w_beta[i] * w_beta[j];",
+     "double wt = J * ub[2 * i + 1] * w_beta[i] * w_beta[j];"),                     # Jacobian in v dropped
+    ("kernels4n(dneg, -ne, ke, ki, k4);", "kernels4n(dneg, ne, ke, ki, k4);"),    # own-patch normal sign
+    ("acc += A[m * nc + ip] * tmp2", "acc += A[ip * nc + m] * tmp2"),              # transposed map
+    ("*dw = 2.0 * M_PI * (da * b - a * db)", "*dw = 2.0 * M_PI * (da * b + a * db)"),   # cov derivative
+]
+
+
+def test_eigenvalue_pin_catches_planted_core_mistakes(tmp_path, monkeypatch):
+    """Sphere of radius 1, k_e = 2, k_i = 4, N_c = 10: every 37th kernel row against the
+    eigenvalues of S and p.v. dS/dn on Y_lm (l <= 4; the pin's bar is 1e-4).  Each mutant of the
+    C core is compiled into its own library and loaded in place of the oracle's."""
+    import os
+    import subprocess
+    from scipy.special import sph_harm_y, spherical_jn, spherical_yn
+
+    prob = sphere_problem(1.0, 2, 10, 4.0)
+    prob.omega = 2.0
+    g = cbie.geometry_of(prob)
+    qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=48, cov_d=4.0)
+    rows = np.arange(0, g.x.shape[0], 37)
+    r = np.linalg.norm(g.x, axis=1)
+    th, ph = np.arccos(np.clip(g.x[:, 2] / r, -1, 1)), np.arctan2(g.x[:, 1], g.x[:, 0])
+
+    def worst():
+        K, _ = cbie.kernel_rows(prob, g, rows, qp)
+        e = 0.0
+        for l, m in ((0, 0), (1, 1), (2, -1), (3, 2), (4, 0)):
+            Yc = sph_harm_y(l, abs(m), th, ph)
+            Y = np.real(Yc) if m >= 0 else np.imag(Yc)
+            for s, k in enumerate((prob.k_ext, prob.k_int)):
+                j, dj = spherical_jn(l, k), spherical_jn(l, k, derivative=True)
+                h, dh = j + 1j * spherical_yn(l, k), dj + 1j * spherical_yn(l, k, derivative=True)
+                lam = (1j * k * j * h, 0.5j * k * k * (dj * h + j * dh))
+                for q in range(2):
+                    err = np.abs(K[2 * q + s] @ Y - lam[q] * Y[rows]).max() / (abs(lam[q]) * np.abs(Y).max())
+                    e = max(e, float(err))
+        return e
+
+    assert worst() < 1e-4
+    src = open(os.path.join(os.path.dirname(cbie.__file__), "cbie_core.c")).read()
+    for i, (old, new) in enumerate(C_MUTANTS):
+        assert src.count(old) == 1, old
+        c, so = tmp_path / f"core_mutant{i}.c", tmp_path / f"libcore_mutant{i}.so"
+        c.write_text(src.replace(old, new))
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", str(c), "-o", str(so), "-lm"])
+        with monkeypatch.context() as m:
+            m.setattr(cbie, "_LIB", None)
+            m.setattr(cbie, "build_core", lambda force=False, so=str(so): so)
+            e = worst()
+        assert e > 1e-4, (old, new, e)
