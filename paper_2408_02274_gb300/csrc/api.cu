@@ -306,7 +306,7 @@ void build(ifgf_plan_t* p) {
     Dl.up_task = A.upload(L.up_task);
     Dl.up_task_ptr = A.upload(L.up_task_ptr);
     Dl.tgt_ptr = A.upload(L.tgt_ptr);
-    Dl.tgt_slot = A.upload(L.tgt_slot);
+    Dl.tgt_slot = A.upload(L.tgt_slot.data(), L.tgt_slot.size());
     Dl.ninter = (int64_t)L.tgt_slot.size();
     Dl.cstride = (size_t)Dl.nslots * kQ * 32;
     p->stats.boxes[dd] = Dl.nboxes;

@@ -49,6 +49,62 @@ cone_key cone_of(const ConeGeom& cg, double x, double y, double z) {
   return cone_encode(g1, g2, g3);
 }
 
+// The cells of cone_of without its two atan2: theta by comparing cos(theta) = z / r, and phi by
+// comparing cos(phi) = x / rho (on the side given by the sign of y), with the cosines of the cell
+// boundaries k pi / na.  Where a cosine lies within kMargin of a boundary's cosine (there the
+// rounding of either computation could decide the cell), on the axis (rho = 0), on the plane
+// y = 0 and for r = 0, cone_of itself decides, so the result is always cone_of's: away from the
+// margin the true angle is more than kMargin from the boundary (|d cos / d angle| <= 1), far
+// beyond the few-ulp errors of atan2, of the quotient by the cell width and of the cosines.
+// The radial cell is computed with cone_of's own operations.
+struct ConeClassifier {
+  static constexpr double kMargin = 4e-12;
+  ConeGeom cg;
+  double ds, inv_dth;
+  std::vector<double> cb;   // cos(k dth), k = 0 .. na (decreasing)
+  explicit ConeClassifier(const ConeGeom& g) : cg(g), ds(g.ds()), inv_dth(1.0 / g.dth()), cb(g.na + 1) {
+    for (int k = 0; k <= g.na; ++k) cb[k] = std::cos(k * g.dth());
+  }
+  // k with cb[k] >= c > cb[k + 1] (0 <= k < na), or -1 where c is within the margin of either.
+  // Few cells: bisection.  Many: the search starts from acos(c) ~ sqrt(1 - |c|) p(|c|), p a
+  // least-squares cubic on [0, 1] (error < 2e-4 rad, under one cell on every level), and the
+  // table steps make k exact.
+  int cell(double c) const {
+    if (!(c < cb[0] - kMargin) || !(c > cb[cg.na] + kMargin)) return -1;
+    int k;
+    if (cg.na <= 12) {          // a few bisection steps
+      int lo = 0, hi = cg.na;
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cb[mid] >= c) lo = mid; else hi = mid;
+      }
+      k = lo;
+    } else {
+      const double a = std::fabs(c);
+      double t = std::sqrt(1.0 - a) * (1.57065637 + a * (-0.21156586 + a * (0.07332775 - 0.01831046 * a)));
+      if (c < 0) t = kPi - t;
+      k = std::min(std::max((int)(t * inv_dth), 0), cg.na - 1);
+      while (k > 0 && cb[k] < c) --k;
+      while (k < cg.na - 1 && cb[k + 1] >= c) ++k;
+    }
+    if (!(std::fabs(c - cb[k]) >= kMargin) || !(std::fabs(c - cb[k + 1]) >= kMargin)) return -1;
+    return k;
+  }
+  cone_key operator()(double x, double y, double z) const {
+    double rho = std::sqrt(x * x + y * y);
+    double r = std::sqrt(rho * rho + z * z);
+    if (!(rho > 0) || y == 0.0) return cone_of(cg, x, y, z);
+    const int g2 = cell(z / r);
+    int g3 = cell(x / rho);
+    if (g2 < 0 || g3 < 0) return cone_of(cg, x, y, z);
+    if (y < 0) g3 = 2 * cg.na - 1 - g3;   // phi = 2 pi - psi with cos(psi) = x / rho
+    double s = cg.h / r;
+    int g1 = (int)std::floor(s / ds);
+    g1 = std::min(std::max(g1, 0), cg.ns - 1);
+    return cone_encode(g1, g2, g3);
+  }
+};
+
 // Interpolation point q of a cone segment relative to the box centre:
 // tensor product of Ps x Pa x Pa open Chebyshev nodes mapped to the cone domain.
 void interp_point(const ConeGeom& cg, cone_key cone, int q, double* X) {
@@ -306,6 +362,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
   for (int d = 3; d <= D; ++d) {
     HostLevel& L = t.lv[d];
     ConeGeom cg = L.cg();
+    const ConeClassifier cls(cg);
     const int nb = (int)L.key.size();
     // (1) the cone of every cousin point: target s in box A and the j-th cousin B of A give
     // the cone of s relative to B's centre.  Records are numbered in target order, ptr[s] + j
@@ -314,7 +371,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     // rc[ptr[pt_begin[A]] + j * |A| + (s - pt_begin[A])].
     std::vector<int64_t> ptr(N + 1, 0);
     for (int s = 0; s < N; ++s) ptr[s + 1] = ptr[s] + (int64_t)L.cousin[t.box_of[d][s]].size();
-    std::vector<cone_key> rc(ptr[N]);
+    host_array<cone_key> rc(ptr[N]);
     parallel_for(N, [&](int64_t s0, int64_t s1) {
       for (int64_t s = s0; s < s1; ++s) {
         const int A = t.box_of[d][s];
@@ -325,7 +382,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
         for (size_t j = 0; j < cs.size(); ++j) {
           double c[3];
           box_center(t, d, L.ic[cs[j]], c);
-          out[(int64_t)j * n] = cone_of(cg, p[0] - c[0], p[1] - c[1], p[2] - c[2]);
+          out[(int64_t)j * n] = cls(p[0] - c[0], p[1] - c[1], p[2] - c[2]);
         }
       }
     });
@@ -349,7 +406,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
               double cx = X[0] - off * ((o & 1) ? 1 : -1);
               double cy = X[1] - off * ((o & 2) ? 1 : -1);
               double cz = X[2] - off * ((o & 4) ? 1 : -1);
-              cc_key[((size_t)ci * 8 + o) * kQ + q] = cone_of(cg, cx, cy, cz);
+              cc_key[((size_t)ci * 8 + o) * kQ + q] = cls(cx, cy, cz);
             }
           }
         }

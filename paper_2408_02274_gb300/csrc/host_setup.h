@@ -1,36 +1,10 @@
 // Host setup entry points (see host_setup.cpp).
 #pragma once
-#include <memory>
-#include <utility>
 #include <vector>
 
 #include "plan.h"
 
 namespace ifgf {
-
-// Allocator that leaves elements default-initialised (no zero fill) on resize: the near-matrix
-// index arrays run to several GB and are written in parallel right after they are sized, so
-// their pages are first touched by the threads that fill them.
-template <typename T>
-struct uninit_alloc : std::allocator<T> {
-  template <typename U>
-  struct rebind {
-    using other = uninit_alloc<U>;
-  };
-  uninit_alloc() = default;
-  template <typename U>
-  uninit_alloc(const uninit_alloc<U>&) noexcept {}
-  template <typename U>
-  void construct(U* q) noexcept {
-    ::new ((void*)q) U;
-  }
-  template <typename U, typename... A>
-  void construct(U* q, A&&... a) {
-    ::new ((void*)q) U(std::forward<A>(a)...);
-  }
-};
-template <typename T>
-using host_array = std::vector<T, uninit_alloc<T>>;
 
 cone_key cone_of(const ConeGeom& cg, double x, double y, double z);
 void interp_point(const ConeGeom& cg, cone_key cone, int q, double* X);

@@ -4,8 +4,10 @@
 #include <stdint.h>
 
 #include <array>
+#include <memory>
 #include <string>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/ifgf.h"
@@ -14,6 +16,31 @@
 namespace ifgf {
 
 // ------------------------------------------------------------------ host octree
+// Allocator that leaves elements default-initialised (no zero fill) on resize: the host
+// setup's large index arrays (cone records, target slots, near-matrix columns; up to several
+// GB) are written in parallel right after they are sized, so their pages are first touched by
+// the threads that fill them.
+template <typename T>
+struct uninit_alloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = uninit_alloc<U>;
+  };
+  uninit_alloc() = default;
+  template <typename U>
+  uninit_alloc(const uninit_alloc<U>&) noexcept {}
+  template <typename U>
+  void construct(U* q) noexcept {
+    ::new ((void*)q) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* q, A&&... a) {
+    ::new ((void*)q) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using host_array = std::vector<T, uninit_alloc<T>>;
+
 struct HostLevel {
   int d = 0;
   double H = 0, h = 0;
@@ -40,7 +67,7 @@ struct HostLevel {
   std::vector<int32_t> up_task_ptr;           // [ncompact * kUpGroups + 1] CSR offsets into up_task
   // target evaluation lists at this level: per sorted target, its slots
   std::vector<int64_t> tgt_ptr;
-  std::vector<int32_t> tgt_slot;
+  host_array<int32_t> tgt_slot;
   ConeGeom cg() const { return ConeGeom{h, ns, na}; }
 };
 
