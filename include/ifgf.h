@@ -366,6 +366,12 @@ const char* ifgf_status_string(ifgf_status s);
  * max_leaf_pts: the point-count leaf rule of the plan descriptor (0 -> off).
  * A tree from ifgf_tree_create is released with ifgf_tree_destroy; the tree
  * of a plan (ifgf_plan_tree) is borrowed and lives as long as the plan.
+ * IFGF_EINVAL (here, and from ifgf_plan_create / ifgf_plan_estimate, which
+ * build the same tree) also for node coordinates that are not finite, fewer
+ * than two distinct points, min_levels above 21 (the octree's depth limit,
+ * 21 bits per Morton coordinate) and cone-segment counts that do not fit the
+ * cone key's 21-bit fields (n_s or 2 n_a above 2^21: k_max times the body
+ * size too large for ns0, na0).
  * Output arrays are caller-owned host arrays; pass NULL to query sizes.
  */
 typedef struct ifgf_tree_t* ifgf_tree;

@@ -211,6 +211,10 @@ static void parallel_dynamic(int64_t n, int64_t chunk, F&& f) {
 void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_levels,
                 double k_max, int ns0, int na0, int max_leaf_pts) {
   if (N <= 0) throw std::invalid_argument("no nodes");
+  // levels are capped at 21: the Morton keys hold 21 bits per axis
+  if (min_levels > 21) throw std::invalid_argument("min_levels above 21 (the octree has at most 21 levels)");
+  for (int64_t i = 0; i < 3 * (int64_t)N; ++i)
+    if (!std::isfinite(x[i])) throw std::invalid_argument("node coordinates must be finite");
   double lo[3] = {x[0], x[1], x[2]}, hi[3] = {x[0], x[1], x[2]};
   for (int i = 0; i < N; ++i)
     for (int a = 0; a < 3; ++a) {
@@ -261,6 +265,10 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     }
     t.lv[d].ns = (d >= 3) ? std::max(ns, 2 * ns0) : 0;
     t.lv[d].na = (d >= 3) ? na : 0;
+    // a cone key holds g1 < ns and g3 < 2 na in 21 bits each
+    if (d >= 3 && (t.lv[d].ns > (1 << kConeBits) || 2 * t.lv[d].na > (1 << kConeBits)))
+      throw std::invalid_argument("cone-segment counts exceed the 21-bit cone key fields "
+                                  "(k_max times the body size is too large for ns0, na0)");
   }
   // leaf keys and Morton order
   const int nside = 1 << (D - 1);

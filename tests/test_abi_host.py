@@ -330,3 +330,37 @@ def test_host_tables_do_not_depend_on_the_thread_count(case, monkeypatch):
             assert len(tabs) == len(ref)
             for a, b in zip(tabs, ref):
                 assert np.array_equal(a, b)
+
+
+def test_degenerate_and_unsupported_point_sets_are_rejected_on_the_host():
+    """Non-finite coordinates, fewer than two distinct points, more than 21 octree levels and
+    cone counts beyond the 21-bit cone-key fields are refused with IFGF_EINVAL before any table
+    is built; the plan estimate (host only) refuses non-finite nodes the same way."""
+    rng = np.random.default_rng(3)
+    good = rng.standard_normal((40, 3))
+    for bad in (np.nan, np.inf, -np.inf):
+        x = good.copy()
+        x[7, 1] = bad
+        with pytest.raises(lib.IfgfError) as e:
+            lib.Tree(x, leaf_size=0.3, k_max=5.0, ns0=2, na0=3)
+        assert e.value.status == lib.IFGF_EINVAL
+    for x in (np.zeros((1, 3)), np.zeros((5, 3))):
+        with pytest.raises(lib.IfgfError):
+            lib.Tree(x, leaf_size=0.3, k_max=5.0, ns0=2, na0=3)
+    with pytest.raises(lib.IfgfError):
+        lib.Tree(good, leaf_size=0.3, k_max=5.0, ns0=2, na0=3, min_levels=22)
+    t = lib.Tree(good, leaf_size=0.3, k_max=5.0, ns0=2, na0=3, min_levels=21)   # the largest depth
+    assert t.levels == 21
+    t.close()
+    # every level doubles the cones (k_max H > 1/2 down to the leaves): 64 * 2^15 angular cells
+    with pytest.raises(lib.IfgfError) as e:
+        lib.Tree(good, leaf_size=1e-5, k_max=1e7, ns0=64, na0=64)
+    assert e.value.status == lib.IFGF_EINVAL
+    prob = CONFIG_SPHERE_SMALL(8)
+    x, xu, xv = prob.nodes()
+    x = x.copy()
+    x[5, 0] = np.nan
+    with pytest.raises(lib.IfgfError) as e:
+        lib.ifgf_plan_estimate(x, xu, xv, prob.fine(), prob.num_patches, prob.nc, prob.k_ext, prob.k_int,
+                               prob.eps_ext, prob.eps_int, delta=0.1)
+    assert e.value.status == lib.IFGF_EINVAL
