@@ -69,6 +69,12 @@ struct ConeClassifier {
   // Few cells: bisection.  Many: the search starts from acos(c) ~ sqrt(1 - |c|) p(|c|), p a
   // least-squares cubic on [0, 1] (error < 2e-4 rad, under one cell on every level), and the
   // table steps make k exact.
+  int cell(double c, int& hint) const {
+    // the previous point's cell, when c lies inside it by more than the margin
+    if (hint >= 0 && c < cb[hint] - kMargin && c > cb[hint + 1] + kMargin) return hint;
+    hint = cell(c);
+    return hint;
+  }
   int cell(double c) const {
     if (!(c < cb[0] - kMargin) || !(c > cb[cg.na] + kMargin)) return -1;
     int k;
@@ -91,11 +97,16 @@ struct ConeClassifier {
     return k;
   }
   cone_key operator()(double x, double y, double z) const {
+    int h2 = -1, h3 = -1;
+    return (*this)(x, y, z, h2, h3);
+  }
+  // with the theta and phi cells of the previous point as hints (updated; -1: none)
+  cone_key operator()(double x, double y, double z, int& h2, int& h3) const {
     double rho = std::sqrt(x * x + y * y);
     double r = std::sqrt(rho * rho + z * z);
     if (!(rho > 0) || y == 0.0) return cone_of(cg, x, y, z);
-    const int g2 = cell(z / r);
-    int g3 = cell(x / rho);
+    const int g2 = cell(z / r, h2);
+    int g3 = cell(x / rho, h3);
     if (g2 < 0 || g3 < 0) return cone_of(cg, x, y, z);
     if (y < 0) g3 = 2 * cg.na - 1 - g3;   // phi = 2 pi - psi with cos(psi) = x / rho
     double s = cg.h / r;
@@ -119,6 +130,41 @@ void interp_point(const ConeGeom& cg, cone_key cone, int q, double* X) {
   X[1] = r * std::sin(th) * std::sin(ph);
   X[2] = r * std::cos(th);
 }
+
+// interp_point for every cone of one level from tables: the radius of each (radial cell, radial
+// node) and the sines and cosines of each (angular cell, angular node), formed with
+// interp_point's own expressions, so the points are interp_point's to the bit.
+struct ConePoints {
+  ConeGeom cg;
+  std::vector<double> r, st, ct, sp, cp;   // [ns][kPs], [na][kPa] (theta), [2na][kPa] (phi)
+  explicit ConePoints(const ConeGeom& g)
+      : cg(g), r((size_t)g.ns * kPs), st((size_t)g.na * kPa), ct(st.size()), sp((size_t)2 * g.na * kPa),
+        cp(sp.size()) {
+    for (int g1 = 0; g1 < g.ns; ++g1)
+      for (int i = 0; i < kPs; ++i) r[(size_t)g1 * kPs + i] = g.h / ((g1 + 0.5 * (1.0 + cheb_node(i, kPs))) * g.ds());
+    for (int g2 = 0; g2 < g.na; ++g2)
+      for (int i = 0; i < kPa; ++i) {
+        const double th = (g2 + 0.5 * (1.0 + cheb_node(i, kPa))) * g.dth();
+        st[(size_t)g2 * kPa + i] = std::sin(th);
+        ct[(size_t)g2 * kPa + i] = std::cos(th);
+      }
+    for (int g3 = 0; g3 < 2 * g.na; ++g3)
+      for (int i = 0; i < kPa; ++i) {
+        const double ph = (g3 + 0.5 * (1.0 + cheb_node(i, kPa))) * g.dth();
+        sp[(size_t)g3 * kPa + i] = std::sin(ph);
+        cp[(size_t)g3 * kPa + i] = std::cos(ph);
+      }
+  }
+  void operator()(cone_key cone, int q, double* X) const {
+    int g1, g2, g3;
+    cone_decode(cone, &g1, &g2, &g3);
+    const int is = q / (kPa * kPa), it = (q / kPa) % kPa, ip = q % kPa;
+    const double rr = r[(size_t)g1 * kPs + is], s_t = st[(size_t)g2 * kPa + it];
+    X[0] = rr * s_t * cp[(size_t)g3 * kPa + ip];
+    X[1] = rr * s_t * sp[(size_t)g3 * kPa + ip];
+    X[2] = rr * ct[(size_t)g2 * kPa + it];
+  }
+};
 
 // Group (0 .. kUpGroups-1) of interpolation point q = (is * 5 + it) * 5 + ip: the 25 angular
 // positions (it, ip) in snake order (ip reversed on odd it), cut into chunks of 6, 6, 6, 7.
@@ -380,17 +426,19 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     std::vector<int64_t> ptr(N + 1, 0);
     for (int s = 0; s < N; ++s) ptr[s + 1] = ptr[s] + (int64_t)L.cousin[t.box_of[d][s]].size();
     host_array<cone_key> rc(ptr[N]);
-    parallel_for(N, [&](int64_t s0, int64_t s1) {
-      for (int64_t s = s0; s < s1; ++s) {
-        const int A = t.box_of[d][s];
+    parallel_dynamic(nb, 1, [&](int, int64_t a0, int64_t a1) {
+      for (int64_t A = a0; A < a1; ++A) {
         const int64_t b = L.pt_begin[A], n = L.pt_end[A] - b;
-        const double* p = &xs[3 * (size_t)s];
         const std::vector<int>& cs = L.cousin[A];
-        cone_key* out = &rc[ptr[b] + (s - b)];
         for (size_t j = 0; j < cs.size(); ++j) {
           double c[3];
           box_center(t, d, L.ic[cs[j]], c);
-          out[(int64_t)j * n] = cls(p[0] - c[0], p[1] - c[1], p[2] - c[2]);
+          cone_key* out = &rc[ptr[b] + (int64_t)j * n];
+          int h2 = -1, h3 = -1;   // neighbouring points of A mostly share B's cells
+          for (int64_t i = 0; i < n; ++i) {
+            const double* p = &xs[3 * (size_t)(b + i)];
+            out[i] = cls(p[0] - c[0], p[1] - c[1], p[2] - c[2], h2, h3);
+          }
         }
       }
     });
@@ -400,7 +448,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     int ncomp_p = 0;
     if (d >= 4) {
       HostLevel& Pp = t.lv[d - 1];
-      ConeGeom pg = Pp.cg();
+      const ConePoints pts(Pp.cg());
       ncomp_p = (int)Pp.upcone_list.size();
       cc_key.assign((size_t)ncomp_p * 8 * kQ, 0);
       parallel_for(ncomp_p, [&](int64_t c0, int64_t c1) {
@@ -408,7 +456,7 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           cone_key pc = Pp.upcone_list[ci];
           for (int q = 0; q < kQ; ++q) {
             double X[3];
-            interp_point(pg, pc, q, X);
+            pts(pc, q, X);
             for (int o = 0; o < 8; ++o) {
               double off = 0.5 * L.H;
               double cx = X[0] - off * ((o & 1) ? 1 : -1);
@@ -540,24 +588,27 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
       Pp.up_order.assign((size_t)ncomp_p * 8 * kQ, 0);
       std::vector<std::vector<int32_t>> ci_tasks(ncomp_p);
       std::vector<int32_t> ci_count((size_t)ncomp_p * kUpGroups, 0);
+      int grp[kQ];
+      for (int q = 0; q < kQ; ++q) grp[q] = up_group(q);
       parallel_for(ncomp_p, [&](int64_t c0, int64_t c1) {
         std::vector<int32_t> runs[kUpGroups];
+        std::vector<int32_t> by_len;
         for (int64_t ci = c0; ci < c1; ++ci) {
           for (auto& r : runs) r.clear();
           for (int o = 0; o < 8; ++o) {
             const size_t g = (size_t)ci * 8 + o;
             const int32_t* cc = &Pp.up_cc[g * kQ];
             int32_t* ord = &Pp.up_order[g * kQ];
-            for (int q = 0; q < kQ; ++q) ord[q] = q;
-            std::stable_sort(ord, ord + kQ, [&](int a, int b) {
-              const int ga = up_group(a), gb = up_group(b);
-              return ga != gb ? ga < gb : cc[a] < cc[b];
-            });
+            // rank by (group, child cone, point): distinct keys, so the order is the stable one
+            int64_t key[kQ];
+            for (int q = 0; q < kQ; ++q) key[q] = ((int64_t)grp[q] << 48) | ((int64_t)(cc[q] + 1) << 8) | q;
+            std::sort(key, key + kQ);
+            for (int q = 0; q < kQ; ++q) ord[q] = (int32_t)(key[q] & 255);
             int r = 0;
             while (r < kQ) {
-              const int w = up_group(ord[r]);
+              const int w = grp[ord[r]];
               int len = 1;
-              while (len < kUpRunMax && r + len < kQ && up_group(ord[r + len]) == w && cc[ord[r + len]] == cc[ord[r]])
+              while (len < kUpRunMax && r + len < kQ && grp[ord[r + len]] == w && cc[ord[r + len]] == cc[ord[r]])
                 ++len;
               runs[w].push_back(r | (len << 8) | (o << 16));
               r += len;
@@ -565,10 +616,13 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
           }
           std::vector<int32_t>& out = ci_tasks[ci];
           for (int w = 0; w < kUpGroups; ++w) {
-            std::stable_sort(runs[w].begin(), runs[w].end(),
-                             [](int32_t a, int32_t b) { return ((a >> 8) & 255) > ((b >> 8) & 255); });
-            out.insert(out.end(), runs[w].begin(), runs[w].end());
-            ci_count[(size_t)ci * kUpGroups + w] = (int32_t)runs[w].size();
+            // longest first, runs of equal length in their order of creation
+            by_len.clear();
+            for (int len = kUpRunMax; len >= 1; --len)
+              for (int32_t rr : runs[w])
+                if (((rr >> 8) & 255) == len) by_len.push_back(rr);
+            out.insert(out.end(), by_len.begin(), by_len.end());
+            ci_count[(size_t)ci * kUpGroups + w] = (int32_t)by_len.size();
           }
         }
       });

@@ -1,9 +1,10 @@
 """The host setup classifies cousin points and parent interpolation points into cone segments by
 comparing cosines with a table of cell-boundary cosines (no atan2); it must give exactly the cells
-of the atan2 definition (cone_of) for every input.  This test compiles the host setup source into
-a small program (g++, CPU only) and compares the two on random points and on points placed on and
-around the cell boundaries, on the axis and on the plane y = 0, for the cone counts of every level
-of the benchmark trees."""
+of the atan2 definition (cone_of) for every input, with and without the previous point's cells as
+hints.  This test compiles the host setup source into a small program (g++, CPU only) and compares
+the two on random points, on coherent walks, and on points placed on and around the cell
+boundaries, on the axis and on the plane y = 0, for the cone counts of every level of the
+benchmark trees."""
 import os
 import shutil
 import subprocess
@@ -19,18 +20,27 @@ PROGRAM = r"""
 #include "host_setup.cpp"
 using namespace ifgf;
 int main() {
-  long bad = 0, n = 0, fallback_region = 0;
+  long bad = 0, n = 0;
   std::mt19937_64 rng(7);
   std::uniform_real_distribution<double> U(-1.0, 1.0);
   const int counts[][2] = {{4, 3}, {4, 6}, {8, 12}, {16, 24}, {32, 48}, {64, 96}, {128, 192}, {512, 768}, {2, 2}};
   for (auto& nc : counts) {
     ConeGeom cg{0.37, nc[0], nc[1]};
     ConeClassifier cls(cg);
+    int h2 = -1, h3 = -1;   // hints carried from point to point, as in the octree's sweeps
     auto check = [&](double x, double y, double z) {
       ++n;
-      if (cls(x, y, z) != cone_of(cg, x, y, z)) ++bad;
+      const cone_key ref = cone_of(cg, x, y, z);
+      if (cls(x, y, z) != ref) ++bad;
+      if (cls(x, y, z, h2, h3) != ref) ++bad;
     };
     for (int i = 0; i < 2000000; ++i) check(U(rng), U(rng), U(rng));
+    // coherent walks (consecutive points close together, crossing cell boundaries now and then)
+    double w[3] = {0.3, -0.2, 0.5};
+    for (int i = 0; i < 1000000; ++i) {
+      for (double& v : w) v = std::min(1.0, std::max(-1.0, v + 1e-3 * U(rng)));
+      check(w[0], w[1], w[2]);
+    }
     // directions on and next to every theta and phi boundary, both signs of y, several radii
     const double eps[] = {0.0, 1e-16, -1e-16, 1e-14, -1e-14, 1e-12, -1e-12, 5e-12, -5e-12, 1e-9, -1e-9};
     for (int k = 0; k <= 2 * cg.na; ++k)
