@@ -114,9 +114,19 @@ static double golden_uv(const patch_geom *g, const double *x, double ua, double 
   return f;
 }
 
-static double snap_edge(double t) {
-  if (t > 1.0 - 1e-9) return 1.0;
-  if (t < -1.0 + 1e-9) return -1.0;
+/* Edge snap after the search (reading R15): a parameter within tol of +-1 is put on the edge,
+ * where the polish below holds it.  tol is the larger of 1e-9 and twice the width the search's
+ * bracket shrinks to, w GOLD^iters for an initial bracket of width w: a shorter search leaves a
+ * minimum on an edge farther from it than 1e-9.  At 60 steps the bracket term is below 2e-12
+ * (w <= 2), so tol is 1e-9. */
+static double snap_tol(double w, int iters) {
+  const double t = 2.0 * w * pow(GOLD, iters);
+  return t > 1e-9 ? t : 1e-9;
+}
+
+static double snap_edge(double t, double tol) {
+  if (t > 1.0 - tol) return 1.0;
+  if (t < -1.0 + tol) return -1.0;
   return t;
 }
 
@@ -354,8 +364,8 @@ int ora_kernel_rows(int P, int nc, int ng, const double *nodes, const double *no
           double va = (jm == nc - 1) ? -1.0 : u_nodes[jm + 1];
           double vz = (jm == 0) ? 1.0 : u_nodes[jm - 1];
           double d2 = golden_uv(&g, x, ua, uz, va, vz, gs_iters, &uc, &vc);
-          uc = snap_edge(uc);
-          vc = snap_edge(vc);
+          uc = snap_edge(uc, snap_tol(uz - ua, gs_iters));
+          vc = snap_edge(vc, snap_tol(vz - va, gs_iters));
           newton_polish(&g, x, &uc, &vc, 4);
           (void)d2;
           double dist = sqrt(dist2_uv(&g, x, uc, vc));
@@ -458,8 +468,8 @@ double ora_closest_point(int nc, int ng, const double *patch_nodes, const double
   double vz = (jm == 0) ? 1.0 : u_nodes[jm - 1];
   double uc, vc;
   golden_uv(&g, x, ua, uz, va, vz, gs_iters, &uc, &vc);
-  uv[0] = snap_edge(uc);
-  uv[1] = snap_edge(vc);
+  uv[0] = snap_edge(uc, snap_tol(uz - ua, gs_iters));
+  uv[1] = snap_edge(vc, snap_tol(vz - va, gs_iters));
   newton_polish(&g, x, &uv[0], &uv[1], 4);
   return sqrt(dist2_uv(&g, x, uv[0], uv[1]));
 }

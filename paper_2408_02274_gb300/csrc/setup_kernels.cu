@@ -175,9 +175,19 @@ __device__ double golden_inner(const PatchCoef& pc, const double* x, double u, d
   return dist2_v(cu, pc.ng, x, *vbest);
 }
 
-__device__ inline double snap_edge(double t) {
-  if (t > 1.0 - 1e-9) return 1.0;
-  if (t < -1.0 + 1e-9) return -1.0;
+// Edge snap after the search (reading R15): a parameter within tol of +-1 goes on the edge,
+// where the Newton polish holds it.  tol is the larger of 1e-9 and twice the width the search's
+// bracket shrinks to (w kGold^iters for an initial width w), so that a shorter search still puts
+// a minimum that lies on an edge there; at 60 steps the bracket term is below 2e-12 (w <= 2) and
+// tol is 1e-9.
+__device__ inline double snap_tol(double w, int iters) {
+  const double t = 2.0 * w * pow(kGold, (double)iters);
+  return t > 1e-9 ? t : 1e-9;
+}
+
+__device__ inline double snap_edge(double t, double tol) {
+  if (t > 1.0 - tol) return 1.0;
+  if (t < -1.0 + tol) return -1.0;
   return t;
 }
 
@@ -304,8 +314,8 @@ __global__ void k_closest(int npairs, int nc, int ng, int iters, double delta, c
   }
   double uc = 0.5 * (a + b), vc;
   golden_inner(pc, xl, uc, va, vb, iters, &vc);
-  uc = snap_edge(uc);
-  vc = snap_edge(vc);
+  uc = snap_edge(uc, snap_tol(ub - ua, iters));
+  vc = snap_edge(vc, snap_tol(vb - va, iters));
   newton_polish(pc, xl, &uc, &vc, 4);
   uv[2 * e] = uc;
   uv[2 * e + 1] = vc;

@@ -107,6 +107,26 @@ def test_closest_point_against_dense_sampling():
         assert -1 <= uv[0] <= 1 and -1 <= uv[1] <= 1
 
 
+
+@pytest.mark.parametrize("iters", [10, 20])
+def test_short_golden_section_reproduces_the_60_step_rows(iters):
+    """Reading R15: the edge snap follows the search's final bracket, so a shorter golden-section
+    search (10 or 20 steps per direction) followed by the same Newton polish finds the 60-step
+    closest points: identical singular sets and kernel rows equal to 1e-12 (measured <= 3e-14),
+    on the 6-patch sphere and on a bar whose end patches have edge minima."""
+    from inputs import CONFIG_SPHERE_SMALL, waveguide_bar
+    for prob in (CONFIG_SPHERE_SMALL(8), waveguide_bar(0.2, half_lengths=(1.25, 0.15, 0.07))):
+        g = cbie.geometry_of(prob)
+        x, _, _ = prob.nodes()
+        xp = x.reshape(prob.num_patches, prob.nc ** 2, 3)
+        diam = [np.linalg.norm(xp[q][:, None] - xp[q][None], axis=-1).max() for q in range(prob.num_patches)]
+        delta = 0.6 * float(np.median(diam))
+        rows = np.arange(0, prob.n, max(1, prob.n // 150))
+        K60, s60 = cbie.kernel_rows(prob, g, rows, cbie.QuadParams(delta=delta, n_beta=48, gs_iters=60))
+        K, s = cbie.kernel_rows(prob, g, rows, cbie.QuadParams(delta=delta, n_beta=48, gs_iters=iters))
+        assert np.array_equal(s, s60)
+        assert np.abs(K - K60).max() <= 1e-12 * np.abs(K60).max()
+
 def _moved(prob, R, shift):
     """The same body rigidly moved: x -> R x + shift, tangents -> R (nodes and fine grid)."""
     import copy
