@@ -761,7 +761,7 @@ def run_waveguide(args):
     prec = lib.IFGF_FP64 if args.precision == "fp64" else lib.IFGF_FP32
     plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=prec,
                                  far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_krylov,
-                                 max_leaf_pts=args.leaf_pts, gmres_scaling=args.gmres_scaling)
+                                 max_leaf_pts=args.leaf_pts, gmres_scaling=args.gmres_scaling, gs_iters=args.gs_iters)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     st = plan.stats()
@@ -769,7 +769,8 @@ def run_waveguide(args):
            "workload": f"bar {args.bar_length:g} x 0.3 x 0.14 lambda0, eps 12.1 / 2.1, patch side {args.bar_h}",
            "n": N, "unknowns": 4 * N, "patches": prob.num_patches, "delta": delta,
            "patch_diameter_quantiles": [float(v) for v in np.quantile(diam, [0.0, 0.5, 1.0])],
-           "max_leaf_pts": args.leaf_pts, "gmres_scaling": args.gmres_scaling, "host_geometry_s": t_host,
+           "max_leaf_pts": args.leaf_pts, "gmres_scaling": args.gmres_scaling, "gs_iters": args.gs_iters,
+           "host_geometry_s": t_host,
            "setup_s": setup, "setup_parts_s": st["setup_parts_s"],
            "device_bytes": st["device_bytes"], "levels": st["levels"], "near_nnz": st["near_nnz"],
            "singular_pairs": st["singular_pairs"], "boxes": st["boxes"], "cones": st["cones"],
@@ -839,6 +840,7 @@ def main():
     ap.add_argument("--leaf-pts", type=int, default=64)
     ap.add_argument("--sample-rows", type=int, default=10000)
     ap.add_argument("--gmres-scaling", type=int, default=1, choices=[0, 1])
+    ap.add_argument("--gs-iters", type=int, default=60, help="golden-section steps of the closest-point search")
     ap.add_argument("--bar-length", type=float, default=20.0)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
