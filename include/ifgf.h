@@ -76,7 +76,9 @@ typedef struct {
   double delta;            /* singular-set distance threshold of Eq. patch_sing; must be > 0 */
   int32_t n_beta;          /* Fejer points per direction of the moment rule (Eq. int_moments_cov), 4..96 */
   double cov_d;            /* change-of-variables order d >= 2 (Eq. mk_cov_1) */
-  int32_t gs_iters;        /* golden-section iterations per direction (Eq. dist_min); 0 -> 60 */
+  int32_t gs_iters;        /* golden-section iterations per direction (Eq. dist_min); 0 -> 60.
+                              The edge snap follows the final bracket, so 10-20 steps find the
+                              same closest points after the Newton polish */
   int32_t precision;       /* IFGF_FP64 or IFGF_FP32: arithmetic of steps (a)-(d) per apply */
   int32_t far_mode;        /* IFGF_FAR_IFGF or IFGF_FAR_DIRECT (plain O(N^2) far sum) */
   int32_t max_krylov;      /* GMRES basis capacity allocated by plan_create (0 -> 300, <= 1000) */
