@@ -637,16 +637,23 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
     // per-target slots: each record (s, j) of (1), found in the sorted cones of box cousin[A][j]
     L.tgt_ptr = ptr;
     L.tgt_slot.resize(ptr[N]);
-    parallel_for(N, [&](int64_t s0, int64_t s1) {
-      for (int64_t s = s0; s < s1; ++s) {
-        const int A = t.box_of[d][s];
+    parallel_dynamic(nb, 1, [&](int, int64_t a0, int64_t a1) {
+      for (int64_t A = a0; A < a1; ++A) {
         const int64_t b = L.pt_begin[A], n = L.pt_end[A] - b;
         const std::vector<int>& cs = L.cousin[A];
-        const cone_key* k = &rc[ptr[b] + (s - b)];
         for (size_t j = 0; j < cs.size(); ++j) {
           const int lo = L.box_slot_ptr[cs[j]], hi = L.box_slot_ptr[cs[j] + 1];
           const auto first = L.slot_cone.begin() + lo, last = L.slot_cone.begin() + hi;
-          L.tgt_slot[ptr[s] + j] = lo + (int)(std::lower_bound(first, last, k[(int64_t)j * n]) - first);
+          const cone_key* k = &rc[ptr[b] + (int64_t)j * n];
+          cone_key prev = -1;
+          int slot = -1;
+          for (int64_t i = 0; i < n; ++i) {
+            if (k[i] != prev) {   // neighbouring points mostly share a cone: search only on a change
+              prev = k[i];
+              slot = lo + (int)(std::lower_bound(first, last, prev) - first);
+            }
+            L.tgt_slot[ptr[b + i] + j] = slot;
+          }
         }
       }
     });
