@@ -69,12 +69,6 @@ struct ConeClassifier {
   // Few cells: bisection.  Many: the search starts from acos(c) ~ sqrt(1 - |c|) p(|c|), p a
   // least-squares cubic on [0, 1] (error < 2e-4 rad, under one cell on every level), and the
   // table steps make k exact.
-  int cell(double c, int& hint) const {
-    // the previous point's cell, when c lies inside it by more than the margin
-    if (hint >= 0 && c < cb[hint] - kMargin && c > cb[hint + 1] + kMargin) return hint;
-    hint = cell(c);
-    return hint;
-  }
   int cell(double c) const {
     if (!(c < cb[0] - kMargin) || !(c > cb[cg.na] + kMargin)) return -1;
     int k;
@@ -95,6 +89,13 @@ struct ConeClassifier {
     }
     if (!(std::fabs(c - cb[k]) >= kMargin) || !(std::fabs(c - cb[k + 1]) >= kMargin)) return -1;
     return k;
+  }
+  // cell(c), trying first the previous point's cell `hint` (kept only when c lies inside it by
+  // more than the margin); hint is updated
+  int cell(double c, int& hint) const {
+    if (hint >= 0 && c < cb[hint] - kMargin && c > cb[hint + 1] + kMargin) return hint;
+    hint = cell(c);
+    return hint;
   }
   cone_key operator()(double x, double y, double z) const {
     int h2 = -1, h3 = -1;
