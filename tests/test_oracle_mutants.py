@@ -166,3 +166,45 @@ def test_eigenvalue_pin_catches_planted_core_mistakes(tmp_path, monkeypatch):
             m.setattr(cbie, "build_core", lambda force=False, so=str(so): so)
             e = worst()
         assert e > 1e-4, (old, new, e)
+
+
+# ------------------------------------------------------------------ octree and cone tables
+TREE_MUTANTS = [
+    ("if c not in mine)", "if True)"),                                            # cousins keep neighbours
+    ("for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]",
+     "for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if abs(dx) + abs(dy) + abs(dz) <= 1]"),
+    ("a = 2 if k_max * H > 0.5 else 1", "a = 1"),                                 # cones never refined
+    ("keys.append(lv.key(cone_of(lv, X)))", "pass"),                              # parent points dropped
+]
+
+
+@pytest.mark.filterwarnings("ignore::RuntimeWarning")   # a mutant that pairs a box with itself divides by 0
+def test_tree_pins_catch_planted_mistakes(monkeypatch):
+    """Mistakes in the octree step (neighbours, cousins, cone counts, relevant cones) fail the
+    exact-decomposition pin (exact box sums = plain far sum to 1e-13) or the accuracy pin
+    (IFGF within 1e-4 / 5e-4 of the plain far sum), on the 216-node sphere whose cone counts double
+    on the upper levels; an exception in the mutated oracle also counts as caught."""
+    prob = sphere_problem(0.5, 1, 6, 2.25)
+    g = cbie.geometry_of(prob)
+    rng = np.random.default_rng(4)
+    a = (rng.standard_normal((prob.n, 8)) + 1j * rng.standard_normal((prob.n, 8))) * g.omega[:, None]
+    kmax = max(prob.k_ext, prob.k_int)
+
+    def pins_hold():
+        tree = ifgf.build_tree(g.x, 0.11, kmax, 1, 2)
+        ref = ifgf.direct_far(g.x, g.n, a, prob.k_ext, prob.k_int, tree.leafc)
+        ex = ifgf.ifgf_far(tree, g.x, g.n, a, prob.k_ext, prob.k_int, exact=True)
+        if rel(ex, ref) >= 1e-13:
+            return False
+        ap = ifgf.ifgf_far(tree, g.x, g.n, a, prob.k_ext, prob.k_int)
+        return rel(ap[:, :16], ref[:, :16]) < 1e-4 and rel(ap[:, 16:], ref[:, 16:]) < 5e-4
+
+    assert pins_hold()
+    for old, new in TREE_MUTANTS:
+        with monkeypatch.context() as m:
+            m.setattr(ifgf, "build_tree", mutant(ifgf, "build_tree", old, new))
+            try:
+                held = pins_hold()
+            except Exception:
+                held = False
+        assert not held, (old, new)
