@@ -728,66 +728,59 @@ void near_candidates(const double* x, int P, int nc, double delta, std::vector<d
     std::vector<int> fill(cell_ptr.begin(), cell_ptr.end() - 1);
     for (int p = 0; p < P; ++p) cell_patch[fill[pc[p]]++] = p;   // patches ascending within a cell
   }
-  // targets split over host threads; each target's candidates in increasing patch order
-  const int nth = host_threads();
-  std::vector<std::vector<int>> part(nth);
-  std::vector<std::vector<int64_t>> cnt(nth);
-  auto work = [&](int tid) {
-    const int l0 = (int)((int64_t)N * tid / nth), l1 = (int)((int64_t)N * (tid + 1) / nth);
-    std::vector<int>& out = part[tid];
-    std::vector<int64_t>& counts = cnt[tid];
-    counts.assign(l1 - l0, 0);
-    std::vector<int> found;
-    for (int l = l0; l < l1; ++l) {
-      const double* xl = x + 3 * (size_t)l;
-      const int pl = l / npp;
-      found.clear();
-      found.push_back(pl);
-      int c[3];
-      cell_of(xl, c);
-      for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
-            if (cx < 0 || cy < 0 || cz < 0 || cx >= dim[0] || cy >= dim[1] || cz >= dim[2]) continue;
-            const size_t ci = ((size_t)cz * dim[1] + cy) * dim[0] + cx;
-            for (int e = cell_ptr[ci]; e < cell_ptr[ci + 1]; ++e) {
-              const int p = cell_patch[e];
-              if (p == pl) continue;
-              double dc = 0;
-              for (int k = 0; k < 3; ++k) dc += (xl[k] - cen[3 * p + k]) * (xl[k] - cen[3 * p + k]);
-              if (std::sqrt(dc) - rad[p] > delta + gap[p]) continue;
-              double dmin = INFINITY;
-              for (int m = 0; m < npp; ++m) {
-                const double* y = x + 3 * ((size_t)p * npp + m);
-                double dd = 0;
-                for (int k = 0; k < 3; ++k) dd += (xl[k] - y[k]) * (xl[k] - y[k]);
-                dmin = std::min(dmin, std::sqrt(dd));
-              }
-              if (dmin <= delta + gap[p]) found.push_back(p);
-            }
-          }
-      std::sort(found.begin(), found.end());
-      out.insert(out.end(), found.begin(), found.end());
-      counts[l - l0] = (int64_t)found.size();
-    }
-  };
-  std::vector<std::thread> th;
-  for (int i = 0; i < nth; ++i) th.emplace_back(work, i);
-  for (auto& w : th) w.join();
+  // targets in chunks handed to host threads on demand; each chunk keeps its targets' candidates
+  // (each target's in increasing patch order) and the chunks are joined in target order, so the
+  // lists do not depend on the thread count
+  const int64_t kChunk = 4096;
+  const int64_t nchunk = ((int64_t)N + kChunk - 1) / kChunk;
+  std::vector<std::vector<int>> part(nchunk);
   cptr.assign(N + 1, 0);
-  cpatch.clear();
-  size_t total = 0;
-  for (auto& v : part) total += v.size();
-  cpatch.reserve(total);
-  int l = 0;
-  for (int i = 0; i < nth; ++i) {
-    cpatch.insert(cpatch.end(), part[i].begin(), part[i].end());
-    for (int64_t c : cnt[i]) {
-      cptr[l + 1] = cptr[l] + c;
-      ++l;
+  parallel_dynamic(nchunk, 1, [&](int, int64_t c0, int64_t c1) {
+    std::vector<int> found;
+    for (int64_t ch = c0; ch < c1; ++ch) {
+      std::vector<int>& out = part[ch];
+      const int l0 = (int)(ch * kChunk), l1 = (int)std::min<int64_t>(N, (ch + 1) * kChunk);
+      for (int l = l0; l < l1; ++l) {
+        const double* xl = x + 3 * (size_t)l;
+        const int pl = l / npp;
+        found.clear();
+        found.push_back(pl);
+        int c[3];
+        cell_of(xl, c);
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int cx = c[0] + dx, cy = c[1] + dy, cz = c[2] + dz;
+              if (cx < 0 || cy < 0 || cz < 0 || cx >= dim[0] || cy >= dim[1] || cz >= dim[2]) continue;
+              const size_t ci = ((size_t)cz * dim[1] + cy) * dim[0] + cx;
+              for (int e = cell_ptr[ci]; e < cell_ptr[ci + 1]; ++e) {
+                const int p = cell_patch[e];
+                if (p == pl) continue;
+                double dc = 0;
+                for (int k = 0; k < 3; ++k) dc += (xl[k] - cen[3 * p + k]) * (xl[k] - cen[3 * p + k]);
+                if (std::sqrt(dc) - rad[p] > delta + gap[p]) continue;
+                double dmin = INFINITY;
+                for (int m = 0; m < npp; ++m) {
+                  const double* y = x + 3 * ((size_t)p * npp + m);
+                  double dd = 0;
+                  for (int k = 0; k < 3; ++k) dd += (xl[k] - y[k]) * (xl[k] - y[k]);
+                  dmin = std::min(dmin, std::sqrt(dd));
+                }
+                if (dmin <= delta + gap[p]) found.push_back(p);
+              }
+            }
+        std::sort(found.begin(), found.end());
+        out.insert(out.end(), found.begin(), found.end());
+        cptr[l + 1] = (int64_t)found.size();   // counts; prefix sums below
+      }
     }
-  }
+  });
+  for (int l = 0; l < N; ++l) cptr[l + 1] += cptr[l];
+  cpatch.resize(cptr[N]);
+  parallel_for(nchunk, [&](int64_t c0, int64_t c1) {
+    for (int64_t ch = c0; ch < c1; ++ch)
+      std::copy(part[ch].begin(), part[ch].end(), cpatch.begin() + cptr[ch * kChunk]);
+  });
 }
 
 int64_t near_nnz_bound(const HostTree& t, int P, int nc, const std::vector<int64_t>& cptr,
@@ -796,26 +789,28 @@ int64_t near_nnz_bound(const HostTree& t, int P, int nc, const std::vector<int64
   const int N = P * npp;
   const int D = t.D;
   const HostLevel& L = t.lv[D];
-  const int nth = host_threads();
-  std::vector<int64_t> part(nth, 0);
-  auto work = [&](int tid) {
-    const int l0 = (int)((int64_t)N * tid / nth), l1 = (int)((int64_t)N * (tid + 1) / nth);
-    std::vector<uint8_t> mark(P, 0);
-    int64_t n = 0;
-    for (int l = l0; l < l1; ++l) {
-      for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = 1;
-      n += (cptr[l + 1] - cptr[l]) * (int64_t)npp;
-      const int A = t.box_of[D][t.iperm[l]];
-      for (int B : L.nbr[A])
-        for (int s = L.pt_begin[B]; s < L.pt_end[B]; ++s) n += mark[t.perm[s] / npp] ? 0 : 1;
-      for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = 0;
+  // per target: every candidate patch's nodes, plus the neighbour-box points on other patches
+  const int64_t kChunk = 4096;
+  const int64_t nchunk = ((int64_t)N + kChunk - 1) / kChunk;
+  std::vector<int64_t> part(nchunk, 0);
+  std::vector<std::vector<uint8_t>> marks(dynamic_workers(nchunk));
+  parallel_dynamic(nchunk, 1, [&](int w, int64_t c0, int64_t c1) {
+    std::vector<uint8_t>& mark = marks[w];
+    if (mark.empty()) mark.assign(P, 0);
+    for (int64_t ch = c0; ch < c1; ++ch) {
+      int64_t n = 0;
+      const int l0 = (int)(ch * kChunk), l1 = (int)std::min<int64_t>(N, (ch + 1) * kChunk);
+      for (int l = l0; l < l1; ++l) {
+        for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = 1;
+        n += (cptr[l + 1] - cptr[l]) * (int64_t)npp;
+        const int A = t.box_of[D][t.iperm[l]];
+        for (int B : L.nbr[A])
+          for (int s = L.pt_begin[B]; s < L.pt_end[B]; ++s) n += mark[t.perm[s] / npp] ? 0 : 1;
+        for (int64_t e = cptr[l]; e < cptr[l + 1]; ++e) mark[cpatch[e]] = 0;
+      }
+      part[ch] = n;
     }
-    part[tid] = n;
-  };
-  std::vector<std::thread> th;
-  for (int i = 1; i < nth; ++i) th.emplace_back(work, i);
-  work(0);
-  for (auto& x : th) x.join();
+  });
   int64_t total = 0;
   for (int64_t v : part) total += v;
   return total;
