@@ -673,7 +673,12 @@ ifgf_status ifgf_apply_direct_patches(ifgf_plan p, const void* y, void* out, con
   if (!p || !y || !out || !patches || y == out) return IFGF_EINVAL;
   if (npatches < 1 || npatches > p->P) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
-  std::vector<uint8_t> seen((size_t)p->P, 0);
+  std::vector<uint8_t> seen;
+  try {
+    seen.assign((size_t)p->P, 0);
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  }
   for (int32_t i = 0; i < npatches; ++i) {
     const int32_t q = patches[i];
     if (q < 0 || q >= p->P || seen[q]) return IFGF_EINVAL;
@@ -786,14 +791,27 @@ ifgf_status bie_rhs(ifgf_plan p, int32_t nrhs, const void* inc, void* b, ifgf_st
   return IFGF_OK;
 }
 
+// No C++ exception leaves the C ABI: a failed host allocation is IFGF_ENOMEM.
 ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
                             int32_t* iters, double* relres, ifgf_stream stream) {
-  return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, false);
+  try {
+    return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, false);
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  } catch (...) {
+    return IFGF_ECUDA;
+  }
 }
 
 ifgf_status bie_solve_precond(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
                               int32_t* iters, double* relres, ifgf_stream stream) {
-  return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, true);
+  try {
+    return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, true);
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  } catch (...) {
+    return IFGF_ECUDA;
+  }
 }
 
 ifgf_status ifgf_precond_attach(ifgf_plan p, int32_t hidden, const float* W1, const float* b1, const float* W2,
@@ -944,26 +962,36 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IFGF_ECUDA;
-  std::vector<ifgf_status> st(nplans, IFGF_OK);
-  std::vector<std::thread> workers;
-  workers.reserve(nplans);
-  for (int i = 0; i < nplans; ++i) {
-    workers.emplace_back([&, i]() {
-      if (cudaSetDevice(dev) != cudaSuccess) {
-        st[i] = IFGF_ECUDA;
-        return;
-      }
-      cudaStream_t s = streams ? (cudaStream_t)streams[i] : nullptr;
-      const bool own = (s == nullptr);
-      if (own && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-        st[i] = IFGF_ECUDA;
-        return;
-      }
-      st[i] = bie_solve_batch(plans[i], nrhs[i], incs[i], tol, max_iter, ys[i], iters ? iters[i] : nullptr,
-                              relres ? relres[i] : nullptr, (ifgf_stream)s);
-      if (own) cudaStreamDestroy(s);
-    });
+  std::vector<ifgf_status> st;
+  try {
+    st.assign(nplans, IFGF_OK);
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
   }
+  auto work = [&](int i) {
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      st[i] = IFGF_ECUDA;
+      return;
+    }
+    cudaStream_t s = streams ? (cudaStream_t)streams[i] : nullptr;
+    const bool own = (s == nullptr);
+    if (own && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      st[i] = IFGF_ECUDA;
+      return;
+    }
+    st[i] = bie_solve_batch(plans[i], nrhs[i], incs[i], tol, max_iter, ys[i], iters ? iters[i] : nullptr,
+                            relres ? relres[i] : nullptr, (ifgf_stream)s);
+    if (own) cudaStreamDestroy(s);
+  };
+  // one host thread per plan; a solve whose thread cannot be started runs here afterwards
+  std::vector<std::thread> workers;
+  int started = 0;
+  try {
+    workers.reserve(nplans);
+    for (; started < nplans; ++started) workers.emplace_back(work, started);
+  } catch (...) {
+  }
+  for (int i = started; i < nplans; ++i) work(i);
   for (auto& w : workers) w.join();
   ifgf_status out = IFGF_OK;
   for (int i = 0; i < nplans; ++i) {
