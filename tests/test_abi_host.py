@@ -364,3 +364,21 @@ def test_degenerate_and_unsupported_point_sets_are_rejected_on_the_host():
         lib.ifgf_plan_estimate(x, xu, xv, prob.fine(), prob.num_patches, prob.nc, prob.k_ext, prob.k_int,
                                prob.eps_ext, prob.eps_int, delta=0.1)
     assert e.value.status == lib.IFGF_EINVAL
+
+
+def test_host_thread_cap_ignores_values_that_are_not_positive(monkeypatch):
+    """IFGF_HOST_THREADS values that are not a positive number (0, -3, text, empty) fall back to
+    all cores; the tables stay the same."""
+    prob = sphere_problem(0.5, 1, 6, 2.25)
+    x, _, _ = prob.nodes()
+    kw = dict(leaf_size=0.11, k_max=max(prob.k_ext, prob.k_int), ns0=2, na0=3)
+    monkeypatch.delenv("IFGF_HOST_THREADS", raising=False)
+    t = lib.Tree(x, **kw)
+    ref = _all_tables(t)
+    t.close()
+    for v in ("0", "-3", "many", ""):
+        monkeypatch.setenv("IFGF_HOST_THREADS", v)
+        t = lib.Tree(x, **kw)
+        got = _all_tables(t)
+        t.close()
+        assert all(np.array_equal(a, b) for a, b in zip(got, ref))
