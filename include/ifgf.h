@@ -194,10 +194,12 @@ ifgf_status ifgf_apply_batch(ifgf_plan plan, int32_t nrhs, const void* y, void* 
  * sources carries ~sqrt(N) FP32 roundings, 1e-4 at N ~ 3e5: too coarse a reference); the
  * densities, near matrix and fields are the plan's own, so against ifgf_apply on the same
  * plan only the far algorithm differs.  For an FP64 plan the entries equal those of
- * ifgf_apply with far_mode IFGF_FAR_DIRECT up to rounding (the same sums, grouped by patch).  Allocates a device copy of the patch
- * list per call and returns after `stream` has finished.  IFGF_EINVAL on a null pointer, y == out,
- * npatches out of range, a patch out of range or repeated; IFGF_ENOMEM if the patch list
- * cannot be allocated; IFGF_ECUDA poisons the plan.
+ * ifgf_apply with far_mode IFGF_FAR_DIRECT bit for bit (each target keeps the full map's
+ * coordinate origin, the first node of its aligned run of 128 nodes, and its summation
+ * order).  Allocates a device list of target blocks per call and returns after `stream` has
+ * finished.  IFGF_EINVAL on a null pointer, y == out, npatches out of range, a patch out of
+ * range or repeated; IFGF_ENOMEM if the block list cannot be allocated; IFGF_ECUDA poisons
+ * the plan.
  */
 ifgf_status ifgf_apply_direct_patches(ifgf_plan plan, const void* y, void* out, const int32_t* patches,
                                       int32_t npatches, ifgf_stream stream);
@@ -344,8 +346,14 @@ ifgf_status ifgf_get_timing(ifgf_plan plan, double* ms, int64_t* calls, int64_t*
  * The working arrays live in one fixed device array compiled into the
  * library (~55 MiB, held by every device that loads the library until the
  * process exits); n is limited to 100000 nodes: larger n returns
- * IFGF_EUNSUPPORTED and the message of ifgf_status_string(IFGF_ECUDA) says
- * so.  No cudaMalloc, cudaFree or allocating library routine is called.
+ * IFGF_EUNSUPPORTED, whose ifgf_status_string message names the limit.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * Targets are taken in runs of 128 consecutive nodes whose first node is
+ * the coordinate origin of the run; with IFGF_FP32 the node differences
+ * keep their digits only if consecutive nodes are close together (grouped
+ * by patch, or in ifgf_tree_perm order): nodes in random order lose up to
+ * FP32 epsilon times (body size / leaf size) in relative accuracy.
+ * IFGF_EINTERNAL (with a message) if a host lock fails.
  * The first call on a device looks up the array's device address (this call
  * should come before any stream capture).  Every call shares the array and
  * clears what must start at zero; calls that overlap on the GPU race.

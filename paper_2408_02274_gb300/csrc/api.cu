@@ -1,5 +1,6 @@
 // C ABI of the CBIE-IFGF library: plan creation (host octree + device setup
 // kernels), forward map, raw scalar fields, GMRES solve, stats.
+#include <algorithm>
 #include <chrono>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,16 @@ static thread_local char g_last_err[512] = "";
 
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_last_err, sizeof(g_last_err), "%s: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+// Explanation of the last non-CUDA failure of this thread, shown by ifgf_status_string for the
+// status it was recorded with.
+static thread_local char g_detail[512] = "";
+static thread_local int g_detail_status = IFGF_OK;
+
+void set_status_detail(int status, const char* msg) {
+  g_detail_status = status;
+  snprintf(g_detail, sizeof(g_detail), "%s", msg);
 }
 
 namespace {
@@ -475,8 +486,8 @@ const char* ifgf_status_string(ifgf_status s) {
     case IFGF_ECUDA: return g_last_err[0] ? g_last_err : "CUDA error";
     case IFGF_ENOCONV: return "GMRES did not reach the tolerance";
     case IFGF_ETIMEOUT: return "device wait timed out";
-    case IFGF_EUNSUPPORTED: return "unsupported option";
-    case IFGF_EINTERNAL: return "internal error";
+    case IFGF_EUNSUPPORTED: return (g_detail_status == s && g_detail[0]) ? g_detail : "unsupported option";
+    case IFGF_EINTERNAL: return (g_detail_status == s && g_detail[0]) ? g_detail : "internal error";
     default: return "unknown status";
   }
 }
@@ -684,19 +695,39 @@ ifgf_status ifgf_apply_direct_patches(ifgf_plan p, const void* y, void* out, con
     if (q < 0 || q >= p->P || seen[q]) return IFGF_EINVAL;
     seen[q] = 1;
   }
+  // target blocks: the listed patches' node ranges cut at multiples of 128, so that every
+  // listed row has the origin (the first node of its aligned run of 128) and the summation
+  // order of the FP64 full map; ranges of adjacent listed patches merge
+  std::vector<int32_t> blk;
+  try {
+    const int npp = p->nc * p->nc;
+    for (int32_t q = 0; q < p->P; ++q) {
+      if (!seen[q]) continue;
+      int32_t a = q * npp, b = (q + 1) * npp;
+      while (q + 1 < p->P && seen[q + 1]) b = (++q + 1) * npp;
+      for (int32_t o = a / 128 * 128; o < b; o += 128) {
+        blk.push_back(o);
+        blk.push_back(std::max(a, o));
+        blk.push_back(std::min(b, o + 128));
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  }
+  const int nblk = (int)(blk.size() / 3);
   cudaStream_t s = (cudaStream_t)stream;
-  int* d_rows = nullptr;   // the patch list on the device
-  if (cudaMalloc(&d_rows, sizeof(int) * (size_t)npatches) != cudaSuccess) {
+  int* d_blk = nullptr;   // the block list on the device
+  if (cudaMalloc(&d_blk, sizeof(int) * blk.size()) != cudaSuccess) {
     cudaGetLastError();
     return IFGF_ENOMEM;
   }
-  cudaError_t e = cudaMemcpyAsync(d_rows, patches, sizeof(int) * (size_t)npatches, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(d_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = launch_density_prep(p, (const double*)y, nullptr, s, 1);
   if (e == cudaSuccess) e = launch_near(p, s, 1);
-  if (e == cudaSuccess) e = launch_far_direct(p, s, 1, d_rows, npatches, true);
+  if (e == cudaSuccess) e = launch_far_direct_blocks(p, s, d_blk, nblk);
   if (e == cudaSuccess) e = launch_combine(p, (const double*)y, (double*)out, s, 1);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(d_rows);
+  cudaFree(d_blk);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "ifgf_apply_direct_patches", __FILE__, __LINE__);
     p->poisoned = true;

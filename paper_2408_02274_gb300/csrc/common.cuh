@@ -135,4 +135,6 @@ __host__ __device__ inline double cheb_node(int k, int n) { return cos((k + 0.5)
 
 namespace ifgf {
 void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+// records the message ifgf_status_string(status) returns for EUNSUPPORTED and EINTERNAL
+void set_status_detail(int status, const char* msg);
 }

@@ -41,11 +41,11 @@ cudaError_t setup_combine_kernels();
 // (d): f28 = near * phi   (overwrites f28)
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 // far field by the plain direct sum (accumulates into f28)
-// patches (device, npatches distinct patch indices) restricts the targets to the nodes of
-// those patches; fp64 computes the sum in FP64 also for an FP32 plan (densities and fields
-// stay in the plan's precision)
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1, const int* patches = nullptr,
-                              int npatches = 0, bool fp64 = false);
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
+// the same sum in FP64 (also for an FP32 plan; densities and fields stay in the plan's
+// precision) on listed target ranges: blocks (device, [nblocks][3]) = (origin, lo, hi) with
+// origin a multiple of 128 and origin <= lo < hi <= min(origin + 128, N)
+cudaError_t launch_far_direct_blocks(const ifgf_plan_t* p, cudaStream_t s, const int* blocks, int nblocks);
 cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
                                   double ke, double ki, int precision, void* f28, cudaStream_t s);
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)

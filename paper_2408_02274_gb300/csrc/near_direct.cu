@@ -108,20 +108,28 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
                                                     const double* __restrict__ nrm,
                                                     const int* __restrict__ leafc,
                                                     const T* __restrict__ a, A ke, A ki,
-                                                    T* __restrict__ f28, const int* __restrict__ patches,
+                                                    T* __restrict__ f28, const int* __restrict__ blocks,
                                                     int npp) {
   __shared__ SrcTile<A> tile[128];
   const size_t rb = blockIdx.y;   // right-hand side of a batched call
   a += rb * 16 * (size_t)N;
   f28 += rb * 56 * (size_t)N;
-  // targets: a chunk of up to 128 nodes of one patch (every patch, or the listed ones):
-  // a compact group whose first node is the block's origin, the same in both modes
-  const int cpp = (npp + 127) / 128, chunk = blockIdx.x % cpp;
-  const int patch = patches ? patches[blockIdx.x / cpp] : (int)(blockIdx.x / cpp);
-  const int l0 = patch * npp + chunk * 128;
-  const int nt_blk = min(min(128, npp - chunk * 128), N - l0);
-  const bool act = (int)threadIdx.x < nt_blk;
-  const int l = l0 + (act ? (int)threadIdx.x : 0);
+  // targets: thread t takes node l0 + t when lo <= l0 + t < hi; node l0 is the block's origin.
+  // Without a block list, a block is a chunk of up to 128 nodes of one patch (npp = N_c^2) or
+  // 128 consecutive nodes (npp = 128); a block list gives (l0, lo, hi) per block explicitly.
+  int l0, lo, hi;
+  if (blocks) {
+    l0 = blocks[3 * blockIdx.x];
+    lo = blocks[3 * blockIdx.x + 1];
+    hi = blocks[3 * blockIdx.x + 2];
+  } else {
+    const int cpp = (npp + 127) / 128, chunk = blockIdx.x % cpp;
+    l0 = lo = (int)(blockIdx.x / cpp) * npp + chunk * 128;
+    hi = min(l0 + min(128, npp - chunk * 128), N);
+  }
+  const int lt = l0 + (int)threadIdx.x;
+  const bool act = lt >= lo && lt < hi;
+  const int l = act ? lt : lo;
   // coordinates relative to the block origin, formed in FP64: the differences of
   // nearby points keep their digits whatever the body's size
   const double o0 = x[3 * (size_t)l0], o1 = x[3 * (size_t)l0 + 1], o2 = x[3 * (size_t)l0 + 2];
@@ -200,24 +208,32 @@ cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs, const int* patches, int npatches,
-                              bool fp64) {
+cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int npp = p->desc.nc * p->desc.nc;
-  const unsigned blocks = (unsigned)((patches ? npatches : p->P) * ((npp + 127) / 128));
-  if (p->desc.precision == IFGF_FP64 && !patches) {
+  if (p->desc.precision == IFGF_FP64) {
     // FP64 keeps the digits of nearby differences without patch-local origins: every block
     // takes 128 consecutive nodes (no idle lanes when N_c^2 is not a multiple of 128)
     k_far_direct<double><<<dim3((unsigned)((p->N + 127) / 128), nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n,
         p->leafc, (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, nullptr, 128);
-  } else if (p->desc.precision == IFGF_FP64)
-    k_far_direct<double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, patches, npp);
-  else if (fp64)
-    k_far_direct<float, double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const float*)p->a_orig, p->desc.k_ext, p->desc.k_int, (float*)p->f28, patches, npp);
-  else
+  } else {
+    // FP32: a block takes a chunk of one patch, a compact group around its origin
+    const unsigned blocks = (unsigned)(p->P * ((npp + 127) / 128));
     k_far_direct<float><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
-        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28, patches, npp);
+        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28, nullptr, npp);
+  }
+  return cudaGetLastError();
+}
+
+// The FP64 direct far sum on listed target ranges (the sampled reference): blocks [nblocks][3] =
+// (origin, lo, hi) with origin = 128 * j, the start of the FP64 full map's j-th block, so that
+// the listed rows see the same origin, tile order and summation order as in that map.
+cudaError_t launch_far_direct_blocks(const ifgf_plan_t* p, cudaStream_t s, const int* blocks, int nblocks) {
+  if (p->desc.precision == IFGF_FP64)
+    k_far_direct<double><<<dim3((unsigned)nblocks, 1), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, blocks, 128);
+  else
+    k_far_direct<float, double><<<dim3((unsigned)nblocks, 1), 128, 0, s>>>(p->N, p->geo.x, p->geo.n,
+        p->leafc, (const float*)p->a_orig, p->desc.k_ext, p->desc.k_int, (float*)p->f28, blocks, 128);
   return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 // The array is shared by every call in the process and keeps the last call's
 // contents; each call clears what must start at zero.  Calls that overlap on
 // the GPU (different streams, or host threads without ordering) race on it.
+#include <exception>
 #include <mutex>
 
 #include "kernels.h"
@@ -52,21 +53,23 @@ __global__ void k_fields_out(size_t n, const T* __restrict__ f, double* __restri
 
 using namespace ifgf;
 
-extern "C" ifgf_status ifgf_far_direct_noalloc(int32_t n, const double* nodes, const double* normals,
-                                               const double* weights, const int32_t* leaf_coords,
-                                               const void* phi, double k_ext, double k_int, int32_t precision,
-                                               void* f28, ifgf_stream stream) {
+static ifgf_status noalloc_impl(int32_t n, const double* nodes, const double* normals, const double* weights,
+                                const int32_t* leaf_coords, const void* phi, double k_ext, double k_int,
+                                int32_t precision, void* f28, ifgf_stream stream) {
   if (n < 1 || !nodes || !normals || !weights || !leaf_coords || !phi || !f28) return IFGF_EINVAL;
   if (!(k_ext > 0) || !(k_int > 0)) return IFGF_EINVAL;
   if (precision != IFGF_FP64 && precision != IFGF_FP32) return IFGF_EINVAL;
   if (n > kNoAllocMaxNodes) {
-    set_last_cuda_error(cudaErrorInvalidValue, "ifgf_far_direct_noalloc: n exceeds the fixed working array (100000 nodes)",
-                        __FILE__, __LINE__);
+    set_status_detail(IFGF_EUNSUPPORTED,
+                      "ifgf_far_direct_noalloc: n exceeds the fixed working array (at most 100000 nodes)");
     return IFGF_EUNSUPPORTED;
   }
   int dev = 0;
   IFGF_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return IFGF_EUNSUPPORTED;
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_status_detail(IFGF_EUNSUPPORTED, "ifgf_far_direct_noalloc: device ordinal beyond 63");
+    return IFGF_EUNSUPPORTED;
+  }
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
@@ -94,4 +97,21 @@ extern "C" ifgf_status ifgf_far_direct_noalloc(int32_t n, const double* nodes, c
     k_fields_out<float><<<blocks, 256, 0, s>>>(56 * (size_t)n, (const float*)acc, (double*)f28);
   IFGF_CUDA_TRY(cudaGetLastError());
   return IFGF_OK;
+}
+
+// No C++ exception leaves the C ABI: the lock can throw std::system_error, reported as
+// IFGF_EINTERNAL with its message.
+extern "C" ifgf_status ifgf_far_direct_noalloc(int32_t n, const double* nodes, const double* normals,
+                                               const double* weights, const int32_t* leaf_coords,
+                                               const void* phi, double k_ext, double k_int, int32_t precision,
+                                               void* f28, ifgf_stream stream) {
+  try {
+    return noalloc_impl(n, nodes, normals, weights, leaf_coords, phi, k_ext, k_int, precision, f28, stream);
+  } catch (const std::exception& e) {
+    set_status_detail(IFGF_EINTERNAL, e.what());
+    return IFGF_EINTERNAL;
+  } catch (...) {
+    set_status_detail(IFGF_EINTERNAL, "ifgf_far_direct_noalloc: unknown exception");
+    return IFGF_EINTERNAL;
+  }
 }
