@@ -149,3 +149,61 @@ def test_radial_floor_on_a_low_frequency_leaf():
         ap = ifgf.ifgf_far(tree, g.x, g.n, a, prob.k_ext, prob.k_int)
         errs[floor] = (rel(ap[:, :16], ref[:, :16]), rel(ap[:, 16:], ref[:, 16:]))
     assert errs[True][0] < 0.4 * errs[False][0] and errs[True][1] < 0.4 * errs[False][1], errs
+
+
+DIRECT_FAR_MUTANTS = [
+    ("dG = nd * (1j * kap - 1.0 / dist) * G", "dG = nd * (1j * kap + 1.0 / dist) * G"),   # sign of 1/r
+    ("G = np.exp(1j * kap * dist) / (4 * np.pi * dist)",
+     "G = np.exp(1j * kap * dist) / (2 * np.pi * dist)"),                                # 1/(4 pi)
+    ("nd = (R @ nrm[l]) / dist", "nd = -(R @ nrm[l]) / dist"),                           # x - y reversed
+    ("G = np.exp(1j * kap * dist)", "G = np.exp(-1j * kap * dist)"),                     # outgoing wave
+]
+
+
+def test_direct_far_equals_the_cores_regular_patch_entries():
+    """The plain far sum (direct_far, the reference of every IFGF pin) against the C core's
+    kernel rows, which the sphere eigen-relations pin independently: for a target l and a
+    source m on a patch regular for l, the core's entries are the Fejer terms G_s(x_l, x_m)
+    omega_m and dG_s/dn(x_l) omega_m (Eq. non_sing).  Sources on patches that may be singular
+    for a tested row (node distance <= delta + the patch's node gap, the core's own safe
+    prefilter) get zero density, so both sides sum the same pairs: the far pairs of the leaf
+    rule on regular patches.  Planted mistakes in direct_far (sign of the 1/r term of dG/dn,
+    the 1/(4 pi), the direction of x - y, an incoming wave) fail the same comparison."""
+    import inspect
+    import textwrap
+
+    prob = sphere_problem(1.0, 3, 6, 2.25)          # 54 patches x 36 nodes
+    g = cbie.geometry_of(prob)
+    qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=24, cov_d=4.0)
+    P, npp = prob.num_patches, prob.nc ** 2
+    rows = np.arange(7 * npp, 8 * npp)
+    gap = cbie.node_gap(g.x, P, prob.nc)
+    xp = g.x.reshape(P, npp, 3)
+    maybe_sing = np.zeros(P, dtype=bool)
+    for l in rows:
+        dmin = np.linalg.norm(xp - g.x[l], axis=-1).min(axis=1)
+        maybe_sing |= dmin <= qp.delta + gap
+    assert 0 < maybe_sing.sum() < 0.5 * P
+    tree = ifgf.build_tree(g.x, 0.2, max(prob.k_ext, prob.k_int), 2, 3)
+    rng = np.random.default_rng(21)
+    phi = rng.standard_normal((prob.n, 8)) + 1j * rng.standard_normal((prob.n, 8))
+    phi[np.repeat(maybe_sing, npp)] = 0.0
+    K, _ = cbie.kernel_rows(prob, g, rows, qp)
+    far = np.array([np.any(np.abs(tree.leafc - tree.leafc[l]) > 1, axis=1) for l in rows])   # [rows, N]
+    assert far.sum() > 0.5 * rows.size * prob.n * (1 - maybe_sing.mean())
+    ref = np.empty((rows.size, 28), dtype=complex)
+    for s in range(2):
+        ref[:, 8 * s:8 * s + 8] = (K[s] * far) @ phi
+        ref[:, 16 + 6 * s:22 + 6 * s] = (K[2 + s] * far) @ phi[:, :6]
+
+    def worst(fn):
+        got = fn(g.x, g.n, phi * g.omega[:, None], prob.k_ext, prob.k_int, tree.leafc)[rows]
+        return max(rel(got[:, :16], ref[:, :16]), rel(got[:, 16:], ref[:, 16:]))
+
+    assert worst(ifgf.direct_far) < 1e-13
+    src = textwrap.dedent(inspect.getsource(ifgf.direct_far))
+    for old, new in DIRECT_FAR_MUTANTS:
+        assert src.count(old) == 1, old
+        ns = dict(vars(ifgf))
+        exec(compile(src.replace(old, new), "<mutant of direct_far>", "exec"), ns)
+        assert worst(ns["direct_far"]) > 1e-3, (old, new)

@@ -123,49 +123,93 @@ C_MUTANTS = [
 ]
 
 
-def test_eigenvalue_pin_catches_planted_core_mistakes(tmp_path, monkeypatch):
-    """Sphere of radius 1, k_e = 2, k_i = 4, N_c = 10: every 37th kernel row against the
-    eigenvalues of S and p.v. dS/dn on Y_lm (l <= 4; the pin's bar is 1e-4).  Each mutant of the
-    C core is compiled into its own library and loaded in place of the oracle's."""
-    import os
-    import subprocess
-    from scipy.special import sph_harm_y, spherical_jn, spherical_yn
-
+def eigen_case():
+    """Sphere of radius 1, k_e = 2, k_i = 4, N_c = 10; every 37th node is a tested row."""
     prob = sphere_problem(1.0, 2, 10, 4.0)
     prob.omega = 2.0
     g = cbie.geometry_of(prob)
     qp = cbie.QuadParams(delta=cbie.default_delta(prob), n_beta=48, cov_d=4.0)
     rows = np.arange(0, g.x.shape[0], 37)
+    return prob, g, qp, rows
+
+
+def eigen_errors(prob, g, rows, K):
+    """Largest relative error of the kernel rows K [4, rows, N] against the eigenvalues of S and
+    p.v. dS/dn on the real Y_lm (l <= 4), separately for S and dS/dn."""
+    from scipy.special import sph_harm_y, spherical_jn, spherical_yn
+
     r = np.linalg.norm(g.x, axis=1)
     th, ph = np.arccos(np.clip(g.x[:, 2] / r, -1, 1)), np.arctan2(g.x[:, 1], g.x[:, 0])
+    e = [0.0, 0.0]
+    for l, m in ((0, 0), (1, 1), (2, -1), (3, 2), (4, 0)):
+        Yc = sph_harm_y(l, abs(m), th, ph)
+        Y = np.real(Yc) if m >= 0 else np.imag(Yc)
+        for s, k in enumerate((prob.k_ext, prob.k_int)):
+            j, dj = spherical_jn(l, k), spherical_jn(l, k, derivative=True)
+            h, dh = j + 1j * spherical_yn(l, k), dj + 1j * spherical_yn(l, k, derivative=True)
+            lam = (1j * k * j * h, 0.5j * k * k * (dj * h + j * dh))
+            for q in range(2):
+                err = np.abs(K[2 * q + s] @ Y - lam[q] * Y[rows]).max() / (abs(lam[q]) * np.abs(Y).max())
+                e[q] = max(e[q], float(err))
+    return e
+
+
+def core_variant(tmp_path, name, old, new):
+    """Path of a library compiled from the oracle's C core with `old` replaced by `new`."""
+    import os
+    import subprocess
+
+    src = open(os.path.join(os.path.dirname(cbie.__file__), "cbie_core.c")).read()
+    assert src.count(old) == 1, old
+    c, so = tmp_path / f"core_{name}.c", tmp_path / f"libcore_{name}.so"
+    c.write_text(src.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", str(c), "-o", str(so), "-lm"])
+    return str(so)
+
+
+def test_eigenvalue_pin_catches_planted_core_mistakes(tmp_path, monkeypatch):
+    """Every 37th kernel row against the eigenvalues of S and p.v. dS/dn on Y_lm (l <= 4; the
+    pin's bar is 1e-4).  Each mutant of the C core is compiled into its own library and loaded
+    in place of the oracle's."""
+    prob, g, qp, rows = eigen_case()
 
     def worst():
         K, _ = cbie.kernel_rows(prob, g, rows, qp)
-        e = 0.0
-        for l, m in ((0, 0), (1, 1), (2, -1), (3, 2), (4, 0)):
-            Yc = sph_harm_y(l, abs(m), th, ph)
-            Y = np.real(Yc) if m >= 0 else np.imag(Yc)
-            for s, k in enumerate((prob.k_ext, prob.k_int)):
-                j, dj = spherical_jn(l, k), spherical_jn(l, k, derivative=True)
-                h, dh = j + 1j * spherical_yn(l, k), dj + 1j * spherical_yn(l, k, derivative=True)
-                lam = (1j * k * j * h, 0.5j * k * k * (dj * h + j * dh))
-                for q in range(2):
-                    err = np.abs(K[2 * q + s] @ Y - lam[q] * Y[rows]).max() / (abs(lam[q]) * np.abs(Y).max())
-                    e = max(e, float(err))
-        return e
+        return max(eigen_errors(prob, g, rows, K))
 
     assert worst() < 1e-4
-    src = open(os.path.join(os.path.dirname(cbie.__file__), "cbie_core.c")).read()
     for i, (old, new) in enumerate(C_MUTANTS):
-        assert src.count(old) == 1, old
-        c, so = tmp_path / f"core_mutant{i}.c", tmp_path / f"libcore_mutant{i}.so"
-        c.write_text(src.replace(old, new))
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", str(c), "-o", str(so), "-lm"])
+        so = core_variant(tmp_path, f"mutant{i}", old, new)
         with monkeypatch.context() as m:
             m.setattr(cbie, "_LIB", None)
-            m.setattr(cbie, "build_core", lambda force=False, so=str(so): so)
+            m.setattr(cbie, "build_core", lambda force=False, so=so: so)
             e = worst()
         assert e > 1e-4, (old, new, e)
+
+
+def test_first_order_normal_term_is_below_the_quadrature_error(tmp_path, monkeypatch):
+    """Reading R21: on the target's own patch the core forms n.(x - y) from the second-order
+    remainder of the patch interpolant and leaves out its first-order part du n.eta_u +
+    dv n.eta_v, which vanishes on the exact surface.  A core that keeps it (the plain
+    n.(x - y) of the interpolant's displacement) changes the dS/dn rows by ~3e-11 relative
+    (measured), six orders of magnitude below the eigen-relation pin's own quadrature error
+    (~7e-5 at N_beta = 48), and leaves that error unchanged to 1e-12: the reading changes no
+    result at the oracle's accuracy."""
+    prob, g, qp, rows = eigen_case()
+    K0, _ = cbie.kernel_rows(prob, g, rows, qp)
+    so = core_variant(tmp_path, "plain_normal", "*ne = nrm[0] * R[0] + nrm[1] * R[1] + nrm[2] * R[2];",
+                      "*ne = nrm[0] * e[0] + nrm[1] * e[1] + nrm[2] * e[2];")
+    with monkeypatch.context() as m:
+        m.setattr(cbie, "_LIB", None)
+        m.setattr(cbie, "build_core", lambda force=False: so)
+        K1, _ = cbie.kernel_rows(prob, g, rows, qp)
+    e0, e1 = eigen_errors(prob, g, rows, K0), eigen_errors(prob, g, rows, K1)
+    assert max(e0) < 1e-4 and max(e1) < 1e-4
+    assert np.array_equal(K0[:2], K1[:2])                 # single-layer rows do not use n.(x - y)
+    for q in (2, 3):
+        d = rel(K1[q], K0[q])
+        assert 0 < d < 1e-3 * e0[1], (q, d, e0)
+    assert abs(e1[1] - e0[1]) < 1e-12
 
 
 # ------------------------------------------------------------------ octree and cone tables
