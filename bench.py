@@ -1,15 +1,19 @@
 """Benchmark: CBIE-IFGF N-Mueller GMRES solves on one GB300 (or N replicas).
 
-A step is one GMRES solve of A y = b (Eq. lin_system) on the 9,600-node
-dielectric sphere (radius 2 wavelengths, eps_r = 4, 96 patches x 10 x 10
-Chebyshev nodes), x-polarised plane wave along +z: every solver iteration
-runs the whole forward map (density prep, near matrix, IFGF leaf step,
-upward interpolation, target evaluation, N-Mueller combination) and a CGS2
-Arnoldi step.  value = unknowns x matvecs / s over the timed solves (4N
-unknowns per matvec).  The GMRES time-to-solve is reported beside it.
+A step is one GMRES solve of A y = b (Eq. lin_system) on the 153,600-node
+dielectric sphere (radius 4 wavelengths, eps_r = 2.25, 600 patches x 16 x 16
+Chebyshev nodes, 614,400 unknowns) for one of the 64 plane-wave incidences of
+the batched configuration (32 Fibonacci directions x 2 polarisations), in
+turn: every solver iteration runs the whole forward map (density prep, near
+matrix, IFGF leaf step, upward interpolation, target evaluation, N-Mueller
+combination) and a CGS2 Arnoldi step.  value = unknowns x matvecs / s over
+the timed solves (4N unknowns per matvec).  The GMRES time-to-solve, the true
+residual of a timed solve against the plain FP64 direct far sum (sampled
+patches) and the forward map's error are reported beside it.
 
 --impl reference times the CPU FP64 oracle (the unaccelerated CBIE forward
-map) on a bounded sample of the same workload instead.
+map, restricted to sampled patches whose kernel rows are built beforehand)
+on the same workload instead.
 """
 from __future__ import annotations
 
@@ -30,14 +34,13 @@ WORKLOADS = {
     "sphere9600": "sphere r=2 lambda, eps_r=4, 96 patches x 10x10 nodes (N=9600, 38400 unknowns)",
     "sphere153600": "sphere r=4 lambda, eps_r=2.25, 600 patches x 16x16 nodes (N=153600, 614400 unknowns)",
 }
-WORKLOAD = WORKLOADS["sphere9600"]
 METRIC = "IFGF N-Mueller unknown*matvecs/s at rel err <=1e-4; GMRES time-to-solve"
 UNIT = "unknown*matvecs/s"
 # cone segments at level D+1: (2, 3) keeps the forward-map error <= 1e-4 on this body
 NS0, NA0 = 2, 3
 
 
-def problem(name: str = "sphere9600"):
+def problem(name: str = "sphere153600"):
     from inputs import CONFIG_SPHERE_MEDIUM, CONFIG_SPHERE_SMALL, sphere_problem
     if name == "sphere384":
         return CONFIG_SPHERE_SMALL(8)
@@ -101,6 +104,9 @@ class ClockSampler:
 # sources whose change invalidates a recorded DRAM traffic figure of the IFGF kernels
 KERNEL_SOURCES = ("paper_2408_02274_gb300/csrc/ifgf.cu", "paper_2408_02274_gb300/csrc/common.cuh",
                   "paper_2408_02274_gb300/csrc/host_setup.cpp")
+
+
+KERNEL_NAMES = {"target": "k_target", "up": "k_up_runs", "leaf": "k_leaf", "near": "k_near"}
 
 
 def kernel_source_hash():
@@ -227,11 +233,22 @@ def alu_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def sampled_patches(prob, count, seed=19):
+    """`count` distinct patches drawn with a fixed seed (sampled accuracy checks)."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(prob.num_patches, size=min(count, prob.num_patches), replace=False))
+
+
+def rows_of(prob, pats):
+    npp = prob.nc ** 2
+    return (np.asarray(pats)[:, None] * npp + np.arange(npp)[None]).ravel()
+
+
 def run_gpu(args):
     import torch
     import paper_2408_02274_gb300 as lib
     from paper_2408_02274_gb300 import build as libbuild
-    from inputs import plane_wave
+    from inputs import fibonacci_incidences
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -244,82 +261,96 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     prob = problem(args.workload)
     delta = delta_of(prob)
+    t0 = time.perf_counter()
     plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
-                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=400)
+                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_iter,
+                                 gmres_scaling=args.gmres_scaling, gs_iters=args.gs_iters)
+    setup_s = time.perf_counter() - t0
     st = plan.stats()
     N = prob.n
     x, _, _ = prob.nodes()
-    # replicas solve different incidences (direction tilted per rank); rank 0 keeps +z
-    ang = 0.1 * rank
-    dvec = (np.sin(ang), 0.0, np.cos(ang))
-    inc = plane_wave(x, prob.k_ext, prob.omega, direction=dvec)
-    inc_h = torch.from_numpy(np.ascontiguousarray(inc)).pin_memory()
-    inc_d = inc_h.cuda()
+    # the 64 incidences of the batched configuration (32 Fibonacci directions x 2 polarisations);
+    # step k of rank r solves incidence (r * 7 + k) mod 64: replicas solve different incidences
+    incs = fibonacci_incidences(x, prob.k_ext, prob.omega)
+    nsteps = args.warmup + args.steps
+    order = [(rank * 7 + k) % incs.shape[0] for k in range(nsteps)]
+    used = sorted(set(order))
+    inc_h = {i: torch.from_numpy(np.ascontiguousarray(incs[i])).pin_memory() for i in used}
+    inc_d = {i: inc_h[i].cuda() for i in used}
+    del incs
     y_d = torch.empty((4, N), dtype=torch.complex128, device="cuda")
     y_h = torch.empty((4, N), dtype=torch.complex128).pin_memory()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    tol = args.tol
+    tol, maxit = args.tol, args.max_iter
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        plan.solve(inc_d, y_d, tol=tol, max_iter=400)
+    for k in range(args.warmup):
+        plan.solve(inc_d[order[k]], y_d, tol=tol, max_iter=maxit)
     # ---- timed device-resident solves (L2 flushed between steps, outside the events)
     lib.ifgf_set_timing(plan.handle, True)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
-    times, iters = [], []
-    for _ in range(args.steps):
+    times, iters, relres = [], [], []
+    for k in range(args.warmup, nsteps):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        it, rr, status = plan.solve(inc_d, y_d, tol=tol, max_iter=400)
+        it, rr, status = plan.solve(inc_d[order[k]], y_d, tol=tol, max_iter=maxit)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
         iters.append(it)
+        relres.append(rr)
     barrier()
     clk = clocks.stop()
     ktime, launches = lib.ifgf_get_timing(plan.handle)
     lib.ifgf_set_timing(plan.handle, False)
     t_tot = float(np.sum(times))
-    mv_total = float(np.sum(iters))
+    last_inc = order[-1]
+    # ---- true residual of the last timed solve, |b - A y| / |b| on sampled whole patches with
+    # A's far field by the plain FP64 direct sum (the operator the IFGF approximates)
+    pats = sampled_patches(prob, args.sample_patches)
+    rows = torch.from_numpy(rows_of(prob, pats)).cuda()
+    b = torch.empty((1, 4, N), dtype=torch.complex128, device="cuda")
+    plan.rhs(inc_d[last_inc][None], b)
+    Ay = torch.empty_like(y_d)
+    plan.apply_direct_patches(y_d, Ay, pats)
+    torch.cuda.synchronize()
+    true_res = float(torch.linalg.norm(b[0][:, rows] - Ay[:, rows]) / torch.linalg.norm(b[0][:, rows]))
     # ---- end to end: host buffers through bie_solve (copies inside the timed call)
-    e2e_times = []
-    for _ in range(max(1, min(args.steps, 3))):
+    e2e_times, e2e_its = [], []
+    for k in range(max(1, min(args.steps, args.e2e_steps))):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        it_h, _, _ = plan.solve(inc_h.numpy(), y_h.numpy(), tol=tol, max_iter=400)
+        it_h, _, _ = plan.solve(inc_h[order[args.warmup + k]].numpy(), y_h.numpy(), tol=tol, max_iter=maxit)
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
+        e2e_its.append(it_h)
     # ---- forward map alone, graph-replayed (median of 20)
     apply_tp = graph_apply_throughput(plan, N, flush)
-    # ---- accuracy of the timed path: one IFGF FP32 matvec vs the plain FP64 direct path
+    # ---- accuracy of the timed path: the FP32 IFGF forward map against the same plan with the
+    # plain FP64 direct far sum, on the sampled patches
     yv = torch.from_numpy(np.ascontiguousarray(
         (np.random.default_rng(7).standard_normal((4, N)) + 1j * np.random.default_rng(8).standard_normal((4, N)))
         / np.sqrt(2))).cuda()
-    o1 = torch.empty_like(yv)
+    o1, o2 = torch.empty_like(yv), torch.empty_like(yv)
     plan.apply(yv, o1)
-    ref_plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0,
-                                     precision=lib.IFGF_FP64 if prob.n <= 20000 else lib.IFGF_FP32,
-                                     far_mode=lib.IFGF_FAR_DIRECT, max_krylov=10)
-    o2 = torch.empty_like(yv)
-    ref_plan.apply(yv, o2)
+    plan.apply_direct_patches(yv, o2, pats)
     torch.cuda.synchronize()
-    matvec_err = float(torch.linalg.norm(o1 - o2) / torch.linalg.norm(o2))
-    ref_plan.close()
+    matvec_err = float(torch.linalg.norm(o1[:, rows] - o2[:, rows]) / torch.linalg.norm(o2[:, rows]))
     # ---- aggregate over ranks (max time)
     t_step = t_tot / args.steps
-    t_tot, e2e_max = aggregate_over_ranks(t_tot, max(e2e_times), dist, device="cuda")
+    t_tot, e2e_max = aggregate_over_ranks(t_tot, float(np.sum(e2e_times)), dist, device="cuda")
     units_per_step = 4.0 * N * float(np.mean(iters))
     value = whole_job_value(world, units_per_step, args.steps, t_tot)
-    e2e_value = whole_job_value(world, 4.0 * N * it_h, 1, e2e_max)
+    e2e_value = whole_job_value(world, 4.0 * N * float(np.mean(e2e_its)), len(e2e_times), e2e_max)
     # ---- roofline of the dominant kernel (largest summed time in the timed region)
     work = kernel_work(st)
     per_apply_launch = {"target": st["levels"] - 2, "up": st["levels"] - 3, "leaf": 1, "near": 1}
@@ -339,32 +370,44 @@ def run_gpu(args):
         achieved = per_launch / (dom_ms / dom_calls / 1e3) / 1e12
         peak = alu_peak_tflops(sm_mhz)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": recorded_traffic("k_up_runs", args.workload) if dom == "up" else None,
+                "traffic": recorded_traffic(KERNEL_NAMES[dom], args.workload),
                 "peak_source": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled)"}
     roof["kernel"] = {"target": "k_target (c)", "up": "k_up_runs (b)", "leaf": "k_leaf (a)", "near": "k_near (d)"}[dom]
+    roof["per_launch_work"] = per_launch
+    roof["launches"] = int(dom_calls)
     if roof["traffic"] is not None:
         roof["traffic_source"] = "profiles/dram_traffic.json (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+    stage_ms = {k: ktime[k][0] / max(napply, 1) for k in ktime}
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 Arnoldi, FP64 setup)", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "far_field": f"IFGF, Ps=3 Pa=5, (ns,na)_(D+1)=({NS0},{NA0})",
-                   "levels": st["levels"], "gmres_tol": tol, "rhs": "plane wave +z, x-pol",
+                   "levels": st["levels"], "gmres_tol": tol,
+                   "rhs": "the 64 plane-wave incidences of the batched configuration (32 Fibonacci directions x "
+                          "2 polarisations), one per step in turn",
+                   "gmres": "no restart, CGS2 FP64 Arnoldi" + (", right-scaled (m, j) blocks"
+                                                              if args.gmres_scaling else ""),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "256 MiB buffer written between timed steps (outside the events)"},
-        "gmres_time_to_solve_s": t_step, "gmres_iters": int(np.mean(iters)),
+        "gmres_time_to_solve_s": t_step, "gmres_iters": [int(i) for i in iters],
+        "gmres_relres_estimate_max": float(np.max(relres)),
+        "true_residual": {"value": true_res, "solve": f"last timed step (incidence {last_inc})",
+                          "operator": "same plan with the plain FP64 direct far sum (ifgf_apply_direct_patches)",
+                          "rows": f"{len(pats)} sampled whole patches ({int(rows.numel())} of {N} nodes)"},
         "matvec_rel_err_vs_direct": matvec_err,
-        "matvec_err_reference": "plain direct far sum, FP64" if prob.n <= 20000 else "plain direct far sum, FP32",
-        "stage_ms_per_apply": {k: ktime[k][0] / max(napply, 1) for k in ktime},
+        "matvec_err_reference": f"plain FP64 direct far sum on {len(pats)} sampled whole patches, same plan",
+        "stage_ms_per_apply": stage_ms,
         "apply_throughput": apply_tp,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 6 * N * 16,
-                "d2h_bytes_per_step": 4 * N * 16},
+                "d2h_bytes_per_step": 4 * N * 16, "solves": len(e2e_times),
+                "path": "bie_solve with pinned host buffers (incident field in, solution out, copies inside)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "plan": {"near_nnz": st["near_nnz"], "cones": st["cones"], "interactions": st["interactions"],
-                 "up_pairs": st["up_pairs"], "leaf_pairs": st["leaf_pairs"],
-                 "setup_s": st["setup_seconds"], "device_bytes": st["device_bytes"]},
+                 "up_pairs": st["up_pairs"], "leaf_pairs": st["leaf_pairs"], "setup_s": setup_s,
+                 "device_bytes": st["device_bytes"]},
     }
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(prob, delta, budget_s=args.cpu_budget)
@@ -374,38 +417,66 @@ def run_gpu(args):
     return result if rank == 0 else None
 
 
-def cpu_baseline(prob, delta, budget_s=15.0, reference_units=False):
-    """The CPU FP64 oracle as it stands: kernel rows of the unaccelerated CBIE
-    operator for whole patches plus the combination, on the host cores; the
-    full forward-map time is extrapolated from the sampled rows."""
-    import os as _os
-    from oracle import cbie
-    cores = _os.cpu_count() or 1
-    _os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    g = cbie.geometry_of(prob)
-    qp = cbie.QuadParams(delta=delta, n_beta=48, cov_d=4.0)
-    npp = prob.nc ** 2
+class OracleMatvec:
+    """The CPU FP64 oracle's unaccelerated CBIE forward map restricted to whole sampled
+    patches: the kernel rows of those patches' targets (Fejer terms, golden-section closest
+    points and singular moments) are built once, outside any timing; a timed "matvec" is what
+    the forward map does per application on those rows: the densities of all nodes (surface
+    divergence per patch), the dense row products of S_e, S_i, D_e, D_i with them, and the
+    N-Mueller combination on the sampled patches."""
+
+    def __init__(self, prob, delta, patches):
+        import os as _os
+        from oracle import cbie
+        self.cores = _os.cpu_count() or 1
+        _os.environ.setdefault("OMP_NUM_THREADS", str(self.cores))
+        self.cbie, self.prob = cbie, prob
+        self.g = cbie.geometry_of(prob)
+        npp = prob.nc ** 2
+        self.rows = np.concatenate([np.arange(p * npp, (p + 1) * npp) for p in patches])
+        self.patches = list(patches)
+        t0 = time.perf_counter()
+        self.K, _ = cbie.kernel_rows(prob, self.g, self.rows, cbie.QuadParams(delta=delta, n_beta=48, cov_d=4.0))
+        self.setup_s = time.perf_counter() - t0
+
+    def __call__(self, y):
+        cbie, prob, rows = self.cbie, self.prob, self.rows
+        phi = cbie.densities(y, self.g)
+        S = np.zeros((2, 8, prob.n), dtype=complex)
+        D = np.zeros((2, 6, prob.n), dtype=complex)
+        S[:, :, rows], D[:, :, rows] = cbie.scalar_fields(self.K, phi)
+        return cbie.combine(prob, self.g, y, S, D)[:, rows]
+
+
+def oracle_patches(prob, count):
+    """`count` patches spread over the body (deterministic)."""
+    return sorted({int(round(k * prob.num_patches / count)) % prob.num_patches for k in range(count)})
+
+
+def cpu_baseline(prob, delta, budget_s=15.0):
+    """The CPU FP64 oracle as it stands, timed on the host cores: repeated sampled matvecs
+    (OracleMatvec) for about `budget_s` seconds; value = unknowns processed per second,
+    4 x (sampled rows) per matvec."""
     from inputs import random_densities
+    om = OracleMatvec(prob, delta, oracle_patches(prob, 1 if prob.n > 50000 else 2))
     y = random_densities(prob.n, 11)
-    phi = cbie.densities(y, g)
+    om(y)                                     # first touch of the row arrays
     t0 = time.perf_counter()
-    rows_done = 0
-    p = 0
+    reps = 0
     while True:
-        rows = np.arange(p * npp, (p + 1) * npp)
-        K, _ = cbie.kernel_rows(prob, g, rows, qp)
-        cbie.scalar_fields(K, phi)
-        rows_done += npp
-        p += 1
-        if time.perf_counter() - t0 > budget_s or p >= prob.num_patches:
+        om(y)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    t_full = dt * prob.n / rows_done
-    return {"value": 4.0 * prob.n / t_full, "unit": UNIT, "cores": int(_os.environ.get("OMP_NUM_THREADS", cores)),
-            "kind": "oracle", "host": cpu_info(),
-            "sample": f"{p} of {prob.num_patches} patches ({rows_done} target rows) of the FP64 CBIE forward map "
-                      f"(kernel rows with singular moments + sums), {dt:.1f} s; full matvec extrapolated "
-                      f"to {t_full:.1f} s"}
+    nrows = om.rows.size
+    return {"value": 4.0 * nrows * reps / dt, "unit": UNIT,
+            "cores": int(os.environ.get("OMP_NUM_THREADS", om.cores)), "kind": "oracle", "host": cpu_info(),
+            "sample": f"{reps} FP64 CBIE forward maps restricted to {len(om.patches)} of {prob.num_patches} "
+                      f"patches ({nrows} of {prob.n} target rows, all {prob.n} sources): densities, dense "
+                      f"kernel-row products and combination, {dt:.1f} s; the rows' kernel entries (singular "
+                      f"moments included) were built once beforehand in {om.setup_s:.1f} s, untimed",
+            "rows_per_matvec": int(nrows), "matvecs": reps, "seconds": dt, "row_setup_s": om.setup_s}
 
 
 def run_apply(args):
@@ -445,24 +516,34 @@ def run_apply(args):
 
 
 def run_reference(args):
+    """The reference arm: the CPU FP64 oracle (there is no other implementation of the
+    method), on rank 0 only.  A step is one oracle forward map restricted to sampled whole
+    patches (OracleMatvec, rows built once before the warm-up); value = 4 x rows x steps / time."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
-    prob = problem()
-    delta = delta_of(prob)
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(prob, delta, budget_s=max(2.0, 30.0 / max(1, args.steps + args.warmup))))
-    timed = vals[args.warmup:]
-    v = float(np.mean([t["value"] for t in timed]))
-    # a step of this arm is one forward map of the oracle, extrapolated from the timed sample
-    ms_step = 1e3 * 4.0 * prob.n / v
+    from inputs import random_densities
+    prob = problem(args.workload)
+    om = OracleMatvec(prob, delta_of(prob), oracle_patches(prob, 1 if prob.n > 50000 else 2))
+    y = random_densities(prob.n, 11)
+    for _ in range(args.warmup):
+        om(y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        om(y)
+    dt = time.perf_counter() - t0
+    nrows = om.rows.size
+    v = 4.0 * nrows * args.steps / dt
+    sample = (f"each step: one FP64 CBIE forward map restricted to {len(om.patches)} of {prob.num_patches} patches "
+              f"({nrows} of {prob.n} target rows, all sources); kernel rows built once beforehand in "
+              f"{om.setup_s:.1f} s, untimed")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": timed[0]["cores"], "kind": "oracle",
-                             "sample": timed[0]["sample"], "host": timed[0]["host"]},
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", om.cores)),
+                             "kind": "oracle", "sample": sample, "host": cpu_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -835,7 +916,10 @@ def main():
     ap.add_argument("--nrhs", type=int, default=8)
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--max-krylov", type=int, default=200)
-    ap.add_argument("--workload", default="sphere9600", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere153600", choices=sorted(WORKLOADS))
+    ap.add_argument("--max-iter", type=int, default=300, help="GMRES iterations (Krylov capacity) of a solve step")
+    ap.add_argument("--sample-patches", type=int, default=24, help="patches of the sampled FP64 accuracy checks")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="host-buffer solves of the end-to-end figure")
     ap.add_argument("--bar-h", type=float, default=0.07)
     ap.add_argument("--leaf-pts", type=int, default=64)
     ap.add_argument("--sample-rows", type=int, default=10000)
