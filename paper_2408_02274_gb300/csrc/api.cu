@@ -358,6 +358,7 @@ void build(ifgf_plan_t* p) {
   p->stats.n = N;
   p->stats.levels = t.D;
   check(setup_combine_kernels(), "combine kernel attributes");
+  check(setup_ifgf_kernels(), "IFGF kernel attributes");
   // ---------------- per-apply buffers and GMRES workspace
   const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
   const size_t B = (size_t)p->batch;

@@ -409,32 +409,46 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
 // kUpRunMax points that fall in the same child cone (box-independent tables
 // built with the octree), one warp per run and one lane per real column.  The
 // warp loads the child cone's 75 x 32 coefficients once into registers (75
-// per lane) and then sweeps the run: per point only the cone scalars are read
-// from shared memory, and the 3D Chebyshev sum is contracted separably (over
-// phi, then theta, then s).  Runs of different children add into the parent
-// values with shared-memory atomics (one column per lane, so no bank
-// conflicts within a warp).
+// per lane) and then sweeps the run: per point the Chebyshev values and the
+// re-centring factor, formed once per (octant, point) in the prologue, are read
+// from shared memory with vector loads, and the 3D Chebyshev sum is contracted
+// separably (over phi, then theta, then s: 74 FMA per lane).  The parent points
+// are split into kUpGroups fixed groups, one per warp, so each warp adds into
+// its own points' values with plain shared-memory adds.
 struct RunTabs {
   const int* order;      // [ncompact][8][75] points ranked by (group, child cone)
   const int* task;       // runs per (compact cone, group), longest first: start | len << 8 | octant << 16
   const int* task_ptr;   // [ncompact * kUpGroups + 1]
 };
 
-template <typename T>
-struct PtInfo2 {
-  int cslot;
-  T ts, tt, tp;
-  T fr[2], fi[2];
+// Per (octant, parent point) data of the FP32 upward pass, formed once in the prologue and
+// read by every lane: the Chebyshev values T_1..T_4 of the local phi and theta coordinates and
+// T_1, T_2 of the radial one (T_0 = 1 is implicit), 16-byte aligned for vector loads.
+struct __align__(16) UpCheb {
+  float tp[4];
+  float tt[4];
+  float ts[2];
+  float pad[2];
 };
 
 constexpr int kUpRunWarps = kUpGroups;   // warp w adds only into the parent points of group w
 
-__global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A, RunTabs RT) {
+// dynamic shared memory of k_up_runs (above the 48 KB static limit)
+constexpr size_t kUpRunSmem = sizeof(UpCheb) * 8 * kQ      // Chebyshev values per (octant, point)
+                              + sizeof(float4) * 8 * kQ    // re-centring factors (re, im) x 2 kernels
+                              + sizeof(int) * 8 * kQ       // child slot per (octant, point)
+                              + sizeof(float) * kQ * kVS   // parent values
+                              + sizeof(float) * kQ * 3;    // parent points
+
+__global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A, RunTabs RT) {
   using T = float;
   __shared__ SmallMaps<T> M;
-  __shared__ T Xp[kQ][3];
-  __shared__ PtInfo2<T> info[8][kQ];
-  __shared__ T vals[kQ * kVS];
+  extern __shared__ float4 up_smem[];
+  UpCheb (*cheb)[kQ] = reinterpret_cast<UpCheb (*)[kQ]>(up_smem);
+  float4 (*fac)[kQ] = reinterpret_cast<float4 (*)[kQ]>(cheb + 8);
+  int (*cslot)[kQ] = reinterpret_cast<int (*)[kQ]>(fac + 8);
+  T* vals = reinterpret_cast<T*>(cslot + 8);
+  T (*Xp)[3] = reinterpret_cast<T (*)[3]>(vals + kQ * kVS);
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
   A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
@@ -448,6 +462,8 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
   __syncthreads();
   const T off = (T)(0.5 * A.Hc);
   const T kk[2] = {A.ke, A.ki};
+  // prologue: per (octant, parent point) the child slot, the Chebyshev values of the point's
+  // local coordinates in its child cone, and the re-centring factor of both kernels
   for (int e = t; e < 8 * kQ; e += blockDim.x) {
     const int o = e / kQ, q = e % kQ;
     const int cb = A.child[8 * P + o];
@@ -456,83 +472,71 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 3) k_up_runs(UpArgs<float> A
     const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
     const int ccx = A.up_cc[((size_t)ci * 8 + o) * kQ + q];
     const cone_key cc = A.ckeys_c[ccx];
-    PtInfo2<T>& I = info[o][q];
-    I.cslot = A.cmap_c[(size_t)cb * A.ncomp_c + ccx];
-    T rc, sth, cth, sph, cph;
-    local_coords(A.cgc, cc, x, y, z, &I.ts, &I.tt, &I.tp, &rc, &sth, &cth, &sph, &cph);
+    cslot[o][q] = A.cmap_c[(size_t)cb * A.ncomp_c + ccx];
+    T ts, tt, tp, rc, sth, cth, sph, cph;
+    local_coords(A.cgc, cc, x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
+    T v5[5], v3[3];
+    UpCheb& C = cheb[o][q];
+    cheb_vals<T, 5>(tp, v5);
+    C.tp[0] = v5[1]; C.tp[1] = v5[2]; C.tp[2] = v5[3]; C.tp[3] = v5[4];
+    cheb_vals<T, 5>(tt, v5);
+    C.tt[0] = v5[1]; C.tt[1] = v5[2]; C.tt[2] = v5[3]; C.tt[3] = v5[4];
+    cheb_vals<T, 3>(ts, v3);
+    C.ts[0] = v3[1]; C.ts[1] = v3[2];
     // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
     const T rp = sqrt_t(Xp[q][0] * Xp[q][0] + Xp[q][1] * Xp[q][1] + Xp[q][2] * Xp[q][2]);
     const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
-    for (int ks = 0; ks < 2; ++ks) {
-      T sn, cs;
-      sincos_t(kk[ks] * dr, &sn, &cs);
-      I.fr[ks] = rp / rc * cs;
-      I.fi[ks] = rp / rc * sn;
-    }
+    T sn0, cs0, sn1, cs1;
+    sincos_t(kk[0] * dr, &sn0, &cs0);
+    sincos_t(kk[1] * dr, &sn1, &cs1);
+    const T a = rp / rc;
+    fac[o][q] = make_float4(a * cs0, a * sn0, a * cs1, a * sn1);
   }
   __syncthreads();
   const int ks = lane >> 4;   // columns 0..15 belong to kernel e, 16..31 to kernel i
+  // complex re-centring on interleaved (re, im) lanes: with w the partner lane's value,
+  // re' = v fr - w fi (even lanes), im' = v fr + w fi (odd lanes)
+  const T sgn = (lane & 1) ? T(1) : T(-1);
   // the warp's own runs (its group of parent points, all octants); runs of absent children
   // are skipped.  Only this warp adds into these points' values: plain shared-memory adds.
   const int w1 = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp + 1);
   for (int w = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp); w < w1; ++w) {
     const int tk = __ldg(RT.task + w);
     const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
+    if (A.child[8 * P + o] < 0) continue;
     const size_t g = (size_t)ci * 8 + o;
-    const bool have = A.child[8 * P + o] >= 0;
-    const int myq = (have && lane < len) ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
-    const int cslot = have ? info[o][__shfl_sync(0xffffffffu, myq, 0)].cslot : -1;
-    if (cslot >= 0) {   // always, for a present child: the host marked every such cone relevant
-      const T* C = A.coefs_c + (size_t)cslot * kQ * 32 + lane;
-      T c[kQ];
+    const int myq = lane < len ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
+    // one child slot per run: the host marked every such cone relevant
+    const T* Cg = A.coefs_c + (size_t)cslot[o][__shfl_sync(0xffffffffu, myq, 0)] * kQ * 32 + lane;
+    T c[kQ];
 #pragma unroll
-      for (int k = 0; k < kQ; ++k) c[k] = __ldg(C + k * 32);
-      // two points per step (the second one repeats the last point of an odd run and
-      // is not added): their contractions interleave
-      for (int a = 0; a < len; a += 2) {
-        const bool two = a + 1 < len;
-        const int q0 = __shfl_sync(0xffffffffu, myq, a);
-        const int q1 = __shfl_sync(0xffffffffu, myq, two ? a + 1 : a);
-        const PtInfo2<T>& I0 = info[o][q0];
-        const PtInfo2<T>& I1 = info[o][q1];
-        T Ts0[3], Tt0[5], Tp0[5], Ts1[3], Tt1[5], Tp1[5];
-        cheb_vals<T, 3>(I0.ts, Ts0);
-        cheb_vals<T, 5>(I0.tt, Tt0);
-        cheb_vals<T, 5>(I0.tp, Tp0);
-        cheb_vals<T, 3>(I1.ts, Ts1);
-        cheb_vals<T, 5>(I1.tt, Tt1);
-        cheb_vals<T, 5>(I1.tp, Tp1);
-        T E0[3] = {T(0), T(0), T(0)}, E1[3] = {T(0), T(0), T(0)};
+    for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
+    for (int a = 0; a < len; ++a) {
+      const int q = __shfl_sync(0xffffffffu, myq, a);
+      const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
+      const float4 P4 = cp[0], T4 = cp[1], S4 = cp[2];
+      const float4 F4 = fac[o][q];
+      const T Tp[4] = {P4.x, P4.y, P4.z, P4.w};
+      const T Tt[4] = {T4.x, T4.y, T4.z, T4.w};
+      // separable contraction (phi, then theta, then s), T_0 = 1 folded in
+      T E[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+      for (int i = 0; i < 3; ++i) {
+        T e = T(0);
 #pragma unroll
-          for (int j = 0; j < 5; ++j) {
-            const T* cij = c + (i * 5 + j) * 5;
-            T d0 = Tp0[0] * cij[0], d1 = Tp1[0] * cij[0];
+        for (int j = 0; j < 5; ++j) {
+          const T* cij = c + (i * 5 + j) * 5;
+          T d = cij[0];
 #pragma unroll
-            for (int k = 1; k < 5; ++k) {
-              d0 += Tp0[k] * cij[k];
-              d1 += Tp1[k] * cij[k];
-            }
-            E0[i] += Tt0[j] * d0;
-            E1[i] += Tt1[j] * d1;
-          }
-        const T v0 = Ts0[0] * E0[0] + Ts0[1] * E0[1] + Ts0[2] * E0[2];
-        const T v1 = Ts1[0] * E1[0] + Ts1[1] * E1[1] + Ts1[2] * E1[2];
-        const T w0 = __shfl_xor_sync(0xffffffffu, v0, 1);
-        const T w1 = __shfl_xor_sync(0xffffffffu, v1, 1);
-        const bool odd = lane & 1;
-        {
-          const T re = odd ? w0 : v0, im = odd ? v0 : w0;
-          const T fr = I0.fr[ks], fi = I0.fi[ks];
-          vals[q0 * kVS + lane] += odd ? (re * fi + im * fr) : (re * fr - im * fi);
+          for (int k = 0; k < 4; ++k) d = fmaf(Tp[k], cij[k + 1], d);
+          e = j == 0 ? d : fmaf(Tt[j - 1], d, e);
         }
-        if (two) {
-          const T re = odd ? w1 : v1, im = odd ? v1 : w1;
-          const T fr = I1.fr[ks], fi = I1.fi[ks];
-          vals[q1 * kVS + lane] += odd ? (re * fi + im * fr) : (re * fr - im * fi);
-        }
+        E[i] = e;
       }
+      const T v = fmaf(S4.y, E[2], fmaf(S4.x, E[1], E[0]));
+      const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
+      const T fr = ks ? F4.z : F4.x, fi = ks ? F4.w : F4.y;
+      vals[q * kVS + lane] += fmaf(v, fr, sgn * fi * wv);
     }
   }
   __syncthreads();
@@ -722,7 +726,8 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {
         if constexpr (std::is_same<T, float>::value)
-          k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, 0, s>>>(U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
+          k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, kUpRunSmem, s>>>(
+              U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
         else
           k_up<T><<<dim3(Pp.nslots, nrhs), kUpThreads, 0, s>>>(U);
       }
@@ -734,6 +739,10 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
 }
 
 }  // namespace
+
+cudaError_t setup_ifgf_kernels() {
+  return cudaFuncSetAttribute(k_up_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRunSmem);
+}
 
 cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   if (p->desc.precision == IFGF_FP64) return run_ifgf<double>(p, s, nrhs);

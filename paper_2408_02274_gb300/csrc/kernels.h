@@ -48,6 +48,8 @@ cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1
 cudaError_t launch_far_direct_blocks(const ifgf_plan_t* p, cudaStream_t s, const int* blocks, int nblocks);
 cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
                                   double ke, double ki, int precision, void* f28, cudaStream_t s);
+// opt the IFGF kernels into the dynamic shared memory they use (once per device)
+cudaError_t setup_ifgf_kernels();
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
 cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 // zero f28

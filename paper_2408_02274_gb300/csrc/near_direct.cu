@@ -50,8 +50,10 @@ __device__ __forceinline__ void near_madd(const T* w, const T* ph, T* acc) {
   }
 }
 
-// One warp per target row; each lane takes two nonzeros per step (FP32) with independent
-// loads (column, weights, gathered densities) so that more of them are in flight.
+// One warp per target row; each lane takes U nonzeros per step (two in FP32, one in FP64,
+// which needs twice the registers per nonzero) with independent loads.  The column indices
+// of the next step are loaded one step ahead, so the gather of the densities (which depends
+// on the column) does not wait behind a column load on every step.
 template <typename T>
 __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__ row_ptr,
                                               const int* __restrict__ col, const T* __restrict__ val,
@@ -66,24 +68,33 @@ __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__
 #pragma unroll
   for (int k = 0; k < 56; ++k) acc[k] = T(0);
   const int64_t e0 = row_ptr[row], e1 = row_ptr[row + 1];
+  constexpr int U = sizeof(T) == 4 ? 2 : 1;
   int64_t e = e0 + lane;
-  // FP32: two nonzeros per step; FP64 (twice the registers per nonzero) takes one
-  constexpr bool kTwo = sizeof(T) == 4;
-  for (; kTwo && e + 32 < e1; e += 64) {
-    const int m0 = __ldg(col + e), m1 = __ldg(col + e + 32);
-    alignas(16) T w0[8], w1[8], p0[16], p1[16];
-    ldg_vec<T, 8>(val + 8 * e, w0);
-    ldg_vec<T, 8>(val + 8 * (e + 32), w1);
-    ldg_vec<T, 16>(phi + 16 * (size_t)m0, p0);
-    ldg_vec<T, 16>(phi + 16 * (size_t)m1, p1);
-    near_madd(w0, p0, acc);
-    near_madd(w1, p1, acc);
+  int mc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) mc[u] = (e + 32 * u < e1) ? __ldg(col + e + 32 * u) : 0;
+  for (; e + 32 * (U - 1) < e1; e += 32 * U) {
+    int mn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t en = e + 32 * (U + u);
+      mn[u] = en < e1 ? __ldg(col + en) : 0;
+    }
+    alignas(16) T w[U][8], ph[U][16];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      ldg_vec<T, 8>(val + 8 * (e + 32 * u), w[u]);
+      ldg_vec<T, 16>(phi + 16 * (size_t)mc[u], ph[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) near_madd(w[u], ph[u], acc);
+#pragma unroll
+    for (int u = 0; u < U; ++u) mc[u] = mn[u];
   }
-  for (; e < e1; e += 32) {
-    const int m0 = __ldg(col + e);
+  if (U > 1 && e < e1) {   // one nonzero left for this lane; its column is mc[0]
     alignas(16) T w0[8], p0[16];
     ldg_vec<T, 8>(val + 8 * e, w0);
-    ldg_vec<T, 16>(phi + 16 * (size_t)m0, p0);
+    ldg_vec<T, 16>(phi + 16 * (size_t)mc[0], p0);
     near_madd(w0, p0, acc);
   }
 #pragma unroll
