@@ -45,7 +45,10 @@ enum {
   IFGF_EINTERNAL = 7      /* an internal consistency check failed */
 };
 
-enum { IFGF_FP64 = 0, IFGF_FP32 = 1 };          /* arithmetic of the per-apply work */
+/* arithmetic of the per-apply work: IFGF_FP64 everything in FP64; IFGF_FP32 everything in FP32
+ * (densities, near matrix, fields, IFGF kernels); IFGF_MIXED the IFGF kernels (a)-(c) in FP32 and
+ * the densities, near-field weights and matvec, fields and N-Mueller combination in FP64 */
+enum { IFGF_FP64 = 0, IFGF_FP32 = 1, IFGF_MIXED = 2 };
 enum { IFGF_FAR_IFGF = 0, IFGF_FAR_DIRECT = 1 }; /* far-field algorithm */
 
 typedef struct ifgf_plan_t* ifgf_plan;
@@ -79,7 +82,7 @@ typedef struct {
   int32_t gs_iters;        /* golden-section iterations per direction (Eq. dist_min); 0 -> 60.
                               The edge snap follows the final bracket, so 10-20 steps find the
                               same closest points after the Newton polish */
-  int32_t precision;       /* IFGF_FP64 or IFGF_FP32: arithmetic of steps (a)-(d) per apply */
+  int32_t precision;       /* IFGF_FP64, IFGF_FP32 or IFGF_MIXED: arithmetic of steps (a)-(d) per apply */
   int32_t far_mode;        /* IFGF_FAR_IFGF or IFGF_FAR_DIRECT (plain O(N^2) far sum) */
   int32_t max_krylov;      /* GMRES basis capacity allocated by plan_create (0 -> 300, <= 1000) */
   int32_t batch;           /* right-hand sides one batched call may carry (ifgf_apply_batch,
@@ -91,6 +94,9 @@ typedef struct {
                               diag(2/(mu_e+mu_i) on m, 2/(eps_e+eps_i) on j) and y = D z, so the
                               identity parts of both block rows become 1 (a constant right
                               scaling: same solution, residuals of the unscaled system) */
+  int32_t upward_tc;       /* 1: the upward step (b) of the FP32 IFGF kernels as TF32 contractions on
+                              the tensor cores (tcgen05; same results to FP32 rounding); 0: FP32 SIMT
+                              contractions (default: faster here, see the header of k_up_tc) */
 } ifgf_plan_desc;
 
 /*

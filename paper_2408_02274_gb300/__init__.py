@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libifgf.so")
 
 IFGF_OK, IFGF_EINVAL, IFGF_ENOMEM, IFGF_ECUDA, IFGF_ENOCONV, IFGF_ETIMEOUT, IFGF_EUNSUPPORTED, IFGF_EINTERNAL = range(8)
-IFGF_FP64, IFGF_FP32 = 0, 1
+IFGF_FP64, IFGF_FP32, IFGF_MIXED = 0, 1, 2
 IFGF_FAR_IFGF, IFGF_FAR_DIRECT = 0, 1
 IFGF_PART_NEAR, IFGF_PART_FAR, IFGF_PART_ALL = 1, 2, 3
 
@@ -44,7 +44,7 @@ class ifgf_plan_desc(ctypes.Structure):
         ("delta", ctypes.c_double), ("n_beta", ctypes.c_int32), ("cov_d", ctypes.c_double),
         ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
         ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_leaf_pts", ctypes.c_int32),
-        ("gmres_scaling", ctypes.c_int32),
+        ("gmres_scaling", ctypes.c_int32), ("upward_tc", ctypes.c_int32),
     ]
 
 
@@ -201,13 +201,13 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                      gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                      max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0,
-                     gmres_scaling: int = 0):
+                     gmres_scaling: int = 0, upward_tc: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
               leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-              max_leaf_pts, gmres_scaling)
+              max_leaf_pts, gmres_scaling, upward_tc)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h
@@ -215,12 +215,12 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
 
 def _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
           leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch, max_leaf_pts,
-          gmres_scaling):
+          gmres_scaling, upward_tc=0):
     ng = int(arrs[3].shape[1])
     return ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
                           k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
                           min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-                          max_leaf_pts, gmres_scaling)
+                          max_leaf_pts, gmres_scaling, upward_tc)
 
 
 def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: float, k_int: float,
@@ -228,13 +228,14 @@ def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext
                        delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
                        leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                        gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
-                       max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0, gmres_scaling: int = 0) -> dict:
+                       max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0, gmres_scaling: int = 0,
+                       upward_tc: int = 0) -> dict:
     """ifgf_plan_estimate: the device memory ifgf_plan_create would allocate for the same
     arguments (host work only; near-matrix figures are upper bounds)."""
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
               leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-              max_leaf_pts, gmres_scaling)
+              max_leaf_pts, gmres_scaling, upward_tc)
     e = ifgf_plan_estimate_t()
     _check(load().ifgf_plan_estimate(ctypes.byref(d), ctypes.byref(e)), "ifgf_plan_estimate")
     out = {name: getattr(e, name) for name, _ in ifgf_plan_estimate_t._fields_ if name != "cones"}

@@ -122,15 +122,24 @@ ifgf_status validate(const ifgf_plan_desc* d) {
   if (!(d->cov_d >= 2)) return IFGF_EINVAL;
   if (d->ns0 < 1 || d->na0 < 1 || d->ns0 > 64 || d->na0 > 64) return IFGF_EINVAL;
   if (d->leaf_size < 0 || d->gs_iters < 0 || d->gs_iters > 200) return IFGF_EINVAL;
-  if (d->precision != IFGF_FP64 && d->precision != IFGF_FP32) return IFGF_EINVAL;
+  if (d->precision != IFGF_FP64 && d->precision != IFGF_FP32 && d->precision != IFGF_MIXED) return IFGF_EINVAL;
   if (d->far_mode != IFGF_FAR_IFGF && d->far_mode != IFGF_FAR_DIRECT) return IFGF_EINVAL;
   if (d->max_krylov < 0 || d->max_krylov > 1000) return IFGF_EINVAL;
   if (d->batch < 0 || d->batch > 1024) return IFGF_EINVAL;
   if (d->max_leaf_pts < 0 || d->max_leaf_pts > 1000000) return IFGF_EINVAL;
   if (d->gmres_scaling < 0 || d->gmres_scaling > 1) return IFGF_EINVAL;
+  if (d->upward_tc < 0 || d->upward_tc > 1) return IFGF_EINVAL;
   if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
   if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
   return IFGF_OK;
+}
+
+// The upward step into level L runs on the tensor cores when the plan asks for it (upward_tc),
+// its IFGF kernels are FP32 (FP32 and mixed plans) and L has tensor-core tables whose cones fit
+// the kernel's unit table.
+bool upward_tc(const ifgf_plan_desc& d, const HostLevel& L) {
+  return d.upward_tc == 1 && !ifgf64(d) && d.far_mode == IFGF_FAR_IFGF && !L.tc_item.empty() &&
+         L.tc_max_units <= kTcMaxUnits;
 }
 
 void build(ifgf_plan_t* p) {
@@ -263,8 +272,8 @@ void build(ifgf_plan_t* p) {
     p->near.row_ptr = A.upload(row_ptr);
     p->near.col = A.upload(col.data(), col.size());
     int* d_pair = SN.upload(pair.data(), pair.size());
-    // the near values in the plan's precision only
-    if (d.precision == IFGF_FP64)
+    // the near values in the plan's storage precision only
+    if (store64(d))
       p->near.val64 = A.dev<double>(8 * (size_t)p->near.nnz);
     else
       p->near.val32 = A.dev<float>(8 * (size_t)p->near.nnz);
@@ -316,7 +325,24 @@ void build(ifgf_plan_t* p) {
     Dl.up_order = A.upload(L.up_order);
     Dl.up_task = A.upload(L.up_task);
     Dl.up_task_ptr = A.upload(L.up_task_ptr);
+    if (upward_tc(d, L)) {
+      Dl.tc = true;
+      Dl.tc_order = A.upload(L.tc_order);
+      Dl.tc_unit = A.upload(L.tc_unit);
+      Dl.tc_unit_ptr = A.upload(L.tc_unit_ptr);
+      Dl.tc_item = A.upload(L.tc_item);
+      Dl.ntc_items = (int)(L.tc_item.size() / kTcBoxes);
+    }
+    {
+      std::vector<double2> th(L.na), ph(2 * (size_t)L.na);
+      for (int g = 0; g < L.na; ++g) th[g] = make_double2(std::cos(g * kPi / L.na), std::sin(g * kPi / L.na));
+      for (int g = 0; g < 2 * L.na; ++g) ph[g] = make_double2(std::cos(g * kPi / L.na), std::sin(g * kPi / L.na));
+      Dl.trig_th = A.upload(th);
+      Dl.trig_ph = A.upload(ph);
+    }
     Dl.tgt_ptr = A.upload(L.tgt_ptr);
+    Dl.tgt_chunk = reinterpret_cast<int2*>(A.upload(L.tgt_chunk));
+    Dl.ntgt_chunks = (int)(L.tgt_chunk.size() / 2);
     Dl.tgt_slot = A.upload(L.tgt_slot.data(), L.tgt_slot.size());
     Dl.ninter = (int64_t)L.tgt_slot.size();
     Dl.cstride = (size_t)Dl.nslots * kQ * 32;
@@ -334,7 +360,7 @@ void build(ifgf_plan_t* p) {
     for (int dd = 3; dd <= t.D; ++dd) need[dd & 1] = std::max(need[dd & 1], p->dl[dd].cstride * (size_t)p->batch);
     void* buf[2] = {nullptr, nullptr};
     for (int a = 0; a < 2; ++a)
-      if (need[a]) buf[a] = (d.precision == IFGF_FP64) ? (void*)A.dev<double>(need[a]) : (void*)A.dev<float>(need[a]);
+      if (need[a]) buf[a] = ifgf64(d) ? (void*)A.dev<double>(need[a]) : (void*)A.dev<float>(need[a]);
     for (int dd = 3; dd <= t.D; ++dd) p->dl[dd].coefs = buf[dd & 1];
   }
   for (int dd = 1; dd < 3 && dd <= t.D; ++dd) p->stats.boxes[dd] = (int)t.lv[dd].key.size();
@@ -360,13 +386,16 @@ void build(ifgf_plan_t* p) {
   check(setup_combine_kernels(), "combine kernel attributes");
   check(setup_ifgf_kernels(), "IFGF kernel attributes");
   // ---------------- per-apply buffers and GMRES workspace
-  const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
+  const size_t el = store64(d) ? sizeof(double) : sizeof(float);
+  const size_t el_s = ifgf64(d) ? sizeof(double) : sizeof(float);   // weighted densities read by IFGF
   const size_t B = (size_t)p->batch;
   p->phi = A.dev<char>(16 * (size_t)N * el * B);
-  p->a_sorted = A.dev<char>(16 * (size_t)N * el * B);
+  p->a_sorted = A.dev<char>(16 * (size_t)N * el_s * B);
   p->a_orig = A.dev<char>(16 * (size_t)N * el * B);
   p->f28 = A.dev<char>(56 * (size_t)N * el * B);
   p->phi64 = A.dev<double>(16 * (size_t)N * B);
+  p->dev_err = A.dev<int>(1);
+  check(cudaMemset(p->dev_err, 0, sizeof(int)), "status word");
   GmresWork& G = p->gm;
   G.max_iter = d.max_krylov > 0 ? d.max_krylov : 300;
   const size_t n4 = 4 * (size_t)N, m1 = (size_t)(G.max_iter + 1);
@@ -540,7 +569,8 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
   const ifgf_plan_desc& d = *desc;
   const int P = d.num_patches, nc = d.nc, ng = d.ng, npp = nc * nc, N = P * npp;
   const size_t B = (size_t)(d.batch > 0 ? d.batch : 1);
-  const size_t el = (d.precision == IFGF_FP64) ? sizeof(double) : sizeof(float);
+  const size_t el = store64(d) ? sizeof(double) : sizeof(float);
+  const size_t el_s = ifgf64(d) ? sizeof(double) : sizeof(float);
   try {
     HostTree t;
     const double leaf = d.leaf_size > 0 ? d.leaf_size : 0.25 * 2.0 * kPi / d.k_ext;
@@ -611,18 +641,28 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
       tb.dev<int32_t>(L.up_order.size());
       tb.dev<int32_t>(L.up_task.size());
       tb.dev<int32_t>(L.up_task_ptr.size());
+      if (upward_tc(d, L)) {
+        tb.dev<int32_t>(L.tc_order.size());
+        tb.dev<int32_t>(L.tc_unit.size());
+        tb.dev<int32_t>(L.tc_unit_ptr.size());
+        tb.dev<int32_t>(L.tc_item.size());
+      }
+      tb.dev<double2>((size_t)L.na);
+      tb.dev<double2>(2 * (size_t)L.na);
       tb.dev<int64_t>(L.tgt_ptr.size());
+      tb.dev<int32_t>(L.tgt_chunk.size());
       tb.dev<int32_t>(L.tgt_slot.size());
       out->cones[dd] = (int64_t)nslots;
       need[dd & 1] = std::max(need[dd & 1], nslots * kQ * 32 * B);
     }
+    tb.dev<int>(1);   // the plan's device status word
     ByteCount cf;
     if (d.far_mode == IFGF_FAR_IFGF)
       for (int a = 0; a < 2; ++a)
-        if (need[a]) (el == sizeof(double)) ? cf.dev<double>(need[a]) : cf.dev<float>(need[a]);
+        if (need[a]) (el_s == sizeof(double)) ? cf.dev<double>(need[a]) : cf.dev<float>(need[a]);
     // per-apply buffers and GMRES workspace
     ByteCount ap, gm;
-    for (int k = 0; k < 3; ++k) ap.dev<char>(16 * (size_t)N * el * B);
+    for (int k = 0; k < 3; ++k) ap.dev<char>(16 * (size_t)N * (k == 1 ? el_s : el) * B);
     ap.dev<char>(56 * (size_t)N * el * B);
     ap.dev<double>(16 * (size_t)N * B);
     const size_t n4 = 4 * (size_t)N, m1 = (size_t)((d.max_krylov > 0 ? d.max_krylov : 300) + 1);

@@ -36,10 +36,12 @@ __device__ inline cv3 cross_rn(const double* n, const cv3& a) {   // n x a (n re
 }
 __device__ inline c64 operator*(c64 a, double s) { return {s * a.r, s * a.i}; }
 
-template <typename T>
+// T: storage of the densities phi and weighted densities a (original order); TS: the weighted
+// densities in octree order, read by the IFGF kernels (FP32 in the mixed-precision plan).
+template <typename T, typename TS = T>
 __global__ void k_density_prep(int nc, const double* __restrict__ y, NodeGeom g,
                                const double* __restrict__ Dm, const int* __restrict__ iperm,
-                               int N, T* __restrict__ phi, T* __restrict__ a_sorted,
+                               int N, T* __restrict__ phi, TS* __restrict__ a_sorted,
                                T* __restrict__ a_orig, double* __restrict__ phi64) {
   extern __shared__ double sm[];
   const int npp = nc * nc;
@@ -99,14 +101,14 @@ __global__ void k_density_prep(int nc, const double* __restrict__ y, NodeGeom g,
     phi[16 * (size_t)l + k] = (T)vals[k];
     phi64[16 * (size_t)l + k] = vals[k];
     a_orig[16 * (size_t)l + k] = (T)(vals[k] * w);
-    a_sorted[16 * (size_t)ls + k] = (T)(vals[k] * w);
+    a_sorted[16 * (size_t)ls + k] = (TS)(vals[k] * w);
   }
 }
 
 // Raw densities given by the caller (fields entry point): convert and weight.
-template <typename T>
+template <typename T, typename TS = T>
 __global__ void k_phi_input(int N, const double* __restrict__ phi_in, const double* __restrict__ w,
-                            const int* __restrict__ iperm, T* phi, T* a_sorted, T* a_orig,
+                            const int* __restrict__ iperm, T* phi, TS* a_sorted, T* a_orig,
                             double* phi64) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 16 * N) return;
@@ -115,7 +117,7 @@ __global__ void k_phi_input(int N, const double* __restrict__ phi_in, const doub
   phi[t] = (T)v;
   phi64[t] = v;
   a_orig[t] = (T)(v * w[l]);
-  a_sorted[16 * (size_t)iperm[l] + k] = (T)(v * w[l]);
+  a_sorted[16 * (size_t)iperm[l] + k] = (TS)(v * w[l]);
 }
 
 template <typename T>
@@ -239,11 +241,15 @@ cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const dou
                                 cudaStream_t s, int nrhs) {
   const int npp = p->nc * p->nc;
   const int* iperm = p->perm + p->N;   // second half of the perm buffer holds original -> sorted
+  const int prec = p->desc.precision;
   if (phi_in) {
     int nt = 16 * p->N;
-    if (p->desc.precision == IFGF_FP64)
+    if (prec == IFGF_FP64)
       k_phi_input<double><<<(nt + 255) / 256, 256, 0, s>>>(p->N, phi_in, p->geo.w, iperm,
           (double*)p->phi, (double*)p->a_sorted, (double*)p->a_orig, p->phi64);
+    else if (prec == IFGF_MIXED)
+      k_phi_input<double, float><<<(nt + 255) / 256, 256, 0, s>>>(p->N, phi_in, p->geo.w, iperm,
+          (double*)p->phi, (float*)p->a_sorted, (double*)p->a_orig, p->phi64);
     else
       k_phi_input<float><<<(nt + 255) / 256, 256, 0, s>>>(p->N, phi_in, p->geo.w, iperm,
           (float*)p->phi, (float*)p->a_sorted, (float*)p->a_orig, p->phi64);
@@ -251,9 +257,12 @@ cudaError_t launch_density_prep(const ifgf_plan_t* p, const double* y, const dou
   }
   size_t smem = sizeof(double) * 8 * npp;
   int threads = ((npp + 31) / 32) * 32;
-  if (p->desc.precision == IFGF_FP64)
+  if (prec == IFGF_FP64)
     k_density_prep<double><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm, p->N,
         (double*)p->phi, (double*)p->a_sorted, (double*)p->a_orig, p->phi64);
+  else if (prec == IFGF_MIXED)
+    k_density_prep<double, float><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm,
+        p->N, (double*)p->phi, (float*)p->a_sorted, (double*)p->a_orig, p->phi64);
   else
     k_density_prep<float><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, y, p->geo, p->tab_D, iperm, p->N,
         (float*)p->phi, (float*)p->a_sorted, (float*)p->a_orig, p->phi64);
@@ -276,7 +285,7 @@ cudaError_t launch_combine(const ifgf_plan_t* p, const double* y, double* out, c
   int threads = ((npp + 31) / 32) * 32;
   Materials M{p->desc.k_ext, p->desc.k_int, p->desc.eps_ext, p->desc.eps_int,
               p->desc.mu_ext, p->desc.mu_int, p->omega};
-  if (p->desc.precision == IFGF_FP64)
+  if (store64(p->desc))
     k_combine<double><<<dim3(p->P, nrhs), threads, smem, s>>>(p->nc, p->N, (const double*)p->f28, y, p->geo,
                                                     p->tab_D, M, out);
   else
@@ -303,7 +312,7 @@ cudaError_t launch_block_scale(int N, int nrhs, double cm, double cj, const doub
 
 cudaError_t launch_zero_f28(const ifgf_plan_t* p, cudaStream_t s) {
   size_t n = (size_t)p->N * 56;
-  if (p->desc.precision == IFGF_FP64)
+  if (store64(p->desc))
     k_zero<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (double*)p->f28);
   else
     k_zero<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (float*)p->f28);
@@ -312,7 +321,7 @@ cudaError_t launch_zero_f28(const ifgf_plan_t* p, cudaStream_t s) {
 
 cudaError_t launch_f28_export(const ifgf_plan_t* p, double* out, cudaStream_t s) {
   size_t n = (size_t)p->N * 56;
-  if (p->desc.precision == IFGF_FP64)
+  if (store64(p->desc))
     k_export<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (const double*)p->f28, out);
   else
     k_export<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (const float*)p->f28, out);

@@ -17,6 +17,8 @@ constexpr int kFR = 2 * kF;                       // real components (re, im int
 constexpr int kNearFields = 28;                   // S_e[8], S_i[8], D_e[6], D_i[6]
 constexpr int kUpRunMax = 32;                     // parent points per upward-pass run (<= 32: one per lane)
 constexpr int kUpGroups = 4;                      // disjoint parent-point groups, one per warp of the upward block
+constexpr int kTcBoxes = 4;                       // parent slots per tensor-core upward tile (M = 4 x 32 rows)
+constexpr int kTcMaxUnits = 192;                  // most (octant, child cone) units of one parent cone on that path
 
 // Complex helpers on plain real pairs (the library keeps complex data interleaved).
 template <typename T>

@@ -634,6 +634,87 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
         for (int64_t ci = c0; ci < c1; ++ci)
           std::copy(ci_tasks[ci].begin(), ci_tasks[ci].end(), Pp.up_task.begin() + Pp.up_task_ptr[ci * kUpGroups]);
       });
+      // Tensor-core tables: per (parent cone, octant) the points ranked by (child cone, point)
+      // and cut into units of at most kUpRunMax points of one child cone (points whose child
+      // cone no child box holds are left out: their octant has no child in any box of this
+      // cone); per parent cone its units in octant order.
+      Pp.tc_order.assign((size_t)ncomp_p * 8 * kQ, 0);
+      std::vector<std::vector<int32_t>> ci_units(ncomp_p);
+      parallel_for(ncomp_p, [&](int64_t c0, int64_t c1) {
+        for (int64_t ci = c0; ci < c1; ++ci) {
+          std::vector<int32_t>& out = ci_units[ci];
+          out.clear();
+          for (int o = 0; o < 8; ++o) {
+            const size_t g = (size_t)ci * 8 + o;
+            const int32_t* cc = &Pp.up_cc[g * kQ];
+            int32_t* ord = &Pp.tc_order[g * kQ];
+            int64_t key[kQ];
+            for (int q = 0; q < kQ; ++q) key[q] = ((int64_t)(cc[q] + 1) << 8) | q;
+            std::sort(key, key + kQ);
+            for (int q = 0; q < kQ; ++q) ord[q] = (int32_t)(key[q] & 255);
+            int r = 0;
+            while (r < kQ) {
+              int len = 1;
+              while (len < kUpRunMax && r + len < kQ && cc[ord[r + len]] == cc[ord[r]]) ++len;
+              if (cc[ord[r]] >= 0) out.push_back(r | (len << 8) | (o << 16));
+              r += len;
+            }
+          }
+        }
+      });
+      Pp.tc_unit_ptr.assign((size_t)ncomp_p + 1, 0);
+      Pp.tc_max_units = 0;
+      for (int64_t ci = 0; ci < ncomp_p; ++ci) {
+        Pp.tc_unit_ptr[ci + 1] = Pp.tc_unit_ptr[ci] + (int32_t)ci_units[ci].size();
+        Pp.tc_max_units = std::max(Pp.tc_max_units, (int)ci_units[ci].size());
+      }
+      Pp.tc_unit.resize(Pp.tc_unit_ptr.back());
+      for (int64_t ci = 0; ci < ncomp_p; ++ci)
+        std::copy(ci_units[ci].begin(), ci_units[ci].end(), Pp.tc_unit.begin() + Pp.tc_unit_ptr[ci]);
+      // slots of one parent cone in groups of kTcBoxes, slots with equal child sets together
+      // (rows of an absent child are computed but not used)
+      {
+        const size_t ns_p = Pp.slot_box.size();
+        std::vector<int64_t> key(ns_p);
+        for (size_t sl = 0; sl < ns_p; ++sl) {
+          int mask = 0;
+          for (int o = 0; o < 8; ++o) mask |= (Pp.child[Pp.slot_box[sl]][o] >= 0) << o;
+          key[sl] = ((int64_t)Pp.slot_upidx[sl] << 40) | ((int64_t)mask << 32) | (int64_t)sl;
+        }
+        std::sort(key.begin(), key.end());
+        Pp.tc_item.clear();
+        size_t a = 0;
+        while (a < ns_p) {
+          const int64_t ci = key[a] >> 40;
+          size_t b = a;
+          while (b < ns_p && (key[b] >> 40) == ci) ++b;
+          for (size_t c = a; c < b; c += kTcBoxes)
+            for (int j = 0; j < kTcBoxes; ++j)
+              Pp.tc_item.push_back(c + j < b ? (int32_t)(key[c + j] & 0xffffffff) : -1);
+          a = b;
+        }
+      }
+    }
+    // chunks of at most 32 consecutive targets of one box (boxes with cousins): the unit of the
+    // FP32 target step, whose targets share their cousin boxes
+    // (listed longest first: work n x cousins, so that the last wave holds the short ones)
+    L.tgt_chunk.clear();
+    {
+      std::vector<std::array<int64_t, 3>> ch;   // (work, first target, count)
+      for (int A = 0; A < nb; ++A) {
+        if (L.cousin[A].empty()) continue;
+        for (int s0 = L.pt_begin[A]; s0 < L.pt_end[A]; s0 += 32) {
+          const int n = std::min(32, L.pt_end[A] - s0);
+          ch.push_back({(int64_t)n * (int64_t)L.cousin[A].size(), s0, n});
+        }
+      }
+      std::stable_sort(ch.begin(), ch.end(), [](const std::array<int64_t, 3>& a, const std::array<int64_t, 3>& b) {
+        return a[0] > b[0];
+      });
+      for (const auto& c : ch) {
+        L.tgt_chunk.push_back((int32_t)c[1]);
+        L.tgt_chunk.push_back((int32_t)c[2]);
+      }
     }
     // per-target slots: each record (s, j) of (1), found in the sorted cones of box cousin[A][j]
     L.tgt_ptr = ptr;

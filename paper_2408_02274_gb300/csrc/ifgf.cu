@@ -543,8 +543,381 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32);
 }
 
+// ------------------------------------------------------------------ (b) on the tensor cores
+// The upward step as dense contractions on the 5th-generation tensor cores (tcgen05, kind::tf32,
+// FP32 accumulation in tensor memory).  A block takes kTcBoxes parent slots of one parent cone
+// (their parent points, child cones and re-centring factors are box-independent) and sweeps the
+// cone's units: the points of one octant that fall in one child cone (at most 32).  Per unit
+//   D[(box, field) x point] = C^T[(box, field) x k] . B[k x point],  M = 128, N = 32, K = 80,
+// with C the child cone's 75 x 32 coefficients (A operand) and B the Chebyshev basis
+// T_i(s) T_j(theta) T_k(phi) of the unit's points, both K-major without swizzle (8-row x 16-byte
+// core matrices), K padded from 75 to 80 with zeros.  FP32 accuracy comes from
+// a three-term split x = hi + lo (hi = x with the 13 low mantissa bits cleared, exactly the
+// TF32 operand): D = A_hi B_hi + A_hi B_lo + A_lo B_hi.  The epilogue re-centres each column
+// (complex factor of the point) and adds it into the parent values in shared memory; the
+// values -> coefficients map runs once per parent slot at the end.
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+// shared-memory matrix descriptor: start address, leading / stride byte offsets, layout
+// (0: no swizzle, 2: 128-byte swizzle), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7) << 61);
+}
+// instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ float hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
+__device__ __forceinline__ void mma(uint32_t td, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(td),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// wait for phase `parity` of an mbarrier, giving up after `limit` polls; true when it completed
+__device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, int limit) {
+  uint32_t done = 0;
+  for (int it = 0; it < limit && !done; ++it)
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return done != 0;
+}
+constexpr int kK = 80;                          // K: 75 Chebyshev terms padded to a multiple of 8
+constexpr int kN = 32;                          // N: points of a unit
+constexpr int kThreads = 256;                   // 8 warps; warps w and w + 4 share box w % 4 in the epilogue
+constexpr int kABytes = kTcBoxes * 32 * kK * 4;   // 40960: 128 rows (box, field) x 80
+constexpr int kBBytes = kN * kK * 4;            // 10240
+// shared memory: A hi / lo, B hi / lo in two buffers, parent values, per-cone tables
+constexpr int kOffAlo = kABytes, kOffB = 2 * kABytes;                    // B buffer i: hi at kOffB + 2 i kBBytes
+constexpr int kOffVals = kOffB + 4 * kBBytes;                            // [kTcBoxes][75][kVS] floats
+constexpr int kOffCheb = kOffVals + kTcBoxes * kQ * kVS * 4;             // [8][75] UpCheb
+constexpr int kOffFac = kOffCheb + 8 * kQ * (int)sizeof(UpCheb);         // [8][75] float4
+constexpr int kOffXp = kOffFac + 8 * kQ * 16;                            // [75][3] floats
+constexpr int kOffCs = kOffXp + kQ * 3 * 4;                              // [kTcBoxes][kTcMaxUnits] child slots
+constexpr int kOffUnit = kOffCs + kTcBoxes * kTcMaxUnits * 4;            // [kTcMaxUnits] unit records
+constexpr int kOffOrder = kOffUnit + kTcMaxUnits * 4;                    // [8][75] points by child cone
+constexpr int kSmem = kOffOrder + 8 * kQ * 4 + 1024;                     // + alignment to 1024 bytes
+constexpr int kWaitLimit = 1 << 24;             // polls before a wait is reported as timed out
+
+// Row m (A: m = box * 32 + field; B: m = point), 16-byte chunk kc (k = 4 kc .. 4 kc + 3) of a
+// K-major operand without swizzle: 8-row x 16-byte core matrices, the 20 chunks of one 8-row
+// group 128 bytes apart (leading byte offset), 8-row groups 2560 bytes apart (stride byte offset)
+__device__ __forceinline__ int kmaj_off(int m, int kc) { return (m >> 3) * 2560 + kc * 128 + ((m & 7) << 4); }
+
+}  // namespace tc
+
+// Basis values T_i(s) T_j(theta) T_k(phi) (k-index (i*5 + j)*5 + k) of one point for the K-indices
+// 4 KC .. 4 KC + 3, as TF32 hi and lo parts into the B operand's 16-byte chunk KC (index 75 is
+// zero; chunk 19 stays zero from the initial clear).
+template <int KC>
+__device__ __forceinline__ void tc_basis(const float* TS, const float* TT, const float* TP, unsigned char* Bhi,
+                                         unsigned char* Blo, int n) {
+  float v[4], h[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = 4 * KC + j;
+    v[j] = k < kQ ? TS[k / 25] * TT[(k / 5) % 5] * TP[k % 5] : 0.f;
+    h[j] = tc::hi(v[j]);
+  }
+  const int off = tc::kmaj_off(n, KC);
+  *reinterpret_cast<float4*>(Bhi + off) = make_float4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<float4*>(Blo + off) = make_float4(v[0] - h[0], v[1] - h[1], v[2] - h[2], v[3] - h[3]);
+}
+
+// The basis chunks of point n written by warp w: chunks w, w + 8 and (w < 3) w + 16.
+__device__ __forceinline__ void tc_basis_warp(int w, const UpCheb& C, unsigned char* Bhi, unsigned char* Blo, int n) {
+  const float TS[3] = {1.f, C.ts[0], C.ts[1]};
+  const float TT[5] = {1.f, C.tt[0], C.tt[1], C.tt[2], C.tt[3]};
+  const float TP[5] = {1.f, C.tp[0], C.tp[1], C.tp[2], C.tp[3]};
+  switch (w) {
+    case 0: tc_basis<0>(TS, TT, TP, Bhi, Blo, n); tc_basis<8>(TS, TT, TP, Bhi, Blo, n);
+            tc_basis<16>(TS, TT, TP, Bhi, Blo, n); break;
+    case 1: tc_basis<1>(TS, TT, TP, Bhi, Blo, n); tc_basis<9>(TS, TT, TP, Bhi, Blo, n);
+            tc_basis<17>(TS, TT, TP, Bhi, Blo, n); break;
+    case 2: tc_basis<2>(TS, TT, TP, Bhi, Blo, n); tc_basis<10>(TS, TT, TP, Bhi, Blo, n);
+            tc_basis<18>(TS, TT, TP, Bhi, Blo, n); break;
+    case 3: tc_basis<3>(TS, TT, TP, Bhi, Blo, n); tc_basis<11>(TS, TT, TP, Bhi, Blo, n); break;
+    case 4: tc_basis<4>(TS, TT, TP, Bhi, Blo, n); tc_basis<12>(TS, TT, TP, Bhi, Blo, n); break;
+    case 5: tc_basis<5>(TS, TT, TP, Bhi, Blo, n); tc_basis<13>(TS, TT, TP, Bhi, Blo, n); break;
+    case 6: tc_basis<6>(TS, TT, TP, Bhi, Blo, n); tc_basis<14>(TS, TT, TP, Bhi, Blo, n); break;
+    default: tc_basis<7>(TS, TT, TP, Bhi, Blo, n); tc_basis<15>(TS, TT, TP, Bhi, Blo, n); break;
+  }
+}
+
+struct TcTabs {
+  const int* order;      // [ncompact][8][75] points ranked by child cone
+  const int* unit;       // units per compact cone: start | len << 8 | octant << 16
+  const int* unit_ptr;   // [ncompact + 1]
+  const int* item;       // [nitems][kTcBoxes] parent slots (-1 padded)
+  int* err;              // device status word: bit 0 set when a wait on the tensor cores timed out
+};
+
+// Software pipeline per unit u (one thread issues the MMAs):
+//   wait MMA(u-1) -> A(u) into shared memory, prefetch A(u+1) -> barrier -> issue MMA(u) into
+//   accumulator u % 2 -> epilogue of unit u-1 from accumulator (u-1) % 2 and basis B(u+1) into
+//   buffer (u+1) % 2, both while MMA(u) runs.
+__global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTabs TT) {
+  using T = float;
+  __shared__ SmallMaps<T> M;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  extern __shared__ unsigned char tc_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* Ahi = sm;
+  unsigned char* Alo = sm + tc::kOffAlo;
+  T* vals = reinterpret_cast<T*>(sm + tc::kOffVals);
+  UpCheb (*cheb)[kQ] = reinterpret_cast<UpCheb (*)[kQ]>(sm + tc::kOffCheb);
+  float4 (*fac)[kQ] = reinterpret_cast<float4 (*)[kQ]>(sm + tc::kOffFac);
+  T (*Xp)[3] = reinterpret_cast<T (*)[3]>(sm + tc::kOffXp);
+  int (*cs)[kTcMaxUnits] = reinterpret_cast<int (*)[kTcMaxUnits]>(sm + tc::kOffCs);
+  int* units = reinterpret_cast<int*>(sm + tc::kOffUnit);
+  int (*order)[kQ] = reinterpret_cast<int (*)[kQ]>(sm + tc::kOffOrder);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
+  A.coefs_p += blockIdx.y * A.cstride_p;
+  int slot[kTcBoxes], Pb[kTcBoxes];
+#pragma unroll
+  for (int b = 0; b < kTcBoxes; ++b) {
+    slot[b] = __ldg(TT.item + (size_t)blockIdx.x * kTcBoxes + b);
+    Pb[b] = slot[b] >= 0 ? __ldg(A.slot_box + slot[b]) : -1;
+  }
+  const int ci = A.slot_upidx[slot[0]];   // every item holds at least one slot, first
+  const cone_key pcone = A.slot_cone[slot[0]];
+  const int u0 = __ldg(TT.unit_ptr + ci);
+  int nunits = __ldg(TT.unit_ptr + ci + 1) - u0;
+  init_maps(M);
+  // clear operands (padding rows and columns must hold zeros) and values
+  for (int e = t; e < tc::kOffCheb / 16; e += blockDim.x) reinterpret_cast<float4*>(sm)[e] = make_float4(0, 0, 0, 0);
+  for (int e = t; e < nunits; e += blockDim.x) units[e] = __ldg(TT.unit + u0 + e);
+  for (int e = t; e < 8 * kQ; e += blockDim.x) order[e / kQ][e % kQ] = __ldg(TT.order + (size_t)ci * 8 * kQ + e);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc::smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t td = tmem_base;
+  if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
+  // child slot of every (box, unit): -1 where the box has no child in the unit's octant
+  for (int e = t; e < kTcBoxes * nunits; e += blockDim.x) {
+    const int b = e / nunits, u = e - b * nunits;
+    const int tk = units[u], o = (tk >> 16) & 7;
+    const size_t g = (size_t)ci * 8 + o;
+    const int q0 = order[o][tk & 255];
+    const int cb = Pb[b] >= 0 ? __ldg(A.child + 8 * Pb[b] + o) : -1;
+    cs[b][u] = cb >= 0 ? __ldg(A.cmap_c + (size_t)cb * A.ncomp_c + __ldg(A.up_cc + g * kQ + q0)) : -1;
+  }
+  __syncthreads();
+  // keep the units in which some box of the item has a child (in place, order kept: one warp
+  // reads a group of 32 units, then writes them to positions at or below the group's start)
+  __shared__ int nact_s;
+  if (warp == 0) {
+    int nact = 0;
+    for (int u0g = 0; u0g < nunits; u0g += 32) {
+      const int u = u0g + lane;
+      int tk = 0, c[kTcBoxes];
+      bool any = false;
+      if (u < nunits) {
+        tk = units[u];
+#pragma unroll
+        for (int b = 0; b < kTcBoxes; ++b) {
+          c[b] = cs[b][u];
+          any = any || c[b] >= 0;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, any);
+      __syncwarp();
+      if (any) {
+        const int pos = nact + __popc(m & ((1u << lane) - 1u));
+        units[pos] = tk;
+#pragma unroll
+        for (int b = 0; b < kTcBoxes; ++b) cs[b][pos] = c[b];
+      }
+      nact += __popc(m);
+      __syncwarp();
+    }
+    if (lane == 0) nact_s = nact;
+  }
+  __syncthreads();
+  nunits = nact_s;
+  // per (octant, parent point): Chebyshev values in the child cone and the re-centring factor
+  // (box-independent; octants without a child in any box of this cone are not used)
+  const T off = (T)(0.5 * A.Hc);
+  const T kk[2] = {A.ke, A.ki};
+  for (int e = t; e < 8 * kQ; e += blockDim.x) {
+    const int o = e / kQ, q = e % kQ;
+    const int ccx = __ldg(A.up_cc + ((size_t)ci * 8 + o) * kQ + q);
+    if (ccx < 0) continue;
+    const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
+    const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
+    T ts, tt, tp, rc, sth, cth, sph, cph;
+    local_coords(A.cgc, A.ckeys_c[ccx], x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
+    T v5[5], v3[3];
+    UpCheb& C = cheb[o][q];
+    cheb_vals<T, 5>(tp, v5);
+    C.tp[0] = v5[1]; C.tp[1] = v5[2]; C.tp[2] = v5[3]; C.tp[3] = v5[4];
+    cheb_vals<T, 5>(tt, v5);
+    C.tt[0] = v5[1]; C.tt[1] = v5[2]; C.tt[2] = v5[3]; C.tt[3] = v5[4];
+    cheb_vals<T, 3>(ts, v3);
+    C.ts[0] = v3[1]; C.ts[1] = v3[2];
+    const T rp = sqrt_t(Xp[q][0] * Xp[q][0] + Xp[q][1] * Xp[q][1] + Xp[q][2] * Xp[q][2]);
+    const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
+    T sn0, cs0, sn1, cs1;
+    sincos_t(kk[0] * dr, &sn0, &cs0);
+    sincos_t(kk[1] * dr, &sn1, &cs1);
+    const T a = rp / rc;
+    fac[o][q] = make_float4(a * cs0, a * sn0, a * cs1, a * sn1);
+  }
+  // A operand of one unit, prefetched into registers: task (box b, chunk kc, field = lane) is the
+  // four coefficients k = 4 kc .. 4 kc + 3 of one field (coalesced 128-byte coefficient rows)
+  constexpr int kChunks = (kQ + 3) / 4;                                    // 19 (k = 75 is padding)
+  constexpr int kTasks = kTcBoxes * kChunks;                               // 76 per warp round
+  constexpr int kAPer = (kTasks + tc::kThreads / 32 - 1) / (tc::kThreads / 32);   // 10
+  float pre[kAPer][4];
+  auto load_a = [&](int u) {
+#pragma unroll
+    for (int i = 0; i < kAPer; ++i) {
+      const int bk = warp + 8 * i;
+      const int b = bk / kChunks, kc = bk - b * kChunks;
+      const int sl = bk < kTasks ? cs[b][u] : -1;
+      const T* C = A.coefs_c + (size_t)(sl >= 0 ? sl : 0) * kQ * 32 + lane;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = 4 * kc + j;
+        pre[i][j] = (sl >= 0 && k < kQ) ? __ldg(C + k * 32) : 0.f;
+      }
+    }
+  };
+  auto store_a = [&]() {
+#pragma unroll
+    for (int i = 0; i < kAPer; ++i) {
+      const int bk = warp + 8 * i;
+      if (bk < kTasks) {
+        const int b = bk / kChunks, kc = bk - b * kChunks;
+        float h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          h[j] = tc::hi(pre[i][j]);
+          l[j] = pre[i][j] - h[j];
+        }
+        const int ao = tc::kmaj_off(32 * b + lane, kc);
+        *reinterpret_cast<float4*>(Ahi + ao) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(Alo + ao) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+    }
+  };
+  auto build_b = [&](int u) {   // lane = point of unit u, warp = range of K chunks
+    const int tk = units[u], len = (tk >> 8) & 255, o = (tk >> 16) & 7;
+    if (lane < len) {
+      unsigned char* Bb = sm + tc::kOffB + (u & 1) * 2 * tc::kBBytes;
+      tc_basis_warp(warp, cheb[o][order[o][(tk & 255) + lane]], Bb, Bb + tc::kBBytes, lane);
+    }
+  };
+  const float sgn = (lane & 1) ? 1.f : -1.f;
+  const int ks = lane >> 4, eb = warp & 3, eh = warp >> 2;   // epilogue: box eb, points 16 eh .. 16 eh + 15
+  auto epilogue = [&](int u) {
+    const int tk = units[u], len = (tk >> 8) & 255, o = (tk >> 16) & 7, st = tk & 255;
+    if (slot[eb] < 0 || cs[eb][u] < 0 || 16 * eh >= len) return;   // warp-uniform
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(td + ((uint32_t)(32 * eb) << 16) + (uint32_t)((u & 1) * tc::kN + 16 * eh)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    T* vb = vals + eb * kQ * kVS;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (16 * eh + j < len) {
+        const int q = order[o][st + 16 * eh + j];
+        const T v = __uint_as_float(r[j]);
+        const T w = __shfl_xor_sync(0xffffffffu, v, 1);
+        const float4 F = fac[o][q];
+        const T fr = ks ? F.z : F.x, fi = ks ? F.w : F.y;
+        vb[q * kVS + lane] += fmaf(v, fr, sgn * fi * w);
+      }
+    }
+  };
+  __syncthreads();
+  if (nunits > 0) {
+    load_a(0);
+    build_b(0);
+  }
+  bool ok = true;
+  for (int u = 0; u < nunits; ++u) {
+    if (u > 0) {   // MMA(u-1) done: A free, accumulator (u-1) % 2 ready
+      ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((u - 1) & 1), tc::kWaitLimit)) != 0;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    store_a();
+    if (u + 1 < nunits) load_a(u + 1);   // in flight during this unit's MMA and the work beside it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (t == 0) {
+      const uint32_t id = tc::idesc(128, tc::kN);
+      const uint32_t aH = tc::smem_u32(Ahi), aL = tc::smem_u32(Alo);
+      const uint32_t bH = tc::smem_u32(sm + tc::kOffB + (u & 1) * 2 * tc::kBBytes), bL = bH + tc::kBBytes;
+      const uint32_t dcol = td + (uint32_t)((u & 1) * tc::kN);
+#pragma unroll 1
+      for (int pass = 0; pass < 3; ++pass) {
+        const uint32_t ab = pass == 2 ? aL : aH, bb = pass == 1 ? bL : bH;
+#pragma unroll
+        for (int k8 = 0; k8 < tc::kK / 8; ++k8)
+          tc::mma(dcol, tc::sdesc(ab + k8 * 256, 128, 2560, 0), tc::sdesc(bb + k8 * 256, 128, 2560, 0), id,
+                  (pass | k8) ? 1u : 0u);
+      }
+      tc::commit(&mbar);
+    }
+    if (u > 0) epilogue(u - 1);
+    if (u + 1 < nunits) build_b(u + 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  if (ok && nunits > 0) {
+    ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((nunits - 1) & 1), tc::kWaitLimit)) != 0;
+    if (ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      epilogue(nunits - 1);
+    }
+  }
+  if (!ok) {
+    // a wait timed out: record it, give the tensor cores a bounded second wait, release and leave
+    if (t == 0) atomicOr(TT.err, 1);
+    tc::wait(&mbar, 0u, tc::kWaitLimit);
+    tc::wait(&mbar, 1u, tc::kWaitLimit);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(td) : "memory");
+  if (!ok) return;
+  // values -> coefficients of every slot of the item
+#pragma unroll 1
+  for (int b = 0; b < kTcBoxes; ++b) {
+    if (slot[b] < 0) break;   // slots fill the item from the front
+    vals_to_coefs_block<T, kVS>(M, vals + b * kQ * kVS, A.coefs_p + (size_t)slot[b] * kQ * 32);
+  }
+}
+
 // ------------------------------------------------------------------ (c) target evaluation
-template <typename T>
+// T: arithmetic and coefficient type; TO: the fields' storage (FP64 in the mixed-precision plan)
+template <typename T, typename TO = T>
 struct TgtArgs {
   int N;
   const int64_t* tgt_ptr;
@@ -557,10 +930,46 @@ struct TgtArgs {
   const double* x_sorted;
   const double* n_sorted;
   const int* perm;
-  T* f28;
+  TO* f28;
   T ke, ki;
   size_t cstride;   // cone coefficients per right-hand side (fields: 56 N)
+  // FP64 geometry of the level for the FP32 kernel's target coordinates and centre phases
+  double h64, ids64, ke64, ki64;
+  const double2* th0;   // [na] (cos, sin) of the theta cells' lower edges g2 * pi / na
+  const double2* ph0;   // [2 na] (cos, sin) of the phi cells' lower edges g3 * pi / na
 };
+
+// Target coordinates of the FP32 target step.  The target's local coordinates in its cone and
+// the centre phases k |x - x_c| feed every interpolated value; rounded in FP32 they would carry
+// ~1e-6 (local coordinates on fine cones, through a full-angle atan2) and ~k r 1e-7 (phases, k r
+// up to ~1e2) of independent noise per target, which the N-Mueller combination's surface
+// derivatives amplify.  So x - x_c, r, s = h / r and the phases are formed in FP64 (the phase
+// reduced to [-pi, pi] before the FP32 sincos), and each angle is measured from its cell's lower
+// edge by rotating the FP64 components (FP32 atan2 then resolves a small angle).
+__device__ inline void target_coords(double h64, double ids64, float idth, const double2* th0, const double2* ph0,
+                                     cone_key cone, double dx, double dy, double dz, double ke, double ki,
+                                     float* ts, float* tt, float* tp, float* r, float* sth, float* cth, float* sph,
+                                     float* cph, float* phase) {
+  int g1, g2, g3;
+  cone_decode(cone, &g1, &g2, &g3);
+  const double rho2 = dx * dx + dy * dy;
+  const double rho = sqrt(rho2), r64 = sqrt(rho2 + dz * dz);
+  const double ir = 1.0 / r64;
+  *ts = (float)(2.0 * (h64 * ir * ids64 - (double)g1) - 1.0);
+  const double2 t0 = th0[g2], p0 = ph0[g3];
+  *tt = 2.f * atan2f((float)(rho * t0.x - dz * t0.y), (float)(dz * t0.x + rho * t0.y)) * idth - 1.f;
+  *tp = 2.f * atan2f((float)(dy * p0.x - dx * p0.y), (float)(dx * p0.x + dy * p0.y)) * idth - 1.f;
+  *r = (float)r64;
+  *sth = (float)(rho * ir);
+  *cth = (float)(dz * ir);
+  const double irho = rho > 0.0 ? 1.0 / rho : 0.0;
+  *cph = rho > 0.0 ? (float)(dx * irho) : 1.f;
+  *sph = rho > 0.0 ? (float)(dy * irho) : 0.f;
+  constexpr double kInv2Pi = 1.0 / (2.0 * kPi);
+  const double a = ke * r64, b = ki * r64;
+  phase[0] = (float)fma(-2.0 * kPi, rint(a * kInv2Pi), a);
+  phase[1] = (float)fma(-2.0 * kPi, rint(b * kInv2Pi), b);
+}
 
 // Per (target, cone) scalars, computed one cone per lane and read back by the
 // whole warp: Chebyshev values and derivatives in (s, theta, phi), the
@@ -576,8 +985,107 @@ struct TgtScal {
 template <typename T>
 __host__ __device__ constexpr int tgt_warps() { return sizeof(T) == 4 ? 8 : 4; }   // keeps the scalars under 48 KB
 
+// Per (target, cone segment) scalars: Chebyshev values and derivatives of the target's local
+// coordinates, the directional-derivative weights of n . grad and the centred factors.
+template <typename T, typename TO>
+__device__ inline void tgt_scalars(const TgtArgs<T, TO>& A, double x0, double x1, double x2, T n0, T n1, T n2,
+                                   int slot, TgtScal<T>& Q) {
+  const T two_ids = T(2) * A.cg.ids, two_idth = T(2) * A.cg.idth, h = A.cg.h;
+  const int box = A.slot_box[slot];
+  const cone_key cone = A.slot_cone[slot];
+  const double dx = x0 - A.box_center[3 * box], dy = x1 - A.box_center[3 * box + 1], dz = x2 - A.box_center[3 * box + 2];
+  const T xr = (T)dx, yr = (T)dy, zr = (T)dz;
+  T ts, tt, tp, r, sth, cth, sph, cph, phase[2];
+  if constexpr (std::is_same<T, float>::value) {
+    target_coords(A.h64, A.ids64, A.cg.idth, A.th0, A.ph0, cone, dx, dy, dz, A.ke64, A.ki64, &ts, &tt, &tp, &r, &sth,
+                  &cth, &sph, &cph, phase);
+  } else {
+    local_coords(A.cg, cone, xr, yr, zr, &ts, &tt, &tp, &r, &sth, &cth, &sph, &cph);
+    phase[0] = A.ke * r;
+    phase[1] = A.ki * r;
+  }
+  cheb_vals<T, 3>(ts, Q.Ts);
+  cheb_vals<T, 5>(tt, Q.Tt);
+  cheb_vals<T, 5>(tp, Q.Tp);
+  cheb_dvals<T, 3>(ts, Q.dTs);
+  cheb_dvals<T, 5>(tt, Q.dTt);
+  cheb_dvals<T, 5>(tp, Q.dTp);
+  // n . grad of (s, theta, phi): grad s = -(h/r^2) r_hat, grad theta = theta_hat / r,
+  // grad phi = phi_hat / (r sin theta)   (analytic derivative of the interpolant, reading R1)
+  const T ir = T(1) / r;
+  const T nr = (n0 * xr + n1 * yr + n2 * zr) * ir;
+  const T nth = n0 * cth * cph + n1 * cth * sph - n2 * sth;
+  const T nph = -n0 * sph + n1 * cph;
+  Q.as = -(h * ir * ir) * nr * two_ids;
+  Q.at = nth * ir * two_idth;
+  const T sthg = sth > T(1e-7) ? sth : T(1e-7);
+  Q.ap = nph * ir / sthg * two_idth;
+  // centred factor G = e^{i k r}/(4 pi r) and its normal derivative (n.r_hat)(i k - 1/r) G
+  const T g = T(1.0 / (4.0 * kPi)) * ir;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const T kap = kk ? A.ki : A.ke;
+    T sn, cs;
+    sincos_t(phase[kk], &sn, &cs);
+    const T Gr = g * cs, Gi = g * sn;
+    Q.G[kk][0] = Gr;
+    Q.G[kk][1] = Gi;
+    Q.G[kk][2] = nr * (-ir * Gr - kap * Gi);
+    Q.G[kk][3] = nr * (-ir * Gi + kap * Gr);
+  }
+  Q.slot = slot;
+}
+
+// The interpolated field of this lane's real column (of 32) and its normal derivative at one
+// (target, cone) pair, times the centred factor: the S part (every lane) and the D part (lanes
+// of densities 0..5).  cc: the cone's 75 coefficients of this lane's column.
 template <typename T>
-__global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T> A) {
+__device__ __forceinline__ void tgt_contract(const TgtScal<T>& Q, const T* cc, int lane, T& outS, T& outD) {
+  // separable contraction: the phi sums with T and T' are shared by F and its three
+  // partial derivatives, dF = a_s F_s + a_theta F_theta + a_phi F_phi
+  T Tp[5], dTp[5], Tt[5], dTt[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    Tp[k] = Q.Tp[k]; dTp[k] = Q.dTp[k]; Tt[k] = Q.Tt[k]; dTt[k] = Q.dTt[k];
+  }
+  T Fs[3], Ft[3], Fp[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Fs[i] = Ft[i] = Fp[i] = T(0);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const T* c = cc + (i * 5 + j) * 5;
+      T d = Tp[0] * c[0], e = dTp[0] * c[0];
+#pragma unroll
+      for (int k = 1; k < 5; ++k) {
+        d += Tp[k] * c[k];
+        e += dTp[k] * c[k];
+      }
+      Fs[i] += Tt[j] * d;    // -> F and dF/d(ts)
+      Ft[i] += dTt[j] * d;   // -> dF/d(tt)
+      Fp[i] += Tt[j] * e;    // -> dF/d(tp)
+    }
+  }
+  const T F = Q.Ts[0] * Fs[0] + Q.Ts[1] * Fs[1] + Q.Ts[2] * Fs[2];
+  const T dF = Q.as * (Q.dTs[0] * Fs[0] + Q.dTs[1] * Fs[1] + Q.dTs[2] * Fs[2]) +
+               Q.at * (Q.Ts[0] * Ft[0] + Q.Ts[1] * Ft[1] + Q.Ts[2] * Ft[2]) +
+               Q.ap * (Q.Ts[0] * Fp[0] + Q.Ts[1] * Fp[1] + Q.Ts[2] * Fp[2]);
+  const int ks = lane >> 4;
+  const T Gr = Q.G[ks][0], Gi = Q.G[ks][1], dGr = Q.G[ks][2], dGi = Q.G[ks][3];
+  const T Fw = __shfl_xor_sync(0xffffffffu, F, 1);
+  const T dFw = __shfl_xor_sync(0xffffffffu, dF, 1);
+  const bool odd = lane & 1;
+  const T Fr = odd ? Fw : F, Fi = odd ? F : Fw;
+  const T dFr = odd ? dFw : dF, dFi = odd ? dF : dFw;
+  outS = odd ? (Gr * Fi + Gi * Fr) : (Gr * Fr - Gi * Fi);
+  const T Dr = dGr * Fr - dGi * Fi + Gr * dFr - Gi * dFi;
+  const T Di = dGr * Fi + dGi * Fr + Gr * dFi + Gi * dFr;
+  outD = odd ? Di : Dr;
+}
+
+// (c), warp per target: the target's pairs in groups of 32, scalars one per lane.
+template <typename T, typename TO>
+__global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T, TO> A) {
   __shared__ TgtScal<T> sc[tgt_warps<T>()][32];
   const int warp = threadIdx.x >> 5;
   const int t = blockIdx.x * tgt_warps<T>() + warp;
@@ -590,109 +1098,104 @@ __global__ void __launch_bounds__(32 * tgt_warps<T>(), 2) k_target(TgtArgs<T> A)
   const double x0 = A.x_sorted[3 * (size_t)t], x1 = A.x_sorted[3 * (size_t)t + 1], x2 = A.x_sorted[3 * (size_t)t + 2];
   const T n0 = (T)A.n_sorted[3 * (size_t)t], n1 = (T)A.n_sorted[3 * (size_t)t + 1], n2 = (T)A.n_sorted[3 * (size_t)t + 2];
   const int ks = lane >> 4;
-  const T two_ids = T(2) * A.cg.ids, two_idth = T(2) * A.cg.idth, h = A.cg.h;
   TgtScal<T>* S = sc[warp];
   T accS = 0, accD = 0;
   for (int64_t c0 = e0; c0 < e1; c0 += 32) {
     const int nc = (int)min((int64_t)32, e1 - c0);
-    if (lane < nc) {
-      TgtScal<T>& Q = S[lane];
-      const int slot = A.tgt_slot[c0 + lane];
-      const int box = A.slot_box[slot];
-      const cone_key cone = A.slot_cone[slot];
-      const T xr = (T)(x0 - A.box_center[3 * box]);
-      const T yr = (T)(x1 - A.box_center[3 * box + 1]);
-      const T zr = (T)(x2 - A.box_center[3 * box + 2]);
-      T ts, tt, tp, r, sth, cth, sph, cph;
-      local_coords(A.cg, cone, xr, yr, zr, &ts, &tt, &tp, &r, &sth, &cth, &sph, &cph);
-      cheb_vals<T, 3>(ts, Q.Ts);
-      cheb_vals<T, 5>(tt, Q.Tt);
-      cheb_vals<T, 5>(tp, Q.Tp);
-      cheb_dvals<T, 3>(ts, Q.dTs);
-      cheb_dvals<T, 5>(tt, Q.dTt);
-      cheb_dvals<T, 5>(tp, Q.dTp);
-      // n . grad of (s, theta, phi): grad s = -(h/r^2) r_hat, grad theta = theta_hat / r,
-      // grad phi = phi_hat / (r sin theta)   (analytic derivative of the interpolant, reading R1)
-      const T ir = T(1) / r;
-      const T nr = (n0 * xr + n1 * yr + n2 * zr) * ir;
-      const T nth = n0 * cth * cph + n1 * cth * sph - n2 * sth;
-      const T nph = -n0 * sph + n1 * cph;
-      Q.as = -(h * ir * ir) * nr * two_ids;
-      Q.at = nth * ir * two_idth;
-      const T sthg = sth > T(1e-7) ? sth : T(1e-7);
-      Q.ap = nph * ir / sthg * two_idth;
-      // centred factor G = e^{i k r}/(4 pi r) and its normal derivative (n.r_hat)(i k - 1/r) G
-      const T g = T(1.0 / (4.0 * kPi)) * ir;
-#pragma unroll
-      for (int kk = 0; kk < 2; ++kk) {
-        const T kap = kk ? A.ki : A.ke;
-        T sn, cs;
-        sincos_t(kap * r, &sn, &cs);
-        const T Gr = g * cs, Gi = g * sn;
-        Q.G[kk][0] = Gr;
-        Q.G[kk][1] = Gi;
-        Q.G[kk][2] = nr * (-ir * Gr - kap * Gi);
-        Q.G[kk][3] = nr * (-ir * Gi + kap * Gr);
-      }
-      Q.slot = slot;
-    }
+    if (lane < nc) tgt_scalars(A, x0, x1, x2, n0, n1, n2, A.tgt_slot[c0 + lane], S[lane]);
     __syncwarp();
     for (int cI = 0; cI < nc; ++cI) {
       const TgtScal<T>& Q = S[cI];
       const T* C = A.coefs + (size_t)Q.slot * kQ * 32 + lane;
-      // separable contraction: the phi sums with T and T' are shared by F and its three
-      // partial derivatives, dF = a_s F_s + a_theta F_theta + a_phi F_phi
-      T Tp[5], dTp[5], Tt[5], dTt[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        Tp[k] = Q.Tp[k]; dTp[k] = Q.dTp[k]; Tt[k] = Q.Tt[k]; dTt[k] = Q.dTt[k];
-      }
       // all 75 coefficient loads are issued before the arithmetic: one round trip per pair
       T cc[kQ];
 #pragma unroll
       for (int k = 0; k < kQ; ++k) cc[k] = __ldg(C + k * 32);
-      T Fs[3], Ft[3], Fp[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        Fs[i] = Ft[i] = Fp[i] = T(0);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          const T* c = cc + (i * 5 + j) * 5;
-          T d = Tp[0] * c[0], e = dTp[0] * c[0];
-#pragma unroll
-          for (int k = 1; k < 5; ++k) {
-            d += Tp[k] * c[k];
-            e += dTp[k] * c[k];
-          }
-          Fs[i] += Tt[j] * d;    // -> F and dF/d(ts)
-          Ft[i] += dTt[j] * d;   // -> dF/d(tt)
-          Fp[i] += Tt[j] * e;    // -> dF/d(tp)
-        }
-      }
-      const T F = Q.Ts[0] * Fs[0] + Q.Ts[1] * Fs[1] + Q.Ts[2] * Fs[2];
-      const T dF = Q.as * (Q.dTs[0] * Fs[0] + Q.dTs[1] * Fs[1] + Q.dTs[2] * Fs[2]) +
-                   Q.at * (Q.Ts[0] * Ft[0] + Q.Ts[1] * Ft[1] + Q.Ts[2] * Ft[2]) +
-                   Q.ap * (Q.Ts[0] * Fp[0] + Q.Ts[1] * Fp[1] + Q.Ts[2] * Fp[2]);
-      const T Gr = Q.G[ks][0], Gi = Q.G[ks][1], dGr = Q.G[ks][2], dGi = Q.G[ks][3];
-      const T Fw = __shfl_xor_sync(0xffffffffu, F, 1);
-      const T dFw = __shfl_xor_sync(0xffffffffu, dF, 1);
-      const bool odd = lane & 1;
-      const T Fr = odd ? Fw : F, Fi = odd ? F : Fw;
-      const T dFr = odd ? dFw : dF, dFi = odd ? dF : dFw;
-      accS += odd ? (Gr * Fi + Gi * Fr) : (Gr * Fr - Gi * Fi);
-      const T Dr = dGr * Fr - dGi * Fi + Gr * dFr - Gi * dFi;
-      const T Di = dGr * Fi + dGi * Fr + Gr * dFi + Gi * dFr;
-      accD += odd ? Di : Dr;
+      T oS, oD;
+      tgt_contract(Q, cc, lane, oS, oD);
+      accS += oS;
+      accD += oD;
     }
     __syncwarp();
   }
-  T* out = A.f28 + 56 * (size_t)A.perm[t];
-  out[lane] += accS;
+  TO* out = A.f28 + 56 * (size_t)A.perm[t];
+  out[lane] += (TO)accS;
   const int dens = (lane >> 1) & 7;
-  if (dens < 6) out[2 * (16 + 6 * ks + dens) + (lane & 1)] += accD;
+  if (dens < 6) out[2 * (16 + 6 * ks + dens) + (lane & 1)] += (TO)accD;
 }
 
-template <typename T>
+// (c), FP32: warp per chunk of at most 32 targets of one box.  The targets of a box share their
+// cousin boxes, and neighbouring targets mostly fall in the same cone segment of a cousin.  The
+// chunk's (target, cousin) pairs are taken 32 at a time, cousin-major (one pair per lane for the
+// scalars); the lanes whose pairs share a cone segment form a group that loads the segment's
+// coefficients once.  Per-target fields accumulate in shared memory.
+constexpr int kTgtBoxWarps = 4;
+constexpr size_t kTgtBoxSmem = (size_t)kTgtBoxWarps * 32 * (sizeof(TgtScal<float>) + 56 * sizeof(float));
+
+template <typename TO>
+__global__ void __launch_bounds__(32 * kTgtBoxWarps) k_target_box(TgtArgs<float, TO> A, const int2* __restrict__ chunks,
+                                                                  int nchunks) {
+  using T = float;
+  extern __shared__ float4 tb_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  TgtScal<T>* S = reinterpret_cast<TgtScal<T>*>(tb_smem) + warp * 32;
+  T* acc = reinterpret_cast<T*>(reinterpret_cast<TgtScal<T>*>(tb_smem) + kTgtBoxWarps * 32) + warp * 32 * 56;
+  const int chunk = blockIdx.x * kTgtBoxWarps + warp;
+  if (chunk >= nchunks) return;   // no block-wide synchronisation below
+  A.coefs += blockIdx.y * A.cstride;   // right-hand side of a batched call
+  A.f28 += blockIdx.y * 56 * (size_t)A.N;
+  const int2 ch = chunks[chunk];
+  const int t0 = ch.x, n = ch.y;
+  const int64_t base0 = A.tgt_ptr[t0];
+  const int ncous = (int)(A.tgt_ptr[t0 + 1] - base0);   // every target of the box has one record per cousin
+  for (int e = lane; e < 32 * 56; e += 32) acc[e] = T(0);
+  const int dens = (lane >> 1) & 7, ks = lane >> 4;
+  const int dcol = 2 * (16 + 6 * ks + dens) + (lane & 1);
+  const int npairs = n * ncous;
+  for (int p0 = 0; p0 < npairs; p0 += 32) {
+    const int pp = p0 + lane;
+    const bool act = pp < npairs;
+    const int j = act ? pp / n : 0, i = act ? pp - j * n : 0;   // cousin j, target t0 + i
+    int myslot = -1;
+    if (act) {
+      const int t = t0 + i;
+      myslot = A.tgt_slot[base0 + (int64_t)i * ncous + j];
+      tgt_scalars(A, A.x_sorted[3 * (size_t)t], A.x_sorted[3 * (size_t)t + 1], A.x_sorted[3 * (size_t)t + 2],
+                  (T)A.n_sorted[3 * (size_t)t], (T)A.n_sorted[3 * (size_t)t + 1], (T)A.n_sorted[3 * (size_t)t + 2],
+                  myslot, S[lane]);
+    }
+    const int mytgt = i;
+    __syncwarp();
+    unsigned rem = __ballot_sync(0xffffffffu, act);
+    while (rem) {
+      const int leader = __ffs(rem) - 1;
+      const int s0 = __shfl_sync(0xffffffffu, myslot, leader);
+      unsigned grp = __ballot_sync(0xffffffffu, myslot == s0) & rem;
+      rem &= ~grp;
+      const T* C = A.coefs + (size_t)s0 * kQ * 32 + lane;
+      T cc[kQ];
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) cc[k] = __ldg(C + k * 32);
+      while (grp) {
+        const int m = __ffs(grp) - 1;
+        grp &= grp - 1;
+        const int ti = __shfl_sync(0xffffffffu, mytgt, m);
+        T oS, oD;
+        tgt_contract(S[m], cc, lane, oS, oD);
+        acc[ti * 56 + lane] += oS;
+        if (dens < 6) acc[ti * 56 + dcol] += oD;
+      }
+    }
+    __syncwarp();
+  }
+  for (int i = 0; i < n; ++i) {
+    TO* out = A.f28 + 56 * (size_t)A.perm[t0 + i];
+    out[lane] += (TO)acc[i * 56 + lane];
+    if (lane < 24) out[32 + lane] += (TO)acc[i * 56 + 32 + lane];
+  }
+}
+
+template <typename T, typename TO = T>
 cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int D = p->tree.D;
   const T ke = (T)p->desc.k_ext, ki = (T)p->desc.k_int;
@@ -711,11 +1214,24 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   }
   for (int d = D; d >= 3; --d) {
     const DevLevel& L = p->dl[d];
-    TgtArgs<T> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
-                 (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (T*)p->f28, ke, ki, L.cstride};
+    TgtArgs<T, TO> B{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
+                     (const T*)L.coefs, p->x_sorted, p->n_sorted, p->perm, (TO*)p->f28, ke, ki, L.cstride,
+                     L.cg.h, 1.0 / L.cg.ds(), p->desc.k_ext, p->desc.k_int, L.trig_th, L.trig_ph};
     int rec = timer_begin(p, TK_TARGET, s);
-    k_target<T><<<dim3((unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), nrhs), 32 * tgt_warps<T>(), 0,
-                  s>>>(B);
+    if constexpr (std::is_same<T, float>::value) {
+      // a warp per box chunk when the level has at least two waves of chunks (152 SMs x 12 warps),
+      // else a warp per target (finer work units on small levels)
+      constexpr int kMinChunks = 2 * 152 * 12;
+      if (L.ntgt_chunks >= kMinChunks)
+        k_target_box<TO><<<dim3((unsigned)((L.ntgt_chunks + kTgtBoxWarps - 1) / kTgtBoxWarps), nrhs),
+                           32 * kTgtBoxWarps, kTgtBoxSmem, s>>>(B, L.tgt_chunk, L.ntgt_chunks);
+      else
+        k_target<T, TO><<<dim3((unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), nrhs), 32 * tgt_warps<T>(),
+                          0, s>>>(B);
+    } else {
+      k_target<T, TO><<<dim3((unsigned)((p->N + tgt_warps<T>() - 1) / tgt_warps<T>()), nrhs), 32 * tgt_warps<T>(), 0,
+                    s>>>(B);
+    }
     timer_end(p, rec, s);
     ++p->launches;
     if (d > 3) {
@@ -725,10 +1241,14 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
                   L.cstride, Pp.cstride};
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {
-        if constexpr (std::is_same<T, float>::value)
-          k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, kUpRunSmem, s>>>(
-              U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
-        else
+        if constexpr (std::is_same<T, float>::value) {
+          if (Pp.tc)
+            k_up_tc<<<dim3(Pp.ntc_items, nrhs), tc::kThreads, tc::kSmem, s>>>(
+                U, TcTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr, Pp.tc_item, p->dev_err});
+          else
+            k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, kUpRunSmem, s>>>(
+                U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
+        } else
           k_up<T><<<dim3(Pp.nslots, nrhs), kUpThreads, 0, s>>>(U);
       }
       timer_end(p, rec, s);
@@ -741,11 +1261,18 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
 }  // namespace
 
 cudaError_t setup_ifgf_kernels() {
-  return cudaFuncSetAttribute(k_up_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRunSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_up_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRunSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_up_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_target_box<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTgtBoxSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_target_box<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTgtBoxSmem);
+  return e;
 }
 
 cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
-  if (p->desc.precision == IFGF_FP64) return run_ifgf<double>(p, s, nrhs);
+  if (ifgf64(p->desc)) return run_ifgf<double>(p, s, nrhs);
+  if (store64(p->desc)) return run_ifgf<float, double>(p, s, nrhs);
   return run_ifgf<float>(p, s, nrhs);
 }
 

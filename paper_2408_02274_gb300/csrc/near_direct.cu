@@ -50,10 +50,10 @@ __device__ __forceinline__ void near_madd(const T* w, const T* ph, T* acc) {
   }
 }
 
-// One warp per target row; each lane takes U nonzeros per step (two in FP32, one in FP64,
-// which needs twice the registers per nonzero) with independent loads.  The column indices
-// of the next step are loaded one step ahead, so the gather of the densities (which depends
-// on the column) does not wait behind a column load on every step.
+// One warp per target row, lanes strided over the row's nonzeros.  Software pipeline per lane:
+// while the multiply-adds of nonzero e run, the weights and densities of e + 32 are in flight
+// and the column index of e + 64 is being loaded, so neither the column -> density gather
+// dependence nor the HBM latency of the weights sits between two steps.
 template <typename T>
 __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__ row_ptr,
                                               const int* __restrict__ col, const T* __restrict__ val,
@@ -68,34 +68,36 @@ __global__ void __launch_bounds__(256) k_near(int N, const int64_t* __restrict__
 #pragma unroll
   for (int k = 0; k < 56; ++k) acc[k] = T(0);
   const int64_t e0 = row_ptr[row], e1 = row_ptr[row + 1];
-  constexpr int U = sizeof(T) == 4 ? 2 : 1;
   int64_t e = e0 + lane;
-  int mc[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) mc[u] = (e + 32 * u < e1) ? __ldg(col + e + 32 * u) : 0;
-  for (; e + 32 * (U - 1) < e1; e += 32 * U) {
-    int mn[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t en = e + 32 * (U + u);
-      mn[u] = en < e1 ? __ldg(col + en) : 0;
+  if constexpr (sizeof(T) == 8) {   // FP64: twice the registers per nonzero, one nonzero per step
+    for (; e < e1; e += 32) {
+      alignas(16) T w0[8], p0[16];
+      ldg_vec<T, 8>(val + 8 * e, w0);
+      ldg_vec<T, 16>(phi + 16 * (size_t)__ldg(col + e), p0);
+      near_madd(w0, p0, acc);
     }
-    alignas(16) T w[U][8], ph[U][16];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      ldg_vec<T, 8>(val + 8 * (e + 32 * u), w[u]);
-      ldg_vec<T, 16>(phi + 16 * (size_t)mc[u], ph[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) near_madd(w[u], ph[u], acc);
-#pragma unroll
-    for (int u = 0; u < U; ++u) mc[u] = mn[u];
+    e = e1;
   }
-  if (U > 1 && e < e1) {   // one nonzero left for this lane; its column is mc[0]
-    alignas(16) T w0[8], p0[16];
-    ldg_vec<T, 8>(val + 8 * e, w0);
-    ldg_vec<T, 16>(phi + 16 * (size_t)mc[0], p0);
-    near_madd(w0, p0, acc);
+  alignas(16) T w[8], p[16];
+  if (e < e1) {
+    ldg_vec<T, 8>(val + 8 * e, w);
+    ldg_vec<T, 16>(phi + 16 * (size_t)__ldg(col + e), p);
+  }
+  int m1 = (e + 32 < e1) ? __ldg(col + e + 32) : 0;   // column of the next step
+  for (; e < e1; e += 32) {
+    const int64_t e1n = e + 32, e2n = e + 64;
+    const int m2 = (e2n < e1) ? __ldg(col + e2n) : 0;   // column two steps ahead
+    alignas(16) T wn[8], pn[16];
+    if (e1n < e1) {
+      ldg_vec<T, 8>(val + 8 * e1n, wn);
+      ldg_vec<T, 16>(phi + 16 * (size_t)m1, pn);
+    }
+    near_madd(w, p, acc);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w[k] = wn[k];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) p[k] = pn[k];
+    m1 = m2;
   }
 #pragma unroll
   for (int k = 0; k < 56; ++k) acc[k] = warp_sum(acc[k]);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int threads = 256;
   const unsigned blocks = (unsigned)(((size_t)p->N * 32 + threads - 1) / threads);
-  if (p->desc.precision == IFGF_FP64)
+  if (store64(p->desc))
     k_near<double><<<dim3(blocks, nrhs), threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,
         p->near.val64, (const double*)p->phi, (double*)p->f28);
   else
@@ -221,7 +223,7 @@ cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
 
 cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int npp = p->desc.nc * p->desc.nc;
-  if (p->desc.precision == IFGF_FP64) {
+  if (store64(p->desc)) {
     // FP64 keeps the digits of nearby differences without patch-local origins: every block
     // takes 128 consecutive nodes (no idle lanes when N_c^2 is not a multiple of 128)
     k_far_direct<double><<<dim3((unsigned)((p->N + 127) / 128), nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n,
@@ -239,7 +241,7 @@ cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
 // (origin, lo, hi) with origin = 128 * j, the start of the FP64 full map's j-th block, so that
 // the listed rows see the same origin, tile order and summation order as in that map.
 cudaError_t launch_far_direct_blocks(const ifgf_plan_t* p, cudaStream_t s, const int* blocks, int nblocks) {
-  if (p->desc.precision == IFGF_FP64)
+  if (store64(p->desc))
     k_far_direct<double><<<dim3((unsigned)nblocks, 1), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
         (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, blocks, 128);
   else

@@ -65,9 +65,18 @@ struct HostLevel {
   std::vector<int32_t> up_order;              // [ncompact][8][75] points ranked by (group, child cone)
   std::vector<int32_t> up_task;               // runs start | len << 8 | octant << 16, per (cone, group)
   std::vector<int32_t> up_task_ptr;           // [ncompact * kUpGroups + 1] CSR offsets into up_task
+  // the same step on the tensor cores: per (compact cone, octant) the points ranked by child cone,
+  // units of at most kUpRunMax of them sharing one child cone (start | len << 8 | octant << 16,
+  // CSR per compact cone), and groups of up to kTcBoxes slots of one compact cone (-1 padded)
+  std::vector<int32_t> tc_order;              // [ncompact][8][75]
+  std::vector<int32_t> tc_unit;
+  std::vector<int32_t> tc_unit_ptr;           // [ncompact + 1]
+  std::vector<int32_t> tc_item;               // [nitems][kTcBoxes]
+  int tc_max_units = 0;                       // most units of one compact cone
   // target evaluation lists at this level: per sorted target, its slots
   std::vector<int64_t> tgt_ptr;
   host_array<int32_t> tgt_slot;
+  std::vector<int32_t> tgt_chunk;             // (first sorted target, count <= 32) per chunk of a box with cousins
   ConeGeom cg() const { return ConeGeom{h, ns, na}; }
 };
 
@@ -102,9 +111,19 @@ struct DevLevel {
   int* up_order = nullptr;        // [ncompact][8][75]
   int* up_task = nullptr;         // runs per (compact cone, group)
   int* up_task_ptr = nullptr;     // [ncompact * kUpGroups + 1]
+  int* tc_order = nullptr;        // [ncompact][8][75]
+  int* tc_unit = nullptr;         // units per compact cone
+  int* tc_unit_ptr = nullptr;     // [ncompact + 1]
+  int* tc_item = nullptr;         // [ntc_items][kTcBoxes]
+  int ntc_items = 0;
+  bool tc = false;                // the upward step into this level runs on the tensor cores
   int64_t* tgt_ptr = nullptr;     // [N+1]
   int* tgt_slot = nullptr;        // [ninter]
+  double2* trig_th = nullptr;     // [na] (cos, sin) of g2 * pi / na: lower edges of the theta cells
+  double2* trig_ph = nullptr;     // [2 na] (cos, sin) of g3 * pi / na: lower edges of the phi cells
   int64_t ninter = 0;
+  int2* tgt_chunk = nullptr;      // [ntgt_chunks] (first sorted target, count <= 32), targets of one box
+  int ntgt_chunks = 0;
   void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan); one buffer
                                   // serves all levels of equal parity (two live levels at a time)
   size_t cstride = 0;             // nslots * 75 * 32: coefficients per right-hand side
@@ -185,6 +204,13 @@ struct KernelTimer {
 
 struct ifgf_tree_t : ifgf::HostTree {};
 
+namespace ifgf {
+// Storage and arithmetic of the densities, near matrix, fields and combination: FP64 in the FP64
+// and mixed plans.  The IFGF kernels (leaf, upward, target) run in FP64 only in the FP64 plan.
+inline bool store64(const ifgf_plan_desc& d) { return d.precision != IFGF_FP32; }
+inline bool ifgf64(const ifgf_plan_desc& d) { return d.precision == IFGF_FP64; }
+}  // namespace ifgf
+
 struct ifgf_plan_t {
   ifgf_plan_desc desc{};
   int N = 0, P = 0, nc = 0, ng = 0;
@@ -198,6 +224,7 @@ struct ifgf_plan_t {
   ifgf_tree_t tree;
   // device data
   ifgf::NodeGeom geo;
+  int* dev_err = nullptr;       // device status word (bit 0: a tensor-core wait timed out)
   double* tab_D = nullptr;      // [nc][nc] Chebyshev differentiation matrix
   double* x_sorted = nullptr;   // [N][3] nodes in sorted order
   double* n_sorted = nullptr;   // [N][3]
