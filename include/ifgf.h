@@ -79,9 +79,10 @@ typedef struct {
   double delta;            /* singular-set distance threshold of Eq. patch_sing; must be > 0 */
   int32_t n_beta;          /* Fejer points per direction of the moment rule (Eq. int_moments_cov), 4..96 */
   double cov_d;            /* change-of-variables order d >= 2 (Eq. mk_cov_1) */
-  int32_t gs_iters;        /* golden-section iterations per direction (Eq. dist_min); 0 -> 60.
+  int32_t gs_iters;        /* golden-section iterations per direction (Eq. dist_min); 0 -> 20.
                               The edge snap follows the final bracket, so 10-20 steps find the
-                              same closest points after the Newton polish */
+                              same closest points after the Newton polish (kernel rows within
+                              3e-14 of 60 steps) */
   int32_t precision;       /* IFGF_FP64, IFGF_FP32 or IFGF_MIXED: arithmetic of steps (a)-(d) per apply */
   int32_t far_mode;        /* IFGF_FAR_IFGF or IFGF_FAR_DIRECT (plain O(N^2) far sum) */
   int32_t max_krylov;      /* GMRES basis capacity allocated by plan_create (0 -> 300, <= 1000) */
@@ -369,6 +370,38 @@ ifgf_status ifgf_far_direct_noalloc(int32_t n, const double* nodes, const double
                                     const double* weights, const int32_t* leaf_coords, const void* phi,
                                     double k_ext, double k_int, int32_t precision, void* f28,
                                     ifgf_stream stream);
+
+/*
+ * Far-field pattern of the scattered electric field of a solution (the quantity of the
+ * scattering experiments of Sec. IV; the reciprocity check of the batched incidences): with the
+ * exterior field representation E^sc = -omega mu_e curl S_e[m] - i (k^2 S_e[j] + grad S_e[div j])
+ * (k = kappa_e, e^{-i omega t}), E^sc(r d) = e^{i k r}/r E_inf(d) + O(1/r^2) and
+ *   E_inf(d) = -i k omega mu_e (d x F[m]) - i k^2 F[j] + k d F[div j],
+ *   F[f] = (1/4 pi) sum_l f(x_l) e^{-i k d.x_l} omega_l  (Nystrom nodes and weights, FP64).
+ * y: DEVICE [nrhs][4][N] complex128 solution (the layout of ifgf_apply); dirs: DEVICE [ndirs][3]
+ * double unit directions; out: DEVICE [nrhs][ndirs][3] complex128.  1 <= nrhs <= batch,
+ * 1 <= ndirs <= 2^24.  Uses the plan's per-apply density buffers (do not overlap with an apply on
+ * another stream); asynchronous on `stream`; allocates nothing.  IFGF_EINVAL on invalid
+ * arguments; IFGF_ECUDA poisons the plan.
+ */
+ifgf_status ifgf_far_field(ifgf_plan plan, int32_t nrhs, const void* y, int32_t ndirs, const double* dirs, void* out,
+                           ifgf_stream stream);
+
+/*
+ * Autotuner (this library's own; the paper runs on CPUs): times, on the plan's own tables and
+ * buffers, the launch shapes whose choice changes the forward map's time, and keeps the faster
+ * one in the plan for later applies and solves:
+ *   - per octree level d of an FP32 or mixed IFGF plan, the target step (c) as a warp per target
+ *     or a warp per chunk of 32 targets of one box (choices[d]: 0 or 1; times_ms[2d], [2d+1]:
+ *     ms per launch of each);
+ *   - the near-field matvec's block size, 128 or 256 threads (choices[25]; times_ms[50], [51]).
+ * reps: timed launches per candidate (after one warm-up), 1..1000.  choices: host int32 [26]
+ * or NULL (-1 where not applicable); times_ms: host float [52] or NULL.  Results of later applies
+ * are unchanged up to summation order (the target step's grouping differs between the two
+ * shapes).  Synchronises `stream`; overwrites the plan's per-apply buffers (call it between
+ * applies, not during a capture).  IFGF_EINVAL for reps out of range; IFGF_ECUDA poisons the plan.
+ */
+ifgf_status ifgf_plan_tune(ifgf_plan plan, int32_t reps, int32_t* choices, float* times_ms, ifgf_stream stream);
 
 /* Human-readable message for a status code (static storage). */
 const char* ifgf_status_string(ifgf_status s);

@@ -10,9 +10,9 @@ CPU oracle and the GPU library can consume it without sharing code.
 from .geometry import (Body, cubed_sphere, ellipsoid, star_body, superellipsoid_bar, rounded_bar,
                        open_cheb_nodes, sample_body)
 from .problems import (Problem, sphere_problem, CONFIG_SPHERE_SMALL, CONFIG_SPHERE_MEDIUM,
-                       random_densities, plane_wave, fibonacci_incidences, ellipsoid_batch,
+                       random_densities, plane_wave, fibonacci_directions, fibonacci_incidences, ellipsoid_batch,
                        dipole_field, star_batch, gaussian_beam, waveguide_bar)
 
-__all__ = ["gaussian_beam", "waveguide_bar", "star_batch", "dipole_field", "ellipsoid_batch", "fibonacci_incidences", "Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar", "rounded_bar",
+__all__ = ["fibonacci_directions", "gaussian_beam", "waveguide_bar", "star_batch", "dipole_field", "ellipsoid_batch", "fibonacci_incidences", "Body", "cubed_sphere", "ellipsoid", "star_body", "superellipsoid_bar", "rounded_bar",
            "open_cheb_nodes", "sample_body", "Problem", "sphere_problem",
            "CONFIG_SPHERE_SMALL", "CONFIG_SPHERE_MEDIUM", "random_densities", "plane_wave"]

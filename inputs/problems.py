@@ -98,11 +98,10 @@ def plane_wave(x: np.ndarray, k_ext: float, omega: float, mu_ext: float = 1.0,
     return np.concatenate([E, H], axis=0)
 
 
-def fibonacci_incidences(x: np.ndarray, k_ext: float, omega: float, n_dirs: int = 32, mu_ext: float = 1.0):
-    """2 n_dirs plane waves: directions on a Fibonacci sphere, z_k = 1 - (2k+1)/n_dirs,
-    phi_k = k pi (3 - sqrt 5), each with two polarisations e1 = z x d / |z x d| (x when d is
-    along z) and e2 = d x e1.  Returns [2 n_dirs, 6, N] complex (see plane_wave)."""
-    out = []
+def fibonacci_directions(n_dirs: int = 32):
+    """Directions d_k on a Fibonacci sphere, z_k = 1 - (2k+1)/n_dirs, phi_k = k pi (3 - sqrt 5), and
+    their polarisations e1 = z x d / |z x d| (x when d is along z), e2 = d x e1: three [n_dirs, 3]."""
+    D, E1, E2 = [], [], []
     for k in range(n_dirs):
         z = 1.0 - (2 * k + 1) / n_dirs
         r = np.sqrt(max(0.0, 1.0 - z * z))
@@ -110,7 +109,19 @@ def fibonacci_incidences(x: np.ndarray, k_ext: float, omega: float, n_dirs: int 
         d = np.array([r * np.cos(ph), r * np.sin(ph), z])
         e1 = np.cross([0.0, 0.0, 1.0], d)
         e1 = e1 / np.linalg.norm(e1) if np.linalg.norm(e1) > 1e-12 else np.array([1.0, 0.0, 0.0])
-        e2 = np.cross(d, e1)
+        D.append(d)
+        E1.append(e1)
+        E2.append(np.cross(d, e1))
+    return np.array(D), np.array(E1), np.array(E2)
+
+
+def fibonacci_incidences(x: np.ndarray, k_ext: float, omega: float, n_dirs: int = 32, mu_ext: float = 1.0):
+    """2 n_dirs plane waves: the directions of fibonacci_directions, each with its two
+    polarisations e1, e2 (incidence 2k + i has direction d_k and polarisation e_{i+1}).
+    Returns [2 n_dirs, 6, N] complex (see plane_wave)."""
+    D, E1, E2 = fibonacci_directions(n_dirs)
+    out = []
+    for d, e1, e2 in zip(D, E1, E2):
         for p in (e1, e2):
             out.append(plane_wave(x, k_ext, omega, mu_ext, direction=d, polarization=p))
     return np.stack(out)

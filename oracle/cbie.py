@@ -484,6 +484,31 @@ def upsampled_quadrature(problem, y, nq: int):
     return xq.reshape(-1, 3), W, fq[0:3].T, fq[3:6].T, fq[6], fq[7]
 
 
+def far_field(problem, y, dirs, nq: int | None = None):
+    """Far-field pattern of the scattered electric field, E^sc(r d) = e^{i k r}/r E_inf(d) + O(1/r^2)
+    for r -> infinity along the unit directions dirs [Q, 3]; returns E_inf [Q, 3].
+
+    From the exterior representation of reading R2, E^sc = -omega mu_e curl S_e[m] - i (k^2 S_e[j]
+    + grad S_e[div j]) with k = kappa_e: along d, G(x, y) = e^{i k r}/(4 pi r) e^{-i k d.y} (1 +
+    O(1/r)) and grad_x -> i k d, so with the far-field moments F[f] = (1/4 pi) int f(y)
+    e^{-i k d.y} dy:
+        E_inf = -i k omega mu_e (d x F[m]) - i k^2 F[j] + k d F[div j].
+    The moments use the Nystrom nodes and weights omega (nq None), or the densities' Chebyshev
+    interpolants on an nq x nq grid per patch (the quadrature of fields_off_surface).
+    """
+    k, mu, om = problem.k_ext, problem.mu_ext, problem.omega
+    d = np.asarray(dirs, dtype=np.float64).reshape(-1, 3)
+    if nq is None:
+        g = geometry_of(problem)
+        phi = densities(y, g)
+        ys, W, m, j, dj = g.x, g.omega, phi[0:3].T, phi[3:6].T, phi[7]
+    else:
+        ys, W, m, j, _, dj = upsampled_quadrature(problem, y, nq)
+    E = np.exp(-1j * k * (d @ ys.T)) * W[None, :] / (4 * np.pi)            # [Q, nodes]
+    Fm, Fj, Fq = E @ m, E @ j, E @ dj
+    return -1j * k * om * mu * np.cross(d, Fm) - 1j * k * k * Fj + k * d * Fq[:, None]
+
+
 def fields_off_surface(problem, y, pts, medium: str, nq: int = 40, chunk: int = 256):
     """E and H of the representation (reading R2) at points off Gamma.
 

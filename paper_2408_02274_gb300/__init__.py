@@ -27,7 +27,8 @@ EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_ba
            "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
            "ifgf_plan_stats", "ifgf_plan_estimate", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
-           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_far_direct_noalloc"]
+           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_far_direct_noalloc", "ifgf_far_field",
+           "ifgf_plan_tune"]
 
 
 class ifgf_plan_desc(ctypes.Structure):
@@ -133,6 +134,8 @@ def load(path: str = LIB_PATH):
     lib.ifgf_tree_targets.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, vp]
     lib.ifgf_tree_upward.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(ctypes.c_int64), vp, vp]
     lib.ifgf_far_direct_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
+    lib.ifgf_far_field.argtypes = [vp, i32, vp, i32, vp, vp, vp]
+    lib.ifgf_plan_tune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), vp]
     for name in EXPORTS:
         if name != "ifgf_status_string":
             getattr(lib, name).restype = ctypes.c_int32
@@ -199,7 +202,7 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      eps_ext: float, eps_int: float, mu_ext: float = 1.0, mu_int: float = 1.0, *,
                      delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
-                     gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
+                     gs_iters: int = 20, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                      max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0,
                      gmres_scaling: int = 0, upward_tc: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
@@ -227,7 +230,7 @@ def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext
                        eps_ext: float, eps_int: float, mu_ext: float = 1.0, mu_int: float = 1.0, *,
                        delta: float, ps: int = 3, pa: int = 5, ns0: int = 1, na0: int = 2,
                        leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
-                       gs_iters: int = 60, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
+                       gs_iters: int = 20, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                        max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0, gmres_scaling: int = 0,
                        upward_tc: int = 0) -> dict:
     """ifgf_plan_estimate: the device memory ifgf_plan_create would allocate for the same
@@ -259,6 +262,29 @@ def ifgf_apply_batch(plan, y, out, stream=None):
     nrhs, n4 = _nrhs(y, "y"), 4 * _plan_n(plan)
     _check(load().ifgf_apply_batch(plan, nrhs, _arg(y, "complex128", nrhs * n4, "y"),
                                    _arg(out, "complex128", nrhs * n4, "out"), _stream(stream)), "ifgf_apply_batch")
+
+
+def ifgf_plan_tune(plan, reps: int = 5, stream=None):
+    """Autotune the plan's launch shapes; returns (choices [26] int32, times_ms [52] float32)."""
+    ch = np.zeros(26, dtype=np.int32)
+    tm = np.zeros(52, dtype=np.float32)
+    _check(load().ifgf_plan_tune(plan, int(reps), ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 tm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
+           "ifgf_plan_tune")
+    return ch, tm
+
+
+def ifgf_far_field(plan, y, dirs, out, stream=None):
+    """Far-field pattern E_inf of the scattered field of solutions y (complex128 CUDA tensor
+    [nrhs, 4, N] or [4, N]) at unit directions dirs (float64 CUDA tensor [ndirs, 3]) into out
+    (complex128 CUDA tensor [nrhs, ndirs, 3] or [ndirs, 3])."""
+    n = _plan_n(plan)
+    nrhs = 1 if y.dim() == 2 else int(y.shape[0])
+    ndirs = int(dirs.shape[0])
+    _check(load().ifgf_far_field(plan, nrhs, _arg(y, "complex128", nrhs * 4 * n, "y"), ndirs,
+                                 _arg(dirs, "float64", 3 * ndirs, "dirs"),
+                                 _arg(out, "complex128", nrhs * ndirs * 3, "out"), _stream(stream)),
+           "ifgf_far_field")
 
 
 def ifgf_apply_direct_patches(plan, y, out, patches, stream=None):
@@ -587,6 +613,12 @@ class Plan:
 
     def apply_batch(self, y, out, stream=None):
         ifgf_apply_batch(self.handle, y, out, stream)
+
+    def tune(self, reps: int = 5, stream=None):
+        return ifgf_plan_tune(self.handle, reps, stream)
+
+    def far_field(self, y, dirs, out, stream=None):
+        ifgf_far_field(self.handle, y, dirs, out, stream)
 
     def apply_direct_patches(self, y, out, patches, stream=None):
         ifgf_apply_direct_patches(self.handle, y, out, patches, stream)

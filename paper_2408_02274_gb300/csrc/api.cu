@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <stdexcept>
@@ -227,7 +228,7 @@ void build(ifgf_plan_t* p) {
     int* d_ppatch = SN.upload(cpatch);
     double* d_uv = SN.dev<double>(2 * (size_t)npairs);
     uint8_t* d_sing = SN.dev<uint8_t>(npairs);
-    int iters = d.gs_iters > 0 ? d.gs_iters : 60;
+    int iters = d.gs_iters > 0 ? d.gs_iters : 20;
     k_closest<<<(npairs + 127) / 128, 128>>>(npairs, nc, ng, iters, d.delta, d_ptgt, d_ppatch, p->geo.x,
                                              fcoef, unodes, d_uv, d_sing);
     check(cudaGetLastError(), "k_closest launch");
@@ -343,6 +344,9 @@ void build(ifgf_plan_t* p) {
     Dl.tgt_ptr = A.upload(L.tgt_ptr);
     Dl.tgt_chunk = reinterpret_cast<int2*>(A.upload(L.tgt_chunk));
     Dl.ntgt_chunks = (int)(L.tgt_chunk.size() / 2);
+    // box chunks when the level has at least two waves of them (12 resident warps per SM), else
+    // a warp per target; ifgf_plan_tune measures both
+    Dl.tgt_mode = Dl.ntgt_chunks >= 2 * 12 * std::max(p->num_sms, 1) ? 1 : 0;
     Dl.tgt_slot = A.upload(L.tgt_slot.data(), L.tgt_slot.size());
     Dl.ninter = (int64_t)L.tgt_slot.size();
     Dl.cstride = (size_t)Dl.nslots * kQ * 32;
@@ -771,6 +775,95 @@ ifgf_status ifgf_apply_direct_patches(ifgf_plan p, const void* y, void* out, con
   cudaFree(d_blk);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "ifgf_apply_direct_patches", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_far_field(ifgf_plan p, int32_t nrhs, const void* y, int32_t ndirs, const double* dirs, void* out,
+                           ifgf_stream stream) {
+  if (!p || !y || !dirs || !out || ndirs < 1 || ndirs > (1 << 24)) return IFGF_EINVAL;
+  if (nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = launch_density_prep(p, (const double*)y, nullptr, s, nrhs);
+  if (e == cudaSuccess) e = launch_far_field(p, nrhs, ndirs, dirs, (double*)out, s);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_far_field", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+// Autotuner: the launch shapes with a measured effect, timed on this plan's own tables and
+// buffers (the fields buffer is scratch between applies).
+static cudaError_t time_ms(cudaStream_t s, int reps, const std::function<cudaError_t()>& run, float* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = run();   // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
+
+ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* times_ms, ifgf_stream stream) {
+  if (!p || reps < 1 || reps > 1000) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  try {
+    if (choices)
+      for (int k = 0; k < 26; ++k) choices[k] = -1;
+    if (times_ms)
+      for (int k = 0; k < 52; ++k) times_ms[k] = 0.f;
+    // (c): per level, a warp per target or per box chunk
+    if (p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
+      for (int d = 3; d <= p->tree.D && e == cudaSuccess; ++d) {
+        float t[2] = {0.f, 0.f};
+        for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+          e = time_ms(s, reps, [&]() { return launch_target_level(p, d, m, s); }, &t[m]);
+        if (e != cudaSuccess) break;
+        p->dl[d].tgt_mode = (t[1] < t[0] && p->dl[d].ntgt_chunks > 0) ? 1 : 0;
+        if (choices && d < 25) choices[d] = p->dl[d].tgt_mode;
+        if (times_ms && d < 25) {
+          times_ms[2 * d] = t[0] / reps;
+          times_ms[2 * d + 1] = t[1] / reps;
+        }
+      }
+    }
+    // (d): the near-field matvec's block size
+    if (e == cudaSuccess) {
+      const int sizes[2] = {128, 256};
+      float t[2] = {0.f, 0.f};
+      for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        p->near_threads = sizes[k];
+        e = time_ms(s, reps, [&]() { return launch_near(p, s, 1); }, &t[k]);
+      }
+      if (e == cudaSuccess) {
+        p->near_threads = t[0] < t[1] ? 128 : 256;
+        if (choices) choices[25] = p->near_threads;
+        if (times_ms) {
+          times_ms[50] = t[0] / reps;
+          times_ms[51] = t[1] / reps;
+        }
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  } catch (const std::exception& ex) {
+    set_status_detail(IFGF_EINTERNAL, ex.what());
+    return IFGF_EINTERNAL;
+  }
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_plan_tune", __FILE__, __LINE__);
     p->poisoned = true;
     return IFGF_ECUDA;
   }

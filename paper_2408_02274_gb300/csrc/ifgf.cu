@@ -1219,10 +1219,9 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
                      L.cg.h, 1.0 / L.cg.ds(), p->desc.k_ext, p->desc.k_int, L.trig_th, L.trig_ph};
     int rec = timer_begin(p, TK_TARGET, s);
     if constexpr (std::is_same<T, float>::value) {
-      // a warp per box chunk when the level has at least two waves of chunks (152 SMs x 12 warps),
-      // else a warp per target (finer work units on small levels)
-      constexpr int kMinChunks = 2 * 152 * 12;
-      if (L.ntgt_chunks >= kMinChunks)
+      // a warp per box chunk or a warp per target: the level's tgt_mode (set at plan creation,
+      // retuned by ifgf_plan_tune)
+      if (L.tgt_mode == 1 && L.ntgt_chunks > 0)
         k_target_box<TO><<<dim3((unsigned)((L.ntgt_chunks + kTgtBoxWarps - 1) / kTgtBoxWarps), nrhs),
                            32 * kTgtBoxWarps, kTgtBoxSmem, s>>>(B, L.tgt_chunk, L.ntgt_chunks);
       else
@@ -1259,6 +1258,36 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
 }
 
 }  // namespace
+
+// The FP32 target step of level d alone in `mode` (0 warp per target, 1 warp per box chunk), for
+// the autotuner; accumulates into the plan's fields buffer like an apply.
+cudaError_t launch_target_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s) {
+  if (ifgf64(p->desc)) return cudaErrorInvalidValue;
+  const DevLevel& L = p->dl[d];
+  TgtArgs<float, float> B32{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center,
+                            cone_geom_t<float>(L.cg), (const float*)L.coefs, p->x_sorted, p->n_sorted, p->perm,
+                            (float*)p->f28, (float)p->desc.k_ext, (float)p->desc.k_int, L.cstride, L.cg.h,
+                            1.0 / L.cg.ds(), p->desc.k_ext, p->desc.k_int, L.trig_th, L.trig_ph};
+  TgtArgs<float, double> B64{p->N, L.tgt_ptr, L.tgt_slot, L.slot_box, L.slot_cone, L.box_center,
+                             cone_geom_t<float>(L.cg), (const float*)L.coefs, p->x_sorted, p->n_sorted, p->perm,
+                             (double*)p->f28, (float)p->desc.k_ext, (float)p->desc.k_int, L.cstride, L.cg.h,
+                             1.0 / L.cg.ds(), p->desc.k_ext, p->desc.k_int, L.trig_th, L.trig_ph};
+  const bool out64 = store64(p->desc);
+  if (mode == 1 && L.ntgt_chunks > 0) {
+    const dim3 g((unsigned)((L.ntgt_chunks + kTgtBoxWarps - 1) / kTgtBoxWarps), 1);
+    if (out64)
+      k_target_box<double><<<g, 32 * kTgtBoxWarps, kTgtBoxSmem, s>>>(B64, L.tgt_chunk, L.ntgt_chunks);
+    else
+      k_target_box<float><<<g, 32 * kTgtBoxWarps, kTgtBoxSmem, s>>>(B32, L.tgt_chunk, L.ntgt_chunks);
+  } else {
+    const dim3 g((unsigned)((p->N + tgt_warps<float>() - 1) / tgt_warps<float>()), 1);
+    if (out64)
+      k_target<float, double><<<g, 32 * tgt_warps<float>(), 0, s>>>(B64);
+    else
+      k_target<float, float><<<g, 32 * tgt_warps<float>(), 0, s>>>(B32);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t setup_ifgf_kernels() {
   cudaError_t e = cudaFuncSetAttribute(k_up_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpRunSmem);

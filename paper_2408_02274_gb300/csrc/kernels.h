@@ -48,10 +48,16 @@ cudaError_t launch_far_direct(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1
 cudaError_t launch_far_direct_blocks(const ifgf_plan_t* p, cudaStream_t s, const int* blocks, int nblocks);
 cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, const int* leafc, const void* a,
                                   double ke, double ki, int precision, void* f28, cudaStream_t s);
+// the FP32 target step of level d alone, warp per target (mode 0) or per box chunk (mode 1)
+cudaError_t launch_target_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s);
 // opt the IFGF kernels into the dynamic shared memory they use (once per device)
 cudaError_t setup_ifgf_kernels();
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
 cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
+// far-field pattern E_inf [nrhs][ndirs][3] complex128 (out) of the scattered field from the densities
+// of the last density preparation (phi64); dirs: device [ndirs][3] unit vectors
+cudaError_t launch_far_field(const ifgf_plan_t* p, int nrhs, int ndirs, const double* dirs, double* out,
+                             cudaStream_t s);
 // zero f28
 cudaError_t launch_zero_f28(const ifgf_plan_t* p, cudaStream_t s);
 // f28 (plan precision) -> complex128 [N][28]

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
 }  // namespace
 
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
-  const int threads = 256;
+  const int threads = p->near_threads;   // 128 or 256 (the kernel's launch bound)
   const unsigned blocks = (unsigned)(((size_t)p->N * 32 + threads - 1) / threads);
   if (store64(p->desc))
     k_near<double><<<dim3(blocks, nrhs), threads, 0, s>>>(p->N, p->near.row_ptr, p->near.col,

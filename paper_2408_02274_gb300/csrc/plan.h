@@ -124,6 +124,7 @@ struct DevLevel {
   int64_t ninter = 0;
   int2* tgt_chunk = nullptr;      // [ntgt_chunks] (first sorted target, count <= 32), targets of one box
   int ntgt_chunks = 0;
+  int tgt_mode = 0;               // FP32 target step at this level: 0 warp per target, 1 warp per box chunk
   void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan); one buffer
                                   // serves all levels of equal parity (two live levels at a time)
   size_t cstride = 0;             // nslots * 75 * 32: coefficients per right-hand side
@@ -221,6 +222,7 @@ struct ifgf_plan_t {
   int64_t launches = 0;         // kernels launched by apply/solve since the last reset
   int device = 0;
   int num_sms = 0;
+  int near_threads = 256;       // block size of the near-field matvec (set by ifgf_plan_tune)
   ifgf_tree_t tree;
   // device data
   ifgf::NodeGeom geo;

@@ -11,6 +11,10 @@ from inputs import CONFIG_SPHERE_SMALL, plane_wave
 from oracle import cbie, mie
 
 
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
 def test_mie_incident_expansion_is_the_plane_wave():
     k, om = 2 * np.pi, 2 * np.pi
     pts = mie.fibonacci_sphere(60, 0.41)
@@ -147,3 +151,50 @@ def test_rounded_bar_reciprocity_converges():
         a, b = _reciprocity(prob, oracle_solve(prob))
         defects.append(abs(a - b) / abs(a))
     assert defects[1] < 0.6 * defects[0] and defects[1] < 5e-3, defects
+
+
+def test_far_field_pattern_pins(sphere_solution):
+    """oracle far_field (the scattered field's far-field pattern from the representation of reading
+    R2) against three outside facts, on the 6-patch sphere's GMRES solution:
+    (1) the representation itself at large distance: r e^{-i k r} E^sc(r d) -> E_inf(d), with the
+        O(1/r) term removed by Richardson extrapolation between r and 2r, on the same upsampled
+        quadrature (to rounding); the Nystrom-node moments agree to the discretisation's level;
+    (2) the optical theorem: (4 pi / k) Im(p . E_inf(d_inc)) equals the integral of |E_inf|^2 over
+        directions (lossless sphere: extinction = scattering);
+    (3) the Mie series' extinction cross section.
+    A planted sign error in the div j term fails (1)."""
+    import inspect
+    import textwrap
+
+    prob, op, y = sphere_solution[:3]
+    k = prob.k_ext
+    dirs = mie.fibonacci_sphere(12, 1.0)
+    ff = cbie.far_field(prob, y, dirs, nq=40)
+    ext = []
+    for R in (1600.0, 3200.0):
+        E, _ = cbie.fields_off_surface(prob, y, R * dirs, "ext", nq=40)
+        ext.append(E * R * np.exp(-1j * k * R))
+    lim = 2 * ext[1] - ext[0]
+    assert rel(ff, lim) < 2e-7                               # O(1/r^2) remainder: 6e-8 measured
+    assert rel(cbie.far_field(prob, y, dirs), lim) < 1e-3   # Nystrom rule at N_c = 8: 1.9e-4
+
+    ct, wt = np.polynomial.legendre.leggauss(40)
+    ph = 2 * np.pi * np.arange(80) / 80
+    C, P = np.meshgrid(ct, ph, indexing="ij")
+    S = np.sqrt(1 - C ** 2)
+    dq = np.stack([S * np.cos(P), S * np.sin(P), C], axis=-1).reshape(-1, 3)
+    wq = (wt[:, None] * np.full(80, 2 * np.pi / 80)[None, :]).reshape(-1)
+    Eq = cbie.far_field(prob, y, dq, nq=40)
+    sig_sca = float(np.sum(wq * np.sum(np.abs(Eq) ** 2, axis=1)))
+    fwd = cbie.far_field(prob, y, np.array([[0.0, 0.0, 1.0]]), nq=40)[0]
+    sig_ext = float(4 * np.pi / k * np.imag(fwd[0]))          # p = x, d_inc = +z
+    assert abs(sig_ext - sig_sca) < 3e-3 * sig_ext
+    qext, _ = mie.efficiencies(k, prob.k_int, 0.5)
+    assert abs(sig_ext - qext * np.pi * 0.25) < 3e-3 * sig_ext
+
+    src = textwrap.dedent(inspect.getsource(cbie.far_field))
+    old = "+ k * d * Fq[:, None]"
+    assert src.count(old) == 1
+    ns = dict(vars(cbie))
+    exec(compile(src.replace(old, "- k * d * Fq[:, None]"), "<mutant of far_field>", "exec"), ns)
+    assert rel(ns["far_field"](prob, y, dirs, nq=40), lim) > 1e-2
