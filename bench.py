@@ -33,6 +33,7 @@ WORKLOADS = {
     "sphere384": "sphere r=0.5 lambda, eps_r=2.25, 6 patches x 8x8 nodes (N=384, 1536 unknowns)",
     "sphere9600": "sphere r=2 lambda, eps_r=4, 96 patches x 10x10 nodes (N=9600, 38400 unknowns)",
     "sphere153600": "sphere r=4 lambda, eps_r=2.25, 600 patches x 16x16 nodes (N=153600, 614400 unknowns)",
+    "sphere24576": "sphere r=2 lambda, eps_r=2.25, 96 patches x 16x16 nodes (N=24576, 98304 unknowns)",
 }
 METRIC = "IFGF N-Mueller unknown*matvecs/s at rel err <=1e-4; GMRES time-to-solve"
 UNIT = "unknown*matvecs/s"
@@ -49,6 +50,8 @@ def problem(name: str = "sphere153600"):
         return CONFIG_SPHERE_SMALL(8)
     if name == "sphere153600":
         return sphere_problem(4.0, 10, 16, 2.25, name="sphere_r4_eps2.25_P600")
+    if name == "sphere24576":   # the benchmark body's node density on a smaller sphere (profiling size)
+        return sphere_problem(2.0, 4, 16, 2.25, name="sphere_r2_eps2.25_P96_nc16")
     return CONFIG_SPHERE_MEDIUM(10)
 
 

@@ -248,7 +248,8 @@ ifgf_status bie_solve(ifgf_plan plan, const void* inc, double tol, int32_t max_i
  * side whose residual estimate reaches tol keeps its iterate (its Arnoldi state is frozen)
  * while the others continue, up to max_iter.  1 <= nrhs <= the plan's batch.  Returns
  * IFGF_ENOCONV if any right-hand side did not reach tol.  Synchronises `stream` (nrhs x 8
- * scalars are read back per iteration).
+ * scalars are read back per iteration).  No C++ exception leaves the call: a failed host
+ * allocation is IFGF_ENOMEM, any other host failure IFGF_EINTERNAL with its message.
  */
 ifgf_status bie_solve_batch(ifgf_plan plan, int32_t nrhs, const void* inc, double tol, int32_t max_iter,
                             void* y, int32_t* iters, double* relres, ifgf_stream stream);
@@ -263,7 +264,8 @@ ifgf_status bie_solve_batch(ifgf_plan plan, int32_t nrhs, const void* inc, doubl
  * non-blocking stream for that solve and destroy it before returning.  status[i] (HOST array,
  * may be NULL) receives each solve's status.  Returns IFGF_OK if every solve reached tol,
  * otherwise the first status other than IFGF_OK and IFGF_ENOCONV, otherwise IFGF_ENOCONV.
- * Returns when all solves have finished.
+ * The message of the first failed solve (plan order) is handed to the calling thread, so that
+ * ifgf_status_string of that status shows it.  Returns when all solves have finished.
  */
 ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t* nrhs,
                            const void* const* incs, double tol, int32_t max_iter, void* const* ys,

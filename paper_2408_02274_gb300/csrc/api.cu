@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <stdexcept>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -963,8 +964,12 @@ ifgf_status bie_solve_batch(ifgf_plan p, int32_t nrhs, const void* inc, double t
     return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, false);
   } catch (const std::bad_alloc&) {
     return IFGF_ENOMEM;
+  } catch (const std::exception& e) {
+    set_status_detail(IFGF_EINTERNAL, e.what());
+    return IFGF_EINTERNAL;
   } catch (...) {
-    return IFGF_ECUDA;
+    set_status_detail(IFGF_EINTERNAL, "bie_solve_batch: unknown exception");
+    return IFGF_EINTERNAL;
   }
 }
 
@@ -974,8 +979,12 @@ ifgf_status bie_solve_precond(ifgf_plan p, int32_t nrhs, const void* inc, double
     return solve_impl(p, nrhs, inc, tol, max_iter, y, iters, relres, stream, true);
   } catch (const std::bad_alloc&) {
     return IFGF_ENOMEM;
+  } catch (const std::exception& e) {
+    set_status_detail(IFGF_EINTERNAL, e.what());
+    return IFGF_EINTERNAL;
   } catch (...) {
-    return IFGF_ECUDA;
+    set_status_detail(IFGF_EINTERNAL, "bie_solve_precond: unknown exception");
+    return IFGF_EINTERNAL;
   }
 }
 
@@ -1133,6 +1142,14 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
   } catch (const std::bad_alloc&) {
     return IFGF_ENOMEM;
   }
+  // the message a failed solve leaves in its worker thread's status strings, handed back to this
+  // thread (the first failure in plan order) after the join
+  std::vector<std::string> msg;
+  try {
+    msg.assign(nplans, std::string());
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  }
   auto work = [&](int i) {
     if (cudaSetDevice(dev) != cudaSuccess) {
       st[i] = IFGF_ECUDA;
@@ -1146,6 +1163,12 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
     }
     st[i] = bie_solve_batch(plans[i], nrhs[i], incs[i], tol, max_iter, ys[i], iters ? iters[i] : nullptr,
                             relres ? relres[i] : nullptr, (ifgf_stream)s);
+    if (st[i] != IFGF_OK && st[i] != IFGF_ENOCONV) {
+      try {
+        msg[i] = ifgf_status_string(st[i]);
+      } catch (...) {
+      }
+    }
     if (own) cudaStreamDestroy(s);
   };
   // one host thread per plan; a solve whose thread cannot be started runs here afterwards
@@ -1158,6 +1181,14 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
   }
   for (int i = started; i < nplans; ++i) work(i);
   for (auto& w : workers) w.join();
+  for (int i = 0; i < nplans; ++i)
+    if (!msg[i].empty()) {
+      if (st[i] == IFGF_ECUDA)
+        snprintf(g_last_err, sizeof(g_last_err), "%s", msg[i].c_str());
+      else
+        set_status_detail(st[i], msg[i].c_str());
+      break;
+    }
   ifgf_status out = IFGF_OK;
   for (int i = 0; i < nplans; ++i) {
     if (status) status[i] = st[i];

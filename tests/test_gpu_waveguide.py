@@ -150,6 +150,7 @@ def test_short_bar_gaussian_beam_solve_true_residual():
     plan.apply_batch(y, Ay)
     true = float(torch.linalg.norm(b - Ay) / torch.linalg.norm(b))
     plan.close()
+    print(f"short bar: {its[0]} iterations, Arnoldi estimate {rrs[0]:.2e}, true residual {true:.2e}")
     assert st == lib.IFGF_OK and rrs[0] <= 1e-5 and its[0] <= 150, (its, rrs, st)
     # the FP32 forward map is linear only to its rounding, which the Krylov combination
     # amplifies: the true residual of the same operator sits a few times above the estimate
