@@ -276,6 +276,9 @@ def run_gpu(args):
     tune_choices, tune_ms = plan.tune(reps=3)   # autotuned launch shapes (part of the setup)
     tune_s = time.perf_counter() - t0
     st = plan.stats()
+    up_modes = [int(tune_choices[32 + d]) for d in range(3, st["levels"])]
+    up_kernel = ("k_up_warp" if all(m == 1 for m in up_modes) else
+                 "k_up_runs" if all(m == 0 for m in up_modes) else "k_up_runs+k_up_warp")
     N = prob.n
     x, _, _ = prob.nodes()
     # the 64 incidences of the batched configuration (32 Fibonacci directions x 2 polarisations);
@@ -379,9 +382,9 @@ def run_gpu(args):
         achieved = per_launch / (dom_ms / dom_calls / 1e3) / 1e12
         peak = alu_peak_tflops(sm_mhz)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(KERNEL_NAMES[dom], args.workload),
+                "traffic": recorded_traffic(up_kernel if dom == "up" else KERNEL_NAMES[dom], args.workload),
                 "peak_source": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flops x {sm_mhz:.0f} MHz (median sampled)"}
-    roof["kernel"] = {"target": "k_target (c)", "up": "k_up_runs (b)", "leaf": "k_leaf (a)", "near": "k_near (d)"}[dom]
+    roof["kernel"] = {"target": "k_target (c)", "up": f"{up_kernel} (b)", "leaf": "k_leaf (a)", "near": "k_near (d)"}[dom]
     roof["per_launch_work"] = per_launch
     roof["launches"] = int(dom_calls)
     if roof["traffic"] is not None:
@@ -422,7 +425,12 @@ def run_gpu(args):
                                              for d in range(3, st["levels"] + 1)},
                    "target_ms_per_level": {str(d): [round(float(tune_ms[2 * d]), 3), round(float(tune_ms[2 * d + 1]), 3)]
                                            for d in range(3, st["levels"] + 1)},
-                   "near_threads": int(tune_choices[25])},
+                   "near_threads": int(tune_choices[25]),
+                   "upward_step_per_level": {str(d): ("warp per slot" if tune_choices[32 + d] == 1 else "group runs")
+                                             for d in range(3, st["levels"])},
+                   "upward_ms_per_level": {str(d): [round(float(tune_ms[64 + 2 * d]), 3),
+                                                    round(float(tune_ms[65 + 2 * d]), 3)]
+                                           for d in range(3, st["levels"])}},
     }
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(prob, delta, budget_s=args.cpu_budget)
@@ -508,6 +516,13 @@ def run_apply(args):
                                  precision=PRECISIONS[args.precision], far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0,
                                  max_krylov=10, upward_tc=args.upward_tc)
     setup = time.perf_counter() - t0
+    tuned = None
+    if args.tune:   # the solve step's autotuned launch shapes
+        ch, _ = plan.tune(reps=3)
+        lv = plan.stats()["levels"]
+        tuned = {"target_box_chunks_per_level": [int(v) for v in ch[3:lv + 1]],
+                 "upward_warp_per_slot_per_level": [int(v) for v in ch[35:32 + lv]],
+                 "near_threads": int(ch[25])}
     y = torch.from_numpy(random_densities(prob.n, 1)).cuda()
     out = torch.empty_like(y)
     for _ in range(args.warmup):
@@ -524,7 +539,7 @@ def run_apply(args):
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     st = plan.stats()
     plan.close()
-    return {"mode": "apply", "workload": WORKLOADS[args.workload], "applies": args.steps,
+    return {"mode": "apply", "workload": WORKLOADS[args.workload], "applies": args.steps, "tuned": tuned,
             "precision": args.precision, "upward": "tensor cores (tcgen05)" if args.upward_tc else "SIMT",
             "ms_per_forward_map": ms, "unknown_matvecs_per_s": 4.0 * prob.n / (ms / 1e3),
             "stage_ms_per_apply": {k: v[0] / max(args.steps, 1) for k, v in kt.items()},
@@ -830,7 +845,8 @@ def run_compare(args):
     right-hand side solved with the plain FP64 direct far sum (the unaccelerated operator on the
     GPU) to --tol, then with the FP32, mixed and FP64 IFGF forward maps, each tolerance halved
     (up to five times) until the true residual |b - A y|/|b|, measured with the FP64 direct
-    operator, is no larger than the plain method's."""
+    operator, is no larger than the plain method's; and the FP32 IFGF solve with mixed-precision
+    refinement whose residuals the plain FP64 operator forms, to the plain method's residual."""
     import torch
     import paper_2408_02274_gb300 as lib
     from paper_2408_02274_gb300 import build as libbuild
@@ -879,8 +895,21 @@ def run_compare(args):
         r["tolerances_tried"] = tries
         rows[name] = r
         plan.close()
+    # mixed-precision iterative refinement: GMRES on the FP32 IFGF map, residuals formed by the
+    # plain FP64 operator itself, solved to the plain method's own final residual
+    plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
+                                 far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_krylov,
+                                 gmres_scaling=args.gmres_scaling, refine=5)
+    plan.set_residual(ref)
+    r = timed_solve(plan, target)
+    r["residual_plan"] = "the plain FP64 direct operator (relres_estimate is the residual it formed)"
+    rows["ifgf_fp32_refined"] = r
+    plan.set_residual(None)
+    plan.close()
     ref.close()
     rows["speedup_ifgf_fp32_vs_direct_fp64"] = rows["direct_fp64"]["seconds"] / rows["ifgf_fp32"]["seconds"]
+    rows["speedup_ifgf_fp32_refined_vs_direct_fp64"] = (rows["direct_fp64"]["seconds"]
+                                                        / rows["ifgf_fp32_refined"]["seconds"])
     return {"mode": "compare", "workload": WORKLOADS[args.workload], "tol_plain": args.tol,
             "equal_residual_target": target, **rows}
 
@@ -923,7 +952,8 @@ def run_waveguide(args):
     prec = PRECISIONS[args.precision]
     plan = lib.Plan.from_problem(prob, delta=delta, n_beta=48, cov_d=4.0, precision=prec,
                                  far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=args.max_krylov,
-                                 max_leaf_pts=args.leaf_pts, gmres_scaling=args.gmres_scaling, gs_iters=args.gs_iters)
+                                 max_leaf_pts=args.leaf_pts, gmres_scaling=args.gmres_scaling, gs_iters=args.gs_iters,
+                                 refine=args.refine)
     torch.cuda.synchronize()
     setup = time.perf_counter() - t0
     st = plan.stats()
@@ -932,6 +962,7 @@ def run_waveguide(args):
            "n": N, "unknowns": 4 * N, "patches": prob.num_patches, "delta": delta,
            "patch_diameter_quantiles": [float(v) for v in np.quantile(diam, [0.0, 0.5, 1.0])],
            "max_leaf_pts": args.leaf_pts, "gmres_scaling": args.gmres_scaling, "gs_iters": args.gs_iters,
+           "refine": args.refine,
            "host_geometry_s": t_host,
            "setup_s": setup, "setup_parts_s": st["setup_parts_s"],
            "device_bytes": st["device_bytes"], "levels": st["levels"], "near_nnz": st["near_nnz"],
@@ -974,7 +1005,14 @@ def run_waveguide(args):
         its, rrs, stt = plan.solve_batch(incd, ys, tol=args.tol, max_iter=args.max_krylov)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        res["solve"] = {"tol": args.tol, "max_iter": args.max_krylov, "iters": its[0], "relres_estimate": rrs[0],
+        # |b - A y| / |b| with the plan's own map (refinement reports this; GMRES alone its Arnoldi estimate)
+        b = torch.empty_like(ys)
+        plan.rhs(incd, b)
+        Ay = torch.empty_like(ys)
+        plan.apply_batch(ys, Ay)
+        own = float(torch.linalg.norm(b - Ay) / torch.linalg.norm(b))
+        res["solve"] = {"tol": args.tol, "max_iter": args.max_krylov, "refine": args.refine, "iters": its[0],
+                        "relres_reported": rrs[0], "relres_of_own_map": own,
                         "status": int(stt), "seconds": dt, "unknown_matvecs_per_s": 4.0 * N * its[0] / dt}
     plan.close()
     return res
@@ -1011,6 +1049,9 @@ def main():
     ap.add_argument("--gs-iters", type=int, default=20, help="golden-section steps of the closest-point search")
     ap.add_argument("--bar-length", type=float, default=20.0)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed", "fp64"])
+    ap.add_argument("--refine", type=int, default=0,
+                    help="waveguide mode: residual refinement sweeps after GMRES (plan option refine)")
+    ap.add_argument("--tune", action="store_true", help="apply mode: autotune the plan's launch shapes first")
     ap.add_argument("--upward-tc", type=int, default=0, choices=[0, 1],
                     help="apply mode: the upward step on the tensor cores (plan option upward_tc)")
     args = ap.parse_args()

@@ -40,7 +40,7 @@ enum {
   IFGF_ENOMEM = 2,        /* a host or device allocation failed (plan_create only) */
   IFGF_ECUDA = 3,         /* a CUDA call failed; the plan is poisoned */
   IFGF_ENOCONV = 4,       /* GMRES reached max_iter above the tolerance (y still written) */
-  IFGF_ETIMEOUT = 5,      /* reserved: a bounded device wait expired */
+  IFGF_ETIMEOUT = 5,      /* a bounded device wait expired (ifgf_plan_check, the solves) */
   IFGF_EUNSUPPORTED = 6,  /* the combination of options is not implemented */
   IFGF_EINTERNAL = 7      /* an internal consistency check failed */
 };
@@ -98,6 +98,14 @@ typedef struct {
   int32_t upward_tc;       /* 1: the upward step (b) of the FP32 IFGF kernels as TF32 contractions on
                               the tensor cores (tcgen05; same results to FP32 rounding); 0: FP32 SIMT
                               contractions (default: faster here, see the header of k_up_tc) */
+  int32_t refine;          /* residual refinement of the solves (bie_solve*), 0..20 sweeps: after
+                              GMRES, r = b - A_r y is formed in FP64, A_r the map of the residual
+                              plan (ifgf_plan_set_residual; this plan's own map without one), and
+                              while |r| / |b| > tol and still falling, GMRES with this plan's map
+                              (cold start) solves A d = r to the relative accuracy that brings |r|
+                              to tol |b| and y += d.  The solves then report the formed residual,
+                              not the Arnoldi estimate, and iters sums the sweeps.  0: GMRES alone.
+                              Two more [batch][4N] complex vectors are allocated */
 } ifgf_plan_desc;
 
 /*
@@ -235,6 +243,9 @@ ifgf_status ifgf_apply_fields(ifgf_plan plan, const void* phi, void* f28, int32_
  * (<= 1000).  iters / relres (host pointers, may be NULL) receive the
  * iteration count and the final relative residual estimate.  Returns
  * IFGF_ENOCONV if tol was not reached (y holds the last iterate).
+ * With the plan's refine > 0, GMRES is followed by residual refinement:
+ * relres is then |b - A y| / |b| formed from the map, iters the Krylov
+ * dimensions summed over the sweeps, max_iter the bound of each sweep.
  * Synchronises `stream` (one scalar is read back per iteration).
  */
 ifgf_status bie_solve(ifgf_plan plan, const void* inc, double tol, int32_t max_iter, void* y,
@@ -271,6 +282,36 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
                            const void* const* incs, double tol, int32_t max_iter, void* const* ys,
                            int32_t* const* iters, double* const* relres, ifgf_status* status,
                            const ifgf_stream* streams);
+
+/*
+ * Device status of a plan.  The one device-side wait of the library, the tensor-core upward
+ * step (upward_tc = 1) waiting for its MMAs, gives up after 1 s, records the timeout in the
+ * plan's device status word, releases its tensor memory and leaves the step's output unwritten;
+ * the context stays usable.  ifgf_plan_check synchronises `stream`, reads and clears that word
+ * and returns IFGF_ETIMEOUT (with a message) if a wait expired in work queued on the plan since
+ * the last check (the results of those applies are then not valid), else IFGF_OK.  The solves
+ * (bie_solve*) check it before they return and report IFGF_ETIMEOUT in the same way.
+ */
+ifgf_status ifgf_plan_check(ifgf_plan plan, ifgf_stream stream);
+
+/*
+ * Residual plan of the refinement (plan field refine): mixed-precision iterative refinement
+ * forms r = b - A_r y with `residual`'s map (e.g. an FP64 IFGF plan, or the plain FP64 direct
+ * sum, IFGF_FAR_DIRECT, of the same body) while GMRES runs on `plan`'s (FP32) map.  The
+ * residual then falls below the FP32 map's own rounding floor, down to tol against A_r.
+ * `residual` must have the same nodes (N) and a batch at least `plan`'s, must not itself have a
+ * residual plan, must outlive the link (NULL unlinks) and must not be applied by another solve
+ * at the same time (bie_solve_many refuses plans that share one).  IFGF_EINVAL otherwise.
+ */
+ifgf_status ifgf_plan_set_residual(ifgf_plan plan, ifgf_plan residual);
+
+/*
+ * Fault injection for the timeout path (no GPU fault involved).  which = 1: the tensor-core
+ * upward step issues no MMA for the first unit of each block, so the wait for it expires (the
+ * waits of this plan then give up after 1 ms instead of 1 s); which = 0: off.  Applies made
+ * while it is on give invalid results and set the status word that ifgf_plan_check reports.
+ */
+ifgf_status ifgf_plan_inject(ifgf_plan plan, int32_t which);
 
 /*
  * Right-hand side of Eq. lin_system: b_r = omega^{-1} (n x E^inc_r, n x H^inc_r) projected on
@@ -396,11 +437,14 @@ ifgf_status ifgf_far_field(ifgf_plan plan, int32_t nrhs, const void* y, int32_t 
  *   - per octree level d of an FP32 or mixed IFGF plan, the target step (c) as a warp per target
  *     or a warp per chunk of 32 targets of one box (choices[d]: 0 or 1; times_ms[2d], [2d+1]:
  *     ms per launch of each);
- *   - the near-field matvec's block size, 128 or 256 threads (choices[25]; times_ms[50], [51]).
- * reps: timed launches per candidate (after one warm-up), 1..1000.  choices: host int32 [26]
- * or NULL (-1 where not applicable); times_ms: host float [52] or NULL.  Results of later applies
- * are unchanged up to summation order (the target step's grouping differs between the two
- * shapes).  Synchronises `stream`; overwrites the plan's per-apply buffers (call it between
+ *   - the near-field matvec's block size, 128 or 256 threads (choices[25]; times_ms[50], [51]);
+ *   - per parent level d of an FP32 or mixed IFGF plan without the tensor-core option, the
+ *     upward step (b) into d by runs of point groups or by a warp per parent slot
+ *     (choices[32 + d]: 0 or 1; times_ms[64 + 2d], [65 + 2d]).
+ * reps: timed launches per candidate (after one warm-up), 1..1000.  choices: host int32 [64]
+ * or NULL (-1 where not applicable); times_ms: host float [128] or NULL.  Results of later
+ * applies are unchanged up to summation order (the target step's grouping differs between its
+ * two shapes; the upward step's two shapes sum each parent value in a different order).  Synchronises `stream`; overwrites the plan's per-apply buffers (call it between
  * applies, not during a capture).  IFGF_EINVAL for reps out of range; IFGF_ECUDA poisons the plan.
  */
 ifgf_status ifgf_plan_tune(ifgf_plan plan, int32_t reps, int32_t* choices, float* times_ms, ifgf_stream stream);

@@ -28,7 +28,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_ba
            "ifgf_plan_stats", "ifgf_plan_estimate", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
            "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_far_direct_noalloc", "ifgf_far_field",
-           "ifgf_plan_tune"]
+           "ifgf_plan_tune", "ifgf_plan_check", "ifgf_plan_inject", "ifgf_plan_set_residual"]
 
 
 class ifgf_plan_desc(ctypes.Structure):
@@ -45,7 +45,7 @@ class ifgf_plan_desc(ctypes.Structure):
         ("delta", ctypes.c_double), ("n_beta", ctypes.c_int32), ("cov_d", ctypes.c_double),
         ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
         ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_leaf_pts", ctypes.c_int32),
-        ("gmres_scaling", ctypes.c_int32), ("upward_tc", ctypes.c_int32),
+        ("gmres_scaling", ctypes.c_int32), ("upward_tc", ctypes.c_int32), ("refine", ctypes.c_int32),
     ]
 
 
@@ -136,6 +136,9 @@ def load(path: str = LIB_PATH):
     lib.ifgf_far_direct_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     lib.ifgf_far_field.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     lib.ifgf_plan_tune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), vp]
+    lib.ifgf_plan_check.argtypes = [vp, vp]
+    lib.ifgf_plan_inject.argtypes = [vp, i32]
+    lib.ifgf_plan_set_residual.argtypes = [vp, vp]
     for name in EXPORTS:
         if name != "ifgf_status_string":
             getattr(lib, name).restype = ctypes.c_int32
@@ -204,13 +207,13 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                      gs_iters: int = 20, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                      max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0,
-                     gmres_scaling: int = 0, upward_tc: int = 0):
+                     gmres_scaling: int = 0, upward_tc: int = 0, refine: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
               leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-              max_leaf_pts, gmres_scaling, upward_tc)
+              max_leaf_pts, gmres_scaling, upward_tc, refine)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h
@@ -218,12 +221,12 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
 
 def _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
           leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch, max_leaf_pts,
-          gmres_scaling, upward_tc=0):
+          gmres_scaling, upward_tc=0, refine=0):
     ng = int(arrs[3].shape[1])
     return ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
                           k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
                           min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-                          max_leaf_pts, gmres_scaling, upward_tc)
+                          max_leaf_pts, gmres_scaling, upward_tc, refine)
 
 
 def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: float, k_int: float,
@@ -232,13 +235,13 @@ def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext
                        leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                        gs_iters: int = 20, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                        max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0, gmres_scaling: int = 0,
-                       upward_tc: int = 0) -> dict:
+                       upward_tc: int = 0, refine: int = 0) -> dict:
     """ifgf_plan_estimate: the device memory ifgf_plan_create would allocate for the same
     arguments (host work only; near-matrix figures are upper bounds)."""
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
               leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-              max_leaf_pts, gmres_scaling, upward_tc)
+              max_leaf_pts, gmres_scaling, upward_tc, refine)
     e = ifgf_plan_estimate_t()
     _check(load().ifgf_plan_estimate(ctypes.byref(d), ctypes.byref(e)), "ifgf_plan_estimate")
     out = {name: getattr(e, name) for name, _ in ifgf_plan_estimate_t._fields_ if name != "cones"}
@@ -265,13 +268,30 @@ def ifgf_apply_batch(plan, y, out, stream=None):
 
 
 def ifgf_plan_tune(plan, reps: int = 5, stream=None):
-    """Autotune the plan's launch shapes; returns (choices [26] int32, times_ms [52] float32)."""
-    ch = np.zeros(26, dtype=np.int32)
-    tm = np.zeros(52, dtype=np.float32)
+    """Autotune the plan's launch shapes; returns (choices [64] int32, times_ms [128] float32)."""
+    ch = np.zeros(64, dtype=np.int32)
+    tm = np.zeros(128, dtype=np.float32)
     _check(load().ifgf_plan_tune(plan, int(reps), ch.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                  tm.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream(stream)),
            "ifgf_plan_tune")
     return ch, tm
+
+
+def ifgf_plan_check(plan, stream=None):
+    """Synchronise the stream and raise IfgfError (IFGF_ETIMEOUT) if a bounded device wait of the
+    plan expired since the last check (its device status word is cleared)."""
+    _check(load().ifgf_plan_check(plan, _stream(stream)), "ifgf_plan_check")
+
+
+def ifgf_plan_set_residual(plan, residual):
+    """Residual plan of the refinement (None unlinks): the solves form b - A y with its map."""
+    _check(load().ifgf_plan_set_residual(plan, residual), "ifgf_plan_set_residual")
+
+
+def ifgf_plan_inject(plan, which: int):
+    """Fault injection for the timeout path: 1 makes the tensor-core upward step skip its first
+    MMAs so that its (1 ms) wait expires; 0 turns it off."""
+    _check(load().ifgf_plan_inject(plan, int(which)), "ifgf_plan_inject")
 
 
 def ifgf_far_field(plan, y, dirs, out, stream=None):
@@ -616,6 +636,18 @@ class Plan:
 
     def tune(self, reps: int = 5, stream=None):
         return ifgf_plan_tune(self.handle, reps, stream)
+
+    def check(self, stream=None):
+        ifgf_plan_check(self.handle, stream)
+
+    def inject(self, which: int):
+        ifgf_plan_inject(self.handle, which)
+
+    def set_residual(self, other):
+        """Form the refinement residual with `other`'s map (a Plan of the same body, or None);
+        `other` is kept alive while linked."""
+        ifgf_plan_set_residual(self.handle, other.handle if other is not None else None)
+        self._resid = other
 
     def far_field(self, y, dirs, out, stream=None):
         ifgf_far_field(self.handle, y, dirs, out, stream)

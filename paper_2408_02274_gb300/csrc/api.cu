@@ -2,6 +2,7 @@
 // kernels), forward map, raw scalar fields, GMRES solve, stats.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -131,9 +132,16 @@ ifgf_status validate(const ifgf_plan_desc* d) {
   if (d->max_leaf_pts < 0 || d->max_leaf_pts > 1000000) return IFGF_EINVAL;
   if (d->gmres_scaling < 0 || d->gmres_scaling > 1) return IFGF_EINVAL;
   if (d->upward_tc < 0 || d->upward_tc > 1) return IFGF_EINVAL;
+  if (d->refine < 0 || d->refine > 20) return IFGF_EINVAL;
   if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
   if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
   return IFGF_OK;
+}
+
+// The FP32 upward step into level L can run by units (the points of one octant in one child
+// cone): the unit tables go to the device for FP32 and mixed IFGF plans.
+bool unit_tables(const ifgf_plan_desc& d, const HostLevel& L) {
+  return !ifgf64(d) && d.far_mode == IFGF_FAR_IFGF && L.tc_unit_ptr.size() > 1;
 }
 
 // The upward step into level L runs on the tensor cores when the plan asks for it (upward_tc),
@@ -327,11 +335,13 @@ void build(ifgf_plan_t* p) {
     Dl.up_order = A.upload(L.up_order);
     Dl.up_task = A.upload(L.up_task);
     Dl.up_task_ptr = A.upload(L.up_task_ptr);
-    if (upward_tc(d, L)) {
-      Dl.tc = true;
+    if (unit_tables(d, L)) {   // the FP32 upward step by units (warp per slot, or tensor cores)
       Dl.tc_order = A.upload(L.tc_order);
       Dl.tc_unit = A.upload(L.tc_unit);
       Dl.tc_unit_ptr = A.upload(L.tc_unit_ptr);
+    }
+    if (upward_tc(d, L)) {
+      Dl.tc = true;
       Dl.tc_item = A.upload(L.tc_item);
       Dl.ntc_items = (int)(L.tc_item.size() / kTcBoxes);
     }
@@ -416,6 +426,10 @@ void build(ifgf_plan_t* p) {
   G.b = A.dev<double>(2 * n4 * B);
   G.y = A.dev<double>(2 * n4 * B);
   G.inc = A.dev<double>(12 * (size_t)N * B);
+  if (d.refine > 0) {
+    G.y_acc = A.dev<double>(2 * n4 * B);
+    G.b_orig = A.dev<double>(2 * n4 * B);
+  }
   G.active = A.dev<int>(B);
   G.kfin = A.dev<int>(B);
   check(cudaMallocHost(&G.hres, 8 * B * sizeof(double)), "pinned scalars");
@@ -520,7 +534,7 @@ const char* ifgf_status_string(ifgf_status s) {
     case IFGF_ENOMEM: return "out of memory";
     case IFGF_ECUDA: return g_last_err[0] ? g_last_err : "CUDA error";
     case IFGF_ENOCONV: return "GMRES did not reach the tolerance";
-    case IFGF_ETIMEOUT: return "device wait timed out";
+    case IFGF_ETIMEOUT: return (g_detail_status == s && g_detail[0]) ? g_detail : "device wait timed out";
     case IFGF_EUNSUPPORTED: return (g_detail_status == s && g_detail[0]) ? g_detail : "unsupported option";
     case IFGF_EINTERNAL: return (g_detail_status == s && g_detail[0]) ? g_detail : "internal error";
     default: return "unknown status";
@@ -646,12 +660,12 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
       tb.dev<int32_t>(L.up_order.size());
       tb.dev<int32_t>(L.up_task.size());
       tb.dev<int32_t>(L.up_task_ptr.size());
-      if (upward_tc(d, L)) {
+      if (unit_tables(d, L)) {
         tb.dev<int32_t>(L.tc_order.size());
         tb.dev<int32_t>(L.tc_unit.size());
         tb.dev<int32_t>(L.tc_unit_ptr.size());
-        tb.dev<int32_t>(L.tc_item.size());
       }
+      if (upward_tc(d, L)) tb.dev<int32_t>(L.tc_item.size());
       tb.dev<double2>((size_t)L.na);
       tb.dev<double2>(2 * (size_t)L.na);
       tb.dev<int64_t>(L.tgt_ptr.size());
@@ -679,6 +693,8 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
     gm.dev<double>(8 * B);
     for (int k = 0; k < 3; ++k) gm.dev<double>(2 * n4 * B);
     gm.dev<double>(12 * (size_t)N * B);
+    if (d.refine > 0)
+      for (int k = 0; k < 2; ++k) gm.dev<double>(2 * n4 * B);
     gm.dev<int>(B);
     gm.dev<int>(B);
     out->bytes_geometry = g.total;
@@ -699,8 +715,14 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
   return IFGF_OK;
 }
 
+static void unlink_residual(ifgf_plan_t* p);
+
 ifgf_status ifgf_plan_destroy(ifgf_plan plan) {
   if (!plan) return IFGF_OK;
+  // residual-plan links in both directions end with the plan
+  unlink_residual(plan);
+  for (ifgf_plan_t* q : plan->resid_of) q->resid = nullptr;
+  plan->resid_of.clear();
   cudaDeviceSynchronize();
   free_all(plan);
   delete plan;
@@ -822,9 +844,9 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
   cudaError_t e = cudaSuccess;
   try {
     if (choices)
-      for (int k = 0; k < 26; ++k) choices[k] = -1;
+      for (int k = 0; k < 64; ++k) choices[k] = -1;
     if (times_ms)
-      for (int k = 0; k < 52; ++k) times_ms[k] = 0.f;
+      for (int k = 0; k < 128; ++k) times_ms[k] = 0.f;
     // (c): per level, a warp per target or per box chunk
     if (p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
       for (int d = 3; d <= p->tree.D && e == cudaSuccess; ++d) {
@@ -837,6 +859,23 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
         if (times_ms && d < 25) {
           times_ms[2 * d] = t[0] / reps;
           times_ms[2 * d + 1] = t[1] / reps;
+        }
+      }
+    }
+    // (b): per parent level, the FP32 SIMT upward step by point-group runs or a warp per slot
+    if (e == cudaSuccess && p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
+      for (int d = 3; d < p->tree.D && e == cudaSuccess; ++d) {
+        DevLevel& Pp = p->dl[d];
+        if (Pp.tc || !Pp.tc_unit_ptr || Pp.nslots == 0) continue;
+        float t[2] = {0.f, 0.f};
+        for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+          e = time_ms(s, reps, [&]() { return launch_up_level(p, d, m, s); }, &t[m]);
+        if (e != cudaSuccess) break;
+        Pp.up_mode = t[1] < t[0] ? 1 : 0;
+        if (choices && d < 25) choices[32 + d] = Pp.up_mode;
+        if (times_ms && d < 25) {
+          times_ms[64 + 2 * d] = t[0] / reps;
+          times_ms[65 + 2 * d] = t[1] / reps;
         }
       }
     }
@@ -888,6 +927,82 @@ ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t w
   return IFGF_OK;
 }
 
+// Reads and clears the plan's device status word (after the work queued on s); *word = its value.
+static cudaError_t take_status_word(ifgf_plan_t* p, cudaStream_t s, int* word) {
+  *word = 0;
+  cudaError_t e = cudaMemcpyAsync(word, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && *word != 0) e = cudaMemsetAsync(p->dev_err, 0, sizeof(int), s);
+  return e;
+}
+
+static const char* kTimeoutMsg =
+    "a bounded tensor-core wait of the upward step (upward_tc) expired; the results of the applies "
+    "queued since the last check are not valid";
+
+// Residual refinement after GMRES (plan field refine): r = b - A y is formed in FP64 from the
+// residual plan's map (ifgf_plan_set_residual; the plan's own map without one); while |r| / |b|
+// > tol and falling (by at least 10% a sweep), GMRES with the plan's own map solves
+// A d = r from zero to the relative accuracy 0.5 tol |b| / |r| and y += d.  A sweep that does not
+// lower a right-hand side's residual is undone for it.  On return p->gm.y holds y, rr the formed
+// residuals and it the Krylov dimensions summed over the sweeps.  Right-hand sides that are done
+// enter the next GMRES with b = 0, which freezes them at zero iterations.
+static cudaError_t refine(ifgf_plan_t* p, int nrhs, double tol, int max_iter, const MatvecFn& mv,
+                          const MatvecFn* pc, bool scaled, double cm, double cj, std::vector<int>& it,
+                          std::vector<double>& rr, cudaStream_t s) {
+  GmresWork& G = p->gm;
+  ifgf_plan_t* q = p->resid ? p->resid : p;   // the map that forms the residual
+  if (q->poisoned) return cudaErrorInvalidResourceHandle;
+  const size_t n2 = 8 * (size_t)p->N;   // doubles per right-hand side
+  const size_t bytes = sizeof(double) * n2 * nrhs;
+  // b_orig: the right-hand side; y_acc: the solution so far; G.b: after each GMRES, a copy of
+  // y_acc before the correction (restored exactly for a right-hand side the sweep did not help)
+  cudaError_t e = cudaMemcpyAsync(G.b_orig, G.b, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G.y_acc, G.y, bytes, cudaMemcpyDeviceToDevice, s);
+  std::vector<double> prev(nrhs, HUGE_VAL);
+  std::vector<int> go(nrhs, 0), it2(nrhs, 0);
+  std::vector<double> rr2(nrhs, 0.0);
+  for (int sweep = 0; e == cudaSuccess; ++sweep) {
+    e = forward(q, G.y_acc, G.w, nrhs, s);
+    if (e == cudaSuccess) e = gmres_residual(p, nrhs, G.b_orig, G.w, G.w, s);   // r in G.w
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G.hres, G.scal, sizeof(double) * 8 * nrhs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    double tol_in = 0.5;
+    int active = 0;
+    for (int r = 0; r < nrhs && e == cudaSuccess; ++r) {
+      const double nb = G.hres[8 * r + 4], nr = G.hres[8 * r + 3];
+      const double rel = nb > 0 ? nr / nb : 0.0;
+      if (sweep > 0 && go[r] && !(rel < prev[r])) {
+        // no gain: back to the solution before this sweep (its residual is prev[r])
+        e = cudaMemcpyAsync(G.y_acc + r * n2, G.b + r * n2, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s);
+        go[r] = 0;
+      } else {
+        go[r] = rel > tol && (sweep == 0 || rel < 0.9 * prev[r]) && sweep < p->desc.refine;
+        rr[r] = rel;
+        prev[r] = rel;
+      }
+      if (go[r]) {
+        ++active;
+        tol_in = std::min(tol_in, 0.5 * tol / rel);
+      }
+    }
+    if (e != cudaSuccess || active == 0) break;
+    // GMRES on A d = r for the right-hand sides still going (b = 0 freezes the others at d = 0)
+    e = cudaMemcpyAsync(G.b, G.w, bytes, cudaMemcpyDeviceToDevice, s);
+    for (int r = 0; r < nrhs && e == cudaSuccess; ++r)
+      if (!go[r]) e = cudaMemsetAsync(G.b + r * n2, 0, sizeof(double) * n2, s);
+    if (e == cudaSuccess)
+      e = gmres_run(p, mv, nrhs, std::max(tol_in, 1e-14), max_iter, it2.data(), rr2.data(), s, pc);
+    if (e == cudaSuccess && scaled) e = launch_block_scale(p->N, nrhs, cm, cj, G.y, G.y, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(G.b, G.y_acc, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = gmres_accumulate(p, nrhs, G.y, G.y_acc, s, false);
+    for (int r = 0; r < nrhs; ++r) it[r] += it2[r];
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G.y, G.y_acc, bytes, cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
 static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
                               int32_t* iters, double* relres, ifgf_stream stream, bool flexible) {
   if (!p || !inc || !y || !(tol > 0) || max_iter < 1) return IFGF_EINVAL;
@@ -923,6 +1038,8 @@ static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double
     };
     e = gmres_run(p, mv, nrhs, tol, max_iter, it.data(), rr.data(), s, flexible ? &pc : nullptr);
     if (e == cudaSuccess && scaled) e = launch_block_scale(p->N, nrhs, cm, cj, p->gm.y, p->gm.y, s);
+    if (e == cudaSuccess && p->desc.refine > 0)
+      e = refine(p, nrhs, tol, max_iter, mv, flexible ? &pc : nullptr, scaled, cm, cj, it, rr, s);
   }
   if (e == cudaSuccess) {
     if (is_device_ptr(y))
@@ -930,11 +1047,16 @@ static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double
     else
       e = cudaMemcpyAsync(y, p->gm.y, sizeof(double) * 2 * n4 * nrhs, cudaMemcpyDeviceToHost, s);
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int word = 0;
+  if (e == cudaSuccess) e = take_status_word(p, s, &word);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "bie_solve", __FILE__, __LINE__);
     p->poisoned = true;
     return IFGF_ECUDA;
+  }
+  if (word != 0) {
+    set_status_detail(IFGF_ETIMEOUT, kTimeoutMsg);
+    return IFGF_ETIMEOUT;
   }
   bool all = true;
   for (int r = 0; r < nrhs; ++r) {
@@ -943,6 +1065,52 @@ static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double
     all = all && rr[r] <= tol;
   }
   return all ? IFGF_OK : IFGF_ENOCONV;
+}
+
+ifgf_status ifgf_plan_check(ifgf_plan p, ifgf_stream stream) {
+  if (!p) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  int word = 0;
+  cudaError_t e = take_status_word(p, (cudaStream_t)stream, &word);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_plan_check", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  if (word != 0) {
+    set_status_detail(IFGF_ETIMEOUT, kTimeoutMsg);
+    return IFGF_ETIMEOUT;
+  }
+  return IFGF_OK;
+}
+
+static void unlink_residual(ifgf_plan_t* p) {
+  if (!p->resid) return;
+  auto& v = p->resid->resid_of;
+  v.erase(std::remove(v.begin(), v.end(), p), v.end());
+  p->resid = nullptr;
+}
+
+ifgf_status ifgf_plan_set_residual(ifgf_plan p, ifgf_plan r) {
+  if (!p || r == p) return IFGF_EINVAL;
+  if (r && (r->N != p->N || r->batch < p->batch || r->resid || !p->resid_of.empty())) return IFGF_EINVAL;
+  try {
+    if (r) r->resid_of.reserve(r->resid_of.size() + 1);
+  } catch (const std::bad_alloc&) {
+    return IFGF_ENOMEM;
+  }
+  unlink_residual(p);
+  if (r) {
+    r->resid_of.push_back(p);
+    p->resid = r;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_plan_inject(ifgf_plan p, int32_t which) {
+  if (!p || which < 0 || which > 1) return IFGF_EINVAL;
+  p->inject = which;
+  return IFGF_OK;
 }
 
 ifgf_status bie_rhs(ifgf_plan p, int32_t nrhs, const void* inc, void* b, ifgf_stream stream) {
@@ -1132,6 +1300,10 @@ ifgf_status bie_solve_many(int32_t nplans, const ifgf_plan* plans, const int32_t
     for (int j = 0; j < i; ++j) {
       if (plans[j] == plans[i]) return IFGF_EINVAL;
       if (streams && streams[i] && streams[j] == streams[i]) return IFGF_EINVAL;
+      // a residual plan's buffers serve one solve at a time
+      if (plans[i]->resid && (plans[i]->resid == plans[j] || plans[i]->resid == plans[j]->resid))
+        return IFGF_EINVAL;
+      if (plans[j]->resid == plans[i]) return IFGF_EINVAL;
     }
   }
   int dev = 0;

@@ -170,6 +170,15 @@ __global__ void k_scale_copy(int64_t n, const double* __restrict__ src, const do
   dst[2 * i + 1] = src[2 * i + 1] * f;
 }
 
+// r_rb = b_rb - w_rb (sub = 1) or r_rb += w_rb (sub = 0), n2 doubles per right-hand side; b and r
+// may be the same array
+__global__ void k_sub_add(int64_t n2, const double* b, const double* w, double* r, int sub) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n2) return;
+  const size_t o = blockIdx.y * (size_t)n2 + i;
+  r[o] = sub ? b[o] - w[o] : r[o] + w[o];
+}
+
 // |w_rb|^2 partials -> out_rb = |w_rb|; one block per right-hand side
 __global__ void k_norm_final(int nblk, const double* __restrict__ part, size_t pstride, double* __restrict__ out) {
   if (threadIdx.x != 0) return;
@@ -302,6 +311,28 @@ cudaError_t project(GmresWork& G, const Batch& B, const Arnoldi& R, int k1, int 
 }
 
 }  // namespace
+
+cudaError_t gmres_residual(ifgf_plan_t* p, int nrhs, const double* b, const double* w, double* r,
+                           cudaStream_t s) {
+  GmresWork& G = p->gm;
+  const int64_t n = 4 * (int64_t)p->N;
+  const int nb = dots_blocks(n);
+  const size_t pstride = 2 * (size_t)nb * (G.max_iter + 1);
+  k_sub_add<<<dim3((unsigned)((2 * n + 255) / 256), nrhs), 256, 0, s>>>(2 * n, b, w, r, 1);
+  k_dots<<<dim3(nb, 1, nrhs), kDotThreads, 0, s>>>(n, 1, r, 0, r, G.part, pstride);
+  k_norm_final<<<nrhs, 32, 0, s>>>(nb, G.part, pstride, G.scal + 3);
+  k_dots<<<dim3(nb, 1, nrhs), kDotThreads, 0, s>>>(n, 1, b, 0, b, G.part, pstride);
+  k_norm_final<<<nrhs, 32, 0, s>>>(nb, G.part, pstride, G.scal + 4);
+  p->launches += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t gmres_accumulate(ifgf_plan_t* p, int nrhs, const double* d, double* y, cudaStream_t s, bool subtract) {
+  const int64_t n2 = 8 * (int64_t)p->N;
+  k_sub_add<<<dim3((unsigned)((n2 + 255) / 256), nrhs), 256, 0, s>>>(n2, y, d, y, subtract ? 1 : 0);
+  ++p->launches;
+  return cudaGetLastError();
+}
 
 cudaError_t gmres_run(ifgf_plan_t* p, const MatvecFn& matvec, int nrhs, double tol, int max_iter, int* iters,
                       double* relres, cudaStream_t s, const MatvecFn* precond) {

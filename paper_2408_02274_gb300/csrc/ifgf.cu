@@ -543,6 +543,142 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32);
 }
 
+// (b), FP32 variant with a warp per parent slot.  The warp walks the slot's units (the points of
+// one octant that fall in one child cone, at most kUpRunMax of them, from the unit tables): it
+// loads the child cone's 75 x 32 coefficients once per unit into registers (75 per lane) and
+// sweeps the unit's points with the separable contraction of k_up_runs.  Owning the whole slot,
+// the warp adds every octant's contributions into its own parent values with plain shared-memory
+// adds, so the units need no split by point groups (about 3.2 units per octant against 8.2 runs
+// per octant in k_up_runs, at 23 points per unit on average) and no block barrier follows the
+// prologue: per octant the warp forms the Chebyshev values and re-centring factors of its points
+// itself, and at the end transforms its values to coefficients column by column (lane = column).
+struct UnitTabs {
+  const int* order;      // [ncompact][8][75] points ranked by child cone
+  const int* unit;       // units per compact cone, in octant order: start | len << 8 | octant << 16
+  const int* unit_ptr;   // [ncompact + 1]
+};
+
+struct __align__(16) UpPoint {   // per parent point of the current octant
+  float tp[4];
+  float tt[4];
+  float ts[2];
+  float pad[2];
+  float4 fac;                    // re-centring factors (re, im) of kernels e and i
+};
+
+constexpr int kUpWarpW = 2;   // warps (parent slots) per block
+constexpr size_t kUpWarpBytes = sizeof(float) * kQ * 32 + sizeof(UpPoint) * kQ + sizeof(float) * kQ * 4;
+constexpr size_t kUpWarpSmem = kUpWarpW * kUpWarpBytes;
+
+__global__ void __launch_bounds__(32 * kUpWarpW, 7) k_up_warp(UpArgs<float> A, UnitTabs UT, int nslots) {
+  using T = float;
+  __shared__ SmallMaps<T> M;
+  extern __shared__ float4 upw_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* base = reinterpret_cast<unsigned char*>(upw_smem) + warp * kUpWarpBytes;
+  T* vals = reinterpret_cast<T*>(base);                                        // [75][32]
+  UpPoint* pt = reinterpret_cast<UpPoint*>(base + sizeof(float) * kQ * 32);   // [75]
+  T (*Xp)[4] = reinterpret_cast<T (*)[4]>(pt + kQ);                           // [75] parent points
+  A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
+  A.coefs_p += blockIdx.y * A.cstride_p;
+  init_maps(M);
+  __syncthreads();
+  const int pslot = blockIdx.x * kUpWarpW + warp;
+  if (pslot >= nslots) return;   // no block barrier follows
+  const int P = __ldg(A.slot_box + pslot), ci = __ldg(A.slot_upidx + pslot);
+  const cone_key pcone = A.slot_cone[pslot];
+  for (int q = lane; q < kQ; q += 32) {
+    cone_point(M, A.cgp, pcone, q, Xp[q]);
+    Xp[q][3] = sqrt_t(Xp[q][0] * Xp[q][0] + Xp[q][1] * Xp[q][1] + Xp[q][2] * Xp[q][2]);
+  }
+  for (int e = lane; e < kQ * 32; e += 32) vals[e] = T(0);
+  __syncwarp();
+  const T off = (T)(0.5 * A.Hc);
+  const T kk[2] = {A.ke, A.ki};
+  const int ks = lane >> 4;
+  const T sgn = (lane & 1) ? T(1) : T(-1);
+  const int u1 = __ldg(UT.unit_ptr + ci + 1);
+  int u = __ldg(UT.unit_ptr + ci);
+  for (int o = 0; o < 8 && u < u1; ++o) {
+    int ue = u;   // units of octant o: [u, ue)
+    while (ue < u1 && ((__ldg(UT.unit + ue) >> 16) & 7) == o) ++ue;
+    const int cb = __ldg(A.child + 8 * P + o);
+    if (cb < 0 || ue == u) {
+      u = ue;
+      continue;
+    }
+    const size_t g = (size_t)ci * 8 + o;
+    // the octant's points: Chebyshev values in their child cone and the re-centring factor
+    const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
+    for (int q = lane; q < kQ; q += 32) {
+      const int ccx = __ldg(A.up_cc + g * kQ + q);
+      if (ccx < 0) continue;
+      const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
+      T ts, tt, tp, rc, sth, cth, sph, cph;
+      local_coords(A.cgc, A.ckeys_c[ccx], x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
+      T v5[5], v3[3];
+      UpPoint& C = pt[q];
+      cheb_vals<T, 5>(tp, v5);
+      C.tp[0] = v5[1]; C.tp[1] = v5[2]; C.tp[2] = v5[3]; C.tp[3] = v5[4];
+      cheb_vals<T, 5>(tt, v5);
+      C.tt[0] = v5[1]; C.tt[1] = v5[2]; C.tt[2] = v5[3]; C.tt[3] = v5[4];
+      cheb_vals<T, 3>(ts, v3);
+      C.ts[0] = v3[1]; C.ts[1] = v3[2];
+      // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
+      const T rp = Xp[q][3];
+      const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
+      T sn0, cs0, sn1, cs1;
+      sincos_t(kk[0] * dr, &sn0, &cs0);
+      sincos_t(kk[1] * dr, &sn1, &cs1);
+      const T a = rp / rc;
+      C.fac = make_float4(a * cs0, a * sn0, a * cs1, a * sn1);
+    }
+    __syncwarp();
+    for (; u < ue; ++u) {
+      const int tk = __ldg(UT.unit + u);
+      const int r0 = tk & 255, len = (tk >> 8) & 255;
+      const int myq = lane < len ? __ldg(UT.order + g * kQ + r0 + lane) : 0;
+      const int q0 = __shfl_sync(0xffffffffu, myq, 0);
+      const int cslot = __ldg(A.cmap_c + (size_t)cb * A.ncomp_c + __ldg(A.up_cc + g * kQ + q0));
+      if (cslot < 0) continue;   // cannot happen: the host marked every such cone relevant
+      const T* Cg = A.coefs_c + (size_t)cslot * kQ * 32 + lane;
+      T c[kQ];
+#pragma unroll
+      for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
+      for (int a = 0; a < len; ++a) {
+        const int q = __shfl_sync(0xffffffffu, myq, a);
+        const float4* cp = reinterpret_cast<const float4*>(&pt[q]);
+        const float4 P4 = cp[0], T4 = cp[1], S4 = cp[2], F4 = cp[3];
+        const T Tp[4] = {P4.x, P4.y, P4.z, P4.w};
+        const T Tt[4] = {T4.x, T4.y, T4.z, T4.w};
+        T E[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          T e = T(0);
+#pragma unroll
+          for (int j = 0; j < 5; ++j) {
+            const T* cij = c + (i * 5 + j) * 5;
+            T d = cij[0];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d = fmaf(Tp[k], cij[k + 1], d);
+            e = j == 0 ? d : fmaf(Tt[j - 1], d, e);
+          }
+          E[i] = e;
+        }
+        const T v = fmaf(S4.y, E[2], fmaf(S4.x, E[1], E[0]));
+        const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
+        const T fr = ks ? F4.z : F4.x, fi = ks ? F4.w : F4.y;
+        vals[q * 32 + lane] += fmaf(v, fr, sgn * fi * wv);
+      }
+    }
+    __syncwarp();   // the next octant's prologue overwrites pt
+  }
+  // values -> coefficients, lane = column, and a coalesced store
+  vals_to_coefs_col(M, vals + lane, 32);
+  T* out = A.coefs_p + (size_t)pslot * kQ * 32 + lane;
+  for (int q = 0; q < kQ; ++q) out[q * 32] = vals[q * 32 + lane];
+}
+
 // ------------------------------------------------------------------ (b) on the tensor cores
 // The upward step as dense contractions on the 5th-generation tensor cores (tcgen05, kind::tf32,
 // FP32 accumulation in tensor memory).  A block takes kTcBoxes parent slots of one parent cone
@@ -582,12 +718,22 @@ __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-// wait for phase `parity` of an mbarrier, giving up after `limit` polls; true when it completed
-__device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, int limit) {
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for phase `parity` of an mbarrier, giving up after `limit_ns` nanoseconds or kWaitPolls
+// polls, whichever comes first; true when the phase completed
+constexpr int kWaitPolls = 1 << 26;
+__device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   uint32_t done = 0;
-  for (int it = 0; it < limit && !done; ++it)
+  const uint64_t t0 = now_ns();
+  for (int it = 0; it < kWaitPolls && !done; ++it) {
     asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                  : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    if (!done && now_ns() - t0 > limit_ns) break;
+  }
   return done != 0;
 }
 constexpr int kK = 80;                          // K: 75 Chebyshev terms padded to a multiple of 8
@@ -605,7 +751,6 @@ constexpr int kOffCs = kOffXp + kQ * 3 * 4;                              // [kTc
 constexpr int kOffUnit = kOffCs + kTcBoxes * kTcMaxUnits * 4;            // [kTcMaxUnits] unit records
 constexpr int kOffOrder = kOffUnit + kTcMaxUnits * 4;                    // [8][75] points by child cone
 constexpr int kSmem = kOffOrder + 8 * kQ * 4 + 1024;                     // + alignment to 1024 bytes
-constexpr int kWaitLimit = 1 << 24;             // polls before a wait is reported as timed out
 
 // Row m (A: m = box * 32 + field; B: m = point), 16-byte chunk kc (k = 4 kc .. 4 kc + 3) of a
 // K-major operand without swizzle: 8-row x 16-byte core matrices, the 20 chunks of one 8-row
@@ -658,6 +803,8 @@ struct TcTabs {
   const int* unit_ptr;   // [ncompact + 1]
   const int* item;       // [nitems][kTcBoxes] parent slots (-1 padded)
   int* err;              // device status word: bit 0 set when a wait on the tensor cores timed out
+  uint64_t wait_ns;      // limit of each wait (1 s; 1 ms under fault injection)
+  int inject;            // fault injection: the first unit's MMAs are not issued, so its wait expires
 };
 
 // Software pipeline per unit u (one thread issues the MMAs):
@@ -860,7 +1007,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTa
   bool ok = true;
   for (int u = 0; u < nunits; ++u) {
     if (u > 0) {   // MMA(u-1) done: A free, accumulator (u-1) % 2 ready
-      ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((u - 1) & 1), tc::kWaitLimit)) != 0;
+      ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((u - 1) & 1), TT.wait_ns)) != 0;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
@@ -870,7 +1017,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTa
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (t == 0) {
+    if (t == 0 && !(TT.inject && u == 0)) {
       const uint32_t id = tc::idesc(128, tc::kN);
       const uint32_t aH = tc::smem_u32(Ahi), aL = tc::smem_u32(Alo);
       const uint32_t bH = tc::smem_u32(sm + tc::kOffB + (u & 1) * 2 * tc::kBBytes), bL = bH + tc::kBBytes;
@@ -890,7 +1037,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTa
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
   if (ok && nunits > 0) {
-    ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((nunits - 1) & 1), tc::kWaitLimit)) != 0;
+    ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((nunits - 1) & 1), TT.wait_ns)) != 0;
     if (ok) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       epilogue(nunits - 1);
@@ -899,8 +1046,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTa
   if (!ok) {
     // a wait timed out: record it, give the tensor cores a bounded second wait, release and leave
     if (t == 0) atomicOr(TT.err, 1);
-    tc::wait(&mbar, 0u, tc::kWaitLimit);
-    tc::wait(&mbar, 1u, tc::kWaitLimit);
+    tc::wait(&mbar, 0u, TT.wait_ns);
+    tc::wait(&mbar, 1u, TT.wait_ns);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -1195,6 +1342,17 @@ __global__ void __launch_bounds__(32 * kTgtBoxWarps) k_target_box(TgtArgs<float,
   }
 }
 
+// The FP32 SIMT upward step into the level below Pp: mode 1 a warp per parent slot (unit
+// tables), mode 0 runs per point group.
+void launch_up_simt(const UpArgs<float>& U, const DevLevel& Pp, int mode, int nrhs, cudaStream_t s) {
+  if (mode == 1 && Pp.tc_unit_ptr)
+    k_up_warp<<<dim3((unsigned)((Pp.nslots + kUpWarpW - 1) / kUpWarpW), nrhs), 32 * kUpWarpW, kUpWarpSmem, s>>>(
+        U, UnitTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr}, Pp.nslots);
+  else
+    k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, kUpRunSmem, s>>>(
+        U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
+}
+
 template <typename T, typename TO = T>
 cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int D = p->tree.D;
@@ -1243,10 +1401,10 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
         if constexpr (std::is_same<T, float>::value) {
           if (Pp.tc)
             k_up_tc<<<dim3(Pp.ntc_items, nrhs), tc::kThreads, tc::kSmem, s>>>(
-                U, TcTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr, Pp.tc_item, p->dev_err});
+                U, TcTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr, Pp.tc_item, p->dev_err,
+                          p->inject ? 1000000ull : 1000000000ull, p->inject});
           else
-            k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, kUpRunSmem, s>>>(
-                U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
+            launch_up_simt(U, Pp, Pp.up_mode, nrhs, s);
         } else
           k_up<T><<<dim3(Pp.nslots, nrhs), kUpThreads, 0, s>>>(U);
       }
@@ -1286,6 +1444,20 @@ cudaError_t launch_target_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s)
     else
       k_target<float, float><<<g, 32 * tgt_warps<float>(), 0, s>>>(B32);
   }
+  return cudaGetLastError();
+}
+
+// The FP32 SIMT upward step from level d + 1 into level d alone in `mode` (0 runs per point
+// group, 1 a warp per parent slot), for the autotuner; writes level d's coefficients like an apply.
+cudaError_t launch_up_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s) {
+  if (ifgf64(p->desc) || d < 3 || d >= p->tree.D) return cudaErrorInvalidValue;
+  const DevLevel& L = p->dl[d + 1];
+  const DevLevel& Pp = p->dl[d];
+  if (Pp.nslots == 0) return cudaSuccess;
+  UpArgs<float> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, cone_geom_t<float>(Pp.cg),
+                  L.cmap, L.ncomp, L.ckeys, cone_geom_t<float>(L.cg), L.H, Pp.up_cc, (const float*)L.coefs,
+                  (float*)Pp.coefs, (float)p->desc.k_ext, (float)p->desc.k_int, L.cstride, Pp.cstride};
+  launch_up_simt(U, Pp, mode, 1, s);
   return cudaGetLastError();
 }
 

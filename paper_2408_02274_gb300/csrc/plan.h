@@ -117,6 +117,8 @@ struct DevLevel {
   int* tc_item = nullptr;         // [ntc_items][kTcBoxes]
   int ntc_items = 0;
   bool tc = false;                // the upward step into this level runs on the tensor cores
+  int up_mode = 0;                // FP32 SIMT upward step into this level: 0 runs per point group,
+                                  // 1 a warp per parent slot over the unit tables
   int64_t* tgt_ptr = nullptr;     // [N+1]
   int* tgt_slot = nullptr;        // [ninter]
   double2* trig_th = nullptr;     // [na] (cos, sin) of g2 * pi / na: lower edges of the theta cells
@@ -164,6 +166,8 @@ struct GmresWork {               // per right-hand side r < batch (layouts below
   double* b = nullptr;          // [batch][4N][2]
   double* y = nullptr;          // [batch][4N][2]
   double* inc = nullptr;        // [batch][6N][2]
+  double* y_acc = nullptr;      // [batch][4N][2] refinement: the solution so far (refine > 0)
+  double* b_orig = nullptr;     // [batch][4N][2] refinement: the right-hand side (refine > 0)
   int* active = nullptr;        // [batch] 1 while a right-hand side iterates
   int* kfin = nullptr;          // [batch] Krylov dimension at the end
   double* hres = nullptr;       // pinned host copy of scal
@@ -227,6 +231,9 @@ struct ifgf_plan_t {
   // device data
   ifgf::NodeGeom geo;
   int* dev_err = nullptr;       // device status word (bit 0: a tensor-core wait timed out)
+  int inject = 0;               // fault injection for the timeout path (ifgf_plan_inject)
+  ifgf_plan_t* resid = nullptr; // plan whose map forms the refinement residual (ifgf_plan_set_residual)
+  std::vector<ifgf_plan_t*> resid_of;   // plans that use this one as their residual plan
   double* tab_D = nullptr;      // [nc][nc] Chebyshev differentiation matrix
   double* x_sorted = nullptr;   // [N][3] nodes in sorted order
   double* n_sorted = nullptr;   // [N][3]

@@ -283,10 +283,11 @@ def test_plan_estimate_matches_the_created_plan(medium, prec):
     candidate patch as singular: the byte difference is exactly the nonzero difference times
     the bytes per nonzero (8 values in the plan's precision + a 4-byte column)."""
     prob, qp = medium[0], medium[1]
+    refine = 2 if prec == lib.IFGF_FP32 else 0   # refinement adds two vectors per right-hand side
     kw = dict(delta=qp.delta, n_beta=qp.n_beta, cov_d=qp.cov_d, gs_iters=qp.gs_iters, precision=prec,
-              ns0=2, na0=3, max_krylov=40, batch=2)
+              ns0=2, na0=3, max_krylov=40, batch=2, refine=refine)
     est = lib.Plan.estimate(prob, **kw)
-    plan = plan_of(prob, qp, precision=prec, ns0=2, na0=3, max_krylov=40, batch=2)
+    plan = plan_of(prob, qp, precision=prec, ns0=2, na0=3, max_krylov=40, batch=2, refine=refine)
     st = plan.stats()
     plan.close()
     el = 8 if prec == lib.IFGF_FP64 else 4

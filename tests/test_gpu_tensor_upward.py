@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2408_02274_gb300 as lib  # noqa: E402
-from inputs import CONFIG_SPHERE_MEDIUM, random_densities  # noqa: E402
+from inputs import CONFIG_SPHERE_MEDIUM, plane_wave, random_densities  # noqa: E402
 from oracle import cbie  # noqa: E402
 
 
@@ -68,3 +68,37 @@ def test_tensor_core_forward_map_and_batch(medium):
     e = rel(one.cpu().numpy(), ref.cpu().numpy())
     print(f"tensor-core IFGF forward map vs plain FP64: {e:.2e}")
     assert e < 1e-4
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_plan_stays_usable(medium):
+    """The one device-side wait (the MMAs of the tensor-core upward step) is bounded: with fault
+    injection the first MMAs of every block are not issued, so the wait expires (1 ms), the step
+    records IFGF_ETIMEOUT in the plan's status word, frees its tensor memory and returns.  The
+    host reads the status (ifgf_plan_check, and the solves before returning), the context stays
+    usable, and the next apply equals the one before the injection."""
+    prob, delta = medium
+    y = torch.from_numpy(random_densities(prob.n, 33)).cuda()
+    p = plan(prob, delta, precision=lib.IFGF_FP32, upward_tc=1)
+    ref = torch.empty_like(y)
+    p.apply(y, ref)
+    p.check()                                     # nothing pending
+    p.inject(1)
+    bad = torch.empty_like(y)
+    p.apply(y, bad)
+    with pytest.raises(lib.IfgfError) as e:
+        p.check()
+    assert e.value.status == lib.IFGF_ETIMEOUT and "tensor-core" in str(e.value)
+    p.check()                                     # the check cleared the word
+    x, _, _ = prob.nodes()
+    inc = torch.from_numpy(np.ascontiguousarray(plane_wave(x, prob.k_ext, prob.omega)[None])).cuda()
+    ys = torch.empty((1, 4, prob.n), dtype=torch.complex128, device="cuda")
+    with pytest.raises(lib.IfgfError) as e:
+        p.solve_batch(inc, ys, tol=1e-3, max_iter=5)
+    assert e.value.status == lib.IFGF_ETIMEOUT
+    p.inject(0)
+    again = torch.empty_like(y)
+    p.apply(y, again)
+    p.check()
+    torch.cuda.synchronize()
+    p.close()
+    assert torch.equal(again, ref)

@@ -1,6 +1,6 @@
-"""The autotuner (ifgf_plan_tune) through the C ABI: it times both target-step shapes per level
-and both near-matvec block sizes, keeps the faster, and the forward map after tuning agrees with
-the one before to FP32 rounding (only the summation grouping of the target step can change)."""
+"""The autotuner (ifgf_plan_tune) through the C ABI: it times both target-step shapes and both
+upward-step shapes per level and both near-matvec block sizes, keeps the faster, and the forward
+map after tuning agrees with the one before to FP32 rounding (only summation orders change)."""
 import numpy as np
 import pytest
 
@@ -29,7 +29,13 @@ def test_tune_keeps_the_faster_shape_and_the_result():
         assert t0 > 0 and t1 > 0
         assert choices[d] == (1 if t1 < t0 else 0)
     assert choices[25] in (128, 256) and times[50] > 0 and times[51] > 0
-    print("target shape per level:", choices[3:levels + 1], "ms:", times[6:2 * levels + 2], "near threads:", choices[25])
+    for d in range(3, levels):   # upward step into parent level d: point-group runs or warp per slot
+        assert choices[32 + d] in (0, 1)
+        t0, t1 = times[64 + 2 * d], times[65 + 2 * d]
+        assert t0 > 0 and t1 > 0
+        assert choices[32 + d] == (1 if t1 < t0 else 0)
+    print("target shape per level:", choices[3:levels + 1], "ms:", times[6:2 * levels + 2], "near threads:", choices[25],
+          "upward shape per level:", choices[35:32 + levels], "ms:", times[70:64 + 2 * levels])
     e = float(torch.linalg.norm(after - before) / torch.linalg.norm(before))
     assert e < 1e-5, e
     plan.close()
