@@ -412,7 +412,8 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
 // per lane) and then sweeps the run: per point the Chebyshev values and the
 // re-centring factor, formed once per (octant, point) in the prologue, are read
 // from shared memory with vector loads, and the 3D Chebyshev sum is contracted
-// separably (over phi, then theta, then s: 74 FMA per lane).  The parent points
+// separably (over phi, then theta, then s: 74 FMA per lane), two points at a time
+// (two independent FMA streams per warp).  The parent points
 // are split into kUpGroups fixed groups, one per warp, so each warp adds into
 // its own points' values with plain shared-memory adds.
 struct RunTabs {
@@ -430,6 +431,37 @@ struct __align__(16) UpCheb {
   float ts[2];
   float pad[2];
 };
+
+// The 3D Chebyshev sum of one lane's 75 coefficients c at NP points, contracted separably (phi,
+// then theta, then s; T_0 = 1 folded in): 74 FMA per point.  The points' sums are independent,
+// so evaluating two at once gives the scheduler two FMA streams that share each coefficient.
+template <int NP>
+__device__ __forceinline__ void up_contract(const float (&c)[kQ], const float4 (&P4)[NP], const float4 (&T4)[NP],
+                                            const float4 (&S4)[NP], float (&v)[NP]) {
+  float E[NP][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float e[NP];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const float* cij = c + (i * 5 + j) * 5;
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        float d = cij[0];
+        d = fmaf(P4[n].x, cij[1], d);
+        d = fmaf(P4[n].y, cij[2], d);
+        d = fmaf(P4[n].z, cij[3], d);
+        d = fmaf(P4[n].w, cij[4], d);
+        const float tt = j == 1 ? T4[n].x : j == 2 ? T4[n].y : j == 3 ? T4[n].z : T4[n].w;
+        e[n] = j == 0 ? d : fmaf(tt, d, e[n]);
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NP; ++n) E[n][i] = e[n];
+  }
+#pragma unroll
+  for (int n = 0; n < NP; ++n) v[n] = fmaf(S4[n].y, E[n][2], fmaf(S4[n].x, E[n][1], E[n][0]));
+}
 
 constexpr int kUpRunWarps = kUpGroups;   // warp w adds only into the parent points of group w
 
@@ -511,32 +543,36 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
     T c[kQ];
 #pragma unroll
     for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
-    for (int a = 0; a < len; ++a) {
+    int a = 0;
+    for (; a + 1 < len; a += 2) {   // two points at a time (independent sums, distinct points)
+      int q[2];
+      float4 P4[2], T4[2], S4[2], F4[2];
+      float v[2];
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        q[n] = __shfl_sync(0xffffffffu, myq, a + n);
+        const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q[n]]);
+        P4[n] = cp[0]; T4[n] = cp[1]; S4[n] = cp[2];
+        F4[n] = fac[o][q[n]];
+      }
+      up_contract<2>(c, P4, T4, S4, v);
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        const T wv = __shfl_xor_sync(0xffffffffu, v[n], 1);
+        const T fr = ks ? F4[n].z : F4[n].x, fi = ks ? F4[n].w : F4[n].y;
+        vals[q[n] * kVS + lane] += fmaf(v[n], fr, sgn * fi * wv);
+      }
+    }
+    if (a < len) {
       const int q = __shfl_sync(0xffffffffu, myq, a);
       const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
-      const float4 P4 = cp[0], T4 = cp[1], S4 = cp[2];
+      const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
       const float4 F4 = fac[o][q];
-      const T Tp[4] = {P4.x, P4.y, P4.z, P4.w};
-      const T Tt[4] = {T4.x, T4.y, T4.z, T4.w};
-      // separable contraction (phi, then theta, then s), T_0 = 1 folded in
-      T E[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        T e = T(0);
-#pragma unroll
-        for (int j = 0; j < 5; ++j) {
-          const T* cij = c + (i * 5 + j) * 5;
-          T d = cij[0];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) d = fmaf(Tp[k], cij[k + 1], d);
-          e = j == 0 ? d : fmaf(Tt[j - 1], d, e);
-        }
-        E[i] = e;
-      }
-      const T v = fmaf(S4.y, E[2], fmaf(S4.x, E[1], E[0]));
-      const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
+      float v[1];
+      up_contract<1>(c, P4, T4, S4, v);
+      const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
       const T fr = ks ? F4.z : F4.x, fi = ks ? F4.w : F4.y;
-      vals[q * kVS + lane] += fmaf(v, fr, sgn * fi * wv);
+      vals[q * kVS + lane] += fmaf(v[0], fr, sgn * fi * wv);
     }
   }
   __syncthreads();
@@ -552,6 +588,9 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
 // per octant in k_up_runs, at 23 points per unit on average) and no block barrier follows the
 // prologue: per octant the warp forms the Chebyshev values and re-centring factors of its points
 // itself, and at the end transforms its values to coefficients column by column (lane = column).
+// Measured on GB300 it is 1.1-1.3x slower than k_up_runs on the sphere workloads despite 12 %
+// fewer instructions (14 warps per SM, the per-octant prologue and each unit's coefficient loads
+// are not overlapped: issue 41 % against 57 %), so it is an autotuner candidate, not the default.
 struct UnitTabs {
   const int* order;      // [ncompact][8][75] points ranked by child cone
   const int* unit;       // units per compact cone, in octant order: start | len << 8 | octant << 16
@@ -645,30 +684,16 @@ __global__ void __launch_bounds__(32 * kUpWarpW, 7) k_up_warp(UpArgs<float> A, U
       T c[kQ];
 #pragma unroll
       for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
-      for (int a = 0; a < len; ++a) {
+      for (int a = 0; a < len; ++a) {   // one point at a time (measured faster here than two)
         const int q = __shfl_sync(0xffffffffu, myq, a);
         const float4* cp = reinterpret_cast<const float4*>(&pt[q]);
-        const float4 P4 = cp[0], T4 = cp[1], S4 = cp[2], F4 = cp[3];
-        const T Tp[4] = {P4.x, P4.y, P4.z, P4.w};
-        const T Tt[4] = {T4.x, T4.y, T4.z, T4.w};
-        T E[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          T e = T(0);
-#pragma unroll
-          for (int j = 0; j < 5; ++j) {
-            const T* cij = c + (i * 5 + j) * 5;
-            T d = cij[0];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) d = fmaf(Tp[k], cij[k + 1], d);
-            e = j == 0 ? d : fmaf(Tt[j - 1], d, e);
-          }
-          E[i] = e;
-        }
-        const T v = fmaf(S4.y, E[2], fmaf(S4.x, E[1], E[0]));
-        const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
+        const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
+        const float4 F4 = cp[3];
+        float v[1];
+        up_contract<1>(c, P4, T4, S4, v);
+        const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
         const T fr = ks ? F4.z : F4.x, fi = ks ? F4.w : F4.y;
-        vals[q * 32 + lane] += fmaf(v, fr, sgn * fi * wv);
+        vals[q * 32 + lane] += fmaf(v[0], fr, sgn * fi * wv);
       }
     }
     __syncwarp();   // the next octant's prologue overwrites pt
