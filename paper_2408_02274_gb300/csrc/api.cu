@@ -377,6 +377,20 @@ void build(ifgf_plan_t* p) {
     for (int a = 0; a < 2; ++a)
       if (need[a]) buf[a] = ifgf64(d) ? (void*)A.dev<double>(need[a]) : (void*)A.dev<float>(need[a]);
     for (int dd = 3; dd <= t.D; ++dd) p->dl[dd].coefs = buf[dd & 1];
+    // tensor-core operand images of level dd's coefficients, read by the upward step into dd-1
+    // when it runs on the tensor cores (same parity sharing as the coefficients)
+    size_t need_img[2] = {0, 0};
+    for (int dd = 4; dd <= t.D; ++dd)
+      if (upward_tc(d, t.lv[dd - 1]))
+        need_img[dd & 1] = std::max(need_img[dd & 1], (size_t)p->dl[dd].nslots * kImgFloatsHost * (size_t)p->batch);
+    float* ibuf[2] = {nullptr, nullptr};
+    for (int a = 0; a < 2; ++a)
+      if (need_img[a]) ibuf[a] = A.dev<float>(need_img[a]);
+    for (int dd = 4; dd <= t.D; ++dd)
+      if (upward_tc(d, t.lv[dd - 1])) {
+        p->dl[dd].img = ibuf[dd & 1];
+        p->dl[dd].istride = (size_t)p->dl[dd].nslots * kImgFloatsHost;
+      }
   }
   for (int dd = 1; dd < 3 && dd <= t.D; ++dd) p->stats.boxes[dd] = (int)t.lv[dd].key.size();
   {
@@ -676,9 +690,16 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
     }
     tb.dev<int>(1);   // the plan's device status word
     ByteCount cf;
-    if (d.far_mode == IFGF_FAR_IFGF)
+    if (d.far_mode == IFGF_FAR_IFGF) {
       for (int a = 0; a < 2; ++a)
         if (need[a]) (el_s == sizeof(double)) ? cf.dev<double>(need[a]) : cf.dev<float>(need[a]);
+      size_t need_img[2] = {0, 0};
+      for (int dd = 4; dd <= t.D; ++dd)
+        if (upward_tc(d, t.lv[dd - 1]))
+          need_img[dd & 1] = std::max(need_img[dd & 1], t.lv[dd].slot_box.size() * kImgFloatsHost * B);
+      for (int a = 0; a < 2; ++a)
+        if (need_img[a]) cf.dev<float>(need_img[a]);
+    }
     // per-apply buffers and GMRES workspace
     ByteCount ap, gm;
     for (int k = 0; k < 3; ++k) ap.dev<char>(16 * (size_t)N * (k == 1 ? el_s : el) * B);

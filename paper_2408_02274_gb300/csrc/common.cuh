@@ -19,6 +19,7 @@ constexpr int kUpRunMax = 32;                     // parent points per upward-pa
 constexpr int kUpGroups = 4;                      // disjoint parent-point groups, one per warp of the upward block
 constexpr int kTcBoxes = 4;                       // parent slots per tensor-core upward tile (M = 4 x 32 rows)
 constexpr int kTcMaxUnits = 192;                  // most (octant, child cone) units of one parent cone on that path
+constexpr size_t kImgFloatsHost = 2 * 32 * 80;     // tensor-core operand image (hi, lo) of one cone segment
 
 // Complex helpers on plain real pairs (the library keeps complex data interleaved).
 template <typename T>

@@ -140,8 +140,17 @@ constexpr int kVS = 33;   // padded row stride of the value buffers
 // consecutive threads on consecutive columns), followed by a coalesced store of the
 // 75 x 32 coefficients of buffer i to out + i * 75 * 32.  Every thread of the block
 // must call it.
+// Tensor-core operand image of one cone segment's coefficients (the upward step on the tensor
+// cores copies it to shared memory as is): the 32 real columns m as rows, K = 80 (k >= 75 zero),
+// K-major without swizzle in 8-row x 16-byte core matrices (chunk kc = k / 4 of row m at float
+// offset img_off(m, kc) + k % 4), first as TF32 hi parts (low 13 mantissa bits cleared), then the
+// lo parts x - hi: 2 x 2560 floats per segment.
+constexpr int kImgFloats = 2 * 32 * 80;
+__device__ __forceinline__ int img_off(int m, int kc) { return (m >> 3) * 640 + kc * 32 + ((m & 7) << 2); }
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
+
 template <typename T, int kStride>
-__device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* vb, T* out, int ns = 1) {
+__device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* vb, T* out, int ns = 1, float* img = nullptr) {
   const int nt = blockDim.x;
   constexpr int kBuf = kQ * kStride;
   for (int e = threadIdx.x; e < ns * 15 * 32; e += nt) {   // phi lines
@@ -193,6 +202,24 @@ __device__ void vals_to_coefs_block(const SmallMaps<T>& M, T* vb, T* out, int ns
     const int b = e / (kQ * 32), r = e - b * kQ * 32;
     out[e] = vb[b * kBuf + (r >> 5) * kStride + (r & 31)];
   }
+  if constexpr (sizeof(T) == 4) {
+    if (img) {   // tensor-core operand images of the same coefficients (see img_off)
+      for (int e = threadIdx.x; e < ns * 32 * 20; e += nt) {
+        const int b = e / (32 * 20), r = e - b * 32 * 20, m = r / 20, kc = r - m * 20;
+        float x[4], h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = 4 * kc + j;
+          x[j] = k < kQ ? (float)vb[b * kBuf + k * kStride + m] : 0.f;
+          h[j] = tf32_hi(x[j]);
+        }
+        float* im = img + (size_t)b * kImgFloats + img_off(m, kc);
+        *reinterpret_cast<float4*>(im) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(im + kImgFloats / 2) =
+            make_float4(x[0] - h[0], x[1] - h[1], x[2] - h[2], x[3] - h[3]);
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------ (a) leaf direct
@@ -212,6 +239,8 @@ struct LeafArgs {
   T* coefs;
   T ke, ki;
   size_t astride, cstride;   // per right-hand side: densities, cone coefficients
+  float* img = nullptr;      // tensor-core operand images of the coefficients (FP32, when the upward
+  size_t istride = 0;        // step into the level above runs on the tensor cores), per rhs stride
 };
 
 template <typename T>
@@ -230,6 +259,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
   const int t = threadIdx.x;
   A.a_sorted += blockIdx.z * A.astride;   // right-hand side of a batched call
   A.coefs += blockIdx.z * A.cstride;
+  if (A.img) A.img += blockIdx.z * A.istride;
   const int sb = A.box_slot_ptr[box] + blockIdx.y * kLeafSlots;
   const int se = min(A.box_slot_ptr[box + 1], sb + kLeafSlots);
   if (sb >= se) return;   // the box has fewer segments than this block's range (uniform per block)
@@ -297,7 +327,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
     if (act)
       for (int k = 0; k < 32; ++k) vbuf[(sl * kQ + q) * kVS + k] = acc[k];
     __syncthreads();
-    vals_to_coefs_block<T, kVS>(M, vbuf, A.coefs + (size_t)s0 * kQ * 32, min(2, se - s0));
+    vals_to_coefs_block<T, kVS>(M, vbuf, A.coefs + (size_t)s0 * kQ * 32, min(2, se - s0),
+                                A.img ? A.img + (size_t)s0 * kImgFloats : nullptr);
   }
 }
 
@@ -323,6 +354,8 @@ struct UpArgs {
   T* coefs_p;
   T ke, ki;
   size_t cstride_c, cstride_p;   // per right-hand side
+  float* img_p = nullptr;        // tensor-core operand images of the parent coefficients (or none)
+  size_t istride_p = 0;          // per right-hand side
 };
 
 template <typename T>
@@ -576,7 +609,8 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
     }
   }
   __syncthreads();
-  vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32);
+  vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32, 1,
+                              A.img_p ? A.img_p + blockIdx.y * A.istride_p + (size_t)pslot * kImgFloats : nullptr);
 }
 
 // (b), FP32 variant with a warp per parent slot.  The warp walks the slot's units (the points of
@@ -702,6 +736,21 @@ __global__ void __launch_bounds__(32 * kUpWarpW, 7) k_up_warp(UpArgs<float> A, U
   vals_to_coefs_col(M, vals + lane, 32);
   T* out = A.coefs_p + (size_t)pslot * kQ * 32 + lane;
   for (int q = 0; q < kQ; ++q) out[q * 32] = vals[q * 32 + lane];
+  if (A.img_p) {   // tensor-core operand image: lane = row m
+    float* im = A.img_p + blockIdx.y * A.istride_p + (size_t)pslot * kImgFloats;
+    for (int kc = 0; kc < 20; ++kc) {
+      float x[4], h[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = 4 * kc + j;
+        x[j] = k < kQ ? vals[k * 32 + lane] : 0.f;
+        h[j] = tf32_hi(x[j]);
+      }
+      *reinterpret_cast<float4*>(im + img_off(lane, kc)) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(im + kImgFloats / 2 + img_off(lane, kc)) =
+          make_float4(x[0] - h[0], x[1] - h[1], x[2] - h[2], x[3] - h[3]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ (b) on the tensor cores
@@ -710,19 +759,33 @@ __global__ void __launch_bounds__(32 * kUpWarpW, 7) k_up_warp(UpArgs<float> A, U
 // (their parent points, child cones and re-centring factors are box-independent) and sweeps the
 // cone's units: the points of one octant that fall in one child cone (at most 32).  Per unit
 //   D[(box, field) x point] = C^T[(box, field) x k] . B[k x point],  M = 128, N = 32, K = 80,
-// with C the child cone's 75 x 32 coefficients (A operand) and B the Chebyshev basis
+// with C the child cones' 75 x 32 coefficients (A operand) and B the Chebyshev basis
 // T_i(s) T_j(theta) T_k(phi) of the unit's points, both K-major without swizzle (8-row x 16-byte
-// core matrices), K padded from 75 to 80 with zeros.  FP32 accuracy comes from
-// a three-term split x = hi + lo (hi = x with the 13 low mantissa bits cleared, exactly the
-// TF32 operand): D = A_hi B_hi + A_hi B_lo + A_lo B_hi.  The epilogue re-centres each column
-// (complex factor of the point) and adds it into the parent values in shared memory; the
-// values -> coefficients map runs once per parent slot at the end.
+// core matrices), K padded from 75 to 80 with zeros.  FP32 accuracy comes from a three-term split
+// x = hi + lo (hi = x with the 13 low mantissa bits cleared, exactly the TF32 operand):
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// The A operand needs no staging by threads: the kernel that produced the child coefficients
+// also wrote them as operand images (img_off: hi and lo parts, the K-major core-matrix layout),
+// and one bulk asynchronous copy per (box, part) moves an image into shared memory, completing on
+// an mbarrier.  The copy for unit u+1 is issued as soon as the MMAs of unit u have read the A
+// buffer, so it runs under unit u's epilogue and unit u+1's basis.  The parent values of the four
+// slots accumulate in tensor memory (lane = (box, field), column = parent point), next to the
+// unit's accumulator D; the epilogue (warp w = box w, the tensor-memory lanes it may access)
+// re-centres D's columns and adds them into the parent columns, and at the end each thread
+// transforms its own column of 75 values to coefficients in registers and writes them, and their
+// operand images when the level above also runs on the tensor cores.
+// Measured on GB300 it is 2.4-2.6x slower than the SIMT kernel k_up_runs (upward step 19.2 against
+// 7.3 ms at 9,600 nodes, 150 against 63 ms at 153,600): the MMAs remove the 74 contraction FMAs of
+// a (parent point, child) pair, but the pair's share of the basis, the re-centring of its 32
+// columns and its scatter-add (~60 warp instructions) remain, since a coefficient block serves
+// only ~20 points, and 8 warps per SM do not hide the serial chain of a unit.  Plan option, not
+// the default.
 namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
 
 // shared-memory matrix descriptor: start address, leading / stride byte offsets, layout
-// (0: no swizzle, 2: 128-byte swizzle), descriptor version 1
+// (0: no swizzle), descriptor version 1
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
   return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(layout & 7) << 61);
@@ -731,8 +794,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
 __host__ __device__ constexpr uint32_t idesc(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ float hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
-
 __device__ __forceinline__ void mma(uint32_t td, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -741,6 +802,18 @@ __device__ __forceinline__ void mma(uint32_t td, uint64_t a, uint64_t b, uint32_
 }
 __device__ __forceinline__ void commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// arm an mbarrier for `bytes` of bulk-copy transactions (one arrival)
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bulk asynchronous copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte
+// aligned), completing its transactions on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
 __device__ __forceinline__ uint64_t now_ns() {
@@ -761,146 +834,165 @@ __device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, uint64_t li
   }
   return done != 0;
 }
+// tensor-memory loads and stores of this warp's 32 lanes (32x32b shapes)
+__device__ __forceinline__ void ld_x32(uint32_t ta, float (&r)[32]) {
+  uint32_t* u = reinterpret_cast<uint32_t*>(r);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]),
+        "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]),
+        "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+      : "r"(ta));
+}
+__device__ __forceinline__ void ld_x16(uint32_t ta, float* r) {
+  uint32_t* u = reinterpret_cast<uint32_t*>(r);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(ta));
+}
+__device__ __forceinline__ void ld_x1(uint32_t ta, float& r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(*reinterpret_cast<uint32_t*>(&r)) : "r"(ta));
+}
+__device__ __forceinline__ void st_x1(uint32_t ta, float v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(ta), "r"(__float_as_uint(v)) : "memory");
+}
+__device__ __forceinline__ void st_x16_zero(uint32_t ta) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(ta),
+      "r"(0u)
+      : "memory");
+}
+// wait for this thread's single-column loads; the registers are operands, so no use of them is
+// scheduled before the wait
+__device__ __forceinline__ void wait_ld_regs(float (&r)[32]) {
+  uint32_t* u = reinterpret_cast<uint32_t*>(r);
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(u[0]), "+r"(u[1]), "+r"(u[2]), "+r"(u[3]), "+r"(u[4]), "+r"(u[5]), "+r"(u[6]), "+r"(u[7]),
+                 "+r"(u[8]), "+r"(u[9]), "+r"(u[10]), "+r"(u[11]), "+r"(u[12]), "+r"(u[13]), "+r"(u[14]), "+r"(u[15]),
+                 "+r"(u[16]), "+r"(u[17]), "+r"(u[18]), "+r"(u[19]), "+r"(u[20]), "+r"(u[21]), "+r"(u[22]),
+                 "+r"(u[23]), "+r"(u[24]), "+r"(u[25]), "+r"(u[26]), "+r"(u[27]), "+r"(u[28]), "+r"(u[29]),
+                 "+r"(u[30]), "+r"(u[31])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
 constexpr int kK = 80;                          // K: 75 Chebyshev terms padded to a multiple of 8
 constexpr int kN = 32;                          // N: points of a unit
-constexpr int kThreads = 256;                   // 8 warps; warps w and w + 4 share box w % 4 in the epilogue
-constexpr int kABytes = kTcBoxes * 32 * kK * 4;   // 40960: 128 rows (box, field) x 80
-constexpr int kBBytes = kN * kK * 4;            // 10240
-// shared memory: A hi / lo, B hi / lo in two buffers, parent values, per-cone tables
-constexpr int kOffAlo = kABytes, kOffB = 2 * kABytes;                    // B buffer i: hi at kOffB + 2 i kBBytes
-constexpr int kOffVals = kOffB + 4 * kBBytes;                            // [kTcBoxes][75][kVS] floats
-constexpr int kOffCheb = kOffVals + kTcBoxes * kQ * kVS * 4;             // [8][75] UpCheb
-constexpr int kOffFac = kOffCheb + 8 * kQ * (int)sizeof(UpCheb);         // [8][75] float4
-constexpr int kOffXp = kOffFac + 8 * kQ * 16;                            // [75][3] floats
-constexpr int kOffCs = kOffXp + kQ * 3 * 4;                              // [kTcBoxes][kTcMaxUnits] child slots
-constexpr int kOffUnit = kOffCs + kTcBoxes * kTcMaxUnits * 4;            // [kTcMaxUnits] unit records
-constexpr int kOffOrder = kOffUnit + kTcMaxUnits * 4;                    // [8][75] points by child cone
-constexpr int kSmem = kOffOrder + 8 * kQ * 4 + 1024;                     // + alignment to 1024 bytes
+constexpr int kThreads = 128;                   // 4 warps: warp w is box w in the epilogue
+constexpr int kImgBytes = 32 * kK * 4;          // one operand image part (hi or lo) of one slot
+constexpr int kCols = 128;                      // tensor-memory columns: parent values 0..79, D 96..127
+constexpr int kColD = 96;
+// shared memory (1024-byte aligned base): A hi [4 boxes] | A lo [4 boxes] | B hi | B lo | unit
+// point data | re-centring factors | parent points | child slots per (box, unit) | unit records
+constexpr int kOffAlo = kTcBoxes * kImgBytes;                 // 40960
+constexpr int kOffB = 2 * kTcBoxes * kImgBytes;               // 81920
+constexpr int kOffBlo = kOffB + kImgBytes;                    // 92160
+constexpr int kOffPts = kOffB + 2 * kImgBytes;                // [32] x 3 float4: T values and the point
+constexpr int kOffFac = kOffPts + kN * 48;                    // [32] float4
+constexpr int kOffXp = kOffFac + kN * 16;                     // [75][4] floats
+constexpr int kOffCs = kOffXp + kQ * 16;                      // [kTcBoxes][kTcMaxUnits] ints
+constexpr int kOffUnit = kOffCs + kTcBoxes * kTcMaxUnits * 4; // [kTcMaxUnits] ints
+constexpr int kSmem = kOffUnit + kTcMaxUnits * 4 + 1024;      // + alignment of the base
+static_assert(kOffPts % 16 == 0 && kOffFac % 16 == 0 && kOffXp % 16 == 0, "16-byte aligned regions");
+static_assert(2 * (kSmem + 1024) <= 228 * 1024, "two blocks per SM");
 
-// Row m (A: m = box * 32 + field; B: m = point), 16-byte chunk kc (k = 4 kc .. 4 kc + 3) of a
-// K-major operand without swizzle: 8-row x 16-byte core matrices, the 20 chunks of one 8-row
-// group 128 bytes apart (leading byte offset), 8-row groups 2560 bytes apart (stride byte offset)
-__device__ __forceinline__ int kmaj_off(int m, int kc) { return (m >> 3) * 2560 + kc * 128 + ((m & 7) << 4); }
+// row m, 16-byte chunk kc of a K-major operand without swizzle (bytes): img_off in bytes
+__device__ __forceinline__ int kmaj_off(int m, int kc) { return 4 * img_off(m, kc); }
 
 }  // namespace tc
-
-// Basis values T_i(s) T_j(theta) T_k(phi) (k-index (i*5 + j)*5 + k) of one point for the K-indices
-// 4 KC .. 4 KC + 3, as TF32 hi and lo parts into the B operand's 16-byte chunk KC (index 75 is
-// zero; chunk 19 stays zero from the initial clear).
-template <int KC>
-__device__ __forceinline__ void tc_basis(const float* TS, const float* TT, const float* TP, unsigned char* Bhi,
-                                         unsigned char* Blo, int n) {
-  float v[4], h[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int k = 4 * KC + j;
-    v[j] = k < kQ ? TS[k / 25] * TT[(k / 5) % 5] * TP[k % 5] : 0.f;
-    h[j] = tc::hi(v[j]);
-  }
-  const int off = tc::kmaj_off(n, KC);
-  *reinterpret_cast<float4*>(Bhi + off) = make_float4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<float4*>(Blo + off) = make_float4(v[0] - h[0], v[1] - h[1], v[2] - h[2], v[3] - h[3]);
-}
-
-// The basis chunks of point n written by warp w: chunks w, w + 8 and (w < 3) w + 16.
-__device__ __forceinline__ void tc_basis_warp(int w, const UpCheb& C, unsigned char* Bhi, unsigned char* Blo, int n) {
-  const float TS[3] = {1.f, C.ts[0], C.ts[1]};
-  const float TT[5] = {1.f, C.tt[0], C.tt[1], C.tt[2], C.tt[3]};
-  const float TP[5] = {1.f, C.tp[0], C.tp[1], C.tp[2], C.tp[3]};
-  switch (w) {
-    case 0: tc_basis<0>(TS, TT, TP, Bhi, Blo, n); tc_basis<8>(TS, TT, TP, Bhi, Blo, n);
-            tc_basis<16>(TS, TT, TP, Bhi, Blo, n); break;
-    case 1: tc_basis<1>(TS, TT, TP, Bhi, Blo, n); tc_basis<9>(TS, TT, TP, Bhi, Blo, n);
-            tc_basis<17>(TS, TT, TP, Bhi, Blo, n); break;
-    case 2: tc_basis<2>(TS, TT, TP, Bhi, Blo, n); tc_basis<10>(TS, TT, TP, Bhi, Blo, n);
-            tc_basis<18>(TS, TT, TP, Bhi, Blo, n); break;
-    case 3: tc_basis<3>(TS, TT, TP, Bhi, Blo, n); tc_basis<11>(TS, TT, TP, Bhi, Blo, n); break;
-    case 4: tc_basis<4>(TS, TT, TP, Bhi, Blo, n); tc_basis<12>(TS, TT, TP, Bhi, Blo, n); break;
-    case 5: tc_basis<5>(TS, TT, TP, Bhi, Blo, n); tc_basis<13>(TS, TT, TP, Bhi, Blo, n); break;
-    case 6: tc_basis<6>(TS, TT, TP, Bhi, Blo, n); tc_basis<14>(TS, TT, TP, Bhi, Blo, n); break;
-    default: tc_basis<7>(TS, TT, TP, Bhi, Blo, n); tc_basis<15>(TS, TT, TP, Bhi, Blo, n); break;
-  }
-}
 
 struct TcTabs {
   const int* order;      // [ncompact][8][75] points ranked by child cone
   const int* unit;       // units per compact cone: start | len << 8 | octant << 16
   const int* unit_ptr;   // [ncompact + 1]
   const int* item;       // [nitems][kTcBoxes] parent slots (-1 padded)
+  const float* img_c;    // child coefficients' operand images [nslots_c][kImgFloats], per rhs istride_c
+  size_t istride_c;
   int* err;              // device status word: bit 0 set when a wait on the tensor cores timed out
   uint64_t wait_ns;      // limit of each wait (1 s; 1 ms under fault injection)
   int inject;            // fault injection: the first unit's MMAs are not issued, so its wait expires
 };
 
-// Software pipeline per unit u (one thread issues the MMAs):
-//   wait MMA(u-1) -> A(u) into shared memory, prefetch A(u+1) -> barrier -> issue MMA(u) into
-//   accumulator u % 2 -> epilogue of unit u-1 from accumulator (u-1) % 2 and basis B(u+1) into
-//   buffer (u+1) % 2, both while MMA(u) runs.
-__global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTabs TT) {
+// Per unit u (one thread issues the copies and the MMAs; phases of both barriers flip per unit):
+//   unit points' coordinates (warp 0) -> basis B(u) (all) -> wait A(u) -> MMA(u) -> wait ->
+//   copy A(u+1) (in flight during the rest) -> epilogue(u) into the parent columns.
+__global__ void __launch_bounds__(tc::kThreads, 2) k_up_tc(UpArgs<float> A, TcTabs TT) {
   using T = float;
   __shared__ SmallMaps<T> M;
-  __shared__ uint64_t mbar;
+  __shared__ __align__(8) uint64_t bar_a, bar_m;
   __shared__ uint32_t tmem_base;
-  extern __shared__ unsigned char tc_raw[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* Ahi = sm;
-  unsigned char* Alo = sm + tc::kOffAlo;
-  T* vals = reinterpret_cast<T*>(sm + tc::kOffVals);
-  UpCheb (*cheb)[kQ] = reinterpret_cast<UpCheb (*)[kQ]>(sm + tc::kOffCheb);
-  float4 (*fac)[kQ] = reinterpret_cast<float4 (*)[kQ]>(sm + tc::kOffFac);
-  T (*Xp)[3] = reinterpret_cast<T (*)[3]>(sm + tc::kOffXp);
+  __shared__ int nact_s;
+  __shared__ int slot[kTcBoxes];
+  extern __shared__ __align__(16) unsigned char tc_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~uintptr_t(1023));
+  float4* pts = reinterpret_cast<float4*>(sm + tc::kOffPts);   // [32][3]
+  float4* fac = reinterpret_cast<float4*>(sm + tc::kOffFac);   // [32]
+  T (*Xp)[4] = reinterpret_cast<T (*)[4]>(sm + tc::kOffXp);
   int (*cs)[kTcMaxUnits] = reinterpret_cast<int (*)[kTcMaxUnits]>(sm + tc::kOffCs);
   int* units = reinterpret_cast<int*>(sm + tc::kOffUnit);
-  int (*order)[kQ] = reinterpret_cast<int (*)[kQ]>(sm + tc::kOffOrder);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
   A.coefs_p += blockIdx.y * A.cstride_p;
-  int slot[kTcBoxes], Pb[kTcBoxes];
-#pragma unroll
-  for (int b = 0; b < kTcBoxes; ++b) {
-    slot[b] = __ldg(TT.item + (size_t)blockIdx.x * kTcBoxes + b);
-    Pb[b] = slot[b] >= 0 ? __ldg(A.slot_box + slot[b]) : -1;
+  const float* imgc = TT.img_c + blockIdx.y * TT.istride_c;
+  float* imgp = A.img_p ? A.img_p + blockIdx.y * A.istride_p : nullptr;
+  if (t < kTcBoxes) slot[t] = __ldg(TT.item + (size_t)blockIdx.x * kTcBoxes + t);
+  init_maps(M);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar_a)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&bar_m)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_base)),
+                 "r"(tc::kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tm = tmem_base;
+  const uint32_t tlane = tm + ((uint32_t)(32 * warp) << 16);   // this warp's tensor-memory lanes
   const int ci = A.slot_upidx[slot[0]];   // every item holds at least one slot, first
   const cone_key pcone = A.slot_cone[slot[0]];
   const int u0 = __ldg(TT.unit_ptr + ci);
   int nunits = __ldg(TT.unit_ptr + ci + 1) - u0;
-  init_maps(M);
-  // clear operands (padding rows and columns must hold zeros) and values
-  for (int e = t; e < tc::kOffCheb / 16; e += blockDim.x) reinterpret_cast<float4*>(sm)[e] = make_float4(0, 0, 0, 0);
   for (int e = t; e < nunits; e += blockDim.x) units[e] = __ldg(TT.unit + u0 + e);
-  for (int e = t; e < 8 * kQ; e += blockDim.x) order[e / kQ][e % kQ] = __ldg(TT.order + (size_t)ci * 8 * kQ + e);
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&mbar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (t < kQ) {
+    cone_point(M, A.cgp, pcone, t, Xp[t]);
+    Xp[t][3] = sqrt_t(Xp[t][0] * Xp[t][0] + Xp[t][1] * Xp[t][1] + Xp[t][2] * Xp[t][2]);
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc::smem_u32(&tmem_base))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  // parent values start at zero (columns 0..79 of every lane)
+#pragma unroll
+  for (int c = 0; c < 80; c += 16) tc::st_x16_zero(tlane + c);
+  tc::wait_st();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t td = tmem_base;
-  if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
   // child slot of every (box, unit): -1 where the box has no child in the unit's octant
   for (int e = t; e < kTcBoxes * nunits; e += blockDim.x) {
     const int b = e / nunits, u = e - b * nunits;
     const int tk = units[u], o = (tk >> 16) & 7;
     const size_t g = (size_t)ci * 8 + o;
-    const int q0 = order[o][tk & 255];
-    const int cb = Pb[b] >= 0 ? __ldg(A.child + 8 * Pb[b] + o) : -1;
+    const int q0 = __ldg(TT.order + g * kQ + (tk & 255));
+    const int P = slot[b] >= 0 ? __ldg(A.slot_box + slot[b]) : -1;
+    const int cb = P >= 0 ? __ldg(A.child + 8 * P + o) : -1;
     cs[b][u] = cb >= 0 ? __ldg(A.cmap_c + (size_t)cb * A.ncomp_c + __ldg(A.up_cc + g * kQ + q0)) : -1;
   }
   __syncthreads();
   // keep the units in which some box of the item has a child (in place, order kept: one warp
   // reads a group of 32 units, then writes them to positions at or below the group's start)
-  __shared__ int nact_s;
   if (warp == 0) {
     int nact = 0;
-    for (int u0g = 0; u0g < nunits; u0g += 32) {
-      const int u = u0g + lane;
+    for (int g0 = 0; g0 < nunits; g0 += 32) {
+      const int u = g0 + lane;
       int tk = 0, c[kTcBoxes];
       bool any = false;
       if (u < nunits) {
@@ -911,180 +1003,218 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_up_tc(UpArgs<float> A, TcTa
           any = any || c[b] >= 0;
         }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, any);
+      const unsigned msk = __ballot_sync(0xffffffffu, any);
       __syncwarp();
       if (any) {
-        const int pos = nact + __popc(m & ((1u << lane) - 1u));
+        const int pos = nact + __popc(msk & ((1u << lane) - 1u));
         units[pos] = tk;
 #pragma unroll
         for (int b = 0; b < kTcBoxes; ++b) cs[b][pos] = c[b];
       }
-      nact += __popc(m);
+      nact += __popc(msk);
       __syncwarp();
     }
     if (lane == 0) nact_s = nact;
   }
   __syncthreads();
   nunits = nact_s;
-  // per (octant, parent point): Chebyshev values in the child cone and the re-centring factor
-  // (box-independent; octants without a child in any box of this cone are not used)
+  auto issue_a = [&](int u) {   // thread 0: the operand images of unit u's child cones
+    uint32_t bytes = 0;
+#pragma unroll
+    for (int b = 0; b < kTcBoxes; ++b) bytes += cs[b][u] >= 0 ? 2u * tc::kImgBytes : 0u;
+    tc::expect_tx(&bar_a, bytes);
+#pragma unroll
+    for (int b = 0; b < kTcBoxes; ++b) {
+      if (cs[b][u] < 0) continue;
+      const float* src = imgc + (size_t)cs[b][u] * kImgFloats;
+      tc::bulk_g2s(sm + b * tc::kImgBytes, src, tc::kImgBytes, &bar_a);
+      tc::bulk_g2s(sm + tc::kOffAlo + b * tc::kImgBytes, src + kImgFloats / 2, tc::kImgBytes, &bar_a);
+    }
+  };
+  if (t == 0 && nunits > 0) issue_a(0);
   const T off = (T)(0.5 * A.Hc);
   const T kk[2] = {A.ke, A.ki};
-  for (int e = t; e < 8 * kQ; e += blockDim.x) {
-    const int o = e / kQ, q = e % kQ;
-    const int ccx = __ldg(A.up_cc + ((size_t)ci * 8 + o) * kQ + q);
-    if (ccx < 0) continue;
-    const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
-    const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
-    T ts, tt, tp, rc, sth, cth, sph, cph;
-    local_coords(A.cgc, A.ckeys_c[ccx], x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
-    T v5[5], v3[3];
-    UpCheb& C = cheb[o][q];
-    cheb_vals<T, 5>(tp, v5);
-    C.tp[0] = v5[1]; C.tp[1] = v5[2]; C.tp[2] = v5[3]; C.tp[3] = v5[4];
-    cheb_vals<T, 5>(tt, v5);
-    C.tt[0] = v5[1]; C.tt[1] = v5[2]; C.tt[2] = v5[3]; C.tt[3] = v5[4];
-    cheb_vals<T, 3>(ts, v3);
-    C.ts[0] = v3[1]; C.ts[1] = v3[2];
-    const T rp = sqrt_t(Xp[q][0] * Xp[q][0] + Xp[q][1] * Xp[q][1] + Xp[q][2] * Xp[q][2]);
-    const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
-    T sn0, cs0, sn1, cs1;
-    sincos_t(kk[0] * dr, &sn0, &cs0);
-    sincos_t(kk[1] * dr, &sn1, &cs1);
-    const T a = rp / rc;
-    fac[o][q] = make_float4(a * cs0, a * sn0, a * cs1, a * sn1);
-  }
-  // A operand of one unit, prefetched into registers: task (box b, chunk kc, field = lane) is the
-  // four coefficients k = 4 kc .. 4 kc + 3 of one field (coalesced 128-byte coefficient rows)
-  constexpr int kChunks = (kQ + 3) / 4;                                    // 19 (k = 75 is padding)
-  constexpr int kTasks = kTcBoxes * kChunks;                               // 76 per warp round
-  constexpr int kAPer = (kTasks + tc::kThreads / 32 - 1) / (tc::kThreads / 32);   // 10
-  float pre[kAPer][4];
-  auto load_a = [&](int u) {
-#pragma unroll
-    for (int i = 0; i < kAPer; ++i) {
-      const int bk = warp + 8 * i;
-      const int b = bk / kChunks, kc = bk - b * kChunks;
-      const int sl = bk < kTasks ? cs[b][u] : -1;
-      const T* C = A.coefs_c + (size_t)(sl >= 0 ? sl : 0) * kQ * 32 + lane;
+  const T sgn = (lane & 1) ? T(1) : T(-1);
+  const int ks = lane >> 4;
+  const uint32_t id = tc::idesc(128, tc::kN);
+  uint32_t ph = 0;
+  bool ok = true, a_pending = nunits > 0, m_pending = false;
+  for (int u = 0; u < nunits; ++u) {
+    const int tk = units[u], r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
+    const size_t g = (size_t)ci * 8 + o;
+    // the unit's points: Chebyshev values in the child cone and re-centring factors (warp 0)
+    if (warp == 0 && lane < len) {
+      const int q = __ldg(TT.order + g * kQ + r0 + lane);
+      const int ccx = __ldg(A.up_cc + g * kQ + q);
+      const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
+      const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
+      T ts, tt, tp, rc, sth, cth, sph, cph;
+      local_coords(A.cgc, A.ckeys_c[ccx], x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
+      T v5[5], w5[5], v3[3];
+      cheb_vals<T, 3>(ts, v3);
+      cheb_vals<T, 5>(tt, v5);
+      cheb_vals<T, 5>(tp, w5);
+      pts[3 * lane] = make_float4(v3[1], v3[2], v5[1], v5[2]);
+      pts[3 * lane + 1] = make_float4(v5[3], v5[4], w5[1], w5[2]);
+      pts[3 * lane + 2] = make_float4(w5[3], w5[4], __int_as_float(q), 0.f);
+      const T rp = Xp[q][3];
+      const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
+      T sn0, cs0, sn1, cs1;
+      sincos_t(kk[0] * dr, &sn0, &cs0);
+      sincos_t(kk[1] * dr, &sn1, &cs1);
+      const T a = rp / rc;
+      fac[lane] = make_float4(a * cs0, a * sn0, a * cs1, a * sn1);
+    }
+    __syncthreads();
+    // basis B(u): (point n, chunk kc) tasks, hi and lo parts (rows n >= len are not read back)
+    for (int e = t; e < len * 20; e += blockDim.x) {
+      const int n = e / 20, kc = e - n * 20;
+      const float4 p0 = pts[3 * n], p1 = pts[3 * n + 1], p2 = pts[3 * n + 2];
+      const T TS[3] = {T(1), p0.x, p0.y};
+      const T TV[5] = {T(1), p0.z, p0.w, p1.x, p1.y};
+      const T TP[5] = {T(1), p1.z, p1.w, p2.x, p2.y};
+      T v[4], h[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int k = 4 * kc + j;
-        pre[i][j] = (sl >= 0 && k < kQ) ? __ldg(C + k * 32) : 0.f;
+        v[j] = k < kQ ? TS[k / 25] * TV[(k / 5) % 5] * TP[k % 5] : T(0);
+        h[j] = tf32_hi(v[j]);
       }
+      const int bo = tc::kmaj_off(n, kc);
+      *reinterpret_cast<float4*>(sm + tc::kOffB + bo) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(sm + tc::kOffBlo + bo) = make_float4(v[0] - h[0], v[1] - h[1], v[2] - h[2], v[3] - h[3]);
     }
-  };
-  auto store_a = [&]() {
-#pragma unroll
-    for (int i = 0; i < kAPer; ++i) {
-      const int bk = warp + 8 * i;
-      if (bk < kTasks) {
-        const int b = bk / kChunks, kc = bk - b * kChunks;
-        float h[4], l[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          h[j] = tc::hi(pre[i][j]);
-          l[j] = pre[i][j] - h[j];
-        }
-        const int ao = tc::kmaj_off(32 * b + lane, kc);
-        *reinterpret_cast<float4*>(Ahi + ao) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4*>(Alo + ao) = make_float4(l[0], l[1], l[2], l[3]);
-      }
-    }
-  };
-  auto build_b = [&](int u) {   // lane = point of unit u, warp = range of K chunks
-    const int tk = units[u], len = (tk >> 8) & 255, o = (tk >> 16) & 7;
-    if (lane < len) {
-      unsigned char* Bb = sm + tc::kOffB + (u & 1) * 2 * tc::kBBytes;
-      tc_basis_warp(warp, cheb[o][order[o][(tk & 255) + lane]], Bb, Bb + tc::kBBytes, lane);
-    }
-  };
-  const float sgn = (lane & 1) ? 1.f : -1.f;
-  const int ks = lane >> 4, eb = warp & 3, eh = warp >> 2;   // epilogue: box eb, points 16 eh .. 16 eh + 15
-  auto epilogue = [&](int u) {
-    const int tk = units[u], len = (tk >> 8) & 255, o = (tk >> 16) & 7, st = tk & 255;
-    if (slot[eb] < 0 || cs[eb][u] < 0 || 16 * eh >= len) return;   // warp-uniform
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(td + ((uint32_t)(32 * eb) << 16) + (uint32_t)((u & 1) * tc::kN + 16 * eh)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    T* vb = vals + eb * kQ * kVS;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (16 * eh + j < len) {
-        const int q = order[o][st + 16 * eh + j];
-        const T v = __uint_as_float(r[j]);
-        const T w = __shfl_xor_sync(0xffffffffu, v, 1);
-        const float4 F = fac[o][q];
-        const T fr = ks ? F.z : F.x, fi = ks ? F.w : F.y;
-        vb[q * kVS + lane] += fmaf(v, fr, sgn * fi * w);
-      }
-    }
-  };
-  __syncthreads();
-  if (nunits > 0) {
-    load_a(0);
-    build_b(0);
-  }
-  bool ok = true;
-  for (int u = 0; u < nunits; ++u) {
-    if (u > 0) {   // MMA(u-1) done: A free, accumulator (u-1) % 2 ready
-      ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((u - 1) & 1), TT.wait_ns)) != 0;
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    }
-    store_a();
-    if (u + 1 < nunits) load_a(u + 1);   // in flight during this unit's MMA and the work beside it
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B visible to the tensor cores
+    ok = __syncthreads_and(tc::wait(&bar_a, ph, TT.wait_ns)) != 0;   // A(u) landed
+    if (!ok) break;
+    a_pending = false;
+    tc::fence_after();
     if (t == 0 && !(TT.inject && u == 0)) {
-      const uint32_t id = tc::idesc(128, tc::kN);
-      const uint32_t aH = tc::smem_u32(Ahi), aL = tc::smem_u32(Alo);
-      const uint32_t bH = tc::smem_u32(sm + tc::kOffB + (u & 1) * 2 * tc::kBBytes), bL = bH + tc::kBBytes;
-      const uint32_t dcol = td + (uint32_t)((u & 1) * tc::kN);
+      const uint32_t aH = tc::smem_u32(sm), aL = tc::smem_u32(sm + tc::kOffAlo);
+      const uint32_t bH = tc::smem_u32(sm + tc::kOffB), bL = tc::smem_u32(sm + tc::kOffBlo);
 #pragma unroll 1
       for (int pass = 0; pass < 3; ++pass) {
         const uint32_t ab = pass == 2 ? aL : aH, bb = pass == 1 ? bL : bH;
 #pragma unroll
         for (int k8 = 0; k8 < tc::kK / 8; ++k8)
-          tc::mma(dcol, tc::sdesc(ab + k8 * 256, 128, 2560, 0), tc::sdesc(bb + k8 * 256, 128, 2560, 0), id,
+          tc::mma(tm + tc::kColD, tc::sdesc(ab + k8 * 256, 128, 2560, 0), tc::sdesc(bb + k8 * 256, 128, 2560, 0), id,
                   (pass | k8) ? 1u : 0u);
       }
-      tc::commit(&mbar);
+      tc::commit(&bar_m);
     }
-    if (u > 0) epilogue(u - 1);
-    if (u + 1 < nunits) build_b(u + 1);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  }
-  if (ok && nunits > 0) {
-    ok = __syncthreads_and(tc::wait(&mbar, (uint32_t)((nunits - 1) & 1), TT.wait_ns)) != 0;
-    if (ok) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      epilogue(nunits - 1);
+    m_pending = true;
+    ok = __syncthreads_and(tc::wait(&bar_m, ph, TT.wait_ns)) != 0;   // MMA(u) done: D ready, A free
+    if (!ok) break;
+    m_pending = false;
+    tc::fence_after();
+    ph ^= 1u;
+    if (t == 0 && u + 1 < nunits) issue_a(u + 1);
+    a_pending = u + 1 < nunits;
+    // epilogue: warp w re-centres box w's columns of D and adds them into the parent columns
+    if (slot[warp] >= 0 && cs[warp][u] >= 0) {
+      float r[32], pv[32];
+      tc::ld_x32(tlane + tc::kColD, r);
+      int qn[32];
+#pragma unroll
+      for (int n = 0; n < 32; ++n) {
+        pv[n] = 0.f;
+        if (n < len) {
+          qn[n] = __float_as_int(pts[3 * n + 2].z);
+          tc::ld_x1(tlane + (uint32_t)qn[n], pv[n]);
+        }
+      }
+      tc::wait_ld_regs(pv);
+#pragma unroll
+      for (int n = 0; n < 32; ++n) {
+        if (n < len) {
+          const T wv = __shfl_xor_sync(0xffffffffu, r[n], 1);
+          const float4 F = fac[n];
+          const T fr = ks ? F.z : F.x, fi = ks ? F.w : F.y;
+          tc::st_x1(tlane + (uint32_t)qn[n], pv[n] + fmaf(r[n], fr, sgn * fi * wv));
+        }
+      }
+      tc::wait_st();
     }
+    tc::fence_before();
+    __syncthreads();
   }
   if (!ok) {
-    // a wait timed out: record it, give the tensor cores a bounded second wait, release and leave
+    // a wait timed out: record it, let the copies and MMAs in flight finish (bounded), release
     if (t == 0) atomicOr(TT.err, 1);
-    tc::wait(&mbar, 0u, TT.wait_ns);
-    tc::wait(&mbar, 1u, TT.wait_ns);
+    if (a_pending) tc::wait(&bar_a, ph, TT.wait_ns);
+    if (m_pending) tc::wait(&bar_m, ph, TT.wait_ns);
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc::fence_before();
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(td) : "memory");
-  if (!ok) return;
-  // values -> coefficients of every slot of the item
-#pragma unroll 1
-  for (int b = 0; b < kTcBoxes; ++b) {
-    if (slot[b] < 0) break;   // slots fill the item from the front
-    vals_to_coefs_block<T, kVS>(M, vals + b * kQ * kVS, A.coefs_p + (size_t)slot[b] * kQ * 32);
+  tc::fence_after();
+  if (ok && slot[warp] >= 0) {
+    // this thread's column (box warp, field lane) of 75 parent values -> coefficients
+    float v[80];
+#pragma unroll
+    for (int c = 0; c < 80; c += 16) tc::ld_x16(tlane + c, v + c);
+    float t5[5];
+#pragma unroll
+    for (int a = 0; a < 15; ++a) {   // phi
+#pragma unroll
+      for (int k = 0; k < 5; ++k) t5[k] = v[a * 5 + k];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        float acc = 0.f;
+#pragma unroll
+        for (int kk2 = 0; kk2 < 5; ++kk2) acc += M.A5[k * 5 + kk2] * t5[kk2];
+        v[a * 5 + k] = acc;
+      }
+    }
+#pragma unroll
+    for (int is = 0; is < 3; ++is)   // theta
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) t5[j] = v[(is * 5 + j) * 5 + k];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          float acc = 0.f;
+#pragma unroll
+          for (int jj = 0; jj < 5; ++jj) acc += M.A5[j * 5 + jj] * t5[jj];
+          v[(is * 5 + j) * 5 + k] = acc;
+        }
+      }
+#pragma unroll
+    for (int jk = 0; jk < 25; ++jk) {   // s
+#pragma unroll
+      for (int i = 0; i < 3; ++i) t5[i] = v[i * 25 + jk];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii) acc += M.A3[i * 3 + ii] * t5[ii];
+        v[i * 25 + jk] = acc;
+      }
+    }
+    T* out = A.coefs_p + (size_t)slot[warp] * kQ * 32 + lane;
+#pragma unroll
+    for (int k = 0; k < kQ; ++k) out[k * 32] = v[k];
+    if (imgp) {   // operand images for the next upward step on the tensor cores
+      float* im = imgp + (size_t)slot[warp] * kImgFloats;
+#pragma unroll
+      for (int kc = 0; kc < 20; ++kc) {
+        float x[4], h[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          x[j] = 4 * kc + j < kQ ? v[4 * kc + j] : 0.f;
+          h[j] = tf32_hi(x[j]);
+        }
+        *reinterpret_cast<float4*>(im + img_off(lane, kc)) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(im + kImgFloats / 2 + img_off(lane, kc)) =
+            make_float4(x[0] - h[0], x[1] - h[1], x[2] - h[2], x[3] - h[3]);
+      }
+    }
   }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(tc::kCols) : "memory");
 }
 
 // ------------------------------------------------------------------ (c) target evaluation
@@ -1385,7 +1515,8 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   {
     const DevLevel& L = p->dl[D];
     LeafArgs<T> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, cone_geom_t<T>(L.cg),
-                  p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki, 16 * (size_t)p->N, L.cstride};
+                  p->x_sorted, (const T*)p->a_sorted, (T*)L.coefs, ke, ki, 16 * (size_t)p->N, L.cstride,
+                  L.img, L.istride};
     int rec = timer_begin(p, TK_LEAF, s);
     if (L.nboxes > 0 && L.max_box_slots > 0) {
       const dim3 grid((unsigned)L.nboxes, (unsigned)((L.max_box_slots + kLeafSlots - 1) / kLeafSlots),
@@ -1420,13 +1551,13 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
       const DevLevel& Pp = p->dl[d - 1];
       UpArgs<T> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, cone_geom_t<T>(Pp.cg),
                   L.cmap, L.ncomp, L.ckeys, cone_geom_t<T>(L.cg), L.H, Pp.up_cc, (const T*)L.coefs, (T*)Pp.coefs, ke, ki,
-                  L.cstride, Pp.cstride};
+                  L.cstride, Pp.cstride, Pp.img, Pp.istride};
       rec = timer_begin(p, TK_UP, s);
       if (Pp.nslots > 0) {
         if constexpr (std::is_same<T, float>::value) {
           if (Pp.tc)
             k_up_tc<<<dim3(Pp.ntc_items, nrhs), tc::kThreads, tc::kSmem, s>>>(
-                U, TcTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr, Pp.tc_item, p->dev_err,
+                U, TcTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr, Pp.tc_item, L.img, L.istride, p->dev_err,
                           p->inject ? 1000000ull : 1000000000ull, p->inject});
           else
             launch_up_simt(U, Pp, Pp.up_mode, nrhs, s);
@@ -1481,7 +1612,8 @@ cudaError_t launch_up_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s) {
   if (Pp.nslots == 0) return cudaSuccess;
   UpArgs<float> U{Pp.slot_box, Pp.slot_cone, Pp.slot_upidx, Pp.child, cone_geom_t<float>(Pp.cg),
                   L.cmap, L.ncomp, L.ckeys, cone_geom_t<float>(L.cg), L.H, Pp.up_cc, (const float*)L.coefs,
-                  (float*)Pp.coefs, (float)p->desc.k_ext, (float)p->desc.k_int, L.cstride, Pp.cstride};
+                  (float*)Pp.coefs, (float)p->desc.k_ext, (float)p->desc.k_int, L.cstride, Pp.cstride,
+                  Pp.img, Pp.istride};
   launch_up_simt(U, Pp, mode, 1, s);
   return cudaGetLastError();
 }

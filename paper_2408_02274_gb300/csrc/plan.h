@@ -130,6 +130,10 @@ struct DevLevel {
   void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan); one buffer
                                   // serves all levels of equal parity (two live levels at a time)
   size_t cstride = 0;             // nslots * 75 * 32: coefficients per right-hand side
+  float* img = nullptr;           // [batch][nslots][2][32 x 80] tensor-core operand images (hi, lo) of the
+                                  // coefficients, when the upward step into level d-1 runs on the tensor
+                                  // cores; one buffer per parity of d, like coefs
+  size_t istride = 0;             // nslots * 5120: images per right-hand side
 };
 
 struct NodeGeom {           // per-node geometry, original order (FP64 SoA)

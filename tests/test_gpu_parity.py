@@ -277,17 +277,18 @@ def test_apply_is_graph_capturable(small, prec):
     plan.close()
 
 
-@pytest.mark.parametrize("prec", [lib.IFGF_FP32, lib.IFGF_FP64])
-def test_plan_estimate_matches_the_created_plan(medium, prec):
+@pytest.mark.parametrize("prec,tc", [(lib.IFGF_FP32, 0), (lib.IFGF_FP32, 1), (lib.IFGF_FP64, 0)])
+def test_plan_estimate_matches_the_created_plan(medium, prec, tc):
     """ifgf_plan_estimate is exact except for the near matrix, which it bounds by counting every
     candidate patch as singular: the byte difference is exactly the nonzero difference times
-    the bytes per nonzero (8 values in the plan's precision + a 4-byte column)."""
+    the bytes per nonzero (8 values in the plan's precision + a 4-byte column).  Refinement adds
+    two vectors per right-hand side, the tensor-core upward step the operand images."""
     prob, qp = medium[0], medium[1]
-    refine = 2 if prec == lib.IFGF_FP32 else 0   # refinement adds two vectors per right-hand side
+    refine = 2 if prec == lib.IFGF_FP32 else 0
     kw = dict(delta=qp.delta, n_beta=qp.n_beta, cov_d=qp.cov_d, gs_iters=qp.gs_iters, precision=prec,
-              ns0=2, na0=3, max_krylov=40, batch=2, refine=refine)
+              ns0=2, na0=3, max_krylov=40, batch=2, refine=refine, upward_tc=tc)
     est = lib.Plan.estimate(prob, **kw)
-    plan = plan_of(prob, qp, precision=prec, ns0=2, na0=3, max_krylov=40, batch=2, refine=refine)
+    plan = plan_of(prob, qp, precision=prec, ns0=2, na0=3, max_krylov=40, batch=2, refine=refine, upward_tc=tc)
     st = plan.stats()
     plan.close()
     el = 8 if prec == lib.IFGF_FP64 else 4
