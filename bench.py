@@ -744,9 +744,14 @@ def run_uneven(args):
 
 
 def run_precond(args):
-    """Learned right preconditioner: train the per-patch network on (v = A e, e) pairs from
-    plain GMRES on random star-shaped bodies (e = converged minus truncated iterates, plus
-    random fields), then compare plain GMRES and flexible GMRES on held-out bodies."""
+    """Right preconditioners in flexible GMRES on random star-shaped dielectric bodies
+    (a = --star-radius, eps_r U[2, 12], cube faces split --star-split x --star-split, N_c =
+    --star-nc): right-scaled GMRES (the plain baseline), the block-Jacobi preconditioner (exact
+    per-patch inverses of the diagonal blocks), and block Jacobi with a learned per-patch
+    correction (a two-layer network trained on (v = A e, e) pairs whose targets are the error the
+    block-Jacobi product leaves).  Training pairs come from training bodies: e = converged minus
+    truncated iterates of plain GMRES, plus random fields.  True residuals |b - A y| / |b| with
+    each plan's forward map."""
     import torch
     import paper_2408_02274_gb300 as lib
     from paper_2408_02274_gb300 import build as libbuild
@@ -756,10 +761,13 @@ def run_precond(args):
     rng = np.random.default_rng(17)
     H = 128
 
+    def bodies(count, seed):
+        return star_batch(count, seed=seed, radius=args.star_radius, split=args.star_split, nc=args.star_nc)
+
     def plan_for(b, batch=2):
         return lib.Plan.from_problem(b, delta=delta_of(b), n_beta=48, cov_d=4.0, precision=lib.IFGF_FP32,
                                      far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, batch=batch,
-                                     max_krylov=args.max_krylov)
+                                     max_krylov=args.max_krylov, gmres_scaling=1)
 
     def incidences(b, n):
         x, _, _ = b.nodes()
@@ -773,11 +781,11 @@ def run_precond(args):
         return torch.from_numpy(np.ascontiguousarray(np.stack(out))).cuda()
 
     t0 = time.perf_counter()
-    Xs, Ts = [], []
-    train = star_batch(args.ntrain, seed=1000)
-    for b in train:
+    Xs, Ts, npairs = [], [], 0
+    for b in bodies(0 if args.skip_learned else args.ntrain, 1000):
         plan = plan_for(b)
-        pc = lib.Preconditioner(plan, hidden=H)                 # used for its feature kernel only
+        plan.block_jacobi()
+        pc = lib.Preconditioner(plan, hidden=H)   # its feature kernel: targets e - A_pp^-1 v per patch
         inc = incidences(b, 2)
         ystar = torch.empty((2, 4, b.n), dtype=torch.complex128, device="cuda")
         plan.solve_batch(inc, ystar, tol=1e-6, max_iter=args.max_krylov)
@@ -786,7 +794,7 @@ def run_precond(args):
             yk = torch.empty_like(ystar)
             plan.solve_batch(inc, yk, tol=1e-12, max_iter=k)
             errs.append(ystar - yk)
-        errs.append(torch.from_numpy(np.stack([random_densities(b.n, 7 * len(Xs) + r) for r in range(2)])).cuda())
+        errs.append(torch.from_numpy(np.stack([random_densities(b.n, 7 * npairs + r) for r in range(2)])).cuda())
         for e in errs:
             e = e.contiguous()
             v = torch.empty_like(e)
@@ -796,48 +804,62 @@ def run_precond(args):
             pc.features(v, e, X, T)
             Xs.append(X)
             Ts.append(T)
+            npairs += 2
         plan.close()
-    X = torch.cat(Xs)
-    T = torch.cat(Ts)
+    X = torch.cat(Xs) if Xs else None
+    T = torch.cat(Ts) if Ts else None
     t_data = time.perf_counter() - t0
-    # train on the first test plan's preconditioner (the weights are plan-independent)
-    test = star_batch(args.ntest, seed=5000)
-    plans = [plan_for(b, batch=1) for b in test]
-    pc0 = lib.Preconditioner(plans[0], hidden=H, seed=2)
-    t0 = time.perf_counter()
-    loss = pc0.train(X, T, steps=args.train_steps, batch=512, lr=1e-3, seed=3)
-    t_train = time.perf_counter() - t0
-    weights = pc0.get()
-    rows = []
-    for b, plan in zip(test, plans):
-        if plan is not plans[0]:
-            lib.Preconditioner(plan, hidden=H, weights=weights)
+    test = bodies(args.ntest, 5000)
+    rows, weights, loss, t_train = [], None, None, 0.0
+    for i, b in enumerate(test):
+        plan = plan_for(b, batch=1)
         inc = incidences(b, 1)
-        x, _, _ = b.nodes()
-        res = {"n": b.n, "eps_r": round(b.eps_int, 3)}
-        for name, fn in (("gmres", plan.solve_batch), ("fgmres", plan.solve_precond)):
+        res = {"n": b.n, "unknowns": 4 * b.n, "patches": b.num_patches, "eps_r": round(b.eps_int, 3)}
+
+        def solve(name, fn):
             y = torch.empty((1, 4, b.n), dtype=torch.complex128, device="cuda")
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             its, rrs, st = fn(inc, y, tol=args.tol, max_iter=args.max_krylov)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t1
-            # true residual |b - A y| / |b| with the plan's forward map and right-hand side
             Ay = torch.empty_like(y)
             plan.apply_batch(y, Ay)
             bb = torch.empty_like(y)
             plan.rhs(inc, bb)
             torch.cuda.synchronize()
-            true_res = float(torch.linalg.norm(bb - Ay) / torch.linalg.norm(bb))
-            res[name] = {"iters": its[0], "relres_estimate": rrs[0], "true_relres": true_res, "status": int(st),
-                         "seconds": dt}
+            res[name] = {"iters": its[0], "relres_estimate": rrs[0],
+                         "true_relres": float(torch.linalg.norm(bb - Ay) / torch.linalg.norm(bb)),
+                         "status": int(st), "seconds": dt}
+
+        solve("gmres_right_scaled", plan.solve_batch)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        plan.block_jacobi()
+        torch.cuda.synchronize()
+        res["block_jacobi_setup_s"] = time.perf_counter() - t1
+        solve("block_jacobi", plan.solve_precond)
+        if X is None:
+            rows.append(res)
+            plan.close()
+            continue
+        if i == 0:   # train on the first test plan (the weights are plan-independent)
+            pc0 = lib.Preconditioner(plan, hidden=H, seed=2)
+            t1 = time.perf_counter()
+            loss = pc0.train(X, T, steps=args.train_steps, batch=512, lr=1e-3, seed=3)
+            t_train = time.perf_counter() - t1
+            weights = pc0.get()
+        else:
+            lib.Preconditioner(plan, hidden=H, weights=weights)
+        solve("block_jacobi_learned", plan.solve_precond)
         rows.append(res)
-    for p in plans:
-        p.close()
-    return {"mode": "precond", "train_bodies": args.ntrain, "samples": int(X.shape[0]), "hidden": H,
-            "data_s": t_data, "train_s": t_train, "train_steps": args.train_steps,
-            "loss_first": float(loss[:50].mean()), "loss_last": float(loss[-50:].mean()), "tol": args.tol,
-            "test": rows}
+        plan.close()
+    return {"mode": "precond", "bodies": f"star a={args.star_radius} lambda, split {args.star_split}, N_c {args.star_nc}",
+            "train_bodies": 0 if X is None else args.ntrain, "pairs": npairs,
+            "samples": 0 if X is None else int(X.shape[0]), "hidden": H, "data_s": t_data, "train_s": t_train,
+            "train_steps": args.train_steps,
+            "loss_first": None if loss is None else float(loss[:50].mean()),
+            "loss_last": None if loss is None else float(loss[-50:].mean()), "tol": args.tol, "test": rows}
 
 
 def run_compare(args):
@@ -1032,6 +1054,10 @@ def main():
     ap.add_argument("--mode", default="solve",
                     choices=["solve", "apply", "batch", "uneven", "precond", "compare", "waveguide", "incidences"])
     ap.add_argument("--ntrain", type=int, default=8)
+    ap.add_argument("--skip-learned", action="store_true", help="precond mode: block Jacobi only, no network")
+    ap.add_argument("--star-radius", type=float, default=0.75, help="precond mode: star bodies' mean radius (lambda)")
+    ap.add_argument("--star-split", type=int, default=4, help="precond mode: cube-face split of the star bodies")
+    ap.add_argument("--star-nc", type=int, default=8, help="precond mode: Chebyshev nodes per patch direction")
     ap.add_argument("--ntest", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--nbodies", type=int, default=16)

@@ -345,8 +345,21 @@ ifgf_status bie_rhs(ifgf_plan plan, int32_t nrhs, const void* inc, void* b, ifgf
  *   before each step goes to `loss` (HOST [steps], may be NULL).  Allocates its scratch on
  *   the first call (and when `batch` grows).  Synchronises `stream`.
  * bie_solve_precond: as bie_solve_batch with flexible GMRES: z_k = M v_k, w = A z_k,
- *   y = Z (H^-1 g); needs an attached network.
+ *   y = Z (H^-1 g); needs an attached network or a built block-Jacobi preconditioner.
+ *
+ * Block-Jacobi preconditioner (ifgf_precond_block_jacobi): per patch the exact inverse of
+ * the operator's diagonal block A_pp (the 4 Nc^2 unknowns of the patch's nodes, rows and
+ * columns; for an IFGF plan its far part is the direct sum that the IFGF approximates),
+ * assembled on the device by probing the operator restricted to self-patch sources and
+ * inverted by Gauss-Jordan with partial pivoting in FP64; stored as P (4 Nc^2)^2 complex128
+ * (allocated with the plan on the first call; also the flexible basis if no network was
+ * attached).  Once built, M = A_pp^{-1} per patch, and with a network attached as well
+ *   z_p = (A_pp^{-1} v)_p + s_p (W2^T relu(W1^T x / s_p + b1) + b2),
+ * a learned correction of the block-Jacobi product, whose training targets
+ * (ifgf_precond_features) become (e_p - (A_pp^{-1} v)_p) / s_p.  Synchronises `stream`;
+ * IFGF_EINTERNAL (with a message) if a block is singular, IFGF_ENOMEM if it does not fit.
  */
+ifgf_status ifgf_precond_block_jacobi(ifgf_plan plan, ifgf_stream stream);
 ifgf_status ifgf_precond_attach(ifgf_plan plan, int32_t hidden, const float* W1, const float* b1, const float* W2,
                                 const float* b2);
 ifgf_status ifgf_precond_get(ifgf_plan plan, float* W1, float* b1, float* W2, float* b2);

@@ -28,7 +28,8 @@ EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_ba
            "ifgf_plan_stats", "ifgf_plan_estimate", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
            "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_far_direct_noalloc", "ifgf_far_field",
-           "ifgf_plan_tune", "ifgf_plan_check", "ifgf_plan_inject", "ifgf_plan_set_residual"]
+           "ifgf_plan_tune", "ifgf_plan_check", "ifgf_plan_inject", "ifgf_plan_set_residual",
+           "ifgf_precond_block_jacobi"]
 
 
 class ifgf_plan_desc(ctypes.Structure):
@@ -139,6 +140,7 @@ def load(path: str = LIB_PATH):
     lib.ifgf_plan_check.argtypes = [vp, vp]
     lib.ifgf_plan_inject.argtypes = [vp, i32]
     lib.ifgf_plan_set_residual.argtypes = [vp, vp]
+    lib.ifgf_precond_block_jacobi.argtypes = [vp, vp]
     for name in EXPORTS:
         if name != "ifgf_status_string":
             getattr(lib, name).restype = ctypes.c_int32
@@ -286,6 +288,11 @@ def ifgf_plan_check(plan, stream=None):
 def ifgf_plan_set_residual(plan, residual):
     """Residual plan of the refinement (None unlinks): the solves form b - A y with its map."""
     _check(load().ifgf_plan_set_residual(plan, residual), "ifgf_plan_set_residual")
+
+
+def ifgf_precond_block_jacobi(plan, stream=None):
+    """Build the block-Jacobi right preconditioner (inverse diagonal blocks) of the plan."""
+    _check(load().ifgf_precond_block_jacobi(plan, _stream(stream)), "ifgf_precond_block_jacobi")
 
 
 def ifgf_plan_inject(plan, which: int):
@@ -642,6 +649,15 @@ class Plan:
 
     def inject(self, which: int):
         ifgf_plan_inject(self.handle, which)
+
+    def block_jacobi(self, stream=None):
+        ifgf_precond_block_jacobi(self.handle, stream)
+
+    def precond_apply(self, v, z, stream=None):
+        """z = M v (block Jacobi and/or the attached network) for complex128 CUDA tensors [nrhs, 4, N]."""
+        nrhs, n4 = _nrhs(v, "v"), 4 * self.N
+        _check(load().ifgf_precond_apply(self.handle, nrhs, _arg(v, "complex128", nrhs * n4, "v"),
+                                         _arg(z, "complex128", nrhs * n4, "z"), _stream(stream)), "ifgf_precond_apply")
 
     def set_residual(self, other):
         """Form the refinement residual with `other`'s map (a Plan of the same body, or None);

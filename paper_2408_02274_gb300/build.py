@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libifgf.so")
 SOURCES = ["api.cu", "host_setup.cpp", "tree_api.cpp", "noalloc.cu", "setup_kernels.cu", "combine.cu", "near_direct.cu", "ifgf.cu",
-           "gmres.cu", "precond.cu", "farfield.cu"]
+           "gmres.cu", "precond.cu", "farfield.cu", "blockjacobi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

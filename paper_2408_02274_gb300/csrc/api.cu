@@ -414,6 +414,7 @@ void build(ifgf_plan_t* p) {
   p->stats.levels = t.D;
   check(setup_combine_kernels(), "combine kernel attributes");
   check(setup_ifgf_kernels(), "IFGF kernel attributes");
+  check(setup_bj_kernels(), "block-Jacobi kernel attributes");
   // ---------------- per-apply buffers and GMRES workspace
   const size_t el = store64(d) ? sizeof(double) : sizeof(float);
   const size_t el_s = ifgf64(d) ? sizeof(double) : sizeof(float);   // weighted densities read by IFGF
@@ -948,6 +949,15 @@ ifgf_status ifgf_apply_fields(ifgf_plan p, const void* phi, void* f28, int32_t w
   return IFGF_OK;
 }
 
+// z = M v for the right preconditioner: the block-Jacobi inverse and/or the network (with both,
+// the network's output corrects the block-Jacobi product).
+static cudaError_t precond_apply(ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (p->bj.inv) e = launch_bj_apply(p, nrhs, v, z, s);
+  if (e == cudaSuccess && p->pc.hidden > 0) e = launch_mlp_apply(p, nrhs, v, z, s, p->bj.inv ? z : v);
+  return e;
+}
+
 // Reads and clears the plan's device status word (after the work queued on s); *word = its value.
 static cudaError_t take_status_word(ifgf_plan_t* p, cudaStream_t s, int* word) {
   *word = 0;
@@ -1027,7 +1037,7 @@ static cudaError_t refine(ifgf_plan_t* p, int nrhs, double tol, int max_iter, co
 static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double tol, int32_t max_iter, void* y,
                               int32_t* iters, double* relres, ifgf_stream stream, bool flexible) {
   if (!p || !inc || !y || !(tol > 0) || max_iter < 1) return IFGF_EINVAL;
-  if (flexible && p->pc.hidden == 0) return IFGF_EINVAL;
+  if (flexible && p->pc.hidden == 0 && !p->bj.inv) return IFGF_EINVAL;
   if (nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
   if (max_iter > p->gm.max_iter) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
@@ -1054,9 +1064,7 @@ static ifgf_status solve_impl(ifgf_plan p, int32_t nrhs, const void* inc, double
       ++p->launches;
       return er != cudaSuccess ? er : forward(p, tmp, w, nrhs, st);
     };
-    MatvecFn pc = [p, nrhs](const double* v, double* z, cudaStream_t st) {
-      return launch_mlp_apply(p, nrhs, v, z, st);
-    };
+    MatvecFn pc = [p, nrhs](const double* v, double* z, cudaStream_t st) { return precond_apply(p, nrhs, v, z, st); };
     e = gmres_run(p, mv, nrhs, tol, max_iter, it.data(), rr.data(), s, flexible ? &pc : nullptr);
     if (e == cudaSuccess && scaled) e = launch_block_scale(p->N, nrhs, cm, cj, p->gm.y, p->gm.y, s);
     if (e == cudaSuccess && p->desc.refine > 0)
@@ -1239,9 +1247,10 @@ ifgf_status ifgf_precond_get(ifgf_plan p, float* W1, float* b1, float* W2, float
 }
 
 ifgf_status ifgf_precond_apply(ifgf_plan p, int32_t nrhs, const void* v, void* z, ifgf_stream stream) {
-  if (!p || !v || !z || v == z || p->pc.hidden == 0 || nrhs < 1 || nrhs > p->batch) return IFGF_EINVAL;
+  if (!p || !v || !z || v == z || (p->pc.hidden == 0 && !p->bj.inv) || nrhs < 1 || nrhs > p->batch)
+    return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
-  cudaError_t e = launch_mlp_apply(p, nrhs, (const double*)v, (double*)z, (cudaStream_t)stream);
+  cudaError_t e = precond_apply(p, nrhs, (const double*)v, (double*)z, (cudaStream_t)stream);
   if (e != cudaSuccess) {
     set_last_cuda_error(e, "ifgf_precond_apply", __FILE__, __LINE__);
     p->poisoned = true;
@@ -1254,11 +1263,73 @@ ifgf_status ifgf_precond_features(ifgf_plan p, int32_t nrhs, const void* v, cons
                                   ifgf_stream stream) {
   if (!p || !v || !e || !X || !T || p->pc.hidden == 0 || nrhs < 1) return IFGF_EINVAL;
   if (p->poisoned) return IFGF_ECUDA;
-  cudaError_t err = launch_mlp_features(p, nrhs, (const double*)v, (const double*)e, X, T, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  double* base = nullptr;   // with block Jacobi: the targets are the error left by its product
+  cudaError_t err = cudaSuccess;
+  if (p->bj.inv) {
+    if (nrhs > p->batch) return IFGF_EINVAL;
+    if (cudaMalloc(&base, sizeof(double) * 8 * (size_t)p->N * nrhs) != cudaSuccess) {
+      cudaGetLastError();
+      return IFGF_ENOMEM;
+    }
+    err = launch_bj_apply(p, nrhs, (const double*)v, base, s);
+  }
+  if (err == cudaSuccess) err = launch_mlp_features(p, nrhs, (const double*)v, (const double*)e, X, T, s, base);
+  if (base) {
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    cudaFree(base);
+  }
   if (err != cudaSuccess) {
     set_last_cuda_error(err, "ifgf_precond_features", __FILE__, __LINE__);
     p->poisoned = true;
     return IFGF_ECUDA;
+  }
+  return IFGF_OK;
+}
+
+ifgf_status ifgf_precond_block_jacobi(ifgf_plan p, ifgf_stream stream) {
+  if (!p) return IFGF_EINVAL;
+  if (p->poisoned) return IFGF_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = 4 * p->nc * p->nc;
+  int* ipiv = nullptr;
+  int* err_dev = nullptr;
+  try {
+    Alloc A{p};
+    if (!p->bj.inv) {
+      p->bj.inv = A.dev<double>(2 * (size_t)p->P * m * m);
+      p->bj.m = m;
+    }
+    if (!p->pc.Z)   // the flexible-GMRES basis (also allocated by ifgf_precond_attach)
+      p->pc.Z = A.dev<double>(2 * 4 * (size_t)p->N * (p->gm.max_iter + 1) * p->batch);
+  } catch (const std::exception&) {
+    cudaGetLastError();
+    return IFGF_ENOMEM;
+  }
+  if (cudaMalloc(&ipiv, sizeof(int) * (size_t)p->P * m) != cudaSuccess ||
+      cudaMalloc(&err_dev, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(ipiv);
+    return IFGF_ENOMEM;
+  }
+  // probe buffers: the first two right-hand-side blocks of the Krylov basis (free between solves)
+  double* yb = p->gm.V;
+  double* ob = p->gm.V + 8 * (size_t)p->N * p->batch;
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(err_dev, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = bj_build(p, yb, ob, ipiv, err_dev, s);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(ipiv);
+  cudaFree(err_dev);
+  if (e != cudaSuccess) {
+    set_last_cuda_error(e, "ifgf_precond_block_jacobi", __FILE__, __LINE__);
+    p->poisoned = true;
+    return IFGF_ECUDA;
+  }
+  if (herr != 0) {
+    p->bj.inv = nullptr;   // stays allocated with the plan; not used
+    set_status_detail(IFGF_EINTERNAL, "ifgf_precond_block_jacobi: a diagonal block is singular");
+    return IFGF_EINTERNAL;
   }
   return IFGF_OK;
 }

@@ -69,10 +69,20 @@ int timer_begin(ifgf_plan_t* p, int kind, cudaStream_t s);   // -1 when timing i
 void timer_end(ifgf_plan_t* p, int rec, cudaStream_t s);
 cudaError_t timer_flush(ifgf_plan_t* p);
 
+// ---- self-patch parts of the operator (near_direct.cu), block-Jacobi preconditioner (blockjacobi.cu)
+cudaError_t launch_near_self(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
+cudaError_t launch_far_self(const ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
+cudaError_t setup_bj_kernels();
+cudaError_t launch_bj_apply(const ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s);
+cudaError_t bj_build(ifgf_plan_t* p, double* yb, double* ob, int* ipiv, int* err_dev, cudaStream_t s);
+
 // ---- learned preconditioner (precond.cu)
-cudaError_t launch_mlp_apply(const ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s);
+// z = base + s MLP(v / s) per patch (base = v when null; base may equal z)
+cudaError_t launch_mlp_apply(const ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s,
+                             const double* base = nullptr);
+// X = v / s, T = (e - base) / s per patch (base = v when null)
 cudaError_t launch_mlp_features(const ifgf_plan_t* p, int nrhs, const double* v, const double* e, float* X, float* T,
-                                cudaStream_t s);
+                                cudaStream_t s, const double* base = nullptr);
 cudaError_t mlp_refresh_bf16(ifgf_plan_t* p, cudaStream_t s);
 cudaError_t mlp_train(ifgf_plan_t* p, int64_t nsamples, const float* X, const float* T, int steps, int batch, float lr,
                       uint64_t seed, float* loss, cudaStream_t s);

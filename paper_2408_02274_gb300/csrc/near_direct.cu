@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
                                                     const int* __restrict__ leafc,
                                                     const T* __restrict__ a, A ke, A ki,
                                                     T* __restrict__ f28, const int* __restrict__ blocks,
-                                                    int npp) {
+                                                    int npp, int self_patch = 0) {
   __shared__ SrcTile<A> tile[128];
   const size_t rb = blockIdx.y;   // right-hand side of a batched call
   a += rb * 16 * (size_t)N;
@@ -162,10 +162,12 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
   for (int k = 0; k < 56; ++k) acc[k] = A(0);
   const A kk[2] = {ke, ki};
   const A inv4pi = A(1.0 / (4.0 * kPi));
-  for (int base = 0; base < N; base += 128) {
+  // sources: all nodes, or (self_patch, blocks of one patch) only the block's own patch
+  const int sb = self_patch ? l0 / npp * npp : 0, se = self_patch ? min(sb + npp, N) : N;
+  for (int base = sb; base < se; base += 128) {
     __syncthreads();
     int m = base + threadIdx.x;
-    if (m < N) {
+    if (m < se) {
       tile[threadIdx.x].x[0] = (A)(x[3 * (size_t)m] - o0);
       tile[threadIdx.x].x[1] = (A)(x[3 * (size_t)m + 1] - o1);
       tile[threadIdx.x].x[2] = (A)(x[3 * (size_t)m + 2] - o2);
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
       for (int k = 0; k < 16; ++k) tile[threadIdx.x].a[k] = (A)a[16 * (size_t)m + k];
     }
     __syncthreads();
-    const int nt = min(128, N - base);
+    const int nt = min(128, se - base);
     if (!act) continue;
     for (int q = 0; q < nt; ++q) {
       const SrcTile<A>& s = tile[q];
@@ -207,7 +209,66 @@ __global__ void __launch_bounds__(128) k_far_direct(int N, const double* __restr
     for (int k = 0; k < 56; ++k) f28[56 * (size_t)l + k] += (T)acc[k];
 }
 
+// The near matvec restricted to sources in the target's own patch (nodes are patch-major,
+// npp per patch): one warp per target row; for the diagonal blocks of the block-Jacobi
+// preconditioner.  Overwrites f28 like k_near.
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_self(int N, int npp, const int64_t* __restrict__ row_ptr,
+                                                   const int* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ phi, T* __restrict__ f28) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  const size_t rb = blockIdx.y;
+  phi += rb * 16 * (size_t)N;
+  f28 += rb * 56 * (size_t)N;
+  T acc[56];
+#pragma unroll
+  for (int k = 0; k < 56; ++k) acc[k] = T(0);
+  const int patch = row / npp;
+  for (int64_t e = row_ptr[row] + lane; e < row_ptr[row + 1]; e += 32) {
+    const int c = __ldg(col + e);
+    if (c / npp != patch) continue;
+    alignas(16) T w[8], pc[16];
+    ldg_vec<T, 8>(val + 8 * e, w);
+    ldg_vec<T, 16>(phi + 16 * (size_t)c, pc);
+    near_madd(w, pc, acc);
+  }
+#pragma unroll
+  for (int k = 0; k < 56; ++k) acc[k] = warp_sum(acc[k]);
+  T* out = f28 + 56 * (size_t)row;
+#pragma unroll
+  for (int k = 0; k < 56; ++k)
+    if ((k & 31) == lane) out[k] = acc[k];
+}
+
 }  // namespace
+
+cudaError_t launch_near_self(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
+  const int npp = p->desc.nc * p->desc.nc;
+  const unsigned blocks = (unsigned)(((size_t)p->N * 32 + 255) / 256);
+  if (store64(p->desc))
+    k_near_self<double><<<dim3(blocks, nrhs), 256, 0, s>>>(p->N, npp, p->near.row_ptr, p->near.col,
+        p->near.val64, (const double*)p->phi, (double*)p->f28);
+  else
+    k_near_self<float><<<dim3(blocks, nrhs), 256, 0, s>>>(p->N, npp, p->near.row_ptr, p->near.col,
+        p->near.val32, (const float*)p->phi, (float*)p->f28);
+  return cudaGetLastError();
+}
+
+// The direct far sum restricted to sources in the target's own patch (blocks are chunks of one
+// patch in both precisions); accumulates into f28.
+cudaError_t launch_far_self(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
+  const int npp = p->desc.nc * p->desc.nc;
+  const unsigned blocks = (unsigned)(p->P * ((npp + 127) / 128));
+  if (store64(p->desc))
+    k_far_direct<double><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+        (const double*)p->a_orig, p->desc.k_ext, p->desc.k_int, (double*)p->f28, nullptr, npp, 1);
+  else
+    k_far_direct<float><<<dim3(blocks, nrhs), 128, 0, s>>>(p->N, p->geo.x, p->geo.n, p->leafc,
+        (const float*)p->a_orig, (float)p->desc.k_ext, (float)p->desc.k_int, (float*)p->f28, nullptr, npp, 1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_near(const ifgf_plan_t* p, cudaStream_t s, int nrhs) {
   const int threads = p->near_threads;   // 128 or 256 (the kernel's launch bound)

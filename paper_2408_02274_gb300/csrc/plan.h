@@ -198,6 +198,12 @@ struct Precond {
   TrainWork tw;
 };
 
+// Block-Jacobi right preconditioner: inverses of the diagonal blocks (blockjacobi.cu).
+struct BlockJacobi {
+  int m = 0;                    // 4 Nc^2 unknowns per patch
+  double* inv = nullptr;        // [P][m][m] complex128, row-major; null until built
+};
+
 // Per-kernel-kind CUDA-event timing of the per-apply work (optional).
 enum TimedKind { TK_PREP = 0, TK_NEAR, TK_LEAF, TK_UP, TK_TARGET, TK_COMBINE, TK_FAR_DIRECT, TK_GMRES, TK_COUNT };
 struct KernelTimer {
@@ -251,7 +257,8 @@ struct ifgf_plan_t {
   void* f28 = nullptr;          // [batch][N][28][2] scalar fields (plan precision)
   double* phi64 = nullptr;      // [batch][N][8][2] FP64 densities (prep output)
   ifgf::GmresWork gm;
-  ifgf::Precond pc;             // hidden == 0: no preconditioner attached
+  ifgf::Precond pc;             // hidden == 0: no network attached
+  ifgf::BlockJacobi bj;         // inv == nullptr: no block-Jacobi preconditioner built
   ifgf_stats stats{};
   std::vector<void*> allocations;
 };

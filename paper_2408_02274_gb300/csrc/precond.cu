@@ -2,7 +2,8 @@
 // paper solves with plain GMRES).  Per patch p, with v_p the 4 Nc^2 complex
 // unknowns of the patch (the (m.t1, m.t2, j.t1, j.t2) components of its nodes)
 // read as 8 Nc^2 reals x and s_p = |x|:
-//   z_p = v_p + s_p (W2^T relu(W1^T (x / s_p) + b1) + b2),
+//   z_p = v_p + s_p (W2^T relu(W1^T (x / s_p) + b1) + b2)
+// (or, with the block-Jacobi preconditioner built, z_p = (A_pp^{-1} v)_p + the same correction),
 // a two-layer network shared by all patches, BF16 weights with FP32
 // accumulation.  Zero output weights give z = v (plain GMRES).  The network
 // is trained on pairs (v, e) with v = A e: per patch the input x = v_p / s_p and
@@ -41,13 +42,14 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_apply(int N, int npp, int i
                                                            const float* __restrict__ b1,
                                                            const __nv_bfloat16* __restrict__ W2,
                                                            const float* __restrict__ b2, const double* __restrict__ v,
-                                                           double* __restrict__ z) {
+                                                           const double* base, double* z) {
   extern __shared__ float sx[];   // [in] features, then [hid] hidden
   __shared__ float red[kMlpThreads / 32];
   float* sh = sx + in;
   const int p = blockIdx.x;
   const size_t rb = blockIdx.y;
   v += rb * 8 * (size_t)N;
+  base += rb * 8 * (size_t)N;
   z += rb * 8 * (size_t)N;
   float ss = 0;
   for (int f = threadIdx.x; f < in; f += blockDim.x) {
@@ -67,20 +69,22 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_apply(int N, int npp, int i
     float a = b2[f];
     for (int h = 0; h < hid; ++h) a += __bfloat162float(W2[(size_t)h * in + f]) * sh[h];
     const size_t i = feat_index(f, p, npp, N);
-    z[i] = v[i] + (s > 0.f ? (double)(s * a) : 0.0);
+    z[i] = base[i] + (s > 0.f ? (double)(s * a) : 0.0);   // base may be z itself (same element)
   }
 }
 
 // training pairs: rows rb P + p of X = v_p / s_p and T = (e_p - v_p) / s_p (zero rows when s_p = 0)
 __global__ void __launch_bounds__(kMlpThreads) k_mlp_features(int N, int npp, int in, int P,
                                                               const double* __restrict__ v,
-                                                              const double* __restrict__ e, float* __restrict__ X,
+                                                              const double* __restrict__ e,
+                                                              const double* __restrict__ base, float* __restrict__ X,
                                                               float* __restrict__ T) {
   __shared__ float red[kMlpThreads / 32];
   const int p = blockIdx.x;
   const size_t rb = blockIdx.y;
   v += rb * 8 * (size_t)N;
   e += rb * 8 * (size_t)N;
+  base += rb * 8 * (size_t)N;
   const size_t row = (rb * P + p) * (size_t)in;
   float ss = 0;
   for (int f = threadIdx.x; f < in; f += blockDim.x) {
@@ -92,7 +96,7 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_features(int N, int npp, in
   for (int f = threadIdx.x; f < in; f += blockDim.x) {
     const size_t i = feat_index(f, p, npp, N);
     X[row + f] = (float)v[i] * is;
-    T[row + f] = (float)(e[i] - v[i]) * is;
+    T[row + f] = (float)(e[i] - base[i]) * is;
   }
 }
 
@@ -200,17 +204,19 @@ cudaError_t gemm(int M, int Nn, int K, const float* A, int ta, const float* B, i
 
 }  // namespace
 
-cudaError_t launch_mlp_apply(const ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s) {
+cudaError_t launch_mlp_apply(const ifgf_plan_t* p, int nrhs, const double* v, double* z, cudaStream_t s,
+                             const double* base) {
   const Precond& M = p->pc;
   const size_t smem = sizeof(float) * (M.in + M.hidden);
   k_mlp_apply<<<dim3(p->P, nrhs), kMlpThreads, smem, s>>>(p->N, p->nc * p->nc, M.in, M.hidden,
-      (const __nv_bfloat16*)M.W1h, M.b1, (const __nv_bfloat16*)M.W2h, M.b2, v, z);
+      (const __nv_bfloat16*)M.W1h, M.b1, (const __nv_bfloat16*)M.W2h, M.b2, v, base ? base : v, z);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_features(const ifgf_plan_t* p, int nrhs, const double* v, const double* e, float* X, float* T,
-                                cudaStream_t s) {
-  k_mlp_features<<<dim3(p->P, nrhs), kMlpThreads, 0, s>>>(p->N, p->nc * p->nc, p->pc.in, p->P, v, e, X, T);
+                                cudaStream_t s, const double* base) {
+  k_mlp_features<<<dim3(p->P, nrhs), kMlpThreads, 0, s>>>(p->N, p->nc * p->nc, p->pc.in, p->P, v, e,
+                                                           base ? base : v, X, T);
   return cudaGetLastError();
 }
 
