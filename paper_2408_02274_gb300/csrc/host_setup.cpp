@@ -167,12 +167,14 @@ struct ConePoints {
   }
 };
 
-// Group (0 .. kUpGroups-1) of interpolation point q = (is * 5 + it) * 5 + ip: the 25 angular
-// positions (it, ip) in snake order (ip reversed on odd it), cut into chunks of 6, 6, 6, 7.
+// Group (0 .. kUpGroups-1) of interpolation point q = (is * 5 + it) * 5 + ip: the points ranked
+// by angular position (it, ip) in snake order (ip reversed on odd it), radial index is within a
+// position, cut into chunks of 19, 19, 19 and 18 points (balanced warps; neighbouring points,
+// which mostly share child cones, stay together).
 static int up_group(int q) {
-  const int a = q % (kPa * kPa), it = a / kPa, ip = a % kPa;
-  const int sidx = it * kPa + ((it & 1) ? kPa - 1 - ip : ip);
-  return sidx < 6 ? 0 : (sidx < 12 ? 1 : (sidx < 18 ? 2 : 3));
+  const int is = q / (kPa * kPa), a = q % (kPa * kPa), it = a / kPa, ip = a % kPa;
+  const int rank = (it * kPa + ((it & 1) ? kPa - 1 - ip : ip)) * kPs + is;
+  return rank < 19 ? 0 : (rank < 38 ? 1 : (rank < 57 ? 2 : 3));
 }
 
 static void box_center(const HostTree& t, int d, const std::array<int, 3>& ic, double* c) {

@@ -579,33 +579,32 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
     int a = 0;
     for (; a + 1 < len; a += 2) {   // two points at a time (independent sums, distinct points)
       int q[2];
-      float4 P4[2], T4[2], S4[2], F4[2];
+      float4 P4[2], T4[2], S4[2];
+      float2 F2[2];
       float v[2];
 #pragma unroll
       for (int n = 0; n < 2; ++n) {
         q[n] = __shfl_sync(0xffffffffu, myq, a + n);
         const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q[n]]);
         P4[n] = cp[0]; T4[n] = cp[1]; S4[n] = cp[2];
-        F4[n] = fac[o][q[n]];
+        F2[n] = reinterpret_cast<const float2*>(&fac[o][q[n]])[ks];   // this lane's kernel: (re, im)
       }
       up_contract<2>(c, P4, T4, S4, v);
 #pragma unroll
       for (int n = 0; n < 2; ++n) {
         const T wv = __shfl_xor_sync(0xffffffffu, v[n], 1);
-        const T fr = ks ? F4[n].z : F4[n].x, fi = ks ? F4[n].w : F4[n].y;
-        vals[q[n] * kVS + lane] += fmaf(v[n], fr, sgn * fi * wv);
+        vals[q[n] * kVS + lane] += fmaf(v[n], F2[n].x, sgn * F2[n].y * wv);
       }
     }
     if (a < len) {
       const int q = __shfl_sync(0xffffffffu, myq, a);
       const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
       const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
-      const float4 F4 = fac[o][q];
+      const float2 F2 = reinterpret_cast<const float2*>(&fac[o][q])[ks];
       float v[1];
       up_contract<1>(c, P4, T4, S4, v);
       const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
-      const T fr = ks ? F4.z : F4.x, fi = ks ? F4.w : F4.y;
-      vals[q * kVS + lane] += fmaf(v[0], fr, sgn * fi * wv);
+      vals[q * kVS + lane] += fmaf(v[0], F2.x, sgn * F2.y * wv);
     }
   }
   __syncthreads();

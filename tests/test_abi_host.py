@@ -243,11 +243,11 @@ def test_upward_run_tables_partition_every_parent_point():
     x, _, _ = prob.nodes()
     tree = lib.Tree(x, leaf_size=0.25, k_max=prob.k_int, ns0=2, na0=3)
 
-    def group(q):
+    def group(q):   # ranks by snake-ordered angular position, radial index within; 19/19/19/18
         a = q % 25
         it, ip = a // 5, a % 5
-        sidx = it * 5 + (4 - ip if it & 1 else ip)
-        return 0 if sidx < 6 else (1 if sidx < 12 else (2 if sidx < 18 else 3))
+        rank = (it * 5 + (4 - ip if it & 1 else ip)) * 3 + q // 25
+        return 0 if rank < 19 else (1 if rank < 38 else (2 if rank < 57 else 3))
 
     for d in range(3, tree.levels):
         cc, order, task, ptr = tree.upward(d)
