@@ -107,18 +107,26 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const d
   }
 }
 
-// h_rb[j] (+)= sum_blk part_rb[blk][j]
-__global__ void k_reduce_parts(int nblk, int k1, const double* __restrict__ part, size_t pstride,
-                               double* __restrict__ h, size_t hstride, int accumulate) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
+// h_rb[j] (+)= sum_blk part_rb[blk][j]: one warp per j, lanes over the chunks, then a warp
+// reduction in a fixed order (the sums do not depend on timing)
+constexpr int kReduceWarps = 4;
+__global__ void __launch_bounds__(32 * kReduceWarps) k_reduce_parts(int nblk, int k1, const double* __restrict__ part,
+                                                                    size_t pstride, double* __restrict__ h,
+                                                                    size_t hstride, int accumulate) {
+  const int j = blockIdx.x * kReduceWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (j >= k1) return;
   part += blockIdx.y * pstride;
   h += blockIdx.y * hstride;
   double sr = 0, si = 0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     sr += part[2 * ((size_t)b * k1 + j)];
     si += part[2 * ((size_t)b * k1 + j) + 1];
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane != 0) return;
   if (accumulate) {
     h[2 * j] += sr;
     h[2 * j + 1] += si;
@@ -181,12 +189,13 @@ __global__ void k_sub_add(int64_t n2, const double* b, const double* w, double* 
 
 // |w_rb|^2 partials -> out_rb = |w_rb|; one block per right-hand side
 __global__ void k_norm_final(int nblk, const double* __restrict__ part, size_t pstride, double* __restrict__ out) {
-  if (threadIdx.x != 0) return;
-  const size_t rb = blockIdx.x;
+  const size_t rb = blockIdx.x;   // one warp per right-hand side, fixed summation order
+  const int lane = threadIdx.x & 31;
   part += rb * pstride;
   double s = 0;
-  for (int b = 0; b < nblk; ++b) s += part[2 * (size_t)b];
-  out[rb * kScal] = sqrt(s);
+  for (int b = lane; b < nblk; b += 32) s += part[2 * (size_t)b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[rb * kScal] = sqrt(s);
 }
 
 struct Arnoldi {                  // per-right-hand-side arrays and their strides (doubles)
@@ -302,10 +311,12 @@ cudaError_t project(GmresWork& G, const Batch& B, const Arnoldi& R, int k1, int 
   double* hpass = R.h + 2 * (size_t)(G.max_iter + 1);   // second half of each rhs's h block
   k_dots<<<dim3(B.nb, (k1 + kDotJ - 1) / kDotJ, B.nrhs), kDotThreads, 0, s>>>(B.n, k1, G.V, B.ldv, G.w, G.part,
                                                                               B.pstride);
-  k_reduce_parts<<<dim3((k1 + 127) / 128, B.nrhs), 128, 0, s>>>(B.nb, k1, G.part, B.pstride, hpass, R.sh, 0);
+  k_reduce_parts<<<dim3((k1 + kReduceWarps - 1) / kReduceWarps, B.nrhs), 32 * kReduceWarps, 0, s>>>(
+      B.nb, k1, G.part, B.pstride, hpass, R.sh, 0);
   k_combo<<<dim3((unsigned)((B.n + 255) / 256), B.nrhs), 256, 0, s>>>(B.n, k1, nullptr, G.V, B.ldv, hpass, R.sh,
                                                                         G.w, 0);
-  k_reduce_parts<<<dim3((k1 + 127) / 128, B.nrhs), 128, 0, s>>>(B.nb, k1, G.part, B.pstride, R.h, R.sh,
+  k_reduce_parts<<<dim3((k1 + kReduceWarps - 1) / kReduceWarps, B.nrhs), 32 * kReduceWarps, 0, s>>>(
+      B.nb, k1, G.part, B.pstride, R.h, R.sh,
                                                                   first ? 0 : 1);
   return cudaGetLastError();
 }
