@@ -446,7 +446,8 @@ __global__ void __launch_bounds__(kUpThreads) k_up(UpArgs<T> A) {
 // re-centring factor, formed once per (octant, point) in the prologue, are read
 // from shared memory with vector loads, and the 3D Chebyshev sum is contracted
 // separably (over phi, then theta, then s: 74 FMA per lane), two points at a time
-// (two independent FMA streams per warp).  The parent points
+// (two independent FMA streams per warp).  The right-hand sides of a batched call are taken
+// one after the other by the same block, so the prologue serves all of them.  The parent points
 // are split into kUpGroups fixed groups, one per warp, so each warp adds into
 // its own points' values with plain shared-memory adds.
 struct RunTabs {
@@ -505,7 +506,7 @@ constexpr size_t kUpRunSmem = sizeof(UpCheb) * 8 * kQ      // Chebyshev values p
                               + sizeof(float) * kQ * kVS   // parent values
                               + sizeof(float) * kQ * 3;    // parent points
 
-__global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A, RunTabs RT) {
+__global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A, RunTabs RT, int nrhs) {
   using T = float;
   __shared__ SmallMaps<T> M;
   extern __shared__ float4 up_smem[];
@@ -516,14 +517,11 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   T (*Xp)[3] = reinterpret_cast<T (*)[3]>(vals + kQ * kVS);
   const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
-  A.coefs_c += blockIdx.y * A.cstride_c;   // right-hand side of a batched call
-  A.coefs_p += blockIdx.y * A.cstride_p;
   init_maps(M);
   const int P = A.slot_box[pslot], ci = A.slot_upidx[pslot];
   const cone_key pcone = A.slot_cone[pslot];
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
-  for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
   __syncthreads();
   const T off = (T)(0.5 * A.Hc);
   const T kk[2] = {A.ke, A.ki};
@@ -562,54 +560,62 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   // complex re-centring on interleaved (re, im) lanes: with w the partner lane's value,
   // re' = v fr - w fi (even lanes), im' = v fr + w fi (odd lanes)
   const T sgn = (lane & 1) ? T(1) : T(-1);
-  // the warp's own runs (its group of parent points, all octants); runs of absent children
-  // are skipped.  Only this warp adds into these points' values: plain shared-memory adds.
+  const int w0 = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp);
   const int w1 = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp + 1);
-  for (int w = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp); w < w1; ++w) {
-    const int tk = __ldg(RT.task + w);
-    const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
-    if (A.child[8 * P + o] < 0) continue;
-    const size_t g = (size_t)ci * 8 + o;
-    const int myq = lane < len ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
-    // one child slot per run: the host marked every such cone relevant
-    const T* Cg = A.coefs_c + (size_t)cslot[o][__shfl_sync(0xffffffffu, myq, 0)] * kQ * 32 + lane;
-    T c[kQ];
+  // the right-hand sides of a batched call one after the other: the prologue's geometry serves all
+  for (int rb = 0; rb < nrhs; ++rb) {
+    const T* coefs_c = A.coefs_c + rb * A.cstride_c;
+    for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
+    __syncthreads();
+    // the warp's own runs (its group of parent points, all octants); runs of absent children
+    // are skipped.  Only this warp adds into these points' values: plain shared-memory adds.
+    for (int w = w0; w < w1; ++w) {
+      const int tk = __ldg(RT.task + w);
+      const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
+      if (A.child[8 * P + o] < 0) continue;
+      const size_t g = (size_t)ci * 8 + o;
+      const int myq = lane < len ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
+      // one child slot per run: the host marked every such cone relevant
+      const T* Cg = coefs_c + (size_t)cslot[o][__shfl_sync(0xffffffffu, myq, 0)] * kQ * 32 + lane;
+      T c[kQ];
 #pragma unroll
-    for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
-    int a = 0;
-    for (; a + 1 < len; a += 2) {   // two points at a time (independent sums, distinct points)
-      int q[2];
-      float4 P4[2], T4[2], S4[2];
-      float2 F2[2];
-      float v[2];
+      for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
+      int a = 0;
+      for (; a + 1 < len; a += 2) {   // two points at a time (independent sums, distinct points)
+        int q[2];
+        float4 P4[2], T4[2], S4[2];
+        float2 F2[2];
+        float v[2];
 #pragma unroll
-      for (int n = 0; n < 2; ++n) {
-        q[n] = __shfl_sync(0xffffffffu, myq, a + n);
-        const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q[n]]);
-        P4[n] = cp[0]; T4[n] = cp[1]; S4[n] = cp[2];
-        F2[n] = reinterpret_cast<const float2*>(&fac[o][q[n]])[ks];   // this lane's kernel: (re, im)
+        for (int n = 0; n < 2; ++n) {
+          q[n] = __shfl_sync(0xffffffffu, myq, a + n);
+          const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q[n]]);
+          P4[n] = cp[0]; T4[n] = cp[1]; S4[n] = cp[2];
+          F2[n] = reinterpret_cast<const float2*>(&fac[o][q[n]])[ks];   // this lane's kernel: (re, im)
+        }
+        up_contract<2>(c, P4, T4, S4, v);
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+          const T wv = __shfl_xor_sync(0xffffffffu, v[n], 1);
+          vals[q[n] * kVS + lane] += fmaf(v[n], F2[n].x, sgn * F2[n].y * wv);
+        }
       }
-      up_contract<2>(c, P4, T4, S4, v);
-#pragma unroll
-      for (int n = 0; n < 2; ++n) {
-        const T wv = __shfl_xor_sync(0xffffffffu, v[n], 1);
-        vals[q[n] * kVS + lane] += fmaf(v[n], F2[n].x, sgn * F2[n].y * wv);
+      if (a < len) {
+        const int q = __shfl_sync(0xffffffffu, myq, a);
+        const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
+        const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
+        const float2 F2 = reinterpret_cast<const float2*>(&fac[o][q])[ks];
+        float v[1];
+        up_contract<1>(c, P4, T4, S4, v);
+        const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
+        vals[q * kVS + lane] += fmaf(v[0], F2.x, sgn * F2.y * wv);
       }
     }
-    if (a < len) {
-      const int q = __shfl_sync(0xffffffffu, myq, a);
-      const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
-      const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
-      const float2 F2 = reinterpret_cast<const float2*>(&fac[o][q])[ks];
-      float v[1];
-      up_contract<1>(c, P4, T4, S4, v);
-      const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
-      vals[q * kVS + lane] += fmaf(v[0], F2.x, sgn * F2.y * wv);
-    }
+    __syncthreads();
+    vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + rb * A.cstride_p + (size_t)pslot * kQ * 32, 1,
+                                A.img_p ? A.img_p + rb * A.istride_p + (size_t)pslot * kImgFloats : nullptr);
+    __syncthreads();   // vals is cleared for the next right-hand side
   }
-  __syncthreads();
-  vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + (size_t)pslot * kQ * 32, 1,
-                              A.img_p ? A.img_p + blockIdx.y * A.istride_p + (size_t)pslot * kImgFloats : nullptr);
 }
 
 // (b), FP32 variant with a warp per parent slot.  The warp walks the slot's units (the points of
@@ -1503,8 +1509,8 @@ void launch_up_simt(const UpArgs<float>& U, const DevLevel& Pp, int mode, int nr
     k_up_warp<<<dim3((unsigned)((Pp.nslots + kUpWarpW - 1) / kUpWarpW), nrhs), 32 * kUpWarpW, kUpWarpSmem, s>>>(
         U, UnitTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr}, Pp.nslots);
   else
-    k_up_runs<<<dim3(Pp.nslots, nrhs), 32 * kUpRunWarps, kUpRunSmem, s>>>(
-        U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr});
+    k_up_runs<<<dim3(Pp.nslots, 1), 32 * kUpRunWarps, kUpRunSmem, s>>>(
+        U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr}, nrhs);
 }
 
 template <typename T, typename TO = T>
