@@ -426,6 +426,8 @@ def run_gpu(args):
                    "target_ms_per_level": {str(d): [round(float(tune_ms[2 * d]), 3), round(float(tune_ms[2 * d + 1]), 3)]
                                            for d in range(3, st["levels"] + 1)},
                    "near_threads": int(tune_choices[25]),
+                   "leaf_products": "tensor pipe (mma)" if tune_choices[30] == 1 else "SIMT",
+                   "leaf_ms": [round(float(tune_ms[60]), 3), round(float(tune_ms[61]), 3)],
                    "upward_step_per_level": {str(d): ("warp per slot" if tune_choices[32 + d] == 1 else "group runs")
                                              for d in range(3, st["levels"])},
                    "upward_ms_per_level": {str(d): [round(float(tune_ms[64 + 2 * d]), 3),
@@ -522,6 +524,7 @@ def run_apply(args):
         lv = plan.stats()["levels"]
         tuned = {"target_box_chunks_per_level": [int(v) for v in ch[3:lv + 1]],
                  "upward_warp_per_slot_per_level": [int(v) for v in ch[35:32 + lv]],
+                 "leaf_tensor_pipe": int(ch[30]),
                  "near_threads": int(ch[25])}
     y = torch.from_numpy(random_densities(prob.n, 1)).cuda()
     out = torch.empty_like(y)

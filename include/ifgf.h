@@ -451,6 +451,8 @@ ifgf_status ifgf_far_field(ifgf_plan plan, int32_t nrhs, const void* y, int32_t 
  *     or a warp per chunk of 32 targets of one box (choices[d]: 0 or 1; times_ms[2d], [2d+1]:
  *     ms per launch of each);
  *   - the near-field matvec's block size, 128 or 256 threads (choices[25]; times_ms[50], [51]);
+ *   - for an FP32 or mixed IFGF plan, the leaf step (a) with SIMT or tensor-pipe (TF32 mma)
+ *     density products (choices[30]: 0 or 1; times_ms[60], [61]);
  *   - per parent level d of an FP32 or mixed IFGF plan without the tensor-core option, the
  *     upward step (b) into d by runs of point groups or by a warp per parent slot
  *     (choices[32 + d]: 0 or 1; times_ms[64 + 2d], [65 + 2d]).

@@ -884,6 +884,20 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
         }
       }
     }
+    // (a): the FP32 leaf step with SIMT or tensor-pipe density products
+    if (e == cudaSuccess && p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
+      float t[2] = {0.f, 0.f};
+      for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+        e = time_ms(s, reps, [&]() { return launch_leaf_level(p, m, s); }, &t[m]);
+      if (e == cudaSuccess) {
+        p->dl[p->tree.D].leaf_mode = t[1] < t[0] ? 1 : 0;
+        if (choices) choices[30] = p->dl[p->tree.D].leaf_mode;
+        if (times_ms) {
+          times_ms[60] = t[0] / reps;
+          times_ms[61] = t[1] / reps;
+        }
+      }
+    }
     // (b): per parent level, the FP32 SIMT upward step by point-group runs or a warp per slot
     if (e == cudaSuccess && p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
       for (int d = 3; d < p->tree.D && e == cudaSuccess; ++d) {

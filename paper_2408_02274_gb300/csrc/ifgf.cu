@@ -332,6 +332,171 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf(LeafArgs<T> A) {
   }
 }
 
+// (a), FP32 on the tensor pipe: the same sums as k_leaf with the density products as warp-level
+// TF32 matrix multiply-accumulates (mma.sync m16n8k8, three-term hi/lo split for FP32 accuracy,
+// FP32 accumulation).  Per kernel kappa, with g_pj = (r / |X_p - y_j|) e^{i kappa (|X_p - y_j| - r)}
+// and the 8 complex densities a_jd, the values V_pd = sum_j g_pj a_jd are one real product
+//   V[p][(d, part)] = sum_{(j, s)} A[p][(j, s)] B[(j, s)][(d, part)],
+//   A[p][(j, 0)] = Re g_pj, A[p][(j, 1)] = Im g_pj,
+//   B[(j, 0)][(d, re)] = Re a_jd, B[(j, 1)][(d, re)] = -Im a_jd,
+//   B[(j, 0)][(d, im)] = Im a_jd, B[(j, 1)][(d, im)] = Re a_jd,
+// 16 points x 8 (4 sources x 2) per step.  Each lane evaluates g for exactly the entries of the A
+// fragment it holds (points groupID and groupID + 8 of the tile, source threadID_in_group), both
+// kernels from one distance, so the kernel values never leave registers; B comes from the staged
+// densities.  A block takes the 2 x 75 points of two cone segments as 10 tiles of 16, two per warp
+// (5 warps), then the values -> coefficients map and stores of k_leaf.
+constexpr int kLeafMmaWarps = 5;
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(32 * kLeafMmaWarps, 4) k_leaf_mma(LeafArgs<float> A) {
+  using T = float;
+  __shared__ SmallMaps<T> M;
+  __shared__ T pool[kLeafChunk * 20 + 2 * kQ * kVS];
+  T (*src)[4] = reinterpret_cast<T (*)[4]>(pool);
+  T (*sa)[16] = reinterpret_cast<T (*)[16]>(pool + kLeafChunk * 4);
+  T* vbuf = pool + kLeafChunk * 20;
+  const int box = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int gid = lane >> 2, tig = lane & 3;
+  A.a_sorted += blockIdx.z * A.astride;   // right-hand side of a batched call
+  A.coefs += blockIdx.z * A.cstride;
+  if (A.img) A.img += blockIdx.z * A.istride;
+  const int sb = A.box_slot_ptr[box] + blockIdx.y * kLeafSlots;
+  const int se = min(A.box_slot_ptr[box + 1], sb + kLeafSlots);
+  if (sb >= se) return;   // uniform per block
+  init_maps(M);
+  const double c0 = A.box_center[3 * box], c1 = A.box_center[3 * box + 1], c2 = A.box_center[3 * box + 2];
+  const int pb = A.box_pt_ptr[box], pe = A.box_pt_ptr[box + 1];
+  const int nsrc = pe - pb;
+  const T kk[2] = {A.ke, A.ki};
+  auto stage = [&](int cb, int nchunk) {
+    for (int e = t; e < nchunk; e += blockDim.x) {
+      const int m = pb + cb + e;
+      T y0 = (T)(A.x_sorted[3 * (size_t)m] - c0);
+      T y1 = (T)(A.x_sorted[3 * (size_t)m + 1] - c1);
+      T y2 = (T)(A.x_sorted[3 * (size_t)m + 2] - c2);
+      src[e][0] = y0; src[e][1] = y1; src[e][2] = y2;
+      src[e][3] = y0 * y0 + y1 * y1 + y2 * y2;
+      for (int k = 0; k < 16; ++k) sa[e][k] = A.a_sorted[16 * (size_t)m + k];
+    }
+  };
+  const bool staged_once = nsrc <= kLeafChunk;
+  if (staged_once) stage(0, nsrc);
+  for (int s0 = sb; s0 < se; s0 += 2) {
+    __syncthreads();
+    // tiles 2 warp and 2 warp + 1 of the pass: tile u covers points 16 (u % 5) .. of slot s0 + u / 5
+    float acc[2][2][2][4];   // [tile][kernel][n-tile][fragment]
+    T X[2][2][3], R[2][2];   // [tile][row half] point and its distance to the box centre
+    bool tile_on[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = 2 * warp + h, sl = u / 5, q0 = 16 * (u % 5);
+      tile_on[h] = s0 + sl < se;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int q = min(q0 + gid + 8 * r, kQ - 1);   // rows beyond 75 repeat the last point
+        X[h][r][0] = X[h][r][1] = X[h][r][2] = T(0);
+        if (tile_on[h]) cone_point(M, A.cg, A.slot_cone[s0 + sl], q, X[h][r]);
+        R[h][r] = sqrt_t(X[h][r][0] * X[h][r][0] + X[h][r][1] * X[h][r][1] + X[h][r][2] * X[h][r][2]);
+      }
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[h][ks][nt][i] = 0.f;
+    }
+    for (int cb = 0; cb < nsrc; cb += kLeafChunk) {
+      const int nchunk = min(kLeafChunk, nsrc - cb);
+      if (!staged_once) {
+        __syncthreads();
+        stage(cb, nchunk);
+        __syncthreads();
+      }
+      for (int j0 = 0; j0 < nchunk; j0 += 4) {
+        const int j = j0 + tig;
+        const bool jon = j < nchunk;
+        // B fragments (shared by both tiles and both kernels): rows (s, j) = (0, tig), (1, tig),
+        // column 8 nt + gid = (density, part)
+        uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int c = 8 * nt + gid, dd = c >> 1, im = c & 1;
+          const T ar = jon ? sa[j][2 * dd] : T(0), ai = jon ? sa[j][2 * dd + 1] : T(0);
+          const T b0 = im ? ai : ar, b1 = im ? ar : -ai;
+          const T h0 = tf32_hi(b0), h1 = tf32_hi(b1);
+          bh[nt][0] = __float_as_uint(h0);
+          bh[nt][1] = __float_as_uint(h1);
+          bl[nt][0] = __float_as_uint(b0 - h0);
+          bl[nt][1] = __float_as_uint(b1 - h1);
+        }
+        const T sy0 = jon ? src[j][0] : T(0), sy1 = jon ? src[j][1] : T(0), sy2 = jon ? src[j][2] : T(0);
+        const T sy3 = jon ? src[j][3] : T(0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (!tile_on[h]) continue;   // warp-uniform
+          // A fragments: a0 (row gid, Re), a1 (row gid + 8, Re), a2 (row gid, Im), a3 (row gid + 8, Im)
+          uint32_t ah[2][4], al[2][4];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            // g_S(X, y) = (r/|X-y|) exp(i k (|X-y| - r)), |X-y| - r = (|y|^2 - 2 X.y)/(|X-y| + r)
+            const T rr = R[h][r];
+            const T dxy = sy3 - T(2) * (X[h][r][0] * sy0 + X[h][r][1] * sy1 + X[h][r][2] * sy2);
+            const T d = sqrt_t(rr * rr + dxy);
+            const T rd = jon ? leaf_div(rr, d) : T(0);
+            const T dd = leaf_div(dxy, d + rr);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              T sn, cs;
+              leaf_sincos(kk[ks] * dd, &sn, &cs);
+              const T gr = rd * cs, gi = rd * sn;
+              const T hr = tf32_hi(gr), hi = tf32_hi(gi);
+              ah[ks][r] = __float_as_uint(hr);
+              ah[ks][r + 2] = __float_as_uint(hi);
+              al[ks][r] = __float_as_uint(gr - hr);
+              al[ks][r + 2] = __float_as_uint(gi - hi);
+            }
+          }
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+              mma_tf32(acc[h][ks][nt], ah[ks], bh[nt]);
+              mma_tf32(acc[h][ks][nt], ah[ks], bl[nt]);
+              mma_tf32(acc[h][ks][nt], al[ks], bh[nt]);
+            }
+        }
+      }
+    }
+    // D fragments -> values: c0 (row gid, column 2 tig), c1 (+1), c2 / c3 (row gid + 8)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!tile_on[h]) continue;
+      const int u = 2 * warp + h, sl = u / 5, q0 = 16 * (u % 5);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int q = q0 + gid + 8 * (i >> 1);
+        if (q >= kQ) continue;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt)
+            vbuf[(sl * kQ + q) * kVS + 16 * ks + 8 * nt + 2 * tig + (i & 1)] = acc[h][ks][nt][i];
+      }
+    }
+    __syncthreads();
+    vals_to_coefs_block<T, kVS>(M, vbuf, A.coefs + (size_t)s0 * kQ * 32, min(2, se - s0),
+                                A.img ? A.img + (size_t)s0 * kImgFloats : nullptr);
+  }
+}
+
 // ------------------------------------------------------------------ (b) upward pass
 constexpr int kUpThreads = 128;
 
@@ -1526,7 +1691,14 @@ cudaError_t run_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
     if (L.nboxes > 0 && L.max_box_slots > 0) {
       const dim3 grid((unsigned)L.nboxes, (unsigned)((L.max_box_slots + kLeafSlots - 1) / kLeafSlots),
                       (unsigned)nrhs);
-      k_leaf<T><<<grid, kLeafThreads, 0, s>>>(A);
+      if constexpr (std::is_same<T, float>::value) {
+        if (L.leaf_mode == 1)
+          k_leaf_mma<<<grid, 32 * kLeafMmaWarps, 0, s>>>(A);
+        else
+          k_leaf<T><<<grid, kLeafThreads, 0, s>>>(A);
+      } else {
+        k_leaf<T><<<grid, kLeafThreads, 0, s>>>(A);
+      }
     }
     timer_end(p, rec, s);
     ++p->launches;
@@ -1620,6 +1792,23 @@ cudaError_t launch_up_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s) {
                   (float*)Pp.coefs, (float)p->desc.k_ext, (float)p->desc.k_int, L.cstride, Pp.cstride,
                   Pp.img, Pp.istride};
   launch_up_simt(U, Pp, mode, 1, s);
+  return cudaGetLastError();
+}
+
+// The FP32 leaf step alone in `mode` (0 SIMT, 1 tensor-pipe products), for the autotuner; writes
+// the leaf level's coefficients like an apply.
+cudaError_t launch_leaf_level(ifgf_plan_t* p, int mode, cudaStream_t s) {
+  if (ifgf64(p->desc)) return cudaErrorInvalidValue;
+  const DevLevel& L = p->dl[p->tree.D];
+  if (L.nboxes == 0 || L.max_box_slots == 0) return cudaSuccess;
+  LeafArgs<float> A{L.box_pt_ptr, L.box_slot_ptr, L.slot_cone, L.box_center, cone_geom_t<float>(L.cg),
+                    p->x_sorted, (const float*)p->a_sorted, (float*)L.coefs, (float)p->desc.k_ext,
+                    (float)p->desc.k_int, 16 * (size_t)p->N, L.cstride, L.img, L.istride};
+  const dim3 grid((unsigned)L.nboxes, (unsigned)((L.max_box_slots + kLeafSlots - 1) / kLeafSlots), 1);
+  if (mode == 1)
+    k_leaf_mma<<<grid, 32 * kLeafMmaWarps, 0, s>>>(A);
+  else
+    k_leaf<float><<<grid, kLeafThreads, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,7 @@ cudaError_t launch_far_direct_raw(int N, const double* x, const double* nrm, con
 // the FP32 target step of level d alone, warp per target (mode 0) or per box chunk (mode 1)
 cudaError_t launch_target_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s);
 cudaError_t launch_up_level(ifgf_plan_t* p, int d, int mode, cudaStream_t s);
+cudaError_t launch_leaf_level(ifgf_plan_t* p, int mode, cudaStream_t s);
 // opt the IFGF kernels into the dynamic shared memory they use (once per device)
 cudaError_t setup_ifgf_kernels();
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)

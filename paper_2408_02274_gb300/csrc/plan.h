@@ -117,6 +117,7 @@ struct DevLevel {
   int* tc_item = nullptr;         // [ntc_items][kTcBoxes]
   int ntc_items = 0;
   bool tc = false;                // the upward step into this level runs on the tensor cores
+  int leaf_mode = 1;              // FP32 leaf step (level D): 0 SIMT products, 1 tensor-pipe products
   int up_mode = 0;                // FP32 SIMT upward step into this level: 0 runs per point group,
                                   // 1 a warp per parent slot over the unit tables
   int64_t* tgt_ptr = nullptr;     // [N+1]

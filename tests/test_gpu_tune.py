@@ -34,6 +34,9 @@ def test_tune_keeps_the_faster_shape_and_the_result():
         t0, t1 = times[64 + 2 * d], times[65 + 2 * d]
         assert t0 > 0 and t1 > 0
         assert choices[32 + d] == (1 if t1 < t0 else 0)
+    assert choices[30] in (0, 1) and times[60] > 0 and times[61] > 0   # leaf: SIMT or tensor-pipe products
+    assert choices[30] == (1 if times[61] < times[60] else 0)
+    print("leaf products (SIMT, tensor pipe) ms:", times[60:62], "choice", choices[30])
     print("target shape per level:", choices[3:levels + 1], "ms:", times[6:2 * levels + 2], "near threads:", choices[25],
           "upward shape per level:", choices[35:32 + levels], "ms:", times[70:64 + 2 * levels])
     e = float(torch.linalg.norm(after - before) / torch.linalg.norm(before))
