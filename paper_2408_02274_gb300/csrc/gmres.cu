@@ -65,11 +65,13 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const d
   const int j0 = blockIdx.y * kDotJ;
   double wr[kDotItems], wi[kDotItems];
   int64_t idx[kDotItems];
+  const double2* w2 = reinterpret_cast<const double2*>(w);   // complex values: 16-byte loads
 #pragma unroll
   for (int it = 0; it < kDotItems; ++it) {
     idx[it] = base + it * kDotThreads + threadIdx.x;
-    wr[it] = idx[it] < n ? w[2 * idx[it]] : 0.0;
-    wi[it] = idx[it] < n ? w[2 * idx[it] + 1] : 0.0;
+    const double2 x = idx[it] < n ? w2[idx[it]] : make_double2(0.0, 0.0);
+    wr[it] = x.x;
+    wi[it] = x.y;
   }
   double acc[2 * kDotJ];
 #pragma unroll
@@ -77,13 +79,13 @@ __global__ void __launch_bounds__(kDotThreads) k_dots(int64_t n, int k1, const d
     double ar = 0, ai = 0;
     const int j = j0 + jj;
     if (j < k1) {
-      const double* v = V + 2 * (size_t)j * ldv;
+      const double2* v = reinterpret_cast<const double2*>(V + 2 * (size_t)j * ldv);
 #pragma unroll
       for (int it = 0; it < kDotItems; ++it)
         if (idx[it] < n) {
-          const double vr = v[2 * idx[it]], vi = v[2 * idx[it] + 1];
-          ar += vr * wr[it] + vi * wi[it];
-          ai += vr * wi[it] - vi * wr[it];
+          const double2 x = v[idx[it]];
+          ar += x.x * wr[it] + x.y * wi[it];
+          ai += x.x * wi[it] - x.y * wr[it];
         }
     }
     acc[2 * jj] = ar;
@@ -149,11 +151,13 @@ __global__ void k_combo(int64_t n, int k1, const int* __restrict__ kvec, const d
   c += rb * cstride;
   w += 2 * rb * (size_t)n;
   double ar = 0, ai = 0;
+  const double2* V2 = reinterpret_cast<const double2*>(V) + i;   // complex values: 16-byte loads
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+#pragma unroll 4
   for (int j = 0; j < k1; ++j) {
-    double vr = V[2 * ((size_t)j * ldv + i)], vi = V[2 * ((size_t)j * ldv + i) + 1];
-    double cr = c[2 * j], ci = c[2 * j + 1];
-    ar += vr * cr - vi * ci;
-    ai += vr * ci + vi * cr;
+    const double2 v = V2[(size_t)j * ldv], cc = c2[j];
+    ar += v.x * cc.x - v.y * cc.y;
+    ai += v.x * cc.y + v.y * cc.x;
   }
   if (overwrite) {
     w[2 * i] = ar;
