@@ -464,14 +464,20 @@ __global__ void __launch_bounds__(32 * kLeafMmaWarps, 4) k_leaf_mma(LeafArgs<flo
               al[ks][r + 2] = __float_as_uint(gi - hi);
             }
           }
+          // the three split terms of the four (kernel, n-tile) accumulators, term-major: four
+          // independent products between two that share an accumulator
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-              mma_tf32(acc[h][ks][nt], ah[ks], bh[nt]);
-              mma_tf32(acc[h][ks][nt], ah[ks], bl[nt]);
-              mma_tf32(acc[h][ks][nt], al[ks], bh[nt]);
-            }
+            for (int nt = 0; nt < 2; ++nt) mma_tf32(acc[h][ks][nt], ah[ks], bh[nt]);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_tf32(acc[h][ks][nt], ah[ks], bl[nt]);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) mma_tf32(acc[h][ks][nt], al[ks], bh[nt]);
         }
       }
     }
