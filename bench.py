@@ -278,7 +278,7 @@ def run_gpu(args):
     st = plan.stats()
     up_modes = [int(tune_choices[32 + d]) for d in range(3, st["levels"])]
     up_kernel = ("k_up_warp" if all(m == 1 for m in up_modes) else
-                 "k_up_runs" if all(m == 0 for m in up_modes) else "k_up_runs+k_up_warp")
+                 "k_up_runs" if all(m in (0, 2) for m in up_modes) else "k_up_runs+k_up_warp")
     N = prob.n
     x, _, _ = prob.nodes()
     # the 64 incidences of the batched configuration (32 Fibonacci directions x 2 polarisations);
@@ -428,10 +428,11 @@ def run_gpu(args):
                    "near_threads": int(tune_choices[25]),
                    "leaf_products": "tensor pipe (mma)" if tune_choices[30] == 1 else "SIMT",
                    "leaf_ms": [round(float(tune_ms[60]), 3), round(float(tune_ms[61]), 3)],
-                   "upward_step_per_level": {str(d): ("warp per slot" if tune_choices[32 + d] == 1 else "group runs")
-                                             for d in range(3, st["levels"])},
+                   "upward_step_per_level": {str(d): ("group runs", "warp per slot", "group runs per item")[
+                                                 int(tune_choices[32 + d])] for d in range(3, st["levels"])},
                    "upward_ms_per_level": {str(d): [round(float(tune_ms[64 + 2 * d]), 3),
-                                                    round(float(tune_ms[65 + 2 * d]), 3)]
+                                                    round(float(tune_ms[65 + 2 * d]), 3),
+                                                    round(float(tune_ms[100 + d]), 3)]
                                            for d in range(3, st["levels"])}},
     }
     if rank == 0 and not args.no_cpu_baseline:

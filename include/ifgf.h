@@ -454,8 +454,9 @@ ifgf_status ifgf_far_field(ifgf_plan plan, int32_t nrhs, const void* y, int32_t 
  *   - for an FP32 or mixed IFGF plan, the leaf step (a) with SIMT or tensor-pipe (TF32 mma)
  *     density products (choices[30]: 0 or 1; times_ms[60], [61]);
  *   - per parent level d of an FP32 or mixed IFGF plan without the tensor-core option, the
- *     upward step (b) into d by runs of point groups or by a warp per parent slot
- *     (choices[32 + d]: 0 or 1; times_ms[64 + 2d], [65 + 2d]).
+ *     upward step (b) into d by runs of point groups with a block per parent slot, by a warp per
+ *     parent slot, or by runs with a block per item of up to four slots of one parent cone
+ *     (choices[32 + d]: 0, 1 or 2; times_ms[64 + 2d], [65 + 2d], [100 + d]).
  * reps: timed launches per candidate (after one warm-up), 1..1000.  choices: host int32 [64]
  * or NULL (-1 where not applicable); times_ms: host float [128] or NULL.  Results of later
  * applies are unchanged up to summation order (the target step's grouping differs between its

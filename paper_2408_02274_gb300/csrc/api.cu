@@ -335,16 +335,14 @@ void build(ifgf_plan_t* p) {
     Dl.up_order = A.upload(L.up_order);
     Dl.up_task = A.upload(L.up_task);
     Dl.up_task_ptr = A.upload(L.up_task_ptr);
-    if (unit_tables(d, L)) {   // the FP32 upward step by units (warp per slot, or tensor cores)
+    if (unit_tables(d, L)) {   // the FP32 upward step by units or items (SIMT candidates, tensor cores)
       Dl.tc_order = A.upload(L.tc_order);
       Dl.tc_unit = A.upload(L.tc_unit);
       Dl.tc_unit_ptr = A.upload(L.tc_unit_ptr);
-    }
-    if (upward_tc(d, L)) {
-      Dl.tc = true;
       Dl.tc_item = A.upload(L.tc_item);
       Dl.ntc_items = (int)(L.tc_item.size() / kTcBoxes);
     }
+    if (upward_tc(d, L)) Dl.tc = true;
     {
       std::vector<double2> th(L.na), ph(2 * (size_t)L.na);
       for (int g = 0; g < L.na; ++g) th[g] = make_double2(std::cos(g * kPi / L.na), std::sin(g * kPi / L.na));
@@ -679,8 +677,8 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
         tb.dev<int32_t>(L.tc_order.size());
         tb.dev<int32_t>(L.tc_unit.size());
         tb.dev<int32_t>(L.tc_unit_ptr.size());
+        tb.dev<int32_t>(L.tc_item.size());
       }
-      if (upward_tc(d, L)) tb.dev<int32_t>(L.tc_item.size());
       tb.dev<double2>((size_t)L.na);
       tb.dev<double2>(2 * (size_t)L.na);
       tb.dev<int64_t>(L.tgt_ptr.size());
@@ -903,15 +901,18 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
       for (int d = 3; d < p->tree.D && e == cudaSuccess; ++d) {
         DevLevel& Pp = p->dl[d];
         if (Pp.tc || !Pp.tc_unit_ptr || Pp.nslots == 0) continue;
-        float t[2] = {0.f, 0.f};
-        for (int m = 0; m < 2 && e == cudaSuccess; ++m)
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int m = 0; m < 3 && e == cudaSuccess; ++m)
           e = time_ms(s, reps, [&]() { return launch_up_level(p, d, m, s); }, &t[m]);
         if (e != cudaSuccess) break;
-        Pp.up_mode = t[1] < t[0] ? 1 : 0;
+        Pp.up_mode = 0;
+        for (int m = 1; m < 3; ++m)
+          if (t[m] < t[Pp.up_mode]) Pp.up_mode = m;
         if (choices && d < 25) choices[32 + d] = Pp.up_mode;
         if (times_ms && d < 25) {
           times_ms[64 + 2 * d] = t[0] / reps;
           times_ms[65 + 2 * d] = t[1] / reps;
+          times_ms[100 + d] = t[2] / reps;
         }
       }
     }

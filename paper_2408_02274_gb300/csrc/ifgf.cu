@@ -673,40 +673,49 @@ constexpr int kUpRunWarps = kUpGroups;   // warp w adds only into the parent poi
 // dynamic shared memory of k_up_runs (above the 48 KB static limit)
 constexpr size_t kUpRunSmem = sizeof(UpCheb) * 8 * kQ      // Chebyshev values per (octant, point)
                               + sizeof(float4) * 8 * kQ    // re-centring factors (re, im) x 2 kernels
-                              + sizeof(int) * 8 * kQ       // child slot per (octant, point)
                               + sizeof(float) * kQ * kVS   // parent values
                               + sizeof(float) * kQ * 3;    // parent points
 
-__global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A, RunTabs RT, int nrhs) {
+__global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A, RunTabs RT, int nrhs,
+                                                                   const int* __restrict__ items) {
   using T = float;
   __shared__ SmallMaps<T> M;
   extern __shared__ float4 up_smem[];
   UpCheb (*cheb)[kQ] = reinterpret_cast<UpCheb (*)[kQ]>(up_smem);
   float4 (*fac)[kQ] = reinterpret_cast<float4 (*)[kQ]>(cheb + 8);
-  int (*cslot)[kQ] = reinterpret_cast<int (*)[kQ]>(fac + 8);
-  T* vals = reinterpret_cast<T*>(cslot + 8);
+  T* vals = reinterpret_cast<T*>(fac + 8);
   T (*Xp)[3] = reinterpret_cast<T (*)[3]>(vals + kQ * kVS);
-  const int pslot = blockIdx.x;
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
+  // the block's parent slots: one, or (items) up to kTcBoxes slots of one parent cone in other
+  // boxes, whose geometry (child cones, local coordinates, re-centring factors) is the same
+  int slots[kTcBoxes], nsl = 1, omask = 0;
+  slots[0] = items ? __ldg(items + (size_t)blockIdx.x * kTcBoxes) : (int)blockIdx.x;
+#pragma unroll
+  for (int b = 1; b < kTcBoxes; ++b) {
+    slots[b] = items ? __ldg(items + (size_t)blockIdx.x * kTcBoxes + b) : -1;
+    nsl += slots[b] >= 0;
+  }
+#pragma unroll
+  for (int b = 0; b < kTcBoxes; ++b)
+    if (slots[b] >= 0)
+      for (int o = 0; o < 8; ++o) omask |= (__ldg(A.child + 8 * __ldg(A.slot_box + slots[b]) + o) >= 0) << o;
   init_maps(M);
-  const int P = A.slot_box[pslot], ci = A.slot_upidx[pslot];
-  const cone_key pcone = A.slot_cone[pslot];
+  const int ci = A.slot_upidx[slots[0]];
+  const cone_key pcone = A.slot_cone[slots[0]];
   __syncthreads();
   if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
   __syncthreads();
   const T off = (T)(0.5 * A.Hc);
   const T kk[2] = {A.ke, A.ki};
-  // prologue: per (octant, parent point) the child slot, the Chebyshev values of the point's
-  // local coordinates in its child cone, and the re-centring factor of both kernels
+  // prologue: per (octant, parent point) the Chebyshev values of the point's local coordinates in
+  // its child cone and the re-centring factor of both kernels (octants with a child in some box)
   for (int e = t; e < 8 * kQ; e += blockDim.x) {
     const int o = e / kQ, q = e % kQ;
-    const int cb = A.child[8 * P + o];
-    if (cb < 0) continue;
+    if (!((omask >> o) & 1)) continue;
     const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
     const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
     const int ccx = A.up_cc[((size_t)ci * 8 + o) * kQ + q];
     const cone_key cc = A.ckeys_c[ccx];
-    cslot[o][q] = A.cmap_c[(size_t)cb * A.ncomp_c + ccx];
     T ts, tt, tp, rc, sth, cth, sph, cph;
     local_coords(A.cgc, cc, x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
     T v5[5], v3[3];
@@ -733,59 +742,66 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   const T sgn = (lane & 1) ? T(1) : T(-1);
   const int w0 = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp);
   const int w1 = __ldg(RT.task_ptr + (size_t)ci * kUpGroups + warp + 1);
-  // the right-hand sides of a batched call one after the other: the prologue's geometry serves all
-  for (int rb = 0; rb < nrhs; ++rb) {
-    const T* coefs_c = A.coefs_c + rb * A.cstride_c;
-    for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
-    __syncthreads();
-    // the warp's own runs (its group of parent points, all octants); runs of absent children
-    // are skipped.  Only this warp adds into these points' values: plain shared-memory adds.
-    for (int w = w0; w < w1; ++w) {
-      const int tk = __ldg(RT.task + w);
-      const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
-      if (A.child[8 * P + o] < 0) continue;
-      const size_t g = (size_t)ci * 8 + o;
-      const int myq = lane < len ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
-      // one child slot per run: the host marked every such cone relevant
-      const T* Cg = coefs_c + (size_t)cslot[o][__shfl_sync(0xffffffffu, myq, 0)] * kQ * 32 + lane;
-      T c[kQ];
+  // the slots, and the right-hand sides of a batched call, one after the other: the prologue's
+  // geometry serves all of them
+  for (int b = 0; b < nsl; ++b) {
+    const int pslot = slots[b], P = __ldg(A.slot_box + pslot);
+    for (int rb = 0; rb < nrhs; ++rb) {
+      const T* coefs_c = A.coefs_c + rb * A.cstride_c;
+      for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
+      __syncthreads();
+      // the warp's own runs (its group of parent points, all octants); runs of absent children
+      // are skipped.  Only this warp adds into these points' values: plain shared-memory adds.
+      for (int w = w0; w < w1; ++w) {
+        const int tk = __ldg(RT.task + w);
+        const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
+        if (A.child[8 * P + o] < 0) continue;
+        const size_t g = (size_t)ci * 8 + o;
+        const int myq = lane < len ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
+        // one child slot per run (the host marked every such cone relevant)
+        const int q0 = __shfl_sync(0xffffffffu, myq, 0);
+        const int cs0 =
+            __ldg(A.cmap_c + (size_t)__ldg(A.child + 8 * P + o) * A.ncomp_c + __ldg(A.up_cc + g * kQ + q0));
+        const T* Cg = coefs_c + (size_t)cs0 * kQ * 32 + lane;
+        T c[kQ];
 #pragma unroll
-      for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
-      int a = 0;
-      for (; a + 1 < len; a += 2) {   // two points at a time (independent sums, distinct points)
-        int q[2];
-        float4 P4[2], T4[2], S4[2];
-        float2 F2[2];
-        float v[2];
+        for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
+        int a = 0;
+        for (; a + 1 < len; a += 2) {   // two points at a time (independent sums, distinct points)
+          int q[2];
+          float4 P4[2], T4[2], S4[2];
+          float2 F2[2];
+          float v[2];
 #pragma unroll
-        for (int n = 0; n < 2; ++n) {
-          q[n] = __shfl_sync(0xffffffffu, myq, a + n);
-          const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q[n]]);
-          P4[n] = cp[0]; T4[n] = cp[1]; S4[n] = cp[2];
-          F2[n] = reinterpret_cast<const float2*>(&fac[o][q[n]])[ks];   // this lane's kernel: (re, im)
+          for (int n = 0; n < 2; ++n) {
+            q[n] = __shfl_sync(0xffffffffu, myq, a + n);
+            const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q[n]]);
+            P4[n] = cp[0]; T4[n] = cp[1]; S4[n] = cp[2];
+            F2[n] = reinterpret_cast<const float2*>(&fac[o][q[n]])[ks];   // this lane's kernel: (re, im)
+          }
+          up_contract<2>(c, P4, T4, S4, v);
+#pragma unroll
+          for (int n = 0; n < 2; ++n) {
+            const T wv = __shfl_xor_sync(0xffffffffu, v[n], 1);
+            vals[q[n] * kVS + lane] += fmaf(v[n], F2[n].x, sgn * F2[n].y * wv);
+          }
         }
-        up_contract<2>(c, P4, T4, S4, v);
-#pragma unroll
-        for (int n = 0; n < 2; ++n) {
-          const T wv = __shfl_xor_sync(0xffffffffu, v[n], 1);
-          vals[q[n] * kVS + lane] += fmaf(v[n], F2[n].x, sgn * F2[n].y * wv);
+        if (a < len) {
+          const int q = __shfl_sync(0xffffffffu, myq, a);
+          const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
+          const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
+          const float2 F2 = reinterpret_cast<const float2*>(&fac[o][q])[ks];
+          float v[1];
+          up_contract<1>(c, P4, T4, S4, v);
+          const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
+          vals[q * kVS + lane] += fmaf(v[0], F2.x, sgn * F2.y * wv);
         }
       }
-      if (a < len) {
-        const int q = __shfl_sync(0xffffffffu, myq, a);
-        const float4* cp = reinterpret_cast<const float4*>(&cheb[o][q]);
-        const float4 P4[1] = {cp[0]}, T4[1] = {cp[1]}, S4[1] = {cp[2]};
-        const float2 F2 = reinterpret_cast<const float2*>(&fac[o][q])[ks];
-        float v[1];
-        up_contract<1>(c, P4, T4, S4, v);
-        const T wv = __shfl_xor_sync(0xffffffffu, v[0], 1);
-        vals[q * kVS + lane] += fmaf(v[0], F2.x, sgn * F2.y * wv);
-      }
+      __syncthreads();
+      vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + rb * A.cstride_p + (size_t)pslot * kQ * 32, 1,
+                                  A.img_p ? A.img_p + rb * A.istride_p + (size_t)pslot * kImgFloats : nullptr);
+      __syncthreads();   // vals is cleared for the next right-hand side
     }
-    __syncthreads();
-    vals_to_coefs_block<T, kVS>(M, vals, A.coefs_p + rb * A.cstride_p + (size_t)pslot * kQ * 32, 1,
-                                A.img_p ? A.img_p + rb * A.istride_p + (size_t)pslot * kImgFloats : nullptr);
-    __syncthreads();   // vals is cleared for the next right-hand side
   }
 }
 
@@ -1673,15 +1689,19 @@ __global__ void __launch_bounds__(32 * kTgtBoxWarps) k_target_box(TgtArgs<float,
   }
 }
 
-// The FP32 SIMT upward step into the level below Pp: mode 1 a warp per parent slot (unit
-// tables), mode 0 runs per point group.
+// The FP32 SIMT upward step into the level below Pp: mode 0 runs per point group (a block per
+// parent slot), 1 a warp per parent slot (unit tables), 2 runs per point group with a block per
+// item of up to kTcBoxes slots of one parent cone (one prologue for the item).
 void launch_up_simt(const UpArgs<float>& U, const DevLevel& Pp, int mode, int nrhs, cudaStream_t s) {
   if (mode == 1 && Pp.tc_unit_ptr)
     k_up_warp<<<dim3((unsigned)((Pp.nslots + kUpWarpW - 1) / kUpWarpW), nrhs), 32 * kUpWarpW, kUpWarpSmem, s>>>(
         U, UnitTabs{Pp.tc_order, Pp.tc_unit, Pp.tc_unit_ptr}, Pp.nslots);
+  else if (mode == 2 && Pp.tc_item)
+    k_up_runs<<<dim3((unsigned)Pp.ntc_items, 1), 32 * kUpRunWarps, kUpRunSmem, s>>>(
+        U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr}, nrhs, Pp.tc_item);
   else
     k_up_runs<<<dim3(Pp.nslots, 1), 32 * kUpRunWarps, kUpRunSmem, s>>>(
-        U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr}, nrhs);
+        U, RunTabs{Pp.up_order, Pp.up_task, Pp.up_task_ptr}, nrhs, nullptr);
 }
 
 template <typename T, typename TO = T>

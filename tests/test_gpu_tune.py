@@ -29,16 +29,17 @@ def test_tune_keeps_the_faster_shape_and_the_result():
         assert t0 > 0 and t1 > 0
         assert choices[d] == (1 if t1 < t0 else 0)
     assert choices[25] in (128, 256) and times[50] > 0 and times[51] > 0
-    for d in range(3, levels):   # upward step into parent level d: point-group runs or warp per slot
-        assert choices[32 + d] in (0, 1)
-        t0, t1 = times[64 + 2 * d], times[65 + 2 * d]
-        assert t0 > 0 and t1 > 0
-        assert choices[32 + d] == (1 if t1 < t0 else 0)
+    for d in range(3, levels):   # upward step into parent level d: runs per slot, warp per slot, runs per item
+        assert choices[32 + d] in (0, 1, 2)
+        t = [times[64 + 2 * d], times[65 + 2 * d], times[100 + d]]
+        assert min(t) > 0
+        assert choices[32 + d] == int(np.argmin(t))
     assert choices[30] in (0, 1) and times[60] > 0 and times[61] > 0   # leaf: SIMT or tensor-pipe products
     assert choices[30] == (1 if times[61] < times[60] else 0)
     print("leaf products (SIMT, tensor pipe) ms:", times[60:62], "choice", choices[30])
     print("target shape per level:", choices[3:levels + 1], "ms:", times[6:2 * levels + 2], "near threads:", choices[25],
-          "upward shape per level:", choices[35:32 + levels], "ms:", times[70:64 + 2 * levels])
+          "upward shape per level:", choices[35:32 + levels], "ms:", times[70:64 + 2 * levels],
+          times[103:100 + levels])
     e = float(torch.linalg.norm(after - before) / torch.linalg.norm(before))
     assert e < 1e-5, e
     plan.close()
