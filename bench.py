@@ -524,7 +524,7 @@ def run_apply(args):
         ch, _ = plan.tune(reps=3)
         lv = plan.stats()["levels"]
         tuned = {"target_box_chunks_per_level": [int(v) for v in ch[3:lv + 1]],
-                 "upward_warp_per_slot_per_level": [int(v) for v in ch[35:32 + lv]],
+                 "upward_mode_per_level": [int(v) for v in ch[35:32 + lv]],   # 0 runs, 1 warp per slot, 2 runs by item
                  "leaf_tensor_pipe": int(ch[30]),
                  "near_threads": int(ch[25])}
     y = torch.from_numpy(random_densities(prob.n, 1)).cuda()
