@@ -108,8 +108,8 @@ class ClockSampler:
 
 
 # sources whose change invalidates a recorded DRAM traffic figure of the IFGF kernels
-KERNEL_SOURCES = ("paper_2408_02274_gb300/csrc/ifgf.cu", "paper_2408_02274_gb300/csrc/common.cuh",
-                  "paper_2408_02274_gb300/csrc/host_setup.cpp")
+KERNEL_SOURCES = ("paper_2408_02274_gb300/csrc/ifgf.cu", "paper_2408_02274_gb300/csrc/ifgf_dev.cuh",
+                  "paper_2408_02274_gb300/csrc/common.cuh", "paper_2408_02274_gb300/csrc/host_setup.cpp")
 
 
 KERNEL_NAMES = {"target": "k_target", "up": "k_up_runs", "leaf": "k_leaf", "near": "k_near"}
@@ -549,6 +549,59 @@ def run_apply(args):
             "stage_ms_per_apply": {k: v[0] / max(args.steps, 1) for k, v in kt.items()},
             "setup_s": setup, "levels": st["levels"], "cones": st["cones"], "near_nnz": st["near_nnz"],
             "device_bytes": st["device_bytes"]}
+
+
+def run_passes(args):
+    """IFGF_Vec against the per-kernel and IFGF_Seq strategies (Sec. III, "IFGF for Multiple
+    Densities: Speed-vs-Memory Trade-off"; Remark "On selection of IFGF approach"; Table I's
+    T_IFGF and T_Seq): one FP32 plan per strategy (fields_per_pass 16, 8, 1), forward maps timed
+    with the library's stage events.  The IFGF time is the leaf, upward and target steps; the
+    coefficient bytes are the two live levels' interpolation data; the accuracy line is each
+    strategy's forward map against the all-fields one."""
+    import torch
+    import paper_2408_02274_gb300 as lib
+    from paper_2408_02274_gb300 import build as libbuild
+    from inputs import random_densities
+    libbuild.build()
+    prob = problem(args.workload)
+    opts = dict(delta=delta_of(prob), n_beta=48, cov_d=4.0, precision=PRECISIONS[args.precision],
+                far_mode=lib.IFGF_FAR_IFGF, ns0=NS0, na0=NA0, max_krylov=10)
+    y = torch.from_numpy(random_densities(prob.n, 1)).cuda()
+    rows, ref = [], None
+    for fpp in (16, 8, 1):
+        plan = lib.Plan.from_problem(prob, fields_per_pass=fpp, **opts)
+        if fpp == 16:
+            plan.tune(reps=3)   # the all-fields kernels' launch shapes, as in the solve step
+        out = torch.empty_like(y)
+        for _ in range(args.warmup):
+            plan.apply(y, out)
+        torch.cuda.synchronize()
+        lib.ifgf_set_timing(plan.handle, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            plan.apply(y, out)
+        e1.record()
+        torch.cuda.synchronize()
+        kt, launches = lib.ifgf_get_timing(plan.handle)
+        st = plan.stats()
+        plan.close()
+        k = max(args.steps, 1)
+        stage = {n: kt[n][0] / k for n in ("leaf", "up", "target")}
+        res = out.cpu().numpy()
+        if ref is None:
+            ref = res
+        est = lib.Plan.estimate(prob, fields_per_pass=fpp, **opts)
+        rows.append({"fields_per_pass": fpp, "traversals": 16 // fpp, "ms_per_forward_map": e0.elapsed_time(e1) / k,
+                     "ifgf_ms": sum(stage.values()), "stage_ms": stage, "launches_per_map": launches / k,
+                     "coef_bytes": est["bytes_coefs"], "device_bytes": st["device_bytes"],
+                     "rel_to_all_fields": float(np.linalg.norm(res - ref) / np.linalg.norm(ref))})
+    t_vec, m_vec = rows[0]["ifgf_ms"], rows[0]["coef_bytes"]
+    for r in rows:
+        r["ifgf_time_vs_vec"] = r["ifgf_ms"] / t_vec
+        r["coef_bytes_vs_vec"] = r["coef_bytes"] / m_vec
+    return {"mode": "passes", "workload": WORKLOADS[args.workload], "precision": args.precision,
+            "applies": args.steps, "strategies": rows}
 
 
 def run_reference(args):
@@ -1056,7 +1109,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "apply", "batch", "uneven", "precond", "compare", "waveguide", "incidences"])
+                    choices=["solve", "apply", "batch", "uneven", "precond", "compare", "waveguide", "incidences",
+                             "passes"])
     ap.add_argument("--ntrain", type=int, default=8)
     ap.add_argument("--skip-learned", action="store_true", help="precond mode: block Jacobi only, no network")
     ap.add_argument("--star-radius", type=float, default=0.75, help="precond mode: star bodies' mean radius (lambda)")
@@ -1101,6 +1155,8 @@ def main():
         res = run_compare(args)
     elif args.mode == "waveguide":
         res = run_waveguide(args)
+    elif args.mode == "passes":
+        res = run_passes(args)
     else:
         res = run_gpu(args)
     if res is not None:

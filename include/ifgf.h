@@ -106,6 +106,17 @@ typedef struct {
                               to tol |b| and y += d.  The solves then report the formed residual,
                               not the Arnoldi estimate, and iters sums the sweeps.  0: GMRES alone.
                               Two more [batch][4N] complex vectors are allocated */
+  int32_t fields_per_pass; /* IFGF fields carried per octree traversal (Sec. III, "IFGF for Multiple
+                              Densities: Speed-vs-Memory Trade-off", and the Remark "On selection of
+                              IFGF approach"); of the 16 sums of Eq. ifgf_sum_em (8 densities x 2
+                              kernels): 0 or 16: all in one traversal (IFGF_Vec, the default);
+                              8: one kernel per traversal (two traversals, half the interpolation
+                              coefficients' memory); 1: one (density, kernel) sum per traversal
+                              (IFGF_Seq: sixteen traversals, 1/16 of that memory).  1 and 8 need
+                              far_mode IFGF_FAR_IFGF, FP32 IFGF kernels (precision IFGF_FP32 or
+                              IFGF_MIXED) and upward_tc 0, else IFGF_EUNSUPPORTED; other values
+                              IFGF_EINVAL.  Same sums to FP32 rounding; the autotuner leaves the
+                              far-field kernels of such a plan untuned */
 } ifgf_plan_desc;
 
 /*

@@ -47,6 +47,7 @@ class ifgf_plan_desc(ctypes.Structure):
         ("gs_iters", ctypes.c_int32), ("precision", ctypes.c_int32), ("far_mode", ctypes.c_int32),
         ("max_krylov", ctypes.c_int32), ("batch", ctypes.c_int32), ("max_leaf_pts", ctypes.c_int32),
         ("gmres_scaling", ctypes.c_int32), ("upward_tc", ctypes.c_int32), ("refine", ctypes.c_int32),
+        ("fields_per_pass", ctypes.c_int32),
     ]
 
 
@@ -209,13 +210,13 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
                      leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                      gs_iters: int = 20, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                      max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0,
-                     gmres_scaling: int = 0, upward_tc: int = 0, refine: int = 0):
+                     gmres_scaling: int = 0, upward_tc: int = 0, refine: int = 0, fields_per_pass: int = 0):
     """ifgf_plan_create: host arrays in, opaque plan handle (c_void_p) out."""
     lib = load()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
               leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-              max_leaf_pts, gmres_scaling, upward_tc, refine)
+              max_leaf_pts, gmres_scaling, upward_tc, refine, fields_per_pass)
     h = ctypes.c_void_p()
     _check(lib.ifgf_plan_create(ctypes.byref(d), ctypes.byref(h)), "ifgf_plan_create")
     return h
@@ -223,12 +224,12 @@ def ifgf_plan_create(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: 
 
 def _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
           leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch, max_leaf_pts,
-          gmres_scaling, upward_tc=0, refine=0):
+          gmres_scaling, upward_tc=0, refine=0, fields_per_pass=0):
     ng = int(arrs[3].shape[1])
     return ifgf_plan_desc(num_patches, nc, _dptr(arrs[0]), _dptr(arrs[1]), _dptr(arrs[2]), ng, _dptr(arrs[3]),
                           k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, ps, pa, ns0, na0, leaf_size,
                           min_levels, delta, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-                          max_leaf_pts, gmres_scaling, upward_tc, refine)
+                          max_leaf_pts, gmres_scaling, upward_tc, refine, fields_per_pass)
 
 
 def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext: float, k_int: float,
@@ -237,13 +238,13 @@ def ifgf_plan_estimate(nodes, dxdu, dxdv, fine, num_patches: int, nc: int, k_ext
                        leaf_size: float = 0.0, min_levels: int = 0, n_beta: int = 48, cov_d: float = 4.0,
                        gs_iters: int = 20, precision: int = IFGF_FP64, far_mode: int = IFGF_FAR_IFGF,
                        max_krylov: int = 0, batch: int = 0, max_leaf_pts: int = 0, gmres_scaling: int = 0,
-                       upward_tc: int = 0, refine: int = 0) -> dict:
+                       upward_tc: int = 0, refine: int = 0, fields_per_pass: int = 0) -> dict:
     """ifgf_plan_estimate: the device memory ifgf_plan_create would allocate for the same
     arguments (host work only; near-matrix figures are upper bounds)."""
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)) for a in (nodes, dxdu, dxdv, fine)]
     d = _desc(arrs, num_patches, nc, k_ext, k_int, eps_ext, eps_int, mu_ext, mu_int, delta, ps, pa, ns0, na0,
               leaf_size, min_levels, n_beta, cov_d, gs_iters, precision, far_mode, max_krylov, batch,
-              max_leaf_pts, gmres_scaling, upward_tc, refine)
+              max_leaf_pts, gmres_scaling, upward_tc, refine, fields_per_pass)
     e = ifgf_plan_estimate_t()
     _check(load().ifgf_plan_estimate(ctypes.byref(d), ctypes.byref(e)), "ifgf_plan_estimate")
     out = {name: getattr(e, name) for name, _ in ifgf_plan_estimate_t._fields_ if name != "cones"}

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libifgf.so")
-SOURCES = ["api.cu", "host_setup.cpp", "tree_api.cpp", "noalloc.cu", "setup_kernels.cu", "combine.cu", "near_direct.cu", "ifgf.cu",
+SOURCES = ["api.cu", "host_setup.cpp", "tree_api.cpp", "noalloc.cu", "setup_kernels.cu", "combine.cu", "near_direct.cu", "ifgf.cu", "ifgf_pass.cu",
            "gmres.cu", "precond.cu", "farfield.cu", "blockjacobi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

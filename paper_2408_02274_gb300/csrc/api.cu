@@ -133,6 +133,13 @@ ifgf_status validate(const ifgf_plan_desc* d) {
   if (d->gmres_scaling < 0 || d->gmres_scaling > 1) return IFGF_EINVAL;
   if (d->upward_tc < 0 || d->upward_tc > 1) return IFGF_EINVAL;
   if (d->refine < 0 || d->refine > 20) return IFGF_EINVAL;
+  if (d->fields_per_pass != 0 && d->fields_per_pass != 1 && d->fields_per_pass != 8 && d->fields_per_pass != 16)
+    return IFGF_EINVAL;
+  if (narrow_passes(*d) && (d->far_mode != IFGF_FAR_IFGF || ifgf64(*d) || d->upward_tc != 0)) {
+    set_status_detail(IFGF_EUNSUPPORTED,
+                      "fields_per_pass 1 or 8 needs far_mode IFGF_FAR_IFGF, FP32 IFGF kernels and upward_tc 0");
+    return IFGF_EUNSUPPORTED;
+  }
   if (d->ps != 3 || d->pa != 5) return IFGF_EUNSUPPORTED;
   if ((int64_t)d->num_patches * d->nc * d->nc > (int64_t)1 << 30) return IFGF_EUNSUPPORTED;
   return IFGF_OK;
@@ -358,7 +365,7 @@ void build(ifgf_plan_t* p) {
     Dl.tgt_mode = Dl.ntgt_chunks >= 2 * 12 * std::max(p->num_sms, 1) ? 1 : 0;
     Dl.tgt_slot = A.upload(L.tgt_slot.data(), L.tgt_slot.size());
     Dl.ninter = (int64_t)L.tgt_slot.size();
-    Dl.cstride = (size_t)Dl.nslots * kQ * 32;
+    Dl.cstride = (size_t)Dl.nslots * kQ * coef_columns(d);
     p->stats.boxes[dd] = Dl.nboxes;
     p->stats.cones[dd] = Dl.nslots;
     p->stats.ns[dd] = L.ns;
@@ -685,7 +692,7 @@ ifgf_status ifgf_plan_estimate(const ifgf_plan_desc* desc, ifgf_plan_estimate_t*
       tb.dev<int32_t>(L.tgt_chunk.size());
       tb.dev<int32_t>(L.tgt_slot.size());
       out->cones[dd] = (int64_t)nslots;
-      need[dd & 1] = std::max(need[dd & 1], nslots * kQ * 32 * B);
+      need[dd & 1] = std::max(need[dd & 1], nslots * kQ * (size_t)coef_columns(d) * B);
     }
     tb.dev<int>(1);   // the plan's device status word
     ByteCount cf;
@@ -867,8 +874,11 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
       for (int k = 0; k < 64; ++k) choices[k] = -1;
     if (times_ms)
       for (int k = 0; k < 128; ++k) times_ms[k] = 0.f;
+    // the far-field kernels below are the all-fields ones; a plan of fewer fields per pass has
+    // coefficient buffers too narrow for them and keeps its single pass shapes
+    const bool vec = p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc) && !narrow_passes(p->desc);
     // (c): per level, a warp per target or per box chunk
-    if (p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
+    if (vec) {
       for (int d = 3; d <= p->tree.D && e == cudaSuccess; ++d) {
         float t[2] = {0.f, 0.f};
         for (int m = 0; m < 2 && e == cudaSuccess; ++m)
@@ -883,7 +893,7 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
       }
     }
     // (a): the FP32 leaf step with SIMT or tensor-pipe density products
-    if (e == cudaSuccess && p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
+    if (e == cudaSuccess && vec) {
       float t[2] = {0.f, 0.f};
       for (int m = 0; m < 2 && e == cudaSuccess; ++m)
         e = time_ms(s, reps, [&]() { return launch_leaf_level(p, m, s); }, &t[m]);
@@ -897,7 +907,7 @@ ifgf_status ifgf_plan_tune(ifgf_plan p, int32_t reps, int32_t* choices, float* t
       }
     }
     // (b): per parent level, the FP32 SIMT upward step by point-group runs or a warp per slot
-    if (e == cudaSuccess && p->desc.far_mode == IFGF_FAR_IFGF && !ifgf64(p->desc)) {
+    if (e == cudaSuccess && vec) {
       for (int d = 3; d < p->tree.D && e == cudaSuccess; ++d) {
         DevLevel& Pp = p->dl[d];
         if (Pp.tc || !Pp.tc_unit_ptr || Pp.nslots == 0) continue;

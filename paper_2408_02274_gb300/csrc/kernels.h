@@ -56,6 +56,8 @@ cudaError_t launch_leaf_level(ifgf_plan_t* p, int mode, cudaStream_t s);
 cudaError_t setup_ifgf_kernels();
 // far field by IFGF: (a), then per level (c) and (b) (accumulates into f28)
 cudaError_t launch_far_ifgf(ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
+// the same with fields_per_pass 1 or 8: one traversal per group of fields (ifgf_pass.cu)
+cudaError_t launch_far_ifgf_pass(ifgf_plan_t* p, cudaStream_t s, int nrhs = 1);
 // far-field pattern E_inf [nrhs][ndirs][3] complex128 (out) of the scattered field from the densities
 // of the last density preparation (phi64); dirs: device [ndirs][3] unit vectors
 cudaError_t launch_far_field(const ifgf_plan_t* p, int nrhs, int ndirs, const double* dirs, double* out,

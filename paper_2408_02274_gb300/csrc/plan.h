@@ -128,9 +128,10 @@ struct DevLevel {
   int2* tgt_chunk = nullptr;      // [ntgt_chunks] (first sorted target, count <= 32), targets of one box
   int ntgt_chunks = 0;
   int tgt_mode = 0;               // FP32 target step at this level: 0 warp per target, 1 warp per box chunk
-  void* coefs = nullptr;          // [batch][nslots][75][32] real (precision of the plan); one buffer
+  void* coefs = nullptr;          // [batch][nslots][75][C] real (precision of the plan), C = 32, or
+                                  // 2 x fields_per_pass for a plan of fewer fields per pass; one buffer
                                   // serves all levels of equal parity (two live levels at a time)
-  size_t cstride = 0;             // nslots * 75 * 32: coefficients per right-hand side
+  size_t cstride = 0;             // nslots * 75 * C: coefficients per right-hand side
   float* img = nullptr;           // [batch][nslots][2][32 x 80] tensor-core operand images (hi, lo) of the
                                   // coefficients, when the upward step into level d-1 runs on the tensor
                                   // cores; one buffer per parity of d, like coefs
@@ -225,6 +226,10 @@ namespace ifgf {
 // and mixed plans.  The IFGF kernels (leaf, upward, target) run in FP64 only in the FP64 plan.
 inline bool store64(const ifgf_plan_desc& d) { return d.precision != IFGF_FP32; }
 inline bool ifgf64(const ifgf_plan_desc& d) { return d.precision == IFGF_FP64; }
+// Fewer than all 16 IFGF fields per octree traversal (fields_per_pass 1 or 8), and the real
+// columns of one cone segment's coefficient rows: 2 per complex field carried.
+inline bool narrow_passes(const ifgf_plan_desc& d) { return d.fields_per_pass == 1 || d.fields_per_pass == 8; }
+inline int coef_columns(const ifgf_plan_desc& d) { return narrow_passes(d) ? 2 * d.fields_per_pass : 32; }
 }  // namespace ifgf
 
 struct ifgf_plan_t {

@@ -234,6 +234,33 @@ def test_plan_estimate_host_only():
     assert err.value.status == lib.IFGF_EINVAL
 
 
+def test_fields_per_pass_memory_and_options():
+    """The speed-vs-memory trade-off of Sec. III ("IFGF for Multiple Densities") as the estimate
+    sees it: one kernel per traversal (8 fields) halves the interpolation coefficients' bytes,
+    one (density, kernel) sum per traversal (IFGF_Seq) takes 1/16 of them; nothing else
+    changes.  The option needs FP32 IFGF kernels, the IFGF far field and the SIMT upward step."""
+    prob = CONFIG_SPHERE_SMALL(6, ng=12)
+    base = dict(delta=0.3, ns0=2, na0=3, precision=lib.IFGF_FP32, max_krylov=20)
+    vec = lib.Plan.estimate(prob, **base)
+    assert lib.Plan.estimate(prob, fields_per_pass=16, **base) == vec
+    for f, div in ((8, 2), (1, 16)):
+        e = lib.Plan.estimate(prob, fields_per_pass=f, **base)
+        assert e["bytes_coefs"] * div == vec["bytes_coefs"]
+        for k in ("bytes_geometry", "bytes_near_max", "bytes_tables", "bytes_apply", "bytes_gmres"):
+            assert e[k] == vec[k]
+        assert e["bytes_plan_max"] == vec["bytes_plan_max"] - vec["bytes_coefs"] + e["bytes_coefs"]
+    mixed = lib.Plan.estimate(prob, fields_per_pass=1, **dict(base, precision=lib.IFGF_MIXED))
+    assert mixed["bytes_coefs"] * 16 == vec["bytes_coefs"]
+    for bad in (2, 4, -1, 17):
+        with pytest.raises(lib.IfgfError) as err:
+            lib.Plan.estimate(prob, fields_per_pass=bad, **base)
+        assert err.value.status == lib.IFGF_EINVAL
+    for opts in (dict(precision=lib.IFGF_FP64), dict(far_mode=lib.IFGF_FAR_DIRECT), dict(upward_tc=1)):
+        with pytest.raises(lib.IfgfError) as err:
+            lib.Plan.estimate(prob, fields_per_pass=8, **dict(base, **opts))
+        assert err.value.status == lib.IFGF_EUNSUPPORTED
+
+
 def test_upward_run_tables_partition_every_parent_point():
     """The upward tables of each parent level: per (compact cone, octant) the ranking is a
     permutation of the 75 points; the runs of a (compact cone, warp group) cover each
