@@ -423,6 +423,7 @@ constexpr int kUpRunWarps = kUpGroups;   // warp w adds only into the parent poi
 // dynamic shared memory of k_up_runs (above the 48 KB static limit)
 constexpr size_t kUpRunSmem = sizeof(UpCheb) * 8 * kQ      // Chebyshev values per (octant, point)
                               + sizeof(float4) * 8 * kQ    // re-centring factors (re, im) x 2 kernels
+                              + sizeof(int) * 8 * kQ       // child slot per (octant, point) of the current slot
                               + sizeof(float) * kQ * kVS   // parent values
                               + sizeof(float) * kQ * 3;    // parent points
 
@@ -433,7 +434,8 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   extern __shared__ float4 up_smem[];
   UpCheb (*cheb)[kQ] = reinterpret_cast<UpCheb (*)[kQ]>(up_smem);
   float4 (*fac)[kQ] = reinterpret_cast<float4 (*)[kQ]>(cheb + 8);
-  T* vals = reinterpret_cast<T*>(fac + 8);
+  int (*cslot)[kQ] = reinterpret_cast<int (*)[kQ]>(fac + 8);
+  T* vals = reinterpret_cast<T*>(cslot + 8);
   T (*Xp)[3] = reinterpret_cast<T (*)[3]>(vals + kQ * kVS);
   const int t = threadIdx.x, warp = t / 32, lane = t % 32;
   // the block's parent slots: one, or (items) up to kTcBoxes slots of one parent cone in other
@@ -496,6 +498,15 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
   // geometry serves all of them
   for (int b = 0; b < nsl; ++b) {
     const int pslot = slots[b], P = __ldg(A.slot_box + pslot);
+    // the child slot of every (octant, parent point) of this slot, so that a run finds its child
+    // coefficients with one shared-memory read (the barrier after the clearing of vals below
+    // publishes it; the barrier that ends the previous slot's last right-hand side retired the
+    // previous table's readers)
+    for (int e = t; e < 8 * kQ; e += blockDim.x) {
+      const int o = e / kQ, q = e % kQ;
+      const int cb = __ldg(A.child + 8 * P + o);
+      if (cb >= 0) cslot[o][q] = __ldg(A.cmap_c + (size_t)cb * A.ncomp_c + __ldg(A.up_cc + ((size_t)ci * 8 + o) * kQ + q));
+    }
     for (int rb = 0; rb < nrhs; ++rb) {
       const T* coefs_c = A.coefs_c + rb * A.cstride_c;
       for (int e = t; e < kQ * kVS; e += blockDim.x) vals[e] = T(0);
@@ -510,9 +521,7 @@ __global__ void __launch_bounds__(32 * kUpRunWarps, 4) k_up_runs(UpArgs<float> A
         const int myq = lane < len ? __ldg(RT.order + g * kQ + r0 + lane) : 0;
         // one child slot per run (the host marked every such cone relevant)
         const int q0 = __shfl_sync(0xffffffffu, myq, 0);
-        const int cs0 =
-            __ldg(A.cmap_c + (size_t)__ldg(A.child + 8 * P + o) * A.ncomp_c + __ldg(A.up_cc + g * kQ + q0));
-        const T* Cg = coefs_c + (size_t)cs0 * kQ * 32 + lane;
+        const T* Cg = coefs_c + (size_t)cslot[o][q0] * kQ * 32 + lane;
         T c[kQ];
 #pragma unroll
         for (int k = 0; k < kQ; ++k) c[k] = __ldg(Cg + k * 32);
