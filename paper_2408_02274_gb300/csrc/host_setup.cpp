@@ -695,6 +695,17 @@ void build_tree(HostTree& t, const double* x, int N, double leaf_size, int min_l
               Pp.tc_item.push_back(c + j < b ? (int32_t)(key[c + j] & 0xffffffff) : -1);
           a = b;
         }
+        // items in the order of their first slot (slots are numbered box by box, boxes in Morton
+        // order): the items running at one time then read the child coefficients of neighbouring
+        // boxes, which stay in L2 for all of them, instead of one cone's children everywhere
+        const size_t ni = Pp.tc_item.size() / kTcBoxes;
+        std::vector<int64_t> io(ni);
+        for (size_t i = 0; i < ni; ++i) io[i] = ((int64_t)Pp.tc_item[i * kTcBoxes] << 32) | (int64_t)i;
+        std::sort(io.begin(), io.end());
+        std::vector<int32_t> items(Pp.tc_item.size());
+        for (size_t i = 0; i < ni; ++i)
+          std::copy_n(&Pp.tc_item[(size_t)(io[i] & 0xffffffff) * kTcBoxes], kTcBoxes, &items[i * kTcBoxes]);
+        Pp.tc_item.swap(items);
       }
     }
     // chunks of at most 32 consecutive targets of one box (boxes with cousins): the unit of the
