@@ -182,6 +182,103 @@ __global__ void __launch_bounds__(kUpThreads) k_up_pass(UpArgs<float> A, int ks)
   vals_to_coefs_block<T, kS, NC>(M, vals, A.coefs_p + (size_t)pslot * kQ * NC, 1);
 }
 
+// (b) by runs: the host's run tables (per parent cone, the points of one octant in one child
+// cone, at most 32, in four fixed point groups, one per warp) let a warp load its child cone's
+// coefficients once per run into registers, 75 per lane, lane = column (NC lanes per point, the
+// 32 / NC lane groups holding the same column set), and sweep the run's points 32 / NC at a time.
+// The prologue puts each (octant, parent point)'s child slot, Chebyshev values and re-centring
+// factor (kernel ks) in shared memory.  A warp adds only into its own group's points.
+template <int NC>
+__global__ void __launch_bounds__(32 * kUpGroups, 4) k_up_pass_runs(UpArgs<float> A, const int* __restrict__ order,
+                                                                     const int* __restrict__ task,
+                                                                     const int* __restrict__ task_ptr, int ks) {
+  using T = float;
+  constexpr int kS = NC + 1;
+  constexpr int kP = 32 / NC;   // points per warp step
+  __shared__ SmallMaps<T> M;
+  __shared__ T Xp[kQ][3];
+  __shared__ int cslot[8][kQ];
+  __shared__ __align__(16) T pt[8][kQ][16];   // T_0..2(ts), T_0..4(tt), T_0..4(tp), Re f, Im f
+  __shared__ T vals[kQ * kS];
+  const int pslot = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  init_maps(M);
+  const int P = A.slot_box[pslot], ci = A.slot_upidx[pslot];
+  const cone_key pcone = A.slot_cone[pslot];
+  __syncthreads();
+  if (t < kQ) cone_point(M, A.cgp, pcone, t, Xp[t]);
+  for (int e = t; e < kQ * kS; e += blockDim.x) vals[e] = 0;
+  __syncthreads();
+  const T off = (T)(0.5 * A.Hc);
+  const T kap = ks ? A.ki : A.ke;
+  for (int e = t; e < 8 * kQ; e += blockDim.x) {
+    const int o = e / kQ, q = e % kQ;
+    const int cb = A.child[8 * P + o];
+    if (cb < 0) continue;
+    const T ox = (o & 1) ? off : -off, oy = (o & 2) ? off : -off, oz = (o & 4) ? off : -off;
+    const T x = Xp[q][0] - ox, y = Xp[q][1] - oy, z = Xp[q][2] - oz;
+    const int ccx = A.up_cc[((size_t)ci * 8 + o) * kQ + q];
+    const cone_key cc = A.ckeys_c[ccx];
+    cslot[o][q] = A.cmap_c[(size_t)cb * A.ncomp_c + ccx];
+    T ts, tt, tp, rc, sth, cth, sph, cph;
+    local_coords(A.cgc, cc, x, y, z, &ts, &tt, &tp, &rc, &sth, &cth, &sph, &cph);
+    T* Q = pt[o][q];
+    cheb_vals<T, 3>(ts, Q);
+    cheb_vals<T, 5>(tt, Q + 3);
+    cheb_vals<T, 5>(tp, Q + 8);
+    // re-centring factor G(x, x_child)/G(x, x_parent) = (r_p/r_c) e^{i k (r_c - r_p)}
+    const T rp = sqrt_t(Xp[q][0] * Xp[q][0] + Xp[q][1] * Xp[q][1] + Xp[q][2] * Xp[q][2]);
+    const T dr = (T(3) * off * off - T(2) * (Xp[q][0] * ox + Xp[q][1] * oy + Xp[q][2] * oz)) / (rc + rp);
+    T sn, cs;
+    sincos_t(kap * dr, &sn, &cs);
+    Q[13] = rp / rc * cs;
+    Q[14] = rp / rc * sn;
+  }
+  __syncthreads();
+  const int col = lane % NC, sub = lane / NC;
+  const bool odd = col & 1;
+  const int w0 = task_ptr[(size_t)ci * kUpGroups + warp], w1 = task_ptr[(size_t)ci * kUpGroups + warp + 1];
+  for (int w = w0; w < w1; ++w) {
+    const int tk = task[w];
+    const int r0 = tk & 255, len = (tk >> 8) & 255, o = (tk >> 16) & 7;
+    if (A.child[8 * P + o] < 0) continue;   // uniform per warp
+    const size_t g = (size_t)ci * 8 + o;
+    const int myq = lane < len ? order[g * kQ + r0 + lane] : 0;
+    // one child slot per run (the host marked every such cone relevant)
+    const T* C = A.coefs_c + (size_t)cslot[o][__shfl_sync(0xffffffffu, myq, 0)] * kQ * NC + col;
+    T c[kQ];
+#pragma unroll
+    for (int k = 0; k < kQ; ++k) c[k] = __ldg(C + k * NC);
+    for (int a = 0; a < len; a += kP) {
+      const int pi = a + sub;
+      const bool on = pi < len;   // equal for both lanes of a (re, im) pair
+      const int q = __shfl_sync(0xffffffffu, myq, on ? pi : 0);
+      const T* Q = pt[o][q];
+      T v = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        T ei = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          T dj = 0;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) dj += Q[8 + k] * c[(i * 5 + j) * 5 + k];
+          ei += Q[3 + j] * dj;
+        }
+        v += Q[i] * ei;
+      }
+      const T wv = __shfl_xor_sync(0xffffffffu, v, 1);
+      if (on) {
+        const T re = odd ? wv : v, im = odd ? v : wv;
+        const T fr = Q[13], fi = Q[14];
+        vals[q * kS + col] += odd ? (re * fi + im * fr) : (re * fr - im * fi);
+      }
+    }
+  }
+  __syncthreads();
+  vals_to_coefs_block<T, kS, NC>(M, vals, A.coefs_p + (size_t)pslot * kQ * NC, 1);
+}
+
 // (c): a warp per target; its (target, cone segment) pairs are taken 32 at a time for the
 // scalars (one pair per lane, centred factor of kernel ks only) and 32 / NC at a time for the
 // contraction (NC lanes per pair, one column each); the lanes of equal column sum at the end.
@@ -275,7 +372,16 @@ cudaError_t run_passes(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
                             L.cmap, L.ncomp, L.ckeys, cone_geom_t<float>(L.cg), L.H, Pp.up_cc,
                             (const float*)L.coefs, (float*)Pp.coefs, ke, ki, 0, 0, nullptr, 0};
             rec = timer_begin(p, TK_UP, s);
-            if (Pp.nslots > 0) k_up_pass<NC><<<(unsigned)Pp.nslots, kUpThreads, 0, s>>>(U, ks);
+            // 16 columns: by runs (1.5-1.6x the all-fields IFGF time per forward map, against 1.9-2.0x
+            // with a task per (point, column)); 2 columns: by tasks (the runs' 16 points per warp step
+            // left the upward step 1.5x slower there)
+            if (Pp.nslots > 0) {
+              if (NC == 16 && Pp.up_task_ptr)
+                k_up_pass_runs<NC><<<(unsigned)Pp.nslots, 32 * kUpGroups, 0, s>>>(U, Pp.up_order, Pp.up_task,
+                                                                                 Pp.up_task_ptr, ks);
+              else
+                k_up_pass<NC><<<(unsigned)Pp.nslots, kUpThreads, 0, s>>>(U, ks);
+            }
             timer_end(p, rec, s);
             ++p->launches;
           }
