@@ -517,6 +517,14 @@ ifgf_status ifgf_tree_level(ifgf_tree tree, int32_t d, int32_t* nboxes, int32_t*
  * start | len << 8 | octant << 16 per (compact cone, group), up_task_ptr [ncompact*4+1]. */
 ifgf_status ifgf_tree_upward(ifgf_tree tree, int32_t d, int64_t* ncompact, int32_t* up_cc, int32_t* up_order,
                              int64_t* ntask, int32_t* up_task, int32_t* up_task_ptr);
+/* level d (3..D-1) as the parent of level d+1: the items of the upward step (Sec. III-G step 3;
+ * the FP32 step per item and the tensor-core step take one item per block): groups of up to 4
+ * slots of level d with one cone key, whose interpolation geometry is therefore shared, taken in
+ * the order (set of child octants, slot), so that slots with equal sets of children tend to share
+ * an item (a block skips the absent children of each slot); items [nitems][4] slot indices, -1
+ * after the last slot of a short item, listed in the order of their first slot.  items may be
+ * NULL (count only). */
+ifgf_status ifgf_tree_items(ifgf_tree tree, int32_t d, int64_t* nitems, int32_t* items);
 /* level d (3..D): per sorted target, the relevant cones (slots of level d) it is evaluated from:
  * tgt_ptr [n+1] (int64), tgt_slot [ninter]; slot_box [nslots] box of each slot */
 ifgf_status ifgf_tree_targets(ifgf_tree tree, int32_t d, int64_t* ninter, int64_t* tgt_ptr,

@@ -27,7 +27,7 @@ EXPORTS = ["ifgf_plan_create", "ifgf_plan_destroy", "ifgf_apply", "ifgf_apply_ba
            "ifgf_precond_get", "ifgf_precond_apply", "ifgf_precond_features", "ifgf_precond_train",
            "ifgf_plan_stats", "ifgf_plan_estimate", "ifgf_set_timing", "ifgf_get_timing", "ifgf_status_string",
            "ifgf_tree_create", "ifgf_tree_destroy", "ifgf_plan_tree", "ifgf_tree_info", "ifgf_tree_perm",
-           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_far_direct_noalloc", "ifgf_far_field",
+           "ifgf_tree_level", "ifgf_tree_targets", "ifgf_tree_upward", "ifgf_tree_items", "ifgf_far_direct_noalloc", "ifgf_far_field",
            "ifgf_plan_tune", "ifgf_plan_check", "ifgf_plan_inject", "ifgf_plan_set_residual",
            "ifgf_precond_block_jacobi"]
 
@@ -135,6 +135,7 @@ def load(path: str = LIB_PATH):
     lib.ifgf_tree_level.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 4 + [vp, vp, vp]
     lib.ifgf_tree_targets.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, vp]
     lib.ifgf_tree_upward.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp, vp, ctypes.POINTER(ctypes.c_int64), vp, vp]
+    lib.ifgf_tree_items.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64), vp]
     lib.ifgf_far_direct_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, i32, vp, vp]
     lib.ifgf_far_field.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     lib.ifgf_plan_tune.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float), vp]
@@ -599,6 +600,16 @@ class Tree:
                                     ctypes.c_void_p(task.ctypes.data), ctypes.c_void_p(ptr.ctypes.data)),
                "ifgf_tree_upward")
         return cc[:nc.value], order[:nc.value], task[:nt.value], ptr
+
+    def items(self, d: int):
+        """items [nitems, 4] of parent level d (3..D-1): slots of one cone and child set, -1 padded."""
+        lib = load()
+        ni = ctypes.c_int64(0)
+        _check(lib.ifgf_tree_items(self.handle, d, ctypes.byref(ni), None), "ifgf_tree_items")
+        it = np.zeros((max(ni.value, 1), 4), dtype=np.int32)
+        _check(lib.ifgf_tree_items(self.handle, d, ctypes.byref(ni), ctypes.c_void_p(it.ctypes.data)),
+               "ifgf_tree_items")
+        return it[:ni.value]
 
     def close(self):
         if self.handle and self.owned:

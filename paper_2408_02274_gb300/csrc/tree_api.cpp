@@ -90,6 +90,14 @@ ifgf_status ifgf_tree_upward(ifgf_tree t, int32_t d, int64_t* ncompact, int32_t*
   return IFGF_OK;
 }
 
+ifgf_status ifgf_tree_items(ifgf_tree t, int32_t d, int64_t* nitems, int32_t* items) {
+  if (!t || d < 3 || d >= t->D) return IFGF_EINVAL;
+  const HostLevel& L = t->lv[d];
+  if (nitems) *nitems = (int64_t)(L.tc_item.size() / kTcBoxes);
+  if (items) std::memcpy(items, L.tc_item.data(), sizeof(int32_t) * L.tc_item.size());
+  return IFGF_OK;
+}
+
 ifgf_status ifgf_tree_targets(ifgf_tree t, int32_t d, int64_t* ninter, int64_t* tgt_ptr, int32_t* tgt_slot,
                               int32_t* slot_box) {
   if (!t || d < 3 || d > t->D) return IFGF_EINVAL;

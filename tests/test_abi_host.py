@@ -261,6 +261,37 @@ def test_fields_per_pass_memory_and_options():
         assert err.value.status == lib.IFGF_EUNSUPPORTED
 
 
+def test_upward_items_group_slots_of_one_cone_and_child_set():
+    """The upward step's items (the FP32 step per item, the tensor-core step): every slot of the
+    parent level lies in exactly one item; an item's slots share their cone key, on which the
+    item's one prologue depends, and come in the order (set of child octants, slot); -1 only
+    after an item's last slot; items in the order of their first slot."""
+    prob = sphere_problem(2.0, 2, 6, 4.0)
+    x, _, _ = prob.nodes()
+    tree = lib.Tree(x, leaf_size=0.25, k_max=prob.k_int, ns0=2, na0=3)
+    assert tree.levels >= 5
+    for d in range(3, tree.levels):
+        coords, ptr, cones, _, _ = tree.level(d)
+        present = set(map(tuple, tree.level(d + 1)[0].tolist()))
+        box_of_slot = np.repeat(np.arange(ptr.size - 1), np.diff(ptr))
+        mask = [sum(1 << o for o in range(8)
+                    if (2 * c[0] + (o & 1), 2 * c[1] + ((o >> 1) & 1), 2 * c[2] + (o >> 2)) in present)
+                for c in coords.tolist()]
+        it = tree.items(d)
+        assert it.shape[1] == 4 and it.shape[0] >= (cones.size + 3) // 4
+        assert sorted(it[it >= 0].tolist()) == list(range(cones.size))
+        for row in it:
+            k = int(np.sum(row >= 0))
+            assert k >= 1 and np.all(row[:k] >= 0) and np.all(row[k:] == -1)
+            assert len(set(cones[row[:k]].tolist())) == 1
+            ks = [(mask[box_of_slot[j]], int(j)) for j in row[:k]]
+            assert ks == sorted(ks) and len(set(ks)) == k
+        assert np.all(np.diff(it[:, 0]) > 0)
+    with pytest.raises(lib.IfgfError):
+        tree.items(tree.levels)
+    tree.close()
+
+
 def test_upward_run_tables_partition_every_parent_point():
     """The upward tables of each parent level: per (compact cone, octant) the ranking is a
     permutation of the 75 points; the runs of a (compact cone, warp group) cover each
