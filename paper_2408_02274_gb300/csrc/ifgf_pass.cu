@@ -376,11 +376,14 @@ cudaError_t run_passes(ifgf_plan_t* p, cudaStream_t s, int nrhs) {
             // with a task per (point, column)); 2 columns: by tasks (the runs' 16 points per warp step
             // left the upward step 1.5x slower there)
             if (Pp.nslots > 0) {
-              if (NC == 16 && Pp.up_task_ptr)
-                k_up_pass_runs<NC><<<(unsigned)Pp.nslots, 32 * kUpGroups, 0, s>>>(U, Pp.up_order, Pp.up_task,
-                                                                                 Pp.up_task_ptr, ks);
-              else
-                k_up_pass<NC><<<(unsigned)Pp.nslots, kUpThreads, 0, s>>>(U, ks);
+              bool runs = false;
+              if constexpr (NC == 16) {
+                runs = Pp.up_task_ptr != nullptr;
+                if (runs)
+                  k_up_pass_runs<NC><<<(unsigned)Pp.nslots, 32 * kUpGroups, 0, s>>>(U, Pp.up_order, Pp.up_task,
+                                                                                   Pp.up_task_ptr, ks);
+              }
+              if (!runs) k_up_pass<NC><<<(unsigned)Pp.nslots, kUpThreads, 0, s>>>(U, ks);
             }
             timer_end(p, rec, s);
             ++p->launches;
