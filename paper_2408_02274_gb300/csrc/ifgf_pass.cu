@@ -6,9 +6,10 @@
 //   F = 8: one kernel per traversal, 2 traversals, coefficient rows of 16 reals (half the
 //          interpolation memory of IFGF_Vec);
 //   F = 1: IFGF_Seq, 16 traversals, rows of 2 reals (1/16 of the memory).
-// Each traversal repeats the work that IFGF_Vec shares between the fields of a pair: the source
-// distances and kernel values at the leaves, the cone coordinates and re-centring factors of the
-// upward step, and the target coordinates and centred factors.  Coefficients are stored per cone
+// Each traversal repeats the work that IFGF_Vec shares among all 16 fields: the source distances
+// and kernel values at the leaves, the cone coordinates and re-centring factors of the upward
+// step, and the target coordinates and centred factors.  The upward step runs by the host's runs
+// (register-resident child coefficients) for F = 8 and by (point, column) tasks for F = 1.  Coefficients are stored per cone
 // segment as [75][NC] reals, NC = 2F (Chebyshev index, then the group's fields, re/im interleaved).
 // FP32 arithmetic (the FP32 and mixed plans), the same formulas as the all-fields kernels.
 #include "ifgf_dev.cuh"
